@@ -1,0 +1,286 @@
+// CPU ORACLE — test infrastructure only (see philox.hpp for the rule).
+//
+// C entry points of the oracle for the test suite (loaded with ctypes). State
+// blocks use the same word format as the product library's boundary (each
+// model's pack/unpack documents it); everything else is the oracle's own.
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "despot.hpp"
+
+using namespace orc;
+
+extern "C" {
+
+typedef struct {
+  int32_t kind;  // 0 grid (1 robot), 1 multigrid (2 robots), 2 car
+  int32_t n, m, P;
+  float gamma;
+  int32_t K, D;
+  uint64_t seed;
+  uint32_t plan_step;
+  const int32_t* rock_cells;  // m entries, x | y << 8
+  float path_len, dt, ped_speed, sigma;
+  double fail_p;
+  int32_t fp64;  // 1: FP64 oracle, 0: FP32 oracle
+} orc_model;
+
+typedef struct {
+  int32_t threads, rounds;
+  double c_a, c_o, xi, target_gap;
+} orc_search_params;
+
+typedef struct {
+  double root_u, root_l;
+  int32_t action, nodes, expansions, rounds;
+  uint64_t steps, signature;
+} orc_search_result;
+
+void orc_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int32_t rounds, uint32_t* out) {
+  Block4 b = philox4x32(ctr, k0, k1, rounds);
+  for (int i = 0; i < 4; ++i) out[i] = b.w[i];
+}
+
+void orc_scenario_random(uint64_t seed, uint32_t scen, uint32_t depth, uint32_t purpose, uint32_t element,
+                         uint32_t plan_step, uint32_t* out) {
+  Block4 b = scenario_random(seed, scen, depth, purpose, element, plan_step);
+  for (int i = 0; i < 4; ++i) out[i] = b.w[i];
+}
+
+void orc_sensor_thresholds(int32_t max_d2, uint64_t* out) {
+  std::vector<uint64_t> t = sensor_thresholds(max_d2);
+  std::memcpy(out, t.data(), t.size() * 8);
+}
+
+void orc_gamma_powers(float gamma, int32_t n, float* out32, double* out64) {
+  std::vector<float> g32 = gamma_powers<float>(gamma, n);
+  std::vector<double> g64 = gamma_powers<double>(gamma, n);
+  for (int i = 0; i < n; ++i) {
+    out32[i] = g32[i];
+    out64[i] = g64[i];
+  }
+}
+
+}  // extern "C"
+
+namespace {
+
+const std::vector<double>& cached_gauss() {
+  static std::once_flag once;
+  static std::vector<double> t;
+  std::call_once(once, [] { t = gauss_table_f64(); });
+  return t;
+}
+
+template <class Real>
+RockSample<Real> make_rs(const orc_model* d) {
+  RockSample<Real> m;
+  m.n = d->n;
+  m.m = d->m;
+  m.robots = d->kind == 1 ? 2 : 1;
+  m.gamma = d->gamma;
+  m.K = d->K;
+  m.D = d->D;
+  m.seed = d->seed;
+  m.plan_step = d->plan_step;
+  for (int i = 0; i < d->m; ++i) {
+    m.rock_x[i] = d->rock_cells[i] & 0xFF;
+    m.rock_y[i] = (d->rock_cells[i] >> 8) & 0xFF;
+  }
+  m.init();
+  return m;
+}
+
+template <class Real>
+Car<Real> make_car(const orc_model* d) {
+  Car<Real> m;
+  m.P = d->P;
+  m.gamma = d->gamma;
+  m.K = d->K;
+  m.D = d->D;
+  m.seed = d->seed;
+  m.plan_step = d->plan_step;
+  m.path_len = d->path_len;
+  m.dt = d->dt;
+  m.ped_speed = d->ped_speed;
+  m.sigma = d->sigma;
+  m.fail_p = d->fail_p;
+  m.G = gamma_powers<Real>(m.gamma, 256);
+  const std::vector<double>& g = cached_gauss();
+  m.gauss.resize(4096);
+  for (int i = 0; i < 4096; ++i) m.gauss[i] = (Real)g[i];
+  m.fail_thresh = (uint64_t)std::floor(m.fail_p * 4294967296.0);
+  return m;
+}
+
+Hist hist_from(const int8_t* h) {
+  Hist x{};
+  if (h)
+    for (int i = 0; i < 32; ++i) x.c[i] = h[i];
+  return x;
+}
+
+// Runs `f(model)` with the model the descriptor names.
+template <class F>
+int with_model(const orc_model* d, F f) {
+  if (d->kind == 0 || d->kind == 1) {
+    if (d->fp64)
+      f(make_rs<double>(d));
+    else
+      f(make_rs<float>(d));
+    return 0;
+  }
+  if (d->kind == 2) {
+    if (d->fp64)
+      f(make_car<double>(d));
+    else
+      f(make_car<float>(d));
+    return 0;
+  }
+  return 1;
+}
+
+template <class M>
+auto unpack_all(const M& m, const uint32_t* block, int cap, int count) {
+  using S = decltype(m.unpack(block, cap, 0));
+  std::vector<S> v(count);
+  for (int i = 0; i < count; ++i) v[i] = m.unpack(block, cap, i);
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+void orc_gauss_table(double* out64, float* out32) {
+  const std::vector<double>& g = cached_gauss();
+  for (int i = 0; i < 4096; ++i) {
+    out64[i] = g[i];
+    out32[i] = (float)g[i];
+  }
+}
+
+int32_t orc_state_words(const orc_model* d) {
+  if (d->kind == 2) return 4 + 2 * d->P + (d->P + 3) / 4;
+  return 5;
+}
+
+// g for each scenario i of a block: (s', z, r) = g(s_i, actions[i], phi_depth).
+int32_t orc_step(const orc_model* d, const uint32_t* in_block, int32_t cap, int32_t count,
+                 const int32_t* actions, int32_t depth, uint32_t* out_block, int32_t out_cap, uint64_t* keys,
+                 double* rewards) {
+  return with_model(d, [&](const auto& m) {
+    auto st = unpack_all(m, in_block, cap, count);
+    for (int i = 0; i < count; ++i) {
+      auto next = st[i];
+      uint64_t key;
+      auto r = m.step(st[i], actions[i], depth, next, &key);
+      m.pack(next, out_block, out_cap, i);
+      keys[i] = key;
+      rewards[i] = (double)r;
+    }
+  });
+}
+
+// Default-policy value (Eq. lb for one scenario) from each state at start_depth;
+// hist holds 32 counters per scenario.
+int32_t orc_rollout(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,
+                    int32_t start_depth, double* values, uint64_t* steps) {
+  return with_model(d, [&](const auto& m) {
+    auto st = unpack_all(m, block, cap, count);
+    uint64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+      uint64_t s = 0;
+      values[i] = (double)rollout(m, st[i], hist_from(hist ? hist + 32 * i : nullptr), start_depth, &s);
+      total += s;
+    }
+    *steps = total;
+  });
+}
+
+// Heuristic u of each state and the horizon tail l.
+int32_t orc_bounds(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count, double* upper,
+                   double* tail) {
+  return with_model(d, [&](const auto& m) {
+    auto st = unpack_all(m, block, cap, count);
+    for (int i = 0; i < count; ++i) {
+      upper[i] = (double)m.upper(st[i]);
+      tail[i] = (double)m.tail(st[i]);
+    }
+  });
+}
+
+int32_t orc_policy(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,
+                   int32_t* actions) {
+  return with_model(d, [&](const auto& m) {
+    auto st = unpack_all(m, block, cap, count);
+    for (int i = 0; i < count; ++i) actions[i] = m.policy(st[i], hist_from(hist ? hist + 32 * i : nullptr));
+  });
+}
+
+// Leaf initialisation of one leaf (see despot.hpp). Output arrays are sized
+// na, na*(cap+1), na*cap and na*n; leaf_block gets the leaf's n states.
+int32_t orc_expand(const orc_model* d, const uint32_t* parent_block, int32_t parent_cap, int32_t parent_count,
+                   const uint16_t* idx, int32_t n, int32_t last_action, int32_t depth, const int8_t* hist,
+                   int32_t a0, int32_t na, int32_t cap, uint32_t* leaf_block, int32_t* child_count,
+                   int32_t* child_off, uint64_t* key, int64_t* rew, int64_t* u, int64_t* l, uint16_t* perm,
+                   uint64_t* steps) {
+  return with_model(d, [&](const auto& m) {
+    auto parent = unpack_all(m, parent_block, parent_cap, parent_count);
+    using S = typename decltype(parent)::value_type;
+    ExpandOut<S> e;
+    expand_leaf(m, parent, idx, n, last_action, depth, hist_from(hist), a0, na, cap, e);
+    if (leaf_block)
+      for (int i = 0; i < n; ++i) m.pack(e.leaf[i], leaf_block, n, i);
+    std::memcpy(child_count, e.child_count.data(), na * 4);
+    std::memcpy(child_off, e.child_off.data(), e.child_off.size() * 4);
+    std::memcpy(key, e.key.data(), e.key.size() * 8);
+    std::memcpy(rew, e.rew.data(), e.rew.size() * 8);
+    std::memcpy(u, e.u.data(), e.u.size() * 8);
+    std::memcpy(l, e.l.data(), e.l.size() * 8);
+    std::memcpy(perm, e.perm.data(), e.perm.size() * 2);
+    *steps = e.steps;
+  });
+}
+
+// One planning step of the tree search from the given root scenarios.
+int32_t orc_plan(const orc_model* d, const uint32_t* root_block, int32_t n, const int8_t* hist,
+                 const orc_search_params* p, orc_search_result* out, int32_t* root_na) {
+  return with_model(d, [&](const auto& m) {
+    auto st = unpack_all(m, root_block, n, n);
+    using S = typename decltype(st)::value_type;
+    SearchParams prm;
+    prm.threads = p->threads;
+    prm.rounds = p->rounds;
+    prm.c_a = p->c_a;
+    prm.c_o = p->c_o;
+    prm.xi = p->xi;
+    prm.target_gap = p->target_gap;
+    Despot<std::decay_t<decltype(m)>, S> ds(m, prm);
+    SearchResult r = ds.plan(st, hist_from(hist));
+    out->root_u = r.root_u;
+    out->root_l = r.root_l;
+    out->action = r.action;
+    out->nodes = r.nodes;
+    out->expansions = r.expansions;
+    out->rounds = r.rounds;
+    out->steps = r.steps;
+    out->signature = r.signature;
+    if (root_na)
+      for (size_t a = 0; a < r.root_na.size(); ++a) root_na[a] = r.root_na[a];
+  });
+}
+
+// Optimal D-horizon value of the scenario tree below the given states.
+double orc_exhaustive(const orc_model* d, const uint32_t* block, int32_t n, const int8_t* hist, int32_t depth) {
+  double v = 0;
+  with_model(d, [&](const auto& m) {
+    auto st = unpack_all(m, block, n, n);
+    v = exhaustive_value(m, st, hist_from(hist), depth);
+  });
+  return v;
+}
+
+}  // extern "C"
