@@ -1,0 +1,173 @@
+/*
+ * dsp.h — C ABI of the B300 GPU leaf-expansion library for HyP-DESPOT
+ * (Cai, Luo, Hsu, Lee, "HyP-DESPOT: A Hybrid Parallel Algorithm for Online
+ * Planning under Uncertainty", arXiv:1802.06215).
+ *
+ * The library runs the data-parallel part of the method, leaf-node
+ * initialisation (Sec. III-D): for a batch of DESPOT leaves it steps the
+ * deterministic model g(s, a, phi) for every (leaf, action, scenario)
+ * (Eq. expand), groups each action's scenarios by observation into children
+ * (Eq. newnodes), and initialises each child's upper bound from a heuristic
+ * (Eq. ub) and its lower bound from default-policy rollouts to depth D
+ * (Eq. lb), summed over the child's scenarios. Around it, a host tree search
+ * with several CPU threads, scenario-based PO-UCT and virtual loss (Sec. III-C)
+ * feeds leaves to the GPU.
+ *
+ * Conventions
+ *  - Plain C: no C++ types or exceptions cross this boundary. Every call
+ *    returns a dsp_status; dsp_last_error() gives the calling thread's last
+ *    message.
+ *  - Ownership: the caller allocates and frees every buffer passed in (device
+ *    memory, or mapped pinned host memory where stated). The library owns only
+ *    the opaque dsp_model, its constant tables and its small workspace.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Kernel calls are asynchronous on it unless stated otherwise.
+ *  - State blocks: a scenario set is a uint32 array of `words` fields x
+ *    `cap` scenarios, field-major (scenario i of field f at [f * cap + i]).
+ *      Rock Sample (5 words): f0/f1 robot r as x | y<<8 | exited<<16 (f1 is 0
+ *        with one robot), f2 good-rock mask, f3 sampled-rock mask, f4 scenario
+ *        id.
+ *      Car (4 + 2P + ceil(P/4) words): f0 distance s (float bits),
+ *        f1 speed | terminal<<8, f2 scenario id, f3 zero, P words of
+ *        pedestrian x, P of y (float bits), goals packed four per word.
+ *  - Random numbers: phi_t of scenario id k is Philox4x32-10 (Salmon et al.,
+ *    SC'11) at counter (k, t, purpose<<24 | element, plan_step) under key
+ *    (seed low, seed high); the same under every action (Sec. III-A).
+ *  - Observation keys are 64-bit; bit 62 marks a terminal outcome.
+ *  - Sums over scenarios are int64 fixed point with scale 2^-32, each
+ *    scenario's FP32 value rounded to nearest even before summing, so they are
+ *    exact and independent of summation order.
+ */
+#ifndef DSP_H
+#define DSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DSP_OK = 0,
+  DSP_E_INVALID = 1,     /* bad argument; nothing was launched */
+  DSP_E_OOM = 2,         /* an allocation of the library failed */
+  DSP_E_CUDA = 3,        /* a CUDA runtime call failed (message has the name) */
+  DSP_E_TIMEOUT = 4,     /* a bounded wait ran out (device or host side) */
+  DSP_E_QUEUE_FULL = 5,  /* the device job queue has no free slot */
+  DSP_E_UNSUPPORTED = 6, /* sizes beyond this build's limits */
+  DSP_E_DEVICE = 7       /* a kernel reported an error in its status word */
+} dsp_status;
+
+typedef enum { DSP_MODEL_GRID = 0, DSP_MODEL_MULTIGRID = 1, DSP_MODEL_CAR = 2 } dsp_model_kind;
+
+typedef struct dsp_model dsp_model; /* opaque, owned by the library */
+
+/* The POMDP (Sec. II-A: S, A, Z, T, O, R, gamma) of one task of Sec. IV-A,
+ * with K scenarios and horizon D (Sec. III-A, Eq. lb). Caller-owned POD. */
+typedef struct {
+  int32_t kind;               /* dsp_model_kind */
+  int32_t n;                  /* Rock Sample map side (2..32) */
+  int32_t m;                  /* Rock Sample rocks (1..32) */
+  int32_t P;                  /* car: pedestrians (1..64) */
+  float gamma;                /* discount */
+  int32_t K;                  /* scenarios per planning step (1..512) */
+  int32_t D;                  /* maximum depth (1..250) */
+  uint64_t seed;              /* Philox key */
+  uint32_t plan_step;         /* fourth Philox counter word */
+  const int32_t* rock_cells;  /* host, m entries x | y<<8, distinct cells */
+  float path_len, dt, ped_speed, sigma; /* car: path length, time step, walking speed, noise */
+  double fail_p;              /* car: probability that accelerate/decelerate fails */
+} dsp_model_desc;
+
+/* Creates a model: validates the descriptor, builds its constant tables
+ * (sensor thresholds floor((0.5 + 0.5 * 2^(-d/20)) * 2^32) by squared distance,
+ * FP32 gamma^k, the 4096-entry inverse-normal table) on the host in FP64 and
+ * uploads them to the current device. Returns DSP_E_INVALID on a bad
+ * descriptor, DSP_E_CUDA/DSP_E_OOM on device failure; *out is NULL then. */
+dsp_status dsp_create_model(const dsp_model_desc* desc, dsp_model** out);
+void dsp_destroy_model(dsp_model* model);
+
+int32_t dsp_state_words(const dsp_model* model);  /* words per scenario */
+int32_t dsp_num_actions(const dsp_model* model);  /* |A| */
+/* Max children per action the result arrays need (grid 4, multigrid 10, car
+ * n_scen). */
+int32_t dsp_max_children(const dsp_model* model, int32_t n_scen);
+
+/* Selects the random streams of a planning step (fourth counter word) for
+ * every later call. */
+dsp_status dsp_set_plan_step(dsp_model* model, uint32_t plan_step);
+
+/* Copies a constant table to host memory for checks: which = 0 sensor
+ * thresholds (uint64 per squared distance), 1 gamma^k (float, 256 entries),
+ * 2 inverse-normal table (float, 4096). *count gets the entry count. */
+dsp_status dsp_get_table(const dsp_model* model, int32_t which, void* host_out, int32_t* count);
+
+/* Eq. expand for a batch: for each i < count,
+ *   (out_i, obs_key[i], reward[i]) = g(in_i, actions[i], phi_depth).
+ * in_block (cap in_cap), out_block (cap out_cap), actions, obs_key, reward:
+ * device pointers. Scenarios already terminal stay put with reward 0. */
+dsp_status dsp_step(const dsp_model* model, const uint32_t* in_block, int32_t in_cap, int32_t count,
+                    const int32_t* actions, int32_t depth, uint32_t* out_block, int32_t out_cap,
+                    uint64_t* obs_key, float* reward, void* stream);
+
+/* Eq. lb for single scenarios: value[i] = sum_{t=start}^{D-1} gamma^(t-start) r_t
+ * + gamma^(D-start) l(s_D) of the default policy rolled out from state i
+ * (tail only if the horizon was reached alive). hist: device, 32 int8 belief
+ * counters per scenario, or NULL for all zero. value: device float[count]. */
+dsp_status dsp_rollout(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
+                       const int8_t* hist, int32_t start_depth, float* value, void* stream);
+
+/* One leaf expansion job (Sec. III-D, "MC_simulation": gather, update,
+ * expansion, bounds). Every pointer is device memory (or mapped pinned host
+ * memory). Result arrays are indexed by action a - first_action. */
+typedef struct {
+  const uint32_t* parent; /* state block holding the parent's scenario list */
+  int32_t parent_cap;     /* its capacity (field stride) */
+  int32_t n_scen;         /* |Phi_b|, 1..512 */
+  const uint16_t* idx;    /* n_scen positions of the leaf's scenarios in parent */
+  int32_t last_action;    /* action into this leaf, applied at depth-1 ("update");
+                             -1: parent already holds the leaf's states (a root) */
+  int32_t depth;          /* depth of the leaf, 0..D-1 */
+  int8_t hist[32];        /* belief counters of the leaf's history (per rock) */
+  int32_t first_action, n_actions; /* actions [first, first + n) to expand */
+  int32_t child_cap;      /* result capacity per action (dsp_max_children) */
+  uint32_t* leaf_states;  /* out: the leaf's own states (cap n_scen), or NULL */
+  int32_t* child_count;   /* out: [n_actions] children per action */
+  int32_t* child_off;     /* out: [n_actions][child_cap + 1] offsets into perm */
+  uint64_t* child_key;    /* out: [n_actions][child_cap] observation keys */
+  int64_t* rew_sum;       /* out: [n_actions][child_cap] sum of step rewards */
+  int64_t* u_sum;         /* out: [n_actions][child_cap] sum of u (Eq. ub) */
+  int64_t* l_sum;         /* out: [n_actions][child_cap] sum of rollout values (Eq. lb) */
+  uint16_t* perm;         /* out: [n_actions][n_scen] leaf positions grouped by child,
+                             children in order of first occurrence, members in
+                             position order */
+} dsp_leaf_job;
+
+/* Expands a batch of leaves in one persistent launch. `jobs` is a HOST array
+ * of n_jobs descriptors (copied before return; the buffers it points to must
+ * stay valid until the stream reaches the end of the work). Sums are
+ * fixed point 2^-32. Validation failures return DSP_E_INVALID and launch
+ * nothing. Asynchronous on `stream`. */
+dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
+
+/* Scenario-steps (g calls on live scenarios: update + expansion + rollout
+ * steps) counted by the kernels since the last reset, and the device status
+ * word (0 = fine). Synchronises the device. */
+dsp_status dsp_read_counters(dsp_model* model, uint64_t* scenario_steps, uint32_t* device_status);
+dsp_status dsp_reset_counters(dsp_model* model, void* stream);
+
+/* Measurement support (no counterpart in the paper): launches a kernel of
+ * independent 32-bit integer xor/add chains over 8 CTAs of 256 threads per SM
+ * and returns the integer operations it performs; the caller times it to get
+ * the device's integer issue rate. sink: device, one uint32. */
+dsp_status dsp_alu_probe(uint32_t* sink, int32_t iters, double* ops_per_launch, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* dsp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSP_H */

@@ -206,3 +206,15 @@ class Model:
         f = lib().orc_exhaustive
         f.restype = C.c_double
         return f(C.byref(self.c), _p(block, _U32), C.c_int32(n), _p(h, _I8), C.c_int32(depth))
+
+
+def ops_reset():
+    """Clears the op counter (op-counting mode: primitive operations of the
+    model definitions, counted in the oracle's calls on this thread)."""
+    lib().orc_ops_reset()
+
+
+def ops_read():
+    f = lib().orc_ops_read
+    f.restype = C.c_uint64
+    return int(f())

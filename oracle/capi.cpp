@@ -154,6 +154,9 @@ auto unpack_all(const M& m, const uint32_t* block, int cap, int count) {
 
 extern "C" {
 
+uint64_t orc_ops_read(void) { return op_counter(); }
+void orc_ops_reset(void) { op_counter() = 0; }
+
 void orc_gauss_table(double* out64, float* out32) {
   const std::vector<double>& g = cached_gauss();
   for (int i = 0; i < 4096; ++i) {

@@ -125,6 +125,7 @@ struct Car {
       if (obs) *obs = o;
       return (Real)0;
     }
+    count_ops(10);  // speed change with failure test, advance, car position
     // 1. speed change, failing with probability fail_p
     Block4 ra = scenario_random(seed, s.scen, (uint32_t)depth, kPurposeTransition, 0, plan_step);
     bool fails = (uint64_t)ra.w[0] < fail_thresh;
@@ -138,6 +139,7 @@ struct Car {
     Real stride = (Real)ped_speed * (Real)dt;
     Block4 rp{};
     for (int i = 0; i < P; ++i) {
+      count_ops(28);  // goal, dx, dy, distance (3 + sqrt), compare, 2 div, 2 mul, 2 add, noise 2x(index, load, mul, add)
       Real gx = goal_x(out.goal[i]), gy = goal_y(out.goal[i]);
       Real dx = gx - out.px[i];
       Real dy = gy - out.py[i];
@@ -160,9 +162,11 @@ struct Car {
     Real r = (a == kDecel) ? (Real)(-0.1f) : (Real)0;
     bool collide = false;
     for (int i = 0; i < P; ++i) {
+      count_ops(7);
       Real ex = out.px[i] - cx, ey = out.py[i] - cy;
       if (ex * ex + ey * ey < (Real)1) collide = true;
     }
+    count_ops(6);  // reward, goal test
     if (collide) {
       r = r + (Real)(-1000);
       out.term = true;
@@ -183,7 +187,9 @@ struct Car {
   // maintain.
   int policy(const CarState<Real>& s, const Hist&) const {
     Real cx = car_x(s), cy = car_y();
+    count_ops(4);
     for (int i = 0; i < P; ++i) {
+      count_ops(6);
       Real ex = s.px[i] - cx, ey = s.py[i] - cy;
       if (ex > (Real)0 && ex <= (Real)4 && ey >= (Real)(-1) && ey <= (Real)1) return kDecel;
     }
@@ -197,6 +203,7 @@ struct Car {
     Real ss = s.s;
     int vv = s.v, t = 0;
     while (true) {
+      count_ops(6);
       if (vv < kMaxSpeed) vv += 1;
       ss = ss + (Real)vv * (Real)dt;
       t += 1;

@@ -64,6 +64,7 @@ auto rollout(const M& m, S s, Hist h, int t0, uint64_t* steps) -> decltype(m.upp
     Real r = m.step(s, a, t, next, &key);
     *steps += 1;
     m.observe(h, a, key);
+    count_ops(6);  // loop and terminal tests, discount lookup, multiply, add, depth increment
     v = v + m.G[t - t0] * r;
     s = next;
     t += 1;

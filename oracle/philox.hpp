@@ -17,6 +17,15 @@
 
 namespace orc {
 
+// Op-counting mode: each primitive arithmetic, compare, logic or select
+// operation the model definitions need is counted here (per thread), so the
+// benchmark can state algorithmic operations per scenario-step.
+inline uint64_t& op_counter() {
+  static thread_local uint64_t ops = 0;
+  return ops;
+}
+inline void count_ops(uint64_t k) { op_counter() += k; }
+
 struct Block4 {
   uint32_t w[4];
 };
@@ -47,6 +56,7 @@ inline void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
 // R-round Philox4x32 (R = 10 is the standard generator). The key is bumped by
 // the Weyl constants before every round after the first.
 inline Block4 philox4x32(const uint32_t ctr[4], uint32_t k0, uint32_t k1, int rounds = 10) {
+  count_ops((uint64_t)rounds * 10);
   uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
   for (int r = 0; r < rounds; ++r) {
     if (r > 0) {

@@ -76,14 +76,18 @@ struct RockSample {
   // One robot's part of g: returns its reward, writes its observation.
   int robot_step(RSState& s, int r, int a, int depth, int* z) const {
     *z = 0;
+    count_ops(1);
     if (s.exited[r]) return 0;
     int reward = 0;
+    count_ops(4);  // decode position, dispatch on the action, re-encode
     if (a == 0) {  // north
+      count_ops(2);
       if (s.y[r] == n - 1)
         reward = -100;
       else
         s.y[r] += 1;
     } else if (a == 1) {  // east
+      count_ops(2);
       if (s.x[r] == n - 1) {
         reward = 10;
         s.exited[r] = true;
@@ -91,16 +95,19 @@ struct RockSample {
         s.x[r] += 1;
       }
     } else if (a == 2) {  // south
+      count_ops(2);
       if (s.y[r] == 0)
         reward = -100;
       else
         s.y[r] -= 1;
     } else if (a == 3) {  // west
+      count_ops(2);
       if (s.x[r] == 0)
         reward = -100;
       else
         s.x[r] -= 1;
     } else if (a == 4) {  // sample
+      count_ops(5);  // cell lookup, good test, mask updates
       int i = rock_at(s.x[r], s.y[r]);
       if (i < 0) {
         reward = -100;
@@ -114,6 +121,7 @@ struct RockSample {
         s.sampled |= 1u << i;
       }
     } else {  // sense rock i
+      count_ops(10);  // index, dx, dy, d^2, threshold compare, truth test, reading
       int i = a - 5;
       int dx = s.x[r] - rock_x[i], dy = s.y[r] - rock_y[i];
       int d2 = dx * dx + dy * dy;
@@ -139,6 +147,7 @@ struct RockSample {
       reward += robot_step(out, 1, a1, depth, &z1);
       *key = (uint64_t)(z0 * 3 + z1);
     }
+    count_ops(robots == 1 ? 2 : 6);  // key, terminal test (joint: split action, sum)
     if (terminal(out)) *key |= kTerminalBit;
     return (Real)reward;
   }
@@ -146,6 +155,7 @@ struct RockSample {
   // Readings of the robots encoded in an observation key (for belief counters).
   void observe(Hist& h, int a, uint64_t key) const {
     int z = (int)(key & ~kTerminalBit);
+    count_ops(2 * robots);
     int acts[2], zs[2];
     if (robots == 1) {
       acts[0] = a;
@@ -172,10 +182,13 @@ struct RockSample {
   // (Manhattan distance, lowest index on ties, x-move before y-move), else
   // walk east. "Believed good" = counter > 0 and not yet sampled.
   int robot_policy(const RSState& s, int r, const Hist& h) const {
+    count_ops(1);
     if (s.exited[r]) return 0;
     int best = -1, bestd = 1 << 30;
+    count_ops(4);  // believed-good mask of the counters and sampled rocks, direction choice
     for (int i = 0; i < m; ++i) {
       if (h.c[i] > 0 && !((s.sampled >> i) & 1u)) {
+        count_ops(8);  // |dx| + |dy|, compare, two selects
         int d = std::abs(s.x[r] - rock_x[i]) + std::abs(s.y[r] - rock_y[i]);
         if (d < bestd) {
           bestd = d;
@@ -200,10 +213,12 @@ struct RockSample {
   // robot's Manhattan distance, plus every robot's exit reward after walking
   // straight east. Summed in rock order, then robot order.
   Real upper(const RSState& s) const {
+    count_ops(1);
     if (terminal(s)) return (Real)0;
     Real u = (Real)0;
     for (int i = 0; i < m; ++i) {
       if (!((s.good >> i) & 1u)) continue;
+      count_ops(2 + 6 * robots);  // per robot |dx|+|dy| and min; 10*G[d] and the sum
       int bestd = 1 << 30;
       for (int r = 0; r < robots; ++r) {
         if (s.exited[r]) continue;
@@ -214,12 +229,14 @@ struct RockSample {
     }
     for (int r = 0; r < robots; ++r)
       if (!s.exited[r]) u = u + (Real)10 * G[n - 1 - s.x[r]];
+    count_ops(4 * robots);
     return u;
   }
 
   // Value past the horizon: every robot walks east (achievable).
   Real tail(const RSState& s) const {
     Real l = (Real)0;
+    count_ops(4 * robots);
     for (int r = 0; r < robots; ++r)
       if (!s.exited[r]) l = l + (Real)10 * G[n - 1 - s.x[r]];
     return l;

@@ -1,0 +1,159 @@
+"""ctypes binding of libdsp.so (include/dsp.h): same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module only converts Python
+values and torch tensor addresses into the C arguments. It fails loudly when
+the library has not been built: there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdsp.so")
+
+DSP_OK, DSP_E_INVALID, DSP_E_OOM, DSP_E_CUDA, DSP_E_TIMEOUT, DSP_E_QUEUE_FULL, DSP_E_UNSUPPORTED, DSP_E_DEVICE = range(8)
+STATUS_NAMES = ["DSP_OK", "DSP_E_INVALID", "DSP_E_OOM", "DSP_E_CUDA", "DSP_E_TIMEOUT", "DSP_E_QUEUE_FULL",
+                "DSP_E_UNSUPPORTED", "DSP_E_DEVICE"]
+
+
+class DspError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class dsp_model_desc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("P", C.c_int32), ("gamma", C.c_float),
+        ("K", C.c_int32), ("D", C.c_int32), ("seed", C.c_uint64), ("plan_step", C.c_uint32),
+        ("rock_cells", C.POINTER(C.c_int32)), ("path_len", C.c_float), ("dt", C.c_float),
+        ("ped_speed", C.c_float), ("sigma", C.c_float), ("fail_p", C.c_double),
+    ]
+
+
+class dsp_leaf_job(C.Structure):
+    _fields_ = [
+        ("parent", C.c_void_p), ("parent_cap", C.c_int32), ("n_scen", C.c_int32), ("idx", C.c_void_p),
+        ("last_action", C.c_int32), ("depth", C.c_int32), ("hist", C.c_int8 * 32),
+        ("first_action", C.c_int32), ("n_actions", C.c_int32), ("child_cap", C.c_int32),
+        ("leaf_states", C.c_void_p), ("child_count", C.c_void_p), ("child_off", C.c_void_p),
+        ("child_key", C.c_void_p), ("rew_sum", C.c_void_p), ("u_sum", C.c_void_p), ("l_sum", C.c_void_p),
+        ("perm", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if libdsp.so is missing (build it with
+    paper_1802_06215_b300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -m paper_1802_06215_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        L.dsp_last_error.restype = C.c_char_p
+        L.dsp_create_model.argtypes = [C.POINTER(dsp_model_desc), C.POINTER(C.c_void_p)]
+        L.dsp_destroy_model.argtypes = [C.c_void_p]
+        L.dsp_destroy_model.restype = None
+        for f in ("dsp_state_words", "dsp_num_actions"):
+            getattr(L, f).argtypes = [C.c_void_p]
+            getattr(L, f).restype = C.c_int32
+        L.dsp_max_children.argtypes = [C.c_void_p, C.c_int32]
+        L.dsp_max_children.restype = C.c_int32
+        L.dsp_set_plan_step.argtypes = [C.c_void_p, C.c_uint32]
+        L.dsp_get_table.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]
+        L.dsp_step.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                               C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.dsp_rollout.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                  C.c_void_p]
+        L.dsp_expand_leaves.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+        L.dsp_read_counters.argtypes = [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]
+        L.dsp_reset_counters.argtypes = [C.c_void_p, C.c_void_p]
+        L.dsp_alu_probe.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != DSP_OK:
+        raise DspError(status, lib().dsp_last_error().decode())
+
+
+def dsp_last_error():
+    return lib().dsp_last_error().decode()
+
+
+def desc_from_config(cfg):
+    import numpy as np
+    rocks = np.ascontiguousarray(cfg.rock_cells if cfg.rock_cells is not None else np.zeros(1), dtype=np.int32)
+    d = dsp_model_desc(kind=cfg.kind, n=cfg.n, m=cfg.m, P=cfg.P, gamma=cfg.gamma, K=cfg.K, D=cfg.D, seed=cfg.seed,
+                       plan_step=cfg.plan_step, rock_cells=rocks.ctypes.data_as(C.POINTER(C.c_int32)),
+                       path_len=cfg.path_len, dt=cfg.dt, ped_speed=cfg.ped_speed, sigma=cfg.sigma,
+                       fail_p=cfg.fail_p)
+    d._keep = rocks
+    return d
+
+
+def dsp_create_model(desc):
+    h = C.c_void_p()
+    check(lib().dsp_create_model(C.byref(desc), C.byref(h)))
+    return h
+
+
+def dsp_destroy_model(h):
+    lib().dsp_destroy_model(h)
+
+
+def dsp_state_words(h):
+    return lib().dsp_state_words(h)
+
+
+def dsp_num_actions(h):
+    return lib().dsp_num_actions(h)
+
+
+def dsp_max_children(h, n_scen):
+    return lib().dsp_max_children(h, n_scen)
+
+
+def dsp_set_plan_step(h, plan_step):
+    check(lib().dsp_set_plan_step(h, plan_step))
+
+
+def dsp_get_table(h, which, out_ptr):
+    cnt = C.c_int32(0)
+    check(lib().dsp_get_table(h, which, C.c_void_p(out_ptr), C.byref(cnt)))
+    return cnt.value
+
+
+def dsp_step(h, in_block, in_cap, count, actions, depth, out_block, out_cap, obs_key, reward, stream=0):
+    check(lib().dsp_step(h, C.c_void_p(in_block), in_cap, count, C.c_void_p(actions), depth, C.c_void_p(out_block),
+                         out_cap, C.c_void_p(obs_key), C.c_void_p(reward), C.c_void_p(stream)))
+
+
+def dsp_rollout(h, block, cap, count, hist, start_depth, value, stream=0):
+    check(lib().dsp_rollout(h, C.c_void_p(block), cap, count, C.c_void_p(hist), start_depth, C.c_void_p(value),
+                            C.c_void_p(stream)))
+
+
+def dsp_expand_leaves(h, jobs_array, n_jobs, stream=0):
+    check(lib().dsp_expand_leaves(h, C.cast(jobs_array, C.c_void_p), n_jobs, C.c_void_p(stream)))
+
+
+def dsp_read_counters(h):
+    s = C.c_uint64(0)
+    st = C.c_uint32(0)
+    check(lib().dsp_read_counters(h, C.byref(s), C.byref(st)))
+    return s.value, st.value
+
+
+def dsp_reset_counters(h, stream=0):
+    check(lib().dsp_reset_counters(h, C.c_void_p(stream)))
+
+
+def dsp_alu_probe(sink, iters, stream=0):
+    ops = C.c_double(0)
+    check(lib().dsp_alu_probe(C.c_void_p(sink), iters, C.byref(ops), C.c_void_p(stream)))
+    return ops.value

@@ -1,0 +1,328 @@
+// C ABI of the leaf-expansion library (include/dsp.h): model creation with its
+// constant tables, argument validation, work-unit scheduling and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "model.hpp"
+
+namespace dsp {
+
+static thread_local std::string g_last_error;
+
+dsp_status fail(dsp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+dsp_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? DSP_E_OOM : DSP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Sensor thresholds: floor((0.5 + 0.5 * 2^(-d/20)) * 2^32) per squared distance.
+static void build_thresholds(uint64_t* t, int max_d2) {
+  for (int d2 = 0; d2 <= max_d2; ++d2) {
+    double p = 0.5 + 0.5 * std::exp2(-std::sqrt((double)d2) / 20.0);
+    t[d2] = (uint64_t)std::floor(p * 4294967296.0);
+  }
+}
+
+// Quantile of N(0,1) by Newton's method on Phi(x) - p from x = 0. Phi is
+// convex left of 0 and concave right of it, so the iterates approach the root
+// monotonically from the side of 0.
+static double normal_quantile(double p) {
+  const double inv_sqrt2pi = 0.39894228040143267794;
+  double x = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    double f = 0.5 * std::erfc(-x * 0.70710678118654752440) - p;
+    double d = inv_sqrt2pi * std::exp(-0.5 * x * x);
+    double nx = x - f / d;
+    if (nx == x) break;
+    if (std::fabs(nx - x) <= 1e-17 * std::max(1.0, std::fabs(x))) {
+      x = nx;
+      break;
+    }
+    x = nx;
+  }
+  return x;
+}
+
+}  // namespace dsp
+
+using namespace dsp;
+
+extern "C" {
+
+const char* dsp_last_error(void) { return g_last_error.c_str(); }
+
+dsp_status dsp_create_model(const dsp_model_desc* d, dsp_model** out) {
+  if (!out) return fail(DSP_E_INVALID, "dsp_create_model: out is NULL");
+  *out = nullptr;
+  if (!d) return fail(DSP_E_INVALID, "dsp_create_model: desc is NULL");
+  if (d->kind < 0 || d->kind > 2) return fail(DSP_E_INVALID, "unknown model kind %d", d->kind);
+  if (d->K < 1 || d->K > kMaxScen) return fail(DSP_E_INVALID, "K=%d outside 1..%d", d->K, kMaxScen);
+  if (d->D < 1 || d->D > kGammaLen - 6) return fail(DSP_E_INVALID, "D=%d outside 1..%d", d->D, kGammaLen - 6);
+  if (!(d->gamma > 0.0f && d->gamma <= 1.0f)) return fail(DSP_E_INVALID, "gamma must be in (0, 1]");
+  DevModel* h = new DevModel();
+  std::memset(h, 0, sizeof(DevModel));
+  h->kind = d->kind;
+  h->K = d->K;
+  h->D = d->D;
+  h->seed = d->seed;
+  h->gamma = d->gamma;
+  if (d->kind == DSP_MODEL_GRID || d->kind == DSP_MODEL_MULTIGRID) {
+    if (d->n < 2 || d->n > kMaxSide) {
+      delete h;
+      return fail(DSP_E_INVALID, "map side n=%d outside 2..%d", d->n, kMaxSide);
+    }
+    if (d->m < 1 || d->m > kMaxRocks || !d->rock_cells) {
+      delete h;
+      return fail(DSP_E_INVALID, "rocks m=%d outside 1..%d (or rock_cells NULL)", d->m, kMaxRocks);
+    }
+    h->n = d->n;
+    h->m = d->m;
+    h->robots = d->kind == DSP_MODEL_GRID ? 1 : 2;
+    h->per_robot = 5 + d->m;
+    h->num_actions = h->robots == 1 ? h->per_robot : h->per_robot * h->per_robot;
+    h->words = 5;
+    std::memset(h->cell_rock, 0xFF, sizeof(h->cell_rock));
+    for (int i = 0; i < d->m; ++i) {
+      int x = d->rock_cells[i] & 0xFF, y = (d->rock_cells[i] >> 8) & 0xFF;
+      if (x >= d->n || y >= d->n || h->cell_rock[y * d->n + x] != 0xFF) {
+        delete h;
+        return fail(DSP_E_INVALID, "rock %d at (%d,%d) outside the map or on another rock", i, x, y);
+      }
+      h->rock_xy[i] = x | (y << 8);
+      h->cell_rock[y * d->n + x] = (uint8_t)i;
+    }
+    build_thresholds(h->thresh, 2 * (d->n - 1) * (d->n - 1));
+  } else {
+    if (d->P < 1 || d->P > kMaxPeds) {
+      delete h;
+      return fail(DSP_E_INVALID, "pedestrians P=%d outside 1..%d", d->P, kMaxPeds);
+    }
+    h->P = d->P;
+    h->num_actions = 3;
+    h->words = 4 + 2 * d->P + (d->P + 3) / 4;
+    h->path_len = d->path_len;
+    h->dt = d->dt;
+    h->ped_speed = d->ped_speed;
+    h->sigma = d->sigma;
+    h->stride = d->ped_speed * d->dt;
+    h->fail_thresh = (uint64_t)std::floor(d->fail_p * 4294967296.0);
+    for (int i = 0; i < kGaussLen; ++i) h->gauss[i] = (float)normal_quantile((i + 0.5) / (double)kGaussLen);
+  }
+  for (int k = 0; k < kGammaLen; ++k) h->G[k] = (float)std::pow((double)d->gamma, (double)k);
+
+  dsp_model* m = new dsp_model();
+  m->desc = *d;
+  m->desc.rock_cells = nullptr;
+  m->host = h;
+  m->plan_step = d->plan_step;
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (e == cudaSuccess) e = cudaMalloc(&m->dmodel, sizeof(DevModel));
+  if (e == cudaSuccess) e = cudaMalloc(&m->dwork, sizeof(DevWork));
+  if (e == cudaSuccess) e = cudaMemcpy(m->dmodel, h, sizeof(DevModel), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->dwork, 0, sizeof(DevWork));
+  if (e != cudaSuccess) {
+    dsp_status st = cuda_fail(e, "dsp_create_model");
+    dsp_destroy_model(m);
+    return st;
+  }
+  *out = m;
+  return DSP_OK;
+}
+
+void dsp_destroy_model(dsp_model* m) {
+  if (!m) return;
+  if (m->dmodel) cudaFree(m->dmodel);
+  if (m->dwork) cudaFree(m->dwork);
+  delete m->host;
+  delete m;
+}
+
+int32_t dsp_state_words(const dsp_model* m) { return m ? m->host->words : 0; }
+int32_t dsp_num_actions(const dsp_model* m) { return m ? m->host->num_actions : 0; }
+int32_t dsp_max_children(const dsp_model* m, int32_t n_scen) {
+  if (!m) return 0;
+  int z = m->host->kind == DSP_MODEL_GRID ? 4 : (m->host->kind == DSP_MODEL_MULTIGRID ? 10 : n_scen);
+  return std::min(z, n_scen);
+}
+
+dsp_status dsp_set_plan_step(dsp_model* m, uint32_t plan_step) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_set_plan_step: model is NULL");
+  m->plan_step = plan_step;
+  return DSP_OK;
+}
+
+dsp_status dsp_get_table(const dsp_model* m, int32_t which, void* out, int32_t* count) {
+  if (!m || !out || !count) return fail(DSP_E_INVALID, "dsp_get_table: NULL argument");
+  const DevModel* h = m->host;
+  if (which == 0) {
+    int n = h->kind == DSP_MODEL_CAR ? 0 : 2 * (h->n - 1) * (h->n - 1) + 1;
+    std::memcpy(out, h->thresh, n * sizeof(uint64_t));
+    *count = n;
+  } else if (which == 1) {
+    std::memcpy(out, h->G, sizeof(h->G));
+    *count = kGammaLen;
+  } else if (which == 2) {
+    std::memcpy(out, h->gauss, sizeof(h->gauss));
+    *count = kGaussLen;
+  } else {
+    return fail(DSP_E_INVALID, "dsp_get_table: unknown table %d", which);
+  }
+  return DSP_OK;
+}
+
+dsp_status dsp_step(const dsp_model* m, const uint32_t* in, int32_t in_cap, int32_t count, const int32_t* actions,
+                    int32_t depth, uint32_t* out, int32_t out_cap, uint64_t* keys, float* rewards, void* stream) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_step: model is NULL");
+  if (count < 0 || in_cap < count || out_cap < count) return fail(DSP_E_INVALID, "dsp_step: bad count/capacity");
+  if (count == 0) return DSP_OK;
+  if (!in || !out || !actions || !keys || !rewards) return fail(DSP_E_INVALID, "dsp_step: NULL buffer");
+  if (depth < 0) return fail(DSP_E_INVALID, "dsp_step: negative depth");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (m->host->kind == DSP_MODEL_CAR)
+    e = launch_car_step(m->dmodel, m->host->P, in, in_cap, count, actions, depth, out, out_cap, keys, rewards,
+                        m->plan_step, st);
+  else
+    e = launch_rs_step(m->dmodel, m->host->robots, in, in_cap, count, actions, depth, out, out_cap, keys, rewards,
+                       m->plan_step, st);
+  return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_step launch");
+}
+
+dsp_status dsp_rollout(const dsp_model* m, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,
+                       int32_t start_depth, float* value, void* stream) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_rollout: model is NULL");
+  if (count < 0 || cap < count) return fail(DSP_E_INVALID, "dsp_rollout: bad count/capacity");
+  if (count == 0) return DSP_OK;
+  if (!block || !value) return fail(DSP_E_INVALID, "dsp_rollout: NULL buffer");
+  if (start_depth < 0 || start_depth > m->host->D)
+    return fail(DSP_E_INVALID, "dsp_rollout: start depth %d outside 0..D", start_depth);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (m->host->kind == DSP_MODEL_CAR)
+    e = launch_car_rollout(m->dmodel, m->host->P, m->dwork, block, cap, count, start_depth, value, m->plan_step,
+                           st);
+  else
+    e = launch_rs_rollout(m->dmodel, m->host->robots, m->dwork, block, cap, count, hist, start_depth, value,
+                          m->plan_step, st);
+  return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_rollout launch");
+}
+
+dsp_status dsp_expand_leaves(dsp_model* m, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_expand_leaves: model is NULL");
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(DSP_E_INVALID, "dsp_expand_leaves: bad job array");
+  if (n_jobs == 0) return DSP_OK;
+  std::vector<int4> units;
+  dsp_status vs = plan_units(m, jobs, n_jobs, units);
+  if (vs != DSP_OK) return vs;
+  return launch_expand(m, jobs, n_jobs, units, (cudaStream_t)stream, nullptr);
+}
+
+dsp_status dsp_read_counters(dsp_model* m, uint64_t* steps, uint32_t* status) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_read_counters: model is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_read_counters sync");
+  DevWork w;
+  e = cudaMemcpy(&w, m->dwork, sizeof(DevWork), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_read_counters copy");
+  if (steps) *steps = w.steps;
+  if (status) *status = w.status;
+  return DSP_OK;
+}
+
+dsp_status dsp_reset_counters(dsp_model* m, void* stream) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_reset_counters: model is NULL");
+  cudaError_t e = cudaMemsetAsync(m->dwork, 0, sizeof(DevWork), (cudaStream_t)stream);
+  return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_reset_counters");
+}
+
+}  // extern "C"
+
+namespace dsp {
+
+// Validates the jobs and cuts them into work units (job, first action, count):
+// Rock Sample units hold at most rs_items_per_unit() (action, scenario) items;
+// car units hold one action.
+dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, std::vector<int4>& units) {
+  const DevModel* h = m->host;
+  units.clear();
+  units.reserve((size_t)n_jobs * 4);
+  int items = h->kind == DSP_MODEL_CAR ? 0 : rs_items_per_unit();
+  for (int j = 0; j < n_jobs; ++j) {
+    const dsp_leaf_job& J = jobs[j];
+    if (J.n_scen < 1 || J.n_scen > kMaxScen) return fail(DSP_E_UNSUPPORTED, "job %d: n_scen=%d outside 1..%d", j, J.n_scen, kMaxScen);
+    if (J.n_actions < 1 || J.first_action < 0 || J.first_action + J.n_actions > h->num_actions)
+      return fail(DSP_E_INVALID, "job %d: actions [%d,%d) outside 0..%d", j, J.first_action,
+                  J.first_action + J.n_actions, h->num_actions);
+    if (J.depth < 0 || J.depth >= h->D) return fail(DSP_E_INVALID, "job %d: depth %d outside 0..D-1", j, J.depth);
+    if (J.last_action >= h->num_actions || J.last_action < -1)
+      return fail(DSP_E_INVALID, "job %d: last action %d", j, J.last_action);
+    if (J.last_action >= 0 && J.depth == 0) return fail(DSP_E_INVALID, "job %d: update step at depth 0", j);
+    if (!J.parent || !J.idx || J.parent_cap < 1) return fail(DSP_E_INVALID, "job %d: parent block missing", j);
+    if (J.child_cap < 1 || !J.child_count || !J.child_off || !J.child_key || !J.rew_sum || !J.u_sum || !J.l_sum ||
+        !J.perm)
+      return fail(DSP_E_INVALID, "job %d: result buffer missing", j);
+    if (h->kind == DSP_MODEL_CAR) {
+      for (int a = 0; a < J.n_actions; ++a) units.push_back(make_int4(j, a, 1, 0));
+    } else {
+      int per = std::max(1, items / J.n_scen);
+      for (int a = 0; a < J.n_actions; a += per) units.push_back(make_int4(j, a, std::min(per, J.n_actions - a), 0));
+    }
+  }
+  return DSP_OK;
+}
+
+// Copies the job and unit tables to stream-ordered device memory and launches
+// the persistent expansion kernel; `head` may name a caller-provided counter.
+dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const std::vector<int4>& units,
+                         cudaStream_t st, unsigned int* head_override) {
+  size_t jb = sizeof(dsp_leaf_job) * (size_t)n_jobs;
+  size_t ub = sizeof(int4) * units.size();
+  size_t total = ((jb + 255) & ~(size_t)255) + ((ub + 255) & ~(size_t)255) + 256;
+  unsigned char* buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&buf, total, st);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves: job table");
+  dsp_leaf_job* djobs = (dsp_leaf_job*)buf;
+  int4* dunits = (int4*)(buf + ((jb + 255) & ~(size_t)255));
+  unsigned int* head = (unsigned int*)(buf + ((jb + 255) & ~(size_t)255) + ((ub + 255) & ~(size_t)255));
+  if (head_override) head = head_override;
+  e = cudaMemcpyAsync(djobs, jobs, jb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dunits, units.data(), ub, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(head, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) {
+    const DevModel* h = m->host;
+    if (h->kind == DSP_MODEL_CAR) {
+      e = launch_car_expand(m, djobs, dunits, (int)units.size(), head, st);
+    } else {
+      int block = m->tune_block > 0 ? m->tune_block : 256;
+      int per_sm = rs_expand_blocks_per_sm(h->robots, block);
+      int grid = std::max(1, std::min((int)units.size(), per_sm * m->num_sms));
+      e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, dunits, (int)units.size(), head, m->plan_step,
+                           grid, block, st);
+    }
+  }
+  cudaError_t e2 = cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "dsp_expand_leaves free");
+  return DSP_OK;
+}
+
+}  // namespace dsp

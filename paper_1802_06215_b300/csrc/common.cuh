@@ -1,0 +1,93 @@
+// Shared device-side definitions of the leaf-expansion library: the model's
+// constant block, Philox4x32-10, fixed-point conversion, small helpers.
+#pragma once
+#include <cstdint>
+
+#include "../../include/dsp.h"
+
+namespace dsp {
+
+constexpr int kMaxRocks = 32;
+constexpr int kMaxSide = 32;
+constexpr int kMaxD2 = 2 * (kMaxSide - 1) * (kMaxSide - 1);
+constexpr int kGammaLen = 256;
+constexpr int kGaussLen = 4096;
+constexpr int kMaxPeds = 64;
+constexpr int kMaxScen = 512;
+constexpr uint64_t kTermBit = 1ull << 62;
+
+// Device status word bits.
+constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusBadJob = 2u;
+constexpr uint32_t kStatusOverflow = 4u;
+constexpr uint32_t kStatusKeyClash = 8u;
+
+// Constant block of a model, resident in device memory.
+struct DevModel {
+  int kind, n, m, robots, per_robot, num_actions, P, K, D, words;
+  uint64_t seed;
+  float gamma;
+  float path_len, dt, ped_speed, sigma, stride;
+  uint64_t fail_thresh;
+  int rock_xy[kMaxRocks];               // x | y << 8
+  uint8_t cell_rock[kMaxSide * kMaxSide]; // rock index at cell y*n+x, 0xFF none
+  float G[kGammaLen];                   // gamma^k in FP32
+  uint64_t thresh[kMaxD2 + 1];          // sensor thresholds by squared distance
+  float gauss[kGaussLen];               // inverse-normal table
+};
+
+// Workspace of a model: counters and the status word.
+struct DevWork {
+  unsigned long long steps;
+  unsigned int status;
+};
+
+// ------------------------------------------------------------ Philox ----
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3): ten rounds of
+// two 32x32->64 multiplies with a Weyl key schedule.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                       uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// phi_depth of scenario `scen` for one purpose and element.
+__device__ __forceinline__ U4 scen_random(uint64_t seed, uint32_t scen, uint32_t depth, uint32_t purpose,
+                                          uint32_t element, uint32_t plan_step) {
+  return philox10(scen, depth, (purpose << 24) | (element & 0xFFFFFFu), plan_step, (uint32_t)seed,
+                  (uint32_t)(seed >> 32));
+}
+
+// FP32 value -> int64 fixed point 2^-32, round to nearest even. x * 2^32 is
+// exact in FP32 (power-of-two scale), so this is the exact rounding of x.
+__device__ __forceinline__ long long to_fixed(float x) { return __float2ll_rn(__fmul_rn(x, 4294967296.0f)); }
+
+__device__ __forceinline__ void report(DevWork* w, uint32_t bits) { atomicOr(&w->status, bits); }
+
+// Saturating +-1 update of belief counter i in 32 packed int8 counters.
+__device__ __forceinline__ void hist_add(uint32_t (&h)[8], int i, int delta) {
+  int sh = 8 * (i & 3);
+  int v = (int)(int8_t)((h[i >> 2] >> sh) & 0xFFu) + delta;
+  v = v > 127 ? 127 : (v < -127 ? -127 : v);
+  h[i >> 2] = (h[i >> 2] & ~(0xFFu << sh)) | ((uint32_t)(uint8_t)(int8_t)v << sh);
+}
+__device__ __forceinline__ int hist_get(const uint32_t (&h)[8], int i) {
+  return (int)(int8_t)((h[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+}
+
+}  // namespace dsp

@@ -1,0 +1,37 @@
+// Host-side model object behind the opaque dsp_model handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+struct dsp_model {
+  dsp_model_desc desc;
+  dsp::DevModel* host = nullptr;     // host copy of the constant block
+  dsp::DevModel* dmodel = nullptr;   // device copy
+  dsp::DevWork* dwork = nullptr;     // counters and status word
+  uint32_t plan_step = 0;
+  int device = 0;
+  int num_sms = 0;
+  int tune_block = 0;                // CTA size chosen by the autotuner (0 = default)
+  int tune_tps = 0;                  // car: threads per scenario (0 = default)
+};
+
+namespace dsp {
+
+dsp_status fail(dsp_status st, const char* fmt, ...);
+dsp_status cuda_fail(cudaError_t e, const char* what);
+dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, std::vector<int4>& units);
+dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const std::vector<int4>& units,
+                         cudaStream_t st, unsigned int* head_override);
+
+cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
+                              unsigned int* head, cudaStream_t st);
+cudaError_t launch_car_step(const DevModel* gm, int P, const uint32_t* in, int in_cap, int count,
+                            const int32_t* actions, int depth, uint32_t* out, int out_cap, uint64_t* keys,
+                            float* rewards, uint32_t plan_step, cudaStream_t st);
+cudaError_t launch_car_rollout(const DevModel* gm, int P, DevWork* work, const uint32_t* block, int cap, int count,
+                               int start_depth, float* value, uint32_t plan_step, cudaStream_t st);
+
+}  // namespace dsp

@@ -1,0 +1,247 @@
+// Rock Sample with R robots (R = 1 "grid", R = 2 "multigrid"): the device
+// step function g, observation bookkeeping, heuristic default policy and
+// bound heuristics of the multi-agent Rock Sample task (Sec. IV-A).
+//
+// Rules and readings (the same as the library's documentation states):
+// per-robot actions 0 N (y+1), 1 E (x+1), 2 S (y-1), 3 W (x-1), 4 Sample,
+// 5+i Sense rock i, joint action a0 * (5+m) + a1; moving off the N/S/W border
+// or sampling where no rock lies costs -100 and does nothing; E from the last
+// column exits (+10); sampling a good rock gives +10 and makes it bad, a bad
+// one -10; robots act in index order; exited robots do nothing; a reading of
+// rock i is right iff the Philox word u (purpose 2, element = robot) is below
+// the threshold of the squared Euclidean distance; observation per robot
+// 0 none / 1 good / 2 bad, joint z0 * 3 + z1, bit 62 = terminal.
+#pragma once
+#include "common.cuh"
+
+namespace dsp {
+
+// Scenario state in registers: robot words x | y<<8 | exited<<16, rock masks,
+// scenario id.
+struct RSS {
+  uint32_t pos[2];
+  uint32_t good, sampled, scen;
+};
+
+// Constants a CTA keeps in shared memory.
+struct RSShared {
+  float G[kGammaLen];
+  int rock_xy[kMaxRocks];
+  uint8_t cell_rock[kMaxSide * kMaxSide];
+};
+
+template <int R>
+struct RSModel {
+  const RSShared* sh;
+  const uint64_t* thresh;  // global, read through the read-only path
+  int n, m, per, D;
+  uint64_t seed;
+  uint32_t plan_step;
+
+  __device__ __forceinline__ bool terminal(const RSS& s) const {
+    bool t = (s.pos[0] >> 16) & 1u;
+    if (R == 2) t = t && ((s.pos[1] >> 16) & 1u);
+    return t;
+  }
+
+  __device__ __forceinline__ int robot_step(RSS& s, int r, int a, int depth, int& z) const {
+    z = 0;
+    uint32_t p = s.pos[r];
+    if ((p >> 16) & 1u) return 0;
+    int x = (int)(p & 0xFFu), y = (int)((p >> 8) & 0xFFu);
+    int reward = 0;
+    if (a == 0) {
+      if (y == n - 1) reward = -100; else y += 1;
+    } else if (a == 1) {
+      if (x == n - 1) { reward = 10; p |= 1u << 16; } else x += 1;
+    } else if (a == 2) {
+      if (y == 0) reward = -100; else y -= 1;
+    } else if (a == 3) {
+      if (x == 0) reward = -100; else x -= 1;
+    } else if (a == 4) {
+      int i = sh->cell_rock[y * n + x];
+      if (i == 0xFF) {
+        reward = -100;
+      } else {
+        uint32_t bit = 1u << i;
+        reward = (s.good & bit) ? 10 : -10;
+        s.good &= ~bit;
+        s.sampled |= bit;
+      }
+    } else {
+      int i = a - 5;
+      int rx = sh->rock_xy[i] & 0xFF, ry = sh->rock_xy[i] >> 8;
+      int dx = x - rx, dy = y - ry;
+      U4 rnd = scen_random(seed, s.scen, (uint32_t)depth, 2u, (uint32_t)r, plan_step);
+      bool correct = (uint64_t)rnd.x < __ldg(thresh + dx * dx + dy * dy);
+      bool is_good = (s.good >> i) & 1u;
+      z = (correct == is_good) ? 1 : 2;
+    }
+    s.pos[r] = (p & 0xFFFF0000u) | (uint32_t)x | ((uint32_t)y << 8);
+    return reward;
+  }
+
+  // g(s, a, phi_depth); returns the reward, writes the observation key.
+  __device__ __forceinline__ float step(RSS& s, int a, int depth, uint64_t& key) const {
+    int z0, z1 = 0, rew;
+    if (R == 1) {
+      rew = robot_step(s, 0, a, depth, z0);
+      key = (uint64_t)z0;
+    } else {
+      int a0 = a / per, a1 = a - a0 * per;
+      rew = robot_step(s, 0, a0, depth, z0);
+      rew += robot_step(s, 1, a1, depth, z1);
+      key = (uint64_t)(z0 * 3 + z1);
+    }
+    if (terminal(s)) key |= kTermBit;
+    return (float)rew;
+  }
+
+  // Belief counters of the history after (a, key); `pmask` tracks which
+  // counters are positive.
+  __device__ __forceinline__ void observe_robot(uint32_t (&h)[8], uint32_t& pmask, int ar, int zr) const {
+    if (ar >= 5 && zr != 0) {
+      int i = ar - 5;
+      int delta = zr == 1 ? 1 : -1;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k == (i >> 2)) {
+          uint32_t hw[8];
+          hw[k] = h[k];
+          int sh8 = 8 * (i & 3);
+          int v = (int)(int8_t)((hw[k] >> sh8) & 0xFFu) + delta;
+          v = v > 127 ? 127 : (v < -127 ? -127 : v);
+          h[k] = (hw[k] & ~(0xFFu << sh8)) | ((uint32_t)(uint8_t)(int8_t)v << sh8);
+          pmask = v > 0 ? (pmask | (1u << i)) : (pmask & ~(1u << i));
+        }
+    }
+  }
+  __device__ __forceinline__ void observe(uint32_t (&h)[8], uint32_t& pmask, int a, uint64_t key) const {
+    int z = (int)(key & ~kTermBit);
+    if (R == 1) {
+      observe_robot(h, pmask, a, z);
+    } else {
+      int a0 = a / per;
+      observe_robot(h, pmask, a0, z / 3);
+      observe_robot(h, pmask, a - a0 * per, z % 3);
+    }
+  }
+
+  // Default policy of one robot: sample a believed-good rock underfoot, else
+  // head for the nearest believed-good unsampled rock (Manhattan, lowest
+  // index on ties, x before y), else east.
+  __device__ __forceinline__ int robot_policy(const RSS& s, int r, uint32_t pmask) const {
+    uint32_t p = s.pos[r];
+    if ((p >> 16) & 1u) return 0;
+    int x = (int)(p & 0xFFu), y = (int)((p >> 8) & 0xFFu);
+    uint32_t cand = pmask & ~s.sampled;
+    int best = -1, bestd = 1 << 30;
+    while (cand) {
+      int i = __ffs(cand) - 1;
+      cand &= cand - 1;
+      int rxy = sh->rock_xy[i];
+      int d = abs(x - (rxy & 0xFF)) + abs(y - (rxy >> 8));
+      if (d < bestd) {
+        bestd = d;
+        best = i;
+      }
+    }
+    if (best < 0) return 1;
+    if (bestd == 0) return 4;
+    int rxy = sh->rock_xy[best];
+    int rx = rxy & 0xFF, ry = rxy >> 8;
+    if (rx > x) return 1;
+    if (rx < x) return 3;
+    if (ry > y) return 0;
+    return 2;
+  }
+  __device__ __forceinline__ int policy(const RSS& s, uint32_t pmask) const {
+    if (R == 1) return robot_policy(s, 0, pmask);
+    return robot_policy(s, 0, pmask) * per + robot_policy(s, 1, pmask);
+  }
+
+  // u(phi): each good rock at its nearest live robot's Manhattan distance,
+  // then each live robot's exit, summed in that order in FP32.
+  __device__ __forceinline__ float upper(const RSS& s) const {
+    if (terminal(s)) return 0.0f;
+    float u = 0.0f;
+    uint32_t g = s.good;
+    while (g) {
+      int i = __ffs(g) - 1;
+      g &= g - 1;
+      int rxy = sh->rock_xy[i];
+      int bestd = 1 << 30;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        uint32_t p = s.pos[r];
+        if (!((p >> 16) & 1u)) {
+          int d = abs((int)(p & 0xFFu) - (rxy & 0xFF)) + abs((int)((p >> 8) & 0xFFu) - (rxy >> 8));
+          bestd = d < bestd ? d : bestd;
+        }
+      }
+      u = __fadd_rn(u, __fmul_rn(10.0f, sh->G[bestd]));
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      uint32_t p = s.pos[r];
+      if (!((p >> 16) & 1u)) u = __fadd_rn(u, __fmul_rn(10.0f, sh->G[n - 1 - (int)(p & 0xFFu)]));
+    }
+    return u;
+  }
+
+  // Past the horizon every live robot walks east.
+  __device__ __forceinline__ float tail(const RSS& s) const {
+    float l = 0.0f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      uint32_t p = s.pos[r];
+      if (!((p >> 16) & 1u)) l = __fadd_rn(l, __fmul_rn(10.0f, sh->G[n - 1 - (int)(p & 0xFFu)]));
+    }
+    return l;
+  }
+
+  // Eq. lb for one scenario from depth t0 with belief counters h.
+  __device__ __forceinline__ float rollout(RSS s, uint32_t (&h)[8], uint32_t pmask, int t0,
+                                           unsigned long long& steps) const {
+    float v = 0.0f;
+    int t = t0;
+    while (t < D && !terminal(s)) {
+      int a = policy(s, pmask);
+      uint64_t key;
+      float r = step(s, a, t, key);
+      steps += 1;
+      observe(h, pmask, a, key);
+      v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
+      t += 1;
+    }
+    if (!terminal(s)) v = __fadd_rn(v, __fmul_rn(sh->G[D - t0], tail(s)));
+    return v;
+  }
+
+  __device__ __forceinline__ RSS load(const uint32_t* block, int cap, int i) const {
+    RSS s;
+    s.pos[0] = block[i];
+    s.pos[1] = R == 2 ? block[cap + i] : 0u;
+    s.good = block[2 * cap + i];
+    s.sampled = block[3 * cap + i];
+    s.scen = block[4 * cap + i];
+    return s;
+  }
+  __device__ __forceinline__ void store(const RSS& s, uint32_t* block, int cap, int i) const {
+    block[i] = s.pos[0];
+    block[cap + i] = R == 2 ? s.pos[1] : 0u;
+    block[2 * cap + i] = s.good;
+    block[3 * cap + i] = s.sampled;
+    block[4 * cap + i] = s.scen;
+  }
+};
+
+__device__ __forceinline__ uint32_t positive_mask(const uint32_t (&h)[8], int m) {
+  uint32_t pm = 0;
+#pragma unroll
+  for (int i = 0; i < kMaxRocks; ++i)
+    if (i < m && (int)(int8_t)((h[i >> 2] >> (8 * (i & 3))) & 0xFFu) > 0) pm |= 1u << i;
+  return pm;
+}
+
+}  // namespace dsp

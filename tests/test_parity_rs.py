@@ -1,0 +1,176 @@
+"""GPU vs CPU oracle, Rock Sample models: bit-exact (integer states, keys,
+grouping, fixed-point sums of FP32 values computed in the same order)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_06215_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dsp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06215_b300 import batch, build
+    build.build()
+    return batch
+
+
+CONFIGS = {"rs7_8": I.rs7_8, "rs15_15": I.rs15_15, "mars15_15": I.mars15_15}
+
+
+def _cmp_expand(g, o, n, tag=""):
+    na = len(o["child_count"])
+    assert np.array_equal(g["leaf"], o["leaf"]), tag + " leaf states"
+    assert np.array_equal(g["child_count"], o["child_count"]), tag + " child counts"
+    for a in range(na):
+        nc = int(o["child_count"][a])
+        assert np.array_equal(g["child_off"][a][: nc + 1], o["child_off"][a][: nc + 1]), (tag, a, "off")
+        assert np.array_equal(g["key"][a][:nc], o["key"][a][:nc]), (tag, a, "key")
+        assert np.array_equal(g["rew"][a][:nc], o["rew"][a][:nc]), (tag, a, "rew")
+        assert np.array_equal(g["u"][a][:nc], o["u"][a][:nc]), (tag, a, "u")
+        assert np.array_equal(g["l"][a][:nc], o["l"][a][:nc]), (tag, a, "l")
+    assert np.array_equal(g["perm"], o["perm"]), tag + " perm"
+
+
+def test_tables_match_oracle(dsp):
+    for name, mk in CONFIGS.items():
+        cfg = mk()
+        m = dsp.Model(cfg)
+        t = m.table(0)
+        assert np.array_equal(t, oracle.sensor_thresholds(len(t) - 1)), name
+        g32, _ = oracle.gamma_powers(cfg.gamma, 256)
+        assert np.array_equal(m.table(1), g32), name
+        m.close()
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_step_parity(dsp, name):
+    cfg = CONFIGS[name]()
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    rng = np.random.default_rng(1)
+    N = 4000
+    b = I.rs_block(cfg, N, rng)
+    b[2] &= ~b[3]
+    # a few robots already out of the map
+    b[0, :50] |= 1 << 16
+    acts = rng.integers(0, m.num_actions, N).astype(np.int32)
+    for depth in (0, 7, 89):
+        go, gk, gr = m.step(b, acts, depth)
+        oo, ok, orr = om.step(b, acts, depth)
+        assert np.array_equal(go, oo)
+        assert np.array_equal(gk, ok)
+        assert np.array_equal(gr.astype(np.float64), orr)
+    m.close()
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_rollout_parity(dsp, name):
+    cfg = CONFIGS[name]()
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    rng = np.random.default_rng(2)
+    N = 3000
+    b = I.rs_block(cfg, N, rng)
+    b[2] &= ~b[3]
+    hist = rng.integers(-2, 3, (N, 32)).astype(np.int8)
+    for d0 in (0, 45, 88, cfg.D):
+        gv = m.rollout(b, hist, d0)
+        ov, _ = om.rollout(b, hist, d0)
+        assert np.array_equal(gv.astype(np.float64), ov), d0
+    m.close()
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+def test_expand_parity_ragged(dsp, name):
+    """Ragged |Phi_b| (1..K, several units per job and several jobs per unit
+    size), random depths, roots and updated leaves."""
+    cfg = CONFIGS[name]()
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    njobs = 24 if cfg.kind == I.GRID else 6
+    jobs = I.job_stream(cfg, njobs, 11)
+    jb = dsp.JobBatch(m, jobs)
+    m.reset_counters()
+    jb.run()
+    steps, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    total = 0
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"{name} job {k}")
+        total += o["steps"]
+    assert steps == total
+    m.close()
+
+
+def test_expand_edge_cases(dsp):
+    """|Phi_b| = 1 and the maximum 512; a leaf at depth D-1 (children take the
+    tail heuristic); every child terminal (robot exits); action subsets."""
+    cfg = I.rs15_15().with_(K=512, D=20)
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    rng = np.random.default_rng(4)
+    jobs = []
+    for n, depth, pos, last in [(1, 0, (3, 3), -1), (512, 0, (0, 7), -1), (300, 19, (5, 5), 2),
+                                (77, 5, (14, 2), 0), (512, 10, (13, 13), 1)]:
+        pb = I.rs_block(cfg, n, rng, pos=[pos])
+        idx = np.arange(n, dtype=np.uint16) if depth == 0 else np.sort(rng.permutation(n)).astype(np.uint16)
+        h = I.random_hist(cfg, rng, 6)
+        jobs.append(I.Job(parent=pb, idx=idx, last_action=last, depth=depth, hist=h, first_action=0,
+                          n_actions=m.num_actions))
+    # an action subset
+    j = jobs[3]
+    jobs.append(I.Job(parent=j.parent, idx=j.idx, last_action=j.last_action, depth=j.depth, hist=j.hist,
+                      first_action=4, n_actions=9))
+    jb = dsp.JobBatch(m, jobs)
+    jb.run()
+    res = jb.all_results()
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, a0=j.first_action, na=j.n_actions,
+                      cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"edge {k}")
+    # exit from the last column: the E children are terminal with zero bounds
+    r = res[3]
+    assert r["child_count"][1] == 1 and (int(r["key"][1][0]) >> 62) & 1
+    assert r["u"][1][0] == 0 and r["l"][1][0] == 0
+    m.close()
+
+
+def test_expand_empty_batch(dsp):
+    m = dsp.Model(I.rs7_8())
+    from paper_1802_06215_b300 import _dsp
+    _dsp.dsp_expand_leaves(m.h, None, 0, 0)
+    m.close()
+
+
+def test_expand_full_size_sampled(dsp):
+    """The benchmark's workload (4096 jobs, 15x15 map, 15 rocks, K=500, D=90)
+    in the benchmark's launch configuration; a sample of jobs checked against
+    the oracle, the partition invariant on all of them."""
+    cfg = I.rs15_15()
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    jobs = I.job_stream(cfg, 4096, 0)
+    jb = dsp.JobBatch(m, jobs)
+    jb.run()
+    _, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    for k in range(0, 4096, 211):
+        j = jobs[k]
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"full job {k}")
+    for k in range(4096):
+        r = res[k]
+        n = len(jobs[k].idx)
+        for a in range(m.num_actions):
+            nc = r["child_count"][a]
+            assert r["child_off"][a][nc] == n
+        assert np.all(np.sort(r["perm"], axis=1) == np.arange(n))
+    m.close()
