@@ -151,6 +151,15 @@ typedef struct {
  * nothing. Asynchronous on `stream`. */
 dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
+/* Launch shape of dsp_expand_leaves (the paper's fixed mapping of actions to
+ * blocks and scenarios to threads, Sec. III-D, made a tunable): block = CTA
+ * size of the Rock Sample rollout phase (128, 256 or 512; the car kernel runs
+ * 256), tps = lanes sharing one car scenario (4, 8, 16 or 32; element-level
+ * parallelism). 0 keeps the default (256, 16). Returns DSP_E_INVALID for
+ * other values. */
+dsp_status dsp_set_tuning(dsp_model* model, int32_t block, int32_t tps);
+dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
+
 /* Scenario-steps (g calls on live scenarios: update + expansion + rollout
  * steps) counted by the kernels since the last reset, and the device status
  * word (0 = fine). Synchronises the device. */

@@ -72,6 +72,8 @@ def lib():
         L.dsp_read_counters.argtypes = [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]
         L.dsp_reset_counters.argtypes = [C.c_void_p, C.c_void_p]
         L.dsp_alu_probe.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]
+        L.dsp_set_tuning.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+        L.dsp_get_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -151,6 +153,16 @@ def dsp_read_counters(h):
 
 def dsp_reset_counters(h, stream=0):
     check(lib().dsp_reset_counters(h, C.c_void_p(stream)))
+
+
+def dsp_set_tuning(h, block, tps):
+    check(lib().dsp_set_tuning(h, block, tps))
+
+
+def dsp_get_tuning(h):
+    b, t = C.c_int32(0), C.c_int32(0)
+    check(lib().dsp_get_tuning(h, C.byref(b), C.byref(t)))
+    return b.value, t.value
 
 
 def dsp_alu_probe(sink, iters, stream=0):

@@ -152,6 +152,7 @@ void dsp_destroy_model(dsp_model* m) {
   if (!m) return;
   if (m->dmodel) cudaFree(m->dmodel);
   if (m->dwork) cudaFree(m->dwork);
+  if (m->scratch) cudaFree(m->scratch);
   delete m->host;
   delete m;
 }
@@ -230,10 +231,10 @@ dsp_status dsp_expand_leaves(dsp_model* m, const dsp_leaf_job* jobs, int32_t n_j
   if (!m) return fail(DSP_E_INVALID, "dsp_expand_leaves: model is NULL");
   if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(DSP_E_INVALID, "dsp_expand_leaves: bad job array");
   if (n_jobs == 0) return DSP_OK;
-  std::vector<int4> units;
-  dsp_status vs = plan_units(m, jobs, n_jobs, units);
+  ExpandPlan plan;
+  dsp_status vs = plan_units(m, jobs, n_jobs, plan);
   if (vs != DSP_OK) return vs;
-  return launch_expand(m, jobs, n_jobs, units, (cudaStream_t)stream, nullptr);
+  return launch_expand(m, jobs, n_jobs, plan, (cudaStream_t)stream);
 }
 
 dsp_status dsp_read_counters(dsp_model* m, uint64_t* steps, uint32_t* status) {
@@ -248,6 +249,26 @@ dsp_status dsp_read_counters(dsp_model* m, uint64_t* steps, uint32_t* status) {
   return DSP_OK;
 }
 
+dsp_status dsp_set_tuning(dsp_model* m, int32_t block, int32_t tps) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_set_tuning: model is NULL");
+  if (!(block == 0 || block == 128 || block == 256 || block == 512))
+    return fail(DSP_E_INVALID, "dsp_set_tuning: block %d not in {0,128,256,512}", block);
+  if (m->host->kind == DSP_MODEL_CAR && block != 0 && block != 256)
+    return fail(DSP_E_INVALID, "dsp_set_tuning: the car kernel runs 256-thread CTAs");
+  if (!(tps == 0 || tps == 4 || tps == 8 || tps == 16 || tps == 32))
+    return fail(DSP_E_INVALID, "dsp_set_tuning: tps %d not in {0,4,8,16,32}", tps);
+  m->tune_block = block;
+  m->tune_tps = tps;
+  return DSP_OK;
+}
+
+dsp_status dsp_get_tuning(const dsp_model* m, int32_t* block, int32_t* tps) {
+  if (!m || !block || !tps) return fail(DSP_E_INVALID, "dsp_get_tuning: NULL argument");
+  *block = m->tune_block > 0 ? m->tune_block : 256;
+  *tps = m->tune_tps > 0 ? m->tune_tps : 16;
+  return DSP_OK;
+}
+
 dsp_status dsp_reset_counters(dsp_model* m, void* stream) {
   if (!m) return fail(DSP_E_INVALID, "dsp_reset_counters: model is NULL");
   cudaError_t e = cudaMemsetAsync(m->dwork, 0, sizeof(DevWork), (cudaStream_t)stream);
@@ -258,17 +279,18 @@ dsp_status dsp_reset_counters(dsp_model* m, void* stream) {
 
 namespace dsp {
 
-// Validates the jobs and cuts them into work units (job, first action, count):
-// Rock Sample units hold at most rs_items_per_unit() (action, scenario) items;
-// car units hold one action.
-dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, std::vector<int4>& units) {
+// Validates the jobs and plans the launch: car units are (job, action); Rock
+// Sample jobs get the first index of their rollout items (n_scen * n_actions
+// each, in job order).
+dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan) {
   const DevModel* h = m->host;
-  units.clear();
-  units.reserve((size_t)n_jobs * 4);
-  int items = h->kind == DSP_MODEL_CAR ? 0 : rs_items_per_unit();
+  plan.units.clear();
+  plan.item_base.clear();
+  plan.total_items = 0;
   for (int j = 0; j < n_jobs; ++j) {
     const dsp_leaf_job& J = jobs[j];
-    if (J.n_scen < 1 || J.n_scen > kMaxScen) return fail(DSP_E_UNSUPPORTED, "job %d: n_scen=%d outside 1..%d", j, J.n_scen, kMaxScen);
+    if (J.n_scen < 1 || J.n_scen > kMaxScen)
+      return fail(DSP_E_UNSUPPORTED, "job %d: n_scen=%d outside 1..%d", j, J.n_scen, kMaxScen);
     if (J.n_actions < 1 || J.first_action < 0 || J.first_action + J.n_actions > h->num_actions)
       return fail(DSP_E_INVALID, "job %d: actions [%d,%d) outside 0..%d", j, J.first_action,
                   J.first_action + J.n_actions, h->num_actions);
@@ -281,42 +303,48 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
         !J.perm)
       return fail(DSP_E_INVALID, "job %d: result buffer missing", j);
     if (h->kind == DSP_MODEL_CAR) {
-      for (int a = 0; a < J.n_actions; ++a) units.push_back(make_int4(j, a, 1, 0));
+      for (int a = 0; a < J.n_actions; ++a) plan.units.push_back(make_int4(j, a, 1, 0));
     } else {
-      int per = std::max(1, items / J.n_scen);
-      for (int a = 0; a < J.n_actions; a += per) units.push_back(make_int4(j, a, std::min(per, J.n_actions - a), 0));
+      plan.item_base.push_back(plan.total_items);
+      plan.total_items += (long long)J.n_scen * J.n_actions;
     }
   }
+  if (plan.total_items >= (1LL << 31)) return fail(DSP_E_UNSUPPORTED, "more than 2^31 (action, scenario) items");
   return DSP_OK;
 }
 
-// Copies the job and unit tables to stream-ordered device memory and launches
-// the persistent expansion kernel; `head` may name a caller-provided counter.
-dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const std::vector<int4>& units,
-                         cudaStream_t st, unsigned int* head_override) {
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Copies the job table (and the car's unit table or Rock Sample's item
+// offsets) to stream-ordered device memory, takes the Rock Sample item list
+// from the same allocation and launches the expansion kernels.
+dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
+                         cudaStream_t st) {
+  const DevModel* h = m->host;
+  const bool car = h->kind == DSP_MODEL_CAR;
   size_t jb = sizeof(dsp_leaf_job) * (size_t)n_jobs;
-  size_t ub = sizeof(int4) * units.size();
-  size_t total = ((jb + 255) & ~(size_t)255) + ((ub + 255) & ~(size_t)255) + 256;
+  size_t ub = car ? sizeof(int4) * plan.units.size() : sizeof(long long) * plan.item_base.size();
+  size_t ib = car ? 0 : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
+  size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
   unsigned char* buf = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&buf, total, st);
-  if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves: job table");
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves: work buffers");
   dsp_leaf_job* djobs = (dsp_leaf_job*)buf;
-  int4* dunits = (int4*)(buf + ((jb + 255) & ~(size_t)255));
-  unsigned int* head = (unsigned int*)(buf + ((jb + 255) & ~(size_t)255) + ((ub + 255) & ~(size_t)255));
-  if (head_override) head = head_override;
+  void* dunits = buf + align256(jb);
+  unsigned int* counters = (unsigned int*)(buf + align256(jb) + align256(ub));
+  uint32_t* items = (uint32_t*)(buf + align256(jb) + align256(ub) + 256);
   e = cudaMemcpyAsync(djobs, jobs, jb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dunits, units.data(), ub, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(head, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dunits, car ? (const void*)plan.units.data() : (const void*)plan.item_base.data(), ub,
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 256, st);
   if (e == cudaSuccess) {
-    const DevModel* h = m->host;
-    if (h->kind == DSP_MODEL_CAR) {
-      e = launch_car_expand(m, djobs, dunits, (int)units.size(), head, st);
+    if (car) {
+      e = launch_car_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, st);
     } else {
-      int block = m->tune_block > 0 ? m->tune_block : 256;
-      int per_sm = rs_expand_blocks_per_sm(h->robots, block);
-      int grid = std::max(1, std::min((int)units.size(), per_sm * m->num_sms));
-      e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, dunits, (int)units.size(), head, m->plan_step,
-                           grid, block, st);
+      int block_b = m->tune_block > 0 ? m->tune_block : 256;
+      e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, (const long long*)dunits, n_jobs,
+                           plan.total_items, items, counters, m->plan_step, m->num_sms, block_b, st);
     }
   }
   cudaError_t e2 = cudaFreeAsync(buf, st);

@@ -1,16 +1,300 @@
-// Car-among-pedestrians kernels (placeholder until the car path lands).
+// Leaf expansion for the car among pedestrians, one persistent kernel: each
+// unit is (job, one action); TPS lanes share a scenario (element-level
+// parallelism, Sec. III-D) through gather, update, the expansion step with its
+// observation key, u0 and the default-policy rollout; then the CTA groups the
+// action's scenarios by key (Eq. newnodes), checks every member's full
+// observation (speed and all pedestrian cells, kept in a per-CTA scratch slot
+// in global memory) against its child's first member, and sums rewards and
+// bounds per child in int64 fixed point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "car_model.cuh"
+#include "group.cuh"
 #include "model.hpp"
 
 namespace dsp {
-cudaError_t launch_car_expand(dsp_model*, const dsp_leaf_job*, const int4*, int, unsigned int*, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int kCarObsWords = kMaxPeds + 1;  // speed | terminal, then one word per pedestrian
+
+struct CarUnitSmem {
+  CarShared c;
+  uint64_t key[kMaxScen];
+  float rew[kMaxScen], uval[kMaxScen], lval[kMaxScen];
+  GroupSmem grp;
+  unsigned long long sr[kMaxScen], su[kMaxScen], sl[kMaxScen];
+  int unit;
+  dsp_leaf_job job;
+};
+
+template <int TPS>
+__device__ __forceinline__ CarModel<TPS> make_model(const DevModel* gm, const CarShared* sh, uint32_t plan_step) {
+  CarModel<TPS> M;
+  M.sh = sh;
+  M.P = gm->P;
+  M.D = gm->D;
+  M.path_len = gm->path_len;
+  M.dt = gm->dt;
+  M.sigma = gm->sigma;
+  M.stride = gm->stride;
+  M.fail_thresh = gm->fail_thresh;
+  M.seed = gm->seed;
+  M.plan_step = plan_step;
+  int lane = threadIdx.x & 31;
+  M.gl = lane % TPS;
+  M.gbase = lane - M.gl;
+  M.gmask = (TPS == 32 ? 0xFFFFFFFFu : ((1u << TPS) - 1u)) << M.gbase;
+  return M;
 }
-cudaError_t launch_car_step(const DevModel*, int, const uint32_t*, int, int, const int32_t*, int, uint32_t*, int,
-                            uint64_t*, float*, uint32_t, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+__device__ __forceinline__ void load_consts(CarShared& c, const DevModel* gm) {
+  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
+  for (int k = threadIdx.x; k < kGaussLen; k += blockDim.x) c.gauss[k] = gm->gauss[k];
 }
-cudaError_t launch_car_rollout(const DevModel*, int, DevWork*, const uint32_t*, int, int, int, float*, uint32_t,
-                               cudaStream_t) {
-  return cudaErrorNotSupported;
+
+template <int TPS>
+__global__ void __launch_bounds__(256) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                         const dsp_leaf_job* __restrict__ jobs,
+                                                         const int4* __restrict__ units, int n_units,
+                                                         unsigned int* head, uint32_t plan_step,
+                                                         uint32_t* scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CarUnitSmem& S = *reinterpret_cast<CarUnitSmem*>(smem_raw);
+  load_consts(S.c, gm);
+  CarModel<TPS> M = make_model<TPS>(gm, &S.c, plan_step);
+  const int P = M.P;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int groups = nthr / TPS, g = tid / TPS;
+  uint32_t* obs = scratch + (size_t)blockIdx.x * kMaxScen * kCarObsWords;
+  unsigned long long steps = 0;
+  __syncthreads();
+  while (true) {
+    if (tid == 0) S.unit = (int)atomicAdd(head, 1u);
+    __syncthreads();
+    const int u = S.unit;
+    __syncthreads();
+    if (u >= n_units) break;
+    const int4 un = units[u];
+    if (tid == 0) S.job = jobs[un.x];
+    __syncthreads();
+    const dsp_leaf_job& job = S.job;
+    const int n = job.n_scen, depth = job.depth;
+    const int a = job.first_action + un.y;
+    const bool first_unit = un.y == 0;
+    for (int base = 0; base < n; base += groups) {
+      const int p = base + g;
+      const bool valid = p < n;
+      CarLane<TPS> L;
+      if (valid) {
+        M.load(L, job.parent, job.parent_cap, job.idx[p]);
+      } else {
+        L.s = 0.0f;
+        L.v = 0;
+        L.term = true;
+        L.scen = 0;
+        L.goals = 0;
+#pragma unroll
+        for (int k = 0; k < 2 * CarLane<TPS>::kPairs; ++k) L.px[k] = L.py[k] = 0.0f;
+      }
+      bool danger = false;
+      uint64_t key = 0;
+      if (job.last_action >= 0) {  // update by the action into this leaf
+        bool live = valid && !L.term;
+        if (live && M.gl == 0 && first_unit) steps += 1;
+        uint32_t uf = M.fail_word(L.scen, depth - 1);
+        M.template step<false>(L, live, job.last_action, depth - 1, uf, danger, key);
+      }
+      if (first_unit && job.leaf_states != nullptr) M.store(L, job.leaf_states, n, p, valid);
+      // Eq. expand with the observation key
+      bool live = valid && !L.term;
+      if (live && M.gl == 0) steps += 1;
+      uint32_t uf = M.fail_word(L.scen, depth);
+      float r = M.template step<true>(L, live, a, depth, uf, danger, key);
+      if (valid) {
+        uint32_t* ob = obs + (size_t)p * kCarObsWords;
+        if (M.gl == 0) ob[0] = (uint32_t)L.v | ((uint32_t)L.term << 8);
+#pragma unroll
+        for (int k = 0; k < CarLane<TPS>::kPairs; ++k)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            int j = 2 * (M.gl + k * TPS) + e;
+            if (j < P) {
+              int qx = (int)floorf(__fmul_rn(2.0f, L.px[2 * k + e]));
+              int qy = (int)floorf(__fmul_rn(2.0f, L.py[2 * k + e]));
+              ob[1 + j] = (uint32_t)(uint16_t)(int16_t)qx | ((uint32_t)(uint16_t)(int16_t)qy << 16);
+            }
+          }
+      }
+      // Eq. ub (the tail heuristic is zero at depth D) and Eq. lb
+      float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(L);
+      float lv = M.rollout(L, valid, danger, depth + 1, steps);
+      if (valid && M.gl == 0) {
+        S.key[p] = key;
+        S.rew[p] = r;
+        S.uval[p] = uv;
+        S.lval[p] = lv;
+      }
+    }
+    for (int c = tid; c < n; c += nthr) {
+      S.sr[c] = 0;
+      S.su[c] = 0;
+      S.sl[c] = 0;
+    }
+    __syncthreads();
+    group_by_key(S.grp, S.key, n);
+    const int nchild = S.grp.nchild;
+    // full-observation check of every member against its child's first member
+    for (int q = tid; q < n; q += nthr) {
+      int c = S.grp.gcid[q];
+      int f = S.grp.cfirst[c];
+      if (f != q) {
+        const uint32_t* a0 = obs + (size_t)f * kCarObsWords;
+        const uint32_t* a1 = obs + (size_t)q * kCarObsWords;
+        bool same = a0[0] == a1[0];
+        for (int w = 1; w <= P; ++w) same = same && (a0[w] == a1[w]);
+        if (!same) report(work, kStatusKeyClash);
+      }
+      atomicAdd(&S.sr[c], (unsigned long long)to_fixed(S.rew[q]));
+      atomicAdd(&S.su[c], (unsigned long long)to_fixed(S.uval[q]));
+      atomicAdd(&S.sl[c], (unsigned long long)to_fixed(S.lval[q]));
+    }
+    __syncthreads();
+    const int cap = job.child_cap;
+    const int ao = un.y;
+    if (tid == 0) {
+      job.child_count[ao] = nchild;
+      if (nchild > cap) report(work, kStatusOverflow);
+    }
+    const int ncw = min(nchild, cap);
+    for (int c = tid; c <= ncw; c += nthr) job.child_off[(size_t)ao * (cap + 1) + c] = c < nchild ? S.grp.coff[c] : n;
+    for (int c = tid; c < ncw; c += nthr) {
+      size_t o = (size_t)ao * cap + c;
+      job.child_key[o] = S.key[S.grp.cfirst[c]];
+      job.rew_sum[o] = (long long)S.sr[c];
+      job.u_sum[o] = (long long)S.su[c];
+      job.l_sum[o] = (long long)S.sl[c];
+    }
+    for (int q = tid; q < n; q += nthr) {
+      int c = S.grp.gcid[q];
+      job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
+
+// dsp_step for the car (TPS = 8 lanes per scenario).
+__global__ void __launch_bounds__(256) car_step_kernel(const DevModel* __restrict__ gm, const uint32_t* in,
+                                                       int in_cap, int count, const int32_t* actions, int depth,
+                                                       uint32_t* out, int out_cap, uint64_t* keys, float* rewards,
+                                                       uint32_t plan_step) {
+  constexpr int TPS = 8;
+  __shared__ CarShared c;
+  load_consts(c, gm);
+  __syncthreads();
+  CarModel<TPS> M = make_model<TPS>(gm, &c, plan_step);
+  const int groups = blockDim.x / TPS;
+  for (int base = blockIdx.x * groups; base < count; base += gridDim.x * groups) {
+    int i = base + (int)threadIdx.x / TPS;
+    bool valid = i < count;
+    CarLane<TPS> L;
+    M.load(L, in, in_cap, valid ? i : 0);
+    bool live = valid && !L.term;
+    int a = valid ? actions[i] : 0;
+    uint32_t uf = M.fail_word(L.scen, depth);
+    bool danger;
+    uint64_t key;
+    float r = M.template step<true>(L, live, a, depth, uf, danger, key);
+    M.store(L, out, out_cap, i, valid);
+    if (valid && M.gl == 0) {
+      keys[i] = key;
+      rewards[i] = r;
+    }
+  }
+}
+
+// dsp_rollout for the car (TPS = 8).
+__global__ void __launch_bounds__(256) car_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                          const uint32_t* block, int cap, int count,
+                                                          int start_depth, float* value, uint32_t plan_step) {
+  constexpr int TPS = 8;
+  __shared__ CarShared c;
+  load_consts(c, gm);
+  __syncthreads();
+  CarModel<TPS> M = make_model<TPS>(gm, &c, plan_step);
+  const int groups = blockDim.x / TPS;
+  unsigned long long steps = 0;
+  for (int base = blockIdx.x * groups; base < count; base += gridDim.x * groups) {
+    int i = base + (int)threadIdx.x / TPS;
+    bool valid = i < count;
+    CarLane<TPS> L;
+    M.load(L, block, cap, valid ? i : 0);
+    if (!valid) L.term = true;
+    bool danger = M.danger_now(L);
+    float v = M.rollout(L, valid, danger, start_depth, steps);
+    if (valid && M.gl == 0) value[i] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
+template <int TPS>
+cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units, unsigned int* head,
+                       cudaStream_t st) {
+  size_t smem = sizeof(CarUnitSmem);
+  cudaError_t e = cudaFuncSetAttribute(car_expand_kernel<TPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, car_expand_kernel<TPS>, 256, smem);
+  per_sm = std::max(1, per_sm);
+  int grid = std::max(1, std::min(n_units, per_sm * m->num_sms));
+  size_t need = (size_t)grid * kMaxScen * kCarObsWords * sizeof(uint32_t);
+  if (m->scratch_bytes < need) {
+    if (m->scratch) cudaFree(m->scratch);
+    m->scratch = nullptr;
+    m->scratch_bytes = 0;
+    e = cudaMalloc(&m->scratch, need);
+    if (e != cudaSuccess) return e;
+    m->scratch_bytes = need;
+  }
+  car_expand_kernel<TPS><<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, head, m->plan_step,
+                                                   m->scratch);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
+                              unsigned int* head, cudaStream_t st) {
+  switch (m->tune_tps > 0 ? m->tune_tps : 16) {
+    case 4: return launch_tps<4>(m, djobs, dunits, n_units, head, st);
+    case 8: return launch_tps<8>(m, djobs, dunits, n_units, head, st);
+    case 32: return launch_tps<32>(m, djobs, dunits, n_units, head, st);
+    default: return launch_tps<16>(m, djobs, dunits, n_units, head, st);
+  }
+}
+
+cudaError_t launch_car_step(const DevModel* gm, int P, const uint32_t* in, int in_cap, int count,
+                            const int32_t* actions, int depth, uint32_t* out, int out_cap, uint64_t* keys,
+                            float* rewards, uint32_t plan_step, cudaStream_t st) {
+  (void)P;
+  int groups = 256 / 8;
+  int grid = std::min(4096, (count + groups - 1) / groups);
+  car_step_kernel<<<grid, 256, 0, st>>>(gm, in, in_cap, count, actions, depth, out, out_cap, keys, rewards,
+                                        plan_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_car_rollout(const DevModel* gm, int P, DevWork* work, const uint32_t* block, int cap, int count,
+                               int start_depth, float* value, uint32_t plan_step, cudaStream_t st) {
+  (void)P;
+  int groups = 256 / 8;
+  int grid = std::min(4096, (count + groups - 1) / groups);
+  car_rollout_kernel<<<grid, 256, 0, st>>>(gm, work, block, cap, count, start_depth, value, plan_step);
+  return cudaGetLastError();
+}
+
 }  // namespace dsp

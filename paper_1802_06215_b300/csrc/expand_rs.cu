@@ -1,23 +1,26 @@
-// Leaf expansion for Rock Sample models (one or two robots): the fused
-// gather -> update -> expansion -> grouping -> bounds -> reduction path of
-// Sec. III-D as one persistent kernel.
+// Leaf expansion for Rock Sample models (one or two robots), Sec. III-D, in
+// two phases.
 //
-// Work is cut into units (job, run of actions) whose items (action, scenario)
-// fit one CTA (<= kItems). A CTA pulls units from a device counter until none
-// is left, so leaves of uneven |Phi_b| and action counts balance across SMs.
-// Per unit:
-//   1. gather the leaf's scenarios from the parent list and apply the last
-//      action (update), keeping the leaf's states in shared memory;
-//   2. step every item with g (Eq. expand);
-//   3. group each action's items by observation (shared-memory hash of
-//      (action, key), first-occurrence leaders, warp ballots for child
-//      numbering, warp __match_any_sync for stable ranks) (Eq. newnodes);
-//   4. in child-grouped order (so a warp's lanes follow the same child and
-//      branch alike) compute u (Eq. ub) and the default-policy rollout
-//      (Eq. lb) in registers;
-//   5. sum rewards, u and l per child in int64 fixed point (shared atomics,
-//      exact in any order) and write the results.
+// Phase A (rs_group_kernel, persistent over jobs): a CTA takes a leaf job,
+// gathers its scenarios from the parent list and applies the last action
+// ("update") once, then steps every (action, scenario) pair with g
+// (Eq. expand) and splits each action's scenarios by observation into
+// children (Eq. newnodes). Each action occupies whole warps, so grouping needs
+// no hash and no serial pass: lanes with the same observation code (z, and
+// whether the step ended the world) meet through __match_any_sync, a small
+// per-warp table gives the cross-warp prefixes, and children are numbered by
+// their first position. Phase A writes the children (counts, offsets, keys,
+// exact reward sums, grouped positions) and appends one rollout item per
+// (action, scenario) to a flat list in child-grouped order.
+//
+// Phase B (rs_rollout_items_kernel): warps pull 32-item chunks of that list
+// (no barriers, full occupancy), compute u (Eq. ub) and the default-policy
+// rollout (Eq. lb) in registers, and add each run of same-child lanes to the
+// child's int64 fixed-point sums with one atomic (exact in any order). A warp's
+// lanes mostly share a child, so they branch alike.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -27,31 +30,25 @@ namespace dsp {
 
 namespace {
 
-constexpr int kItems = 512;      // items (action, scenario) per unit
-constexpr int kTable = 1024;     // hash slots (>= 2 * kItems)
-constexpr uint64_t kEmpty = ~0ull;
+constexpr int kBlockA = 512;          // phase-A CTA: 16 warps
+constexpr int kWarpsA = kBlockA / 32;
+constexpr int kCodes = 18;            // observation code z + 9 * terminal, z <= 8
 
-struct RSUnitSmem {
+struct RSGroupSmem {
   RSShared c;
-  uint32_t leaf[5][kMaxScen];      // the leaf's states, field-major
-  uint32_t next[5][kItems];        // stepped state of each item
-  uint64_t key[kItems];
-  float rew[kItems];
-  uint16_t slot[kItems];
-  uint16_t gcid[kItems];
-  uint16_t rank[kItems];
-  uint16_t permitem[kItems];       // item at each grouped position
-  uint64_t tkey[kTable];
-  uint32_t tfirst[kTable];
-  uint16_t tcid[kTable];
-  int32_t cfirst[kItems];          // first item of each child
-  int32_t ccount[kItems];
-  int32_t coff[kItems];
-  int32_t abase[kItems + 1];       // first child of each action of the unit
-  unsigned long long sr[kItems], su[kItems], sl[kItems];
-  int nchild;
-  int unit;
-  dsp_leaf_job job;
+  uint32_t leaf[5][kMaxScen];          // the leaf's states, field-major
+  int wcnt[kWarpsA][kCodes];           // per warp: lanes holding each code
+  int wfirst[kWarpsA][kCodes];         // per warp: first position of each code
+  int wpre[kWarpsA][kCodes];           // items of the code in earlier warps of the action
+  int acnt[kWarpsA][kCodes];           // per action of the pass: scenarios per code
+  int afirst[kWarpsA][kCodes];
+  int aoff[kWarpsA][kCodes];           // offset of the code's child in the grouped order
+  int acid[kWarpsA][kCodes];           // child index of the code
+  int anch[kWarpsA];                   // children per action
+  unsigned long long sr[kWarpsA][kCodes];
+  uint32_t pm_job;
+  int job;
+  dsp_leaf_job J;
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -60,220 +57,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-__device__ __forceinline__ uint32_t hash_slot(uint64_t ident) {
-  uint64_t z = ident * 0x9E3779B97F4A7C15ull;
-  return (uint32_t)(z >> 40) & (kTable - 1);
+__device__ __forceinline__ void load_rs_consts(RSShared& c, const DevModel* gm) {
+  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
+  for (int k = threadIdx.x; k < kMaxRocks; k += blockDim.x) c.rock_xy[k] = gm->rock_xy[k];
+  for (int k = threadIdx.x; k < kMaxSide * kMaxSide; k += blockDim.x) c.cell_rock[k] = gm->cell_rock[k];
 }
 
 template <int R>
-__device__ void rs_unit(RSUnitSmem& S, const RSModel<R>& M, const dsp_leaf_job& job, int a_begin, int a_count,
-                        DevWork* work, unsigned long long& steps) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int n = job.n_scen;
-  const int items = a_count * n;
-  const int depth = job.depth;
-  const int a_first = job.first_action + a_begin;
-
-  // 1. gather + update
-  for (int p = tid; p < n; p += nthr) {
-    RSS s = M.load(job.parent, job.parent_cap, job.idx[p]);
-    if (job.last_action >= 0) {
-      if (!M.terminal(s) && a_begin == 0) steps += 1;
-      uint64_t k;
-      M.step(s, job.last_action, depth - 1, k);
-    }
-    S.leaf[0][p] = s.pos[0];
-    S.leaf[1][p] = s.pos[1];
-    S.leaf[2][p] = s.good;
-    S.leaf[3][p] = s.sampled;
-    S.leaf[4][p] = s.scen;
-    if (a_begin == 0 && job.leaf_states != nullptr) M.store(s, job.leaf_states, n, p);
-  }
-  for (int t = tid; t < kTable; t += nthr) {
-    S.tkey[t] = kEmpty;
-    S.tfirst[t] = 0xFFFFFFFFu;
-  }
-  for (int g = tid; g < items; g += nthr) {
-    S.sr[g] = 0;
-    S.su[g] = 0;
-    S.sl[g] = 0;
-  }
-  __syncthreads();
-
-  // 2. expansion step of every item, 3a. hash insert of (action, key)
-  for (int i = tid; i < items; i += nthr) {
-    int al = i / n, p = i - al * n;
-    RSS s;
-    s.pos[0] = S.leaf[0][p];
-    s.pos[1] = S.leaf[1][p];
-    s.good = S.leaf[2][p];
-    s.sampled = S.leaf[3][p];
-    s.scen = S.leaf[4][p];
-    if (!M.terminal(s)) steps += 1;
-    uint64_t key;
-    float r = M.step(s, a_first + al, depth, key);
-    S.next[0][i] = s.pos[0];
-    S.next[1][i] = s.pos[1];
-    S.next[2][i] = s.good;
-    S.next[3][i] = s.sampled;
-    S.next[4][i] = s.scen;
-    S.key[i] = key;
-    S.rew[i] = r;
-    uint64_t ident = ((uint64_t)al << 32) | (key & 0xFFFFull) | ((key >> 62) << 31);
-    uint32_t h = hash_slot(ident);
-    while (true) {
-      unsigned long long prev = atomicCAS((unsigned long long*)&S.tkey[h], (unsigned long long)kEmpty,
-                                          (unsigned long long)ident);
-      if (prev == kEmpty || prev == ident) break;
-      h = (h + 1) & (kTable - 1);
-    }
-    atomicMin(&S.tfirst[h], (uint32_t)i);
-    S.slot[i] = (uint16_t)h;
-  }
-  __syncthreads();
-
-  // 3b. number children in item order (first occurrence), 3c. stable ranks
-  if (warp == 0) {
-    int base = 0;
-    for (int c0 = 0; c0 < items; c0 += 32) {
-      int i = c0 + lane;
-      bool lead = i < items && S.tfirst[S.slot[i]] == (uint32_t)i;
-      uint32_t bal = __ballot_sync(0xFFFFFFFFu, lead);
-      if (lead) {
-        int g = base + __popc(bal & lanemask_lt());
-        S.tcid[S.slot[i]] = (uint16_t)g;
-        S.cfirst[g] = i;
-        S.ccount[g] = 0;
-      }
-      base += __popc(bal);
-    }
-    if (lane == 0) S.nchild = base;
-    __syncwarp();
-    for (int c0 = 0; c0 < items; c0 += 32) {
-      int i = c0 + lane;
-      bool ok = i < items;
-      int g = ok ? S.tcid[S.slot[i]] : -1 - lane;
-      uint32_t peers = __match_any_sync(0xFFFFFFFFu, g);
-      int base_g = ok ? S.ccount[g] : 0;
-      __syncwarp();
-      if (ok) {
-        S.gcid[i] = (uint16_t)g;
-        S.rank[i] = (uint16_t)(base_g + __popc(peers & lanemask_lt()));
-        if ((peers >> lane) == 1u) S.ccount[g] = base_g + __popc(peers);
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-
-  // 3d. first child of each action; offsets within the action. Children are
-  // numbered in item order and every action has exactly n items, so the
-  // children of earlier actions hold al * n items in total.
-  const int nchild = S.nchild;
-  for (int g = tid; g < nchild; g += nthr) {
-    int al = S.cfirst[g] / n;
-    if (g == 0 || S.cfirst[g - 1] / n != al) S.abase[al] = g;
-  }
-  if (tid == 0) S.abase[a_count] = nchild;
-  if (warp == 0) {
-    int carry = 0;
-    for (int c0 = 0; c0 < nchild; c0 += 32) {
-      int g = c0 + lane;
-      int cnt = g < nchild ? S.ccount[g] : 0;
-      int v = cnt;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        int o = __shfl_up_sync(0xFFFFFFFFu, v, d);
-        if (lane >= d) v += o;
-      }
-      if (g < nchild) S.coff[g] = carry + v - cnt - (S.cfirst[g] / n) * n;
-      carry += __shfl_sync(0xFFFFFFFFu, v, 31);
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < items; i += nthr) {
-    int al = i / n;
-    int g = S.gcid[i];
-    S.permitem[al * n + S.coff[g] + S.rank[i]] = (uint16_t)i;
-  }
-  __syncthreads();
-
-  // 4. bounds in child-grouped order, 5. fixed-point sums per child
-  const uint32_t* hw = reinterpret_cast<const uint32_t*>(job.hist);
-  for (int q = tid; q < items; q += nthr) {
-    int i = S.permitem[q];
-    int al = i / n;
-    int a = a_first + al;
-    int g = S.gcid[i];
-    RSS s;
-    s.pos[0] = S.next[0][i];
-    s.pos[1] = S.next[1][i];
-    s.good = S.next[2][i];
-    s.sampled = S.next[3][i];
-    s.scen = S.next[4][i];
-    uint64_t key = S.key[i];
-    float u = (depth + 1 >= M.D) ? M.tail(s) : M.upper(s);
-    float v = 0.0f;
-    if (M.terminal(s)) {
-      u = 0.0f;
-    } else {
-      uint32_t h[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) h[k] = hw[k];
-      uint32_t pm = positive_mask(h, M.m);
-      M.observe(h, pm, a, key);
-      v = M.rollout(s, h, pm, depth + 1, steps);
-    }
-    atomicAdd(&S.sr[g], (unsigned long long)to_fixed(S.rew[i]));
-    atomicAdd(&S.su[g], (unsigned long long)to_fixed(u));
-    atomicAdd(&S.sl[g], (unsigned long long)to_fixed(v));
-  }
-  __syncthreads();
-
-  // results
-  const int cap = job.child_cap;
-  for (int al = warp; al < a_count; al += nthr / 32) {
-    int g0 = S.abase[al], nc = S.abase[al + 1] - g0;
-    int ao = a_begin + al;
-    if (lane == 0) {
-      job.child_count[ao] = nc;
-      if (nc > cap) report(work, kStatusOverflow);
-    }
-    int ncw = nc < cap ? nc : cap;
-    for (int c = lane; c <= ncw; c += 32) {
-      size_t o = (size_t)ao * (cap + 1) + c;
-      job.child_off[o] = c < nc ? S.coff[g0 + c] : n;
-    }
-    for (int c = lane; c < ncw; c += 32) {
-      size_t o = (size_t)ao * cap + c;
-      int g = g0 + c;
-      job.child_key[o] = S.key[S.cfirst[g]];
-      job.rew_sum[o] = (long long)S.sr[g];
-      job.u_sum[o] = (long long)S.su[g];
-      job.l_sum[o] = (long long)S.sl[g];
-    }
-  }
-  for (int q = tid; q < items; q += nthr) {
-    int al = q / n;
-    int i = S.permitem[q];
-    job.perm[(size_t)(a_begin + al) * n + (q - al * n)] = (uint16_t)(i - al * n);
-  }
-  __syncthreads();
-}
-
-template <int R>
-__global__ void __launch_bounds__(256) rs_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
-                                                        const dsp_leaf_job* __restrict__ jobs,
-                                                        const int4* __restrict__ units, int n_units,
-                                                        unsigned int* head, uint32_t plan_step) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  RSUnitSmem& S = *reinterpret_cast<RSUnitSmem*>(smem_raw);
-  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) S.c.G[k] = gm->G[k];
-  for (int k = threadIdx.x; k < kMaxRocks; k += blockDim.x) S.c.rock_xy[k] = gm->rock_xy[k];
-  for (int k = threadIdx.x; k < kMaxSide * kMaxSide; k += blockDim.x) S.c.cell_rock[k] = gm->cell_rock[k];
+__device__ __forceinline__ RSModel<R> make_rs(const DevModel* gm, const RSShared* c, uint32_t plan_step) {
   RSModel<R> M;
-  M.sh = &S.c;
+  M.sh = c;
   M.thresh = gm->thresh;
   M.n = gm->n;
   M.m = gm->m;
@@ -281,22 +74,253 @@ __global__ void __launch_bounds__(256) rs_expand_kernel(const DevModel* __restri
   M.D = gm->D;
   M.seed = gm->seed;
   M.plan_step = plan_step;
+  return M;
+}
+
+// Item list (field-major, `total` items): robot 0 [, robot 1], good, sampled,
+// scenario, positive-counter mask of the child's history, depth<<24 | slot
+// (slot = action * child_cap + child in the job's result arrays), job.
+template <int R>
+struct Items {
+  static constexpr int kFields = R == 2 ? 8 : 7;
+  uint32_t* base;
+  long long total;
+  __device__ __forceinline__ uint32_t* f(int k) const { return base + (size_t)k * total; }
+};
+
+template <int R>
+__global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                             const dsp_leaf_job* __restrict__ jobs,
+                                                             const long long* __restrict__ item_base, int n_jobs,
+                                                             unsigned int* head, uint32_t plan_step,
+                                                             Items<R> items) {
+  __shared__ RSGroupSmem S;
+  load_rs_consts(S.c, gm);
+  const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned long long steps = 0;
   __syncthreads();
   while (true) {
-    if (threadIdx.x == 0) S.unit = (int)atomicAdd(head, 1u);
+    if (tid == 0) {
+      S.job = (int)atomicAdd(head, 1u);
+      if (S.job < n_jobs) S.J = jobs[S.job];
+    }
     __syncthreads();
-    int u = S.unit;
-    __syncthreads();
-    if (u >= n_units) break;
-    int4 un = units[u];
-    if (threadIdx.x == 0) S.job = jobs[un.x];
-    __syncthreads();
-    rs_unit<R>(S, M, S.job, un.y, un.z, work, steps);
+    const int j = S.job;
+    if (j >= n_jobs) break;
+    const dsp_leaf_job& J = S.J;
+    const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
+    const long long ibase = item_base[j];
+
+    // gather + update, once per job
+    for (int p = tid; p < n; p += kBlockA) {
+      RSS s = M.load(J.parent, J.parent_cap, J.idx[p]);
+      if (J.last_action >= 0) {
+        if (!M.terminal(s)) steps += 1;
+        uint64_t k;
+        M.step(s, J.last_action, depth - 1, k);
+      }
+      S.leaf[0][p] = s.pos[0];
+      S.leaf[1][p] = s.pos[1];
+      S.leaf[2][p] = s.good;
+      S.leaf[3][p] = s.sampled;
+      S.leaf[4][p] = s.scen;
+      if (J.leaf_states != nullptr) M.store(s, J.leaf_states, n, p);
+    }
+    if (tid == 0) {
+      uint32_t h[8];
+      const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) h[k] = hw[k];
+      S.pm_job = positive_mask(h, M.m);
+    }
+    // each action takes wpa whole warps; apass actions per pass
+    const int wpa = (n + 31) >> 5;
+    const int apass = kWarpsA / wpa;
+    for (int a0 = 0; a0 < A; a0 += apass) {
+      for (int t = tid; t < kWarpsA * kCodes; t += kBlockA) {
+        (&S.wcnt[0][0])[t] = 0;
+        (&S.wfirst[0][0])[t] = 0x7FFFFFFF;
+        (&S.sr[0][0])[t] = 0ull;
+      }
+      __syncthreads();
+      const int al = warp / wpa;
+      const int p = (warp - al * wpa) * 32 + lane;
+      const int a = a0 + al;
+      const bool valid = al < apass && a < A && p < n;
+      RSS s;
+      uint64_t key = 0;
+      int code = 32 + lane, rint = 0;
+      if (valid) {
+        s.pos[0] = S.leaf[0][p];
+        s.pos[1] = S.leaf[1][p];
+        s.good = S.leaf[2][p];
+        s.sampled = S.leaf[3][p];
+        s.scen = S.leaf[4][p];
+        if (!M.terminal(s)) steps += 1;
+        rint = (int)M.step(s, J.first_action + a, depth, key);
+        code = (int)(key & 0xFu) + 9 * (int)(key >> 62);
+      }
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, code);
+      const int wrank = __popc(peers & lanemask_lt());
+      const int leader = __ffs(peers) - 1;
+      const int rsum = __reduce_add_sync(peers, rint);
+      if (valid && lane == leader) {
+        S.wcnt[warp][code] = __popc(peers);
+        S.wfirst[warp][code] = p;
+        atomicAdd(&S.sr[al][code], (unsigned long long)((long long)rsum * 4294967296LL));
+      }
+      __syncthreads();
+      // cross-warp prefixes per (action, code)
+      if (tid < apass * kCodes) {
+        int bl = tid / kCodes, c = tid - bl * kCodes;
+        int run = 0, first = 0x7FFFFFFF;
+        for (int w = bl * wpa; w < (bl + 1) * wpa; ++w) {
+          S.wpre[w][c] = run;
+          run += S.wcnt[w][c];
+          first = min(first, S.wfirst[w][c]);
+        }
+        S.acnt[bl][c] = run;
+        S.afirst[bl][c] = first;
+      }
+      __syncthreads();
+      // children in order of first position
+      if (tid < apass * kCodes) {
+        int bl = tid / kCodes, c = tid - bl * kCodes;
+        int cnt = S.acnt[bl][c], first = S.afirst[bl][c];
+        int cid = 0, off = 0, nch = 0;
+        for (int c2 = 0; c2 < kCodes; ++c2) {
+          int n2 = S.acnt[bl][c2];
+          if (n2 > 0) {
+            nch += 1;
+            if (S.afirst[bl][c2] < first) {
+              cid += 1;
+              off += n2;
+            }
+          }
+        }
+        S.acid[bl][c] = cnt > 0 ? cid : -1;
+        S.aoff[bl][c] = off;
+        if (c == 0) S.anch[bl] = nch;
+      }
+      __syncthreads();
+      // grouped position, perm, rollout item
+      if (valid) {
+        const int cid = S.acid[al][code];
+        const int q = S.aoff[al][code] + S.wpre[warp][code] + wrank;
+        J.perm[(size_t)a * n + q] = (uint16_t)p;
+        uint32_t h[8];
+        const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = hw[k];
+        uint32_t pm = S.pm_job;
+        M.observe(h, pm, J.first_action + a, key);
+        const size_t it = (size_t)(ibase + (long long)a * n + q);
+        items.f(0)[it] = s.pos[0];
+        int f = 1;
+        if (R == 2) items.f(f++)[it] = s.pos[1];
+        items.f(f++)[it] = s.good;
+        items.f(f++)[it] = s.sampled;
+        items.f(f++)[it] = s.scen;
+        items.f(f++)[it] = pm;
+        items.f(f++)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(cid, cap - 1));
+        items.f(f++)[it] = (uint32_t)j;
+      }
+      // per-action results: counts, offsets, keys, reward sums; u and l start at 0
+      if (tid < apass * kCodes) {
+        int bl = tid / kCodes, c = tid - bl * kCodes;
+        int a2 = a0 + bl;
+        int cid = S.acid[bl][c];
+        if (a2 < A && cid >= 0) {
+          int nch = S.anch[bl];
+          if (cid == 0) {
+            J.child_count[a2] = nch;
+            if (nch > cap) report(work, kStatusOverflow);
+            if (nch <= cap) J.child_off[(size_t)a2 * (cap + 1) + nch] = n;
+          }
+          if (cid < cap) {
+            size_t o = (size_t)a2 * cap + cid;
+            J.child_off[(size_t)a2 * (cap + 1) + cid] = S.aoff[bl][c];
+            J.child_key[o] = (uint64_t)(c % 9) | ((uint64_t)(c / 9) << 62);
+            J.rew_sum[o] = (long long)S.sr[bl][c];
+            J.u_sum[o] = 0;
+            J.l_sum[o] = 0;
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
-  // block-wide sum of the scenario-step counter
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
-  if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
+  if (lane == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
+template <int R>
+__global__ void __launch_bounds__(512) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                              const dsp_leaf_job* __restrict__ jobs,
+                                                              Items<R> items, unsigned int* chunk_head,
+                                                              uint32_t plan_step) {
+  __shared__ RSShared c;
+  load_rs_consts(c, gm);
+  __syncthreads();
+  const RSModel<R> M = make_rs<R>(gm, &c, plan_step);
+  const int lane = threadIdx.x & 31;
+  const long long nchunks = (items.total + 31) >> 5;
+  unsigned long long steps = 0;
+  while (true) {
+    long long chunk = 0;
+    if (lane == 0) chunk = (long long)atomicAdd(chunk_head, 1u);
+    chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+    if (chunk >= nchunks) break;
+    const long long it = chunk * 32 + lane;
+    const bool ok = it < items.total;
+    uint32_t job = 0xFFFFFFFFu, slot = 0;
+    long long fu = 0, fl = 0;
+    if (ok) {
+      RSS s;
+      s.pos[0] = items.f(0)[it];
+      int f = 1;
+      s.pos[1] = R == 2 ? items.f(f++)[it] : 0u;
+      s.good = items.f(f++)[it];
+      s.sampled = items.f(f++)[it];
+      s.scen = items.f(f++)[it];
+      const uint32_t pm = items.f(f++)[it];
+      const uint32_t meta = items.f(f++)[it];
+      job = items.f(f++)[it];
+      slot = meta & 0xFFFFFFu;
+      const int depth = (int)(meta >> 24);
+      float u = 0.0f, v = 0.0f;
+      if (!M.terminal(s)) {
+        u = (depth + 1 >= M.D) ? M.tail(s) : M.upper(s);
+        v = M.rollout(s, pm, depth + 1, steps);
+      }
+      fu = to_fixed(u);
+      fl = to_fixed(v);
+    }
+    // runs of lanes with the same (job, slot) are contiguous: segmented scan
+    const uint32_t pj = __shfl_up_sync(0xFFFFFFFFu, job, 1);
+    const uint32_t ps = __shfl_up_sync(0xFFFFFFFFu, slot, 1);
+    const uint32_t starts = __ballot_sync(0xFFFFFFFFu, lane == 0 || pj != job || ps != slot);
+    const uint32_t le = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+    const int lo = 31 - __clz(starts & le);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      long long yu = __shfl_up_sync(0xFFFFFFFFu, fu, d);
+      long long yl = __shfl_up_sync(0xFFFFFFFFu, fl, d);
+      if (lane - d >= lo) {
+        fu += yu;
+        fl += yl;
+      }
+    }
+    const bool last = lane == 31 || ((starts >> (lane + 1)) & 1u);
+    if (ok && last) {
+      const dsp_leaf_job* J = jobs + job;
+      atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)fu);
+      atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)fl);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if (lane == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
 // dsp_step: one g call per scenario.
@@ -305,11 +329,9 @@ __global__ void rs_step_kernel(const DevModel* __restrict__ gm, const uint32_t* 
                                const int32_t* actions, int depth, uint32_t* out, int out_cap, uint64_t* keys,
                                float* rewards, uint32_t plan_step) {
   __shared__ RSShared c;
-  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
-  for (int k = threadIdx.x; k < kMaxRocks; k += blockDim.x) c.rock_xy[k] = gm->rock_xy[k];
-  for (int k = threadIdx.x; k < kMaxSide * kMaxSide; k += blockDim.x) c.cell_rock[k] = gm->cell_rock[k];
+  load_rs_consts(c, gm);
   __syncthreads();
-  RSModel<R> M{&c, gm->thresh, gm->n, gm->m, gm->per_robot, gm->D, gm->seed, plan_step};
+  const RSModel<R> M = make_rs<R>(gm, &c, plan_step);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     RSS s = M.load(in, in_cap, i);
     uint64_t key;
@@ -330,11 +352,9 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
                                   int count, const int8_t* hist, int start_depth, float* value,
                                   uint32_t plan_step) {
   __shared__ RSShared c;
-  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
-  for (int k = threadIdx.x; k < kMaxRocks; k += blockDim.x) c.rock_xy[k] = gm->rock_xy[k];
-  for (int k = threadIdx.x; k < kMaxSide * kMaxSide; k += blockDim.x) c.cell_rock[k] = gm->cell_rock[k];
+  load_rs_consts(c, gm);
   __syncthreads();
-  RSModel<R> M{&c, gm->thresh, gm->n, gm->m, gm->per_robot, gm->D, gm->seed, plan_step};
+  const RSModel<R> M = make_rs<R>(gm, &c, plan_step);
   unsigned long long steps = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     RSS s = M.load(block, cap, i);
@@ -342,43 +362,45 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       h[k] = hist ? *reinterpret_cast<const uint32_t*>(hist + 32 * (size_t)i + 4 * k) : 0u;
-    uint32_t pm = positive_mask(h, M.m);
-    value[i] = M.rollout(s, h, pm, start_depth, steps);
+    value[i] = M.rollout(s, positive_mask(h, M.m), start_depth, steps);
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
+template <int R>
+cudaError_t launch_two_phase(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs, const long long* item_base,
+                             int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
+                             uint32_t plan_step, int num_sms, int block_b, cudaStream_t st) {
+  Items<R> items{item_buf, total_items};
+  int per_sm_a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, rs_group_kernel<R>, kBlockA, 0);
+  int grid_a = std::max(1, std::min(n_jobs, std::max(1, per_sm_a) * num_sms));
+  rs_group_kernel<R><<<grid_a, kBlockA, 0, st>>>(gm, work, jobs, item_base, n_jobs, counters, plan_step, items);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int per_sm_b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, rs_rollout_items_kernel<R>, block_b, 0);
+  long long chunks = (total_items + 31) / 32;
+  long long want = (chunks + block_b / 32 - 1) / (block_b / 32);
+  int grid_b = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm_b) * num_sms));
+  rs_rollout_items_kernel<R><<<grid_b, block_b, 0, st>>>(gm, work, jobs, items, counters + 1, plan_step);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t rs_expand_smem() { return sizeof(RSUnitSmem); }
-
-int rs_expand_blocks_per_sm(int robots, int block) {
-  int n = 0;
-  size_t smem = sizeof(RSUnitSmem);
-  if (robots == 1) {
-    cudaFuncSetAttribute(rs_expand_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_expand_kernel<1>, block, smem);
-  } else {
-    cudaFuncSetAttribute(rs_expand_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_expand_kernel<2>, block, smem);
-  }
-  return n > 0 ? n : 1;
-}
-int rs_items_per_unit() { return kItems; }
+int rs_item_fields(int robots) { return robots == 2 ? Items<2>::kFields : Items<1>::kFields; }
 
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, DevWork* work, const dsp_leaf_job* jobs,
-                             const int4* units, int n_units, unsigned int* head, uint32_t plan_step, int grid,
-                             int block, cudaStream_t st) {
-  size_t smem = sizeof(RSUnitSmem);
-  if (robots == 1) {
-    cudaFuncSetAttribute(rs_expand_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rs_expand_kernel<1><<<grid, block, smem, st>>>(gm, work, jobs, units, n_units, head, plan_step);
-  } else {
-    cudaFuncSetAttribute(rs_expand_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rs_expand_kernel<2><<<grid, block, smem, st>>>(gm, work, jobs, units, n_units, head, plan_step);
-  }
-  return cudaGetLastError();
+                             const long long* item_base, int n_jobs, long long total_items, uint32_t* item_buf,
+                             unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
+                             cudaStream_t st) {
+  if (robots == 1)
+    return launch_two_phase<1>(gm, work, jobs, item_base, n_jobs, total_items, item_buf, counters, plan_step,
+                               num_sms, block_b, st);
+  return launch_two_phase<2>(gm, work, jobs, item_base, n_jobs, total_items, item_buf, counters, plan_step,
+                             num_sms, block_b, st);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,

@@ -16,15 +16,23 @@ struct dsp_model {
   int num_sms = 0;
   int tune_block = 0;                // CTA size chosen by the autotuner (0 = default)
   int tune_tps = 0;                  // car: threads per scenario (0 = default)
+  uint32_t* scratch = nullptr;       // car: per-CTA observation slots of the expansion kernel
+  size_t scratch_bytes = 0;
 };
 
 namespace dsp {
 
 dsp_status fail(dsp_status st, const char* fmt, ...);
 dsp_status cuda_fail(cudaError_t e, const char* what);
-dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, std::vector<int4>& units);
-dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const std::vector<int4>& units,
-                         cudaStream_t st, unsigned int* head_override);
+
+struct ExpandPlan {
+  std::vector<int4> units;            // car: (job, action, 1, 0)
+  std::vector<long long> item_base;   // Rock Sample: first rollout item of each job
+  long long total_items = 0;
+};
+dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan);
+dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
+                         cudaStream_t st);
 
 cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
                               unsigned int* head, cudaStream_t st);

@@ -200,20 +200,22 @@ struct RSModel {
     return l;
   }
 
-  // Eq. lb for one scenario from depth t0 with belief counters h.
-  __device__ __forceinline__ float rollout(RSS s, uint32_t (&h)[8], uint32_t pmask, int t0,
-                                           unsigned long long& steps) const {
+  // Eq. lb for one scenario from depth t0; pmask marks the rocks whose belief
+  // counter is positive. The heuristic policy never senses, so the counters
+  // stay fixed and the step only meets moves and Sample. A zero reward adds
+  // +0.0 to v, which is never -0.0, so skipping it (and its discount-table
+  // load) leaves v unchanged.
+  __device__ __forceinline__ float rollout(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
     float v = 0.0f;
     int t = t0;
     while (t < D && !terminal(s)) {
       int a = policy(s, pmask);
       uint64_t key;
       float r = step(s, a, t, key);
-      steps += 1;
-      observe(h, pmask, a, key);
-      v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
+      if (r != 0.0f) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
       t += 1;
     }
+    steps += (unsigned long long)(t - t0);
     if (!terminal(s)) v = __fadd_rn(v, __fmul_rn(sh->G[D - t0], tail(s)));
     return v;
   }

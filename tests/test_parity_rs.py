@@ -174,3 +174,24 @@ def test_expand_full_size_sampled(dsp):
             assert r["child_off"][a][nc] == n
         assert np.all(np.sort(r["perm"], axis=1) == np.arange(n))
     m.close()
+
+
+@pytest.mark.parametrize("block", [128, 512])
+def test_expand_parity_block_sizes(dsp, block):
+    """Every rollout-phase CTA size the autotuner may pick gives the oracle's
+    result."""
+    from paper_1802_06215_b300 import _dsp
+    cfg = I.rs15_15()
+    m = dsp.Model(cfg)
+    _dsp.dsp_set_tuning(m.h, block, 0)
+    om = oracle.Model(cfg)
+    jobs = I.job_stream(cfg, 10, 5)
+    jb = dsp.JobBatch(m, jobs)
+    jb.run()
+    _, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"block {block} job {k}")
+    m.close()
