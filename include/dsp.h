@@ -160,6 +160,30 @@ dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t
 dsp_status dsp_set_tuning(dsp_model* model, int32_t block, int32_t tps);
 dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
 
+/* dsp_expand_leaves for callers that must not allocate device memory while
+ * they plan (the paper has no counterpart). dsp_expand_leaves takes its work
+ * buffers from cudaMallocAsync on every call; this entry point calls no
+ * cudaMalloc, cudaFree or other allocating routine. It is for code that owns
+ * all device memory through its own fixed pool, and for replanning loops with
+ * a hard time budget, where an allocation call can block on the device.
+ * Instead it runs the same Rock Sample kernels on one fixed scratch array that
+ * the library keeps in device memory on every GPU that loads it (about 33 MB)
+ * until the process exits.
+ *  - Limits: Rock Sample models only (DSP_E_UNSUPPORTED for the car); at most
+ *    8192 jobs and 2^20 (action, scenario) items (sum of n_scen * n_actions)
+ *    per call. Larger calls fail with DSP_E_UNSUPPORTED and a message giving
+ *    the limit; nothing is launched.
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    with that device current. Make that first call before any stream capture
+ *    on the device.
+ *  - Sharing: every call uses the same array, which keeps the last call's
+ *    contents; the counters the kernels need at zero are cleared on the
+ *    stream at the start of each call. Calls that overlap on the GPU (other
+ *    streams, other threads) race on the array: order them on one stream.
+ * Arguments, outputs and asynchrony are those of dsp_expand_leaves; `jobs` is
+ * a host array, copied before return. */
+dsp_status dsp_expand_leaves_noalloc(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
+
 /* Scenario-steps (g calls on live scenarios: update + expansion + rollout
  * steps) counted by the kernels since the last reset, and the device status
  * word (0 = fine). Synchronises the device. */

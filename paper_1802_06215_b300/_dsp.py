@@ -72,6 +72,7 @@ def lib():
         L.dsp_read_counters.argtypes = [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]
         L.dsp_reset_counters.argtypes = [C.c_void_p, C.c_void_p]
         L.dsp_alu_probe.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_void_p]
+        L.dsp_expand_leaves_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
         L.dsp_set_tuning.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
         L.dsp_get_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         _lib = L
@@ -142,6 +143,12 @@ def dsp_rollout(h, block, cap, count, hist, start_depth, value, stream=0):
 
 def dsp_expand_leaves(h, jobs_array, n_jobs, stream=0):
     check(lib().dsp_expand_leaves(h, C.cast(jobs_array, C.c_void_p), n_jobs, C.c_void_p(stream)))
+
+
+def dsp_expand_leaves_noalloc(h, jobs_array, n_jobs, stream=0):
+    """dsp_expand_leaves without device allocation (fixed library scratch;
+    limits and sharing rules in include/dsp.h)."""
+    check(lib().dsp_expand_leaves_noalloc(h, C.cast(jobs_array, C.c_void_p), n_jobs, C.c_void_p(stream)))
 
 
 def dsp_read_counters(h):

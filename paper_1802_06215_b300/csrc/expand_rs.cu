@@ -430,3 +430,100 @@ cudaError_t launch_rs_rollout(const DevModel* gm, int robots, DevWork* work, con
 }
 
 }  // namespace dsp
+
+// ---------------------------------------------------------------------------
+// Leaf expansion without device allocation (dsp_expand_leaves_noalloc).
+//
+// dsp_expand_leaves takes its job table, item offsets, counters and the
+// rollout-item list from cudaMallocAsync on every call. Callers that cannot
+// allocate device memory during planning use this variant instead: the same
+// two kernels run on a fixed scratch array that the library keeps in device
+// memory for the life of the process. Its size caps one call at
+// kNoAllocJobs jobs and kNoAllocItems (action, scenario) items.
+#include <mutex>
+
+#include "model.hpp"
+
+namespace dsp {
+namespace {
+
+constexpr int kNoAllocJobs = 8192;
+constexpr long long kNoAllocItems = 1LL << 20;
+constexpr size_t kNoAllocJobBytes = ((sizeof(dsp_leaf_job) * kNoAllocJobs + 255) / 256) * 256;
+constexpr size_t kNoAllocBaseBytes = sizeof(long long) * kNoAllocJobs;
+constexpr size_t kNoAllocCounterBytes = 256;
+constexpr size_t kNoAllocItemBytes = sizeof(uint32_t) * 8 * (size_t)kNoAllocItems;  // 8 = most item fields
+constexpr size_t kNoAllocBytes = kNoAllocJobBytes + kNoAllocBaseBytes + kNoAllocCounterBytes + kNoAllocItemBytes;
+
+// One copy per GPU that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+// Device address of the scratch array on `device`, looked up once per device
+// with that device current (the array's name in host code is only a stand-in).
+dsp_status noalloc_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= 256) return fail(DSP_E_UNSUPPORTED, "device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[device] == nullptr) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc: cudaGetDevice");
+    if (cur != device) {
+      e = cudaSetDevice(device);
+      if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc: cudaSetDevice");
+    }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e2 = cur != device ? cudaSetDevice(cur) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc: cudaGetSymbolAddress");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "dsp_expand_leaves_noalloc: restoring the device");
+    g_noalloc_addr[device] = p;
+  }
+  *out = (unsigned char*)g_noalloc_addr[device];
+  return DSP_OK;
+}
+
+}  // namespace
+}  // namespace dsp
+
+extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job* jobs, int32_t n_jobs,
+                                                void* stream) {
+  using namespace dsp;
+  if (!m) return fail(DSP_E_INVALID, "dsp_expand_leaves_noalloc: model is NULL");
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(DSP_E_INVALID, "dsp_expand_leaves_noalloc: bad job array");
+  if (m->host->kind == DSP_MODEL_CAR)
+    return fail(DSP_E_UNSUPPORTED, "dsp_expand_leaves_noalloc: Rock Sample models only");
+  if (n_jobs == 0) return DSP_OK;
+  if (n_jobs > kNoAllocJobs)
+    return fail(DSP_E_UNSUPPORTED, "dsp_expand_leaves_noalloc: %d jobs, the fixed scratch holds at most %d", n_jobs,
+                kNoAllocJobs);
+  ExpandPlan plan;
+  dsp_status vs = plan_units(m, jobs, n_jobs, plan);
+  if (vs != DSP_OK) return vs;
+  if (plan.total_items > kNoAllocItems)
+    return fail(DSP_E_UNSUPPORTED,
+                "dsp_expand_leaves_noalloc: %lld (action, scenario) items, the fixed scratch holds at most %lld",
+                plan.total_items, kNoAllocItems);
+  unsigned char* base = nullptr;
+  vs = noalloc_scratch(m->device, &base);
+  if (vs != DSP_OK) return vs;
+  cudaStream_t st = (cudaStream_t)stream;
+  dsp_leaf_job* djobs = (dsp_leaf_job*)base;
+  long long* dbase = (long long*)(base + kNoAllocJobBytes);
+  unsigned int* counters = (unsigned int*)(base + kNoAllocJobBytes + kNoAllocBaseBytes);
+  uint32_t* items = (uint32_t*)(base + kNoAllocJobBytes + kNoAllocBaseBytes + kNoAllocCounterBytes);
+  cudaError_t e = cudaMemcpyAsync(djobs, jobs, sizeof(dsp_leaf_job) * (size_t)n_jobs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dbase, plan.item_base.data(), sizeof(long long) * plan.item_base.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kNoAllocCounterBytes, st);
+  if (e == cudaSuccess) {
+    int block_b = m->tune_block > 0 ? m->tune_block : 256;
+    e = launch_rs_expand(m->dmodel, m->host->robots, m->dwork, djobs, dbase, n_jobs, plan.total_items, items,
+                         counters, m->plan_step, m->num_sms, block_b, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc launch");
+  return DSP_OK;
+}
