@@ -151,6 +151,40 @@ typedef struct {
  * nothing. Asynchronous on `stream`. */
 dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
+/* Parameters of one planning step of the tree search (Sec. III-C). */
+typedef struct {
+  int32_t threads;       /* T search threads (trials per round), 1..256 */
+  int32_t rounds;        /* trial budget: rounds (deterministic) or trials per thread (free running) */
+  double time_limit_s;   /* free running: wall-clock budget, 0 = none */
+  double c_a;            /* PO-UCT exploration scale (Eq. UCT); 0 = plain DESPOT argmax of the upper bound */
+  double c_o;            /* virtual-loss scale, zeta = c_o * eps(b0) per traversing thread (Eq. augmented_WEU) */
+  double xi;             /* target uncertainty ratio of WEU (Eq. select_lb) */
+  double target_gap;     /* stop once the root gap U - L is at most this */
+  int32_t deterministic; /* 1: rounds (select in thread order, one batched expansion, backups in thread order);
+                            0: free-running threads, one CUDA stream each */
+} dsp_search_params;
+
+typedef struct {
+  double root_u, root_l;     /* root bounds (weighted by |Phi_b0|/K) */
+  int32_t action;            /* argmax_a of the lower bound of the root's actions, lowest index on ties */
+  int32_t nodes, expansions, rounds;
+  uint64_t scenario_steps;   /* g calls on live scenarios during the step */
+  uint64_t signature;        /* digest of the tree in node-creation order (depth, key, bounds, |Phi|, visits) */
+  double seconds;            /* wall-clock time of the step */
+} dsp_search_result;
+
+/* One planning step (Sec. III-A forward search, leaf initialisation on the
+ * GPU, Eq. backup): builds a DESPOT tree over the n root scenarios
+ * (root_states: HOST state block of capacity n; hist: HOST 32 belief
+ * counters or NULL) with T threads, scenario-based PO-UCT for actions,
+ * weighted excess uncertainty minus virtual loss for observations, one trial =
+ * descend to one leaf, expand it, back up. Stops at the trial budget, the
+ * time limit, a root gap <= target_gap, or when no branch is worth expanding.
+ * Synchronous; root_visits (HOST, |A| entries, may be NULL) gets N(b0, a).
+ * Device memory for the tree is allocated for the step and freed after it. */
+dsp_status dsp_plan(dsp_model* model, const uint32_t* root_states, int32_t n, const int8_t* hist,
+                    const dsp_search_params* params, dsp_search_result* result, int32_t* root_visits);
+
 /* Launch shape of dsp_expand_leaves (the paper's fixed mapping of actions to
  * blocks and scenarios to threads, Sec. III-D, made a tunable): block = CTA
  * size of the Rock Sample rollout phase (128, 256 or 512; the car kernel runs

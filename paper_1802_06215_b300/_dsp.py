@@ -176,3 +176,32 @@ def dsp_alu_probe(sink, iters, stream=0):
     ops = C.c_double(0)
     check(lib().dsp_alu_probe(C.c_void_p(sink), iters, C.byref(ops), C.c_void_p(stream)))
     return ops.value
+
+
+class dsp_search_params(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("rounds", C.c_int32), ("time_limit_s", C.c_double), ("c_a", C.c_double),
+                ("c_o", C.c_double), ("xi", C.c_double), ("target_gap", C.c_double), ("deterministic", C.c_int32)]
+
+
+class dsp_search_result(C.Structure):
+    _fields_ = [("root_u", C.c_double), ("root_l", C.c_double), ("action", C.c_int32), ("nodes", C.c_int32),
+                ("expansions", C.c_int32), ("rounds", C.c_int32), ("scenario_steps", C.c_uint64),
+                ("signature", C.c_uint64), ("seconds", C.c_double)]
+
+
+def dsp_plan(h, root_states, hist, params, num_actions):
+    """root_states: numpy uint32 (words, n); hist: numpy int8[32] or None."""
+    import numpy as np
+    rs = np.ascontiguousarray(root_states, dtype=np.uint32)
+    n = rs.shape[1]
+    hs = None if hist is None else np.ascontiguousarray(hist, dtype=np.int8)
+    res = dsp_search_result()
+    visits = np.zeros(num_actions, np.int32)
+    L = lib()
+    L.dsp_plan.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(dsp_search_params),
+                           C.POINTER(dsp_search_result), C.c_void_p]
+    check(L.dsp_plan(h, rs.ctypes.data, n, None if hs is None else hs.ctypes.data, C.byref(params), C.byref(res),
+                     visits.ctypes.data))
+    out = {f: getattr(res, f) for f, _ in dsp_search_result._fields_}
+    out["root_visits"] = visits
+    return out

@@ -152,7 +152,6 @@ void dsp_destroy_model(dsp_model* m) {
   if (!m) return;
   if (m->dmodel) cudaFree(m->dmodel);
   if (m->dwork) cudaFree(m->dwork);
-  if (m->scratch) cudaFree(m->scratch);
   delete m->host;
   delete m;
 }

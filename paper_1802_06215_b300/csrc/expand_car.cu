@@ -251,18 +251,17 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, car_expand_kernel<TPS>, 256, smem);
   per_sm = std::max(1, per_sm);
   int grid = std::max(1, std::min(n_units, per_sm * m->num_sms));
+  // observation slots, one per CTA, stream-ordered so that launches on other
+  // streams (other search threads) never share them
   size_t need = (size_t)grid * kMaxScen * kCarObsWords * sizeof(uint32_t);
-  if (m->scratch_bytes < need) {
-    if (m->scratch) cudaFree(m->scratch);
-    m->scratch = nullptr;
-    m->scratch_bytes = 0;
-    e = cudaMalloc(&m->scratch, need);
-    if (e != cudaSuccess) return e;
-    m->scratch_bytes = need;
-  }
+  uint32_t* scratch = nullptr;
+  e = cudaMallocAsync((void**)&scratch, need, st);
+  if (e != cudaSuccess) return e;
   car_expand_kernel<TPS><<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, head, m->plan_step,
-                                                   m->scratch);
-  return cudaGetLastError();
+                                                   scratch);
+  e = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  return e != cudaSuccess ? e : e2;
 }
 
 }  // namespace

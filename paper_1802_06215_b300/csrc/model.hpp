@@ -16,8 +16,6 @@ struct dsp_model {
   int num_sms = 0;
   int tune_block = 0;                // CTA size chosen by the autotuner (0 = default)
   int tune_tps = 0;                  // car: threads per scenario (0 = default)
-  uint32_t* scratch = nullptr;       // car: per-CTA observation slots of the expansion kernel
-  size_t scratch_bytes = 0;
 };
 
 namespace dsp {

@@ -1,0 +1,573 @@
+// Host tree search of HyP-DESPOT (Sec. III-C) around the GPU leaf expansion.
+//
+// T CPU threads search one DESPOT tree (Sec. III-A): each trial descends from
+// the root choosing actions by scenario-based PO-UCT (Eq. UCT) and
+// observation branches by weighted excess uncertainty minus virtual loss
+// (Eq. select_lb, Eq. augmented_WEU), expands the leaf it reaches on the GPU
+// (dsp_expand_leaves: Eq. expand, newnodes, ub, lb), creates the children on
+// the host and backs the bounds up to the root (Eq. backup). Node values are
+// kept weighted by |Phi_b|/K; a node's scenario list lives on the device as
+// the leaf states its expansion wrote, and its children refer to it through
+// the grouped positions (perm) the kernel wrote, so scenario data never comes
+// back to the host.
+//
+// Two schedules:
+//  - deterministic rounds: the T trials of a round select in thread order,
+//    their leaves are expanded as one batch, and they back up in thread
+//    order, so the tree is reproducible bit for bit;
+//  - free running: T std::threads, each with its own CUDA stream
+//    (Sec. III-D, node-level parallelism), selecting and backing up under one
+//    tree lock and expanding concurrently.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "model.hpp"
+
+namespace dsp {
+namespace {
+
+uint64_t mix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Device memory for one plan: bump allocation from 256 MB chunks.
+class Arena {
+ public:
+  ~Arena() {
+    for (void* p : chunks_) cudaFree(p);
+  }
+  cudaError_t alloc(size_t bytes, void** out) {
+    std::lock_guard<std::mutex> lock(mu_);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (chunks_.empty() || off_ + bytes > cap_) {
+      size_t cap = std::max(bytes, (size_t)256 << 20);
+      void* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, cap);
+      if (e != cudaSuccess) return e;
+      chunks_.push_back(p);
+      cap_ = cap;
+      off_ = 0;
+    }
+    *out = (char*)chunks_.back() + off_;
+    off_ += bytes;
+    return cudaSuccess;
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<void*> chunks_;
+  size_t cap_ = 0, off_ = 0;
+};
+
+struct Node;
+struct QBranch {
+  double R = 0, U = 0, L = 0;
+  std::vector<Node*> ch;
+};
+struct Node {
+  int depth = 0, n = 0;
+  double W = 1;
+  Node* parent = nullptr;
+  int pa = -1;                     // action into this node
+  const uint16_t* d_idx = nullptr; // positions in the parent's states (device)
+  uint32_t* d_states = nullptr;    // own states once expanded (root: the given ones)
+  uint16_t* d_perm = nullptr;      // grouped positions written by the expansion
+  int8_t hist[32] = {};
+  uint64_t key = 0;
+  bool term = false, expanded = false, claimed = false;
+  double U = 0, L = 0;
+  long long N = 0;
+  std::vector<long long> Na;
+  int vl = 0;
+  std::vector<QBranch> q;
+};
+
+// Pinned host buffer of one search thread, grown on demand.
+struct Pinned {
+  char* p = nullptr;
+  size_t cap = 0;
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+  cudaError_t reserve(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMallocHost((void**)&p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+};
+
+// Small per-job results, contiguous so one copy brings them to the host.
+struct JobOut {
+  int na = 0, cap = 0;
+  size_t bytes = 0;
+  size_t o_cnt = 0, o_off = 0, o_key = 0, o_rew = 0, o_u = 0, o_l = 0;
+  void layout(int na_, int cap_) {
+    na = na_;
+    cap = cap_;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+      size_t r = o;
+      o += (b + 15) & ~(size_t)15;
+      return r;
+    };
+    o_cnt = take(4 * (size_t)na);
+    o_off = take(4 * (size_t)na * (cap + 1));
+    o_key = take(8 * (size_t)na * cap);
+    o_rew = take(8 * (size_t)na * cap);
+    o_u = take(8 * (size_t)na * cap);
+    o_l = take(8 * (size_t)na * cap);
+    bytes = o;
+  }
+};
+
+class Search {
+ public:
+  Search(dsp_model* m, const dsp_search_params& p) : m_(m), p_(p) {
+    na_ = m->host->num_actions;
+    K_ = (double)m->host->K;
+    gamma_ = (double)m->host->gamma;
+    D_ = m->host->D;
+    words_ = m->host->words;
+    kind_ = m->host->kind;
+    per_ = m->host->per_robot;
+  }
+
+  dsp_status run(const uint32_t* root_host, int n, const int8_t* hist, dsp_search_result* out, int32_t* visits);
+
+ private:
+  struct Trial {
+    std::vector<Node*> path;
+    std::vector<int> acts;
+    Node* leaf = nullptr;
+  };
+
+  Node* new_node() {
+    pool_.emplace_back(new Node());
+    return pool_.back().get();
+  }
+
+  void observe(int8_t* h, int a, uint64_t key) const {
+    if (kind_ == DSP_MODEL_CAR) return;
+    int z = (int)(key & ~(1ull << 62));
+    int acts[2], zs[2], robots = kind_ == DSP_MODEL_GRID ? 1 : 2;
+    if (robots == 1) {
+      acts[0] = a;
+      zs[0] = z;
+    } else {
+      acts[0] = a / per_;
+      acts[1] = a % per_;
+      zs[0] = z / 3;
+      zs[1] = z % 3;
+    }
+    for (int r = 0; r < robots; ++r) {
+      if (acts[r] >= 5 && zs[r] != 0) {
+        int i = acts[r] - 5;
+        int v = (int)h[i] + (zs[r] == 1 ? 1 : -1);
+        h[i] = (int8_t)(v > 127 ? 127 : (v < -127 ? -127 : v));
+      }
+    }
+  }
+
+  void refresh(Node* b) {
+    double bu = -std::numeric_limits<double>::infinity(), bl = bu;
+    for (auto& q : b->q) {
+      bu = std::max(bu, q.U);
+      bl = std::max(bl, q.L);
+    }
+    b->U = bu;
+    b->L = bl;
+  }
+  void refresh_action(Node* b, int a) {
+    QBranch& q = b->q[a];
+    double su = 0, sl = 0;
+    for (Node* c : q.ch) {
+      su += c->U;
+      sl += c->L;
+    }
+    q.U = q.R + gamma_ * su;
+    q.L = q.R + gamma_ * sl;
+  }
+
+  int choose_action(Node* b) const {
+    int best = 0;
+    double bestv = -std::numeric_limits<double>::infinity();
+    for (int a = 0; a < (int)b->q.size(); ++a) {
+      double v = b->q[a].U / b->W;
+      if (p_.c_a != 0) {
+        if (b->Na[a] == 0)
+          v = std::numeric_limits<double>::infinity();
+        else
+          v += p_.c_a * std::sqrt(std::log((double)b->n * (double)b->N) / ((double)b->n * (double)b->Na[a]));
+      }
+      if (v > bestv) {
+        bestv = v;
+        best = a;
+      }
+    }
+    return best;
+  }
+
+  // Forward search of one trial from the root (caller holds the tree lock).
+  Trial select() {
+    Trial t;
+    Node* b = root_;
+    t.path.push_back(b);
+    while (true) {
+      if (!b->expanded) {
+        if (b->depth < D_ && !b->term && !b->claimed) {
+          b->claimed = true;
+          t.leaf = b;
+        }
+        return t;
+      }
+      b->N += 1;
+      int a = choose_action(b);
+      b->Na[a] += 1;
+      double eps0 = root_->U - root_->L;
+      Node* best = nullptr;
+      double beste = -std::numeric_limits<double>::infinity();
+      for (Node* c : b->q[a].ch) {
+        double e = (c->U - c->L) - c->W * p_.xi * eps0 - p_.c_o * eps0 * (double)c->vl;
+        if (e > beste) {
+          beste = e;
+          best = c;
+        }
+      }
+      t.acts.push_back(a);
+      if (best == nullptr || !(beste > 0)) return t;
+      best->vl += 1;
+      t.path.push_back(best);
+      b = best;
+    }
+  }
+
+  void backup(Trial& t) {
+    for (int i = (int)t.path.size() - 1; i >= 0; --i) {
+      Node* b = t.path[i];
+      if (i < (int)t.acts.size() && b->expanded) {
+        refresh_action(b, t.acts[i]);
+        refresh(b);
+      }
+      if (i > 0) b->vl -= 1;
+    }
+  }
+
+  // Device buffers and the job descriptor of one leaf (caller prepares `jo`).
+  dsp_status prepare(Node* b, dsp_leaf_job& J, const JobOut& jo, char* dsmall) {
+    int n = b->n;
+    std::memset(&J, 0, sizeof(J));
+    if (b->parent == nullptr) {
+      J.parent = b->d_states;
+      J.parent_cap = n;
+      J.idx = d_ident_;
+      J.last_action = -1;
+    } else {
+      J.parent = b->parent->d_states;
+      J.parent_cap = b->parent->n;
+      J.idx = b->d_idx;
+      J.last_action = b->pa;
+    }
+    J.n_scen = n;
+    J.depth = b->depth;
+    std::memcpy(J.hist, b->hist, 32);
+    J.first_action = 0;
+    J.n_actions = na_;
+    J.child_cap = jo.cap;
+    void* p = nullptr;
+    cudaError_t e = arena_.alloc((size_t)words_ * n * 4, &p);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: node states");
+    J.leaf_states = (uint32_t*)p;
+    e = arena_.alloc((size_t)na_ * n * 2, &p);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: grouped positions");
+    J.perm = (uint16_t*)p;
+    J.child_count = (int32_t*)(dsmall + jo.o_cnt);
+    J.child_off = (int32_t*)(dsmall + jo.o_off);
+    J.child_key = (uint64_t*)(dsmall + jo.o_key);
+    J.rew_sum = (int64_t*)(dsmall + jo.o_rew);
+    J.u_sum = (int64_t*)(dsmall + jo.o_u);
+    J.l_sum = (int64_t*)(dsmall + jo.o_l);
+    return DSP_OK;
+  }
+
+  // Children of an expanded leaf from its copied results (caller holds the
+  // tree lock in free-running mode).
+  void create_children(Node* b, const dsp_leaf_job& J, const JobOut& jo, const char* hsmall) {
+    const int32_t* cnt = (const int32_t*)(hsmall + jo.o_cnt);
+    const int32_t* off = (const int32_t*)(hsmall + jo.o_off);
+    const uint64_t* key = (const uint64_t*)(hsmall + jo.o_key);
+    const int64_t* rew = (const int64_t*)(hsmall + jo.o_rew);
+    const int64_t* us = (const int64_t*)(hsmall + jo.o_u);
+    const int64_t* ls = (const int64_t*)(hsmall + jo.o_l);
+    b->d_states = J.leaf_states;
+    b->d_perm = J.perm;
+    b->q.assign(na_, QBranch());
+    b->Na.assign(na_, 0);
+    const int cap = jo.cap, n = b->n;
+    for (int a = 0; a < na_; ++a) {
+      QBranch& q = b->q[a];
+      int nc = std::min(cnt[a], cap);
+      int64_t rsum = 0;
+      for (int c = 0; c < nc; ++c) rsum += rew[(size_t)a * cap + c];
+      q.R = ((double)rsum / 4294967296.0) / K_;
+      double su = 0, sl = 0;
+      for (int c = 0; c < nc; ++c) {
+        Node* ch = new_node();
+        int o0 = off[(size_t)a * (cap + 1) + c], o1 = off[(size_t)a * (cap + 1) + c + 1];
+        ch->depth = b->depth + 1;
+        ch->n = o1 - o0;
+        ch->W = (double)ch->n / K_;
+        ch->parent = b;
+        ch->pa = a;
+        ch->d_idx = J.perm + (size_t)a * n + o0;
+        ch->key = key[(size_t)a * cap + c];
+        ch->term = (ch->key >> 62) & 1u;
+        std::memcpy(ch->hist, b->hist, 32);
+        observe(ch->hist, a, ch->key);
+        ch->U = ((double)us[(size_t)a * cap + c] / 4294967296.0) / K_;
+        ch->L = ((double)ls[(size_t)a * cap + c] / 4294967296.0) / K_;
+        q.ch.push_back(ch);
+        su += ch->U;
+        sl += ch->L;
+      }
+      q.U = q.R + gamma_ * su;
+      q.L = q.R + gamma_ * sl;
+    }
+    b->expanded = true;
+    refresh(b);
+  }
+
+  // Expands leaves as one batch on `st` and creates their children in order.
+  dsp_status expand_batch(const std::vector<Node*>& leaves, cudaStream_t st, Pinned& pinned) {
+    int L = (int)leaves.size();
+    std::vector<dsp_leaf_job> jobs(L);
+    std::vector<JobOut> jo(L);
+    size_t total = 0;
+    std::vector<size_t> base(L);
+    for (int k = 0; k < L; ++k) {
+      jo[k].layout(na_, dsp_max_children(m_, leaves[k]->n));
+      base[k] = total;
+      total += jo[k].bytes;
+    }
+    void* dsmall = nullptr;
+    cudaError_t e = arena_.alloc(total, &dsmall);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: results");
+    for (int k = 0; k < L; ++k) {
+      dsp_status s = prepare(leaves[k], jobs[k], jo[k], (char*)dsmall + base[k]);
+      if (s != DSP_OK) return s;
+    }
+    dsp_status s = dsp_expand_leaves(m_, jobs.data(), L, st);
+    if (s != DSP_OK) return s;
+    e = pinned.reserve(total);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: pinned results");
+    char* host = pinned.p;
+    e = cudaMemcpyAsync(host, dsmall, total, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: results copy");
+    {
+      std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
+      if (p_.deterministic == 0) lock.lock();
+      for (int k = 0; k < L; ++k) create_children(leaves[k], jobs[k], jo[k], host + base[k]);
+    }
+    expansions_ += L;
+    return DSP_OK;
+  }
+
+  dsp_status run_rounds();
+  dsp_status run_threads();
+
+  dsp_model* m_;
+  dsp_search_params p_;
+  int na_, D_, words_, kind_, per_;
+  double K_, gamma_;
+  Arena arena_;
+  std::vector<std::unique_ptr<Node>> pool_;
+  Node* root_ = nullptr;
+  uint16_t* d_ident_ = nullptr;
+  std::mutex tree_mu_;
+  std::atomic<int> expansions_{0};
+  int rounds_ = 0;
+};
+
+dsp_status Search::run_rounds() {
+  cudaStream_t st;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: stream");
+  Pinned staging;
+  dsp_status s = DSP_OK;
+  for (int r = 0; r < p_.rounds; ++r) {
+    std::vector<Trial> trials;
+    for (int t = 0; t < p_.threads; ++t) trials.push_back(select());
+    std::vector<Node*> leaves;
+    for (auto& t : trials)
+      if (t.leaf) leaves.push_back(t.leaf);
+    if (!leaves.empty()) {
+      s = expand_batch(leaves, st, staging);
+      if (s != DSP_OK) break;
+    }
+    for (auto& t : trials) backup(t);
+    for (Node* l : leaves) l->claimed = false;
+    rounds_ += 1;
+    if (root_->expanded && root_->U - root_->L <= p_.target_gap) break;
+    if (leaves.empty()) break;
+  }
+  cudaStreamDestroy(st);
+  return s;
+}
+
+dsp_status Search::run_threads() {
+  auto t0 = std::chrono::steady_clock::now();
+  std::atomic<bool> stop{false};
+  std::atomic<int> in_flight{0};
+  std::vector<dsp_status> status(p_.threads, DSP_OK);
+  const long long budget = (long long)p_.threads * p_.rounds;
+  long long started = 0;  // expansions begun (guarded by the tree lock)
+  auto worker = [&](int tid) {
+    cudaSetDevice(m_->device);
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      status[tid] = fail(DSP_E_CUDA, "dsp_plan: stream");
+      stop = true;
+      return;
+    }
+    Pinned staging;
+    while (!stop.load()) {
+      Trial t;
+      {
+        std::lock_guard<std::mutex> lock(tree_mu_);
+        if (stop.load()) break;
+        if (started >= budget) {  // every budgeted expansion is taken
+          stop = true;
+          break;
+        }
+        t = select();
+        if (t.leaf) {
+          in_flight += 1;
+          started += 1;
+        }
+      }
+      if (t.leaf) {
+        dsp_status s = expand_batch({t.leaf}, st, staging);
+        std::lock_guard<std::mutex> lock(tree_mu_);
+        in_flight -= 1;
+        if (s != DSP_OK) {
+          status[tid] = s;
+          stop = true;
+        }
+        backup(t);
+        t.leaf->claimed = false;
+      } else {
+        std::lock_guard<std::mutex> lock(tree_mu_);
+        backup(t);
+        if (in_flight.load() == 0) stop = true;  // nothing left worth expanding
+      }
+      {
+        std::lock_guard<std::mutex> lock(tree_mu_);
+        if (root_->expanded && root_->U - root_->L <= p_.target_gap) stop = true;
+      }
+      if (p_.time_limit_s > 0) {
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el >= p_.time_limit_s) stop = true;
+      }
+      if (!t.leaf && !stop.load()) std::this_thread::yield();
+    }
+    cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> th;
+  for (int i = 0; i < p_.threads; ++i) th.emplace_back(worker, i);
+  for (auto& x : th) x.join();
+  for (auto s : status)
+    if (s != DSP_OK) return s;
+  return DSP_OK;
+}
+
+dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp_search_result* out,
+                       int32_t* visits) {
+  auto t0 = std::chrono::steady_clock::now();
+  root_ = new_node();
+  root_->n = n;
+  root_->W = (double)n / K_;
+  if (hist) std::memcpy(root_->hist, hist, 32);
+  void* p = nullptr;
+  cudaError_t e = arena_.alloc((size_t)words_ * n * 4, &p);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: root states");
+  root_->d_states = (uint32_t*)p;
+  e = cudaMemcpy(root_->d_states, root_host, (size_t)words_ * n * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: root upload");
+  e = arena_.alloc((size_t)n * 2, &p);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: identity");
+  d_ident_ = (uint16_t*)p;
+  std::vector<uint16_t> ident(n);
+  for (int i = 0; i < n; ++i) ident[i] = (uint16_t)i;
+  e = cudaMemcpy(d_ident_, ident.data(), (size_t)n * 2, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: identity upload");
+  uint64_t steps0 = 0, steps1 = 0;
+  uint32_t status = 0;
+  dsp_status s = dsp_read_counters(m_, &steps0, &status);
+  if (s != DSP_OK) return s;
+  s = p_.deterministic ? run_rounds() : run_threads();
+  if (s != DSP_OK) return s;
+  s = dsp_read_counters(m_, &steps1, &status);
+  if (s != DSP_OK) return s;
+  if (status != 0) return fail(DSP_E_DEVICE, "dsp_plan: device status word %u", status);
+  out->root_u = root_->U;
+  out->root_l = root_->L;
+  out->nodes = (int32_t)pool_.size();
+  out->expansions = expansions_.load();
+  out->rounds = rounds_;
+  out->scenario_steps = steps1 - steps0;
+  int best = -1;
+  double bl = -std::numeric_limits<double>::infinity();
+  for (int a = 0; a < (int)root_->q.size(); ++a)
+    if (root_->q[a].L > bl) {
+      bl = root_->q[a].L;
+      best = a;
+    }
+  out->action = best;
+  uint64_t sig = 0x12345678ull;
+  for (auto& up : pool_) {
+    Node* v = up.get();
+    uint64_t ub, lb;
+    std::memcpy(&ub, &v->U, 8);
+    std::memcpy(&lb, &v->L, 8);
+    sig = mix64(sig ^ (uint64_t)v->depth) ^ v->key;
+    sig = mix64(sig ^ ub) ^ lb;
+    sig = mix64(sig ^ (uint64_t)v->n ^ ((uint64_t)v->N << 32));
+  }
+  out->signature = sig;
+  if (visits)
+    for (int a = 0; a < (int)root_->Na.size(); ++a) visits[a] = (int32_t)root_->Na[a];
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return DSP_OK;
+}
+
+}  // namespace
+}  // namespace dsp
+
+extern "C" dsp_status dsp_plan(dsp_model* m, const uint32_t* root_states, int32_t n, const int8_t* hist,
+                               const dsp_search_params* p, dsp_search_result* out, int32_t* root_visits) {
+  using namespace dsp;
+  if (!m || !root_states || !p || !out) return fail(DSP_E_INVALID, "dsp_plan: NULL argument");
+  if (n < 1 || n > kMaxScen || n > m->host->K) return fail(DSP_E_INVALID, "dsp_plan: %d root scenarios", n);
+  if (p->threads < 1 || p->threads > 256) return fail(DSP_E_INVALID, "dsp_plan: threads %d", p->threads);
+  if (p->rounds < 1) return fail(DSP_E_INVALID, "dsp_plan: rounds %d", p->rounds);
+  std::memset(out, 0, sizeof(*out));
+  Search s(m, *p);
+  return s.run(root_states, n, hist, out, root_visits);
+}

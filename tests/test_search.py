@@ -1,0 +1,108 @@
+"""Tree search (Sec. III-C) on the GPU expansion against the CPU oracle.
+
+Deterministic rounds must reproduce the oracle's search bit for bit (root
+bounds, decision, node count, visit counts, tree digest); free-running threads
+must keep valid bounds around the exhaustive optimum."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_06215_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06215_b300 import _dsp, batch, build
+    build.build()
+    return _dsp, batch
+
+
+def root_states(cfg, rng, n=None):
+    n = cfg.K if n is None else n
+    if cfg.kind == I.CAR:
+        base = (rng.uniform(0, 40, cfg.P), rng.uniform(0, 40, cfg.P))
+        return I.car_block(cfg, n, rng, s=0.0, v=1, base=base, jitter=0.0)
+    pos = [(0, cfg.n // 2), (0, cfg.n // 2 - 1)][: (2 if cfg.kind == I.MULTIGRID else 1)]
+    return I.rs_block(cfg, n, rng, pos=pos)
+
+
+def plan_both(env, cfg, b, **kw):
+    _dsp, batch = env
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=kw.get("threads", 1), rounds=kw.get("rounds", 20), time_limit_s=0.0,
+                               c_a=kw.get("c_a", 0.0), c_o=kw.get("c_o", 0.0), xi=kw.get("xi", 0.95),
+                               target_gap=kw.get("target_gap", 0.0), deterministic=1)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    o = oracle.Model(cfg).plan(b, None, threads=p.threads, rounds=p.rounds, c_a=p.c_a, c_o=p.c_o, xi=p.xi,
+                               target_gap=p.target_gap)
+    m.close()
+    return g, o
+
+
+@pytest.mark.parametrize("name,cfg_fn,kw", [
+    ("rs7_8 plain DESPOT", I.rs7_8, dict(threads=1, rounds=30)),
+    ("rs7_8 T=4 UCT+vloss", I.rs7_8, dict(threads=4, rounds=25, c_a=1.0, c_o=0.5)),
+    ("rs15_15 T=4", I.rs15_15, dict(threads=4, rounds=10, c_a=1.0, c_o=0.5)),
+    ("mars small", lambda: I.grid_config(7, 4, K=40, D=30, seed=3, robots=2), dict(threads=4, rounds=8, c_a=1.0,
+                                                                                   c_o=0.5)),
+    ("car small", lambda: I.car_config(P=10, K=40, D=20, seed=2), dict(threads=2, rounds=6, c_a=1.0, c_o=0.5)),
+])
+def test_deterministic_rounds_match_oracle(env, name, cfg_fn, kw):
+    cfg = cfg_fn()
+    b = root_states(cfg, np.random.default_rng(7))
+    g, o = plan_both(env, cfg, b, **kw)
+    assert g["root_u"] == o["root_u"] and g["root_l"] == o["root_l"], name
+    assert g["action"] == o["action"], name
+    assert g["nodes"] == o["nodes"] and g["expansions"] == o["expansions"] and g["rounds"] == o["rounds"], name
+    assert np.array_equal(g["root_visits"], o["root_na"]), name
+    assert g["signature"] == o["signature"], name
+    assert g["scenario_steps"] == o["steps"], name
+
+
+def test_search_converges_to_exhaustive_optimum(env):
+    """xi = 0 expands every branch with a gap: the root bounds meet at V*_D of
+    the tiny scenario tree (3x3 map, 2 rocks, K = 6, D = 4)."""
+    cfg = I.Config(kind=I.GRID, n=3, m=2, K=6, D=4, seed=1,
+                   rock_cells=np.array([1 | (1 << 8), 2], np.int32))
+    b = root_states(cfg, np.random.default_rng(1))
+    vstar = oracle.Model(cfg, fp64=True).exhaustive(b, None, 0)
+    g, o = plan_both(env, cfg, b, threads=2, rounds=100000, xi=0.0)
+    assert abs(g["root_u"] - vstar) < 1e-5 and abs(g["root_l"] - vstar) < 1e-5
+
+
+@pytest.mark.parametrize("threads", [1, 4, 16])
+def test_free_running_threads_valid(env, threads):
+    """Free-running threads with PO-UCT and virtual loss: bounds stay around
+    the exhaustive optimum and the budget holds."""
+    _dsp, batch = env
+    cfg = I.Config(kind=I.MULTIGRID, n=3, m=2, K=6, D=4, seed=4,
+                   rock_cells=np.array([1 | (1 << 8), 2], np.int32))
+    b = root_states(cfg, np.random.default_rng(4))
+    vstar = oracle.Model(cfg, fp64=True).exhaustive(b, None, 0)
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=threads, rounds=20, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    assert g["root_l"] <= vstar + 1e-5 and vstar <= g["root_u"] + 1e-5
+    assert 1 <= g["expansions"] <= threads * 20
+    assert g["root_visits"].sum() >= 1
+    m.close()
+
+
+def test_free_running_rs15_time_limit(env):
+    """The 15x15 task with 4 threads under a time budget returns valid bounds."""
+    _dsp, batch = env
+    cfg = I.rs15_15()
+    b = root_states(cfg, np.random.default_rng(2))
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=4, rounds=100000, time_limit_s=0.5, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    assert g["root_l"] <= g["root_u"] + 1e-9
+    assert g["expansions"] >= 4 and g["seconds"] < 5.0
+    m.close()
