@@ -151,6 +151,28 @@ typedef struct {
  * nothing. Asynchronous on `stream`. */
 dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
+/* Device job queue (Sec. III-D, node-level parallelism: the paper launches one
+ * kernel per leaf on the submitting thread's stream; here one persistent
+ * kernel, launched from a CUDA graph, pulls leaf jobs that many host threads
+ * submit). Jobs go into a ring of `capacity` slots in mapped pinned host
+ * memory; the kernel takes them in ticket order, expands each (same results
+ * as dsp_expand_leaves) and marks it done; it exits after idle_ns nanoseconds
+ * without a job (0 = 2 ms) and a monitor thread relaunches it when jobs are
+ * pending. Rock Sample models only (DSP_E_UNSUPPORTED for the car). All job
+ * pointers are device memory. submit and wait are thread-safe. */
+typedef struct dsp_queue dsp_queue;
+dsp_status dsp_queue_create(dsp_model* model, int32_t capacity, uint64_t idle_ns, dsp_queue** out);
+/* Publishes one job (copied); *ticket identifies it. Waits at most timeout_ns
+ * (0 = no limit) for a free slot, else DSP_E_QUEUE_FULL with no ticket taken. */
+dsp_status dsp_queue_submit(dsp_queue* queue, const dsp_leaf_job* job, uint64_t timeout_ns, uint64_t* ticket);
+/* Waits at most timeout_ns (0 = no limit) until the job's results are written
+ * (DSP_E_TIMEOUT otherwise); DSP_E_CUDA if the persistent kernel failed. */
+dsp_status dsp_queue_wait(dsp_queue* queue, uint64_t ticket, uint64_t timeout_ns);
+/* Kernel launches so far and tickets handed out. */
+dsp_status dsp_queue_stats(dsp_queue* queue, uint64_t* launches, uint64_t* submitted);
+/* Finishes the submitted jobs, stops the kernel and frees the queue. */
+void dsp_queue_destroy(dsp_queue* queue);
+
 /* Parameters of one planning step of the tree search (Sec. III-C). */
 typedef struct {
   int32_t threads;       /* T search threads (trials per round), 1..256 */

@@ -205,3 +205,41 @@ def dsp_plan(h, root_states, hist, params, num_actions):
     out = {f: getattr(res, f) for f, _ in dsp_search_result._fields_}
     out["root_visits"] = visits
     return out
+
+
+def dsp_queue_create(h, capacity, idle_ns=0):
+    L = lib()
+    L.dsp_queue_create.argtypes = [C.c_void_p, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]
+    q = C.c_void_p()
+    check(L.dsp_queue_create(h, capacity, idle_ns, C.byref(q)))
+    return q
+
+
+def dsp_queue_submit(q, job, timeout_ns=0):
+    """job: a dsp_leaf_job (device pointers); returns the ticket."""
+    L = lib()
+    L.dsp_queue_submit.argtypes = [C.c_void_p, C.POINTER(dsp_leaf_job), C.c_uint64, C.POINTER(C.c_uint64)]
+    t = C.c_uint64(0)
+    check(L.dsp_queue_submit(q, C.byref(job), timeout_ns, C.byref(t)))
+    return t.value
+
+
+def dsp_queue_wait(q, ticket, timeout_ns=0):
+    L = lib()
+    L.dsp_queue_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64]
+    check(L.dsp_queue_wait(q, ticket, timeout_ns))
+
+
+def dsp_queue_stats(q):
+    L = lib()
+    L.dsp_queue_stats.argtypes = [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+    a, b = C.c_uint64(0), C.c_uint64(0)
+    check(L.dsp_queue_stats(q, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def dsp_queue_destroy(q):
+    L = lib()
+    L.dsp_queue_destroy.argtypes = [C.c_void_p]
+    L.dsp_queue_destroy.restype = None
+    L.dsp_queue_destroy(q)

@@ -88,29 +88,15 @@ struct Items {
   __device__ __forceinline__ uint32_t* f(int k) const { return base + (size_t)k * total; }
 };
 
+// Phase A for the job in S.J (index j in its job table, first item ibase). All
+// threads of the CTA call it; it ends with a barrier.
 template <int R>
-__global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
-                                                             const dsp_leaf_job* __restrict__ jobs,
-                                                             const long long* __restrict__ item_base, int n_jobs,
-                                                             unsigned int* head, uint32_t plan_step,
-                                                             Items<R> items) {
-  __shared__ RSGroupSmem S;
-  load_rs_consts(S.c, gm);
-  const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
+__device__ void rs_group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase, Items<R> items,
+                             DevWork* work, unsigned long long& steps) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned long long steps = 0;
-  __syncthreads();
-  while (true) {
-    if (tid == 0) {
-      S.job = (int)atomicAdd(head, 1u);
-      if (S.job < n_jobs) S.J = jobs[S.job];
-    }
-    __syncthreads();
-    const int j = S.job;
-    if (j >= n_jobs) break;
+  {
     const dsp_leaf_job& J = S.J;
     const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
-    const long long ibase = item_base[j];
 
     // gather + update, once per job
     for (int p = tid; p < n; p += kBlockA) {
@@ -251,27 +237,39 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
       __syncthreads();
     }
   }
-  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
-  if (lane == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
 template <int R>
-__global__ void __launch_bounds__(512) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
-                                                              const dsp_leaf_job* __restrict__ jobs,
-                                                              Items<R> items, unsigned int* chunk_head,
-                                                              uint32_t plan_step) {
-  __shared__ RSShared c;
-  load_rs_consts(c, gm);
-  __syncthreads();
-  const RSModel<R> M = make_rs<R>(gm, &c, plan_step);
-  const int lane = threadIdx.x & 31;
-  const long long nchunks = (items.total + 31) >> 5;
+__global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                             const dsp_leaf_job* __restrict__ jobs,
+                                                             const long long* __restrict__ item_base, int n_jobs,
+                                                             unsigned int* head, uint32_t plan_step,
+                                                             Items<R> items) {
+  __shared__ RSGroupSmem S;
+  load_rs_consts(S.c, gm);
+  const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
   unsigned long long steps = 0;
+  __syncthreads();
   while (true) {
-    long long chunk = 0;
-    if (lane == 0) chunk = (long long)atomicAdd(chunk_head, 1u);
-    chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
-    if (chunk >= nchunks) break;
+    if (threadIdx.x == 0) {
+      S.job = (int)atomicAdd(head, 1u);
+      if (S.job < n_jobs) S.J = jobs[S.job];
+    }
+    __syncthreads();
+    const int j = S.job;
+    if (j >= n_jobs) break;
+    rs_group_job<R>(S, M, j, item_base[j], items, work, steps);
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
+// Phase B for one 32-item chunk of the item list (one whole warp calls it).
+template <int R>
+__device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_leaf_job* __restrict__ jobs,
+                                                 Items<R> items, long long chunk, unsigned long long& steps) {
+  const int lane = threadIdx.x & 31;
+  {
     const long long it = chunk * 32 + lane;
     const bool ok = it < items.total;
     uint32_t job = 0xFFFFFFFFu, slot = 0;
@@ -318,6 +316,27 @@ __global__ void __launch_bounds__(512) rs_rollout_items_kernel(const DevModel* _
       atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)fu);
       atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)fl);
     }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(512) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                              const dsp_leaf_job* __restrict__ jobs,
+                                                              Items<R> items, unsigned int* chunk_head,
+                                                              uint32_t plan_step) {
+  __shared__ RSShared c;
+  load_rs_consts(c, gm);
+  __syncthreads();
+  const RSModel<R> M = make_rs<R>(gm, &c, plan_step);
+  const int lane = threadIdx.x & 31;
+  const long long nchunks = (items.total + 31) >> 5;
+  unsigned long long steps = 0;
+  while (true) {
+    long long chunk = 0;
+    if (lane == 0) chunk = (long long)atomicAdd(chunk_head, 1u);
+    chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+    if (chunk >= nchunks) break;
+    rs_rollout_chunk<R>(M, jobs, items, chunk, steps);
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);
@@ -388,9 +407,128 @@ cudaError_t launch_two_phase(const DevModel* gm, DevWork* work, const dsp_leaf_j
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ job queue ---
+// Persistent expansion fed by host threads through a ring in mapped pinned
+// host memory (ticket t lives in slot t % cap: seq = t + 1 once its job is
+// published, seq = t + cap once the slot may take ticket t + cap; done = t + 1
+// once its results are written). A CTA claims the next ticket only after its
+// job is published, so no ticket is ever held without a job; then it runs
+// phase A and phase B of that job itself on its own scratch slot. Every wait
+// is bounded by %globaltimer: a CTA that finds no job for idle_ns (or finds
+// the ring closed and empty) exits, and the host relaunches the kernel when
+// more jobs arrive.
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int R>
+__global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                             QueueRing ring, unsigned long long* head,
+                                                             uint32_t plan_step, uint32_t* scratch,
+                                                             size_t slot_words, dsp_leaf_job* jcopy,
+                                                             unsigned long long idle_ns) {
+  __shared__ RSGroupSmem S;
+  __shared__ long long s_ticket;
+  __shared__ int s_chunk;
+  load_rs_consts(S.c, gm);
+  const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
+  const int tid = threadIdx.x, lane = tid & 31;
+  dsp_leaf_job* myjob = jcopy + blockIdx.x;
+  unsigned long long steps = 0;
+  __syncthreads();
+  while (true) {
+    if (tid == 0) {
+      long long ticket = -1;
+      unsigned long long deadline = global_ns() + idle_ns;
+      while (true) {
+        unsigned long long h = *(volatile unsigned long long*)head;
+        unsigned long long s = ld_acquire_sys(ring.seq + (h % ring.cap));
+        if (s == h + 1) {
+          if (atomicCAS(head, h, h + 1) == h) {
+            ticket = (long long)h;
+            break;
+          }
+          continue;
+        }
+        if (*(volatile unsigned int*)ring.close != 0u || global_ns() > deadline) break;
+        __nanosleep(500);
+      }
+      s_ticket = ticket;
+      if (ticket >= 0) {
+        const int slot = (int)(ticket % ring.cap);
+        const volatile uint32_t* src = (const volatile uint32_t*)(ring.jobs + slot);
+        uint32_t* dst = (uint32_t*)&S.J;
+        for (int w = 0; w < (int)(sizeof(dsp_leaf_job) / 4); ++w) dst[w] = src[w];
+        *myjob = S.J;
+        st_release_sys(ring.seq + slot, (unsigned long long)ticket + ring.cap);
+      }
+    }
+    __syncthreads();
+    const long long ticket = s_ticket;
+    if (ticket < 0) break;
+    const int n = S.J.n_scen;
+    if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
+      Items<R> items{scratch + (size_t)blockIdx.x * slot_words, (long long)n * S.J.n_actions};
+      __threadfence_block();
+      rs_group_job<R>(S, M, 0, 0, items, work, steps);
+      if (tid == 0) s_chunk = 0;
+      __syncthreads();
+      const long long nchunks = (items.total + 31) >> 5;
+      while (true) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(&s_chunk, 1);
+        chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+        if (chunk >= nchunks) break;
+        rs_rollout_chunk<R>(M, myjob, items, chunk, steps);
+      }
+    }
+    __threadfence_system();
+    __syncthreads();
+    if (tid == 0) st_release_sys(ring.done + (ticket % ring.cap), (unsigned long long)ticket + 1);
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if (lane == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
 }  // namespace
 
 int rs_item_fields(int robots) { return robots == 2 ? Items<2>::kFields : Items<1>::kFields; }
+
+size_t rs_queue_slot_words(int robots, int num_actions) {
+  return (size_t)rs_item_fields(robots) * (size_t)kMaxScen * (size_t)num_actions;
+}
+
+int rs_queue_blocks_per_sm(int robots) {
+  int n = 0;
+  if (robots == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_queue_kernel<1>, kBlockA, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_queue_kernel<2>, kBlockA, 0);
+  return n > 0 ? n : 1;
+}
+
+cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, QueueRing ring, unsigned long long* head,
+                            uint32_t plan_step, uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy,
+                            unsigned long long idle_ns, int grid, cudaStream_t st) {
+  if (robots == 1)
+    rs_queue_kernel<1><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, plan_step, scratch, slot_words, jcopy,
+                                                 idle_ns);
+  else
+    rs_queue_kernel<2><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, plan_step, scratch, slot_words, jcopy,
+                                                 idle_ns);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, int n_jobs, long long total_items, uint32_t* item_buf,

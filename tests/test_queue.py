@@ -1,0 +1,111 @@
+"""Device job queue: many host threads submit leaves of uneven |Phi_b| to one
+persistent kernel; results must equal dsp_expand_leaves bit for bit."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1802_06215_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("leaf", "child_count", "child_off", "key", "rew", "u", "l", "perm")
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06215_b300 import _dsp, batch, build
+    build.build()
+    return torch, _dsp, batch
+
+
+def _run_threads(_dsp, q, jb, n_threads):
+    errors = []
+    idx = list(range(len(jb.jobs)))
+
+    def worker(tid):
+        try:
+            for k in idx[tid::n_threads]:
+                t = _dsp.dsp_queue_submit(q, jb.descs[k], 10_000_000_000)
+                _dsp.dsp_queue_wait(q, t, 30_000_000_000)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(n_threads)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errors, errors
+
+
+@pytest.mark.parametrize("mk,njobs,threads", [(I.mars15_15, 48, 16), (I.rs15_15, 96, 16), (I.rs7_8, 40, 4)])
+def test_queue_matches_batch(env, mk, njobs, threads):
+    torch, _dsp, batch = env
+    cfg = mk()
+    m = batch.Model(cfg)
+    jobs = I.job_stream(cfg, njobs, 17)
+    ref = batch.JobBatch(m, jobs)
+    ref.run()
+    torch.cuda.synchronize()
+    out = batch.JobBatch(m, jobs)
+    q = _dsp.dsp_queue_create(m.h, 64)
+    _run_threads(_dsp, q, out, threads)
+    launches, submitted = _dsp.dsp_queue_stats(q)
+    _dsp.dsp_queue_destroy(q)
+    assert submitted == njobs and launches >= 1
+    _, status = m.counters()
+    assert status == 0
+    for k, (a, b) in enumerate(zip(ref.all_results(), out.all_results())):
+        for f in FIELDS:
+            assert np.array_equal(a[f], b[f]), (k, f)
+    m.close()
+
+
+def test_queue_relaunch_after_idle(env):
+    """With a 50 us idle limit the kernel's bounded wait runs out between
+    bursts; the monitor relaunches it and every job still completes."""
+    torch, _dsp, batch = env
+    cfg = I.rs15_15()
+    m = batch.Model(cfg)
+    jobs = I.job_stream(cfg, 12, 23, max_scen=100)
+    ref = batch.JobBatch(m, jobs)
+    ref.run()
+    out = batch.JobBatch(m, jobs)
+    q = _dsp.dsp_queue_create(m.h, 4, 50_000)
+    for burst in (range(0, 6), range(6, 12)):
+        tickets = [_dsp.dsp_queue_submit(q, out.descs[k], 10_000_000_000) for k in burst]
+        for t in tickets:
+            _dsp.dsp_queue_wait(q, t, 30_000_000_000)
+        time.sleep(0.05)
+    launches, submitted = _dsp.dsp_queue_stats(q)
+    _dsp.dsp_queue_destroy(q)
+    assert submitted == 12 and launches >= 2
+    for k, (a, b) in enumerate(zip(ref.all_results(), out.all_results())):
+        for f in FIELDS:
+            assert np.array_equal(a[f], b[f]), (k, f)
+    m.close()
+
+
+def test_queue_rejects_bad_input(env):
+    torch, _dsp, batch = env
+    m = batch.Model(I.rs7_8())
+    q = _dsp.dsp_queue_create(m.h, 8)
+    with pytest.raises(_dsp.DspError) as e:
+        _dsp.dsp_queue_wait(q, 5, 1000)  # never issued
+    assert e.value.status == _dsp.DSP_E_INVALID
+    bad = _dsp.dsp_leaf_job()  # null pointers, zero scenarios
+    with pytest.raises(_dsp.DspError) as e:
+        _dsp.dsp_queue_submit(q, bad, 1000)
+    assert e.value.status in (_dsp.DSP_E_INVALID, _dsp.DSP_E_UNSUPPORTED)
+    _dsp.dsp_queue_destroy(q)
+    car = batch.Model(I.car50())
+    with pytest.raises(_dsp.DspError) as e:
+        _dsp.dsp_queue_create(car.h, 8)
+    assert e.value.status == _dsp.DSP_E_UNSUPPORTED
+    car.close()
+    m.close()
