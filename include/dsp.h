@@ -184,6 +184,8 @@ typedef struct {
   double target_gap;     /* stop once the root gap U - L is at most this */
   int32_t deterministic; /* 1: rounds (select in thread order, one batched expansion, backups in thread order);
                             0: free-running threads, one CUDA stream each */
+  int32_t use_queue;     /* free running, Rock Sample: threads submit their leaves to one device job queue
+                            (dsp_queue_*) instead of launching their own expansions */
 } dsp_search_params;
 
 typedef struct {

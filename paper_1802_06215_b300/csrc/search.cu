@@ -372,7 +372,15 @@ class Search {
       dsp_status s = prepare(leaves[k], jobs[k], jo[k], (char*)dsmall + base[k]);
       if (s != DSP_OK) return s;
     }
-    dsp_status s = dsp_expand_leaves(m_, jobs.data(), L, st);
+    dsp_status s = DSP_OK;
+    if (queue_ != nullptr) {
+      // through the device job queue: publish, wait (bounded), then copy
+      std::vector<uint64_t> tickets(L);
+      for (int k = 0; k < L && s == DSP_OK; ++k) s = dsp_queue_submit(queue_, &jobs[k], 10000000000ull, &tickets[k]);
+      for (int k = 0; k < L && s == DSP_OK; ++k) s = dsp_queue_wait(queue_, tickets[k], 60000000000ull);
+    } else {
+      s = dsp_expand_leaves(m_, jobs.data(), L, st);
+    }
     if (s != DSP_OK) return s;
     e = pinned.reserve(total);
     if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: pinned results");
@@ -402,6 +410,7 @@ class Search {
   uint16_t* d_ident_ = nullptr;
   std::mutex tree_mu_;
   std::atomic<int> expansions_{0};
+  dsp_queue* queue_ = nullptr;  // free running with use_queue: the shared device job queue
   int rounds_ = 0;
 };
 
@@ -521,7 +530,15 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   uint32_t status = 0;
   dsp_status s = dsp_read_counters(m_, &steps0, &status);
   if (s != DSP_OK) return s;
+  if (!p_.deterministic && p_.use_queue) {
+    s = dsp_queue_create(m_, 4 * p_.threads, 0, &queue_);
+    if (s != DSP_OK) return s;
+  }
   s = p_.deterministic ? run_rounds() : run_threads();
+  if (queue_ != nullptr) {
+    dsp_queue_destroy(queue_);
+    queue_ = nullptr;
+  }
   if (s != DSP_OK) return s;
   s = dsp_read_counters(m_, &steps1, &status);
   if (s != DSP_OK) return s;

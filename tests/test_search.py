@@ -106,3 +106,36 @@ def test_free_running_rs15_time_limit(env):
     assert g["root_l"] <= g["root_u"] + 1e-9
     assert g["expansions"] >= 4 and g["seconds"] < 5.0
     m.close()
+
+
+@pytest.mark.parametrize("mk", [lambda: I.Config(kind=I.MULTIGRID, n=3, m=2, K=6, D=4, seed=4,
+                                                 rock_cells=np.array([1 | (1 << 8), 2], np.int32))])
+def test_free_running_through_queue(env, mk):
+    """16 threads submitting their leaves to the device job queue: valid
+    bounds around the exhaustive optimum."""
+    _dsp, batch = env
+    cfg = mk()
+    b = root_states(cfg, np.random.default_rng(4))
+    vstar = oracle.Model(cfg, fp64=True).exhaustive(b, None, 0)
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=16, rounds=10, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, use_queue=1)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    assert g["root_l"] <= vstar + 1e-5 and vstar <= g["root_u"] + 1e-5
+    assert 1 <= g["expansions"] <= 160
+    m.close()
+
+
+def test_mars15_16_threads_queue(env):
+    """The two-robot 15x15 task (400 joint actions, K = 500) planned by 16
+    threads through the queue for 1 s: valid bounds, many expansions."""
+    _dsp, batch = env
+    cfg = I.mars15_15()
+    b = root_states(cfg, np.random.default_rng(3))
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=16, rounds=100000, time_limit_s=1.0, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, use_queue=1)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    assert g["root_l"] <= g["root_u"] + 1e-9
+    assert g["expansions"] >= 16
+    m.close()
