@@ -242,6 +242,15 @@ dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
  * a host array, copied before return. */
 dsp_status dsp_expand_leaves_noalloc(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
+/* Autotuner (the paper fixes the work-to-thread mapping, Sec. III-D; here it
+ * is measured): times dsp_expand_leaves on the caller's jobs (HOST array, as
+ * for dsp_expand_leaves; results are written to their buffers) for every
+ * candidate launch shape, `reps` timed calls each after one warm-up, keeps the
+ * fastest in the model (dsp_set_tuning) and returns it with its mean time in
+ * ms. Synchronises `stream`. */
+dsp_status dsp_autotune(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, int32_t reps, void* stream,
+                        int32_t* best_block, int32_t* best_tps, float* best_ms);
+
 /* Scenario-steps (g calls on live scenarios: update + expansion + rollout
  * steps) counted by the kernels since the last reset, and the device status
  * word (0 = fine). Synchronises the device. */

@@ -1,0 +1,67 @@
+// Autotuner of the expansion's launch shape. The paper fixes the mapping of
+// work to the GPU (actions to thread blocks, scenarios to threads, factored
+// elements to warps; Sec. III-D); here the mapping is a parameter: the CTA
+// size of the Rock Sample rollout phase, or the lanes that share one car
+// scenario (element-level parallelism). Each candidate is timed with CUDA
+// events on the caller's jobs and the fastest is kept in the model.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "model.hpp"
+
+extern "C" dsp_status dsp_autotune(dsp_model* m, const dsp_leaf_job* jobs, int32_t n_jobs, int32_t reps,
+                                   void* stream, int32_t* best_block, int32_t* best_tps, float* best_ms) {
+  using namespace dsp;
+  if (!m || !jobs || n_jobs < 1 || reps < 1 || !best_block || !best_tps || !best_ms)
+    return fail(DSP_E_INVALID, "dsp_autotune: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<std::pair<int, int>> cands;
+  if (m->host->kind == DSP_MODEL_CAR)
+    cands = {{0, 4}, {0, 8}, {0, 16}, {0, 32}};
+  else
+    cands = {{128, 0}, {256, 0}, {512, 0}};
+  const int keep_block = m->tune_block, keep_tps = m->tune_tps;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(DSP_E_CUDA, "dsp_autotune: events");
+  float best = -1.0f;
+  int bb = keep_block, bt = keep_tps;
+  dsp_status s = DSP_OK;
+  for (auto& c : cands) {
+    m->tune_block = c.first;
+    m->tune_tps = c.second;
+    s = dsp_expand_leaves(m, jobs, n_jobs, st);  // warm-up
+    if (s != DSP_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && s == DSP_OK; ++r) s = dsp_expand_leaves(m, jobs, n_jobs, st);
+    cudaEventRecord(e1, st);
+    if (s != DSP_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "dsp_autotune: timing");
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (best < 0 || ms < best) {
+      best = ms;
+      bb = c.first;
+      bt = c.second;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != DSP_OK) {
+    m->tune_block = keep_block;
+    m->tune_tps = keep_tps;
+    return s;
+  }
+  m->tune_block = bb;
+  m->tune_tps = bt;
+  *best_block = bb > 0 ? bb : 256;
+  *best_tps = bt > 0 ? bt : 16;
+  *best_ms = best;
+  return DSP_OK;
+}
