@@ -11,11 +11,15 @@ D. Prints one JSON line.
 
 value = scenario-steps/s (g calls on live scenarios, counted in-kernel) with
 inputs resident in HBM; e2e = the same through pinned host buffers with the
-inputs copied in and every result copied out inside the timed region.
+inputs copied in and every result copied out inside the timed region. A
+planning step (multi-threaded tree search, Sec. III-C) afterwards gives the
+root bound gap.
 """
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -30,18 +34,22 @@ import numpy as np  # noqa: E402
 from paper_1802_06215_b300 import inputs  # noqa: E402
 
 WORKLOADS = {
-    # name: (config factory, jobs per step, description)
+    # name: (config factory, jobs per step, description, planning (threads, seconds, use_queue))
     "rs15_15": (inputs.rs15_15, 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=500, D=90; 4096 leaf jobs, "
-                                      "|Phi_b|~U{1..500}, depth~U{0..10}"),
+                                      "|Phi_b|~U{1..500}, depth~U{0..10}", (4, 0.5, 0)),
     "rs7_8": (inputs.rs7_8, 4096, "Rock Sample 7x7, 8 rocks, |A|=13, K=100, D=90; 4096 leaf jobs, "
-                                  "|Phi_b|~U{1..100}, depth~U{0..10}"),
+                                  "|Phi_b|~U{1..100}, depth~U{0..10}", (4, 0.5, 0)),
     "mars15_15": (inputs.mars15_15, 512, "two-robot Rock Sample 15x15, 15 rocks, |A|=400, K=500, D=90; 512 leaf "
-                                         "jobs, |Phi_b|~U{1..500}, depth~U{0..10}"),
+                                         "jobs, |Phi_b|~U{1..500}, depth~U{0..10}", (16, 0.5, 1)),
     "car50": (inputs.car50, 1024, "car among 50 pedestrians, |A|=3, K=500, D=50; 1024 leaf jobs, "
-                                  "|Phi_b|~U{1..500}, depth~U{0..10}"),
+                                  "|Phi_b|~U{1..500}, depth~U{0..10}", (4, 0.1, 0)),
 }
 SMS, LANES_PER_SM, MAX_SM_MHZ = 148, 128, 2032.0
 METRIC = "scenario-steps/sec and leaf expansions/sec at K=500, D=90 (fraction of roofline); root gap"
+KERNEL_SOURCES = {
+    "rs": ["expand_rs.cu", "rs_model.cuh", "common.cuh"],
+    "car": ["expand_car.cu", "car_model.cuh", "group.cuh", "common.cuh"],
+}
 
 
 def parse():
@@ -54,63 +62,75 @@ def parse():
     p.add_argument("--jobs", type=int, default=0, help="override jobs per step")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plan", action="store_true")
     return p.parse_args()
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clocks and throttle reasons sampled every 5 ms through NVML while the
+    timed region runs (nvidia-smi every 200 ms if NVML is unavailable)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap"}
 
     def __init__(self, index):
         self.index = index
-        self.proc = None
-        self.lines = []
+        self.samples = []
+        self.method = "nvml"
+        self.error = None
+        self.stop = threading.Event()
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
-            self.proc = None
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def _run(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            reasons = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
+            while not self.stop.is_set():
+                sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+                self.samples.append((sm, mx, reasons(h)))
+                time.sleep(0.002)
+            return
+        except Exception as e:
+            self.error = repr(e)[:120]
+            self.method = "nvidia-smi"
+        proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm",
+                                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                stderr=subprocess.DEVNULL, text=True)
+        while not self.stop.is_set():
+            line = proc.stdout.readline()
+            try:
+                a, b = (float(x) for x in line.split(","))
+                self.samples.append((a, b, 0))
+            except ValueError:
+                pass
+        proc.terminate()
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
+        self.stop.set()
+        self.t.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set()
+        for _, _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        out = {"sm_mhz": statistics.median(s[0] for s in self.samples),
+               "sm_max_mhz": max(s[1] for s in self.samples), "reasons": sorted(reasons),
+               "samples": len(self.samples), "method": self.method}
+        if self.error:
+            out["nvml_error"] = self.error
+        return out
 
 
 def cpu_oracle_run(cfg, jobs, seconds, threads):
@@ -145,10 +165,14 @@ def cpu_oracle_run(cfg, jobs, seconds, threads):
     return dict(steps=steps, jobs=done, seconds=dt, ops=ops)
 
 
+def _dtype(cfg):
+    return "f32" if cfg.kind == inputs.CAR else "int32"
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    mk, njobs, desc = WORKLOADS[args.workload]
+    mk, njobs, desc, _ = WORKLOADS[args.workload]
     cfg = mk()
     njobs = args.jobs or njobs
     jobs = inputs.job_stream(cfg, njobs, 1000)
@@ -163,7 +187,7 @@ def run_reference(args, rank, world):
         tot_jobs += r["jobs"]
         tot_t += r["seconds"]
     value = tot_steps / tot_t
-    sample = f"each step: leading jobs of the {njobs}-job stream for ~{per_step:.1f} s on {cores} threads"
+    sample = f"each step: leading jobs of the {njobs}-job stream for up to {per_step:.1f} s on {cores} threads"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "scenario-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": _dtype(cfg),
@@ -175,8 +199,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _dtype(cfg):
-    return "f32" if cfg.kind == inputs.CAR else "int32"
+def source_digest(kind):
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_1802_06215_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(workload, kind):
+    """DRAM bytes per launch of this workload's expansion kernels from the
+    committed ncu summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    digest = source_digest(kind)
+    for line in open(path):
+        m = re.match(r"\|\s*(\w+)\s*\|\s*([0-9.eE+]+)\s*\|\s*(\w+)\s*\|", line)
+        if m and m.group(1) == workload and m.group(3) == digest:
+            return float(m.group(2))
+    return None
+
+
+def root_states(cfg, rng):
+    if cfg.kind == inputs.CAR:
+        base = (rng.uniform(0, 40, cfg.P), rng.uniform(0, 40, cfg.P))
+        b = inputs.car_block(cfg, cfg.K, rng, s=0.0, v=0, base=base, jitter=0.0)
+        return b
+    pos = [(0, cfg.n // 2), (0, cfg.n // 2 - 1)][: (2 if cfg.kind == inputs.MULTIGRID else 1)]
+    return inputs.rs_block(cfg, cfg.K, rng, pos=pos)
+
+
+def planning_step(_dsp, m, cfg, plan):
+    threads, seconds, use_queue = plan
+    b = root_states(cfg, np.random.default_rng(99))
+    p = _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=seconds, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, use_queue=use_queue)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    return {"root_u": g["root_u"], "root_l": g["root_l"], "root_gap": g["root_u"] - g["root_l"],
+            "threads": threads, "planning_time_s": seconds, "through_queue": bool(use_queue),
+            "expansions": g["expansions"], "nodes": g["nodes"], "seconds": g["seconds"],
+            "expansions_per_s": g["expansions"] / g["seconds"],
+            "scenario_steps_per_s": g["scenario_steps"] / g["seconds"], "action": g["action"]}
 
 
 def run_ours(args, rank, world):
@@ -189,7 +253,7 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl")
     from paper_1802_06215_b300 import _dsp, batch, build
     build.build()
-    mk, njobs, desc = WORKLOADS[args.workload]
+    mk, njobs, desc, plan = WORKLOADS[args.workload]
     cfg = mk()
     njobs = args.jobs or njobs
     jobs = inputs.job_stream(cfg, njobs, 1000 + rank)
@@ -200,10 +264,12 @@ def run_ours(args, rank, world):
     for _ in range(max(3, args.warmup)):
         jb.run()
     torch.cuda.synchronize()
+    kernels_per_step = 1 if cfg.kind == inputs.CAR else 2
 
     # device-resident timing (L2 flushed before every step, outside the events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     m.reset_counters()
+    _dsp.dsp_kernel_timing(m.h, True)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -214,6 +280,7 @@ def run_ours(args, rank, world):
             jb.run()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+    kernel_ms, kernel_calls = _dsp.dsp_kernel_timing(m.h, False)
     times = [a.elapsed_time(b) for a, b in ev]
     steps_total, status = m.counters()
     if status != 0:
@@ -265,25 +332,34 @@ def run_ours(args, rank, world):
             dist.destroy_process_group()
         return
     clocks = clk.summary()
+    planning = None if args.no_plan else planning_step(_dsp, m, cfg, plan)
     cpu = None
     ops_per_step = None
     if not args.no_cpu_baseline:
         r1 = cpu_oracle_run(cfg, jobs, args.cpu_seconds, 1)
         ops_per_step = r1["ops"] / max(1, r1["steps"])
+        cores = os.cpu_count() or 1
+        rn = cpu_oracle_run(cfg, jobs, args.cpu_seconds / 2, cores)
         cpu = {"value": r1["steps"] / r1["seconds"], "unit": "scenario-steps/s", "cores": 1, "kind": "oracle",
                "sample": f"first {r1['jobs']} of the {njobs} jobs of this workload, single-threaded, "
-                         f"{r1['seconds']:.1f} s", "ops_per_scenario_step": ops_per_step}
-    avg_launch_s = t_ms / args.steps / 1000.0
-    max_mhz = clocks.get("sm_max_mhz") or MAX_SM_MHZ
+                         f"{r1['seconds']:.1f} s", "ops_per_scenario_step": ops_per_step,
+               "all_cores": {"value": rn["steps"] / rn["seconds"], "cores": cores,
+                             "sample": f"first {rn['jobs']} jobs on {cores} threads, {rn['seconds']:.1f} s"}}
+    kind = "car" if cfg.kind == inputs.CAR else "rs"
+    avg_kernel_s = kernel_ms / max(1, kernel_calls) / 1000.0
     peak_tops = SMS * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     roof = None
     if ops_per_step:
-        achieved = ops_per_step * steps_per_launch / avg_launch_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s", "frac": achieved / peak_tops,
-                "traffic": None, "peak_source": "148 SMs x 128 lanes x 2032 MHz (issue rate, one 32-bit op per lane "
-                                                 "per clock)", "probe_tops": probe_tops,
-                "ops_per_scenario_step": ops_per_step, "kernel": "rs_expand_kernel" if cfg.kind != inputs.CAR
-                else "car_expand_kernel"}
+        achieved = ops_per_step * steps_per_launch / avg_kernel_s / 1e12
+        traffic = measured_traffic(args.workload, kind)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": traffic,
+                "peak_source": "derived: 148 SMs x 128 lanes x 2032 MHz (one 32-bit op per lane per clock)",
+                "probe_tops": probe_tops, "ops_per_scenario_step": ops_per_step,
+                "kernel": ("rs_group_kernel + rs_rollout_items_kernel (one expansion)" if kind == "rs"
+                           else "car_expand_kernel"),
+                "kernel_ms_per_launch": avg_kernel_s * 1000.0,
+                "achieved_hbm_gbs": (jb.input_bytes + jb.output_bytes) / avg_kernel_s / 1e9}
     line = {
         "metric": METRIC, "value": value, "unit": "scenario-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -294,9 +370,10 @@ def run_ours(args, rank, world):
         "scenario_steps_per_step": steps_per_launch,
         "e2e": {"value": e2_value, "unit": "scenario-steps/s", "h2d_bytes_per_step": jb.input_bytes,
                 "d2h_bytes_per_step": jb.output_bytes},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * kernels_per_step,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "planning": planning,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -308,9 +385,7 @@ def run_ours(args, rank, world):
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus else 1))
-    if world != args.gpus and "WORLD_SIZE" not in os.environ:
-        world = 1
+    world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

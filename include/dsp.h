@@ -242,6 +242,12 @@ dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
  * a host array, copied before return. */
 dsp_status dsp_expand_leaves_noalloc(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
+/* Measurement support (no counterpart in the paper): returns the summed GPU
+ * time of the expansion kernels of every dsp_expand_leaves call recorded since
+ * the last call (CUDA events on each call's stream, around its kernels only),
+ * then turns recording on (enable = 1) or off. Synchronises those events. */
+dsp_status dsp_kernel_timing(dsp_model* model, int32_t enable, double* total_ms, int32_t* calls);
+
 /* Autotuner (the paper fixes the work-to-thread mapping, Sec. III-D; here it
  * is measured): times dsp_expand_leaves on the caller's jobs (HOST array, as
  * for dsp_expand_leaves; results are written to their buffers) for every

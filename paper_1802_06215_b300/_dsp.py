@@ -244,3 +244,13 @@ def dsp_queue_destroy(q):
     L.dsp_queue_destroy.argtypes = [C.c_void_p]
     L.dsp_queue_destroy.restype = None
     L.dsp_queue_destroy(q)
+
+
+def dsp_kernel_timing(h, enable):
+    """(summed ms of the expansion kernels recorded so far, calls); then
+    recording is switched on or off."""
+    L = lib()
+    L.dsp_kernel_timing.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+    ms, n = C.c_double(0), C.c_int32(0)
+    check(L.dsp_kernel_timing(h, 1 if enable else 0, C.byref(ms), C.byref(n)))
+    return ms.value, n.value

@@ -152,6 +152,7 @@ void dsp_destroy_model(dsp_model* m) {
   if (!m) return;
   if (m->dmodel) cudaFree(m->dmodel);
   if (m->dwork) cudaFree(m->dwork);
+  for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
   delete m->host;
   delete m;
 }
@@ -268,6 +269,27 @@ dsp_status dsp_get_tuning(const dsp_model* m, int32_t* block, int32_t* tps) {
   return DSP_OK;
 }
 
+dsp_status dsp_kernel_timing(dsp_model* m, int32_t enable, double* total_ms, int32_t* calls) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_kernel_timing: model is NULL");
+  std::lock_guard<std::mutex> lock(m->timing_mu);
+  double tot = 0;
+  int n = 0;
+  for (size_t i = 0; i + 1 < m->timing_events.size(); i += 2) {
+    cudaError_t e = cudaEventSynchronize(m->timing_events[i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_kernel_timing");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, m->timing_events[i], m->timing_events[i + 1]);
+    tot += ms;
+    n += 1;
+  }
+  for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
+  m->timing_events.clear();
+  m->timing = enable != 0;
+  if (total_ms) *total_ms = tot;
+  if (calls) *calls = n;
+  return DSP_OK;
+}
+
 dsp_status dsp_reset_counters(dsp_model* m, void* stream) {
   if (!m) return fail(DSP_E_INVALID, "dsp_reset_counters: model is NULL");
   cudaError_t e = cudaMemsetAsync(m->dwork, 0, sizeof(DevWork), (cudaStream_t)stream);
@@ -338,12 +360,24 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 256, st);
   if (e == cudaSuccess) {
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (m->timing) {
+      cudaEventCreate(&ev[0]);
+      cudaEventCreate(&ev[1]);
+      cudaEventRecord(ev[0], st);
+    }
     if (car) {
       e = launch_car_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
       e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, (const long long*)dunits, n_jobs,
                            plan.total_items, items, counters, m->plan_step, m->num_sms, block_b, st);
+    }
+    if (m->timing) {
+      cudaEventRecord(ev[1], st);
+      std::lock_guard<std::mutex> lock(m->timing_mu);
+      m->timing_events.push_back(ev[0]);
+      m->timing_events.push_back(ev[1]);
     }
   }
   cudaError_t e2 = cudaFreeAsync(buf, st);
