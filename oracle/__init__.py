@@ -218,3 +218,64 @@ def ops_read():
     f = lib().orc_ops_read
     f.restype = C.c_uint64
     return int(f())
+
+
+MLP_IN, MLP_HID, MLP_OUT = 64, 256, 32
+
+
+def _w(weights):
+    names = ("W1", "b1", "W2", "b2", "W3", "b3")
+    arrs = [np.ascontiguousarray(weights[k], np.float64) for k in names]
+    return arrs, [_p(a, _F64) for a in arrs]
+
+
+def mlp_forward(weights, X, bf16=False):
+    """Logits (B, 32) of the policy network; bf16=True: BF16 weights, features
+    and activations with FP32 sums (the tensor-core arithmetic)."""
+    keep, ptrs = _w(weights)
+    X = np.ascontiguousarray(X, np.float64)
+    out = np.zeros((X.shape[0], MLP_OUT), np.float64)
+    lib().orc_mlp_forward(*ptrs, _p(X, _F64), C.c_int32(X.shape[0]), C.c_int32(1 if bf16 else 0), _p(out, _F64))
+    return out
+
+
+def mlp_loss_grad(weights, X, y, n_actions):
+    """Mean softmax cross-entropy and its FP64 gradient (dict like weights)."""
+    keep, ptrs = _w(weights)
+    X = np.ascontiguousarray(X, np.float64)
+    y = np.ascontiguousarray(y, np.int32)
+    g = {k: np.zeros_like(np.asarray(weights[k], np.float64)) for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    loss = C.c_double(0)
+    lib().orc_mlp_loss_grad(*ptrs, _p(X, _F64), _p(y, _I32), C.c_int32(X.shape[0]), C.c_int32(n_actions),
+                            C.byref(loss), *[_p(g[k], _F64) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+    return loss.value, g
+
+
+def features_rs(model, block, hist):
+    block = np.ascontiguousarray(block, np.uint32)
+    w, cap = block.shape
+    h = None if hist is None else np.ascontiguousarray(hist, np.int8).reshape(cap, 32)
+    out = np.zeros((cap, MLP_IN), np.float32)
+    lib().orc_features_rs(C.byref(model.c), _p(block, _U32), C.c_int32(cap), C.c_int32(cap),
+                          None if h is None else _p(h, _I8), _p(out, _F32))
+    return out
+
+
+def rollout_learned(model, block, hist, start_depth, weights, logged=None, tol=1e-2):
+    """Learned-policy rollout values (one robot); with `logged` actions
+    (count x D) it replays them and returns, per scenario, the steps whose
+    logged action loses to the network's argmax by more than `tol`."""
+    block = np.ascontiguousarray(block, np.uint32)
+    w, cap = block.shape
+    h = None if hist is None else np.ascontiguousarray(hist, np.int8).reshape(cap, 32)
+    keep, ptrs = _w(weights)
+    vals = np.zeros(cap, np.float64)
+    bad = np.zeros(cap, np.int32)
+    lg = None if logged is None else np.ascontiguousarray(logged, np.int32)
+    steps = C.c_uint64(0)
+    rc = lib().orc_rollout_learned(C.byref(model.c), _p(block, _U32), C.c_int32(cap), C.c_int32(cap),
+                                   None if h is None else _p(h, _I8), C.c_int32(start_depth), *ptrs,
+                                   None if lg is None else _p(lg, _I32), C.c_double(tol), _p(vals, _F64),
+                                   _p(bad, _I32), C.byref(steps))
+    assert rc == 0
+    return vals, bad, steps.value

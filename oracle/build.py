@@ -7,7 +7,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = ["capi.cpp", "mlp.cpp"]
+SRC = ["capi.cpp"]
 OUT = os.path.join(HERE, "liboracle.so")
 
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "despot.hpp"
+#include "mlp.hpp"
 
 using namespace orc;
 
@@ -284,6 +285,92 @@ double orc_exhaustive(const orc_model* d, const uint32_t* block, int32_t n, cons
     v = exhaustive_value(m, st, hist_from(hist), depth);
   });
   return v;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------- learned pi0 ---
+
+extern "C" {
+
+int32_t orc_mlp_forward(const double* W1, const double* b1, const double* W2, const double* b2, const double* W3,
+                        const double* b3, const double* X, int32_t B, int32_t bf16, double* logits) {
+  return mlp_forward(W1, b1, W2, b2, W3, b3, X, B, bf16, logits);
+}
+
+int32_t orc_mlp_loss_grad(const double* W1, const double* b1, const double* W2, const double* b2, const double* W3,
+                          const double* b3, const double* X, const int32_t* y, int32_t B, int32_t n_actions,
+                          double* loss, double* gW1, double* gb1, double* gW2, double* gb2, double* gW3,
+                          double* gb3) {
+  return mlp_loss_grad(W1, b1, W2, b2, W3, b3, X, y, B, n_actions, loss, gW1, gb1, gW2, gb2, gW3, gb3);
+}
+
+int32_t orc_features_rs(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,
+                        float* out) {
+  return features_rs(d->n, d->m, d->rock_cells, block, cap, count, hist, out);
+}
+
+// Default-policy rollout (Eq. lb) of one-robot Rock Sample with the learned
+// policy: at every step the features of (state, counters) go through the
+// network in its BF16/FP32 form and the action is the argmax over the first
+// |A| logits (lowest index on ties). With `logged` (count x D actions) the
+// rollout follows the logged actions instead and counts, per scenario, the
+// steps whose logged action differs from this argmax by more than `tol` in
+// logit margin.
+int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count,
+                            const int8_t* hist, int32_t start_depth, const double* W1, const double* b1,
+                            const double* W2, const double* b2, const double* W3, const double* b3,
+                            const int32_t* logged, double tol, double* values, int32_t* disagree,
+                            uint64_t* steps) {
+  if (d->kind != 0) return 1;
+  RockSample<float> m = make_rs<float>(d);
+  Net w{W1, b1, W2, b2, W3, b3};
+  const int na = m.num_actions();
+  uint64_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    RSState s = m.unpack(block, cap, i);
+    Hist h = hist_from(hist ? hist + 32 * (size_t)i : nullptr);
+    float v = 0.0f;
+    int t = start_depth, k = 0, bad = 0;
+    while (t < m.D && !m.terminal(s)) {
+      // features of this state and history (the same map as features_rs)
+      uint32_t one[5];
+      for (int f = 0; f < 5; ++f) one[f] = 0;
+      m.pack(s, one, 1, 0);
+      int8_t hh[32];
+      for (int r = 0; r < 32; ++r) hh[r] = h.c[r];
+      float fx[kMlpIn];
+      features_rs(d->n, d->m, d->rock_cells, one, 1, 1, hh, fx);
+      double x64[kMlpIn], lg[kMlpOut];
+      for (int q = 0; q < kMlpIn; ++q) x64[q] = (double)fx[q];
+      forward_bf16(w, x64, lg);
+      int best = 0;
+      for (int a = 1; a < na; ++a)
+        if (lg[a] > lg[best]) best = a;
+      double second = -1e300;
+      for (int a = 0; a < na; ++a)
+        if (a != best && lg[a] > second) second = lg[a];
+      int a = best;
+      if (logged) {
+        a = logged[(size_t)i * m.D + k];
+        if (a != best && lg[best] - lg[a] > tol) bad += 1;
+      }
+      RSState next;
+      uint64_t key;
+      float r = m.step(s, a, t, next, &key);
+      m.observe(h, a, key);
+      v = v + m.G[t - start_depth] * r;
+      s = next;
+      t += 1;
+      k += 1;
+    }
+    if (!m.terminal(s)) v = v + m.G[m.D - start_depth] * m.tail(s);
+    values[i] = (double)v;
+    if (disagree) disagree[i] = bad;
+    total += (uint64_t)k;
+  }
+  *steps = total;
+  return 0;
 }
 
 }  // extern "C"
