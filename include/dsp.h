@@ -242,6 +242,31 @@ dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
  * a host array, copied before return. */
 dsp_status dsp_expand_leaves_noalloc(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
+/* Learned default policy pi0 (the paper's pi0 is a hand-written default
+ * policy, Sec. III-D, Eq. lb; this one is learned): an MLP 64 -> 256 -> 256 -> 32
+ * with ReLU hidden layers whose first |A| logits score the actions, trained by
+ * imitation (softmax cross-entropy) on (state features, planner action)
+ * pairs. FP32 master weights with Adam; BF16 copies feed the tensor-core
+ * GEMMs (FP32 accumulation). Packed FP32 parameter layout (input-major):
+ * W1[64][256] b1[256] W2[256][256] b2[256] W3[256][32] b3[32] (90656 floats).
+ * Features of one-robot Rock Sample: x/n, y/n, then per rock (rock x - x)/n,
+ * (rock y - y)/n, clamp(counter, -3, 3)/3, sampled; zero-padded to 64. */
+typedef struct dsp_mlp dsp_mlp;
+/* He-normal weights from `seed`, zero biases; buffers for batches <= max_batch. */
+dsp_status dsp_mlp_create(int32_t max_batch, uint64_t seed, dsp_mlp** out);
+void dsp_mlp_destroy(dsp_mlp* mlp);
+dsp_status dsp_mlp_set_weights(dsp_mlp* mlp, const float* host_params);  /* packed FP32, host */
+dsp_status dsp_mlp_get_weights(const dsp_mlp* mlp, float* host_params);
+/* logits (device, B x 32 FP32) of features X (device, B x 64 FP32). */
+dsp_status dsp_mlp_forward(dsp_mlp* mlp, const float* X, int32_t B, float* logits, void* stream);
+/* Mean loss over the batch and its packed FP32 gradient (host), no update. */
+dsp_status dsp_mlp_grad(dsp_mlp* mlp, const float* X, const int32_t* y, int32_t B, int32_t n_actions, float* loss,
+                        float* grad_host, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr); *loss (host,
+ * may be NULL) gets the batch's mean loss before the step. */
+dsp_status dsp_mlp_train_step(dsp_mlp* mlp, const float* X, const int32_t* y, int32_t B, int32_t n_actions,
+                              float lr, float* loss, void* stream);
+
 /* Measurement support (no counterpart in the paper): returns the summed GPU
  * time of the expansion kernels of every dsp_expand_leaves call recorded since
  * the last call (CUDA events on each call's stream, around its kernels only),

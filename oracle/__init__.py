@@ -239,15 +239,17 @@ def mlp_forward(weights, X, bf16=False):
     return out
 
 
-def mlp_loss_grad(weights, X, y, n_actions):
-    """Mean softmax cross-entropy and its FP64 gradient (dict like weights)."""
+def mlp_loss_grad(weights, X, y, n_actions, bf16_forward=False):
+    """Mean softmax cross-entropy and its FP64 gradient (dict like weights);
+    bf16_forward=True evaluates it at the BF16/FP32 forward's activations."""
     keep, ptrs = _w(weights)
     X = np.ascontiguousarray(X, np.float64)
     y = np.ascontiguousarray(y, np.int32)
     g = {k: np.zeros_like(np.asarray(weights[k], np.float64)) for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
     loss = C.c_double(0)
     lib().orc_mlp_loss_grad(*ptrs, _p(X, _F64), _p(y, _I32), C.c_int32(X.shape[0]), C.c_int32(n_actions),
-                            C.byref(loss), *[_p(g[k], _F64) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+                            C.byref(loss), *[_p(g[k], _F64) for k in ("W1", "b1", "W2", "b2", "W3", "b3")],
+                            C.c_int32(1 if bf16_forward else 0))
     return loss.value, g
 
 

@@ -301,8 +301,9 @@ int32_t orc_mlp_forward(const double* W1, const double* b1, const double* W2, co
 int32_t orc_mlp_loss_grad(const double* W1, const double* b1, const double* W2, const double* b2, const double* W3,
                           const double* b3, const double* X, const int32_t* y, int32_t B, int32_t n_actions,
                           double* loss, double* gW1, double* gb1, double* gW2, double* gb2, double* gW3,
-                          double* gb3) {
-  return mlp_loss_grad(W1, b1, W2, b2, W3, b3, X, y, B, n_actions, loss, gW1, gb1, gW2, gb2, gW3, gb3);
+                          double* gb3, int32_t bf16_forward) {
+  return mlp_loss_grad(W1, b1, W2, b2, W3, b3, X, y, B, n_actions, loss, gW1, gb1, gW2, gb2, gW3, gb3,
+                       bf16_forward);
 }
 
 int32_t orc_features_rs(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,

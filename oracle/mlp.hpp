@@ -54,7 +54,8 @@ inline void forward64(const Net& w, const double* x, double* h1, double* h2, dou
   }
 }
 
-inline void forward_bf16(const Net& w, const double* x64, double* logit) {
+inline void forward_bf16(const Net& w, const double* x64, double* logit, double* h1_out = nullptr,
+                         double* h2_out = nullptr) {
   float x[kMlpIn], h1[kMlpHid], h2[kMlpHid];
   for (int k = 0; k < kMlpIn; ++k) x[k] = bf16_round((float)x64[k]);
   for (int n = 0; n < kMlpHid; ++n) {
@@ -74,6 +75,10 @@ inline void forward_bf16(const Net& w, const double* x64, double* logit) {
     for (int k = 0; k < kMlpHid; ++k) s += h2[k] * bf16_round((float)w.W3[k * kMlpOut + n]);
     logit[n] = (double)(s + (float)w.b3[n]);
   }
+  if (h1_out)
+    for (int n = 0; n < kMlpHid; ++n) h1_out[n] = (double)h1[n];
+  if (h2_out)
+    for (int n = 0; n < kMlpHid; ++n) h2_out[n] = (double)h2[n];
 }
 
 
@@ -94,9 +99,12 @@ inline int mlp_forward(const double* W1, const double* b1, const double* W2, con
 
 // Mean softmax cross-entropy over the batch (softmax over the first n_actions
 // logits, target y[i]) and its gradient with respect to every parameter, FP64.
+// bf16_forward = 1 takes the activations and logits of the BF16/FP32 forward
+// form (the backward stays FP64): the gradient the BF16 network has.
 inline int mlp_loss_grad(const double* W1, const double* b1, const double* W2, const double* b2, const double* W3,
                       const double* b3, const double* X, const int32_t* y, int B, int n_actions, double* loss,
-                      double* gW1, double* gb1, double* gW2, double* gb2, double* gW3, double* gb3) {
+                      double* gW1, double* gb1, double* gW2, double* gb2, double* gW3, double* gb3,
+                      int bf16_forward = 0) {
   Net w{W1, b1, W2, b2, W3, b3};
   std::memset(gW1, 0, sizeof(double) * kMlpIn * kMlpHid);
   std::memset(gb1, 0, sizeof(double) * kMlpHid);
@@ -108,7 +116,10 @@ inline int mlp_loss_grad(const double* W1, const double* b1, const double* W2, c
   double total = 0;
   for (int i = 0; i < B; ++i) {
     const double* x = X + (size_t)i * kMlpIn;
-    forward64(w, x, h1.data(), h2.data(), lg.data());
+    if (bf16_forward)
+      forward_bf16(w, x, lg.data(), h1.data(), h2.data());
+    else
+      forward64(w, x, h1.data(), h2.data(), lg.data());
     double mx = lg[0];
     for (int a = 1; a < n_actions; ++a) mx = std::max(mx, lg[a]);
     double z = 0;

@@ -254,3 +254,84 @@ def dsp_kernel_timing(h, enable):
     ms, n = C.c_double(0), C.c_int32(0)
     check(L.dsp_kernel_timing(h, 1 if enable else 0, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+MLP_PARAMS = 64 * 256 + 256 + 256 * 256 + 256 + 256 * 32 + 32
+MLP_SHAPES = (("W1", (64, 256)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 32)),
+              ("b3", (32,)))
+
+
+def pack_params(w):
+    import numpy as np
+    return np.concatenate([np.asarray(w[k], np.float32).reshape(-1) for k, _ in MLP_SHAPES])
+
+
+def unpack_params(flat):
+    out, o = {}, 0
+    for k, shp in MLP_SHAPES:
+        n = 1
+        for s in shp:
+            n *= s
+        out[k] = flat[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+def dsp_mlp_create(max_batch, seed):
+    L = lib()
+    L.dsp_mlp_create.argtypes = [C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]
+    h = C.c_void_p()
+    check(L.dsp_mlp_create(max_batch, seed, C.byref(h)))
+    return h
+
+
+def dsp_mlp_destroy(h):
+    L = lib()
+    L.dsp_mlp_destroy.argtypes = [C.c_void_p]
+    L.dsp_mlp_destroy.restype = None
+    L.dsp_mlp_destroy(h)
+
+
+def dsp_mlp_set_weights(h, flat):
+    import numpy as np
+    a = np.ascontiguousarray(flat, np.float32)
+    L = lib()
+    L.dsp_mlp_set_weights.argtypes = [C.c_void_p, C.c_void_p]
+    check(L.dsp_mlp_set_weights(h, a.ctypes.data))
+
+
+def dsp_mlp_get_weights(h):
+    import numpy as np
+    a = np.zeros(MLP_PARAMS, np.float32)
+    L = lib()
+    L.dsp_mlp_get_weights.argtypes = [C.c_void_p, C.c_void_p]
+    check(L.dsp_mlp_get_weights(h, a.ctypes.data))
+    return a
+
+
+def dsp_mlp_forward(h, X_ptr, B, logits_ptr, stream=0):
+    L = lib()
+    L.dsp_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
+    check(L.dsp_mlp_forward(h, C.c_void_p(X_ptr), B, C.c_void_p(logits_ptr), C.c_void_p(stream)))
+
+
+def dsp_mlp_grad(h, X_ptr, y_ptr, B, n_actions, stream=0):
+    import numpy as np
+    g = np.zeros(MLP_PARAMS, np.float32)
+    loss = C.c_float(0)
+    L = lib()
+    L.dsp_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                               C.c_void_p, C.c_void_p]
+    check(L.dsp_mlp_grad(h, C.c_void_p(X_ptr), C.c_void_p(y_ptr), B, n_actions, C.byref(loss), g.ctypes.data,
+                         C.c_void_p(stream)))
+    return loss.value, g
+
+
+def dsp_mlp_train_step(h, X_ptr, y_ptr, B, n_actions, lr, stream=0):
+    loss = C.c_float(0)
+    L = lib()
+    L.dsp_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float,
+                                     C.POINTER(C.c_float), C.c_void_p]
+    check(L.dsp_mlp_train_step(h, C.c_void_p(X_ptr), C.c_void_p(y_ptr), B, n_actions, lr, C.byref(loss),
+                               C.c_void_p(stream)))
+    return loss.value
