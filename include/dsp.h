@@ -267,6 +267,22 @@ dsp_status dsp_mlp_grad(dsp_mlp* mlp, const float* X, const int32_t* y, int32_t 
 dsp_status dsp_mlp_train_step(dsp_mlp* mlp, const float* X, const int32_t* y, int32_t B, int32_t n_actions,
                               float lr, float* loss, void* stream);
 
+/* Makes `mlp` (its current weights, copied) the default policy of every later
+ * rollout of the model (dsp_expand_leaves, dsp_expand_leaves_noalloc,
+ * dsp_rollout): at each rollout step the network maps the scenario's features
+ * to logits and the argmax of the first |A| (lowest index on ties) is the
+ * action, evaluated as BF16 tensor-core tiles over 64 live scenarios per CTA
+ * with FP32 accumulation. g is still stepped exactly, so the rollout value is
+ * a true policy value and l0 a valid lower bound. NULL restores the heuristic
+ * policy. One-robot Rock Sample with at most 15 rocks (DSP_E_UNSUPPORTED
+ * otherwise); the device job queue keeps the heuristic policy. */
+dsp_status dsp_set_policy(dsp_model* model, const dsp_mlp* mlp);
+/* dsp_rollout with the learned policy, also recording the action of every
+ * step: actions (device, count x D int32, may be NULL) gets at
+ * [i * D + (t - start_depth)] the action taken at depth t. */
+dsp_status dsp_rollout_logged(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
+                              const int8_t* hist, int32_t start_depth, float* value, int32_t* actions, void* stream);
+
 /* Measurement support (no counterpart in the paper): returns the summed GPU
  * time of the expansion kernels of every dsp_expand_leaves call recorded since
  * the last call (CUDA events on each call's stream, around its kernels only),

@@ -335,3 +335,21 @@ def dsp_mlp_train_step(h, X_ptr, y_ptr, B, n_actions, lr, stream=0):
     check(L.dsp_mlp_train_step(h, C.c_void_p(X_ptr), C.c_void_p(y_ptr), B, n_actions, lr, C.byref(loss),
                                C.c_void_p(stream)))
     return loss.value
+
+
+def dsp_set_policy(model_h, mlp_h):
+    """Makes the MLP's current weights the model's rollout policy (copied; a
+    null mlp_h returns the model to the heuristic policy)."""
+    L = lib()
+    L.dsp_set_policy.argtypes = [C.c_void_p, C.c_void_p]
+    check(L.dsp_set_policy(model_h, mlp_h))
+
+
+def dsp_rollout_logged(model_h, block_ptr, cap, count, hist_ptr, start_depth, value_ptr, actions_ptr=0, stream=0):
+    """dsp_rollout with the learned policy; actions (device count x D int32)
+    receives the action of every step, -1 after the rollout ends."""
+    L = lib()
+    L.dsp_rollout_logged.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]
+    check(L.dsp_rollout_logged(model_h, C.c_void_p(block_ptr), cap, count, C.c_void_p(hist_ptr), start_depth,
+                               C.c_void_p(value_ptr), C.c_void_p(actions_ptr or None), C.c_void_p(stream)))

@@ -152,6 +152,7 @@ void dsp_destroy_model(dsp_model* m) {
   if (!m) return;
   if (m->dmodel) cudaFree(m->dmodel);
   if (m->dwork) cudaFree(m->dwork);
+  if (m->policy) cudaFree(m->policy);
   for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
   delete m->host;
   delete m;
@@ -216,6 +217,7 @@ dsp_status dsp_rollout(const dsp_model* m, const uint32_t* block, int32_t cap, i
   if (!block || !value) return fail(DSP_E_INVALID, "dsp_rollout: NULL buffer");
   if (start_depth < 0 || start_depth > m->host->D)
     return fail(DSP_E_INVALID, "dsp_rollout: start depth %d outside 0..D", start_depth);
+  if (m->policy_on) return dsp_rollout_logged(m, block, cap, count, hist, start_depth, value, nullptr, stream);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (m->host->kind == DSP_MODEL_CAR)
@@ -371,7 +373,8 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
       e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, (const long long*)dunits, n_jobs,
-                           plan.total_items, items, counters, m->plan_step, m->num_sms, block_b, st);
+                           plan.total_items, items, counters, m->plan_step, m->num_sms, block_b,
+                           m->policy_on ? m->policy : nullptr, st);
     }
     if (m->timing) {
       cudaEventRecord(ev[1], st);

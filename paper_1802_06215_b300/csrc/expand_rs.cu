@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "rs_common.cuh"
 #include "rs_model.cuh"
 
 namespace dsp {
@@ -56,37 +57,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
-
-__device__ __forceinline__ void load_rs_consts(RSShared& c, const DevModel* gm) {
-  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
-  for (int k = threadIdx.x; k < kMaxRocks; k += blockDim.x) c.rock_xy[k] = gm->rock_xy[k];
-  for (int k = threadIdx.x; k < kMaxSide * kMaxSide; k += blockDim.x) c.cell_rock[k] = gm->cell_rock[k];
-}
-
-template <int R>
-__device__ __forceinline__ RSModel<R> make_rs(const DevModel* gm, const RSShared* c, uint32_t plan_step) {
-  RSModel<R> M;
-  M.sh = c;
-  M.thresh = gm->thresh;
-  M.n = gm->n;
-  M.m = gm->m;
-  M.per = gm->per_robot;
-  M.D = gm->D;
-  M.seed = gm->seed;
-  M.plan_step = plan_step;
-  return M;
-}
-
-// Item list (field-major, `total` items): robot 0 [, robot 1], good, sampled,
-// scenario, positive-counter mask of the child's history, depth<<24 | slot
-// (slot = action * child_cap + child in the job's result arrays), job.
-template <int R>
-struct Items {
-  static constexpr int kFields = R == 2 ? 8 : 7;
-  uint32_t* base;
-  long long total;
-  __device__ __forceinline__ uint32_t* f(int k) const { return base + (size_t)k * total; }
-};
 
 // Phase A for the job in S.J (index j in its job table, first item ibase). All
 // threads of the CTA call it; it ends with a barrier.
@@ -390,7 +360,7 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
 template <int R>
 cudaError_t launch_two_phase(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs, const long long* item_base,
                              int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
-                             uint32_t plan_step, int num_sms, int block_b, cudaStream_t st) {
+                             uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st) {
   Items<R> items{item_buf, total_items};
   int per_sm_a = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, rs_group_kernel<R>, kBlockA, 0);
@@ -398,6 +368,9 @@ cudaError_t launch_two_phase(const DevModel* gm, DevWork* work, const dsp_leaf_j
   rs_group_kernel<R><<<grid_a, kBlockA, 0, st>>>(gm, work, jobs, item_base, n_jobs, counters, plan_step, items);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (policy != nullptr && R == 1)
+    return launch_rs_rollout_mlp_items(gm, work, jobs, item_buf, total_items, counters + 1, policy, plan_step,
+                                       num_sms, st);
   int per_sm_b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, rs_rollout_items_kernel<R>, block_b, 0);
   long long chunks = (total_items + 31) / 32;
@@ -533,12 +506,12 @@ cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, Queue
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, int n_jobs, long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
-                             cudaStream_t st) {
+                             const void* policy, cudaStream_t st) {
   if (robots == 1)
     return launch_two_phase<1>(gm, work, jobs, item_base, n_jobs, total_items, item_buf, counters, plan_step,
-                               num_sms, block_b, st);
+                               num_sms, block_b, policy, st);
   return launch_two_phase<2>(gm, work, jobs, item_base, n_jobs, total_items, item_buf, counters, plan_step,
-                             num_sms, block_b, st);
+                             num_sms, block_b, nullptr, st);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,
@@ -660,7 +633,7 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
   if (e == cudaSuccess) {
     int block_b = m->tune_block > 0 ? m->tune_block : 256;
     e = launch_rs_expand(m->dmodel, m->host->robots, m->dwork, djobs, dbase, n_jobs, plan.total_items, items,
-                         counters, m->plan_step, m->num_sms, block_b, st);
+                         counters, m->plan_step, m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc launch");
   return DSP_OK;

@@ -11,10 +11,16 @@ int rs_item_fields(int robots);
 // Rock Sample two-phase expansion: phase A over n_jobs jobs (item_base[j] =
 // first item of job j, total_items in all), phase B over the item list.
 // counters: two device uints, zero on entry (job head, chunk head).
+// policy: learned pi0 for the rollout phase (one robot), or null for the
+// heuristic policy.
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, int n_jobs, long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
-                             cudaStream_t st);
+                             const void* policy, cudaStream_t st);
+// Learned-policy rollout phase over the item list (one robot).
+cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs,
+                                        uint32_t* item_buf, long long total_items, unsigned int* counter,
+                                        const void* policy, uint32_t plan_step, int num_sms, cudaStream_t st);
 // Device view of the job ring (device addresses of mapped pinned host memory).
 struct QueueRing {
   unsigned long long* seq;   // [cap] t + 1: ticket t published; t + cap: slot free for ticket t + cap

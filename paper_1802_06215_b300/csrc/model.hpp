@@ -17,6 +17,8 @@ struct dsp_model {
   int num_sms = 0;
   int tune_block = 0;                // CTA size chosen by the autotuner (0 = default)
   int tune_tps = 0;                  // car: threads per scenario (0 = default)
+  void* policy = nullptr;            // learned pi0 for rollouts (device, transposed BF16 weights)
+  bool policy_on = false;
   bool timing = false;               // record events around the expansion kernels
   std::mutex timing_mu;
   std::vector<cudaEvent_t> timing_events;  // start, end per dsp_expand_leaves call

@@ -162,6 +162,7 @@ dsp_status dsp_queue_submit(dsp_queue* q, const dsp_leaf_job* job, uint64_t time
     if (q->shutdown)
       return q->monitor_status != DSP_OK ? (dsp_status)q->monitor_status.load() : fail(DSP_E_INVALID, "queue closed");
   }
+  if (q->m->policy_on) return fail(DSP_E_UNSUPPORTED, "dsp_queue_submit: the queue rolls out the heuristic policy");
   ExpandPlan plan;
   dsp_status vs = plan_units(q->m, job, 1, plan);  // validation only
   if (vs != DSP_OK) return vs;

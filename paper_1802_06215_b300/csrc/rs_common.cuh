@@ -1,0 +1,41 @@
+// Pieces of the Rock Sample expansion shared by its kernels: constant loading,
+// model set-up and the rollout-item list that links the grouping phase to the
+// rollout phase.
+#pragma once
+#include "common.cuh"
+#include "rs_model.cuh"
+
+namespace dsp {
+
+__device__ __forceinline__ void load_rs_consts(RSShared& c, const DevModel* gm) {
+  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
+  for (int k = threadIdx.x; k < kMaxRocks; k += blockDim.x) c.rock_xy[k] = gm->rock_xy[k];
+  for (int k = threadIdx.x; k < kMaxSide * kMaxSide; k += blockDim.x) c.cell_rock[k] = gm->cell_rock[k];
+}
+
+template <int R>
+__device__ __forceinline__ RSModel<R> make_rs(const DevModel* gm, const RSShared* c, uint32_t plan_step) {
+  RSModel<R> M;
+  M.sh = c;
+  M.thresh = gm->thresh;
+  M.n = gm->n;
+  M.m = gm->m;
+  M.per = gm->per_robot;
+  M.D = gm->D;
+  M.seed = gm->seed;
+  M.plan_step = plan_step;
+  return M;
+}
+
+// Item list (field-major, `total` items): robot 0 [, robot 1], good, sampled,
+// scenario, positive-counter mask of the child's history, depth<<24 | slot
+// (slot = action * child_cap + child in the job's result arrays), job.
+template <int R>
+struct Items {
+  static constexpr int kFields = R == 2 ? 8 : 7;
+  uint32_t* base;
+  long long total;
+  __device__ __forceinline__ uint32_t* f(int k) const { return base + (size_t)k * total; }
+};
+
+}  // namespace dsp

@@ -1,0 +1,151 @@
+"""Rollouts with the learned policy on the GPU against the CPU oracle.
+
+The network runs as BF16 tensor-core tiles on the GPU and as a BF16/FP32
+restatement in the oracle, so logits agree only to rounding: the oracle
+replays the GPU's logged actions (values then agree bit for bit, g being
+stepped identically) and checks that no logged action loses to its own argmax
+by more than a small logit margin."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_06215_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+G32 = float(np.float32(0.95))
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06215_b300 import _dsp, batch, build
+    build.build()
+    return torch, _dsp, batch
+
+
+def bf16_exact(a):
+    a = np.asarray(a, np.float32).copy()
+    u = a.view(np.uint32)
+    u += 0x7FFF + ((u >> 16) & 1)
+    u &= 0xFFFF0000
+    return a
+
+
+def weights(seed, zero=False):
+    rng = np.random.default_rng(seed)
+    w = {"W1": rng.normal(0, np.sqrt(2 / 64), (64, 256)), "b1": rng.normal(0, 0.1, 256),
+         "W2": rng.normal(0, np.sqrt(2 / 256), (256, 256)), "b2": rng.normal(0, 0.1, 256),
+         "W3": rng.normal(0, 3 * np.sqrt(2 / 256), (256, 32)), "b3": rng.normal(0, 0.5, 32)}
+    if zero:
+        for k in w:
+            w[k][:] = 0
+    return {k: bf16_exact(v).astype(np.float64) for k, v in w.items()}
+
+
+def install(_dsp, m, w):
+    h = _dsp.dsp_mlp_create(64, 0)
+    _dsp.dsp_mlp_set_weights(h, _dsp.pack_params(w))
+    _dsp.dsp_set_policy(m.h, h)
+    return h
+
+
+def logged_rollout(torch, _dsp, m, cfg, b, hist, d0):
+    n = b.shape[1]
+    bd = torch.tensor(b.view(np.int32), device="cuda")
+    hd = torch.tensor(hist, device="cuda")
+    val = torch.zeros(n, dtype=torch.float32, device="cuda")
+    act = torch.full((n, cfg.D), -1, dtype=torch.int32, device="cuda")
+    _dsp.dsp_rollout_logged(m.h, bd.data_ptr(), n, n, hd.data_ptr(), d0, val.data_ptr(), act.data_ptr())
+    torch.cuda.synchronize()
+    return val.cpu().numpy(), act.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_learned_rollout_replays_in_oracle(env, seed):
+    torch, _dsp, batch = env
+    cfg = I.rs15_15().with_(D=40)
+    m = batch.Model(cfg)
+    w = weights(seed)
+    hm = install(_dsp, m, w)
+    rng = np.random.default_rng(seed)
+    N = 300
+    b = I.rs_block(cfg, N, rng)
+    b[2] &= ~b[3]
+    hist = rng.integers(-3, 4, (N, 32)).astype(np.int8)
+    val, act = logged_rollout(torch, _dsp, m, cfg, b, hist, 5)
+    om = oracle.Model(cfg)
+    ov, bad, steps = oracle.rollout_learned(om, b, hist, 5, w, logged=act, tol=5e-2)
+    assert np.array_equal(val.astype(np.float64), ov)
+    assert bad.sum() == 0, (bad.sum(), steps)
+    # the policy does sense and sample, not only walk
+    used = set(act[act >= 0].tolist())
+    assert len(used) >= 4
+    _, st = m.counters()
+    assert st == 0
+    _dsp.dsp_mlp_destroy(hm)
+    m.close()
+
+
+def test_constant_east_network_closed_form(env):
+    """Logits equal to a bias favouring E: the learned rollout walks east, worth
+    10 * gamma^(n-1-x)."""
+    torch, _dsp, batch = env
+    cfg = I.rs15_15()
+    m = batch.Model(cfg)
+    w = weights(0, zero=True)
+    w["b3"][1] = 4.0
+    hm = install(_dsp, m, w)
+    rng = np.random.default_rng(0)
+    for x in (0, 9, 14):
+        b = I.rs_block(cfg, 70, rng, pos=[(x, 5)])
+        val, act = logged_rollout(torch, _dsp, m, cfg, b, np.zeros((70, 32), np.int8), 2)
+        assert np.allclose(val, 10 * G32 ** (14 - x), rtol=1e-6)
+        assert np.all(act[:, : 15 - x] == 1)
+    _dsp.dsp_mlp_destroy(hm)
+    m.close()
+
+
+def test_learned_expansion(env):
+    """With a learned policy the expansion keeps the oracle's children, rewards
+    and u0 (they do not depend on the policy), and each child's l0 sum equals
+    the sum of the logged single rollouts of its scenarios, which the oracle
+    replays bit for bit."""
+    torch, _dsp, batch = env
+    cfg = I.rs15_15().with_(D=30)
+    m = batch.Model(cfg)
+    w = weights(9)
+    hm = install(_dsp, m, w)
+    om = oracle.Model(cfg)
+    jobs = I.job_stream(cfg, 6, 4, max_scen=80)
+    jb = batch.JobBatch(m, jobs)
+    jb.run()
+    _, st = m.counters()
+    assert st == 0
+    res = jb.all_results()
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        g = res[k]
+        assert np.array_equal(g["perm"], o["perm"]) and np.array_equal(g["child_count"], o["child_count"])
+        leaf = o["leaf"]
+        n = leaf.shape[1]
+        for a in range(m.num_actions):
+            nc = int(o["child_count"][a])
+            assert np.array_equal(g["rew"][a][:nc], o["rew"][a][:nc])
+            assert np.array_equal(g["u"][a][:nc], o["u"][a][:nc])
+            nxt, keys, _ = om.step(leaf, np.full(n, a, np.int32), j.depth)
+            hist = np.tile(j.hist, (n, 1))
+            if a >= 5:
+                z = (keys & np.uint64(3)).astype(np.int64)
+                hist[:, a - 5] = np.clip(hist[:, a - 5].astype(int) + np.where(z == 1, 1, np.where(z == 2, -1, 0)),
+                                         -127, 127)
+            val, act = logged_rollout(torch, _dsp, m, cfg, nxt, hist, j.depth + 1)
+            ov, bad, _ = oracle.rollout_learned(om, nxt, hist, j.depth + 1, w, logged=act, tol=5e-2)
+            assert np.array_equal(val.astype(np.float64), ov) and bad.sum() == 0
+            fixed = np.round(val.astype(np.float64) * 2 ** 32).astype(np.int64)
+            for c in range(nc):
+                mem = g["perm"][a][g["child_off"][a][c]:g["child_off"][a][c + 1]]
+                assert g["l"][a][c] == fixed[mem].sum(), (k, a, c)
+    _dsp.dsp_mlp_destroy(hm)
+    m.close()
