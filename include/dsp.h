@@ -209,6 +209,27 @@ typedef struct {
 dsp_status dsp_plan(dsp_model* model, const uint32_t* root_states, int32_t n, const int8_t* hist,
                     const dsp_search_params* params, dsp_search_result* result, int32_t* root_visits);
 
+/* One node of a finished planning step, as dsp_plan_nodes exports it. */
+typedef struct {
+  int32_t depth;   /* tree depth, root 0 */
+  int32_t n;       /* |Phi_b| */
+  int32_t action;  /* argmax_a L(b, a), lowest index on ties: the action the tree's lower bound takes at b */
+  int32_t visits;  /* N(b) */
+  double U, L;     /* node bounds (weighted by |Phi_b|/K) */
+  int8_t hist[32]; /* belief counters at b (per rock: sensed good minus sensed bad, clamped) */
+} dsp_plan_node;
+
+/* dsp_plan, then export of the tree (no counterpart in the paper; the source
+ * of (state, action) pairs for imitation training of a learned default
+ * policy): every expanded, non-terminal node with |Phi_b| >= min_scen, in
+ * node-creation order, up to cap nodes. nodes: HOST array of cap records.
+ * states: HOST state block of capacity cap (may be NULL) that receives the
+ * first scenario of each exported node (position and sampled mask are common
+ * to the node's scenarios in Rock Sample). *count = nodes written. */
+dsp_status dsp_plan_nodes(dsp_model* model, const uint32_t* root_states, int32_t n, const int8_t* hist,
+                          const dsp_search_params* params, dsp_search_result* result, int32_t* root_visits,
+                          int32_t min_scen, int32_t cap, dsp_plan_node* nodes, uint32_t* states, int32_t* count);
+
 /* Launch shape of dsp_expand_leaves (the paper's fixed mapping of actions to
  * blocks and scenarios to threads, Sec. III-D, made a tunable): block = CTA
  * size of the Rock Sample rollout phase (128, 256 or 512; the car kernel runs
@@ -282,6 +303,14 @@ dsp_status dsp_set_policy(dsp_model* model, const dsp_mlp* mlp);
  * [i * D + (t - start_depth)] the action taken at depth t. */
 dsp_status dsp_rollout_logged(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
                               const int8_t* hist, int32_t start_depth, float* value, int32_t* actions, void* stream);
+
+/* Policy features of one-robot Rock Sample states (the learned policy's
+ * input, the same function the learned rollout evaluates): out (device,
+ * count x 64 FP32) row i = x/n, y/n, then per rock (rock x - x)/n,
+ * (rock y - y)/n, clamp(counter, -3, 3)/3, sampled, zero-padded. block:
+ * device state block of capacity cap; hist: device count x 32 counters. */
+dsp_status dsp_features(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
+                        const int8_t* hist, float* out, void* stream);
 
 /* Measurement support (no counterpart in the paper): returns the summed GPU
  * time of the expansion kernels of every dsp_expand_leaves call recorded since

@@ -311,13 +311,34 @@ int32_t orc_features_rs(const orc_model* d, const uint32_t* block, int32_t cap, 
   return features_rs(d->n, d->m, d->rock_cells, block, cap, count, hist, out);
 }
 
+// Actions the learned policy may take in a one-robot Rock Sample state with
+// counters h (a function of the observable history only): no move off the N,
+// S or W border and no Sample off an unsampled rock (both cost -100 and leave
+// the state as it was, so a deterministic policy would repeat them to depth
+// D), and no Sense of a sampled rock or of one whose counter already reads
+// +-3 (the features clamp there, so a repeated Sense could never change the
+// policy's input). East is always allowed.
+static bool learned_allowed(const RockSample<float>& m, const RSState& s, const Hist& h, int a) {
+  const int x = s.x[0], y = s.y[0];
+  if (a == 0) return y < m.n - 1;
+  if (a == 1) return true;
+  if (a == 2) return y > 0;
+  if (a == 3) return x > 0;
+  if (a == 4) {
+    int i = m.rock_at(x, y);
+    return i >= 0 && !((s.sampled >> i) & 1u);
+  }
+  int i = a - 5;
+  return !((s.sampled >> i) & 1u) && h.c[i] < 3 && h.c[i] > -3;
+}
+
 // Default-policy rollout (Eq. lb) of one-robot Rock Sample with the learned
 // policy: at every step the features of (state, counters) go through the
-// network in its BF16/FP32 form and the action is the argmax over the first
-// |A| logits (lowest index on ties). With `logged` (count x D actions) the
-// rollout follows the logged actions instead and counts, per scenario, the
-// steps whose logged action differs from this argmax by more than `tol` in
-// logit margin.
+// network in its BF16/FP32 form and the action is the argmax of the logits
+// over the allowed actions (learned_allowed; lowest index on ties). With
+// `logged` (count x D actions) the rollout follows the logged actions instead
+// and counts, per scenario, the steps whose logged action is not allowed or
+// trails this argmax by more than `tol` in logit.
 int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count,
                             const int8_t* hist, int32_t start_depth, const double* W1, const double* b1,
                             const double* W2, const double* b2, const double* W3, const double* b3,
@@ -345,16 +366,14 @@ int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t c
       double x64[kMlpIn], lg[kMlpOut];
       for (int q = 0; q < kMlpIn; ++q) x64[q] = (double)fx[q];
       forward_bf16(w, x64, lg);
-      int best = 0;
-      for (int a = 1; a < na; ++a)
-        if (lg[a] > lg[best]) best = a;
-      double second = -1e300;
+      int best = -1;
       for (int a = 0; a < na; ++a)
-        if (a != best && lg[a] > second) second = lg[a];
+        if (learned_allowed(m, s, h, a) && (best < 0 || lg[a] > lg[best])) best = a;
       int a = best;
       if (logged) {
         a = logged[(size_t)i * m.D + k];
-        if (a != best && lg[best] - lg[a] > tol) bad += 1;
+        if (a < 0 || a >= na || !learned_allowed(m, s, h, a) || lg[best] - lg[a] > tol) bad += 1;
+        if (a < 0 || a >= na) a = best;
       }
       RSState next;
       uint64_t key;

@@ -353,3 +353,44 @@ def dsp_rollout_logged(model_h, block_ptr, cap, count, hist_ptr, start_depth, va
                                      C.c_void_p, C.c_void_p, C.c_void_p]
     check(L.dsp_rollout_logged(model_h, C.c_void_p(block_ptr), cap, count, C.c_void_p(hist_ptr), start_depth,
                                C.c_void_p(value_ptr), C.c_void_p(actions_ptr or None), C.c_void_p(stream)))
+
+
+class dsp_plan_node(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("n", C.c_int32), ("action", C.c_int32), ("visits", C.c_int32),
+                ("U", C.c_double), ("L", C.c_double), ("hist", C.c_int8 * 32)]
+
+
+def dsp_plan_nodes(h, root_states, hist, params, num_actions, min_scen, cap, words):
+    """dsp_plan plus the export of the tree's expanded nodes: returns the plan
+    result dict, a list-free numpy view of the nodes (depth, n, action,
+    visits, U, L, hist) and the (words, count) block of their first states."""
+    import numpy as np
+    rs = np.ascontiguousarray(root_states, dtype=np.uint32)
+    n = rs.shape[1]
+    hs = None if hist is None else np.ascontiguousarray(hist, dtype=np.int8)
+    res = dsp_search_result()
+    visits = np.zeros(num_actions, np.int32)
+    nodes = (dsp_plan_node * cap)()
+    states = np.zeros((words, cap), np.uint32)
+    count = C.c_int32(0)
+    L = lib()
+    L.dsp_plan_nodes.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(dsp_search_params),
+                                 C.POINTER(dsp_search_result), C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                 C.c_void_p, C.POINTER(C.c_int32)]
+    check(L.dsp_plan_nodes(h, rs.ctypes.data, n, None if hs is None else hs.ctypes.data, C.byref(params),
+                           C.byref(res), visits.ctypes.data, min_scen, cap, nodes, states.ctypes.data,
+                           C.byref(count)))
+    k = count.value
+    rec = np.frombuffer(nodes, dtype=np.dtype([("depth", "<i4"), ("n", "<i4"), ("action", "<i4"),
+                                               ("visits", "<i4"), ("U", "<f8"), ("L", "<f8"),
+                                               ("hist", "i1", 32)]), count=k).copy()
+    out = {f: getattr(res, f) for f, _ in dsp_search_result._fields_}
+    out["root_visits"] = visits
+    return out, rec, np.ascontiguousarray(states[:, :k])
+
+
+def dsp_features(h, block_ptr, cap, count, hist_ptr, out_ptr, stream=0):
+    L = lib()
+    L.dsp_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    check(L.dsp_features(h, C.c_void_p(block_ptr), cap, count, C.c_void_p(hist_ptr), C.c_void_p(out_ptr),
+                         C.c_void_p(stream)))

@@ -46,6 +46,7 @@ struct MlpSmem {
   float b1[kMlpHid], b2[kMlpHid], b3[kMlpOut];
   RSShared c;
   int act[kRows];
+  uint32_t allow[kRows];  // bit a: action a allowed for the row (learned_allow)
 };
 
 __device__ __forceinline__ int swz(int row, int word) { return word ^ ((row & 7) << 2); }
@@ -64,8 +65,28 @@ __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// The network on the 64 rows of S.x; writes S.act (argmax over the first na
-// logits). All 128 threads; warp w owns rows 16w .. 16w + 15.
+// Actions the learned policy may take (a function of the observable history):
+// no move off the N, S or W border and no Sample off an unsampled rock (both
+// cost -100 and leave the state unchanged, so a deterministic policy would
+// repeat them to depth D), no Sense of a sampled rock or of one whose counter
+// reads +-3 (the features clamp there). East is always allowed.
+__device__ __forceinline__ uint32_t learned_allow(const RSShared& c, int n, int m, uint32_t pos, uint32_t sampled,
+                                                  const int8_t* cnt) {
+  const int x = (int)(pos & 0xFFu), y = (int)((pos >> 8) & 0xFFu);
+  uint32_t a = 0x2u;
+  if (y < n - 1) a |= 0x1u;
+  if (y > 0) a |= 0x4u;
+  if (x > 0) a |= 0x8u;
+  const int i = c.cell_rock[y * n + x];
+  if (i != 0xFF && !((sampled >> i) & 1u)) a |= 0x10u;
+  for (int r = 0; r < m; ++r)
+    if (!((sampled >> r) & 1u) && cnt[r] < 3 && cnt[r] > -3) a |= 0x20u << r;
+  return a;
+}
+
+// The network on the 64 rows of S.x; writes S.act (argmax of the logits over
+// the allowed actions of S.allow, lowest index on ties). All 128 threads;
+// warp w owns rows 16w .. 16w + 15.
 __device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -136,6 +157,7 @@ __device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
   }
   float best0 = -3.0e38f, best1 = -3.0e38f;
   int arg0 = 0x7FFF, arg1 = 0x7FFF;
+  const uint32_t al0 = S.allow[r0], al1 = S.allow[r1];
 #pragma unroll
   for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -143,11 +165,11 @@ __device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
       int col = 8 * j + 2 * t + e;
       if (col < na) {
         float v0 = acc[j][e] + S.b3[col], v1 = acc[j][2 + e] + S.b3[col];
-        if (v0 > best0) {
+        if (((al0 >> col) & 1u) && (arg0 == 0x7FFF || v0 > best0)) {
           best0 = v0;
           arg0 = col;
         }
-        if (v1 > best1) {
+        if (((al1 >> col) & 1u) && (arg1 == 0x7FFF || v1 > best1)) {
           best1 = v1;
           arg1 = col;
         }
@@ -157,11 +179,11 @@ __device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
   for (int o = 1; o <= 2; o <<= 1) {
     float ov0 = __shfl_xor_sync(0xFFFFFFFFu, best0, o), ov1 = __shfl_xor_sync(0xFFFFFFFFu, best1, o);
     int oa0 = __shfl_xor_sync(0xFFFFFFFFu, arg0, o), oa1 = __shfl_xor_sync(0xFFFFFFFFu, arg1, o);
-    if (ov0 > best0 || (ov0 == best0 && oa0 < arg0)) {
+    if (oa0 != 0x7FFF && (arg0 == 0x7FFF || ov0 > best0 || (ov0 == best0 && oa0 < arg0))) {
       best0 = ov0;
       arg0 = oa0;
     }
-    if (ov1 > best1 || (ov1 == best1 && oa1 < arg1)) {
+    if (oa1 != 0x7FFF && (arg1 == 0x7FFF || ov1 > best1 || (ov1 == best1 && oa1 < arg1))) {
       best1 = ov1;
       arg1 = oa1;
     }
@@ -281,7 +303,9 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_mlp_kernel(const DevMo
 #pragma unroll
         for (int r = 0; r < kMaxRocks; ++r) cnt[r] = (int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
         rs_features(M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, cnt, f);
+        S.allow[tid] = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, cnt);
       } else {
+        S.allow[tid] = 0x2u;
 #pragma unroll
         for (int k = 0; k < kMlpIn; ++k) f[k] = 0.0f;
       }
@@ -366,11 +390,34 @@ cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const
   return launch_mlp<true>(gm, work, (const uint8_t*)policy, src, plan_step, num_sms, total_items, st);
 }
 
+__global__ void features_kernel(const DevModel* __restrict__ gm, const uint32_t* __restrict__ block, int cap,
+                                int count, const int8_t* __restrict__ hist, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float f[kMlpIn];
+  rs_features(gm->n, gm->m, gm->rock_xy, block[i], block[3 * (size_t)cap + i], hist + (size_t)i * 32, f);
+  float4* o = reinterpret_cast<float4*>(out + (size_t)i * kMlpIn);
+  for (int k = 0; k < kMlpIn / 4; ++k) o[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+}
+
 }  // namespace dsp
 
 using namespace dsp;
 
 extern "C" {
+
+dsp_status dsp_features(const dsp_model* m, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,
+                        float* out, void* stream) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_features: model is NULL");
+  if (m->host->kind != DSP_MODEL_GRID) return fail(DSP_E_UNSUPPORTED, "dsp_features: one-robot Rock Sample only");
+  if (count < 0 || cap < count || (count > 0 && (!block || !hist || !out)))
+    return fail(DSP_E_INVALID, "dsp_features: bad buffers");
+  if (((uintptr_t)out & 15) != 0) return fail(DSP_E_INVALID, "dsp_features: out must be 16-byte aligned");
+  if (count == 0) return DSP_OK;
+  features_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m->dmodel, block, cap, count, hist, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_features");
+}
 
 dsp_status dsp_set_policy(dsp_model* m, const dsp_mlp* mlp) {
   if (!m) return fail(DSP_E_INVALID, "dsp_set_policy: model is NULL");

@@ -150,6 +150,7 @@ class Search {
   }
 
   dsp_status run(const uint32_t* root_host, int n, const int8_t* hist, dsp_search_result* out, int32_t* visits);
+  dsp_status export_nodes(int min_scen, int cap, dsp_plan_node* nodes, uint32_t* states, int32_t* count);
 
  private:
   struct Trial {
@@ -574,6 +575,37 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   return DSP_OK;
 }
 
+// Expanded, non-terminal nodes with at least min_scen scenarios, in creation
+// order: the tree's lower-bound action at each and its first scenario's state.
+dsp_status Search::export_nodes(int min_scen, int cap, dsp_plan_node* nodes, uint32_t* states, int32_t* count) {
+  int k = 0;
+  std::vector<uint32_t> one(words_);
+  for (auto& up : pool_) {
+    if (k >= cap) break;
+    const Node* v = up.get();
+    if (!v->expanded || v->term || v->n < min_scen || v->d_states == nullptr) continue;
+    dsp_plan_node& o = nodes[k];
+    o.depth = v->depth;
+    o.n = v->n;
+    o.visits = (int32_t)v->N;
+    o.U = v->U;
+    o.L = v->L;
+    std::memcpy(o.hist, v->hist, 32);
+    int best = 0;
+    for (int a = 1; a < (int)v->q.size(); ++a)
+      if (v->q[a].L > v->q[best].L) best = a;
+    o.action = best;
+    if (states) {
+      cudaError_t e = cudaMemcpy2D(one.data(), 4, v->d_states, (size_t)v->n * 4, 4, words_, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "dsp_plan_nodes: node state");
+      for (int w = 0; w < words_; ++w) states[(size_t)w * cap + k] = one[w];
+    }
+    ++k;
+  }
+  *count = k;
+  return DSP_OK;
+}
+
 }  // namespace
 }  // namespace dsp
 
@@ -587,4 +619,22 @@ extern "C" dsp_status dsp_plan(dsp_model* m, const uint32_t* root_states, int32_
   std::memset(out, 0, sizeof(*out));
   Search s(m, *p);
   return s.run(root_states, n, hist, out, root_visits);
+}
+
+extern "C" dsp_status dsp_plan_nodes(dsp_model* m, const uint32_t* root_states, int32_t n, const int8_t* hist,
+                                     const dsp_search_params* p, dsp_search_result* out, int32_t* root_visits,
+                                     int32_t min_scen, int32_t cap, dsp_plan_node* nodes, uint32_t* states,
+                                     int32_t* count) {
+  using namespace dsp;
+  if (!nodes || !count || cap < 0) return fail(DSP_E_INVALID, "dsp_plan_nodes: NULL node buffer");
+  *count = 0;
+  if (!m || !root_states || !p || !out) return fail(DSP_E_INVALID, "dsp_plan_nodes: NULL argument");
+  if (n < 1 || n > kMaxScen || n > m->host->K) return fail(DSP_E_INVALID, "dsp_plan_nodes: %d root scenarios", n);
+  if (p->threads < 1 || p->threads > 256) return fail(DSP_E_INVALID, "dsp_plan_nodes: threads %d", p->threads);
+  if (p->rounds < 1) return fail(DSP_E_INVALID, "dsp_plan_nodes: rounds %d", p->rounds);
+  std::memset(out, 0, sizeof(*out));
+  Search s(m, *p);
+  dsp_status st = s.run(root_states, n, hist, out, root_visits);
+  if (st != DSP_OK) return st;
+  return s.export_nodes(min_scen, cap, nodes, states, count);
 }

@@ -96,3 +96,99 @@ def test_learned_rollout_constant_east_is_closed_form():
         logged = np.full((3, cfg.D), 1, np.int32)
         v2, bad2, _ = oracle.rollout_learned(m, b, None, 3, w, logged=logged)
         assert np.array_equal(v, v2) and np.all(bad2 == 0)
+
+
+def bias_net(prefs):
+    """A network whose logits are its output bias: prefs maps action -> logit."""
+    w = rand_weights(7)
+    for k in w:
+        w[k][:] = 0
+    for a, v in prefs.items():
+        w["b3"][a] = v
+    return w
+
+
+def test_learned_rollout_masks_border_moves():
+    """N preferred, then E: the robot climbs to the top row, where N is not
+    allowed (it would cost -100 and stay), then walks east along it:
+    10 * gamma^((n-1-y) + (n-1-x))."""
+    cfg = I.rs15_15()
+    m = oracle.Model(cfg)
+    w = bias_net({0: 5.0, 1: 1.0})
+    rng = np.random.default_rng(1)
+    for x, y in ((0, 0), (3, 14), (14, 9), (6, 6)):
+        b = I.rs_block(cfg, 2, rng, pos=[(x, y)])
+        v, _, steps = oracle.rollout_learned(m, b, None, 0, w)
+        assert np.allclose(v, 10 * G32 ** ((14 - y) + (14 - x)), rtol=1e-6)
+        assert steps == 2 * ((14 - y) + (15 - x))
+        # a logged border move is reported as a disagreement
+        logged = np.full((2, cfg.D), 1, np.int32)
+        logged[:, 0] = 3 if x == 0 else 0
+        _, bad, _ = oracle.rollout_learned(m, b, None, 0, w, logged=logged)
+        if x == 0 or y == 14:
+            assert np.all(bad >= 1)
+
+
+def test_learned_rollout_samples_only_unsampled_rocks():
+    """Sample preferred, then E: along a row the robot samples each unsampled
+    rock it stands on once (+-10 by its hidden state) and exits."""
+    cfg = I.rs15_15()
+    m = oracle.Model(cfg)
+    w = bias_net({4: 5.0, 1: 1.0})
+    cells = cfg.rock_cells
+    rx, ry = cells & 0xFF, cells >> 8
+    rng = np.random.default_rng(2)
+    for y in range(cfg.n):
+        on_row = [i for i in range(cfg.m) if ry[i] == y]
+        for pre in (0, 1):
+            b = I.rs_block(cfg, 4, rng, pos=[(0, y)])
+            if pre and on_row:
+                b[3] |= np.uint32(1 << on_row[0])
+                b[2] &= ~b[3]
+            v, _, _ = oracle.rollout_learned(m, b, None, 0, w)
+            for s in range(4):
+                t, expect = 0, 0.0
+                for xx in range(cfg.n):
+                    for i in on_row:
+                        if rx[i] == xx and not (int(b[3, s]) >> i) & 1:
+                            expect += G32 ** t * (10.0 if (int(b[2, s]) >> i) & 1 else -10.0)
+                            t += 1
+                    t += 1
+                expect += 10.0 * G32 ** (t - 1) - 0.0
+                assert np.isclose(v[s], expect, rtol=1e-5), (y, pre, s, v[s], expect)
+
+
+def test_learned_rollout_sensing_is_bounded():
+    """Sense rock 0 preferred, then E: the robot senses until the counter
+    reads +-3 (an odd number k >= 3 of readings) and walks east, so the value
+    is 10 * gamma^(k + n-1-x); with rock 0 sampled it walks east at once."""
+    cfg = I.rs15_15()
+    m = oracle.Model(cfg)
+    w = bias_net({5: 5.0, 1: 1.0})
+    rng = np.random.default_rng(3)
+    b = I.rs_block(cfg, 200, rng, pos=[(4, 2)])
+    v, _, _ = oracle.rollout_learned(m, b, None, 0, w)
+    k = np.log(v / 10.0) / np.log(G32) - 10
+    kr = np.round(k)
+    assert np.allclose(k, kr, atol=1e-3)
+    assert np.all(kr >= 3) and np.all(kr % 2 == 1)
+    b[3] |= 1
+    b[2] &= ~b[3]
+    v2, _, _ = oracle.rollout_learned(m, b, None, 0, w)
+    assert np.allclose(v2, 10 * G32 ** 10, rtol=1e-6)
+
+
+def test_learned_rollout_never_pays_illegal_penalties():
+    """Whatever the network, the allowed-action rule keeps every reward at
+    least -10 (a bad rock), so a rollout is worth more than -10 per rock."""
+    cfg = I.rs15_15()
+    m = oracle.Model(cfg)
+    rng = np.random.default_rng(4)
+    for seed in range(3):
+        w = rand_weights(seed)
+        w["b3"] = rng.normal(0, 3, 32)
+        b = I.rs_block(cfg, 40, rng)
+        b[2] &= ~b[3]
+        hist = rng.integers(-4, 5, (40, 32)).astype(np.int8)
+        v, _, _ = oracle.rollout_learned(m, b, hist, 0, w)
+        assert np.all(v >= -10.0 * cfg.m)
