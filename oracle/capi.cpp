@@ -334,11 +334,13 @@ static bool learned_allowed(const RockSample<float>& m, const RSState& s, const 
 
 // Default-policy rollout (Eq. lb) of one-robot Rock Sample with the learned
 // policy: at every step the features of (state, counters) go through the
-// network in its BF16/FP32 form and the action is the argmax of the logits
-// over the allowed actions (learned_allowed; lowest index on ties). With
-// `logged` (count x D actions) the rollout follows the logged actions instead
-// and counts, per scenario, the steps whose logged action is not allowed or
-// trails this argmax by more than `tol` in logit.
+// network in its BF16/FP32 form; the argmax of logits 0..|A| over the allowed
+// actions (learned_allowed) and logit |A| ("defer", always allowed), lowest
+// index on ties, picks the action, defer meaning the heuristic policy's
+// action. With `logged` (count x D actions) the rollout follows the logged
+// actions instead and counts, per scenario, the steps whose logged action is
+// neither this choice nor reachable by a column (an allowed action, or defer
+// for the heuristic's action) within `tol` of the best logit.
 int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count,
                             const int8_t* hist, int32_t start_depth, const double* W1, const double* b1,
                             const double* W2, const double* b2, const double* W3, const double* b3,
@@ -367,13 +369,18 @@ int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t c
       for (int q = 0; q < kMlpIn; ++q) x64[q] = (double)fx[q];
       forward_bf16(w, x64, lg);
       int best = -1;
-      for (int a = 0; a < na; ++a)
-        if (learned_allowed(m, s, h, a) && (best < 0 || lg[a] > lg[best])) best = a;
-      int a = best;
+      for (int a = 0; a <= na; ++a)
+        if ((a == na || learned_allowed(m, s, h, a)) && (best < 0 || lg[a] > lg[best])) best = a;
+      const int heur = m.policy(s, h);
+      const int chosen = best == na ? heur : best;
+      int a = chosen;
       if (logged) {
         a = logged[(size_t)i * m.D + k];
-        if (a < 0 || a >= na || !learned_allowed(m, s, h, a) || lg[best] - lg[a] > tol) bad += 1;
-        if (a < 0 || a >= na) a = best;
+        bool ok = a == chosen;
+        if (!ok && a >= 0 && a < na && learned_allowed(m, s, h, a) && lg[best] - lg[a] <= tol) ok = true;
+        if (!ok && a == heur && lg[best] - lg[na] <= tol) ok = true;
+        if (!ok) bad += 1;
+        if (a < 0 || a >= na) a = chosen;
       }
       RSState next;
       uint64_t key;

@@ -46,7 +46,8 @@ struct MlpSmem {
   float b1[kMlpHid], b2[kMlpHid], b3[kMlpOut];
   RSShared c;
   int act[kRows];
-  uint32_t allow[kRows];  // bit a: action a allowed for the row (learned_allow)
+  uint32_t allow[kRows];  // bit a: action a allowed for the row (learned_allow); bit |A|: defer
+  int heur[kRows];        // the heuristic policy's action for the row (taken on defer)
 };
 
 __device__ __forceinline__ int swz(int row, int word) { return word ^ ((row & 7) << 2); }
@@ -84,9 +85,10 @@ __device__ __forceinline__ uint32_t learned_allow(const RSShared& c, int n, int 
   return a;
 }
 
-// The network on the 64 rows of S.x; writes S.act (argmax of the logits over
-// the allowed actions of S.allow, lowest index on ties). All 128 threads;
-// warp w owns rows 16w .. 16w + 15.
+// The network on the 64 rows of S.x; writes S.act: the argmax of the logits
+// over the allowed actions of S.allow and column na ("defer"), lowest index on
+// ties, with defer replaced by the heuristic's action S.heur. All 128
+// threads; warp w owns rows 16w .. 16w + 15.
 __device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -163,7 +165,7 @@ __device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       int col = 8 * j + 2 * t + e;
-      if (col < na) {
+      if (col <= na) {
         float v0 = acc[j][e] + S.b3[col], v1 = acc[j][2 + e] + S.b3[col];
         if (((al0 >> col) & 1u) && (arg0 == 0x7FFF || v0 > best0)) {
           best0 = v0;
@@ -189,8 +191,8 @@ __device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
     }
   }
   if (t == 0) {
-    S.act[r0] = arg0;
-    S.act[r1] = arg1;
+    S.act[r0] = arg0 == na ? S.heur[r0] : arg0;
+    S.act[r1] = arg1 == na ? S.heur[r1] : arg1;
   }
 }
 
@@ -303,9 +305,11 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_mlp_kernel(const DevMo
 #pragma unroll
         for (int r = 0; r < kMaxRocks; ++r) cnt[r] = (int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
         rs_features(M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, cnt, f);
-        S.allow[tid] = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, cnt);
+        S.allow[tid] = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, cnt) | (1u << na);
+        S.heur[tid] = M.policy(s, pm);
       } else {
         S.allow[tid] = 0x2u;
+        S.heur[tid] = 1;
 #pragma unroll
         for (int k = 0; k < kMlpIn; ++k) f[k] = 0.0f;
       }
@@ -427,7 +431,8 @@ dsp_status dsp_set_policy(dsp_model* m, const dsp_mlp* mlp) {
   }
   if (m->host->kind != DSP_MODEL_GRID)
     return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: the learned policy serves one-robot Rock Sample");
-  if (m->host->num_actions > kMlpOut) return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: more than 32 actions");
+  if (m->host->num_actions + 1 > kMlpOut)
+    return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: more than 31 actions (the network's last used logit defers)");
   if (m->host->m > 15) return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: features hold 15 rocks");
   cudaError_t e = cudaSuccess;
   if (m->policy == nullptr) e = cudaMalloc(&m->policy, kPolBytes);

@@ -1,30 +1,34 @@
-"""Learned default policy pi0 for one-robot Rock Sample: harvest, imitation
-training and the comparison with the heuristic pi0.
+"""Learned default policy pi0 for one-robot Rock Sample: training data,
+training, and the comparison with the heuristic pi0.
 
 The paper's leaf initialisation rolls out a hand-written default policy to get
-l0 (Sec. III-A, Eq. lb). Here a network may take its place:
+l0 (Sec. III-A, Eq. lb). Here a network may take its place. Its logits cover
+the |A| actions plus one more column, "defer", which takes the heuristic
+policy's action; the rollout takes the argmax over the actions allowed in the
+observable state and defer (the rule of `allowed_mask`). Every rollout still
+steps g, so l0 stays the value of a policy and a valid lower bound.
 
-1. Planner episodes on fresh world seeds. At each step `dsp_plan_nodes` plans
-   from the current belief (K scenarios drawn from per-rock posteriors), the
-   world takes the chosen action (`dsp_step` of the same model on the world's
-   own random stream, a plan-step counter no planning call uses) and the belief
-   is updated by Bayes' rule with the sensor accuracy 0.5 + 0.5 * 2^(-d/20) of
-   the Rock Sample model (Sec. IV-A).
-2. Every expanded tree node with enough scenarios gives one pair: the features
-   of its state and belief counters (`dsp_features`, the same map the learned
-   rollout evaluates) and argmax_a L(b, a), the action the tree's lower bound
-   takes there. With the heuristic pi0 in the rollouts that label is one step
-   of policy improvement over it.
-3. Minibatch Adam on softmax cross-entropy with `dsp_mlp_train_step` (BF16
-   tensor-core forward and backward, FP32 master weights).
-4. `dsp_set_policy` installs the network. Every rollout still steps g, so l0
-   stays the value of a policy and a valid lower bound.
+Approximate policy iteration (`policy_iteration`, the `api` command, which
+made the shipped weights): pi_0 is the heuristic. At iteration k, states are
+drawn uniformly over the observable space plus from pi_k's own rollouts
+(logged actions replayed with `dsp_step`); each gets Q^{pi_k}(s, a) from one
+leaf expansion (`dsp_expand_leaves`, rollouts running pi_k) over scenarios
+drawn from the belief its counters imply; the label is the best allowed action
+where it beats the heuristic's action by a margin, else defer. The network is
+trained on all labels so far (`dsp_mlp_train_step`: BF16 tensor-core forward
+and backward, FP32 master weights, Adam) and installed (`dsp_set_policy`) as
+pi_{k+1}.
+
+Planner imitation (`harvest`, the `train` command): planner episodes on fresh
+world seeds, with Bayes belief updates (sensor accuracy 0.5 + 0.5 * 2^(-d/20),
+Sec. IV-A); every expanded tree node exported by `dsp_plan_nodes` gives its
+features (`dsp_features`) and argmax_a L(b, a).
 
 PyTorch only holds device buffers here; every step of the computation runs in
 the library's kernels.
 
-    python -m paper_1802_06215_b300.learn train --out weights.npz
-    python -m paper_1802_06215_b300.learn compare --weights weights.npz
+    python -m paper_1802_06215_b300.learn api --iterations 4 --epochs 30
+    python -m paper_1802_06215_b300.learn compare
 """
 import argparse
 import json
@@ -216,6 +220,250 @@ def accuracy(h, X, Y, n_actions, batch_size):
     return hits / max(len(Y), 1)
 
 
+def allowed_mask(cfg, pos, sampled, hist):
+    """(count, |A| + 1) bool: the actions the learned policy may take (the
+    same rule the learned rollout applies): no move off the N, S or W border,
+    no Sample off an unsampled rock, no Sense of a sampled rock or of one whose
+    counter reads +-3; East and column |A| (defer to the heuristic) always."""
+    n, m = cfg.n, cfg.m
+    x, y = (pos & 0xFF).astype(np.int64), ((pos >> 8) & 0xFF).astype(np.int64)
+    cnt = len(pos)
+    al = np.zeros((cnt, 6 + m), bool)
+    al[:, 5 + m] = True
+    al[:, 0] = y < n - 1
+    al[:, 1] = True
+    al[:, 2] = y > 0
+    al[:, 3] = x > 0
+    cells = np.asarray(cfg.rock_cells, np.int64)
+    samp = (sampled[:, None].astype(np.int64) >> np.arange(m)) & 1
+    on = (cells[None, :] & 0xFF) == x[:, None]
+    on &= (cells[None, :] >> 8) == y[:, None]
+    al[:, 4] = (on & (samp == 0)).any(axis=1)
+    h = hist[:, :m].astype(np.int64)
+    al[:, 5:5 + m] = (samp == 0) & (h < 3) & (h > -3)
+    return al
+
+
+def heuristic_action(cfg, pos, sampled, hist):
+    """The hand-written default policy's action (one robot): Sample a
+    believed-good (counter > 0, unsampled) rock underfoot, else step towards
+    the nearest one (Manhattan, lowest index on ties, x before y), else E."""
+    m = cfg.m
+    x, y = (pos & 0xFF).astype(np.int64), ((pos >> 8) & 0xFF).astype(np.int64)
+    cells = np.asarray(cfg.rock_cells, np.int64)
+    rx, ry = cells & 0xFF, cells >> 8
+    samp = (sampled[:, None].astype(np.int64) >> np.arange(m)) & 1
+    believed = (hist[:, :m].astype(np.int64) > 0) & (samp == 0)
+    d = np.abs(rx[None, :] - x[:, None]) + np.abs(ry[None, :] - y[:, None])
+    d = np.where(believed, d, 1 << 30)
+    best = np.argmin(d, axis=1)
+    bd = d[np.arange(len(pos)), best]
+    tx, ty = rx[best], ry[best]
+    a = np.where(tx > x, 1, np.where(tx < x, 3, np.where(ty > y, 0, 2)))
+    a = np.where(bd == 0, 4, a)
+    return np.where(bd >= (1 << 30), 1, a).astype(np.int32)
+
+
+def counter_posterior(c, q=0.85):
+    """P(rock good) implied by a belief counter c (readings of a sensor of
+    accuracy q): q^c / (q^c + (1-q)^c)."""
+    c = np.clip(np.asarray(c, np.float64), -30, 30)
+    return 1.0 / (1.0 + ((1 - q) / q) ** c)
+
+
+def q_labels(model, cfg, pos, sampled, hist, depth, rng, Kq=128, chunk=2048, thr=0.25):
+    """Conservative greedy labels of Q(s, a), estimated by one leaf expansion
+    per state over Kq scenarios drawn from the belief the counters imply:
+    Q(s, a) = sum over children of (reward sum + gamma * l0 sum) per scenario,
+    the rollouts running the model's current default policy (common random
+    numbers across actions). The label is |A| (defer to the heuristic) unless
+    the best allowed action beats the heuristic's action by more than thr;
+    then it is that action. Returns labels and that advantage."""
+    m_ = cfg.m
+    na = 5 + m_
+    labels = np.zeros(len(pos), np.int32)
+    margin = np.zeros(len(pos))
+    al = allowed_mask(cfg, pos, sampled, hist)[:, :na]
+    ha = heuristic_action(cfg, pos, sampled, hist)
+    bits = np.arange(m_, dtype=np.uint32)
+    for s0 in range(0, len(pos), chunk):
+        jobs = []
+        for i in range(s0, min(len(pos), s0 + chunk)):
+            p = counter_posterior(hist[i, :m_])
+            good = ((rng.random((Kq, m_)) < p).astype(np.uint32) << bits).sum(axis=1, dtype=np.uint32)
+            b = np.zeros((5, Kq), np.uint32)
+            b[0] = pos[i]
+            b[2] = good & np.uint32(~int(sampled[i]) & 0xFFFFFFFF)
+            b[3] = sampled[i]
+            b[4] = rng.choice(cfg.K, Kq, replace=False).astype(np.uint32)
+            jobs.append(inputs.Job(parent=b, idx=np.arange(Kq, dtype=np.uint16), last_action=-1,
+                                   depth=int(depth[i]), hist=hist[i].astype(np.int8)))
+        jb = batch.JobBatch(model, jobs)
+        jb.run()
+        res = jb.all_results()
+        for k, r in enumerate(res):
+            i = s0 + k
+            q = np.full(model.num_actions, -np.inf)
+            for a in range(model.num_actions):
+                nc = int(r["child_count"][a])
+                q[a] = (float(np.sum(r["rew"][a][:nc], dtype=np.float64)) +
+                        cfg.gamma * float(np.sum(r["l"][a][:nc], dtype=np.float64))) / (2.0 ** 32 * Kq)
+            q[~al[i]] = -np.inf
+            best = int(np.argmax(q))
+            margin[i] = q[best] - q[ha[i]]
+            labels[i] = best if margin[i] > thr else na
+    return labels, margin
+
+
+def random_states(cfg, count, rng):
+    """Observable Rock Sample states spread over the whole space: position
+    uniform, each rock sampled with a per-state probability, counters zero or
+    uniform in -3..3, depth uniform in 0..10."""
+    x = rng.integers(0, cfg.n, count)
+    y = rng.integers(0, cfg.n, count)
+    pos = (x | (y << 8)).astype(np.uint32)
+    ps = rng.random(count)[:, None]
+    sampled = ((rng.random((count, cfg.m)) < ps).astype(np.uint32) << np.arange(cfg.m, dtype=np.uint32)).sum(
+        axis=1, dtype=np.uint32)
+    hist = np.zeros((count, 32), np.int8)
+    c = rng.integers(-3, 4, (count, cfg.m)) * (rng.random((count, cfg.m)) < 0.5)
+    hist[:, :cfg.m] = c
+    depth = rng.integers(0, 11, count).astype(np.int32)
+    return pos, sampled, hist, depth
+
+
+def on_policy_states(model, cfg, pos, sampled, hist, depth, rng, per_rollout=6):
+    """States the model's learned policy visits: one logged rollout from each
+    given state (good rocks drawn from the counters' belief), replayed step by
+    step with dsp_step to recover positions, sampled masks and counters, then
+    per_rollout of the visited states chosen at random."""
+    import torch
+    N = len(pos)
+    b = np.zeros((5, N), np.uint32)
+    p = counter_posterior(hist[:, :cfg.m])
+    b[0] = pos
+    b[2] = ((rng.random((N, cfg.m)) < p).astype(np.uint32) << np.arange(cfg.m, dtype=np.uint32)).sum(
+        axis=1, dtype=np.uint32) & ~sampled
+    b[3] = sampled
+    b[4] = rng.integers(0, cfg.K, N).astype(np.uint32)
+    out = [[] for _ in range(4)]
+    for d0 in np.unique(depth):
+        sel = np.nonzero(depth == d0)[0]
+        blk = np.ascontiguousarray(b[:, sel])
+        n = len(sel)
+        bd = torch.as_tensor(blk.view(np.int32), device="cuda")
+        hd = torch.as_tensor(np.ascontiguousarray(hist[sel]), device="cuda")
+        val = torch.empty(n, dtype=torch.float32, device="cuda")
+        act = torch.full((n, cfg.D), -1, dtype=torch.int32, device="cuda")
+        _dsp.dsp_rollout_logged(model.h, bd.data_ptr(), n, n, hd.data_ptr(), int(d0), val.data_ptr(),
+                                act.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        acts = act.cpu().numpy()
+        cur, h = blk, hist[sel].copy()
+        visited = [[] for _ in range(n)]
+        for t in range(cfg.D - int(d0)):
+            live = np.nonzero(acts[:, t] >= 0)[0]
+            if len(live) == 0:
+                break
+            for i in live:
+                visited[i].append((cur[0, i], cur[3, i], h[i].copy(), int(d0) + t))
+            nxt, keys, _ = model.step(np.ascontiguousarray(cur[:, live]), acts[live, t], int(d0) + t)
+            a = acts[live, t]
+            z = (keys & np.uint64(3)).astype(np.int64)
+            sense = a >= SENSE0
+            for j in np.nonzero(sense & (z > 0))[0]:
+                r = a[j] - SENSE0
+                i = live[j]
+                h[i, r] = np.int8(max(-127, min(127, int(h[i, r]) + (1 if z[j] == 1 else -1))))
+            cur = cur.copy()
+            cur[:, live] = nxt
+        for v in visited:
+            if not v:
+                continue
+            for k in rng.choice(len(v), min(per_rollout, len(v)), replace=False):
+                for o, e in zip(out, v[k]):
+                    o.append(e)
+    return (np.array(out[0], np.uint32), np.array(out[1], np.uint32), np.array(out[2], np.int8).reshape(-1, 32),
+            np.array(out[3], np.int32))
+
+
+def mean_rollout_value(model, cfg, pos, sampled, hist, depth, rng, reps=1):
+    """Mean default-policy rollout value from the given states (good rocks
+    drawn from the counters' belief) under the model's current policy."""
+    import torch
+    vals = []
+    for _ in range(reps):
+        N = len(pos)
+        b = np.zeros((5, N), np.uint32)
+        p = counter_posterior(hist[:, :cfg.m])
+        b[0] = pos
+        b[2] = ((rng.random((N, cfg.m)) < p).astype(np.uint32) << np.arange(cfg.m, dtype=np.uint32)).sum(
+            axis=1, dtype=np.uint32) & ~sampled
+        b[3] = sampled
+        b[4] = rng.integers(0, cfg.K, N).astype(np.uint32)
+        for d0 in np.unique(depth):
+            sel = np.nonzero(depth == d0)[0]
+            vals.append(model.rollout(np.ascontiguousarray(b[:, sel]), hist[sel], int(d0)))
+    return float(np.mean(np.concatenate(vals)))
+
+
+def policy_iteration(cfg, iterations=4, n_random=60000, n_onpolicy=4000, Kq=64, epochs=30, seed=0, init=None,
+                     log=print):
+    """Approximate policy iteration: at iteration k the labels are the greedy
+    actions of Q^{pi_k} (pi_0 the heuristic) on random states plus the states
+    pi_k's own rollouts visit; the network is trained on all labels so far
+    and becomes pi_{k+1}."""
+    rng = np.random.default_rng([seed, 0xA91])
+    model = batch.Model(cfg)
+    policy = None
+    if init is not None:
+        policy = _dsp.dsp_mlp_create(64, 0)
+        _dsp.dsp_mlp_set_weights(policy, init)
+        _dsp.dsp_set_policy(model.h, policy)
+    Xs, Ys, hist_log = [], [], []
+    ev = random_states(cfg, 4000, np.random.default_rng([seed, 0xE7A1]))
+    start = (np.full(2000, start_word(cfg), np.uint32), np.zeros(2000, np.uint32), np.zeros((2000, 32), np.int8),
+             np.zeros(2000, np.int32))
+    _dsp.dsp_set_policy(model.h, None)
+    base = {"random_states": mean_rollout_value(model, cfg, *ev, np.random.default_rng(1)),
+            "start": mean_rollout_value(model, cfg, *start, np.random.default_rng(2))}
+    log(json.dumps({"heuristic_value": base}))
+    _dsp.dsp_set_policy(model.h, policy)
+    for it in range(iterations):
+        t0 = time.time()
+        pos, sampled, hist, depth = random_states(cfg, n_random, rng)
+        if policy is not None:
+            seeds = random_states(cfg, n_onpolicy, rng)
+            s2 = (np.concatenate([seeds[0], start[0][:n_onpolicy // 4]]),
+                  np.concatenate([seeds[1], start[1][:n_onpolicy // 4]]),
+                  np.concatenate([seeds[2], start[2][:n_onpolicy // 4]]),
+                  np.concatenate([seeds[3], start[3][:n_onpolicy // 4]]))
+            op = on_policy_states(model, cfg, *s2, rng)
+            pos, sampled = np.concatenate([pos, op[0]]), np.concatenate([sampled, op[1]])
+            hist, depth = np.concatenate([hist, op[2]]), np.concatenate([depth, op[3]])
+        y, margin = q_labels(model, cfg, pos, sampled, hist, depth, rng, Kq=Kq)
+        X = features(model, np.stack([pos, np.zeros_like(pos), np.zeros_like(pos), sampled, np.zeros_like(pos)]),
+                     hist)
+        Xs.append(X)
+        Ys.append(y)
+        t1 = time.time()
+        h, acc = train(np.concatenate(Xs), np.concatenate(Ys), model.num_actions + 1, epochs=epochs,
+                       seed=seed + it, log=lambda *_: None)
+        if policy is not None:
+            _dsp.dsp_mlp_destroy(policy)
+        policy = h
+        _dsp.dsp_set_policy(model.h, policy)
+        val = {"random_states": mean_rollout_value(model, cfg, *ev, np.random.default_rng(1)),
+               "start": mean_rollout_value(model, cfg, *start, np.random.default_rng(2))}
+        rec = {"iteration": it + 1, "states": int(len(y)), "pairs": int(sum(len(v) for v in Ys)),
+               "override_frac": float(np.mean(y != model.num_actions)),
+               "val_accuracy": acc, "label_seconds": t1 - t0, "train_seconds": time.time() - t1,
+               "learned_value": val, "heuristic_value": base}
+        hist_log.append(rec)
+        log(json.dumps(rec))
+    model.close()
+    return policy, hist_log
+
+
 def compare(cfg, policy, roots, seconds, threads=4):
     """Root gap u - l after one planning step of `seconds` from each root
     belief, heuristic pi0 then learned pi0, on the same random streams."""
@@ -266,7 +514,7 @@ def eval_roots(cfg, world_seeds, steps, seconds, threads=4):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["train", "compare"])
+    ap.add_argument("cmd", choices=["train", "api", "compare"])
     ap.add_argument("--worlds", type=int, default=32)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--plan-seconds", type=float, default=0.1)
@@ -281,7 +529,11 @@ def main(argv=None):
     from . import build
     build.build()
     cfg = inputs.rs15_15()
-    if a.cmd == "train":
+    if a.cmd == "api":
+        policy, hl = policy_iteration(cfg, iterations=a.iterations, epochs=a.epochs)
+        save_weights(a.out or a.weights, policy, {"config": "rs15_15", "method": "approximate policy iteration",
+                                                  "iterations": hl})
+    elif a.cmd == "train":
         policy, init, meta = None, None, {"iterations": []}
         X_all, Y_all = [], []
         for it in range(a.iterations):

@@ -149,3 +149,31 @@ def test_learned_expansion(env):
                 assert g["l"][a][c] == fixed[mem].sum(), (k, a, c)
     _dsp.dsp_mlp_destroy(hm)
     m.close()
+
+
+def test_defer_network_is_the_heuristic(env):
+    """A network that always defers reproduces the heuristic rollout kernel
+    bit for bit (values and step counts)."""
+    torch, _dsp, batch = env
+    cfg = I.rs15_15()
+    m = batch.Model(cfg)
+    rng = np.random.default_rng(11)
+    N = 4000
+    b = I.rs_block(cfg, N, rng)
+    b[3] = rng.integers(0, 1 << 15, N).astype(np.uint32)
+    b[2] &= ~b[3]
+    hist = rng.integers(-2, 4, (N, 32)).astype(np.int8)
+    m.reset_counters()
+    vh = m.rollout(b, hist, 3)
+    sh, _ = m.counters()
+    w = weights(0, zero=True)
+    w["b3"][20] = 3.0
+    w["b3"][4] = 1.0
+    hm = install(_dsp, m, w)
+    m.reset_counters()
+    vl = m.rollout(b, hist, 3)
+    sl, st = m.counters()
+    assert st == 0 and sl == sh
+    assert np.array_equal(np.asarray(vh).view(np.uint32), np.asarray(vl).view(np.uint32))
+    _dsp.dsp_mlp_destroy(hm)
+    m.close()

@@ -192,3 +192,25 @@ def test_learned_rollout_never_pays_illegal_penalties():
         hist = rng.integers(-4, 5, (40, 32)).astype(np.int8)
         v, _, _ = oracle.rollout_learned(m, b, hist, 0, w)
         assert np.all(v >= -10.0 * cfg.m)
+
+
+def test_learned_rollout_defer_is_the_heuristic():
+    """A network whose largest logit is column |A| ("defer") takes the
+    heuristic policy's action at every step: its rollouts equal the heuristic
+    rollouts (Eq. lb with the hand-written default policy) value for value."""
+    cfg = I.rs15_15()
+    m = oracle.Model(cfg)
+    w = bias_net({20: 5.0, 1: 1.0, 4: 2.0})
+    rng = np.random.default_rng(6)
+    b = I.rs_block(cfg, 300, rng)
+    b[3] = rng.integers(0, 1 << 15, 300).astype(np.uint32)
+    b[2] &= ~b[3]
+    hist = rng.integers(-2, 4, (300, 32)).astype(np.int8)
+    for d0 in (0, 7):
+        v, bad, steps = oracle.rollout_learned(m, b, hist, d0, w)
+        vh, steps_h = m.rollout(b, hist, d0)
+        assert np.array_equal(v.astype(np.float32), vh.astype(np.float32)) and steps == steps_h
+    # the same network one logit lower on defer: the East/Sample preferences take over
+    w2 = bias_net({20: 0.5, 1: 1.0, 4: 2.0})
+    v2, _, _ = oracle.rollout_learned(m, b, hist, 0, w2)
+    assert not np.array_equal(v2, oracle.rollout_learned(m, b, hist, 0, w)[0])
