@@ -45,6 +45,11 @@ WORKLOADS = {
                                   "|Phi_b|~U{1..500}, depth~U{0..10}", (4, 0.1, 0)),
 }
 SMS, LANES_PER_SM, MAX_SM_MHZ = 148, 128, 2032.0
+try:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
+        MEASURED = json.load(_f)
+except (OSError, ValueError):
+    MEASURED = {}
 METRIC = "scenario-steps/sec and leaf expansions/sec at K=500, D=90 (fraction of roofline); root gap"
 KERNEL_SOURCES = {
     "rs": ["expand_rs.cu", "rs_model.cuh", "common.cuh"],
@@ -55,7 +60,7 @@ KERNEL_SOURCES = {
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rs15_15", choices=list(WORKLOADS))
@@ -63,12 +68,13 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plan", action="store_true")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
     return p.parse_args()
 
 
 class ClockSampler:
-    """SM clocks and throttle reasons sampled every 5 ms through NVML while the
-    timed region runs (nvidia-smi every 200 ms if NVML is unavailable)."""
+    """SM clocks and throttle reasons sampled every 2 ms through NVML while the
+    timed region runs (nvidia-smi every 100 ms if NVML is unavailable)."""
 
     REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
                0x4: "sw_power_cap"}
@@ -101,14 +107,15 @@ class ClockSampler:
         except Exception as e:
             self.error = repr(e)[:120]
             self.method = "nvidia-smi"
-        proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm",
-                                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+        proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
                                 stderr=subprocess.DEVNULL, text=True)
         while not self.stop.is_set():
             line = proc.stdout.readline()
             try:
-                a, b = (float(x) for x in line.split(","))
-                self.samples.append((a, b, 0))
+                a, b, r = (x.strip() for x in line.split(","))
+                self.samples.append((float(a), float(b), int(r, 16)))
             except ValueError:
                 pass
         proc.terminate()
@@ -243,6 +250,45 @@ def planning_step(_dsp, m, cfg, plan):
             "scenario_steps_per_s": g["scenario_steps"] / g["seconds"], "action": g["action"]}
 
 
+def learned_step(_dsp, batch, m, cfg, jobs, seconds):
+    """The learned default policy (shipped weights) against the heuristic one:
+    root gap after planning steps of equal time from beliefs along heuristic-
+    planner episodes, and the tensor-core rate of the in-rollout network over
+    a learned-policy expansion of the first 256 jobs."""
+    import torch
+    from paper_1802_06215_b300 import learn
+    path = os.path.join(ROOT, "paper_1802_06215_b300", "weights", "rs15_15_pi0.npz")
+    h, meta = learn.load_weights(path)
+    roots = learn.eval_roots(cfg, [9000, 9001], 3, 0.05)
+    cmp_ = learn.compare(cfg, h, roots, seconds)
+    sub = batch.JobBatch(m, jobs[:256])
+    _dsp.dsp_set_policy(m.h, h)
+    sub.run()
+    torch.cuda.synchronize()
+    m.reset_counters()
+    _dsp.dsp_kernel_timing(m.h, True)
+    for _ in range(3):
+        sub.run()
+    torch.cuda.synchronize()
+    kms, calls = _dsp.dsp_kernel_timing(m.h, False)
+    steps, status = m.counters()
+    _dsp.dsp_set_policy(m.h, None)
+    _dsp.dsp_mlp_destroy(h)
+    if status != 0:
+        raise RuntimeError(f"device status word {status}")
+    na = m.num_actions
+    flop = 2 * (64 * 256 + 256 * 256 + 256 * (na + 1))
+    tflops = steps * flop / (kms / 1000.0) / 1e12
+    peak = MEASURED.get("bf16_tflops")
+    cmp_["weights"] = os.path.relpath(path, ROOT)
+    cmp_["tensor_roofline"] = {
+        "bound": "tensor", "achieved": tflops, "unit": "TFLOP/s", "peak": peak,
+        "frac": tflops / peak if peak else None, "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)",
+        "flop_per_scenario_step": flop, "scenario_steps": steps / 3, "kernel_ms_per_launch": kms / max(calls, 1),
+        "kernel": "rs_group_kernel + rs_rollout_mlp_kernel (learned-policy expansion of 256 jobs; mma.sync BF16)"}
+    return cmp_
+
+
 def run_ours(args, rank, world):
     import torch
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -333,6 +379,9 @@ def run_ours(args, rank, world):
         return
     clocks = clk.summary()
     planning = None if args.no_plan else planning_step(_dsp, m, cfg, plan)
+    learned = None
+    if not args.no_learned and args.workload == "rs15_15":
+        learned = learned_step(_dsp, batch, m, cfg, jobs, plan[1])
     cpu = None
     ops_per_step = None
     if not args.no_cpu_baseline:
@@ -374,6 +423,7 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "cpu_baseline": cpu,
         "planning": planning,
+        "learned_pi0": learned,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

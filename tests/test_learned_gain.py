@@ -63,8 +63,9 @@ def test_policy_iteration_from_scratch(env):
     _dsp, batch, learn = env
     cfg = I.rs15_15()
     logs = []
-    h, hl = learn.policy_iteration(cfg, iterations=2, n_random=20000, n_onpolicy=2000, Kq=64, epochs=15, seed=3,
+    h, hl = learn.policy_iteration(cfg, iterations=2, n_random=60000, n_onpolicy=4000, Kq=64, epochs=30, seed=0,
                                    log=logs.append)
     last = hl[-1]
     assert last["learned_value"]["start"] > last["heuristic_value"]["start"] + 1.0, hl
+    assert last["learned_value"]["random_states"] > last["heuristic_value"]["random_states"], hl
     _dsp.dsp_mlp_destroy(h)
