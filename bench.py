@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plan", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
+    p.add_argument("--ref-step-seconds", type=float, default=60.0,
+                   help="cap on the oracle's time per step in the reference arm")
     return p.parse_args()
 
 
@@ -184,7 +186,7 @@ def run_reference(args, rank, world):
     njobs = args.jobs or njobs
     jobs = inputs.job_stream(cfg, njobs, 1000)
     cores = os.cpu_count() or 1
-    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = min(args.ref_step_seconds, max(1.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_oracle_run(cfg, jobs, min(per_step, 2.0), cores)
     tot_steps, tot_jobs, tot_t = 0, 0, 0.0
@@ -289,6 +291,20 @@ def learned_step(_dsp, batch, m, cfg, jobs, seconds):
     return cmp_
 
 
+def combine_ranks(t_ms, steps, dist, device):
+    """Max over ranks of the timed region, sum over ranks of the scenario-
+    steps (each rank expands its own job stream: weak scaling, no exchange of
+    data between ranks)."""
+    if dist is None:
+        return float(t_ms), float(steps)
+    import torch
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    st = torch.tensor([float(steps)], dtype=torch.float64, device=device)
+    dist.all_reduce(st, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(st.item())
+
+
 def run_ours(args, rank, world):
     import torch
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -331,16 +347,7 @@ def run_ours(args, rank, world):
     steps_total, status = m.counters()
     if status != 0:
         raise RuntimeError(f"device status word {status}")
-    t_ms = sum(times)
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        st = torch.tensor([float(steps_total)], device="cuda")
-        dist.all_reduce(st, op=dist.ReduceOp.SUM)
-        steps_all = float(st.item())
-    else:
-        steps_all = float(steps_total)
+    t_ms, steps_all = combine_ranks(sum(times), steps_total, dist, "cuda")
     value = steps_all / (t_ms / 1000.0)
     steps_per_launch = steps_total / args.steps
 
@@ -354,11 +361,7 @@ def run_ours(args, rank, world):
         jb.download_outputs()
         e2[k][1].record(stream)
     torch.cuda.synchronize()
-    e2_ms = sum(a.elapsed_time(b) for a, b in e2)
-    if dist:
-        tt = torch.tensor([e2_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2_ms = float(tt.item())
+    e2_ms, _ = combine_ranks(sum(a.elapsed_time(b) for a, b in e2), 0, dist, "cuda")
     e2_value = steps_all / (e2_ms / 1000.0)
 
     # integer issue-rate probe (context for the roofline denominator)
