@@ -50,6 +50,7 @@ struct RSGroupSmem {
   uint32_t pm_job;
   int job;
   dsp_leaf_job J;
+  uint8_t code1[kWarpsA][kMaxScen];    // one robot: each warp's observation codes of its action
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -209,6 +210,193 @@ __device__ void rs_group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long lo
   }
 }
 
+// Gather + update of the job in S.J into S.leaf (and J.leaf_states), and the
+// job's positive-counter mask. Ends with a barrier.
+template <int R>
+__device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& M, unsigned long long& steps) {
+  const int tid = threadIdx.x;
+  const dsp_leaf_job& J = S.J;
+  const int n = J.n_scen, depth = J.depth;
+  for (int p = tid; p < n; p += kBlockA) {
+    RSS s = M.load(J.parent, J.parent_cap, J.idx[p]);
+    if (J.last_action >= 0) {
+      if (!M.terminal(s)) steps += 1;
+      uint64_t k;
+      M.step(s, J.last_action, depth - 1, k);
+    }
+    S.leaf[0][p] = s.pos[0];
+    S.leaf[1][p] = s.pos[1];
+    S.leaf[2][p] = s.good;
+    S.leaf[3][p] = s.sampled;
+    S.leaf[4][p] = s.scen;
+    if (J.leaf_states != nullptr) M.store(s, J.leaf_states, n, p);
+  }
+  if (tid == 0) {
+    uint32_t h[8];
+    const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = hw[k];
+    S.pm_job = positive_mask(h, M.m);
+  }
+  __syncthreads();
+}
+
+// Phase A for one robot, where an action's scenarios fall into at most a few
+// children: observation z in {0, 1, 2} and whether the step ended the world
+// give 6 codes (a move or Sample gives every scenario of a job one code, a
+// Sense at most two). Each warp expands whole actions: pass 1 steps the
+// action's scenarios 32 at a time, keeps each scenario's code in shared memory
+// and counts codes, first positions and exact reward sums with ballots and
+// warp reductions; pass 2 numbers the children by first position and writes
+// the grouped positions and the rollout items, re-stepping only the actions
+// that draw no random numbers (a Sense leaves the state as it was). The result
+// is identical to the general grouping; no barrier is needed inside the job.
+__device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long long ibase, Items<1> items,
+                              DevWork* work, unsigned long long& steps) {
+  constexpr int kC = 6;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  gather_update<1>(S, M, steps);
+  const dsp_leaf_job& J = S.J;
+  const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
+  const uint32_t lt = lanemask_lt();
+  uint8_t* codes = S.code1[warp];
+  const uint32_t pm_job = S.pm_job;
+  for (int a = warp; a < A; a += kWarpsA) {
+    const int aa = J.first_action + a;
+    int cnt[kC], first[kC], rsum[kC];  // |reward sum| <= 100 * 512 fits 32 bits
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      cnt[c] = 0;
+      first[c] = 0x7FFFFFFF;
+      rsum[c] = 0;
+    }
+    for (int w = 0; w * 32 < n; ++w) {
+      const int p = w * 32 + lane;
+      int code = kC, rint = 0;
+      if (p < n) {
+        RSS s;
+        s.pos[0] = S.leaf[0][p];
+        s.pos[1] = 0u;
+        s.good = S.leaf[2][p];
+        s.sampled = S.leaf[3][p];
+        s.scen = S.leaf[4][p];
+        if (!M.terminal(s)) steps += 1;
+        uint64_t key;
+        rint = (int)M.step(s, aa, depth, key);
+        code = (int)(key & 3u) + 3 * (int)(key >> 62);
+        codes[p] = (uint8_t)code;
+      }
+#pragma unroll
+      for (int c = 0; c < kC; ++c) {
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
+        if (b) {
+          if (cnt[c] == 0) first[c] = w * 32 + __ffs(b) - 1;
+          cnt[c] += __popc(b);
+          rsum[c] += __reduce_add_sync(0xFFFFFFFFu, code == c ? rint : 0);
+        }
+      }
+    }
+    __syncwarp();
+    // children in order of first position
+    int cid[kC], off[kC], nch = 0;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      cid[c] = -1;
+      off[c] = 0;
+      if (cnt[c] > 0) {
+        nch += 1;
+        int k = 0, o = 0;
+#pragma unroll
+        for (int c2 = 0; c2 < kC; ++c2)
+          if (cnt[c2] > 0 && first[c2] < first[c]) {
+            k += 1;
+            o += cnt[c2];
+          }
+        cid[c] = k;
+        off[c] = o;
+      }
+    }
+    // per-action results: counts, offsets, keys, exact reward sums; u and l start at 0
+    if (lane == 0) {
+      J.child_count[a] = nch;
+      if (nch > cap) report(work, kStatusOverflow);
+      if (nch <= cap) J.child_off[(size_t)a * (cap + 1) + nch] = n;
+#pragma unroll
+      for (int c = 0; c < kC; ++c)
+        if (cnt[c] > 0 && cid[c] < cap) {
+          const size_t o = (size_t)a * cap + cid[c];
+          J.child_off[(size_t)a * (cap + 1) + cid[c]] = off[c];
+          J.child_key[o] = (uint64_t)(c % 3) | ((uint64_t)(c / 3) << 62);
+          J.rew_sum[o] = (long long)rsum[c] * 4294967296LL;
+          J.u_sum[o] = 0;
+          J.l_sum[o] = 0;
+        }
+    }
+    // the item's positive-counter mask: a Sense reading moves rock i's counter
+    // by +-1 (clamped to +-127, as the belief bookkeeping does)
+    uint32_t pm_z[3] = {pm_job, pm_job, pm_job};
+    if (aa >= 5) {
+      const int i = aa - 5;
+      const int c0 = (int)J.hist[i];
+      const int cg = min(c0 + 1, 127), cb = max(c0 - 1, -127);
+      pm_z[1] = cg > 0 ? (pm_job | (1u << i)) : (pm_job & ~(1u << i));
+      pm_z[2] = cb > 0 ? (pm_job | (1u << i)) : (pm_job & ~(1u << i));
+    }
+    // grouped positions and rollout items
+    int run[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) run[c] = 0;
+    for (int w = 0; w * 32 < n; ++w) {
+      const int p = w * 32 + lane;
+      const int code = p < n ? (int)codes[p] : kC;
+      int q = 0, mycid = 0;
+#pragma unroll
+      for (int c = 0; c < kC; ++c) {
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
+        if (code == c) {
+          q = off[c] + run[c] + __popc(b & lt);
+          mycid = cid[c];
+        }
+        run[c] += __popc(b);
+      }
+      if (p < n) {
+        RSS s;
+        s.pos[0] = S.leaf[0][p];
+        s.pos[1] = 0u;
+        s.good = S.leaf[2][p];
+        s.sampled = S.leaf[3][p];
+        s.scen = S.leaf[4][p];
+        if (aa < 5) {
+          uint64_t k;
+          M.step(s, aa, depth, k);
+        }
+        J.perm[(size_t)a * n + q] = (uint16_t)p;
+        const int z = code % 3;
+        const uint32_t pm = z == 1 ? pm_z[1] : (z == 2 ? pm_z[2] : pm_z[0]);
+        const size_t it = (size_t)(ibase + (long long)a * n + q);
+        items.f(0)[it] = s.pos[0];
+        items.f(1)[it] = s.good;
+        items.f(2)[it] = s.sampled;
+        items.f(3)[it] = s.scen;
+        items.f(4)[it] = pm;
+        items.f(5)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1));
+        items.f(6)[it] = (uint32_t)j;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+template <int R>
+__device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase,
+                                          Items<R> items, DevWork* work, unsigned long long& steps) {
+  if constexpr (R == 1)
+    rs1_group_job(S, M, j, ibase, items, work, steps);
+  else
+    rs_group_job<R>(S, M, j, ibase, items, work, steps);
+}
+
 template <int R>
 __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                              const dsp_leaf_job* __restrict__ jobs,
@@ -228,7 +416,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
     __syncthreads();
     const int j = S.job;
     if (j >= n_jobs) break;
-    rs_group_job<R>(S, M, j, item_base[j], items, work, steps);
+    group_job<R>(S, M, j, item_base[j], items, work, steps);
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
@@ -454,7 +642,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
     if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
       Items<R> items{scratch + (size_t)blockIdx.x * slot_words, (long long)n * S.J.n_actions};
       __threadfence_block();
-      rs_group_job<R>(S, M, 0, 0, items, work, steps);
+      group_job<R>(S, M, 0, 0, items, work, steps);
       if (tid == 0) s_chunk = 0;
       __syncthreads();
       const long long nchunks = (items.total + 31) >> 5;

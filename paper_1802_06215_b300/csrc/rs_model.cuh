@@ -206,6 +206,7 @@ struct RSModel {
   // +0.0 to v, which is never -0.0, so skipping it (and its discount-table
   // load) leaves v unchanged.
   __device__ __forceinline__ float rollout(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
+    if constexpr (R == 1) return rollout_one(s, pmask, t0, steps);
     float v = 0.0f;
     int t = t0;
     while (t < D && !terminal(s)) {
@@ -217,6 +218,67 @@ struct RSModel {
     }
     steps += (unsigned long long)(t - t0);
     if (!terminal(s)) v = __fadd_rn(v, __fmul_rn(sh->G[D - t0], tail(s)));
+    return v;
+  }
+
+  // The same rollout for one robot with the state unpacked into registers.
+  // The heuristic policy only moves and samples, and its moves never leave
+  // the map except E from the last column (the exit), so each step is one
+  // branch on the action: E while no believed-good unsampled rock is left,
+  // else a step toward the nearest one or Sample on it. Rewards, their order
+  // and the step count are those of step() and policy().
+  __device__ __forceinline__ float rollout_one(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
+    const uint32_t p0 = s.pos[0];
+    int x = (int)(p0 & 0xFFu), y = (int)((p0 >> 8) & 0xFFu);
+    bool ex = (p0 >> 16) & 1u;
+    uint32_t good = s.good, sampled = s.sampled;
+    float v = 0.0f;
+    int t = t0;
+    while (t < D && !ex) {
+      const uint32_t cand = pmask & ~sampled;
+      int reward = 0;
+      if (cand == 0) {
+        if (x == n - 1) {
+          reward = 10;
+          ex = true;
+        } else {
+          x += 1;
+        }
+      } else {
+        int best = 0, bestd = 1 << 30, bxy = 0;
+        uint32_t c = cand;
+        while (c) {
+          const int i = __ffs(c) - 1;
+          c &= c - 1;
+          const int rxy = sh->rock_xy[i];
+          const int d = abs(x - (rxy & 0xFF)) + abs(y - (rxy >> 8));
+          if (d < bestd) {
+            bestd = d;
+            best = i;
+            bxy = rxy;
+          }
+        }
+        const int rx = bxy & 0xFF, ry = bxy >> 8;
+        if (bestd == 0) {
+          const uint32_t bit = 1u << best;
+          reward = (good & bit) ? 10 : -10;
+          good &= ~bit;
+          sampled |= bit;
+        } else if (rx > x) {
+          x += 1;
+        } else if (rx < x) {
+          x -= 1;
+        } else if (ry > y) {
+          y += 1;
+        } else {
+          y -= 1;
+        }
+      }
+      if (reward != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)reward));
+      t += 1;
+    }
+    steps += (unsigned long long)(t - t0);
+    if (!ex) v = __fadd_rn(v, __fmul_rn(sh->G[D - t0], __fmul_rn(10.0f, sh->G[n - 1 - x])));
     return v;
   }
 
