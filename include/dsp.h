@@ -148,7 +148,10 @@ typedef struct {
  * of n_jobs descriptors (copied before return; the buffers it points to must
  * stay valid until the stream reaches the end of the work). Sums are
  * fixed point 2^-32. Validation failures return DSP_E_INVALID and launch
- * nothing. Asynchronous on `stream`. */
+ * nothing. Asynchronous on `stream`. Work buffers (job table, rollout-item
+ * list, about 28 B per (action, scenario) for one robot) come from a memory
+ * pool the model owns; the pool keeps its largest size mapped until
+ * dsp_destroy_model, so repeated calls do not map memory again. */
 dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
 /* Device job queue (Sec. III-D, node-level parallelism: the paper launches one
@@ -234,14 +237,14 @@ dsp_status dsp_plan_nodes(dsp_model* model, const uint32_t* root_states, int32_t
  * blocks and scenarios to threads, Sec. III-D, made a tunable): block = CTA
  * size of the Rock Sample rollout phase (128, 256 or 512; the car kernel runs
  * 256), tps = lanes sharing one car scenario (4, 8, 16 or 32; element-level
- * parallelism). 0 keeps the default (256, 16). Returns DSP_E_INVALID for
+ * parallelism). 0 keeps the default (256, 32). Returns DSP_E_INVALID for
  * other values. */
 dsp_status dsp_set_tuning(dsp_model* model, int32_t block, int32_t tps);
 dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
 
 /* dsp_expand_leaves for callers that must not allocate device memory while
  * they plan (the paper has no counterpart). dsp_expand_leaves takes its work
- * buffers from cudaMallocAsync on every call; this entry point calls no
+ * buffers from the model's stream-ordered memory pool on every call; this entry point calls no
  * cudaMalloc, cudaFree or other allocating routine. It is for code that owns
  * all device memory through its own fixed pool, and for replanning loops with
  * a hard time budget, where an allocation call can block on the device.

@@ -135,6 +135,20 @@ dsp_status dsp_create_model(const dsp_model_desc* d, dsp_model** out) {
   m->plan_step = d->plan_step;
   cudaError_t e = cudaGetDevice(&m->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (e == cudaSuccess) {
+    // The work buffers of each call come from this pool. Its release threshold
+    // keeps freed memory mapped, so a call after a synchronisation does not
+    // map its buffers again (the default pool returns them at every sync).
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = m->device;
+    e = cudaMemPoolCreate(&m->pool, &props);
+    if (e == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(m->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&m->dmodel, sizeof(DevModel));
   if (e == cudaSuccess) e = cudaMalloc(&m->dwork, sizeof(DevWork));
   if (e == cudaSuccess) e = cudaMemcpy(m->dmodel, h, sizeof(DevModel), cudaMemcpyHostToDevice);
@@ -154,6 +168,7 @@ void dsp_destroy_model(dsp_model* m) {
   if (m->dwork) cudaFree(m->dwork);
   if (m->policy) cudaFree(m->policy);
   for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
+  if (m->pool) cudaMemPoolDestroy(m->pool);
   delete m->host;
   delete m;
 }
@@ -333,6 +348,20 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
     }
   }
   if (plan.total_items >= (1LL << 31)) return fail(DSP_E_UNSUPPORTED, "more than 2^31 (action, scenario) items");
+  // Largest work first (units and jobs are independent, so the order changes
+  // no result): persistent CTAs that pull work in this order end together
+  // instead of waiting on one large unit drawn last.
+  if (h->kind == DSP_MODEL_CAR) {
+    std::stable_sort(plan.units.begin(), plan.units.end(), [&](const int4& x, const int4& y) {
+      return jobs[x.x].n_scen > jobs[y.x].n_scen;
+    });
+  } else {
+    plan.order.resize(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) plan.order[j] = j;
+    std::stable_sort(plan.order.begin(), plan.order.end(), [&](int x, int y) {
+      return (long long)jobs[x].n_scen * jobs[x].n_actions > (long long)jobs[y].n_scen * jobs[y].n_actions;
+    });
+  }
   return DSP_OK;
 }
 
@@ -346,20 +375,28 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   const DevModel* h = m->host;
   const bool car = h->kind == DSP_MODEL_CAR;
   size_t jb = sizeof(dsp_leaf_job) * (size_t)n_jobs;
-  size_t ub = car ? sizeof(int4) * plan.units.size() : sizeof(long long) * plan.item_base.size();
+  size_t ub = car ? sizeof(int4) * plan.units.size()
+                  : sizeof(long long) * plan.item_base.size() + sizeof(int) * plan.order.size();
   size_t ib = car ? 0 : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
   size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
   unsigned char* buf = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&buf, total, st);
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, total, m->pool, st);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves: work buffers");
   dsp_leaf_job* djobs = (dsp_leaf_job*)buf;
   void* dunits = buf + align256(jb);
   unsigned int* counters = (unsigned int*)(buf + align256(jb) + align256(ub));
   uint32_t* items = (uint32_t*)(buf + align256(jb) + align256(ub) + 256);
   e = cudaMemcpyAsync(djobs, jobs, jb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dunits, car ? (const void*)plan.units.data() : (const void*)plan.item_base.data(), ub,
+  const int* dorder = car ? nullptr : (const int*)((const long long*)dunits + plan.item_base.size());
+  if (e == cudaSuccess && car)
+    e = cudaMemcpyAsync(dunits, plan.units.data(), ub, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !car) {
+    e = cudaMemcpyAsync(dunits, plan.item_base.data(), sizeof(long long) * plan.item_base.size(),
                         cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)dorder, plan.order.data(), sizeof(int) * plan.order.size(), cudaMemcpyHostToDevice,
+                          st);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 256, st);
   if (e == cudaSuccess) {
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -372,7 +409,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
       e = launch_car_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
-      e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, (const long long*)dunits, n_jobs,
+      e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, (const long long*)dunits, dorder, n_jobs,
                            plan.total_items, items, counters, m->plan_step, m->num_sms, block_b,
                            m->policy_on ? m->policy : nullptr, st);
     }

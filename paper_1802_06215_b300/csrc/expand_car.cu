@@ -55,7 +55,7 @@ __device__ __forceinline__ void load_consts(CarShared& c, const DevModel* gm) {
 }
 
 template <int TPS>
-__global__ void __launch_bounds__(256) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                          const dsp_leaf_job* __restrict__ jobs,
                                                          const int4* __restrict__ units, int n_units,
                                                          unsigned int* head, uint32_t plan_step,
@@ -255,7 +255,7 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
   // streams (other search threads) never share them
   size_t need = (size_t)grid * kMaxScen * kCarObsWords * sizeof(uint32_t);
   uint32_t* scratch = nullptr;
-  e = cudaMallocAsync((void**)&scratch, need, st);
+  e = cudaMallocFromPoolAsync((void**)&scratch, need, m->pool, st);
   if (e != cudaSuccess) return e;
   car_expand_kernel<TPS><<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, head, m->plan_step,
                                                    scratch);
@@ -268,11 +268,11 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
 
 cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
                               unsigned int* head, cudaStream_t st) {
-  switch (m->tune_tps > 0 ? m->tune_tps : 16) {
+  switch (m->tune_tps > 0 ? m->tune_tps : 32) {
     case 4: return launch_tps<4>(m, djobs, dunits, n_units, head, st);
     case 8: return launch_tps<8>(m, djobs, dunits, n_units, head, st);
-    case 32: return launch_tps<32>(m, djobs, dunits, n_units, head, st);
-    default: return launch_tps<16>(m, djobs, dunits, n_units, head, st);
+    case 16: return launch_tps<16>(m, djobs, dunits, n_units, head, st);
+    default: return launch_tps<32>(m, djobs, dunits, n_units, head, st);
   }
 }
 

@@ -400,7 +400,8 @@ __device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, i
 template <int R>
 __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                              const dsp_leaf_job* __restrict__ jobs,
-                                                             const long long* __restrict__ item_base, int n_jobs,
+                                                             const long long* __restrict__ item_base,
+                                                             const int* __restrict__ order, int n_jobs,
                                                              unsigned int* head, uint32_t plan_step,
                                                              Items<R> items) {
   __shared__ RSGroupSmem S;
@@ -410,7 +411,8 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
   __syncthreads();
   while (true) {
     if (threadIdx.x == 0) {
-      S.job = (int)atomicAdd(head, 1u);
+      const int k = (int)atomicAdd(head, 1u);
+      S.job = k < n_jobs ? (order != nullptr ? order[k] : k) : n_jobs;
       if (S.job < n_jobs) S.J = jobs[S.job];
     }
     __syncthreads();
@@ -547,13 +549,14 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
 
 template <int R>
 cudaError_t launch_two_phase(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs, const long long* item_base,
-                             int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
+                             const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st) {
   Items<R> items{item_buf, total_items};
   int per_sm_a = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, rs_group_kernel<R>, kBlockA, 0);
   int grid_a = std::max(1, std::min(n_jobs, std::max(1, per_sm_a) * num_sms));
-  rs_group_kernel<R><<<grid_a, kBlockA, 0, st>>>(gm, work, jobs, item_base, n_jobs, counters, plan_step, items);
+  rs_group_kernel<R><<<grid_a, kBlockA, 0, st>>>(gm, work, jobs, item_base, order, n_jobs, counters, plan_step,
+                                                  items);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (policy != nullptr && R == 1)
@@ -692,14 +695,14 @@ cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, Queue
 }
 
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, DevWork* work, const dsp_leaf_job* jobs,
-                             const long long* item_base, int n_jobs, long long total_items, uint32_t* item_buf,
-                             unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
-                             const void* policy, cudaStream_t st) {
+                             const long long* item_base, const int* order, int n_jobs, long long total_items,
+                             uint32_t* item_buf, unsigned int* counters, uint32_t plan_step, int num_sms,
+                             int block_b, const void* policy, cudaStream_t st) {
   if (robots == 1)
-    return launch_two_phase<1>(gm, work, jobs, item_base, n_jobs, total_items, item_buf, counters, plan_step,
-                               num_sms, block_b, policy, st);
-  return launch_two_phase<2>(gm, work, jobs, item_base, n_jobs, total_items, item_buf, counters, plan_step,
-                             num_sms, block_b, nullptr, st);
+    return launch_two_phase<1>(gm, work, jobs, item_base, order, n_jobs, total_items, item_buf, counters,
+                               plan_step, num_sms, block_b, policy, st);
+  return launch_two_phase<2>(gm, work, jobs, item_base, order, n_jobs, total_items, item_buf, counters,
+                             plan_step, num_sms, block_b, nullptr, st);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,
@@ -734,7 +737,7 @@ cudaError_t launch_rs_rollout(const DevModel* gm, int robots, DevWork* work, con
 // Leaf expansion without device allocation (dsp_expand_leaves_noalloc).
 //
 // dsp_expand_leaves takes its job table, item offsets, counters and the
-// rollout-item list from cudaMallocAsync on every call. Callers that cannot
+// rollout-item list from the model's memory pool on every call. Callers that cannot
 // allocate device memory during planning use this variant instead: the same
 // two kernels run on a fixed scratch array that the library keeps in device
 // memory for the life of the process. Its size caps one call at
@@ -820,7 +823,8 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kNoAllocCounterBytes, st);
   if (e == cudaSuccess) {
     int block_b = m->tune_block > 0 ? m->tune_block : 256;
-    e = launch_rs_expand(m->dmodel, m->host->robots, m->dwork, djobs, dbase, n_jobs, plan.total_items, items,
+    e = launch_rs_expand(m->dmodel, m->host->robots, m->dwork, djobs, dbase, nullptr, n_jobs, plan.total_items,
+                         items,
                          counters, m->plan_step, m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc launch");

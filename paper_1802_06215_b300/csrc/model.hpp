@@ -15,6 +15,7 @@ struct dsp_model {
   uint32_t plan_step = 0;
   int device = 0;
   int num_sms = 0;
+  cudaMemPool_t pool = nullptr;      // stream-ordered work buffers; keeps its peak size until destroy
   int tune_block = 0;                // CTA size chosen by the autotuner (0 = default)
   int tune_tps = 0;                  // car: threads per scenario (0 = default)
   void* policy = nullptr;            // learned pi0 for rollouts (device, transposed BF16 weights)
@@ -32,6 +33,7 @@ dsp_status cuda_fail(cudaError_t e, const char* what);
 struct ExpandPlan {
   std::vector<int4> units;            // car: (job, action, 1, 0)
   std::vector<long long> item_base;   // Rock Sample: first rollout item of each job
+  std::vector<int> order;             // Rock Sample: jobs by decreasing n_scen * n_actions (phase-A order)
   long long total_items = 0;
 };
 dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan);

@@ -465,7 +465,7 @@ dsp_status dsp_rollout_logged(const dsp_model* m, const uint32_t* block, int32_t
   if (count == 0) return DSP_OK;
   cudaStream_t st = (cudaStream_t)stream;
   unsigned int* counter = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&counter, sizeof(unsigned int), st);
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&counter, sizeof(unsigned int), m->pool, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) {
     ItemSource src{};
