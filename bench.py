@@ -287,7 +287,7 @@ def learned_step(_dsp, batch, m, cfg, jobs, seconds):
         "bound": "tensor", "achieved": tflops, "unit": "TFLOP/s", "peak": peak,
         "frac": tflops / peak if peak else None, "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)",
         "flop_per_scenario_step": flop, "scenario_steps": steps / 3, "kernel_ms_per_launch": kms / max(calls, 1),
-        "kernel": "rs_group_kernel + rs_rollout_mlp_kernel (learned-policy expansion of 256 jobs; mma.sync BF16)"}
+        "kernel": "rs_group_kernel + rs_rollout_tc_kernel (learned-policy expansion of 256 jobs; tcgen05.mma BF16, TMEM accumulators)"}
     return cmp_
 
 

@@ -1,12 +1,12 @@
 // Default-policy rollouts (Eq. lb) with the learned policy pi0, one-robot Rock
-// Sample. A CTA keeps 64 live scenarios (rows) and advances them one step at a
-// time: each row writes its features (BF16) into a shared tile, the network
-// runs as tensor-core tiles over the 64 rows (mma.sync m16n8k16, BF16 inputs,
-// FP32 accumulation; weights resident in shared memory), each row takes the
-// argmax of its first |A| logits (lowest index on ties) and steps g exactly as
-// the heuristic rollout does. A row whose scenario ends (terminal or depth D)
-// adds its value to its child and takes the next item at once, so the tile
-// stays full until the item list runs out.
+// Sample, on the fifth-generation tensor cores. A CTA keeps 128 live
+// scenarios (rows) and advances them one step at a time: the network runs as
+// tcgen05.mma over the 128 rows (BF16 inputs, FP32 accumulators in tensor
+// memory, weights resident in shared memory), each row takes the argmax of its
+// logits over the allowed actions and "defer" (the heuristic's action) and
+// steps g exactly as the heuristic rollout does. A row whose scenario ends
+// (terminal or depth D) adds its value to its child and takes the next item at
+// once, so the tile stays full until the item list runs out.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -23,8 +23,8 @@ extern "C" dsp_status dsp_mlp_get_weights(const dsp_mlp* mlp, float* host_params
 namespace dsp {
 namespace {
 
-constexpr int kRows = 64;        // scenarios per CTA
-constexpr int kThreads = 128;    // 4 warps x 16 rows for the tensor-core layers
+constexpr int kRows = 128;       // scenarios per CTA: the MMA's M, one thread per row
+constexpr int kThreads = 128;    // warp w reads and writes TMEM lanes 32w .. 32w + 31 (its rows)
 // device policy buffer: transposed BF16 weights [n][k], FP32 biases
 constexpr size_t kPolW1 = 0;
 constexpr size_t kPolW2 = kPolW1 + (size_t)kMlpHid * kMlpIn * 2;
@@ -34,36 +34,152 @@ constexpr size_t kPolB2 = kPolB1 + kMlpHid * 4;
 constexpr size_t kPolB3 = kPolB2 + kMlpHid * 4;
 constexpr size_t kPolBytes = kPolB3 + kMlpOut * 4;
 
-// shared memory in 32-bit words (BF16 pairs); rows of 32 or 128 words with
-// the word index XOR-swizzled by (row & 7) << 2, so the eight rows a fragment
-// load touches fall in distinct banks
-struct MlpSmem {
-  uint32_t w1[kMlpHid * (kMlpIn / 2)];
-  uint32_t w2[kMlpHid * (kMlpHid / 2)];
-  uint32_t w3[kMlpOut * (kMlpHid / 2)];
-  uint32_t x[kRows * (kMlpIn / 2)];
-  uint32_t h[kRows * (kMlpHid / 2)];
+// Tensor memory of a CTA (all 512 columns; the kernel's shared memory keeps
+// one CTA per SM): layer-1 and layer-2 accumulators share columns 0..255
+// (FP32, row r in lane r), the hidden activations of the next layer's A
+// operand take 256..383 (BF16 pairs along K), the logits 384..415.
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColD = 0;
+constexpr uint32_t kColH = 256;
+constexpr uint32_t kColL = 384;
+
+// Shared memory. Matrices are stored in the canonical K-major layout without
+// swizzle that tcgen05 descriptors address: 8 rows x 16 bytes form a core
+// matrix (128 contiguous bytes), core matrices along K lie 128 bytes apart
+// (leading byte offset) and 8-row groups lie K/8 * 128 bytes apart (stride
+// byte offset).
+struct TcSmem {
+  uint8_t w1[kMlpHid * kMlpIn * 2];   // B of layer 1: N = 256, K = 64
+  uint8_t w2[kMlpHid * kMlpHid * 2];  // B of layer 2: N = 256, K = 256
+  uint8_t w3[kMlpOut * kMlpHid * 2];  // B of layer 3: N = 32, K = 256
+  uint8_t x[kRows * kMlpIn * 2];      // A of layer 1: M = 128, K = 64 (features)
   float b1[kMlpHid], b2[kMlpHid], b3[kMlpOut];
   RSShared c;
-  int act[kRows];
-  uint32_t allow[kRows];  // bit a: action a allowed for the row (learned_allow); bit |A|: defer
-  int heur[kRows];        // the heuristic policy's action for the row (taken on defer)
+  unsigned long long mbar;            // completion of each layer's MMAs
+  uint32_t tmem_base;
 };
 
-__device__ __forceinline__ int swz(int row, int word) { return word ^ ((row & 7) << 2); }
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k, int K) {
+  return (uint32_t)((row >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all in 16-byte units), descriptor version 1, base offset 0, no
+// swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase with this parity to complete, for at most 2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  if (mbar_try(mbar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  while (!mbar_try(mbar, parity))
+    if (global_timer() - t0 > 2000000000ull) return false;
+  return true;
+}
+
+// 32 FP32 columns of the warp's 32 lanes (one row per thread), waited for.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 columns of 32-bit words into the warp's 32 lanes.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::
+          "r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+// Hidden layer epilogue of one row: ReLU(accumulator + bias), rounded to BF16,
+// written back as the next layer's A operand.
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias) {
+#pragma unroll 1
+  for (int c = 0; c < kMlpHid / 32; ++c) {
+    float acc[32];
+    tmem_ld32(trow + kColD + 32 * c, acc);
+    uint32_t packed[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float lo = fmaxf(__fadd_rn(acc[2 * j], bias[32 * c + 2 * j]), 0.0f);
+      float hi = fmaxf(__fadd_rn(acc[2 * j + 1], bias[32 * c + 2 * j + 1]), 0.0f);
+      packed[j] = pack_bf16(lo, hi);
+    }
+    tmem_st16(trow + kColH + 16 * c, packed);
+  }
+  tmem_wait_st();
 }
 
 // Actions the learned policy may take (a function of the observable history):
@@ -85,117 +201,6 @@ __device__ __forceinline__ uint32_t learned_allow(const RSShared& c, int n, int 
   return a;
 }
 
-// The network on the 64 rows of S.x; writes S.act: the argmax of the logits
-// over the allowed actions of S.allow and column na ("defer"), lowest index on
-// ties, with defer replaced by the heuristic's action S.heur. All 128
-// threads; warp w owns rows 16w .. 16w + 15.
-__device__ __forceinline__ void policy_tile(MlpSmem& S, int na) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int r0 = 16 * warp + g, r1 = r0 + 8;
-  // layer 1: h = relu(x W1 + b1), 64 columns at a time
-  for (int nc = 0; nc < kMlpHid; nc += 64) {
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-#pragma unroll
-    for (int kw = 0; kw < kMlpIn / 2; kw += 8) {
-      uint32_t a0 = S.x[r0 * 32 + swz(r0, kw + t)], a1 = S.x[r1 * 32 + swz(r1, kw + t)];
-      uint32_t a2 = S.x[r0 * 32 + swz(r0, kw + t + 4)], a3 = S.x[r1 * 32 + swz(r1, kw + t + 4)];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        int n = nc + 8 * j + g;
-        mma16816(acc[j], a0, a1, a2, a3, S.w1[n * 32 + swz(n, kw + t)], S.w1[n * 32 + swz(n, kw + t + 4)]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      int col = nc + 8 * j + 2 * t;
-      float bl = S.b1[col], bh = S.b1[col + 1];
-      S.h[r0 * 128 + swz(r0, col / 2)] = pack_bf16(fmaxf(acc[j][0] + bl, 0.0f), fmaxf(acc[j][1] + bh, 0.0f));
-      S.h[r1 * 128 + swz(r1, col / 2)] = pack_bf16(fmaxf(acc[j][2] + bl, 0.0f), fmaxf(acc[j][3] + bh, 0.0f));
-    }
-  }
-  __syncwarp();
-  // layer 2: h = relu(h W2 + b2), all 256 columns kept in registers, then
-  // written over the warp's own rows
-  {
-    float acc[32][4];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-#pragma unroll 2
-    for (int kw = 0; kw < kMlpHid / 2; kw += 8) {
-      uint32_t a0 = S.h[r0 * 128 + swz(r0, kw + t)], a1 = S.h[r1 * 128 + swz(r1, kw + t)];
-      uint32_t a2 = S.h[r0 * 128 + swz(r0, kw + t + 4)], a3 = S.h[r1 * 128 + swz(r1, kw + t + 4)];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        int n = 8 * j + g;
-        mma16816(acc[j], a0, a1, a2, a3, S.w2[n * 128 + swz(n, kw + t)], S.w2[n * 128 + swz(n, kw + t + 4)]);
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      int col = 8 * j + 2 * t;
-      float bl = S.b2[col], bh = S.b2[col + 1];
-      S.h[r0 * 128 + swz(r0, col / 2)] = pack_bf16(fmaxf(acc[j][0] + bl, 0.0f), fmaxf(acc[j][1] + bh, 0.0f));
-      S.h[r1 * 128 + swz(r1, col / 2)] = pack_bf16(fmaxf(acc[j][2] + bl, 0.0f), fmaxf(acc[j][3] + bh, 0.0f));
-    }
-  }
-  __syncwarp();
-  // layer 3: logits = h W3 + b3, then the argmax of each row
-  float acc[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-#pragma unroll 4
-  for (int kw = 0; kw < kMlpHid / 2; kw += 8) {
-    uint32_t a0 = S.h[r0 * 128 + swz(r0, kw + t)], a1 = S.h[r1 * 128 + swz(r1, kw + t)];
-    uint32_t a2 = S.h[r0 * 128 + swz(r0, kw + t + 4)], a3 = S.h[r1 * 128 + swz(r1, kw + t + 4)];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int n = 8 * j + g;
-      mma16816(acc[j], a0, a1, a2, a3, S.w3[n * 128 + swz(n, kw + t)], S.w3[n * 128 + swz(n, kw + t + 4)]);
-    }
-  }
-  float best0 = -3.0e38f, best1 = -3.0e38f;
-  int arg0 = 0x7FFF, arg1 = 0x7FFF;
-  const uint32_t al0 = S.allow[r0], al1 = S.allow[r1];
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      int col = 8 * j + 2 * t + e;
-      if (col <= na) {
-        float v0 = acc[j][e] + S.b3[col], v1 = acc[j][2 + e] + S.b3[col];
-        if (((al0 >> col) & 1u) && (arg0 == 0x7FFF || v0 > best0)) {
-          best0 = v0;
-          arg0 = col;
-        }
-        if (((al1 >> col) & 1u) && (arg1 == 0x7FFF || v1 > best1)) {
-          best1 = v1;
-          arg1 = col;
-        }
-      }
-    }
-#pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    float ov0 = __shfl_xor_sync(0xFFFFFFFFu, best0, o), ov1 = __shfl_xor_sync(0xFFFFFFFFu, best1, o);
-    int oa0 = __shfl_xor_sync(0xFFFFFFFFu, arg0, o), oa1 = __shfl_xor_sync(0xFFFFFFFFu, arg1, o);
-    if (oa0 != 0x7FFF && (arg0 == 0x7FFF || ov0 > best0 || (ov0 == best0 && oa0 < arg0))) {
-      best0 = ov0;
-      arg0 = oa0;
-    }
-    if (oa1 != 0x7FFF && (arg1 == 0x7FFF || ov1 > best1 || (ov1 == best1 && oa1 < arg1))) {
-      best1 = ov1;
-      arg1 = oa1;
-    }
-  }
-  if (t == 0) {
-    S.act[r0] = arg0 == na ? S.heur[r0] : arg0;
-    S.act[r1] = arg1 == na ? S.heur[r1] : arg1;
-  }
-}
-
 // Where the rows' scenarios come from and where their values go.
 struct ItemSource {
   // expansion: the grouping phase's item list
@@ -210,21 +215,39 @@ struct ItemSource {
   unsigned int* next;  // item counter
 };
 
+// A CTA keeps 128 live scenarios (rows, one per thread) and advances them one
+// step at a time: each row writes its features (BF16) into the layer-1 A tile
+// in shared memory, one elected thread issues the three layers as tcgen05.mma
+// (M = 128, BF16 in, FP32 accumulators in tensor memory, weights resident in
+// shared memory as the B operands, the hidden activations fed back through
+// tensor memory as the A operand), and after each layer's completion every
+// thread reads its own row from tensor memory: bias + ReLU + BF16 for the
+// hidden layers, then the masked argmax of its logits. A row whose scenario
+// ends adds its value to its child and takes the next item at once.
 template <bool kExpand>
-__global__ void __launch_bounds__(kThreads, 1) rs_rollout_mlp_kernel(const DevModel* __restrict__ gm, DevWork* work,
-                                                                     const uint8_t* __restrict__ policy,
-                                                                     ItemSource src, uint32_t plan_step) {
+__global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                                    const uint8_t* __restrict__ policy,
+                                                                    ItemSource src, uint32_t plan_step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  MlpSmem& S = *reinterpret_cast<MlpSmem*>(smem_raw);
-  const int tid = threadIdx.x;
+  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
   load_rs_consts(S.c, gm);
   {
-    const uint32_t* w1 = reinterpret_cast<const uint32_t*>(policy + kPolW1);
-    const uint32_t* w2 = reinterpret_cast<const uint32_t*>(policy + kPolW2);
-    const uint32_t* w3 = reinterpret_cast<const uint32_t*>(policy + kPolW3);
-    for (int i = tid; i < kMlpHid * 32; i += kThreads) S.w1[(i / 32) * 32 + swz(i / 32, i % 32)] = w1[i];
-    for (int i = tid; i < kMlpHid * 128; i += kThreads) S.w2[(i / 128) * 128 + swz(i / 128, i % 128)] = w2[i];
-    for (int i = tid; i < kMlpOut * 128; i += kThreads) S.w3[(i / 128) * 128 + swz(i / 128, i % 128)] = w3[i];
+    const uint4* w1 = reinterpret_cast<const uint4*>(policy + kPolW1);
+    const uint4* w2 = reinterpret_cast<const uint4*>(policy + kPolW2);
+    const uint4* w3 = reinterpret_cast<const uint4*>(policy + kPolW3);
+    for (int i = tid; i < kMlpHid * kMlpIn / 8; i += kThreads) {
+      const int n = i / (kMlpIn / 8), c = i % (kMlpIn / 8);
+      *reinterpret_cast<uint4*>(S.w1 + kmajor_off(n, 8 * c, kMlpIn)) = w1[i];
+    }
+    for (int i = tid; i < kMlpHid * kMlpHid / 8; i += kThreads) {
+      const int n = i / (kMlpHid / 8), c = i % (kMlpHid / 8);
+      *reinterpret_cast<uint4*>(S.w2 + kmajor_off(n, 8 * c, kMlpHid)) = w2[i];
+    }
+    for (int i = tid; i < kMlpOut * kMlpHid / 8; i += kThreads) {
+      const int n = i / (kMlpHid / 8), c = i % (kMlpHid / 8);
+      *reinterpret_cast<uint4*>(S.w3 + kmajor_off(n, 8 * c, kMlpHid)) = w3[i];
+    }
     const float* b1 = reinterpret_cast<const float*>(policy + kPolB1);
     const float* b2 = reinterpret_cast<const float*>(policy + kPolB2);
     const float* b3 = reinterpret_cast<const float*>(policy + kPolB3);
@@ -234,93 +257,181 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_mlp_kernel(const DevMo
     }
     for (int i = tid; i < kMlpOut; i += kThreads) S.b3[i] = b3[i];
   }
+  const uint32_t mbar = smem_u32(&S.mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before_sync();
   __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = S.tmem_base;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's lanes
+  const uint32_t sx = smem_u32(S.x), sw1 = smem_u32(S.w1), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
+  constexpr uint32_t kId1 = idesc_bf16(kRows, kMlpHid), kId3 = idesc_bf16(kRows, kMlpOut);
+
   const RSModel<1> M = make_rs<1>(gm, &S.c, plan_step);
   const int na = gm->num_actions;
   const long long total = kExpand ? src.items.total : (long long)src.count;
-  // per-row state (threads 0..63)
   RSS s;
   uint32_t h[8];
-  uint32_t pm = 0;
-  int t = 0, t0 = 0;
+  uint32_t pm = 0, allow = 0;
+  int t = 0, t0 = 0, heur = 1;
   float v = 0.0f, u = 0.0f;
   long long item = -1;
   bool alive = false, exhausted = false;
   const dsp_leaf_job* J = nullptr;
-  uint32_t slot = 0;
+  uint32_t slot = 0, phase = 0;
   unsigned long long steps = 0;
+  bool failed = false;
   while (true) {
-    if (tid < kRows) {
-      // refill: take items until one needs rolling out (or none is left)
-      while (!alive && !exhausted) {
-        long long it = (long long)atomicAdd(src.next, 1u);
-        if (it >= total) {
-          exhausted = true;
-          break;
-        }
-        item = it;
-        v = 0.0f;
+    // refill: take items until one needs rolling out (or none is left)
+    while (!alive && !exhausted) {
+      long long it = (long long)atomicAdd(src.next, 1u);
+      if (it >= total) {
+        exhausted = true;
+        break;
+      }
+      item = it;
+      v = 0.0f;
+      if (kExpand) {
+        s.pos[0] = src.items.f(0)[it];
+        s.pos[1] = 0u;
+        s.good = src.items.f(1)[it];
+        s.sampled = src.items.f(2)[it];
+        s.scen = src.items.f(3)[it];
+        const uint32_t meta = src.items.f(5)[it];
+        J = src.jobs + src.items.f(6)[it];
+        slot = meta & 0xFFFFFFu;
+        t0 = (int)(meta >> 24) + 1;
+        const uint32_t* hw = reinterpret_cast<const uint32_t*>(J->hist);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = hw[k];
+        pm = positive_mask(h, M.m);
+        const int cap = J->child_cap;
+        M.observe(h, pm, J->first_action + (int)(slot / (uint32_t)cap), J->child_key[slot]);
+        u = M.terminal(s) ? 0.0f : ((t0 >= M.D) ? M.tail(s) : M.upper(s));
+      } else {
+        s = M.load(src.block, src.cap, (int)it);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          h[k] = src.hist ? *reinterpret_cast<const uint32_t*>(src.hist + 32 * (size_t)it + 4 * k) : 0u;
+        pm = positive_mask(h, M.m);
+        t0 = src.start_depth;
+      }
+      t = t0;
+      if (t < M.D && !M.terminal(s)) {
+        alive = true;
+      } else {
+        if (!M.terminal(s)) v = __fadd_rn(v, __fmul_rn(S.c.G[M.D - t0], M.tail(s)));
         if (kExpand) {
-          s.pos[0] = src.items.f(0)[it];
-          s.pos[1] = 0u;
-          s.good = src.items.f(1)[it];
-          s.sampled = src.items.f(2)[it];
-          s.scen = src.items.f(3)[it];
-          const uint32_t meta = src.items.f(5)[it];
-          J = src.jobs + src.items.f(6)[it];
-          slot = meta & 0xFFFFFFu;
-          t0 = (int)(meta >> 24) + 1;
-          const uint32_t* hw = reinterpret_cast<const uint32_t*>(J->hist);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) h[k] = hw[k];
-          pm = positive_mask(h, M.m);
-          const int cap = J->child_cap;
-          M.observe(h, pm, J->first_action + (int)(slot / (uint32_t)cap), J->child_key[slot]);
-          u = M.terminal(s) ? 0.0f : ((t0 >= M.D) ? M.tail(s) : M.upper(s));
+          atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)to_fixed(u));
+          atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)to_fixed(v));
         } else {
-          s = M.load(src.block, src.cap, (int)it);
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            h[k] = src.hist ? *reinterpret_cast<const uint32_t*>(src.hist + 32 * (size_t)it + 4 * k) : 0u;
-          pm = positive_mask(h, M.m);
-          t0 = src.start_depth;
-        }
-        t = t0;
-        if (t < M.D && !M.terminal(s)) {
-          alive = true;
-        } else {
-          if (!M.terminal(s)) v = __fadd_rn(v, __fmul_rn(S.c.G[M.D - t0], M.tail(s)));
-          if (kExpand) {
-            atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)to_fixed(u));
-            atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)to_fixed(v));
-          } else {
-            src.value[it] = v;
-          }
+          src.value[it] = v;
         }
       }
-      // features of the row's state and counters, BF16 into the tile
+    }
+    // features of the row's state and counters, BF16 into the A tile
+    {
       float f[kMlpIn];
       if (alive) {
         int8_t cnt[kMaxRocks];
 #pragma unroll
         for (int r = 0; r < kMaxRocks; ++r) cnt[r] = (int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
         rs_features(M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, cnt, f);
-        S.allow[tid] = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, cnt) | (1u << na);
-        S.heur[tid] = M.policy(s, pm);
+        allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, cnt) | (1u << na);
+        heur = M.policy(s, pm);
       } else {
-        S.allow[tid] = 0x2u;
-        S.heur[tid] = 1;
 #pragma unroll
         for (int k = 0; k < kMlpIn; ++k) f[k] = 0.0f;
       }
 #pragma unroll
-      for (int w = 0; w < kMlpIn / 2; ++w) S.x[tid * 32 + swz(tid, w)] = pack_bf16(f[2 * w], f[2 * w + 1]);
+      for (int c = 0; c < kMlpIn / 8; ++c) {
+        uint4 q;
+        q.x = pack_bf16(f[8 * c + 0], f[8 * c + 1]);
+        q.y = pack_bf16(f[8 * c + 2], f[8 * c + 3]);
+        q.z = pack_bf16(f[8 * c + 4], f[8 * c + 5]);
+        q.w = pack_bf16(f[8 * c + 6], f[8 * c + 7]);
+        *reinterpret_cast<uint4*>(S.x + kmajor_off(tid, 8 * c, kMlpIn)) = q;
+      }
     }
+    fence_async_smem();
     if (!__syncthreads_or(alive ? 1 : 0)) break;
-    policy_tile(S, na);
+    // layer 1: D = X W1^T, four K = 16 steps
+    if (tid == 0) {
+      fence_after_sync();
+#pragma unroll
+      for (int k = 0; k < kMlpIn / 16; ++k)
+        mma_ss(tmem + kColD, smem_desc(sx + 256 * k, 128, (kMlpIn / 8) * 128),
+               smem_desc(sw1 + 256 * k, 128, (kMlpIn / 8) * 128), kId1, k > 0);
+      mma_commit(mbar);
+    }
+    if (!__syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0)) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after_sync();
+    hidden_epilogue(trow, S.b1);
+    fence_before_sync();
     __syncthreads();
-    if (tid < kRows && alive) {
-      const int a = S.act[tid];
+    // layer 2: D = H1 W2^T, A from tensor memory, sixteen K = 16 steps
+    if (tid == 0) {
+      fence_after_sync();
+#pragma unroll 4
+      for (int k = 0; k < kMlpHid / 16; ++k)
+        mma_ts(tmem + kColD, tmem + kColH + 8 * k, smem_desc(sw2 + 256 * k, 128, (kMlpHid / 8) * 128), kId1, k > 0);
+      mma_commit(mbar);
+    }
+    if (!__syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0)) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after_sync();
+    hidden_epilogue(trow, S.b2);
+    fence_before_sync();
+    __syncthreads();
+    // layer 3: logits = H2 W3^T
+    if (tid == 0) {
+      fence_after_sync();
+#pragma unroll 4
+      for (int k = 0; k < kMlpHid / 16; ++k)
+        mma_ts(tmem + kColL, tmem + kColH + 8 * k, smem_desc(sw3 + 256 * k, 128, (kMlpHid / 8) * 128), kId3, k > 0);
+      mma_commit(mbar);
+    }
+    if (!__syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0)) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after_sync();
+    float lg[32];
+    tmem_ld32(trow + kColL, lg);
+    fence_before_sync();
+    if (alive) {
+      // argmax over the allowed actions and defer (column na), lowest index on ties
+      int best = -1;
+      float bv = 0.0f;
+#pragma unroll
+      for (int col = 0; col < 32; ++col) {
+        if (col <= na && ((allow >> col) & 1u)) {
+          const float x = __fadd_rn(lg[col], S.b3[col]);
+          if (best < 0 || x > bv) {
+            bv = x;
+            best = col;
+          }
+        }
+      }
+      const int a = best == na ? heur : best;
       if (!kExpand && src.log) src.log[(size_t)item * M.D + (t - t0)] = a;
       uint64_t key;
       float r = M.step(s, a, t, key);
@@ -340,6 +451,17 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_mlp_kernel(const DevMo
       }
     }
   }
+  if (failed) {
+    // a layer did not complete in time: report, give the MMAs in flight one
+    // more bounded wait, then free the tensor memory
+    if (tid == 0) report(work, kStatusTimeout);
+    mbar_wait(mbar, phase);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
@@ -373,12 +495,12 @@ __global__ void pack_policy(const float* master, uint8_t* pol) {
 template <bool kExpand>
 cudaError_t launch_mlp(const DevModel* gm, DevWork* work, const uint8_t* policy, const ItemSource& src,
                        uint32_t plan_step, int num_sms, long long total, cudaStream_t st) {
-  size_t smem = sizeof(MlpSmem);
-  cudaError_t e = cudaFuncSetAttribute(rs_rollout_mlp_kernel<kExpand>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  size_t smem = sizeof(TcSmem);
+  cudaError_t e = cudaFuncSetAttribute(rs_rollout_tc_kernel<kExpand>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int grid = (int)std::max(1LL, std::min<long long>((total + kRows - 1) / kRows, (long long)num_sms));
-  rs_rollout_mlp_kernel<kExpand><<<grid, kThreads, smem, st>>>(gm, work, policy, src, plan_step);
+  rs_rollout_tc_kernel<kExpand><<<grid, kThreads, smem, st>>>(gm, work, policy, src, plan_step);
   return cudaGetLastError();
 }
 
