@@ -23,8 +23,9 @@ extern "C" dsp_status dsp_mlp_get_weights(const dsp_mlp* mlp, float* host_params
 namespace dsp {
 namespace {
 
-constexpr int kRows = 128;       // scenarios per CTA: the MMA's M, one thread per row
-constexpr int kThreads = 128;    // warp w reads and writes TMEM lanes 32w .. 32w + 31 (its rows)
+constexpr int kRows = 128;       // scenarios per CTA: the MMA's M
+constexpr int kThreads = 256;    // two threads per row: warps w and w + 4 reach TMEM lanes 32w .. 32w + 31
+                                 // and split the hidden epilogues' columns; the first owns the scenario
 // device policy buffer: transposed BF16 weights [n][k], FP32 biases
 constexpr size_t kPolW1 = 0;
 constexpr size_t kPolW2 = kPolW1 + (size_t)kMlpHid * kMlpIn * 2;
@@ -146,6 +147,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 64 FP32 columns of the warp's 32 lanes, waited for.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 16 columns of 32-bit words into the warp's 32 lanes.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
@@ -163,23 +177,59 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Hidden layer epilogue of one row: ReLU(accumulator + bias), rounded to BF16,
-// written back as the next layer's A operand.
-__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias) {
+// Hidden layer epilogue of one row, columns [128 half, 128 half + 128):
+// ReLU(accumulator + bias), rounded to BF16, written back as the next layer's
+// A operand.
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias, int half) {
 #pragma unroll 1
-  for (int c = 0; c < kMlpHid / 32; ++c) {
-    float acc[32];
-    tmem_ld32(trow + kColD + 32 * c, acc);
-    uint32_t packed[16];
+  for (int c = 2 * half; c < 2 * half + 2; ++c) {
+    float acc[64];
+    tmem_ld64(trow + kColD + 64 * c, acc);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      float lo = fmaxf(__fadd_rn(acc[2 * j], bias[32 * c + 2 * j]), 0.0f);
-      float hi = fmaxf(__fadd_rn(acc[2 * j + 1], bias[32 * c + 2 * j + 1]), 0.0f);
-      packed[j] = pack_bf16(lo, hi);
+    for (int q = 0; q < 2; ++q) {
+      uint32_t packed[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = 64 * c + 32 * q + 2 * j;
+        float lo = fmaxf(__fadd_rn(acc[32 * q + 2 * j], bias[col]), 0.0f);
+        float hi = fmaxf(__fadd_rn(acc[32 * q + 2 * j + 1], bias[col + 1]), 0.0f);
+        packed[j] = pack_bf16(lo, hi);
+      }
+      tmem_st16(trow + kColH + 32 * c + 16 * q, packed);
     }
-    tmem_st16(trow + kColH + 16 * c, packed);
   }
   tmem_wait_st();
+}
+
+// The row's features (the feature map of rs_features, same arithmetic) as
+// BF16 pairs straight into the layer-1 A tile: pair 0 = (x/n, y/n), pairs
+// 1 + 2r = ((rock x - x)/n, (rock y - y)/n), 2 + 2r = (clamp(c_r)/3, sampled_r),
+// zero beyond 1 + 2m. Fully unrolled, so nothing goes through local memory.
+__device__ __forceinline__ void write_features(uint8_t* xs, int row, int n, int m, const int* rock_xy, uint32_t pos,
+                                               uint32_t sampled, const uint32_t (&h)[8]) {
+  const float inv_n = 1.0f / (float)n;
+  const float third = 1.0f / 3.0f;
+  const int x = (int)(pos & 0xFFu), y = (int)((pos >> 8) & 0xFFu);
+  uint32_t pr[kMlpIn / 2];
+  pr[0] = pack_bf16((float)x * inv_n, (float)y * inv_n);
+#pragma unroll
+  for (int r = 0; r < 15; ++r) {
+    if (r < m) {
+      const int rxy = rock_xy[r];
+      int c = (int)(int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
+      c = c > 3 ? 3 : (c < -3 ? -3 : c);
+      pr[1 + 2 * r] = pack_bf16((float)((rxy & 0xFF) - x) * inv_n, (float)((rxy >> 8) - y) * inv_n);
+      pr[2 + 2 * r] = pack_bf16((float)c * third, ((sampled >> r) & 1u) ? 1.0f : 0.0f);
+    } else {
+      pr[1 + 2 * r] = 0u;
+      pr[2 + 2 * r] = 0u;
+    }
+  }
+  pr[31] = 0u;
+#pragma unroll
+  for (int c = 0; c < kMlpIn / 8; ++c)
+    *reinterpret_cast<uint4*>(xs + kmajor_off(row, 8 * c, kMlpIn)) =
+        make_uint4(pr[4 * c], pr[4 * c + 1], pr[4 * c + 2], pr[4 * c + 3]);
 }
 
 // Actions the learned policy may take (a function of the observable history):
@@ -188,7 +238,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias
 // repeat them to depth D), no Sense of a sampled rock or of one whose counter
 // reads +-3 (the features clamp there). East is always allowed.
 __device__ __forceinline__ uint32_t learned_allow(const RSShared& c, int n, int m, uint32_t pos, uint32_t sampled,
-                                                  const int8_t* cnt) {
+                                                  const uint32_t (&h)[8]) {
   const int x = (int)(pos & 0xFFu), y = (int)((pos >> 8) & 0xFFu);
   uint32_t a = 0x2u;
   if (y < n - 1) a |= 0x1u;
@@ -196,8 +246,11 @@ __device__ __forceinline__ uint32_t learned_allow(const RSShared& c, int n, int 
   if (x > 0) a |= 0x8u;
   const int i = c.cell_rock[y * n + x];
   if (i != 0xFF && !((sampled >> i) & 1u)) a |= 0x10u;
-  for (int r = 0; r < m; ++r)
-    if (!((sampled >> r) & 1u) && cnt[r] < 3 && cnt[r] > -3) a |= 0x20u << r;
+#pragma unroll
+  for (int r = 0; r < 15; ++r) {
+    const int cr = (int)(int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
+    if (r < m && !((sampled >> r) & 1u) && cr < 3 && cr > -3) a |= 0x20u << r;
+  }
   return a;
 }
 
@@ -230,7 +283,8 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
                                                                     ItemSource src, uint32_t plan_step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, half = tid >> 7;
+  const bool owner = half == 0;  // the thread that holds the row's scenario
   load_rs_consts(S.c, gm);
   {
     const uint4* w1 = reinterpret_cast<const uint4*>(policy + kPolW1);
@@ -273,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = S.tmem_base;
-  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's lanes
+  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
   const uint32_t sx = smem_u32(S.x), sw1 = smem_u32(S.w1), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
   constexpr uint32_t kId1 = idesc_bf16(kRows, kMlpHid), kId3 = idesc_bf16(kRows, kMlpOut);
 
@@ -286,44 +340,80 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
   int t = 0, t0 = 0, heur = 1;
   float v = 0.0f, u = 0.0f;
   long long item = -1;
-  bool alive = false, exhausted = false;
+  bool alive = false;
   const dsp_leaf_job* J = nullptr;
   uint32_t slot = 0, phase = 0;
   unsigned long long steps = 0;
   bool failed = false;
-  while (true) {
-    // refill: take items until one needs rolling out (or none is left)
-    while (!alive && !exhausted) {
-      long long it = (long long)atomicAdd(src.next, 1u);
-      if (it >= total) {
-        exhausted = true;
-        break;
-      }
-      item = it;
-      v = 0.0f;
+  // The row's next item, fetched one dependent stage per step so that no
+  // load latency stalls the tile when a rollout ends: 0 nothing fetched,
+  // 1 index claimed, 2 fields loaded, 3 ready (job data loaded), 4 no items left.
+  int pst = 0;
+  long long pit = -1;
+  uint32_t pf[7], ph[8], pcap = 1, pfa = 0;
+  uint64_t pkey = 0;
+  auto advance = [&]() {
+    if (pst == 0) {
+      pit = (long long)atomicAdd(src.next, 1u);
+      pst = pit < total ? 1 : 4;
+    } else if (pst == 1) {
       if (kExpand) {
-        s.pos[0] = src.items.f(0)[it];
-        s.pos[1] = 0u;
-        s.good = src.items.f(1)[it];
-        s.sampled = src.items.f(2)[it];
-        s.scen = src.items.f(3)[it];
-        const uint32_t meta = src.items.f(5)[it];
-        J = src.jobs + src.items.f(6)[it];
-        slot = meta & 0xFFFFFFu;
-        t0 = (int)(meta >> 24) + 1;
-        const uint32_t* hw = reinterpret_cast<const uint32_t*>(J->hist);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) h[k] = hw[k];
-        pm = positive_mask(h, M.m);
-        const int cap = J->child_cap;
-        M.observe(h, pm, J->first_action + (int)(slot / (uint32_t)cap), J->child_key[slot]);
-        u = M.terminal(s) ? 0.0f : ((t0 >= M.D) ? M.tail(s) : M.upper(s));
+        for (int k = 0; k < 7; ++k) pf[k] = src.items.f(k)[pit];
+        pst = 2;
       } else {
-        s = M.load(src.block, src.cap, (int)it);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) pf[k] = src.block[(size_t)k * src.cap + pit];
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-          h[k] = src.hist ? *reinterpret_cast<const uint32_t*>(src.hist + 32 * (size_t)it + 4 * k) : 0u;
-        pm = positive_mask(h, M.m);
+          ph[k] = src.hist ? *reinterpret_cast<const uint32_t*>(src.hist + 32 * (size_t)pit + 4 * k) : 0u;
+        pst = 3;
+      }
+    } else if (pst == 2) {
+      const dsp_leaf_job* PJ = src.jobs + pf[6];
+      const uint32_t* hw = reinterpret_cast<const uint32_t*>(PJ->hist);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ph[k] = hw[k];
+      pcap = (uint32_t)PJ->child_cap;
+      pfa = (uint32_t)PJ->first_action;
+      pkey = PJ->child_key[pf[5] & 0xFFFFFFu];
+      pst = 3;
+    }
+  };
+  if (owner) {
+    advance();
+    advance();
+    advance();
+  }
+  while (true) {
+    // rows whose scenario ended take the fetched item (an item that needs no
+    // rollout is settled at once and the row waits for the next fetch)
+    while (owner && !alive && pst == 3) {
+      const long long it = pit;
+      pst = 0;
+      item = it;
+      v = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) h[k] = ph[k];
+      pm = positive_mask(h, M.m);
+      if (kExpand) {
+        s.pos[0] = pf[0];
+        s.pos[1] = 0u;
+        s.good = pf[1];
+        s.sampled = pf[2];
+        s.scen = pf[3];
+        const uint32_t meta = pf[5];
+        J = src.jobs + pf[6];
+        slot = meta & 0xFFFFFFu;
+        t0 = (int)(meta >> 24) + 1;
+        M.observe(h, pm, (int)pfa + (int)(slot / pcap), pkey);
+        u = M.terminal(s) ? 0.0f : ((t0 >= M.D) ? M.tail(s) : M.upper(s));
+      } else {
+        s.pos[0] = pf[0];
+        s.pos[1] = 0u;  // one robot (as RSModel<1>::load)
+        s.good = pf[2];
+        s.sampled = pf[3];
+        s.scen = pf[4];
         t0 = src.start_depth;
       }
       t = t0;
@@ -339,32 +429,21 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
         }
       }
     }
+    if (owner) advance();
     // features of the row's state and counters, BF16 into the A tile
-    {
-      float f[kMlpIn];
+    if (owner) {
       if (alive) {
-        int8_t cnt[kMaxRocks];
-#pragma unroll
-        for (int r = 0; r < kMaxRocks; ++r) cnt[r] = (int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
-        rs_features(M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, cnt, f);
-        allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, cnt) | (1u << na);
+        write_features(S.x, tid, M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, h);
+        allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << na);
         heur = M.policy(s, pm);
       } else {
 #pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) f[k] = 0.0f;
-      }
-#pragma unroll
-      for (int c = 0; c < kMlpIn / 8; ++c) {
-        uint4 q;
-        q.x = pack_bf16(f[8 * c + 0], f[8 * c + 1]);
-        q.y = pack_bf16(f[8 * c + 2], f[8 * c + 3]);
-        q.z = pack_bf16(f[8 * c + 4], f[8 * c + 5]);
-        q.w = pack_bf16(f[8 * c + 6], f[8 * c + 7]);
-        *reinterpret_cast<uint4*>(S.x + kmajor_off(tid, 8 * c, kMlpIn)) = q;
+        for (int c = 0; c < kMlpIn / 8; ++c)
+          *reinterpret_cast<uint4*>(S.x + kmajor_off(tid, 8 * c, kMlpIn)) = make_uint4(0u, 0u, 0u, 0u);
       }
     }
     fence_async_smem();
-    if (!__syncthreads_or(alive ? 1 : 0)) break;
+    if (!__syncthreads_or((alive || (owner && pst != 4)) ? 1 : 0)) break;
     // layer 1: D = X W1^T, four K = 16 steps
     if (tid == 0) {
       fence_after_sync();
@@ -380,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
     }
     phase ^= 1u;
     fence_after_sync();
-    hidden_epilogue(trow, S.b1);
+    hidden_epilogue(trow, S.b1, half);
     fence_before_sync();
     __syncthreads();
     // layer 2: D = H1 W2^T, A from tensor memory, sixteen K = 16 steps
@@ -397,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
     }
     phase ^= 1u;
     fence_after_sync();
-    hidden_epilogue(trow, S.b2);
+    hidden_epilogue(trow, S.b2, half);
     fence_before_sync();
     __syncthreads();
     // layer 3: logits = H2 W3^T
@@ -415,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
     phase ^= 1u;
     fence_after_sync();
     float lg[32];
-    tmem_ld32(trow + kColL, lg);
+    if (owner) tmem_ld32(trow + kColL, lg);
     fence_before_sync();
     if (alive) {
       // argmax over the allowed actions and defer (column na), lowest index on ties
