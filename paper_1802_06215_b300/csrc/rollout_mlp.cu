@@ -39,6 +39,7 @@ constexpr size_t kPolBytes = kPolB3 + kMlpOut * 4;
 // one CTA per SM): layer-1 and layer-2 accumulators share columns 0..255
 // (FP32, row r in lane r), the hidden activations of the next layer's A
 // operand take 256..383 (BF16 pairs along K), the logits 384..415.
+constexpr int kDxy = 63;          // rock offsets -31..31 (map side <= 32)
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColD = 0;
 constexpr uint32_t kColH = 256;
@@ -55,6 +56,8 @@ struct TcSmem {
   uint8_t w3[kMlpOut * kMlpHid * 2];  // B of layer 3: N = 32, K = 256
   uint8_t x[kRows * kMlpIn * 2];      // A of layer 1: M = 128, K = 64 (features)
   float b1[kMlpHid], b2[kMlpHid], b3[kMlpOut];
+  uint32_t fdxy[kDxy * kDxy];          // BF16 pair ((float)dx / n, (float)dy / n), dx, dy in -31..31
+  uint32_t fcs[14];                    // BF16 pair (clamp(c) / 3, sampled), c in -3..3
   RSShared c;
   unsigned long long mbar;            // completion of each layer's MMAs
   uint32_t tmem_base;
@@ -205,10 +208,23 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias
 // BF16 pairs straight into the layer-1 A tile: pair 0 = (x/n, y/n), pairs
 // 1 + 2r = ((rock x - x)/n, (rock y - y)/n), 2 + 2r = (clamp(c_r)/3, sampled_r),
 // zero beyond 1 + 2m. Fully unrolled, so nothing goes through local memory.
-__device__ __forceinline__ void write_features(uint8_t* xs, int row, int n, int m, const int* rock_xy, uint32_t pos,
-                                               uint32_t sampled, const uint32_t (&h)[8]) {
+// The BF16 feature pairs that depend on one rock, tabulated per CTA with the
+// arithmetic of rs_features: fdxy[(dx + 31) * 63 + dy + 31] for the offset
+// pair and fcs[(c + 3) * 2 + sampled] for the counter/sampled pair.
+__device__ __forceinline__ void build_feature_tables(uint32_t* fdxy, uint32_t* fcs, int n) {
   const float inv_n = 1.0f / (float)n;
   const float third = 1.0f / 3.0f;
+  for (int i = threadIdx.x; i < kDxy * kDxy; i += blockDim.x) {
+    const int dx = i / kDxy - 31, dy = i % kDxy - 31;
+    fdxy[i] = pack_bf16((float)dx * inv_n, (float)dy * inv_n);
+  }
+  for (int i = threadIdx.x; i < 14; i += blockDim.x) fcs[i] = pack_bf16((float)(i / 2 - 3) * third, (i & 1) ? 1.0f : 0.0f);
+}
+
+__device__ __forceinline__ void write_features(uint8_t* xs, int row, int n, int m, const int* rock_xy, uint32_t pos,
+                                               uint32_t sampled, const uint32_t (&h)[8], const uint32_t* fdxy,
+                                               const uint32_t* fcs) {
+  const float inv_n = 1.0f / (float)n;
   const int x = (int)(pos & 0xFFu), y = (int)((pos >> 8) & 0xFFu);
   uint32_t pr[kMlpIn / 2];
   pr[0] = pack_bf16((float)x * inv_n, (float)y * inv_n);
@@ -218,8 +234,8 @@ __device__ __forceinline__ void write_features(uint8_t* xs, int row, int n, int 
       const int rxy = rock_xy[r];
       int c = (int)(int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
       c = c > 3 ? 3 : (c < -3 ? -3 : c);
-      pr[1 + 2 * r] = pack_bf16((float)((rxy & 0xFF) - x) * inv_n, (float)((rxy >> 8) - y) * inv_n);
-      pr[2 + 2 * r] = pack_bf16((float)c * third, ((sampled >> r) & 1u) ? 1.0f : 0.0f);
+      pr[1 + 2 * r] = fdxy[((rxy & 0xFF) - x + 31) * kDxy + ((rxy >> 8) - y + 31)];
+      pr[2 + 2 * r] = fcs[(c + 3) * 2 + (int)((sampled >> r) & 1u)];
     } else {
       pr[1 + 2 * r] = 0u;
       pr[2 + 2 * r] = 0u;
@@ -311,6 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
     }
     for (int i = tid; i < kMlpOut; i += kThreads) S.b3[i] = b3[i];
   }
+  build_feature_tables(S.fdxy, S.fcs, gm->n);
   const uint32_t mbar = smem_u32(&S.mbar);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
@@ -429,13 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
         }
       }
     }
-    if (owner) advance();
     // features of the row's state and counters, BF16 into the A tile
     if (owner) {
       if (alive) {
-        write_features(S.x, tid, M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, h);
-        allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << na);
-        heur = M.policy(s, pm);
+        write_features(S.x, tid, M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, h, S.fdxy, S.fcs);
       } else {
 #pragma unroll
         for (int c = 0; c < kMlpIn / 8; ++c)
@@ -452,6 +466,15 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
         mma_ss(tmem + kColD, smem_desc(sx + 256 * k, 128, (kMlpIn / 8) * 128),
                smem_desc(sw1 + 256 * k, 128, (kMlpIn / 8) * 128), kId1, k > 0);
       mma_commit(mbar);
+    }
+    // while layer 1 runs: the row's allowed actions, the heuristic's action
+    // and the next fetch stage
+    if (owner) {
+      if (alive) {
+        allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << na);
+        heur = M.policy(s, pm);
+      }
+      advance();
     }
     if (!__syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0)) {
       failed = true;
@@ -498,18 +521,25 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
     fence_before_sync();
     if (alive) {
       // argmax over the allowed actions and defer (column na), lowest index on ties
-      int best = -1;
-      float bv = 0.0f;
+      float xv[32];
+      int xi[32];
 #pragma unroll
       for (int col = 0; col < 32; ++col) {
-        if (col <= na && ((allow >> col) & 1u)) {
-          const float x = __fadd_rn(lg[col], S.b3[col]);
-          if (best < 0 || x > bv) {
-            bv = x;
-            best = col;
-          }
-        }
+        const bool ok = col <= na && ((allow >> col) & 1u);
+        xv[col] = ok ? __fadd_rn(lg[col], S.b3[col]) : 0.0f;
+        xi[col] = ok ? col : 0x7FFF;
       }
+      // pairwise tournament; the right entry wins only if strictly larger,
+      // so the lowest index wins ties
+#pragma unroll
+      for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+          const bool take = xi[k + w] != 0x7FFF && (xi[k] == 0x7FFF || xv[k + w] > xv[k]);
+          xv[k] = take ? xv[k + w] : xv[k];
+          xi[k] = take ? xi[k + w] : xi[k];
+        }
+      const int best = xi[0];
       const int a = best == na ? heur : best;
       if (!kExpand && src.log) src.log[(size_t)item * M.D + (t - t0)] = a;
       uint64_t key;
