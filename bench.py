@@ -52,7 +52,7 @@ except (OSError, ValueError):
     MEASURED = {}
 METRIC = "scenario-steps/sec and leaf expansions/sec at K=500, D=90 (fraction of roofline); root gap"
 KERNEL_SOURCES = {
-    "rs": ["expand_rs.cu", "rs_model.cuh", "common.cuh"],
+    "rs": ["expand_rs.cu", "rs_model.cuh", "rs_common.cuh", "common.cuh"],
     "car": ["expand_car.cu", "car_model.cuh", "group.cuh", "common.cuh"],
 }
 
@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plan", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
+    p.add_argument("--learned-rollouts", type=int, default=0,
+                   help="time only the learned-policy rollout kernel on this many start states and exit")
     p.add_argument("--ref-step-seconds", type=float, default=60.0,
                    help="cap on the oracle's time per step in the reference arm")
     return p.parse_args()
@@ -305,6 +307,48 @@ def combine_ranks(t_ms, steps, dist, device):
     return float(tt.item()), float(st.item())
 
 
+def learned_rollouts(args):
+    """The learned-policy rollout kernel alone (dsp_rollout_logged) on N
+    Rock Sample 15x15 start states with the shipped weights: tensor rate of
+    the in-rollout network against the measured BF16 peak."""
+    import torch
+    from paper_1802_06215_b300 import _dsp, batch, build, learn
+    build.build()
+    cfg = inputs.rs15_15()
+    m = batch.Model(cfg)
+    n = args.learned_rollouts
+    b = inputs.rs_block(cfg, n, np.random.default_rng(0), pos=[(0, cfg.n // 2)])
+    bd = torch.tensor(b.view(np.int32), device="cuda")
+    hd = torch.zeros((n, 32), dtype=torch.int8, device="cuda")
+    val = torch.zeros(n, dtype=torch.float32, device="cuda")
+    h, _ = learn.load_weights(os.path.join(ROOT, "paper_1802_06215_b300", "weights", "rs15_15_pi0.npz"))
+    _dsp.dsp_set_policy(m.h, h)
+    st = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):
+        _dsp.dsp_rollout_logged(m.h, bd.data_ptr(), n, n, hd.data_ptr(), 1, val.data_ptr(), 0, st.cuda_stream)
+    torch.cuda.synchronize()
+    m.reset_counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        _dsp.dsp_rollout_logged(m.h, bd.data_ptr(), n, n, hd.data_ptr(), 1, val.data_ptr(), 0, st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    steps, status = m.counters()
+    if status != 0:
+        raise RuntimeError(f"device status word {status}")
+    flop = 2 * (64 * 256 + 256 * 256 + 256 * (m.num_actions + 1))
+    tflops = steps / args.steps * flop / (ms / 1000.0) / 1e12
+    peak = MEASURED.get("bf16_tflops")
+    print(json.dumps({"metric": "learned-policy rollout tensor rate", "value": tflops, "unit": "TFLOP/s",
+                      "rollouts": n, "ms_per_launch": ms, "scenario_steps_per_launch": steps / args.steps,
+                      "flop_per_scenario_step": flop, "peak": peak, "frac": tflops / peak if peak else None,
+                      "mean_value": float(val.mean().item()), "kernel": "rs_rollout_tc_kernel<false>"}), flush=True)
+    _dsp.dsp_mlp_destroy(h)
+    m.close()
+
+
 def run_ours(args, rank, world):
     import torch
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -441,6 +485,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.learned_rollouts:
+        if rank == 0:
+            learned_rollouts(args)
     else:
         run_ours(args, rank, world)
 
