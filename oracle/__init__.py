@@ -263,8 +263,18 @@ def features_rs(model, block, hist):
     return out
 
 
+def features_car(model, block):
+    """Learned-policy features of car states (64 per state)."""
+    block = np.ascontiguousarray(block, np.uint32)
+    w, cap = block.shape
+    out = np.zeros((cap, MLP_IN), np.float32)
+    rc = lib().orc_features_car(C.byref(model.c), _p(block, _U32), C.c_int32(cap), C.c_int32(cap), _p(out, _F32))
+    assert rc == 0
+    return out
+
+
 def rollout_learned(model, block, hist, start_depth, weights, logged=None, tol=1e-2):
-    """Learned-policy rollout values (one robot); with `logged` actions
+    """Learned-policy rollout values (one-robot Rock Sample or the car); with `logged` actions
     (count x D) it replays them and returns, per scenario, the steps whose
     logged action loses to the network's argmax by more than `tol`."""
     block = np.ascontiguousarray(block, np.uint32)

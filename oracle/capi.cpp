@@ -306,9 +306,109 @@ int32_t orc_mlp_loss_grad(const double* W1, const double* b1, const double* W2, 
                        bf16_forward);
 }
 
+// Policy features of a car state (not in the paper; the learned default
+// policy's input): s / path length, v / 3, then for the 8 pedestrians nearest
+// to the car (squared distance from the car's position, lower index first on
+// ties, nearest first): dx / 10, dy / 10 (pedestrian minus car) and 1 when the
+// pedestrian is in the danger zone of the heuristic policy (0 < dx <= 4,
+// -1 <= dy <= 1), else 0; zero beyond. All FP32 in this order.
+static void car_features(const Car<float>& m, const CarState<float>& s, float* f) {
+  for (int k = 0; k < kMlpIn; ++k) f[k] = 0.0f;
+  const float inv_len = 1.0f / m.path_len;
+  const float third = 1.0f / 3.0f;
+  f[0] = s.s * inv_len;
+  f[1] = (float)s.v * third;
+  const float cx = m.car_x(s), cy = m.car_y();
+  int idx[8];
+  float dd[8];
+  int k = 0;
+  for (int i = 0; i < m.P; ++i) {
+    const float ex = s.px[i] - cx, ey = s.py[i] - cy;
+    const float d2 = ex * ex + ey * ey;
+    // insertion into the sorted list of the nearest (strictly nearer goes first)
+    int at = k;
+    while (at > 0 && dd[at - 1] > d2) --at;
+    if (at >= 8) continue;
+    for (int q = (k < 8 ? k : 7); q > at; --q) {
+      dd[q] = dd[q - 1];
+      idx[q] = idx[q - 1];
+    }
+    dd[at] = d2;
+    idx[at] = i;
+    if (k < 8) ++k;
+  }
+  for (int q = 0; q < k; ++q) {
+    const float ex = s.px[idx[q]] - cx, ey = s.py[idx[q]] - cy;
+    f[2 + 3 * q] = ex * 0.1f;
+    f[3 + 3 * q] = ey * 0.1f;
+    f[4 + 3 * q] = (ex > 0.0f && ex <= 4.0f && ey >= -1.0f && ey <= 1.0f) ? 1.0f : 0.0f;
+  }
+}
+
+int32_t orc_features_car(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count, float* out) {
+  if (d->kind != 2) return 1;
+  Car<float> m = make_car<float>(d);
+  for (int i = 0; i < count; ++i) car_features(m, m.unpack(block, cap, i), out + (size_t)i * kMlpIn);
+  return 0;
+}
+
 int32_t orc_features_rs(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,
                         float* out) {
   return features_rs(d->n, d->m, d->rock_cells, block, cap, count, hist, out);
+}
+
+// Default-policy rollout (Eq. lb) of the car with the learned policy: the
+// argmax of logits 0..3 (every action is allowed; logit 3 "defer" takes the
+// heuristic policy's action), lowest index on ties; with `logged` the logged
+// actions are replayed as for Rock Sample.
+static int32_t rollout_learned_car(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count,
+                                   int32_t start_depth, const double* W1, const double* b1, const double* W2,
+                                   const double* b2, const double* W3, const double* b3, const int32_t* logged,
+                                   double tol, double* values, int32_t* disagree, uint64_t* steps) {
+  Car<float> m = make_car<float>(d);
+  Net w{W1, b1, W2, b2, W3, b3};
+  const int na = m.num_actions();
+  uint64_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    CarState<float> s = m.unpack(block, cap, i);
+    Hist h = hist_from(nullptr);
+    float v = 0.0f;
+    int t = start_depth, k = 0, bad = 0;
+    while (t < m.D && !m.terminal(s)) {
+      float fx[kMlpIn];
+      car_features(m, s, fx);
+      double x64[kMlpIn], lg[kMlpOut];
+      for (int q = 0; q < kMlpIn; ++q) x64[q] = (double)fx[q];
+      forward_bf16(w, x64, lg);
+      int best = 0;
+      for (int a = 1; a <= na; ++a)
+        if (lg[a] > lg[best]) best = a;
+      const int heur = m.policy(s, h);
+      const int chosen = best == na ? heur : best;
+      int a = chosen;
+      if (logged) {
+        a = logged[(size_t)i * m.D + k];
+        bool ok = a == chosen;
+        if (!ok && a >= 0 && a < na && lg[best] - lg[a] <= tol) ok = true;
+        if (!ok && a == heur && lg[best] - lg[na] <= tol) ok = true;
+        if (!ok) bad += 1;
+        if (a < 0 || a >= na) a = chosen;
+      }
+      CarState<float> next;
+      uint64_t key;
+      float r = m.step(s, a, t, next, &key);
+      v = v + m.G[t - start_depth] * r;
+      s = next;
+      t += 1;
+      k += 1;
+    }
+    if (!m.terminal(s)) v = v + m.G[m.D - start_depth] * m.tail(s);
+    values[i] = (double)v;
+    if (disagree) disagree[i] = bad;
+    total += (uint64_t)k;
+  }
+  *steps = total;
+  return 0;
 }
 
 // Actions the learned policy may take in a one-robot Rock Sample state with
@@ -346,6 +446,8 @@ int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t c
                             const double* W2, const double* b2, const double* W3, const double* b3,
                             const int32_t* logged, double tol, double* values, int32_t* disagree,
                             uint64_t* steps) {
+  if (d->kind == 2) return rollout_learned_car(d, block, cap, count, start_depth, W1, b1, W2, b2, W3, b3, logged, tol,
+                                              values, disagree, steps);
   if (d->kind != 0) return 1;
   RockSample<float> m = make_rs<float>(d);
   Net w{W1, b1, W2, b2, W3, b3};

@@ -214,3 +214,60 @@ def test_learned_rollout_defer_is_the_heuristic():
     w2 = bias_net({20: 0.5, 1: 1.0, 4: 2.0})
     v2, _, _ = oracle.rollout_learned(m, b, hist, 0, w2)
     assert not np.array_equal(v2, oracle.rollout_learned(m, b, hist, 0, w)[0])
+
+
+def car_state(cfg, s, v, peds):
+    b = np.zeros((I.words(cfg), 1), np.uint32)
+    b[0, 0] = np.float32(s).view(np.uint32)
+    b[1, 0] = v
+    for j, (x, y, g) in enumerate(peds):
+        b[4 + j, 0] = np.float32(x).view(np.uint32)
+        b[4 + cfg.P + j, 0] = np.float32(y).view(np.uint32)
+        b[4 + 2 * cfg.P + j // 4, 0] |= np.uint32(g << (8 * (j % 4)))
+    return b
+
+
+def test_car_features_golden():
+    cfg = I.car_config(P=3, K=4, D=10, seed=0)
+    b = car_state(cfg, 5.0, 2, [(-2.0, 20.5, 0), (-5.0, 26.0, 0), (0.0, 19.0, 0)])
+    f = oracle.features_car(oracle.Model(cfg), b)[0]
+    vals = [float(x) for x in open(os.path.join(os.path.dirname(__file__), "golden", "car_features.txt")).read()
+            .split("\n")[-2].split()]
+    assert np.allclose(f[:11], vals, atol=1e-6)
+    assert np.all(f[11:] == 0)
+
+
+def test_car_learned_defer_is_the_heuristic():
+    """A network whose largest logit is column 3 ("defer") takes the car
+    heuristic's action at every step: value for value the heuristic rollout."""
+    cfg = I.car50()
+    m = oracle.Model(cfg)
+    w = bias_net({3: 5.0, 0: 1.0})
+    rng = np.random.default_rng(8)
+    b = I.car_block(cfg, 24, rng)
+    for d0 in (0, 20):
+        v, _, steps = oracle.rollout_learned(m, b, None, d0, w)
+        vh, sh = m.rollout(b, None, d0)
+        assert np.array_equal(v.astype(np.float32), vh.astype(np.float32)) and steps == sh
+
+
+def test_car_learned_constant_actions_closed_form():
+    """With action failures off and one pedestrian standing far away:
+    always Accelerate reaches s = 60 m after T steps (speeds 1, 2, 3, 3, ...
+    m/s, 0.33 s per step), worth 1000 gamma^(T-1); always Decelerate stays at
+    rest and pays 0.1 per step, -0.1 (1 - gamma^n) / (1 - gamma)."""
+    cfg = I.car_config(P=1, K=4, D=100, seed=0).with_(fail_p=0.0)
+    m = oracle.Model(cfg)
+    b = car_state(cfg, 0.0, 0, [(0.0, 0.0, 0)])
+    s, v, T = np.float32(0), 0, None
+    for t in range(cfg.D):
+        v = min(v + 1, 3)
+        s = np.float32(s + np.float32(v) * np.float32(0.33))
+        if s >= 60:
+            T = t + 1
+            break
+    va, _, steps = oracle.rollout_learned(m, b, None, 0, bias_net({0: 5.0}))
+    assert np.isclose(va[0], 1000 * 0.95 ** (T - 1), rtol=1e-5) and steps == T
+    vd, _, steps = oracle.rollout_learned(m, b, None, 0, bias_net({2: 5.0}))
+    n = cfg.D
+    assert np.isclose(vd[0], -0.1 * (1 - 0.95 ** n) / (1 - 0.95), rtol=1e-5) and steps == n
