@@ -293,13 +293,20 @@ dsp_status dsp_mlp_train_step(dsp_mlp* mlp, const float* X, const int32_t* y, in
 
 /* Makes `mlp` (its current weights, copied) the default policy of every later
  * rollout of the model (dsp_expand_leaves, dsp_expand_leaves_noalloc,
- * dsp_rollout): at each rollout step the network maps the scenario's features
- * to logits and the argmax of the first |A| (lowest index on ties) is the
- * action, evaluated as BF16 tensor-core tiles over 64 live scenarios per CTA
- * with FP32 accumulation. g is still stepped exactly, so the rollout value is
- * a true policy value and l0 a valid lower bound. NULL restores the heuristic
- * policy. One-robot Rock Sample with at most 15 rocks (DSP_E_UNSUPPORTED
- * otherwise); the device job queue keeps the heuristic policy. */
+ * dsp_rollout). At each rollout step the network maps the scenario's features
+ * (dsp_features) to logits. The action is the argmax, lowest index on ties,
+ * over the allowed actions and logit |A| ("defer", which takes the heuristic
+ * policy's action).
+ *  - Rock Sample: no move off the N, S or W border and no Sample off an
+ *    unsampled rock; no Sense of a sampled rock or of one whose counter reads
+ *    +-3.
+ *  - Car: every action is allowed.
+ * The network runs as tcgen05 tensor-core tiles over 128 live scenarios per
+ * CTA, BF16 inputs with FP32 accumulation. g is still stepped exactly, so the
+ * rollout value is a true policy value and l0 a valid lower bound. NULL
+ * restores the heuristic policy. One-robot Rock Sample with at most 15 rocks,
+ * or the car (DSP_E_UNSUPPORTED for two robots); the device job queue keeps
+ * the heuristic policy. */
 dsp_status dsp_set_policy(dsp_model* model, const dsp_mlp* mlp);
 /* dsp_rollout with the learned policy, also recording the action of every
  * step: actions (device, count x D int32, may be NULL) gets at
@@ -307,11 +314,16 @@ dsp_status dsp_set_policy(dsp_model* model, const dsp_mlp* mlp);
 dsp_status dsp_rollout_logged(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
                               const int8_t* hist, int32_t start_depth, float* value, int32_t* actions, void* stream);
 
-/* Policy features of one-robot Rock Sample states (the learned policy's
- * input, the same function the learned rollout evaluates): out (device,
- * count x 64 FP32) row i = x/n, y/n, then per rock (rock x - x)/n,
- * (rock y - y)/n, clamp(counter, -3, 3)/3, sampled, zero-padded. block:
- * device state block of capacity cap; hist: device count x 32 counters. */
+/* Policy features (the learned policy's input, the same function the learned
+ * rollout evaluates): out (device, count x 64 FP32, 16-byte aligned); block:
+ * device state block of capacity cap.
+ *  - One-robot Rock Sample: row i = x/n, y/n, then per rock (rock x - x)/n,
+ *    (rock y - y)/n, clamp(counter, -3, 3)/3, sampled, zero-padded. hist:
+ *    device count x 32 counters.
+ *  - Car: s / path length, v / 3, then for the 8 pedestrians nearest to the
+ *    car (squared distance, lower index on ties) dx / 10, dy / 10 and 1 if the
+ *    pedestrian is in the heuristic policy's danger zone (0 < dx <= 4,
+ *    |dy| <= 1), zero-padded. hist is ignored (may be NULL). */
 dsp_status dsp_features(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
                         const int8_t* hist, float* out, void* stream);
 

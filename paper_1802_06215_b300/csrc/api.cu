@@ -355,6 +355,11 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
     std::stable_sort(plan.units.begin(), plan.units.end(), [&](const int4& x, const int4& y) {
       return jobs[x.x].n_scen > jobs[y.x].n_scen;
     });
+    // first rollout item of each unit (used when a learned policy rolls out)
+    for (int4& u : plan.units) {
+      u.z = (int)plan.total_items;
+      plan.total_items += jobs[u.x].n_scen;
+    }
   } else {
     plan.order.resize(n_jobs);
     for (int j = 0; j < n_jobs; ++j) plan.order[j] = j;
@@ -377,7 +382,9 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   size_t jb = sizeof(dsp_leaf_job) * (size_t)n_jobs;
   size_t ub = car ? sizeof(int4) * plan.units.size()
                   : sizeof(long long) * plan.item_base.size() + sizeof(int) * plan.order.size();
-  size_t ib = car ? 0 : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
+  const bool car_items = car && m->policy_on;
+  size_t ib = car ? (car_items ? sizeof(uint32_t) * (size_t)(h->words + 2) * (size_t)plan.total_items : 0)
+                  : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
   size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
   unsigned char* buf = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, total, m->pool, st);
@@ -406,7 +413,9 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
       cudaEventRecord(ev[0], st);
     }
     if (car) {
-      e = launch_car_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, st);
+      CarItems ci{car_items ? items : nullptr, plan.total_items, h->words};
+      e = launch_car_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, ci, st);
+      if (e == cudaSuccess && car_items) e = launch_car_rollout_mlp_items(m, djobs, ci, counters + 1, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
       e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, (const long long*)dunits, dorder, n_jobs,

@@ -14,6 +14,8 @@
 // mix of (speed + 1) plus the mixes of every (index+1)<<48 | cell x<<16 |
 // cell y, cells = floor(2 * position); bit 62 = terminal.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace dsp {
@@ -34,7 +36,9 @@ template <int TPS>
 struct CarLane {
   static constexpr int kPairs = (kMaxPeds / 2 + TPS - 1) / TPS;  // pairs a lane may own
   float px[2 * kPairs], py[2 * kPairs];
-  uint32_t goals;   // 2 bits per owned pedestrian
+  // 2 bits per owned pedestrian: 64 bits once a lane owns more than 16
+  using Goals = typename std::conditional<(2 * kPairs > 16), unsigned long long, uint32_t>::type;
+  Goals goals;
   float s;
   int v;
   bool term;
@@ -75,7 +79,7 @@ struct CarModel {
           L.px[2 * k + e] = __uint_as_float(b[(size_t)(4 + j) * cap + i]);
           L.py[2 * k + e] = __uint_as_float(b[(size_t)(4 + P + j) * cap + i]);
           uint32_t gw = b[(size_t)(4 + 2 * P + j / 4) * cap + i];
-          L.goals |= ((gw >> (8 * (j % 4))) & 3u) << (2 * (2 * k + e));
+          L.goals |= (typename CarLane<TPS>::Goals)((gw >> (8 * (j % 4))) & 3u) << (2 * (2 * k + e));
         } else {
           L.px[2 * k + e] = 0.0f;
           L.py[2 * k + e] = 0.0f;
@@ -110,12 +114,12 @@ struct CarModel {
 #pragma unroll
     for (int k = 0; k < CarLane<TPS>::kPairs; ++k) {
       int q = gl + k * TPS;
-      uint32_t mine = (L.goals >> (4 * k)) & 15u;
+      uint32_t mine = (uint32_t)(L.goals >> (4 * k)) & 15u;
       int q2 = q + 1;
       int src = gbase + (q2 % TPS);
       int k2 = q2 / TPS;
-      uint32_t other_all = __shfl_sync(0xFFFFFFFFu, L.goals, src);
-      uint32_t other = (other_all >> (4 * k2)) & 15u;
+      const typename CarLane<TPS>::Goals other_all = __shfl_sync(0xFFFFFFFFu, L.goals, src);
+      uint32_t other = (uint32_t)(other_all >> (4 * k2)) & 15u;
       if (valid && (q & 1) == 0 && 2 * q < P) {
         uint32_t w = (mine & 3u) | ((mine >> 2) << 8);
         if (2 * q2 < P) w |= ((other & 3u) << 16) | ((other >> 2) << 24);
@@ -157,7 +161,7 @@ struct CarModel {
             float& x = L.px[2 * k + e];
             float& y = L.py[2 * k + e];
             if (live) {
-              int gi = (L.goals >> (2 * (2 * k + e))) & 3;
+              int gi = (int)(L.goals >> (2 * (2 * k + e))) & 3;
               float gx = (gi & 1) ? 40.0f : 0.0f, gy = (gi & 2) ? 40.0f : 0.0f;
               float dx = __fsub_rn(gx, x), dy = __fsub_rn(gy, y);
               float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
@@ -274,5 +278,31 @@ struct CarModel {
     return v;
   }
 };
+
+// A group's view of the model: TPS consecutive lanes share one scenario.
+template <int TPS>
+__device__ __forceinline__ CarModel<TPS> make_car_model(const DevModel* gm, const CarShared* sh, uint32_t plan_step) {
+  CarModel<TPS> M;
+  M.sh = sh;
+  M.P = gm->P;
+  M.D = gm->D;
+  M.path_len = gm->path_len;
+  M.dt = gm->dt;
+  M.sigma = gm->sigma;
+  M.stride = gm->stride;
+  M.fail_thresh = gm->fail_thresh;
+  M.seed = gm->seed;
+  M.plan_step = plan_step;
+  int lane = threadIdx.x & 31;
+  M.gl = lane % TPS;
+  M.gbase = lane - M.gl;
+  M.gmask = (TPS == 32 ? 0xFFFFFFFFu : ((1u << TPS) - 1u)) << M.gbase;
+  return M;
+}
+
+__device__ __forceinline__ void load_car_consts(CarShared& c, const DevModel* gm) {
+  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
+  for (int k = threadIdx.x; k < kGaussLen; k += blockDim.x) c.gauss[k] = gm->gauss[k];
+}
 
 }  // namespace dsp

@@ -90,4 +90,15 @@ __device__ __forceinline__ int hist_get(const uint32_t (&h)[8], int i) {
   return (int)(int8_t)((h[i >> 2] >> (8 * (i & 3))) & 0xFFu);
 }
 
+// Rollout items of a car expansion with a learned policy: the stepped states
+// as a state block of capacity `total` (words fields), then per item the
+// meta word depth << 24 | child slot and the job index.
+struct CarItems {
+  uint32_t* base;  // null: the expansion rolls out with the heuristic policy
+  long long total;
+  int words;
+  __host__ __device__ uint32_t* meta() const { return base + (size_t)words * total; }
+  __host__ __device__ uint32_t* job() const { return base + (size_t)(words + 1) * total; }
+};
+
 }  // namespace dsp

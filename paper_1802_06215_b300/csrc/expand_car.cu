@@ -30,40 +30,15 @@ struct CarUnitSmem {
 };
 
 template <int TPS>
-__device__ __forceinline__ CarModel<TPS> make_model(const DevModel* gm, const CarShared* sh, uint32_t plan_step) {
-  CarModel<TPS> M;
-  M.sh = sh;
-  M.P = gm->P;
-  M.D = gm->D;
-  M.path_len = gm->path_len;
-  M.dt = gm->dt;
-  M.sigma = gm->sigma;
-  M.stride = gm->stride;
-  M.fail_thresh = gm->fail_thresh;
-  M.seed = gm->seed;
-  M.plan_step = plan_step;
-  int lane = threadIdx.x & 31;
-  M.gl = lane % TPS;
-  M.gbase = lane - M.gl;
-  M.gmask = (TPS == 32 ? 0xFFFFFFFFu : ((1u << TPS) - 1u)) << M.gbase;
-  return M;
-}
-
-__device__ __forceinline__ void load_consts(CarShared& c, const DevModel* gm) {
-  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) c.G[k] = gm->G[k];
-  for (int k = threadIdx.x; k < kGaussLen; k += blockDim.x) c.gauss[k] = gm->gauss[k];
-}
-
-template <int TPS>
 __global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                          const dsp_leaf_job* __restrict__ jobs,
                                                          const int4* __restrict__ units, int n_units,
                                                          unsigned int* head, uint32_t plan_step,
-                                                         uint32_t* scratch) {
+                                                         uint32_t* scratch, CarItems items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CarUnitSmem& S = *reinterpret_cast<CarUnitSmem*>(smem_raw);
-  load_consts(S.c, gm);
-  CarModel<TPS> M = make_model<TPS>(gm, &S.c, plan_step);
+  load_car_consts(S.c, gm);
+  CarModel<TPS> M = make_car_model<TPS>(gm, &S.c, plan_step);
   const int P = M.P;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int groups = nthr / TPS, g = tid / TPS;
@@ -127,9 +102,15 @@ __global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(cons
             }
           }
       }
-      // Eq. ub (the tail heuristic is zero at depth D) and Eq. lb
+      // Eq. ub (the tail heuristic is zero at depth D) and Eq. lb; with a
+      // learned policy the stepped state goes to the item list instead and the
+      // learned-rollout kernel adds the rollout values afterwards
       float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(L);
-      float lv = M.rollout(L, valid, danger, depth + 1, steps);
+      float lv = 0.0f;
+      if (items.base != nullptr)
+        M.store(L, items.base, (int)items.total, un.z + p, valid);
+      else
+        lv = M.rollout(L, valid, danger, depth + 1, steps);
       if (valid && M.gl == 0) {
         S.key[p] = key;
         S.rew[p] = r;
@@ -179,6 +160,10 @@ __global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(cons
     for (int q = tid; q < n; q += nthr) {
       int c = S.grp.gcid[q];
       job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
+      if (items.base != nullptr) {
+        items.meta()[un.z + q] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
+        items.job()[un.z + q] = (uint32_t)un.x;
+      }
     }
     __syncthreads();
   }
@@ -193,9 +178,9 @@ __global__ void __launch_bounds__(256) car_step_kernel(const DevModel* __restric
                                                        uint32_t plan_step) {
   constexpr int TPS = 8;
   __shared__ CarShared c;
-  load_consts(c, gm);
+  load_car_consts(c, gm);
   __syncthreads();
-  CarModel<TPS> M = make_model<TPS>(gm, &c, plan_step);
+  CarModel<TPS> M = make_car_model<TPS>(gm, &c, plan_step);
   const int groups = blockDim.x / TPS;
   for (int base = blockIdx.x * groups; base < count; base += gridDim.x * groups) {
     int i = base + (int)threadIdx.x / TPS;
@@ -222,9 +207,9 @@ __global__ void __launch_bounds__(256) car_rollout_kernel(const DevModel* __rest
                                                           int start_depth, float* value, uint32_t plan_step) {
   constexpr int TPS = 8;
   __shared__ CarShared c;
-  load_consts(c, gm);
+  load_car_consts(c, gm);
   __syncthreads();
-  CarModel<TPS> M = make_model<TPS>(gm, &c, plan_step);
+  CarModel<TPS> M = make_car_model<TPS>(gm, &c, plan_step);
   const int groups = blockDim.x / TPS;
   unsigned long long steps = 0;
   for (int base = blockIdx.x * groups; base < count; base += gridDim.x * groups) {
@@ -243,7 +228,7 @@ __global__ void __launch_bounds__(256) car_rollout_kernel(const DevModel* __rest
 
 template <int TPS>
 cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units, unsigned int* head,
-                       cudaStream_t st) {
+                       CarItems items, cudaStream_t st) {
   size_t smem = sizeof(CarUnitSmem);
   cudaError_t e = cudaFuncSetAttribute(car_expand_kernel<TPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -258,7 +243,7 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
   e = cudaMallocFromPoolAsync((void**)&scratch, need, m->pool, st);
   if (e != cudaSuccess) return e;
   car_expand_kernel<TPS><<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, head, m->plan_step,
-                                                   scratch);
+                                                   scratch, items);
   e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   return e != cudaSuccess ? e : e2;
@@ -267,12 +252,12 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
 }  // namespace
 
 cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
-                              unsigned int* head, cudaStream_t st) {
+                              unsigned int* head, CarItems items, cudaStream_t st) {
   switch (m->tune_tps > 0 ? m->tune_tps : 32) {
-    case 4: return launch_tps<4>(m, djobs, dunits, n_units, head, st);
-    case 8: return launch_tps<8>(m, djobs, dunits, n_units, head, st);
-    case 16: return launch_tps<16>(m, djobs, dunits, n_units, head, st);
-    default: return launch_tps<32>(m, djobs, dunits, n_units, head, st);
+    case 4: return launch_tps<4>(m, djobs, dunits, n_units, head, items, st);
+    case 8: return launch_tps<8>(m, djobs, dunits, n_units, head, items, st);
+    case 16: return launch_tps<16>(m, djobs, dunits, n_units, head, items, st);
+    default: return launch_tps<32>(m, djobs, dunits, n_units, head, items, st);
   }
 }
 

@@ -41,7 +41,17 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
                          cudaStream_t st);
 
 cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
-                              unsigned int* head, cudaStream_t st);
+                              unsigned int* head, CarItems items, cudaStream_t st);
+// Learned-policy rollouts of the car expansion's items; counter: a device
+// uint, zero on entry.
+cudaError_t launch_car_rollout_mlp_items(dsp_model* m, const dsp_leaf_job* jobs, CarItems items, unsigned int* counter,
+                                         cudaStream_t st);
+// Learned-policy rollouts of single car scenarios (dsp_rollout_logged).
+cudaError_t launch_car_rollout_logged(const dsp_model* m, const uint32_t* block, int cap, int count, int start_depth,
+                                      float* value, int32_t* actions, unsigned int* counter, cudaStream_t st);
+// Learned-policy features of car states (dsp_features).
+cudaError_t launch_car_features(const dsp_model* m, const uint32_t* block, int cap, int count, float* out,
+                                cudaStream_t st);
 cudaError_t launch_car_step(const DevModel* gm, int P, const uint32_t* in, int in_cap, int count,
                             const int32_t* actions, int depth, uint32_t* out, int out_cap, uint64_t* keys,
                             float* rewards, uint32_t plan_step, cudaStream_t st);

@@ -16,6 +16,7 @@
 #include "mlp.cuh"
 #include "model.hpp"
 #include "rs_common.cuh"
+#include "tc_mlp.cuh"
 
 struct dsp_mlp;  // training object (mlp_train.cu); its FP32 master is read here
 extern "C" dsp_status dsp_mlp_get_weights(const dsp_mlp* mlp, float* host_params);
@@ -23,39 +24,14 @@ extern "C" dsp_status dsp_mlp_get_weights(const dsp_mlp* mlp, float* host_params
 namespace dsp {
 namespace {
 
-constexpr int kRows = 128;       // scenarios per CTA: the MMA's M
-constexpr int kThreads = 256;    // two threads per row: warps w and w + 4 reach TMEM lanes 32w .. 32w + 31
-                                 // and split the hidden epilogues' columns; the first owns the scenario
-// device policy buffer: transposed BF16 weights [n][k], FP32 biases
-constexpr size_t kPolW1 = 0;
-constexpr size_t kPolW2 = kPolW1 + (size_t)kMlpHid * kMlpIn * 2;
-constexpr size_t kPolW3 = kPolW2 + (size_t)kMlpHid * kMlpHid * 2;
-constexpr size_t kPolB1 = kPolW3 + (size_t)kMlpOut * kMlpHid * 2;
-constexpr size_t kPolB2 = kPolB1 + kMlpHid * 4;
-constexpr size_t kPolB3 = kPolB2 + kMlpHid * 4;
-constexpr size_t kPolBytes = kPolB3 + kMlpOut * 4;
+using namespace tc;
 
-// Tensor memory of a CTA (all 512 columns; the kernel's shared memory keeps
-// one CTA per SM): layer-1 and layer-2 accumulators share columns 0..255
-// (FP32, row r in lane r), the hidden activations of the next layer's A
-// operand take 256..383 (BF16 pairs along K), the logits 384..415.
+
 constexpr int kDxy = 63;          // rock offsets -31..31 (map side <= 32)
-constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColD = 0;
-constexpr uint32_t kColH = 256;
-constexpr uint32_t kColL = 384;
 
-// Shared memory. Matrices are stored in the canonical K-major layout without
-// swizzle that tcgen05 descriptors address: 8 rows x 16 bytes form a core
-// matrix (128 contiguous bytes), core matrices along K lie 128 bytes apart
-// (leading byte offset) and 8-row groups lie K/8 * 128 bytes apart (stride
-// byte offset).
 struct TcSmem {
-  uint8_t w1[kMlpHid * kMlpIn * 2];   // B of layer 1: N = 256, K = 64
-  uint8_t w2[kMlpHid * kMlpHid * 2];  // B of layer 2: N = 256, K = 256
-  uint8_t w3[kMlpOut * kMlpHid * 2];  // B of layer 3: N = 32, K = 256
+  Weights W;
   uint8_t x[kRows * kMlpIn * 2];      // A of layer 1: M = 128, K = 64 (features)
-  float b1[kMlpHid], b2[kMlpHid], b3[kMlpOut];
   uint32_t fdxy[kDxy * kDxy];          // BF16 pair ((float)dx / n, (float)dy / n), dx, dy in -31..31
   uint32_t fcs[14];                    // BF16 pair (clamp(c) / 3, sampled), c in -3..3
   RSShared c;
@@ -63,151 +39,6 @@ struct TcSmem {
   uint32_t tmem_base;
 };
 
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k, int K) {
-  return (uint32_t)((row >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: start address, leading and stride byte
-// offsets (all in 16-byte units), descriptor version 1, base offset 0, no
-// swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N >> 3 and M >> 4.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ uint64_t global_timer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase with this parity to complete, for at most 2 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  if (mbar_try(mbar, parity)) return true;
-  const uint64_t t0 = global_timer();
-  while (!mbar_try(mbar, parity))
-    if (global_timer() - t0 > 2000000000ull) return false;
-  return true;
-}
-
-// 32 FP32 columns of the warp's 32 lanes (one row per thread), waited for.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 64 FP32 columns of the warp's 32 lanes, waited for.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 16 columns of 32-bit words into the warp's 32 lanes.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::
-          "r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-// Hidden layer epilogue of one row, columns [128 half, 128 half + 128):
-// ReLU(accumulator + bias), rounded to BF16, written back as the next layer's
-// A operand.
-__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias, int half) {
-#pragma unroll 1
-  for (int c = 2 * half; c < 2 * half + 2; ++c) {
-    float acc[64];
-    tmem_ld64(trow + kColD + 64 * c, acc);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      uint32_t packed[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = 64 * c + 32 * q + 2 * j;
-        float lo = fmaxf(__fadd_rn(acc[32 * q + 2 * j], bias[col]), 0.0f);
-        float hi = fmaxf(__fadd_rn(acc[32 * q + 2 * j + 1], bias[col + 1]), 0.0f);
-        packed[j] = pack_bf16(lo, hi);
-      }
-      tmem_st16(trow + kColH + 32 * c + 16 * q, packed);
-    }
-  }
-  tmem_wait_st();
-}
-
-// The row's features (the feature map of rs_features, same arithmetic) as
-// BF16 pairs straight into the layer-1 A tile: pair 0 = (x/n, y/n), pairs
-// 1 + 2r = ((rock x - x)/n, (rock y - y)/n), 2 + 2r = (clamp(c_r)/3, sampled_r),
-// zero beyond 1 + 2m. Fully unrolled, so nothing goes through local memory.
 // The BF16 feature pairs that depend on one rock, tabulated per CTA with the
 // arithmetic of rs_features: fdxy[(dx + 31) * 63 + dy + 31] for the offset
 // pair and fcs[(c + 3) * 2 + sampled] for the counter/sampled pair.
@@ -221,6 +52,10 @@ __device__ __forceinline__ void build_feature_tables(uint32_t* fdxy, uint32_t* f
   for (int i = threadIdx.x; i < 14; i += blockDim.x) fcs[i] = pack_bf16((float)(i / 2 - 3) * third, (i & 1) ? 1.0f : 0.0f);
 }
 
+// The row's features (the feature map of rs_features, same arithmetic) as
+// BF16 pairs straight into the layer-1 A tile: pair 0 = (x/n, y/n), pairs
+// 1 + 2r = ((rock x - x)/n, (rock y - y)/n), 2 + 2r = (clamp(c_r)/3, sampled_r),
+// zero beyond 1 + 2m. Fully unrolled, so nothing goes through local memory.
 __device__ __forceinline__ void write_features(uint8_t* xs, int row, int n, int m, const int* rock_xy, uint32_t pos,
                                                uint32_t sampled, const uint32_t (&h)[8], const uint32_t* fdxy,
                                                const uint32_t* fcs) {
@@ -302,51 +137,17 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
   const int tid = threadIdx.x, warp = tid >> 5, half = tid >> 7;
   const bool owner = half == 0;  // the thread that holds the row's scenario
   load_rs_consts(S.c, gm);
-  {
-    const uint4* w1 = reinterpret_cast<const uint4*>(policy + kPolW1);
-    const uint4* w2 = reinterpret_cast<const uint4*>(policy + kPolW2);
-    const uint4* w3 = reinterpret_cast<const uint4*>(policy + kPolW3);
-    for (int i = tid; i < kMlpHid * kMlpIn / 8; i += kThreads) {
-      const int n = i / (kMlpIn / 8), c = i % (kMlpIn / 8);
-      *reinterpret_cast<uint4*>(S.w1 + kmajor_off(n, 8 * c, kMlpIn)) = w1[i];
-    }
-    for (int i = tid; i < kMlpHid * kMlpHid / 8; i += kThreads) {
-      const int n = i / (kMlpHid / 8), c = i % (kMlpHid / 8);
-      *reinterpret_cast<uint4*>(S.w2 + kmajor_off(n, 8 * c, kMlpHid)) = w2[i];
-    }
-    for (int i = tid; i < kMlpOut * kMlpHid / 8; i += kThreads) {
-      const int n = i / (kMlpHid / 8), c = i % (kMlpHid / 8);
-      *reinterpret_cast<uint4*>(S.w3 + kmajor_off(n, 8 * c, kMlpHid)) = w3[i];
-    }
-    const float* b1 = reinterpret_cast<const float*>(policy + kPolB1);
-    const float* b2 = reinterpret_cast<const float*>(policy + kPolB2);
-    const float* b3 = reinterpret_cast<const float*>(policy + kPolB3);
-    for (int i = tid; i < kMlpHid; i += kThreads) {
-      S.b1[i] = b1[i];
-      S.b2[i] = b2[i];
-    }
-    for (int i = tid; i < kMlpOut; i += kThreads) S.b3[i] = b3[i];
-  }
+  load_weights(S.W, policy);
   build_feature_tables(S.fdxy, S.fcs, gm->n);
   const uint32_t mbar = smem_u32(&S.mbar);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  setup(mbar, smem_u32(&S.tmem_base));
   fence_async_smem();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = S.tmem_base;
   const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
-  const uint32_t sx = smem_u32(S.x), sw1 = smem_u32(S.w1), sw2 = smem_u32(S.w2), sw3 = smem_u32(S.w3);
-  constexpr uint32_t kId1 = idesc_bf16(kRows, kMlpHid), kId3 = idesc_bf16(kRows, kMlpOut);
+  const uint32_t sx = smem_u32(S.x);
 
   const RSModel<1> M = make_rs<1>(gm, &S.c, plan_step);
   const int na = gm->num_actions;
@@ -458,88 +259,27 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
     }
     fence_async_smem();
     if (!__syncthreads_or((alive || (owner && pst != 4)) ? 1 : 0)) break;
-    // layer 1: D = X W1^T, four K = 16 steps
-    if (tid == 0) {
-      fence_after_sync();
-#pragma unroll
-      for (int k = 0; k < kMlpIn / 16; ++k)
-        mma_ss(tmem + kColD, smem_desc(sx + 256 * k, 128, (kMlpIn / 8) * 128),
-               smem_desc(sw1 + 256 * k, 128, (kMlpIn / 8) * 128), kId1, k > 0);
-      mma_commit(mbar);
-    }
-    // while layer 1 runs: the row's allowed actions, the heuristic's action
-    // and the next fetch stage
-    if (owner) {
-      if (alive) {
-        allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << na);
-        heur = M.policy(s, pm);
+    // the network; while layer 1 runs: the row's allowed actions, the
+    // heuristic's action and the next fetch stage
+    const bool ok = run_layers(S.W, sx, tmem, trow, mbar, phase, half, [&]() {
+      if (owner) {
+        if (alive) {
+          allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << na);
+          heur = M.policy(s, pm);
+        }
+        advance();
       }
-      advance();
-    }
-    if (!__syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0)) {
+    });
+    if (!ok) {
       failed = true;
       break;
     }
-    phase ^= 1u;
-    fence_after_sync();
-    hidden_epilogue(trow, S.b1, half);
-    fence_before_sync();
-    __syncthreads();
-    // layer 2: D = H1 W2^T, A from tensor memory, sixteen K = 16 steps
-    if (tid == 0) {
-      fence_after_sync();
-#pragma unroll 4
-      for (int k = 0; k < kMlpHid / 16; ++k)
-        mma_ts(tmem + kColD, tmem + kColH + 8 * k, smem_desc(sw2 + 256 * k, 128, (kMlpHid / 8) * 128), kId1, k > 0);
-      mma_commit(mbar);
-    }
-    if (!__syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0)) {
-      failed = true;
-      break;
-    }
-    phase ^= 1u;
-    fence_after_sync();
-    hidden_epilogue(trow, S.b2, half);
-    fence_before_sync();
-    __syncthreads();
-    // layer 3: logits = H2 W3^T
-    if (tid == 0) {
-      fence_after_sync();
-#pragma unroll 4
-      for (int k = 0; k < kMlpHid / 16; ++k)
-        mma_ts(tmem + kColL, tmem + kColH + 8 * k, smem_desc(sw3 + 256 * k, 128, (kMlpHid / 8) * 128), kId3, k > 0);
-      mma_commit(mbar);
-    }
-    if (!__syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0)) {
-      failed = true;
-      break;
-    }
-    phase ^= 1u;
-    fence_after_sync();
     float lg[32];
     if (owner) tmem_ld32(trow + kColL, lg);
     fence_before_sync();
     if (alive) {
       // argmax over the allowed actions and defer (column na), lowest index on ties
-      float xv[32];
-      int xi[32];
-#pragma unroll
-      for (int col = 0; col < 32; ++col) {
-        const bool ok = col <= na && ((allow >> col) & 1u);
-        xv[col] = ok ? __fadd_rn(lg[col], S.b3[col]) : 0.0f;
-        xi[col] = ok ? col : 0x7FFF;
-      }
-      // pairwise tournament; the right entry wins only if strictly larger,
-      // so the lowest index wins ties
-#pragma unroll
-      for (int w = 16; w >= 1; w >>= 1)
-#pragma unroll
-        for (int k = 0; k < w; ++k) {
-          const bool take = xi[k + w] != 0x7FFF && (xi[k] == 0x7FFF || xv[k + w] > xv[k]);
-          xv[k] = take ? xv[k + w] : xv[k];
-          xi[k] = take ? xi[k + w] : xi[k];
-        }
-      const int best = xi[0];
+      const int best = masked_argmax(lg, S.W.b3, allow, na);
       const int a = best == na ? heur : best;
       if (!kExpand && src.log) src.log[(size_t)item * M.D + (t - t0)] = a;
       uint64_t key;
@@ -560,17 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
       }
     }
   }
-  if (failed) {
-    // a layer did not complete in time: report, give the MMAs in flight one
-    // more bounded wait, then free the tensor memory
-    if (tid == 0) report(work, kStatusTimeout);
-    mbar_wait(mbar, phase);
-  }
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  teardown(tmem, mbar, phase, failed, work);
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
@@ -644,11 +374,17 @@ extern "C" {
 dsp_status dsp_features(const dsp_model* m, const uint32_t* block, int32_t cap, int32_t count, const int8_t* hist,
                         float* out, void* stream) {
   if (!m) return fail(DSP_E_INVALID, "dsp_features: model is NULL");
-  if (m->host->kind != DSP_MODEL_GRID) return fail(DSP_E_UNSUPPORTED, "dsp_features: one-robot Rock Sample only");
-  if (count < 0 || cap < count || (count > 0 && (!block || !hist || !out)))
+  if (m->host->kind == DSP_MODEL_MULTIGRID)
+    return fail(DSP_E_UNSUPPORTED, "dsp_features: one-robot Rock Sample or the car");
+  const bool car = m->host->kind == DSP_MODEL_CAR;
+  if (count < 0 || cap < count || (count > 0 && (!block || (!car && !hist) || !out)))
     return fail(DSP_E_INVALID, "dsp_features: bad buffers");
   if (((uintptr_t)out & 15) != 0) return fail(DSP_E_INVALID, "dsp_features: out must be 16-byte aligned");
   if (count == 0) return DSP_OK;
+  if (car) {
+    cudaError_t e = launch_car_features(m, block, cap, count, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_features");
+  }
   features_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m->dmodel, block, cap, count, hist, out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_features");
@@ -660,11 +396,12 @@ dsp_status dsp_set_policy(dsp_model* m, const dsp_mlp* mlp) {
     m->policy_on = false;
     return DSP_OK;
   }
-  if (m->host->kind != DSP_MODEL_GRID)
-    return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: the learned policy serves one-robot Rock Sample");
+  if (m->host->kind == DSP_MODEL_MULTIGRID)
+    return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: the learned policy serves one-robot Rock Sample and the car");
   if (m->host->num_actions + 1 > kMlpOut)
     return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: more than 31 actions (the network's last used logit defers)");
-  if (m->host->m > 15) return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: features hold 15 rocks");
+  if (m->host->kind == DSP_MODEL_GRID && m->host->m > 15)
+    return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: features hold 15 rocks");
   cudaError_t e = cudaSuccess;
   if (m->policy == nullptr) e = cudaMalloc(&m->policy, kPolBytes);
   float* master = nullptr;
@@ -708,7 +445,11 @@ dsp_status dsp_rollout_logged(const dsp_model* m, const uint32_t* block, int32_t
     src.value = value;
     src.log = actions;
     src.next = counter;
-    e = launch_mlp<false>(m->dmodel, m->dwork, (const uint8_t*)m->policy, src, m->plan_step, m->num_sms, count, st);
+    if (m->host->kind == DSP_MODEL_CAR)
+      e = launch_car_rollout_logged(m, block, cap, count, start_depth, value, actions, counter, st);
+    else
+      e = launch_mlp<false>(m->dmodel, m->dwork, (const uint8_t*)m->policy, src, m->plan_step, m->num_sms, count,
+                            st);
   }
   if (counter) cudaFreeAsync(counter, st);
   return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_rollout_logged");
