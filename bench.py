@@ -261,9 +261,10 @@ def learned_step(_dsp, batch, m, cfg, jobs, seconds):
     a learned-policy expansion of the first 256 jobs."""
     import torch
     from paper_1802_06215_b300 import learn
-    path = os.path.join(ROOT, "paper_1802_06215_b300", "weights", "rs15_15_pi0.npz")
+    car = cfg.kind == inputs.CAR
+    path = os.path.join(ROOT, "paper_1802_06215_b300", "weights", "car50_pi0.npz" if car else "rs15_15_pi0.npz")
     h, meta = learn.load_weights(path)
-    roots = learn.eval_roots(cfg, [9000, 9001], 3, 0.05)
+    roots = learn.car_roots(cfg, 6, 9000) if car else learn.eval_roots(cfg, [9000, 9001], 3, 0.05)
     cmp_ = learn.compare(cfg, h, roots, seconds)
     sub = batch.JobBatch(m, jobs[:256])
     _dsp.dsp_set_policy(m.h, h)
@@ -283,13 +284,17 @@ def learned_step(_dsp, batch, m, cfg, jobs, seconds):
     na = m.num_actions
     flop = 2 * (64 * 256 + 256 * 256 + 256 * (na + 1))
     tflops = steps * flop / (kms / 1000.0) / 1e12
+    kname = ("car_expand_kernel + car_rollout_tc_kernel (learned-policy expansion of 256 jobs; tcgen05.mma BF16, "
+             "TMEM accumulators)" if car else
+             "rs_group_kernel + rs_rollout_tc_kernel (learned-policy expansion of 256 jobs; tcgen05.mma BF16, TMEM "
+             "accumulators)")
     peak = MEASURED.get("bf16_tflops")
     cmp_["weights"] = os.path.relpath(path, ROOT)
     cmp_["tensor_roofline"] = {
         "bound": "tensor", "achieved": tflops, "unit": "TFLOP/s", "peak": peak,
         "frac": tflops / peak if peak else None, "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)",
         "flop_per_scenario_step": flop, "scenario_steps": steps / 3, "kernel_ms_per_launch": kms / max(calls, 1),
-        "kernel": "rs_group_kernel + rs_rollout_tc_kernel (learned-policy expansion of 256 jobs; tcgen05.mma BF16, TMEM accumulators)"}
+        "kernel": kname}
     return cmp_
 
 
@@ -427,7 +432,7 @@ def run_ours(args, rank, world):
     clocks = clk.summary()
     planning = None if args.no_plan else planning_step(_dsp, m, cfg, plan)
     learned = None
-    if not args.no_learned and args.workload == "rs15_15":
+    if not args.no_learned and args.workload in ("rs15_15", "car50"):
         learned = learned_step(_dsp, batch, m, cfg, jobs, plan[1])
     cpu = None
     ops_per_step = None

@@ -464,6 +464,183 @@ def policy_iteration(cfg, iterations=4, n_random=60000, n_onpolicy=4000, Kq=64, 
     return policy, hist_log
 
 
+# ---------------------------------------------------------------- the car ----
+
+def car_heuristic_action(cfg, block):
+    """The car's hand-written default policy on a state block: Decelerate (2)
+    when a pedestrian is within 4 m ahead in the 2 m corridor, else Accelerate
+    (0) below 3 m/s, else Maintain (1)."""
+    P = cfg.P
+    s = block[0].view(np.float32)
+    v = (block[1] & 0xFF).astype(np.int64)
+    px = block[4:4 + P].view(np.float32)
+    py = block[4 + P:4 + 2 * P].view(np.float32)
+    cx = np.float32(-10.0) + s
+    ex = px - cx[None, :]
+    ey = py - np.float32(20.0)
+    danger = ((ex > 0) & (ex <= 4) & (ey >= -1) & (ey <= 1)).any(axis=0)
+    return np.where(danger, 2, np.where(v < 3, 0, 1)).astype(np.int32)
+
+
+def car_states(cfg, count, rng):
+    """Car states spread over the task: s uniform on [0, 58) m, speed uniform
+    on 0..3, pedestrians uniform on the 40 x 40 m region, goals drawn per
+    scenario later; depth uniform in 0..10."""
+    b = inputs.car_block(cfg, count, rng)
+    b[0] = rng.uniform(0.0, 58.0, count).astype(np.float32).view(np.uint32)
+    depth = rng.integers(0, 11, count).astype(np.int32)
+    return b, depth
+
+
+def car_belief_block(cfg, state_col, Kq, rng):
+    """Kq scenarios of one car state: position, speed and pedestrian positions
+    as observed, hidden goals drawn uniformly (the belief over them)."""
+    P = cfg.P
+    s = float(state_col[0:1].view(np.float32)[0])
+    v = int(state_col[1] & 0xFF)
+    base = (state_col[4:4 + P].view(np.float32).astype(np.float64), state_col[4 + P:4 + 2 * P].view(np.float32)
+            .astype(np.float64))
+    b = inputs.car_block(cfg, Kq, rng, s=s, v=v, base=base, jitter=0.0,
+                         scen=rng.choice(cfg.K, Kq, replace=False))
+    b[0] = state_col[0]
+    b[4:4 + 2 * P] = state_col[4:4 + 2 * P, None]
+    return b
+
+
+def car_q_labels(model, cfg, block, depth, rng, Kq=64, chunk=1024, thr=2.0):
+    """Conservative greedy labels for car states, as q_labels: Q(s, a) from one
+    leaf expansion over Kq goal-belief scenarios (rollouts with the model's
+    current default policy); label 3 (defer) unless the best action beats the
+    heuristic's by more than thr."""
+    n = block.shape[1]
+    labels = np.zeros(n, np.int32)
+    ha = car_heuristic_action(cfg, block)
+    na = model.num_actions
+    for s0 in range(0, n, chunk):
+        jobs = []
+        for i in range(s0, min(n, s0 + chunk)):
+            b = car_belief_block(cfg, block[:, i], Kq, rng)
+            jobs.append(inputs.Job(parent=b, idx=np.arange(Kq, dtype=np.uint16), last_action=-1, depth=int(depth[i]),
+                                   hist=np.zeros(32, np.int8)))
+        jb = batch.JobBatch(model, jobs)
+        jb.run()
+        for k, r in enumerate(jb.all_results()):
+            i = s0 + k
+            q = np.zeros(na)
+            for a in range(na):
+                nc = int(r["child_count"][a])
+                q[a] = (float(np.sum(r["rew"][a][:nc], dtype=np.float64)) +
+                        cfg.gamma * float(np.sum(r["l"][a][:nc], dtype=np.float64))) / (2.0 ** 32 * Kq)
+            best = int(np.argmax(q))
+            labels[i] = best if q[best] - q[ha[i]] > thr else na
+    return labels
+
+
+def car_features(model, block):
+    import torch
+    n = block.shape[1]
+    b = torch.as_tensor(np.ascontiguousarray(block).view(np.int32), device="cuda")
+    f = torch.empty((n, 64), dtype=torch.float32, device="cuda")
+    _dsp.dsp_features(model.h, b.data_ptr(), n, n, 0, f.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return f.cpu().numpy()
+
+
+def car_on_policy_states(model, cfg, block, depth, rng, per_rollout=4):
+    """States the model's learned car policy visits: logged rollouts from the
+    given states, replayed with dsp_step, per_rollout visited states each."""
+    import torch
+    out_cols, out_depth = [], []
+    for d0 in np.unique(depth):
+        sel = np.nonzero(depth == d0)[0]
+        cur = np.ascontiguousarray(block[:, sel])
+        n = len(sel)
+        bd = torch.as_tensor(cur.view(np.int32), device="cuda")
+        val = torch.empty(n, dtype=torch.float32, device="cuda")
+        act = torch.full((n, cfg.D), -1, dtype=torch.int32, device="cuda")
+        _dsp.dsp_rollout_logged(model.h, bd.data_ptr(), n, n, 0, int(d0), val.data_ptr(), act.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+        acts = act.cpu().numpy()
+        visited = [[] for _ in range(n)]
+        for t in range(cfg.D - int(d0)):
+            live = np.nonzero(acts[:, t] >= 0)[0]
+            if len(live) == 0:
+                break
+            for i in live:
+                visited[i].append(t)
+            nxt, _, _ = model.step(np.ascontiguousarray(cur[:, live]), acts[live, t], int(d0) + t)
+            cur = cur.copy()
+            for col, i in enumerate(live):
+                if len(visited[i]) and rng.random() < per_rollout / max(1, cfg.D - int(d0)):
+                    out_cols.append(cur[:, i].copy())
+                    out_depth.append(int(d0) + t)
+            cur[:, live] = nxt
+    if not out_cols:
+        return np.zeros((block.shape[0], 0), np.uint32), np.zeros(0, np.int32)
+    return np.stack(out_cols, axis=1), np.array(out_depth, np.int32)
+
+
+def car_mean_value(model, cfg, block, depth, rng):
+    vals = []
+    for d0 in np.unique(depth):
+        sel = np.nonzero(depth == d0)[0]
+        b = np.ascontiguousarray(block[:, sel]).copy()
+        # hidden goals as the belief draws them
+        b[4 + 2 * cfg.P:] = inputs.car_block(cfg, len(sel), rng)[4 + 2 * cfg.P:]
+        vals.append(model.rollout(b, None, int(d0)))
+    return float(np.mean(np.concatenate(vals)))
+
+
+def car_policy_iteration(cfg, iterations=3, n_random=12000, n_onpolicy=2000, Kq=64, epochs=30, seed=0,
+                         log=print):
+    """Approximate policy iteration for the car (as policy_iteration)."""
+    rng = np.random.default_rng([seed, 0xCA2])
+    model = batch.Model(cfg)
+    policy = None
+    Xs, Ys, hist_log = [], [], []
+    ev_b, ev_d = car_states(cfg, 3000, np.random.default_rng([seed, 0xE7A2]))
+    base = {"random_states": car_mean_value(model, cfg, ev_b, ev_d, np.random.default_rng(1))}
+    log(json.dumps({"heuristic_value": base}))
+    for it in range(iterations):
+        t0 = time.time()
+        b, d = car_states(cfg, n_random, rng)
+        if policy is not None:
+            sb, sd = car_states(cfg, n_onpolicy, rng)
+            ob, od = car_on_policy_states(model, cfg, sb, sd, rng)
+            b, d = np.concatenate([b, ob], axis=1), np.concatenate([d, od])
+        y = car_q_labels(model, cfg, b, d, rng, Kq=Kq)
+        X = car_features(model, b)
+        Xs.append(X)
+        Ys.append(y)
+        t1 = time.time()
+        h, acc = train(np.concatenate(Xs), np.concatenate(Ys), model.num_actions + 1, epochs=epochs, seed=seed + it,
+                       log=lambda *_: None)
+        if policy is not None:
+            _dsp.dsp_mlp_destroy(policy)
+        policy = h
+        _dsp.dsp_set_policy(model.h, policy)
+        val = {"random_states": car_mean_value(model, cfg, ev_b, ev_d, np.random.default_rng(1))}
+        rec = {"iteration": it + 1, "states": int(len(y)), "pairs": int(sum(len(v) for v in Ys)),
+               "override_frac": float(np.mean(y != model.num_actions)), "val_accuracy": acc,
+               "label_seconds": t1 - t0, "train_seconds": time.time() - t1, "learned_value": val,
+               "heuristic_value": base}
+        hist_log.append(rec)
+        log(json.dumps(rec))
+    model.close()
+    return policy, hist_log
+
+
+def car_roots(cfg, count, seed):
+    """Planning roots of the car: at the start of the path, at rest, each with
+    its own pedestrian layout and K goal-belief scenarios."""
+    roots = []
+    for k in range(count):
+        rng = np.random.default_rng([seed, k])
+        base = (rng.uniform(0, 40, cfg.P), rng.uniform(0, 40, cfg.P))
+        roots.append((inputs.car_block(cfg, cfg.K, rng, s=0.0, v=0, base=base, jitter=0.0), None))
+    return roots
+
+
 def compare(cfg, policy, roots, seconds, threads=4):
     """Root gap u - l after one planning step of `seconds` from each root
     belief, heuristic pi0 then learned pi0, on the same random streams."""
@@ -514,13 +691,13 @@ def eval_roots(cfg, world_seeds, steps, seconds, threads=4):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["train", "api", "compare"])
+    ap.add_argument("cmd", choices=["train", "api", "compare", "api-car", "compare-car"])
     ap.add_argument("--worlds", type=int, default=32)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--plan-seconds", type=float, default=0.1)
     ap.add_argument("--iterations", type=int, default=2, help="harvest/train rounds (later ones roll out the net)")
     ap.add_argument("--epochs", type=int, default=40)
-    ap.add_argument("--weights", default="paper_1802_06215_b300/weights/rs15_15_pi0.npz")
+    ap.add_argument("--weights", default=None, help="weights file (default: the shipped one of the task)")
     ap.add_argument("--out", default=None)
     ap.add_argument("--eval-worlds", type=int, default=8)
     ap.add_argument("--eval-steps", type=int, default=8)
@@ -529,9 +706,21 @@ def main(argv=None):
     from . import build
     build.build()
     cfg = inputs.rs15_15()
+    if a.cmd == "api-car":
+        ccfg = inputs.car50()
+        policy, hl = car_policy_iteration(ccfg, iterations=a.iterations, epochs=a.epochs)
+        save_weights(a.out or "paper_1802_06215_b300/weights/car50_pi0.npz", policy,
+                     {"config": "car50", "method": "approximate policy iteration", "iterations": hl})
+        return
+    if a.cmd == "compare-car":
+        ccfg = inputs.car50()
+        policy, meta = load_weights(a.weights or "paper_1802_06215_b300/weights/car50_pi0.npz")
+        print(json.dumps(compare(ccfg, policy, car_roots(ccfg, a.eval_worlds, 9000), a.eval_seconds)))
+        return
     if a.cmd == "api":
         policy, hl = policy_iteration(cfg, iterations=a.iterations, epochs=a.epochs)
-        save_weights(a.out or a.weights, policy, {"config": "rs15_15", "method": "approximate policy iteration",
+        save_weights(a.out or a.weights or "paper_1802_06215_b300/weights/rs15_15_pi0.npz", policy,
+                     {"config": "rs15_15", "method": "approximate policy iteration",
                                                   "iterations": hl})
     elif a.cmd == "train":
         policy, init, meta = None, None, {"iterations": []}
@@ -549,9 +738,9 @@ def main(argv=None):
                 _dsp.dsp_mlp_destroy(policy)
             policy = h
         meta.update({"config": "rs15_15", "steps": a.steps, "plan_seconds": a.plan_seconds, "epochs": a.epochs})
-        save_weights(a.out or a.weights, policy, meta)
+        save_weights(a.out or a.weights or "paper_1802_06215_b300/weights/rs15_15_pi0.npz", policy, meta)
     else:
-        policy, meta = load_weights(a.weights)
+        policy, meta = load_weights(a.weights or "paper_1802_06215_b300/weights/rs15_15_pi0.npz")
         roots = eval_roots(cfg, range(9000, 9000 + a.eval_worlds), a.eval_steps, 0.05)
         print(json.dumps(compare(cfg, policy, roots, a.eval_seconds)))
 

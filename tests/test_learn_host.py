@@ -50,3 +50,23 @@ def test_belief_update_is_bayes():
     b.update(1, 0, b.pos + 1, 0)   # a move changes nothing but the position
     assert b.pos == learn.start_word(cfg) + 1 and np.count_nonzero(b.hist) == 0
     assert math.isclose(learn.counter_posterior(2, 0.8), 0.64 / 0.68)
+
+
+def test_car_heuristic_action_matches_oracle_policy():
+    cfg = I.car50()
+    b, _ = learn.car_states(cfg, 800, np.random.default_rng(3))
+    o = np.asarray(oracle.Model(cfg).policy(b, None)).ravel()
+    assert np.array_equal(o, learn.car_heuristic_action(cfg, b))
+
+
+def test_car_belief_block_keeps_the_observed_state():
+    cfg = I.car50()
+    rng = np.random.default_rng(4)
+    b, _ = learn.car_states(cfg, 5, rng)
+    bb = learn.car_belief_block(cfg, b[:, 2], 32, rng)
+    P = cfg.P
+    assert np.all(bb[0] == b[0, 2]) and np.all((bb[1] & 0xFF) == (b[1, 2] & 0xFF))
+    assert np.all(bb[4:4 + 2 * P] == b[4:4 + 2 * P, 2:3])
+    assert len(set(bb[2].tolist())) == 32  # distinct scenario streams
+    goals = bb[4 + 2 * P:]
+    assert len({tuple(goals[:, k]) for k in range(32)}) > 1  # goals are drawn per scenario

@@ -69,3 +69,32 @@ def test_policy_iteration_from_scratch(env):
     assert last["learned_value"]["start"] > last["heuristic_value"]["start"] + 1.0, hl
     assert last["learned_value"]["random_states"] > last["heuristic_value"]["random_states"], hl
     _dsp.dsp_mlp_destroy(h)
+
+
+CAR_WEIGHTS = os.path.join(os.path.dirname(__file__), "..", "paper_1802_06215_b300", "weights", "car50_pi0.npz")
+
+
+def test_trained_car_policy_raises_rollout_values(env):
+    _dsp, batch, learn = env
+    cfg = I.car50()
+    m = batch.Model(cfg)
+    b, d = learn.car_states(cfg, 2000, np.random.default_rng(21))
+    heur = learn.car_mean_value(m, cfg, b, d, np.random.default_rng(2))
+    h, _ = learn.load_weights(CAR_WEIGHTS)
+    _dsp.dsp_set_policy(m.h, h)
+    lrn = learn.car_mean_value(m, cfg, b, d, np.random.default_rng(2))
+    _, status = m.counters()
+    assert status == 0
+    assert lrn > heur + 10.0, (lrn, heur)
+    _dsp.dsp_mlp_destroy(h)
+    m.close()
+
+
+def test_trained_car_policy_tightens_root_gap(env):
+    _dsp, batch, learn = env
+    cfg = I.car50()
+    h, _ = learn.load_weights(CAR_WEIGHTS)
+    out = learn.compare(cfg, h, learn.car_roots(cfg, 3, 9100), 0.1)
+    assert out["learned"]["mean_root_gap"] < out["heuristic"]["mean_root_gap"], out
+    assert out["learned"]["mean_root_l"] > out["heuristic"]["mean_root_l"], out
+    _dsp.dsp_mlp_destroy(h)
