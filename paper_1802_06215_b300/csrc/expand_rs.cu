@@ -573,14 +573,25 @@ cudaError_t launch_two_phase(const DevModel* gm, DevWork* work, const dsp_leaf_j
 
 // ------------------------------------------------------------ job queue ---
 // Persistent expansion fed by host threads through a ring in mapped pinned
-// host memory (ticket t lives in slot t % cap: seq = t + 1 once its job is
-// published, seq = t + cap once the slot may take ticket t + cap; done = t + 1
-// once its results are written). A CTA claims the next ticket only after its
-// job is published, so no ticket is ever held without a job; then it runs
-// phase A and phase B of that job itself on its own scratch slot. Every wait
-// is bounded by %globaltimer: a CTA that finds no job for idle_ns (or finds
-// the ring closed and empty) exits, and the host relaunches the kernel when
-// more jobs arrive.
+// host memory. Ticket t lives in slot t % cap:
+//  - seq = t + 1 once its job is published, seq = t + cap once the slot may
+//    take ticket t + cap;
+//  - done = t + 1 once its results are written.
+// A CTA claims the next ticket only after its job is published, so no ticket
+// is ever held without a job.
+//
+// Work is shared across the whole grid:
+//  - The CTA that claims a job runs phase A into the slot's item list and
+//    publishes the job's rollout chunks in the slot's claim word: the ticket's
+//    low 32 bits, and the next chunk.
+//  - Any warp of any CTA takes chunks of any published job by compare-and-swap
+//    on that word, which succeeds only while the job it read is still the
+//    slot's.
+//  - The warp that finishes a job's last chunk closes the word (chunk field
+//    all ones), writes done and frees the slot.
+// No CTA waits on another. A CTA that finds neither a job nor a chunk for
+// idle_ns (or finds the ring closed) exits, and the host relaunches the
+// kernel when more jobs arrive.
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -592,8 +603,60 @@ __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long
   asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr unsigned int kClosed = 0xFFFFFFFFu;
+
+// The job in `slot` is finished: close its claim word, publish done, free the slot.
+__device__ __forceinline__ void queue_complete(const QueueRing& ring, int slot, unsigned long long ticket) {
+  atomicExch(&ring.share[slot].claim, ((ticket & 0xFFFFFFFFull) << 32) | kClosed);
+  __threadfence_system();
+  st_release_sys(ring.done + slot, ticket + 1);
+  st_release_sys(ring.seq + slot, ticket + (unsigned long long)ring.cap);
+}
+
+// One warp looks for rollout chunks of any published job and claims up to the
+// job's grain of them (consecutive). Returns the slot (or -1), the first chunk
+// and the count, the same in every lane.
+__device__ __forceinline__ int queue_claim_chunk(const QueueRing& ring, unsigned int& chunk, unsigned int& count) {
+  const int lane = threadIdx.x & 31;
+  const int start = (int)((blockIdx.x * 7 + (threadIdx.x >> 5)) % (unsigned)ring.cap);
+  for (int base = 0; base < ring.cap; base += 32) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      const int s = (start + base + lane) % ring.cap;
+      bool can = false;
+      unsigned long long c = 0;
+      if (base + lane < ring.cap) {
+        c = ld_acquire_gpu(&ring.share[s].claim);
+        const unsigned int idx = (unsigned int)(c & 0xFFFFFFFFull);
+        can = idx != kClosed && idx < *(volatile unsigned int*)&ring.share[s].nchunks;
+      }
+      const unsigned int ready = __ballot_sync(0xFFFFFFFFu, can);
+      if (ready == 0u) break;
+      const int leader = __ffs(ready) - 1;
+      unsigned int got = 0;
+      if (lane == leader) {
+        const unsigned int idx = (unsigned int)(c & 0xFFFFFFFFull);
+        const unsigned int n = *(volatile unsigned int*)&ring.share[s].nchunks;
+        const unsigned int g = min(*(volatile unsigned int*)&ring.share[s].grain, n - idx);
+        got = atomicCAS(&ring.share[s].claim, c, c + g) == c ? g : 0u;
+      }
+      got = __shfl_sync(0xFFFFFFFFu, got, leader);
+      if (got) {
+        count = got;
+        chunk = __shfl_sync(0xFFFFFFFFu, (unsigned int)(c & 0xFFFFFFFFull), leader);
+        return __shfl_sync(0xFFFFFFFFu, s, leader);
+      }
+    }
+  }
+  return -1;
 }
 
 template <int R>
@@ -604,62 +667,85 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
                                                              unsigned long long idle_ns) {
   __shared__ RSGroupSmem S;
   __shared__ long long s_ticket;
-  __shared__ int s_chunk;
+  __shared__ int s_work, s_exit;
   load_rs_consts(S.c, gm);
   const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
   const int tid = threadIdx.x, lane = tid & 31;
-  dsp_leaf_job* myjob = jcopy + blockIdx.x;
-  unsigned long long steps = 0;
+  unsigned long long steps = 0, last_work = global_ns();
   __syncthreads();
   while (true) {
+    // a new job from the ring, if one is published (no waiting)
     if (tid == 0) {
       long long ticket = -1;
-      unsigned long long deadline = global_ns() + idle_ns;
-      while (true) {
-        unsigned long long h = *(volatile unsigned long long*)head;
-        unsigned long long s = ld_acquire_sys(ring.seq + (h % ring.cap));
-        if (s == h + 1) {
-          if (atomicCAS(head, h, h + 1) == h) {
-            ticket = (long long)h;
-            break;
-          }
-          continue;
-        }
-        if (*(volatile unsigned int*)ring.close != 0u || global_ns() > deadline) break;
-        __nanosleep(500);
-      }
-      s_ticket = ticket;
-      if (ticket >= 0) {
-        const int slot = (int)(ticket % ring.cap);
+      const unsigned long long h = *(volatile unsigned long long*)head;
+      if (ld_acquire_sys(ring.seq + (h % ring.cap)) == h + 1 && atomicCAS(head, h, h + 1) == h) {
+        ticket = (long long)h;
+        const int slot = (int)(h % ring.cap);
         const volatile uint32_t* src = (const volatile uint32_t*)(ring.jobs + slot);
         uint32_t* dst = (uint32_t*)&S.J;
         for (int w = 0; w < (int)(sizeof(dsp_leaf_job) / 4); ++w) dst[w] = src[w];
-        *myjob = S.J;
-        st_release_sys(ring.seq + slot, (unsigned long long)ticket + ring.cap);
+        jcopy[slot] = S.J;
       }
+      s_ticket = ticket;
+      s_work = 0;
     }
     __syncthreads();
     const long long ticket = s_ticket;
-    if (ticket < 0) break;
-    const int n = S.J.n_scen;
-    if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
-      Items<R> items{scratch + (size_t)blockIdx.x * slot_words, (long long)n * S.J.n_actions};
-      __threadfence_block();
-      group_job<R>(S, M, 0, 0, items, work, steps);
-      if (tid == 0) s_chunk = 0;
+    if (ticket >= 0) {
+      const int slot = (int)(ticket % ring.cap);
+      const int n = S.J.n_scen;
+      long long nchunks = 0;
+      if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
+        Items<R> items{scratch + (size_t)slot * slot_words, (long long)n * S.J.n_actions};
+        group_job<R>(S, M, 0, 0, items, work, steps);
+        nchunks = (items.total + 31) >> 5;
+      }
+      __threadfence();  // every thread's phase-A results, before the job is published
       __syncthreads();
-      const long long nchunks = (items.total + 31) >> 5;
-      while (true) {
-        int chunk = 0;
-        if (lane == 0) chunk = atomicAdd(&s_chunk, 1);
-        chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
-        if (chunk >= nchunks) break;
-        rs_rollout_chunk<R>(M, myjob, items, chunk, steps);
+      if (tid == 0) {
+        if (nchunks == 0) {
+          queue_complete(ring, slot, (unsigned long long)ticket);
+        } else {
+          QueueShare& sh = ring.share[slot];
+          sh.ticket = (unsigned long long)ticket;
+          sh.nchunks = (unsigned int)nchunks;
+          sh.remaining = (unsigned int)nchunks;
+          // large jobs hand out several chunks per claim, so claims do not
+          // queue up on the claim word; small ones one chunk at a time
+          sh.grain = (unsigned int)max(1LL, min(16LL, nchunks / 256));
+          __threadfence();
+          atomicExch(&sh.claim, ((unsigned long long)ticket & 0xFFFFFFFFull) << 32);
+        }
       }
     }
-    __threadfence_system();
+    // rollout chunks of any published job, warp by warp, until none is left
+    bool did = false;
+    while (true) {
+      unsigned int chunk = 0, count = 0;
+      const int slot = queue_claim_chunk(ring, chunk, count);
+      if (slot < 0) break;
+      const dsp_leaf_job* J = jcopy + slot;
+      Items<R> items{scratch + (size_t)slot * slot_words, (long long)J->n_scen * J->n_actions};
+      for (unsigned int k = 0; k < count; ++k) rs_rollout_chunk<R>(M, J, items, chunk + k, steps);
+      __threadfence();  // every lane's sums, before the chunks count as done
+      __syncwarp();
+      if (lane == 0) {
+        if (atomicSub(&ring.share[slot].remaining, count) == count)
+          queue_complete(ring, slot, *(volatile unsigned long long*)&ring.share[slot].ticket);
+      }
+      did = true;
+    }
+    if (did && lane == 0) s_work = 1;
     __syncthreads();
-    if (tid == 0) st_release_sys(ring.done + (ticket % ring.cap), (unsigned long long)ticket + 1);
+    if (tid == 0) {
+      const unsigned long long now = global_ns();
+      const bool busy = ticket >= 0 || s_work != 0;
+      if (busy) last_work = now;
+      s_exit = !busy && (*(volatile unsigned int*)ring.close != 0u || now - last_work > idle_ns);
+      if (!busy && !s_exit) __nanosleep(1000);
+    }
+    __syncthreads();
+    if (s_exit) break;
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);

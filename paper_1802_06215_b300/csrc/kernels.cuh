@@ -24,11 +24,21 @@ cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const
                                         uint32_t* item_buf, long long total_items, unsigned int* counter,
                                         const void* policy, uint32_t plan_step, int num_sms, cudaStream_t st);
 // Device view of the job ring (device addresses of mapped pinned host memory).
+// Work sharing of one ring slot's job across the grid (device memory).
+struct QueueShare {
+  unsigned long long claim;   // (ticket & 0xFFFFFFFF) << 32 | next chunk; chunk 0xFFFFFFFF: closed
+  unsigned long long ticket;  // full ticket of the published job
+  unsigned int nchunks;       // rollout chunks of 32 items
+  unsigned int remaining;     // chunks not yet finished
+  unsigned int grain;         // chunks a warp takes per claim
+  unsigned int pad;
+};
 struct QueueRing {
   unsigned long long* seq;   // [cap] t + 1: ticket t published; t + cap: slot free for ticket t + cap
   dsp_leaf_job* jobs;        // [cap]
   unsigned long long* done;  // [cap] last finished ticket + 1
   unsigned int* close;       // nonzero: exit once no job is ready
+  QueueShare* share;         // [cap] device memory
   int cap;
 };
 size_t rs_queue_slot_words(int robots, int num_actions);

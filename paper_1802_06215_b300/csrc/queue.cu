@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <thread>
+#include <vector>
 
 #include "kernels.cuh"
 #include "model.hpp"
@@ -28,8 +29,9 @@ struct dsp_queue {
   unsigned int* close = nullptr;
   dsp::QueueRing ring{};
   unsigned long long* d_head = nullptr;  // device: next ticket to consume
-  uint32_t* d_scratch = nullptr;         // device: one rollout-item slot per CTA
-  dsp_leaf_job* d_jcopy = nullptr;       // device: one job copy per CTA
+  uint32_t* d_scratch = nullptr;         // device: one rollout-item list per ring slot
+  dsp_leaf_job* d_jcopy = nullptr;       // device: one job copy per ring slot
+  dsp::QueueShare* d_share = nullptr;    // device: work sharing per ring slot
   size_t slot_words = 0;
   int grid = 0;
   unsigned long long idle_ns = 0;
@@ -142,8 +144,22 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
     e = cudaMalloc(&q->d_head, sizeof(unsigned long long));
   }
   if (e == cudaSuccess) e = cudaMemset(q->d_head, 0, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&q->d_scratch, sizeof(uint32_t) * q->slot_words * (size_t)q->grid);
-  if (e == cudaSuccess) e = cudaMalloc(&q->d_jcopy, sizeof(dsp_leaf_job) * (size_t)q->grid);
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_scratch, sizeof(uint32_t) * q->slot_words * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_jcopy, sizeof(dsp_leaf_job) * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_share, sizeof(dsp::QueueShare) * (size_t)capacity);
+  if (e == cudaSuccess) {
+    std::vector<dsp::QueueShare> init(capacity);
+    for (dsp::QueueShare& sh : init) {
+      sh.claim = 0xFFFFFFFFull;  // closed
+      sh.ticket = 0;
+      sh.nchunks = 0;
+      sh.remaining = 0;
+      sh.grain = 1;
+      sh.pad = 0;
+    }
+    e = cudaMemcpy(q->d_share, init.data(), sizeof(dsp::QueueShare) * (size_t)capacity, cudaMemcpyHostToDevice);
+    q->ring.share = q->d_share;
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     dsp_status st = cuda_fail(e, "dsp_queue_create");
@@ -235,6 +251,7 @@ void dsp_queue_destroy(dsp_queue* q) {
   if (q->d_head) cudaFree(q->d_head);
   if (q->d_scratch) cudaFree(q->d_scratch);
   if (q->d_jcopy) cudaFree(q->d_jcopy);
+  if (q->d_share) cudaFree(q->d_share);
   if (q->host) cudaFreeHost(q->host);
   delete q;
 }
