@@ -418,7 +418,8 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
       if (e == cudaSuccess && car_items) e = launch_car_rollout_mlp_items(m, djobs, ci, counters + 1, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
-      e = launch_rs_expand(m->dmodel, h->robots, m->dwork, djobs, (const long long*)dunits, dorder, n_jobs,
+      e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, m->dwork, djobs, (const long long*)dunits, dorder,
+                           n_jobs,
                            plan.total_items, items, counters, m->plan_step, m->num_sms, block_b,
                            m->policy_on ? m->policy : nullptr, st);
     }

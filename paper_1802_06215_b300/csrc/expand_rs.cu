@@ -217,7 +217,7 @@ __device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& 
   const int tid = threadIdx.x;
   const dsp_leaf_job& J = S.J;
   const int n = J.n_scen, depth = J.depth;
-  for (int p = tid; p < n; p += kBlockA) {
+  for (int p = tid; p < n; p += (int)blockDim.x) {
     RSS s = M.load(J.parent, J.parent_cap, J.idx[p]);
     if (J.last_action >= 0) {
       if (!M.terminal(s)) steps += 1;
@@ -261,7 +261,8 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
   const uint32_t lt = lanemask_lt();
   uint8_t* codes = S.code1[warp];
   const uint32_t pm_job = S.pm_job;
-  for (int a = warp; a < A; a += kWarpsA) {
+  const int nwarps = (int)(blockDim.x >> 5);
+  for (int a = warp; a < A; a += nwarps) {
     const int aa = J.first_action + a;
     int cnt[kC], first[kC], rsum[kC];  // |reward sum| <= 100 * 512 fits 32 bits
 #pragma unroll
@@ -548,14 +549,23 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
 }
 
 template <int R>
-cudaError_t launch_two_phase(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs, const long long* item_base,
-                             const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
+cudaError_t launch_two_phase(const DevModel* gm, int num_actions, DevWork* work, const dsp_leaf_job* jobs,
+                             const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st) {
   Items<R> items{item_buf, total_items};
+  // One robot: each warp expands whole actions, so the CTA takes as many warps
+  // as give every warp the same number of a job's actions (20 actions: 10
+  // warps of 2). Two robots use the full 16-warp grouping.
+  int block_a = kBlockA;
+  if (R == 1) {
+    const int na = std::max(1, num_actions);
+    const int per_warp = (na + kWarpsA - 1) / kWarpsA;
+    block_a = 32 * ((na + per_warp - 1) / per_warp);
+  }
   int per_sm_a = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, rs_group_kernel<R>, kBlockA, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, rs_group_kernel<R>, block_a, 0);
   int grid_a = std::max(1, std::min(n_jobs, std::max(1, per_sm_a) * num_sms));
-  rs_group_kernel<R><<<grid_a, kBlockA, 0, st>>>(gm, work, jobs, item_base, order, n_jobs, counters, plan_step,
+  rs_group_kernel<R><<<grid_a, block_a, 0, st>>>(gm, work, jobs, item_base, order, n_jobs, counters, plan_step,
                                                   items);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -780,14 +790,14 @@ cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, Queue
   return cudaGetLastError();
 }
 
-cudaError_t launch_rs_expand(const DevModel* gm, int robots, DevWork* work, const dsp_leaf_job* jobs,
-                             const long long* item_base, const int* order, int n_jobs, long long total_items,
-                             uint32_t* item_buf, unsigned int* counters, uint32_t plan_step, int num_sms,
-                             int block_b, const void* policy, cudaStream_t st) {
+cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, DevWork* work,
+                             const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
+                             long long total_items, uint32_t* item_buf, unsigned int* counters, uint32_t plan_step,
+                             int num_sms, int block_b, const void* policy, cudaStream_t st) {
   if (robots == 1)
-    return launch_two_phase<1>(gm, work, jobs, item_base, order, n_jobs, total_items, item_buf, counters,
-                               plan_step, num_sms, block_b, policy, st);
-  return launch_two_phase<2>(gm, work, jobs, item_base, order, n_jobs, total_items, item_buf, counters,
+    return launch_two_phase<1>(gm, num_actions, work, jobs, item_base, order, n_jobs, total_items, item_buf,
+                               counters, plan_step, num_sms, block_b, policy, st);
+  return launch_two_phase<2>(gm, num_actions, work, jobs, item_base, order, n_jobs, total_items, item_buf, counters,
                              plan_step, num_sms, block_b, nullptr, st);
 }
 
@@ -909,8 +919,8 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kNoAllocCounterBytes, st);
   if (e == cudaSuccess) {
     int block_b = m->tune_block > 0 ? m->tune_block : 256;
-    e = launch_rs_expand(m->dmodel, m->host->robots, m->dwork, djobs, dbase, nullptr, n_jobs, plan.total_items,
-                         items,
+    e = launch_rs_expand(m->dmodel, m->host->robots, m->host->num_actions, m->dwork, djobs, dbase, nullptr, n_jobs,
+                         plan.total_items, items,
                          counters, m->plan_step, m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc launch");

@@ -14,9 +14,9 @@ int rs_item_fields(int robots);
 // policy: learned pi0 for the rollout phase (one robot), or null for the
 // heuristic policy.
 // order: phase A takes jobs in this order (null: index order).
-cudaError_t launch_rs_expand(const DevModel* gm, int robots, DevWork* work, const dsp_leaf_job* jobs,
-                             const long long* item_base, const int* order, int n_jobs, long long total_items,
-                             uint32_t* item_buf,
+cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, DevWork* work,
+                             const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
+                             long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
                              const void* policy, cudaStream_t st);
 // Learned-policy rollout phase over the item list (one robot).
