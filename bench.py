@@ -69,6 +69,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plan", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
+    p.add_argument("--episodes", type=int, default=0,
+                   help="run planner episodes on this many held-out Rock Sample 15x15 worlds (heuristic and learned "
+                        "default policy) and exit")
+    p.add_argument("--episode-steps", type=int, default=100)
+    p.add_argument("--plan-seconds", type=float, default=0.1)
     p.add_argument("--learned-rollouts", type=int, default=0,
                    help="time only the learned-policy rollout kernel on this many start states and exit")
     p.add_argument("--ref-step-seconds", type=float, default=60.0,
@@ -312,6 +317,22 @@ def combine_ranks(t_ms, steps, dist, device):
     return float(tt.item()), float(st.item())
 
 
+def episodes(args):
+    """Whole-planner episodes (the Rock Sample 15x15 task, 4 search threads,
+    --plan-seconds per decision, up to --episode-steps decisions, worlds
+    9000.. held out from training): heuristic against learned default policy."""
+    from paper_1802_06215_b300 import build, learn
+    build.build()
+    cfg = inputs.rs15_15()
+    seeds = list(range(9000, 9000 + args.episodes))
+    heur = learn.run_episodes(cfg, seeds, args.episode_steps, args.plan_seconds)
+    h, _ = learn.load_weights(os.path.join(ROOT, "paper_1802_06215_b300", "weights", "rs15_15_pi0.npz"))
+    lrn = learn.run_episodes(cfg, seeds, args.episode_steps, args.plan_seconds, policy=h)
+    print(json.dumps({"metric": "planner episodes (discounted return, decisions/s, root gap)", "workload":
+                      f"rs15_15: {len(seeds)} worlds x up to {args.episode_steps} decisions of "
+                      f"{args.plan_seconds} s, 4 threads", "heuristic": heur, "learned": lrn}), flush=True)
+
+
 def learned_rollouts(args):
     """The learned-policy rollout kernel alone (dsp_rollout_logged) on N
     Rock Sample 15x15 start states with the shipped weights: tensor rate of
@@ -490,6 +511,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.episodes:
+        if rank == 0:
+            episodes(args)
     elif args.learned_rollouts:
         if rank == 0:
             learned_rollouts(args)

@@ -104,7 +104,7 @@ def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node
     world[4] = 0
     belief = Belief(cfg, world[0, 0])
     ret, disc = 0.0, 1.0
-    roots, states, hists, labels, decisions = [], [], [], [], 0
+    roots, states, hists, labels, decisions, gaps = [], [], [], [], 0, []
     t_plan = 0.0
     for t in range(steps):
         K = cfg.K
@@ -122,6 +122,7 @@ def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node
         else:
             res = _dsp.dsp_plan(model.h, root, belief.hist, p, model.num_actions)
         t_plan += res["seconds"]
+        gaps.append(res["root_u"] - res["root_l"])
         decisions += 1
         a = int(res["action"])
         model.set_plan_step(WORLD_STEP_BASE + (world_seed & 0x3FFFFFFF))
@@ -132,7 +133,7 @@ def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node
         world = nxt
         if (int(key[0]) >> 62) & 1 or (int(nxt[0, 0]) >> 16) & 1:
             break
-    out = {"return": ret, "roots": roots, "decisions": decisions, "plan_seconds": t_plan}
+    out = {"return": ret, "roots": roots, "decisions": decisions, "plan_seconds": t_plan, "gaps": gaps}
     if harvest and states:
         out["states"] = np.concatenate(states, axis=1)
         out["hist"] = np.concatenate(hists, axis=0)
@@ -462,6 +463,25 @@ def policy_iteration(cfg, iterations=4, n_random=60000, n_onpolicy=4000, Kq=64, 
         log(json.dumps(rec))
     model.close()
     return policy, hist_log
+
+
+def run_episodes(cfg, world_seeds, steps, seconds, policy=None, threads=4):
+    """Planner episodes on the given worlds (Sec. IV-A task, belief updated by
+    Bayes' rule after every real step): mean discounted return, decisions per
+    second of planning time and mean root gap at decision time; `policy` (a
+    dsp_mlp handle) replaces the heuristic default policy in the rollouts."""
+    model = batch.Model(cfg)
+    _dsp.dsp_set_policy(model.h, policy)
+    rets, dec, secs, gaps = [], 0, 0.0, []
+    for s in world_seeds:
+        ep = episode(model, cfg, s, steps, seconds, threads, harvest=False)
+        rets.append(ep["return"])
+        dec += ep["decisions"]
+        secs += ep["plan_seconds"]
+        gaps += ep["gaps"]
+    model.close()
+    return {"worlds": len(rets), "mean_return": float(np.mean(rets)), "min_return": float(np.min(rets)),
+            "decisions": dec, "decisions_per_s": dec / max(secs, 1e-9), "mean_root_gap": float(np.mean(gaps))}
 
 
 # ---------------------------------------------------------------- the car ----
