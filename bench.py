@@ -69,6 +69,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plan", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
+    p.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
     p.add_argument("--episodes", type=int, default=0,
                    help="run planner episodes on this many held-out Rock Sample 15x15 worlds (heuristic and learned "
                         "default policy) and exit")
@@ -452,6 +453,26 @@ def run_ours(args, rank, world):
         return
     clocks = clk.summary()
     planning = None if args.no_plan else planning_step(_dsp, m, cfg, plan)
+    # the same planning step with the leaves going through the device job queue;
+    # the model creates its queue (and the kernel's graph) on the first such
+    # step and keeps it, so the second step is what a replanning loop sees
+    planning_queue = None
+    if not args.no_plan and cfg.kind != inputs.CAR and not plan[2]:
+        first = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
+        planning_queue = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
+        planning_queue["first_step_with_queue_creation"] = {k: first[k] for k in ("expansions", "seconds",
+                                                                                   "expansions_per_s")}
+    # the autotuner's choice of launch shape on the first 512 jobs (after the
+    # timed region, which ran the default shape; the default is kept after)
+    autotuned = None
+    if not args.no_autotune:
+        from paper_1802_06215_b300 import autotune as AT
+        sub = batch.JobBatch(m, jobs[:512])
+        default = _dsp.dsp_get_tuning(m.h)
+        best = AT.dsp_autotune(m.h, sub.descs, len(sub.jobs), reps=3)
+        autotuned = {"jobs": len(sub.jobs), "block": best["block"], "tps": best["tps"], "ms": best["ms"],
+                     "default": list(default)}
+        _dsp.dsp_set_tuning(m.h, *default)
     learned = None
     if not args.no_learned and args.workload in ("rs15_15", "car50"):
         learned = learned_step(_dsp, batch, m, cfg, jobs, plan[1])
@@ -496,6 +517,8 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "cpu_baseline": cpu,
         "planning": planning,
+        "planning_queue": planning_queue,
+        "autotune": autotuned,
         "learned_pi0": learned,
         "clocks": clocks,
     }

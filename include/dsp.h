@@ -159,14 +159,17 @@ dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t
  * kernel, launched from a CUDA graph, pulls leaf jobs that many host threads
  * submit). Jobs go into a ring of `capacity` slots in mapped pinned host
  * memory; the kernel takes them in ticket order, expands each (same results
- * as dsp_expand_leaves) and marks it done; it exits after idle_ns nanoseconds
+ * as dsp_expand_leaves; a job's rollouts are shared by every CTA of the grid)
+ * and marks it done; it exits after idle_ns nanoseconds
  * without a job (0 = 2 ms) and a monitor thread relaunches it when jobs are
  * pending. Rock Sample models only (DSP_E_UNSUPPORTED for the car). All job
  * pointers are device memory. submit and wait are thread-safe. */
 typedef struct dsp_queue dsp_queue;
 dsp_status dsp_queue_create(dsp_model* model, int32_t capacity, uint64_t idle_ns, dsp_queue** out);
-/* Publishes one job (copied); *ticket identifies it. Waits at most timeout_ns
- * (0 = no limit) for a free slot, else DSP_E_QUEUE_FULL with no ticket taken. */
+/* Publishes one job (copied, with the model's plan step at this moment: the
+ * job draws its random streams under it); *ticket identifies it. A ring slot
+ * is free again once its job has completed. Waits at most timeout_ns (0 = no
+ * limit) for a free slot, else DSP_E_QUEUE_FULL with no ticket taken. */
 dsp_status dsp_queue_submit(dsp_queue* queue, const dsp_leaf_job* job, uint64_t timeout_ns, uint64_t* ticket);
 /* Waits at most timeout_ns (0 = no limit) until the job's results are written
  * (DSP_E_TIMEOUT otherwise); DSP_E_CUDA if the persistent kernel failed. */
@@ -188,7 +191,8 @@ typedef struct {
   int32_t deterministic; /* 1: rounds (select in thread order, one batched expansion, backups in thread order);
                             0: free-running threads, one CUDA stream each */
   int32_t use_queue;     /* free running, Rock Sample: threads submit their leaves to one device job queue
-                            (dsp_queue_*) instead of launching their own expansions */
+                            (dsp_queue_*) instead of launching their own expansions; the model keeps that
+                            queue (capacity max(64, 4 x threads)) until dsp_destroy_model */
 } dsp_search_params;
 
 typedef struct {

@@ -168,6 +168,7 @@ void dsp_destroy_model(dsp_model* m) {
   if (m->dwork) cudaFree(m->dwork);
   if (m->policy) cudaFree(m->policy);
   for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
+  if (m->queue) dsp_queue_destroy(m->queue);
   if (m->pool) cudaMemPoolDestroy(m->pool);
   delete m->host;
   delete m;
@@ -282,7 +283,7 @@ dsp_status dsp_set_tuning(dsp_model* m, int32_t block, int32_t tps) {
 dsp_status dsp_get_tuning(const dsp_model* m, int32_t* block, int32_t* tps) {
   if (!m || !block || !tps) return fail(DSP_E_INVALID, "dsp_get_tuning: NULL argument");
   *block = m->tune_block > 0 ? m->tune_block : 256;
-  *tps = m->tune_tps > 0 ? m->tune_tps : 16;
+  *tps = m->tune_tps > 0 ? m->tune_tps : 32;
   return DSP_OK;
 }
 

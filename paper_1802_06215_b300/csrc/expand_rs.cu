@@ -672,14 +672,14 @@ __device__ __forceinline__ int queue_claim_chunk(const QueueRing& ring, unsigned
 template <int R>
 __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                              QueueRing ring, unsigned long long* head,
-                                                             uint32_t plan_step, uint32_t* scratch,
-                                                             size_t slot_words, dsp_leaf_job* jcopy,
-                                                             unsigned long long idle_ns) {
+                                                             uint32_t* scratch, size_t slot_words,
+                                                             dsp_leaf_job* jcopy, unsigned long long idle_ns) {
   __shared__ RSGroupSmem S;
   __shared__ long long s_ticket;
+  __shared__ unsigned int s_plan_step;
   __shared__ int s_work, s_exit;
   load_rs_consts(S.c, gm);
-  const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
+  RSModel<R> M = make_rs<R>(gm, &S.c, 0u);  // each job carries its own plan step
   const int tid = threadIdx.x, lane = tid & 31;
   unsigned long long steps = 0, last_work = global_ns();
   __syncthreads();
@@ -695,6 +695,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
         uint32_t* dst = (uint32_t*)&S.J;
         for (int w = 0; w < (int)(sizeof(dsp_leaf_job) / 4); ++w) dst[w] = src[w];
         jcopy[slot] = S.J;
+        s_plan_step = *(volatile unsigned int*)(ring.plan_step + slot);
       }
       s_ticket = ticket;
       s_work = 0;
@@ -705,6 +706,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       const int slot = (int)(ticket % ring.cap);
       const int n = S.J.n_scen;
       long long nchunks = 0;
+      M.plan_step = s_plan_step;
       if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
         Items<R> items{scratch + (size_t)slot * slot_words, (long long)n * S.J.n_actions};
         group_job<R>(S, M, 0, 0, items, work, steps);
@@ -723,6 +725,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
           // large jobs hand out several chunks per claim, so claims do not
           // queue up on the claim word; small ones one chunk at a time
           sh.grain = (unsigned int)max(1LL, min(16LL, nchunks / 256));
+          sh.plan_step = s_plan_step;
           __threadfence();
           atomicExch(&sh.claim, ((unsigned long long)ticket & 0xFFFFFFFFull) << 32);
         }
@@ -736,6 +739,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       if (slot < 0) break;
       const dsp_leaf_job* J = jcopy + slot;
       Items<R> items{scratch + (size_t)slot * slot_words, (long long)J->n_scen * J->n_actions};
+      M.plan_step = *(volatile unsigned int*)&ring.share[slot].plan_step;
       for (unsigned int k = 0; k < count; ++k) rs_rollout_chunk<R>(M, J, items, chunk + k, steps);
       __threadfence();  // every lane's sums, before the chunks count as done
       __syncwarp();
@@ -779,14 +783,12 @@ int rs_queue_blocks_per_sm(int robots) {
 }
 
 cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, QueueRing ring, unsigned long long* head,
-                            uint32_t plan_step, uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy,
-                            unsigned long long idle_ns, int grid, cudaStream_t st) {
+                            uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy, unsigned long long idle_ns,
+                            int grid, cudaStream_t st) {
   if (robots == 1)
-    rs_queue_kernel<1><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, plan_step, scratch, slot_words, jcopy,
-                                                 idle_ns);
+    rs_queue_kernel<1><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, scratch, slot_words, jcopy, idle_ns);
   else
-    rs_queue_kernel<2><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, plan_step, scratch, slot_words, jcopy,
-                                                 idle_ns);
+    rs_queue_kernel<2><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, scratch, slot_words, jcopy, idle_ns);
   return cudaGetLastError();
 }
 

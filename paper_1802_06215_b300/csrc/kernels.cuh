@@ -31,21 +31,22 @@ struct QueueShare {
   unsigned int nchunks;       // rollout chunks of 32 items
   unsigned int remaining;     // chunks not yet finished
   unsigned int grain;         // chunks a warp takes per claim
-  unsigned int pad;
+  unsigned int plan_step;     // plan step of the published job
 };
 struct QueueRing {
   unsigned long long* seq;   // [cap] t + 1: ticket t published; t + cap: slot free for ticket t + cap
   dsp_leaf_job* jobs;        // [cap]
   unsigned long long* done;  // [cap] last finished ticket + 1
   unsigned int* close;       // nonzero: exit once no job is ready
+  unsigned int* plan_step;   // [cap] plan step (fourth Philox counter word) of the slot's job
   QueueShare* share;         // [cap] device memory
   int cap;
 };
 size_t rs_queue_slot_words(int robots, int num_actions);
 int rs_queue_blocks_per_sm(int robots);
 cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, QueueRing ring, unsigned long long* head,
-                            uint32_t plan_step, uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy,
-                            unsigned long long idle_ns, int grid, cudaStream_t st);
+                            uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy, unsigned long long idle_ns,
+                            int grid, cudaStream_t st);
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,
                            const int32_t* actions, int depth, uint32_t* out, int out_cap, uint64_t* keys,

@@ -16,6 +16,8 @@ struct dsp_model {
   int device = 0;
   int num_sms = 0;
   cudaMemPool_t pool = nullptr;      // stream-ordered work buffers; keeps its peak size until destroy
+  dsp_queue* queue = nullptr;        // device job queue of the tree search, kept across planning steps
+  int queue_cap = 0;
   int tune_block = 0;                // CTA size chosen by the autotuner (0 = default)
   int tune_tps = 0;                  // car: threads per scenario (0 = default)
   void* policy = nullptr;            // learned pi0 for rollouts (device, transposed BF16 weights)

@@ -21,11 +21,12 @@
 struct dsp_queue {
   dsp_model* m = nullptr;
   int cap = 0;
-  // mapped pinned host memory: seq[cap], done[cap], jobs[cap], close flag
+  // mapped pinned host memory: seq[cap], done[cap], jobs[cap], plan_step[cap], close flag
   unsigned char* host = nullptr;
   unsigned long long* seq = nullptr;
   unsigned long long* done = nullptr;
   dsp_leaf_job* jobs = nullptr;
+  unsigned int* plan_step = nullptr;
   unsigned int* close = nullptr;
   dsp::QueueRing ring{};
   unsigned long long* d_head = nullptr;  // device: next ticket to consume
@@ -37,7 +38,6 @@ struct dsp_queue {
   unsigned long long idle_ns = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
-  uint32_t graph_plan_step = 0;
   std::atomic<unsigned long long> tail{0};  // next ticket to hand out
   std::atomic<unsigned long long> launches{0};
   std::atomic<unsigned long long> consumed{0};
@@ -60,7 +60,7 @@ dsp_status build_graph(dsp_queue* q) {
   cudaError_t e = cudaStreamBeginCapture(q->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_queue: begin capture");
   cudaError_t el = launch_rs_queue(q->m->dmodel, q->m->host->robots, q->m->dwork, q->ring, q->d_head,
-                                   q->m->plan_step, q->d_scratch, q->slot_words, q->d_jcopy, q->idle_ns, q->grid,
+                                   q->d_scratch, q->slot_words, q->d_jcopy, q->idle_ns, q->grid,
                                    q->stream);
   e = cudaStreamEndCapture(q->stream, &g);
   if (el != cudaSuccess) return cuda_fail(el, "dsp_queue: capture launch");
@@ -68,7 +68,6 @@ dsp_status build_graph(dsp_queue* q) {
   e = cudaGraphInstantiate(&q->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_queue: instantiate");
-  q->graph_plan_step = q->m->plan_step;
   return DSP_OK;
 }
 
@@ -83,7 +82,7 @@ void monitor_loop(dsp_queue* q) {
       if (q->shutdown && q->tail.load() <= q->consumed.load()) break;
     }
     dsp_status s = DSP_OK;
-    if (q->graph == nullptr || q->graph_plan_step != q->m->plan_step) s = build_graph(q);
+    if (q->graph == nullptr) s = build_graph(q);
     cudaError_t e = cudaSuccess;
     if (s == DSP_OK) e = cudaGraphLaunch(q->graph, q->stream);
     if (s == DSP_OK && e == cudaSuccess) q->launches += 1;
@@ -118,7 +117,8 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
   q->m = m;
   q->cap = capacity;
   q->idle_ns = idle_ns;
-  size_t bytes = sizeof(unsigned long long) * 2 * (size_t)capacity + sizeof(dsp_leaf_job) * (size_t)capacity + 256;
+  size_t bytes = sizeof(unsigned long long) * 2 * (size_t)capacity + sizeof(dsp_leaf_job) * (size_t)capacity +
+                 sizeof(unsigned int) * (size_t)capacity + 256;
   cudaError_t e = cudaHostAlloc((void**)&q->host, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
   if (e != cudaSuccess) {
     delete q;
@@ -128,7 +128,8 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
   q->seq = (unsigned long long*)q->host;
   q->done = q->seq + capacity;
   q->jobs = (dsp_leaf_job*)(q->done + capacity);
-  q->close = (unsigned int*)(q->jobs + capacity);
+  q->plan_step = (unsigned int*)(q->jobs + capacity);
+  q->close = q->plan_step + capacity;
   for (int i = 0; i < capacity; ++i) q->seq[i] = (unsigned long long)i;  // slot i takes ticket i first
   void* dp = nullptr;
   e = cudaHostGetDevicePointer(&dp, q->host, 0);
@@ -137,7 +138,8 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
     q->ring.seq = (unsigned long long*)d;
     q->ring.done = q->ring.seq + capacity;
     q->ring.jobs = (dsp_leaf_job*)(q->ring.done + capacity);
-    q->ring.close = (unsigned int*)(q->ring.jobs + capacity);
+    q->ring.plan_step = (unsigned int*)(q->ring.jobs + capacity);
+    q->ring.close = q->ring.plan_step + capacity;
     q->ring.cap = capacity;
     q->grid = rs_queue_blocks_per_sm(m->host->robots) * m->num_sms;
     q->slot_words = rs_queue_slot_words(m->host->robots, m->host->num_actions);
@@ -155,7 +157,7 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
       sh.nchunks = 0;
       sh.remaining = 0;
       sh.grain = 1;
-      sh.pad = 0;
+      sh.plan_step = 0;
     }
     e = cudaMemcpy(q->d_share, init.data(), sizeof(dsp::QueueShare) * (size_t)capacity, cudaMemcpyHostToDevice);
     q->ring.share = q->d_share;
@@ -203,6 +205,7 @@ dsp_status dsp_queue_submit(dsp_queue* q, const dsp_leaf_job* job, uint64_t time
     std::this_thread::yield();
   }
   q->jobs[slot] = *job;
+  q->plan_step[slot] = q->m->plan_step;  // the job's random streams: the model's plan step at submission
   __atomic_store_n(&q->seq[slot], t + 1, __ATOMIC_RELEASE);
   { std::lock_guard<std::mutex> lock(q->mu); }  // the monitor cannot miss this wake-up
   q->cv.notify_all();

@@ -532,14 +532,22 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   dsp_status s = dsp_read_counters(m_, &steps0, &status);
   if (s != DSP_OK) return s;
   if (!p_.deterministic && p_.use_queue) {
-    s = dsp_queue_create(m_, 4 * p_.threads, 0, &queue_);
-    if (s != DSP_OK) return s;
+    // the model keeps its queue (and the persistent kernel's graph) across
+    // planning steps; every job carries the plan step it was submitted under
+    const int want = std::max(64, 4 * p_.threads);
+    if (m_->queue != nullptr && m_->queue_cap < want) {
+      dsp_queue_destroy(m_->queue);
+      m_->queue = nullptr;
+    }
+    if (m_->queue == nullptr) {
+      s = dsp_queue_create(m_, want, 0, &m_->queue);
+      if (s != DSP_OK) return s;
+      m_->queue_cap = want;
+    }
+    queue_ = m_->queue;
   }
   s = p_.deterministic ? run_rounds() : run_threads();
-  if (queue_ != nullptr) {
-    dsp_queue_destroy(queue_);
-    queue_ = nullptr;
-  }
+  queue_ = nullptr;
   if (s != DSP_OK) return s;
   s = dsp_read_counters(m_, &steps1, &status);
   if (s != DSP_OK) return s;
