@@ -109,3 +109,59 @@ def test_queue_rejects_bad_input(env):
     assert e.value.status == _dsp.DSP_E_UNSUPPORTED
     car.close()
     m.close()
+
+
+def test_queue_jobs_keep_their_plan_step(env):
+    """Each job draws its random streams under the plan step the model had
+    when it was submitted (Sense readings differ between plan steps): jobs
+    submitted under alternating plan steps, while one persistent kernel runs,
+    equal batch expansions taken under the same plan steps."""
+    torch, _dsp, batch = env
+    cfg = I.rs15_15()
+    m = batch.Model(cfg)
+    jobs = I.job_stream(cfg, 10, 31, max_scen=200)
+    steps = [5 if k % 2 == 0 else 9 for k in range(len(jobs))]
+    refs = {}
+    for ps in (5, 9):
+        m.set_plan_step(ps)
+        r = batch.JobBatch(m, jobs)
+        r.run()
+        torch.cuda.synchronize()
+        refs[ps] = r.all_results()
+    assert any(not np.array_equal(refs[5][k]["key"], refs[9][k]["key"]) for k in range(len(jobs)))
+    out = batch.JobBatch(m, jobs)
+    q = _dsp.dsp_queue_create(m.h, 16)
+    tickets = []
+    for k in range(len(jobs)):
+        m.set_plan_step(steps[k])
+        tickets.append(_dsp.dsp_queue_submit(q, out.descs[k], 10_000_000_000))
+    for t in tickets:
+        _dsp.dsp_queue_wait(q, t, 30_000_000_000)
+    _dsp.dsp_queue_destroy(q)
+    got = out.all_results()
+    for k in range(len(jobs)):
+        for f in FIELDS:
+            assert np.array_equal(refs[steps[k]][k][f], got[k][f]), (k, f)
+    _, status = m.counters()
+    assert status == 0
+    m.close()
+
+
+def test_search_keeps_its_queue_across_planning_steps(env):
+    """Two free-running planning steps through the device queue on one model:
+    the model keeps the queue (and its persistent kernel's graph) and both
+    steps finish with consistent root bounds."""
+    torch, _dsp, batch = env
+    cfg = I.rs15_15()
+    m = batch.Model(cfg)
+    root = I.rs_block(cfg, cfg.K, np.random.default_rng(1), pos=[(0, 7)])
+    p = _dsp.dsp_search_params(threads=4, rounds=40, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95, target_gap=0.0,
+                               deterministic=0, use_queue=1)
+    for k in range(2):
+        m.set_plan_step(100 + k)
+        r = _dsp.dsp_plan(m.h, root, None, p, m.num_actions)
+        assert r["expansions"] >= 1 and r["root_l"] <= r["root_u"] + 1e-9
+        assert 0 <= r["action"] < m.num_actions
+    _, status = m.counters()
+    assert status == 0
+    m.close()
