@@ -1,23 +1,27 @@
 // Leaf expansion for Rock Sample models (one or two robots), Sec. III-D, in
 // two phases.
 //
-// Phase A (rs_group_kernel, persistent over jobs): a CTA takes a leaf job,
-// gathers its scenarios from the parent list and applies the last action
-// ("update") once, then steps every (action, scenario) pair with g
-// (Eq. expand) and splits each action's scenarios by observation into
-// children (Eq. newnodes). Each action occupies whole warps, so grouping needs
-// no hash and no serial pass: lanes with the same observation code (z, and
-// whether the step ended the world) meet through __match_any_sync, a small
-// per-warp table gives the cross-warp prefixes, and children are numbered by
-// their first position. Phase A writes the children (counts, offsets, keys,
-// exact reward sums, grouped positions) and appends one rollout item per
-// (action, scenario) to a flat list in child-grouped order.
+// Phase A (rs_group_kernel, persistent over jobs, largest first): a CTA takes
+// a leaf job, gathers its scenarios from the parent list and applies the last
+// action ("update") once. Each warp then expands whole actions of the job in
+// two passes over 32-scenario chunks:
+//  1. Step every (action, scenario) pair with g (Eq. expand) and count each
+//     observation code (z, and whether the step ended the world): its
+//     scenarios, first position and exact reward sum, by ballots (one robot,
+//     6 codes, in registers) or __match_any_sync leaders (two robots, 18
+//     codes, in the warp's rows of shared tables).
+//  2. Number the children by first position (Eq. newnodes), then write the
+//     grouped positions and one rollout item per (action, scenario), in
+//     child-grouped order. Actions that draw no random numbers are re-applied;
+//     Sense leaves the state unchanged.
+// No barrier is needed inside a job. Phase A also writes the children's
+// counts, offsets, keys and reward sums.
 //
 // Phase B (rs_rollout_items_kernel): warps pull 32-item chunks of that list
 // (no barriers, full occupancy), compute u (Eq. ub) and the default-policy
 // rollout (Eq. lb) in registers, and add each run of same-child lanes to the
-// child's int64 fixed-point sums with one atomic (exact in any order). A warp's
-// lanes mostly share a child, so they branch alike.
+// child's int64 fixed-point sums with one atomic (exact in any order). A
+// warp's lanes mostly share a child, so they branch alike.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,176 +42,23 @@ constexpr int kCodes = 18;            // observation code z + 9 * terminal, z <=
 struct RSGroupSmem {
   RSShared c;
   uint32_t leaf[5][kMaxScen];          // the leaf's states, field-major
-  int wcnt[kWarpsA][kCodes];           // per warp: lanes holding each code
-  int wfirst[kWarpsA][kCodes];         // per warp: first position of each code
-  int wpre[kWarpsA][kCodes];           // items of the code in earlier warps of the action
-  int acnt[kWarpsA][kCodes];           // per action of the pass: scenarios per code
-  int afirst[kWarpsA][kCodes];
+  // two robots, per warp and observation code of the warp's current action:
+  int wcnt[kWarpsA][kCodes];           // scenarios holding the code
+  int wfirst[kWarpsA][kCodes];         // first position of the code
+  int wpre[kWarpsA][kCodes];           // scenarios of the code placed so far (pass 2)
   int aoff[kWarpsA][kCodes];           // offset of the code's child in the grouped order
   int acid[kWarpsA][kCodes];           // child index of the code
-  int anch[kWarpsA];                   // children per action
-  unsigned long long sr[kWarpsA][kCodes];
+  unsigned long long sr[kWarpsA][kCodes];  // exact reward sum (fixed point)
   uint32_t pm_job;
   int job;
   dsp_leaf_job J;
-  uint8_t code1[kWarpsA][kMaxScen];    // one robot: each warp's observation codes of its action
+  uint8_t code1[kWarpsA][kMaxScen];    // each warp's observation codes of its current action
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
-}
-
-// Phase A for the job in S.J (index j in its job table, first item ibase). All
-// threads of the CTA call it; it ends with a barrier.
-template <int R>
-__device__ void rs_group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase, Items<R> items,
-                             DevWork* work, unsigned long long& steps) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  {
-    const dsp_leaf_job& J = S.J;
-    const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
-
-    // gather + update, once per job
-    for (int p = tid; p < n; p += kBlockA) {
-      RSS s = M.load(J.parent, J.parent_cap, J.idx[p]);
-      if (J.last_action >= 0) {
-        if (!M.terminal(s)) steps += 1;
-        uint64_t k;
-        M.step(s, J.last_action, depth - 1, k);
-      }
-      S.leaf[0][p] = s.pos[0];
-      S.leaf[1][p] = s.pos[1];
-      S.leaf[2][p] = s.good;
-      S.leaf[3][p] = s.sampled;
-      S.leaf[4][p] = s.scen;
-      if (J.leaf_states != nullptr) M.store(s, J.leaf_states, n, p);
-    }
-    if (tid == 0) {
-      uint32_t h[8];
-      const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) h[k] = hw[k];
-      S.pm_job = positive_mask(h, M.m);
-    }
-    // each action takes wpa whole warps; apass actions per pass
-    const int wpa = (n + 31) >> 5;
-    const int apass = kWarpsA / wpa;
-    for (int a0 = 0; a0 < A; a0 += apass) {
-      for (int t = tid; t < kWarpsA * kCodes; t += kBlockA) {
-        (&S.wcnt[0][0])[t] = 0;
-        (&S.wfirst[0][0])[t] = 0x7FFFFFFF;
-        (&S.sr[0][0])[t] = 0ull;
-      }
-      __syncthreads();
-      const int al = warp / wpa;
-      const int p = (warp - al * wpa) * 32 + lane;
-      const int a = a0 + al;
-      const bool valid = al < apass && a < A && p < n;
-      RSS s;
-      uint64_t key = 0;
-      int code = 32 + lane, rint = 0;
-      if (valid) {
-        s.pos[0] = S.leaf[0][p];
-        s.pos[1] = S.leaf[1][p];
-        s.good = S.leaf[2][p];
-        s.sampled = S.leaf[3][p];
-        s.scen = S.leaf[4][p];
-        if (!M.terminal(s)) steps += 1;
-        rint = (int)M.step(s, J.first_action + a, depth, key);
-        code = (int)(key & 0xFu) + 9 * (int)(key >> 62);
-      }
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, code);
-      const int wrank = __popc(peers & lanemask_lt());
-      const int leader = __ffs(peers) - 1;
-      const int rsum = __reduce_add_sync(peers, rint);
-      if (valid && lane == leader) {
-        S.wcnt[warp][code] = __popc(peers);
-        S.wfirst[warp][code] = p;
-        atomicAdd(&S.sr[al][code], (unsigned long long)((long long)rsum * 4294967296LL));
-      }
-      __syncthreads();
-      // cross-warp prefixes per (action, code)
-      if (tid < apass * kCodes) {
-        int bl = tid / kCodes, c = tid - bl * kCodes;
-        int run = 0, first = 0x7FFFFFFF;
-        for (int w = bl * wpa; w < (bl + 1) * wpa; ++w) {
-          S.wpre[w][c] = run;
-          run += S.wcnt[w][c];
-          first = min(first, S.wfirst[w][c]);
-        }
-        S.acnt[bl][c] = run;
-        S.afirst[bl][c] = first;
-      }
-      __syncthreads();
-      // children in order of first position
-      if (tid < apass * kCodes) {
-        int bl = tid / kCodes, c = tid - bl * kCodes;
-        int cnt = S.acnt[bl][c], first = S.afirst[bl][c];
-        int cid = 0, off = 0, nch = 0;
-        for (int c2 = 0; c2 < kCodes; ++c2) {
-          int n2 = S.acnt[bl][c2];
-          if (n2 > 0) {
-            nch += 1;
-            if (S.afirst[bl][c2] < first) {
-              cid += 1;
-              off += n2;
-            }
-          }
-        }
-        S.acid[bl][c] = cnt > 0 ? cid : -1;
-        S.aoff[bl][c] = off;
-        if (c == 0) S.anch[bl] = nch;
-      }
-      __syncthreads();
-      // grouped position, perm, rollout item
-      if (valid) {
-        const int cid = S.acid[al][code];
-        const int q = S.aoff[al][code] + S.wpre[warp][code] + wrank;
-        J.perm[(size_t)a * n + q] = (uint16_t)p;
-        uint32_t h[8];
-        const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) h[k] = hw[k];
-        uint32_t pm = S.pm_job;
-        M.observe(h, pm, J.first_action + a, key);
-        const size_t it = (size_t)(ibase + (long long)a * n + q);
-        items.f(0)[it] = s.pos[0];
-        int f = 1;
-        if (R == 2) items.f(f++)[it] = s.pos[1];
-        items.f(f++)[it] = s.good;
-        items.f(f++)[it] = s.sampled;
-        items.f(f++)[it] = s.scen;
-        items.f(f++)[it] = pm;
-        items.f(f++)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(cid, cap - 1));
-        items.f(f++)[it] = (uint32_t)j;
-      }
-      // per-action results: counts, offsets, keys, reward sums; u and l start at 0
-      if (tid < apass * kCodes) {
-        int bl = tid / kCodes, c = tid - bl * kCodes;
-        int a2 = a0 + bl;
-        int cid = S.acid[bl][c];
-        if (a2 < A && cid >= 0) {
-          int nch = S.anch[bl];
-          if (cid == 0) {
-            J.child_count[a2] = nch;
-            if (nch > cap) report(work, kStatusOverflow);
-            if (nch <= cap) J.child_off[(size_t)a2 * (cap + 1) + nch] = n;
-          }
-          if (cid < cap) {
-            size_t o = (size_t)a2 * cap + cid;
-            J.child_off[(size_t)a2 * (cap + 1) + cid] = S.aoff[bl][c];
-            J.child_key[o] = (uint64_t)(c % 9) | ((uint64_t)(c / 9) << 62);
-            J.rew_sum[o] = (long long)S.sr[bl][c];
-            J.u_sum[o] = 0;
-            J.l_sum[o] = 0;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
 }
 
 // Gather + update of the job in S.J into S.leaf (and J.leaf_states), and the
@@ -389,13 +240,149 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
   __syncthreads();
 }
 
+// Phase A for two robots, organised like rs1_group_job: each warp expands
+// whole actions in two passes over 32-scenario chunks. The codes (z0 * 3 + z1
+// and whether the step ended the world, up to 18) are too many for
+// registers, so each warp keeps its per-code counts, first positions, reward
+// sums, child numbers, offsets and running counts in its own rows of the
+// shared tables. Lanes with the same code meet through __match_any_sync and
+// their leader updates the code's row; the warp's own __syncwarp orders the
+// updates. The result is identical to the general grouping.
+__device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long long ibase, Items<2> items,
+                              DevWork* work, unsigned long long& steps) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  gather_update<2>(S, M, steps);
+  const dsp_leaf_job& J = S.J;
+  const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
+  const uint32_t lt = lanemask_lt();
+  uint8_t* codes = S.code1[warp];
+  int* cnt = S.wcnt[warp];
+  int* first = S.wfirst[warp];
+  int* run = S.wpre[warp];
+  int* off = S.aoff[warp];
+  int* cid = S.acid[warp];
+  unsigned long long* rsum = S.sr[warp];
+  const int nwarps = (int)(blockDim.x >> 5);
+  for (int a = warp; a < A; a += nwarps) {
+    const int aa = J.first_action + a;
+    const int a0 = aa / M.per, a1 = aa - a0 * M.per;
+    if (lane < kCodes) {
+      cnt[lane] = 0;
+      first[lane] = 0x7FFFFFFF;
+      rsum[lane] = 0ull;
+    }
+    __syncwarp();
+    // pass 1: step, record each scenario's code, per-code counts and sums
+    for (int w = 0; w * 32 < n; ++w) {
+      const int p = w * 32 + lane;
+      int code = kCodes, rint = 0;
+      if (p < n) {
+        RSS s;
+        s.pos[0] = S.leaf[0][p];
+        s.pos[1] = S.leaf[1][p];
+        s.good = S.leaf[2][p];
+        s.sampled = S.leaf[3][p];
+        s.scen = S.leaf[4][p];
+        if (!M.terminal(s)) steps += 1;
+        uint64_t key;
+        rint = (int)M.step(s, aa, depth, key);
+        code = (int)(key & 0xFu) + 9 * (int)(key >> 62);
+        codes[p] = (uint8_t)code;
+      }
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, code);
+      const int rs = __reduce_add_sync(peers, rint);
+      if (p < n && lane == __ffs(peers) - 1) {
+        if (cnt[code] == 0) first[code] = p;
+        cnt[code] += __popc(peers);
+        rsum[code] += (unsigned long long)((long long)rs * 4294967296LL);
+      }
+      __syncwarp();
+    }
+    // children in order of first position
+    int nch = 0;
+    if (lane < kCodes) {
+      int k = 0, o = 0;
+      const int mine = first[lane];
+      if (cnt[lane] > 0)
+        for (int c2 = 0; c2 < kCodes; ++c2)
+          if (cnt[c2] > 0 && first[c2] < mine) {
+            k += 1;
+            o += cnt[c2];
+          }
+      cid[lane] = cnt[lane] > 0 ? k : -1;
+      off[lane] = o;
+      run[lane] = 0;
+    }
+    nch = __popc(__ballot_sync(0xFFFFFFFFu, lane < kCodes && cnt[lane] > 0));
+    __syncwarp();
+    // per-action results: counts, offsets, keys, exact reward sums; u and l start at 0
+    if (lane == 0) {
+      J.child_count[a] = nch;
+      if (nch > cap) report(work, kStatusOverflow);
+      if (nch <= cap) J.child_off[(size_t)a * (cap + 1) + nch] = n;
+    }
+    if (lane < kCodes && cid[lane] >= 0 && cid[lane] < cap) {
+      const size_t o = (size_t)a * cap + cid[lane];
+      J.child_off[(size_t)a * (cap + 1) + cid[lane]] = off[lane];
+      J.child_key[o] = (uint64_t)(lane % 9) | ((uint64_t)(lane / 9) << 62);
+      J.rew_sum[o] = (long long)rsum[lane];
+      J.u_sum[o] = 0;
+      J.l_sum[o] = 0;
+    }
+    // pass 2: grouped positions and rollout items; only Sense draws random
+    // numbers and it leaves the state as it was, so each robot's other
+    // actions are simply applied again
+    for (int w = 0; w * 32 < n; ++w) {
+      const int p = w * 32 + lane;
+      const int code = p < n ? (int)codes[p] : kCodes;
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, code);
+      int q = 0, mycid = 0;
+      if (p < n) {
+        q = off[code] + run[code] + __popc(peers & lt);
+        mycid = cid[code];
+      }
+      __syncwarp();
+      if (p < n && lane == __ffs(peers) - 1) run[code] += __popc(peers);
+      if (p < n) {
+        RSS s;
+        s.pos[0] = S.leaf[0][p];
+        s.pos[1] = S.leaf[1][p];
+        s.good = S.leaf[2][p];
+        s.sampled = S.leaf[3][p];
+        s.scen = S.leaf[4][p];
+        int z;
+        if (a0 < 5) M.robot_step(s, 0, a0, depth, z);
+        if (a1 < 5) M.robot_step(s, 1, a1, depth, z);
+        J.perm[(size_t)a * n + q] = (uint16_t)p;
+        uint32_t h[8];
+        const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = hw[k];
+        uint32_t pm = S.pm_job;
+        M.observe(h, pm, aa, (uint64_t)(code % 9));
+        const size_t it = (size_t)(ibase + (long long)a * n + q);
+        items.f(0)[it] = s.pos[0];
+        items.f(1)[it] = s.pos[1];
+        items.f(2)[it] = s.good;
+        items.f(3)[it] = s.sampled;
+        items.f(4)[it] = s.scen;
+        items.f(5)[it] = pm;
+        items.f(6)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1));
+        items.f(7)[it] = (uint32_t)j;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 template <int R>
 __device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase,
                                           Items<R> items, DevWork* work, unsigned long long& steps) {
   if constexpr (R == 1)
     rs1_group_job(S, M, j, ibase, items, work, steps);
   else
-    rs_group_job<R>(S, M, j, ibase, items, work, steps);
+    rs2_group_job(S, M, j, ibase, items, work, steps);
 }
 
 template <int R>
@@ -553,11 +540,11 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, DevWork* work,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st) {
   Items<R> items{item_buf, total_items};
-  // One robot: each warp expands whole actions, so the CTA takes as many warps
-  // as give every warp the same number of a job's actions (20 actions: 10
-  // warps of 2). Two robots use the full 16-warp grouping.
+  // Each warp expands whole actions, so the CTA takes as many warps as give
+  // every warp the same number of a job's actions (20 actions: 10 warps of 2;
+  // 400: 16 of 25).
   int block_a = kBlockA;
-  if (R == 1) {
+  {
     const int na = std::max(1, num_actions);
     const int per_warp = (na + kWarpsA - 1) / kWarpsA;
     block_a = 32 * ((na + per_warp - 1) / per_warp);

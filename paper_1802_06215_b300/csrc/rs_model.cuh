@@ -206,18 +206,95 @@ struct RSModel {
   // +0.0 to v, which is never -0.0, so skipping it (and its discount-table
   // load) leaves v unchanged.
   __device__ __forceinline__ float rollout(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
-    if constexpr (R == 1) return rollout_one(s, pmask, t0, steps);
+    if constexpr (R == 1)
+      return rollout_one(s, pmask, t0, steps);
+    else
+      return rollout_two(s, pmask, t0, steps);
+  }
+
+  // One robot's heuristic decision on the state both robots see: the
+  // nearest believed-good unsampled rock (Manhattan, lowest index on ties) and
+  // its distance, or -1 when there is none (the robot walks east).
+  __device__ __forceinline__ int nearest_target(int x, int y, uint32_t cand, int& bestd, int& bxy) const {
+    int best = -1;
+    bestd = 1 << 30;
+    bxy = 0;
+    while (cand) {
+      const int i = __ffs(cand) - 1;
+      cand &= cand - 1;
+      const int rxy = sh->rock_xy[i];
+      const int d = abs(x - (rxy & 0xFF)) + abs(y - (rxy >> 8));
+      if (d < bestd) {
+        bestd = d;
+        best = i;
+        bxy = rxy;
+      }
+    }
+    return best;
+  }
+
+  // Applies one robot's heuristic action (decided before either robot moved)
+  // to the unpacked state: E while no target (exit from the last column),
+  // else a step toward the target or Sample on it. Returns the reward.
+  __device__ __forceinline__ int apply_heuristic(int& x, int& y, bool& ex, int best, int bestd, int bxy,
+                                                 uint32_t& good, uint32_t& sampled) const {
+    if (ex) return 0;
+    if (best < 0) {
+      if (x == n - 1) {
+        ex = true;
+        return 10;
+      }
+      x += 1;
+      return 0;
+    }
+    const int rx = bxy & 0xFF, ry = bxy >> 8;
+    if (bestd == 0) {
+      const uint32_t bit = 1u << best;
+      const int r = (good & bit) ? 10 : -10;
+      good &= ~bit;
+      sampled |= bit;
+      return r;
+    }
+    if (rx > x)
+      x += 1;
+    else if (rx < x)
+      x -= 1;
+    else if (ry > y)
+      y += 1;
+    else
+      y -= 1;
+    return 0;
+  }
+
+  // The same rollout for two robots with the state unpacked into registers:
+  // both robots decide on the state before the step (the joint heuristic
+  // policy), robot 0 acts first (a rock both stand on is sampled by robot 0,
+  // robot 1's Sample then finds it bad), an exited robot does nothing, the
+  // rewards are summed, and the world ends when both have exited.
+  __device__ __forceinline__ float rollout_two(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
+    int x0 = (int)(s.pos[0] & 0xFFu), y0 = (int)((s.pos[0] >> 8) & 0xFFu);
+    int x1 = (int)(s.pos[1] & 0xFFu), y1 = (int)((s.pos[1] >> 8) & 0xFFu);
+    bool ex0 = (s.pos[0] >> 16) & 1u, ex1 = (s.pos[1] >> 16) & 1u;
+    uint32_t good = s.good, sampled = s.sampled;
     float v = 0.0f;
     int t = t0;
-    while (t < D && !terminal(s)) {
-      int a = policy(s, pmask);
-      uint64_t key;
-      float r = step(s, a, t, key);
-      if (r != 0.0f) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
+    while (t < D && !(ex0 && ex1)) {
+      const uint32_t cand = pmask & ~sampled;
+      int d0 = 0, b0 = 0, d1 = 0, b1 = 0;
+      const int i0 = ex0 ? -1 : nearest_target(x0, y0, cand, d0, b0);
+      const int i1 = ex1 ? -1 : nearest_target(x1, y1, cand, d1, b1);
+      int reward = apply_heuristic(x0, y0, ex0, i0, d0, b0, good, sampled);
+      reward += apply_heuristic(x1, y1, ex1, i1, d1, b1, good, sampled);
+      if (reward != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)reward));
       t += 1;
     }
     steps += (unsigned long long)(t - t0);
-    if (!terminal(s)) v = __fadd_rn(v, __fmul_rn(sh->G[D - t0], tail(s)));
+    if (!(ex0 && ex1)) {
+      float l = 0.0f;
+      if (!ex0) l = __fadd_rn(l, __fmul_rn(10.0f, sh->G[n - 1 - x0]));
+      if (!ex1) l = __fadd_rn(l, __fmul_rn(10.0f, sh->G[n - 1 - x1]));
+      v = __fadd_rn(v, __fmul_rn(sh->G[D - t0], l));
+    }
     return v;
   }
 
