@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -110,6 +111,16 @@ dsp_status dsp_create_model(const dsp_model_desc* d, dsp_model** out) {
       h->cell_rock[y * d->n + x] = (uint8_t)i;
     }
     build_thresholds(h->thresh, 2 * (d->n - 1) * (d->n - 1));
+    const int nn = d->n * d->n;
+    for (int i = 0; i < d->m; ++i) {
+      const int rx = h->rock_xy[i] & 0xFF, ry = h->rock_xy[i] >> 8;
+      for (int y = 0; y < d->n; ++y)
+        for (int x = 0; x < d->n; ++x) {
+          const int dist = std::abs(x - rx) + std::abs(y - ry);
+          const int mv = rx > x ? 1 : rx < x ? 3 : ry > y ? 0 : 2;
+          h->nkey[i * nn + y * d->n + x] = (uint16_t)((dist << 7) | (i << 2) | (dist == 0 ? 0 : mv));
+        }
+    }
   } else {
     if (d->P < 1 || d->P > kMaxPeds) {
       delete h;
@@ -153,6 +164,7 @@ dsp_status dsp_create_model(const dsp_model_desc* d, dsp_model** out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->dwork, sizeof(DevWork));
   if (e == cudaSuccess) e = cudaMemcpy(m->dmodel, h, sizeof(DevModel), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->dwork, 0, sizeof(DevWork));
+  if (e == cudaSuccess && h->robots > 0) e = rs_set_key_smem(h->robots, rs_key_words(h));
   if (e != cudaSuccess) {
     dsp_status st = cuda_fail(e, "dsp_create_model");
     dsp_destroy_model(m);
@@ -419,7 +431,8 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
       if (e == cudaSuccess && car_items) e = launch_car_rollout_mlp_items(m, djobs, ci, counters + 1, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
-      e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, m->dwork, djobs, (const long long*)dunits, dorder,
+      e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, rs_key_words(h), m->dwork, djobs,
+                           (const long long*)dunits, dorder,
                            n_jobs,
                            plan.total_items, items, counters, m->plan_step, m->num_sms, block_b,
                            m->policy_on ? m->policy : nullptr, st);

@@ -34,7 +34,14 @@ struct DevModel {
   float G[kGammaLen];                   // gamma^k in FP32
   uint64_t thresh[kMaxD2 + 1];          // sensor thresholds by squared distance
   float gauss[kGaussLen];               // inverse-normal table
+  // Heuristic-policy key of rock i seen from cell c, at [i * n * n + c]:
+  // Manhattan distance << 7 | i << 2 | the move toward the rock (0 N, 1 E,
+  // 2 S, 3 W; x first). The smallest key over a rock set is the nearest rock
+  // with the lowest index on ties, and carries the policy's move.
+  uint16_t nkey[kMaxRocks * kMaxSide * kMaxSide];
 };
+// Entries of the policy-key table: a row of n * n keys per rock.
+inline int rs_key_words(const DevModel* h) { return h->m * h->n * h->n; }
 
 // Workspace of a model: counters and the status word.
 struct DevWork {

@@ -473,9 +473,12 @@ __global__ void __launch_bounds__(512) rs_rollout_items_kernel(const DevModel* _
                                                               Items<R> items, unsigned int* chunk_head,
                                                               uint32_t plan_step) {
   __shared__ RSShared c;
+  extern __shared__ uint16_t rs_keys[];
   load_rs_consts(c, gm);
+  load_rs_keys(rs_keys, gm);
   __syncthreads();
-  const RSModel<R> M = make_rs<R>(gm, &c, plan_step);
+  RSModel<R> M = make_rs<R>(gm, &c, plan_step);
+  M.nkey = rs_keys;
   const int lane = threadIdx.x & 31;
   const long long nchunks = (items.total + 31) >> 5;
   unsigned long long steps = 0;
@@ -536,7 +539,7 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
 }
 
 template <int R>
-cudaError_t launch_two_phase(const DevModel* gm, int num_actions, DevWork* work, const dsp_leaf_job* jobs,
+cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st) {
   Items<R> items{item_buf, total_items};
@@ -559,12 +562,14 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, DevWork* work,
   if (policy != nullptr && R == 1)
     return launch_rs_rollout_mlp_items(gm, work, jobs, item_buf, total_items, counters + 1, policy, plan_step,
                                        num_sms, st);
+  // phase B keeps the policy-key table in shared memory (limit set by rs_set_key_smem)
+  const size_t key_bytes = sizeof(uint16_t) * (size_t)key_words;
   int per_sm_b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, rs_rollout_items_kernel<R>, block_b, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, rs_rollout_items_kernel<R>, block_b, key_bytes);
   long long chunks = (total_items + 31) / 32;
   long long want = (chunks + block_b / 32 - 1) / (block_b / 32);
   int grid_b = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm_b) * num_sms));
-  rs_rollout_items_kernel<R><<<grid_b, block_b, 0, st>>>(gm, work, jobs, items, counters + 1, plan_step);
+  rs_rollout_items_kernel<R><<<grid_b, block_b, key_bytes, st>>>(gm, work, jobs, items, counters + 1, plan_step);
   return cudaGetLastError();
 }
 
@@ -665,8 +670,11 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
   __shared__ long long s_ticket;
   __shared__ unsigned int s_plan_step;
   __shared__ int s_work, s_exit;
+  extern __shared__ uint16_t rs_keys[];
   load_rs_consts(S.c, gm);
+  load_rs_keys(rs_keys, gm);
   RSModel<R> M = make_rs<R>(gm, &S.c, 0u);  // each job carries its own plan step
+  M.nkey = rs_keys;
   const int tid = threadIdx.x, lane = tid & 31;
   unsigned long long steps = 0, last_work = global_ns();
   __syncthreads();
@@ -760,34 +768,58 @@ size_t rs_queue_slot_words(int robots, int num_actions) {
   return (size_t)rs_item_fields(robots) * (size_t)kMaxScen * (size_t)num_actions;
 }
 
-int rs_queue_blocks_per_sm(int robots) {
+// The persistent kernel keeps the policy-key table in dynamic shared memory.
+// The queue sets the kernel's shared-memory limit when it is created, before
+// any capture (rs_queue_blocks_per_sm).
+template <int R>
+static cudaError_t rs_queue_smem(int key_words, size_t& bytes) {
+  bytes = sizeof(uint16_t) * (size_t)key_words;
+  if (bytes + sizeof(RSGroupSmem) > 48 * 1024)
+    return cudaFuncSetAttribute(rs_queue_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+int rs_queue_blocks_per_sm(int robots, int key_words) {
   int n = 0;
-  if (robots == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_queue_kernel<1>, kBlockA, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_queue_kernel<2>, kBlockA, 0);
+  size_t bytes = 0;
+  if (robots == 1) {
+    if (rs_queue_smem<1>(key_words, bytes) == cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_queue_kernel<1>, kBlockA, bytes);
+  } else {
+    if (rs_queue_smem<2>(key_words, bytes) == cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rs_queue_kernel<2>, kBlockA, bytes);
+  }
   return n > 0 ? n : 1;
 }
 
-cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, QueueRing ring, unsigned long long* head,
-                            uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy, unsigned long long idle_ns,
-                            int grid, cudaStream_t st) {
+cudaError_t launch_rs_queue(const DevModel* gm, int robots, int key_words, DevWork* work, QueueRing ring,
+                            unsigned long long* head, uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy,
+                            unsigned long long idle_ns, int grid, cudaStream_t st) {
+  const size_t bytes = sizeof(uint16_t) * (size_t)key_words;
   if (robots == 1)
-    rs_queue_kernel<1><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, scratch, slot_words, jcopy, idle_ns);
+    rs_queue_kernel<1><<<grid, kBlockA, bytes, st>>>(gm, work, ring, head, scratch, slot_words, jcopy, idle_ns);
   else
-    rs_queue_kernel<2><<<grid, kBlockA, 0, st>>>(gm, work, ring, head, scratch, slot_words, jcopy, idle_ns);
+    rs_queue_kernel<2><<<grid, kBlockA, bytes, st>>>(gm, work, ring, head, scratch, slot_words, jcopy, idle_ns);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, DevWork* work,
+cudaError_t rs_set_key_smem(int robots, int key_words) {
+  const size_t bytes = sizeof(uint16_t) * (size_t)key_words;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (robots == 1)
+    return cudaFuncSetAttribute(rs_rollout_items_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaFuncSetAttribute(rs_rollout_items_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, int key_words, DevWork* work,
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf, unsigned int* counters, uint32_t plan_step,
                              int num_sms, int block_b, const void* policy, cudaStream_t st) {
   if (robots == 1)
-    return launch_two_phase<1>(gm, num_actions, work, jobs, item_base, order, n_jobs, total_items, item_buf,
-                               counters, plan_step, num_sms, block_b, policy, st);
-  return launch_two_phase<2>(gm, num_actions, work, jobs, item_base, order, n_jobs, total_items, item_buf, counters,
-                             plan_step, num_sms, block_b, nullptr, st);
+    return launch_two_phase<1>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items,
+                               item_buf, counters, plan_step, num_sms, block_b, policy, st);
+  return launch_two_phase<2>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items, item_buf,
+                             counters, plan_step, num_sms, block_b, nullptr, st);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,
@@ -908,7 +940,8 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kNoAllocCounterBytes, st);
   if (e == cudaSuccess) {
     int block_b = m->tune_block > 0 ? m->tune_block : 256;
-    e = launch_rs_expand(m->dmodel, m->host->robots, m->host->num_actions, m->dwork, djobs, dbase, nullptr, n_jobs,
+    e = launch_rs_expand(m->dmodel, m->host->robots, m->host->num_actions, rs_key_words(m->host), m->dwork, djobs,
+                         dbase, nullptr, n_jobs,
                          plan.total_items, items,
                          counters, m->plan_step, m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st);
   }

@@ -14,7 +14,11 @@ int rs_item_fields(int robots);
 // policy: learned pi0 for the rollout phase (one robot), or null for the
 // heuristic policy.
 // order: phase A takes jobs in this order (null: index order).
-cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, DevWork* work,
+// Raises the rollout phase's dynamic shared-memory limit to hold the model's
+// policy-key table (m * n * n keys); called once when the model is created.
+cudaError_t rs_set_key_smem(int robots, int key_words);
+// key_words: entries of the model's policy-key table, m * n * n.
+cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, int key_words, DevWork* work,
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
@@ -43,10 +47,10 @@ struct QueueRing {
   int cap;
 };
 size_t rs_queue_slot_words(int robots, int num_actions);
-int rs_queue_blocks_per_sm(int robots);
-cudaError_t launch_rs_queue(const DevModel* gm, int robots, DevWork* work, QueueRing ring, unsigned long long* head,
-                            uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy, unsigned long long idle_ns,
-                            int grid, cudaStream_t st);
+int rs_queue_blocks_per_sm(int robots, int key_words);
+cudaError_t launch_rs_queue(const DevModel* gm, int robots, int key_words, DevWork* work, QueueRing ring,
+                            unsigned long long* head, uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy,
+                            unsigned long long idle_ns, int grid, cudaStream_t st);
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,
                            const int32_t* actions, int depth, uint32_t* out, int out_cap, uint64_t* keys,

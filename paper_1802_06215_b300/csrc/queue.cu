@@ -59,7 +59,8 @@ dsp_status build_graph(dsp_queue* q) {
   cudaGraph_t g;
   cudaError_t e = cudaStreamBeginCapture(q->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_queue: begin capture");
-  cudaError_t el = launch_rs_queue(q->m->dmodel, q->m->host->robots, q->m->dwork, q->ring, q->d_head,
+  cudaError_t el = launch_rs_queue(q->m->dmodel, q->m->host->robots, rs_key_words(q->m->host), q->m->dwork,
+                                   q->ring, q->d_head,
                                    q->d_scratch, q->slot_words, q->d_jcopy, q->idle_ns, q->grid,
                                    q->stream);
   e = cudaStreamEndCapture(q->stream, &g);
@@ -141,7 +142,7 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
     q->ring.plan_step = (unsigned int*)(q->ring.jobs + capacity);
     q->ring.close = q->ring.plan_step + capacity;
     q->ring.cap = capacity;
-    q->grid = rs_queue_blocks_per_sm(m->host->robots) * m->num_sms;
+    q->grid = rs_queue_blocks_per_sm(m->host->robots, rs_key_words(m->host)) * m->num_sms;
     q->slot_words = rs_queue_slot_words(m->host->robots, m->host->num_actions);
     e = cudaMalloc(&q->d_head, sizeof(unsigned long long));
   }

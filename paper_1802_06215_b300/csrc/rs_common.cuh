@@ -13,12 +13,20 @@ __device__ __forceinline__ void load_rs_consts(RSShared& c, const DevModel* gm) 
   for (int k = threadIdx.x; k < kMaxSide * kMaxSide; k += blockDim.x) c.cell_rock[k] = gm->cell_rock[k];
 }
 
+// Copies the policy-key table into shared memory (no barrier).
+__device__ __forceinline__ void load_rs_keys(uint16_t* dst, const DevModel* gm) {
+  const int total = gm->m * gm->n * gm->n;
+  for (int k = threadIdx.x; k < total; k += blockDim.x) dst[k] = gm->nkey[k];
+}
+
 template <int R>
 __device__ __forceinline__ RSModel<R> make_rs(const DevModel* gm, const RSShared* c, uint32_t plan_step) {
   RSModel<R> M;
   M.sh = c;
   M.thresh = gm->thresh;
   M.n = gm->n;
+  M.nn = gm->n * gm->n;
+  M.nkey = gm->nkey;
   M.m = gm->m;
   M.per = gm->per_robot;
   M.D = gm->D;

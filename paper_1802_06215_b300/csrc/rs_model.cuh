@@ -34,7 +34,8 @@ template <int R>
 struct RSModel {
   const RSShared* sh;
   const uint64_t* thresh;  // global, read through the read-only path
-  int n, m, per, D;
+  const uint16_t* nkey;    // policy keys of (rock, cell), in shared or global memory
+  int n, nn, m, per, D;
   uint64_t seed;
   uint32_t plan_step;
 
@@ -212,34 +213,30 @@ struct RSModel {
       return rollout_two(s, pmask, t0, steps);
   }
 
-  // One robot's heuristic decision on the state both robots see: the
-  // nearest believed-good unsampled rock (Manhattan, lowest index on ties) and
-  // its distance, or -1 when there is none (the robot walks east).
-  __device__ __forceinline__ int nearest_target(int x, int y, uint32_t cand, int& bestd, int& bxy) const {
-    int best = -1;
-    bestd = 1 << 30;
-    bxy = 0;
-    while (cand) {
-      const int i = __ffs(cand) - 1;
-      cand &= cand - 1;
-      const int rxy = sh->rock_xy[i];
-      const int d = abs(x - (rxy & 0xFF)) + abs(y - (rxy >> 8));
-      if (d < bestd) {
-        bestd = d;
-        best = i;
-        bxy = rxy;
-      }
-    }
-    return best;
+  // The heuristic's decision for one robot at cell y*n+x among the non-empty
+  // rock set cand: the smallest key of the model's policy-key table, i.e. the
+  // nearest rock (Manhattan, lowest index on ties) with its distance and the
+  // move toward it. Rocks are visited from the highest index down; the key
+  // order does the tie-breaking.
+  __device__ __forceinline__ int nearest_key(int cell, uint32_t cand) const {
+    int key = 0xFFFF;
+    const uint16_t* col = nkey + cell;
+    do {
+      const int i = 31 - __clz(cand);
+      cand ^= 1u << i;
+      key = min(key, (int)col[i * nn]);
+    } while (cand);
+    return key;
   }
 
-  // Applies one robot's heuristic action (decided before either robot moved)
-  // to the unpacked state: E while no target (exit from the last column),
-  // else a step toward the target or Sample on it. Returns the reward.
-  __device__ __forceinline__ int apply_heuristic(int& x, int& y, bool& ex, int best, int bestd, int bxy,
-                                                 uint32_t& good, uint32_t& sampled) const {
+  // Applies one robot's heuristic action (decided on the state before either
+  // robot moved) to the unpacked state: E while no target is left (exit from
+  // the last column), else the key's move, or Sample when the key's distance
+  // is 0. Returns the reward.
+  __device__ __forceinline__ int apply_heuristic(int& x, int& y, bool& ex, int key, uint32_t& good,
+                                                 uint32_t& sampled) const {
     if (ex) return 0;
-    if (best < 0) {
+    if (key == 0xFFFF) {
       if (x == n - 1) {
         ex = true;
         return 10;
@@ -247,22 +244,18 @@ struct RSModel {
       x += 1;
       return 0;
     }
-    const int rx = bxy & 0xFF, ry = bxy >> 8;
-    if (bestd == 0) {
-      const uint32_t bit = 1u << best;
+    if (key < 128) {
+      const uint32_t bit = 1u << (key >> 2);
       const int r = (good & bit) ? 10 : -10;
       good &= ~bit;
       sampled |= bit;
       return r;
     }
-    if (rx > x)
-      x += 1;
-    else if (rx < x)
-      x -= 1;
-    else if (ry > y)
-      y += 1;
+    const int a = key & 3;
+    if (a & 1)
+      x += 2 - a;
     else
-      y -= 1;
+      y += 1 - a;
     return 0;
   }
 
@@ -280,11 +273,13 @@ struct RSModel {
     int t = t0;
     while (t < D && !(ex0 && ex1)) {
       const uint32_t cand = pmask & ~sampled;
-      int d0 = 0, b0 = 0, d1 = 0, b1 = 0;
-      const int i0 = ex0 ? -1 : nearest_target(x0, y0, cand, d0, b0);
-      const int i1 = ex1 ? -1 : nearest_target(x1, y1, cand, d1, b1);
-      int reward = apply_heuristic(x0, y0, ex0, i0, d0, b0, good, sampled);
-      reward += apply_heuristic(x1, y1, ex1, i1, d1, b1, good, sampled);
+      int k0 = 0xFFFF, k1 = 0xFFFF;
+      if (cand != 0) {
+        if (!ex0) k0 = nearest_key(y0 * n + x0, cand);
+        if (!ex1) k1 = nearest_key(y1 * n + x1, cand);
+      }
+      int reward = apply_heuristic(x0, y0, ex0, k0, good, sampled);
+      reward += apply_heuristic(x1, y1, ex1, k1, good, sampled);
       if (reward != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)reward));
       t += 1;
     }
@@ -302,8 +297,8 @@ struct RSModel {
   // The heuristic policy only moves and samples, and its moves never leave
   // the map except E from the last column (the exit), so each step is one
   // branch on the action: E while no believed-good unsampled rock is left,
-  // else a step toward the nearest one or Sample on it. Rewards, their order
-  // and the step count are those of step() and policy().
+  // else the policy key's move toward the nearest one, or Sample on it.
+  // Rewards, their order and the step count are those of step() and policy().
   __device__ __forceinline__ float rollout_one(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
     const uint32_t p0 = s.pos[0];
     int x = (int)(p0 & 0xFFu), y = (int)((p0 >> 8) & 0xFFu);
@@ -313,45 +308,29 @@ struct RSModel {
     int t = t0;
     while (t < D && !ex) {
       const uint32_t cand = pmask & ~sampled;
-      int reward = 0;
       if (cand == 0) {
         if (x == n - 1) {
-          reward = 10;
+          v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], 10.0f));
           ex = true;
         } else {
           x += 1;
         }
       } else {
-        int best = 0, bestd = 1 << 30, bxy = 0;
-        uint32_t c = cand;
-        while (c) {
-          const int i = __ffs(c) - 1;
-          c &= c - 1;
-          const int rxy = sh->rock_xy[i];
-          const int d = abs(x - (rxy & 0xFF)) + abs(y - (rxy >> 8));
-          if (d < bestd) {
-            bestd = d;
-            best = i;
-            bxy = rxy;
-          }
-        }
-        const int rx = bxy & 0xFF, ry = bxy >> 8;
-        if (bestd == 0) {
-          const uint32_t bit = 1u << best;
-          reward = (good & bit) ? 10 : -10;
+        const int key = nearest_key(y * n + x, cand);
+        if (key < 128) {
+          const uint32_t bit = 1u << (key >> 2);
+          const float r = (good & bit) ? 10.0f : -10.0f;
           good &= ~bit;
           sampled |= bit;
-        } else if (rx > x) {
-          x += 1;
-        } else if (rx < x) {
-          x -= 1;
-        } else if (ry > y) {
-          y += 1;
+          v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
         } else {
-          y -= 1;
+          const int a = key & 3;
+          if (a & 1)
+            x += 2 - a;
+          else
+            y += 1 - a;
         }
       }
-      if (reward != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)reward));
       t += 1;
     }
     steps += (unsigned long long)(t - t0);

@@ -19,7 +19,13 @@ def dsp():
     return batch
 
 
-CONFIGS = {"rs7_8": I.rs7_8, "rs15_15": I.rs15_15, "mars15_15": I.mars15_15}
+def rs32_32():
+    """The largest map: 32x32 with 32 rocks, whose 64 KB policy-key table
+    needs the rollout kernels' opt-in shared memory."""
+    return I.grid_config(32, 32, K=100, D=120, seed=3)
+
+
+CONFIGS = {"rs7_8": I.rs7_8, "rs15_15": I.rs15_15, "mars15_15": I.mars15_15, "rs32_32": rs32_32}
 
 
 def _cmp_expand(g, o, n, tag=""):

@@ -43,7 +43,12 @@ def _run_threads(_dsp, q, jb, n_threads):
     assert not errors, errors
 
 
-@pytest.mark.parametrize("mk,njobs,threads", [(I.mars15_15, 48, 16), (I.rs15_15, 96, 16), (I.rs7_8, 40, 4)])
+def _rs32_32():
+    return I.grid_config(32, 32, K=100, D=120, seed=3)
+
+
+@pytest.mark.parametrize("mk,njobs,threads", [(I.mars15_15, 48, 16), (I.rs15_15, 96, 16), (I.rs7_8, 40, 4),
+                                              (_rs32_32, 24, 4)])
 def test_queue_matches_batch(env, mk, njobs, threads):
     torch, _dsp, batch = env
     cfg = mk()
