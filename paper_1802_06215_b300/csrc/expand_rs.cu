@@ -412,6 +412,18 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
   if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
+// Exact sum of an int64 over the full warp from three 32-bit warp reductions:
+// x = hi * 2^32 + lo with lo unsigned, and lo split in 16-bit halves, so no
+// partial sum of 32 lanes overflows.
+__device__ __forceinline__ long long warp_sum64(long long x) {
+  const uint32_t lo = (uint32_t)(unsigned long long)x;
+  const int hi = (int)(x >> 32);
+  const unsigned a = __reduce_add_sync(0xFFFFFFFFu, lo & 0xFFFFu);
+  const unsigned b = __reduce_add_sync(0xFFFFFFFFu, lo >> 16);
+  const int h = __reduce_add_sync(0xFFFFFFFFu, hi);
+  return (long long)h * 4294967296LL + (long long)b * 65536LL + (long long)a;
+}
+
 // Phase B for one 32-item chunk of the item list (one whole warp calls it).
 template <int R>
 __device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_leaf_job* __restrict__ jobs,
@@ -443,10 +455,23 @@ __device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_
       fu = to_fixed(u);
       fl = to_fixed(v);
     }
-    // runs of lanes with the same (job, slot) are contiguous: segmented scan
+    // runs of lanes with the same (job, slot) are contiguous
     const uint32_t pj = __shfl_up_sync(0xFFFFFFFFu, job, 1);
     const uint32_t ps = __shfl_up_sync(0xFFFFFFFFu, slot, 1);
     const uint32_t starts = __ballot_sync(0xFFFFFFFFu, lane == 0 || pj != job || ps != slot);
+    if (starts == 1u) {
+      // the whole chunk is one child (lane 0 always holds an item, so every
+      // lane does): one warp sum per value
+      fu = warp_sum64(fu);
+      fl = warp_sum64(fl);
+      if (lane == 0 && ok) {
+        const dsp_leaf_job* J = jobs + job;
+        atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)fu);
+        atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)fl);
+      }
+      return;
+    }
+    // else a segmented scan
     const uint32_t le = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
     const int lo = 31 - __clz(starts & le);
 #pragma unroll
@@ -468,7 +493,7 @@ __device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_
 }
 
 template <int R>
-__global__ void __launch_bounds__(512) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__global__ void __launch_bounds__(512, 4) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                               const dsp_leaf_job* __restrict__ jobs,
                                                               Items<R> items, unsigned int* chunk_head,
                                                               uint32_t plan_step) {

@@ -161,32 +161,33 @@ struct RSModel {
     return robot_policy(s, 0, pmask) * per + robot_policy(s, 1, pmask);
   }
 
-  // u(phi): each good rock at its nearest live robot's Manhattan distance,
-  // then each live robot's exit, summed in that order in FP32.
+  // u(phi): each good rock (of the m) at its nearest live robot's Manhattan
+  // distance, read from the policy-key table, then each live robot's exit,
+  // summed in that order in FP32.
   __device__ __forceinline__ float upper(const RSS& s) const {
     if (terminal(s)) return 0.0f;
+    int cell[R];
+    bool live[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t p = s.pos[r];
+      live[r] = !((p >> 16) & 1u);
+      cell[r] = (int)(p & 0xFFu) + (int)((p >> 8) & 0xFFu) * n;
+    }
     float u = 0.0f;
-    uint32_t g = s.good;
+    uint32_t g = s.good & (m == 32 ? 0xFFFFFFFFu : (1u << m) - 1u);
     while (g) {
-      int i = __ffs(g) - 1;
+      const int i = __ffs(g) - 1;
       g &= g - 1;
-      int rxy = sh->rock_xy[i];
       int bestd = 1 << 30;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        uint32_t p = s.pos[r];
-        if (!((p >> 16) & 1u)) {
-          int d = abs((int)(p & 0xFFu) - (rxy & 0xFF)) + abs((int)((p >> 8) & 0xFFu) - (rxy >> 8));
-          bestd = d < bestd ? d : bestd;
-        }
-      }
+      for (int r = 0; r < R; ++r)
+        if (live[r]) bestd = min(bestd, (int)nkey[i * nn + cell[r]] >> 7);
       u = __fadd_rn(u, __fmul_rn(10.0f, sh->G[bestd]));
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      uint32_t p = s.pos[r];
-      if (!((p >> 16) & 1u)) u = __fadd_rn(u, __fmul_rn(10.0f, sh->G[n - 1 - (int)(p & 0xFFu)]));
-    }
+    for (int r = 0; r < R; ++r)
+      if (live[r]) u = __fadd_rn(u, __fmul_rn(10.0f, sh->G[n - 1 - (int)(s.pos[r] & 0xFFu)]));
     return u;
   }
 
@@ -303,35 +304,36 @@ struct RSModel {
     const uint32_t p0 = s.pos[0];
     int x = (int)(p0 & 0xFFu), y = (int)((p0 >> 8) & 0xFFu);
     bool ex = (p0 >> 16) & 1u;
-    uint32_t good = s.good, sampled = s.sampled;
+    uint32_t good = s.good, cand = pmask & ~s.sampled;  // cand loses each sampled rock
     float v = 0.0f;
     int t = t0;
-    while (t < D && !ex) {
-      const uint32_t cand = pmask & ~sampled;
-      if (cand == 0) {
-        if (x == n - 1) {
-          v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], 10.0f));
-          ex = true;
-        } else {
+    if (!ex) {
+      for (; t < D; ++t) {
+        if (cand == 0) {
+          if (x == n - 1) {
+            v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], 10.0f));
+            ex = true;
+            ++t;
+            break;
+          }
           x += 1;
-        }
-      } else {
-        const int key = nearest_key(y * n + x, cand);
-        if (key < 128) {
-          const uint32_t bit = 1u << (key >> 2);
-          const float r = (good & bit) ? 10.0f : -10.0f;
-          good &= ~bit;
-          sampled |= bit;
-          v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
         } else {
-          const int a = key & 3;
-          if (a & 1)
-            x += 2 - a;
-          else
-            y += 1 - a;
+          const int key = nearest_key(y * n + x, cand);
+          if (key < 128) {
+            const uint32_t bit = 1u << (key >> 2);
+            const float r = (good & bit) ? 10.0f : -10.0f;
+            good &= ~bit;
+            cand &= ~bit;
+            v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
+          } else {
+            const int a = key & 3;
+            if (a & 1)
+              x += 2 - a;
+            else
+              y += 1 - a;
+          }
         }
       }
-      t += 1;
     }
     steps += (unsigned long long)(t - t0);
     if (!ex) v = __fadd_rn(v, __fmul_rn(sh->G[D - t0], __fmul_rn(10.0f, sh->G[n - 1 - x])));
