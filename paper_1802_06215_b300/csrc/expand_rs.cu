@@ -138,10 +138,12 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
         code = (int)(key & 3u) + 3 * (int)(key >> 62);
         codes[p] = (uint8_t)code;
       }
+      // codes held by the chunk (warp-uniform): absent codes are skipped
+      const uint32_t present = __reduce_or_sync(0xFFFFFFFFu, code < kC ? 1u << code : 0u);
 #pragma unroll
       for (int c = 0; c < kC; ++c) {
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
-        if (b) {
+        if (present & (1u << c)) {
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
           if (cnt[c] == 0) first[c] = w * 32 + __ffs(b) - 1;
           cnt[c] += __popc(b);
           rsum[c] += __reduce_add_sync(0xFFFFFFFFu, code == c ? rint : 0);
@@ -204,12 +206,14 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
       int q = 0, mycid = 0;
 #pragma unroll
       for (int c = 0; c < kC; ++c) {
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
-        if (code == c) {
-          q = off[c] + run[c] + __popc(b & lt);
-          mycid = cid[c];
+        if (cnt[c] > 0) {  // the action's codes (warp-uniform)
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
+          if (code == c) {
+            q = off[c] + run[c] + __popc(b & lt);
+            mycid = cid[c];
+          }
+          run[c] += __popc(b);
         }
-        run[c] += __popc(b);
       }
       if (p < n) {
         RSS s;

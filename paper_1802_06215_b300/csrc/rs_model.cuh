@@ -233,9 +233,9 @@ struct RSModel {
   // Applies one robot's heuristic action (decided on the state before either
   // robot moved) to the unpacked state: E while no target is left (exit from
   // the last column), else the key's move, or Sample when the key's distance
-  // is 0. Returns the reward.
+  // is 0 (the rock leaves the candidate set). Returns the reward.
   __device__ __forceinline__ int apply_heuristic(int& x, int& y, bool& ex, int key, uint32_t& good,
-                                                 uint32_t& sampled) const {
+                                                 uint32_t& cand) const {
     if (ex) return 0;
     if (key == 0xFFFF) {
       if (x == n - 1) {
@@ -249,7 +249,7 @@ struct RSModel {
       const uint32_t bit = 1u << (key >> 2);
       const int r = (good & bit) ? 10 : -10;
       good &= ~bit;
-      sampled |= bit;
+      cand &= ~bit;
       return r;
     }
     const int a = key & 3;
@@ -269,18 +269,17 @@ struct RSModel {
     int x0 = (int)(s.pos[0] & 0xFFu), y0 = (int)((s.pos[0] >> 8) & 0xFFu);
     int x1 = (int)(s.pos[1] & 0xFFu), y1 = (int)((s.pos[1] >> 8) & 0xFFu);
     bool ex0 = (s.pos[0] >> 16) & 1u, ex1 = (s.pos[1] >> 16) & 1u;
-    uint32_t good = s.good, sampled = s.sampled;
+    uint32_t good = s.good, cand = pmask & ~s.sampled;  // cand loses each sampled rock
     float v = 0.0f;
     int t = t0;
     while (t < D && !(ex0 && ex1)) {
-      const uint32_t cand = pmask & ~sampled;
       int k0 = 0xFFFF, k1 = 0xFFFF;
       if (cand != 0) {
         if (!ex0) k0 = nearest_key(y0 * n + x0, cand);
         if (!ex1) k1 = nearest_key(y1 * n + x1, cand);
       }
-      int reward = apply_heuristic(x0, y0, ex0, k0, good, sampled);
-      reward += apply_heuristic(x1, y1, ex1, k1, good, sampled);
+      int reward = apply_heuristic(x0, y0, ex0, k0, good, cand);
+      reward += apply_heuristic(x1, y1, ex1, k1, good, cand);
       if (reward != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)reward));
       t += 1;
     }
