@@ -42,6 +42,7 @@ constexpr int kCodes = 18;            // observation code z + 9 * terminal, z <=
 struct RSGroupSmem {
   RSShared c;
   uint32_t leaf[5][kMaxScen];          // the leaf's states, field-major
+  uint32_t sense[2][kMaxScen];         // each scenario's sensor word per robot at the leaf's depth
   // two robots, per warp and observation code of the warp's current action:
   int wcnt[kWarpsA][kCodes];           // scenarios holding the code
   int wfirst[kWarpsA][kCodes];         // first position of the code
@@ -80,6 +81,8 @@ __device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& 
     S.leaf[2][p] = s.good;
     S.leaf[3][p] = s.sampled;
     S.leaf[4][p] = s.scen;
+#pragma unroll
+    for (int r = 0; r < R; ++r) S.sense[r][p] = M.sense_word(s.scen, depth, r);
     if (J.leaf_states != nullptr) M.store(s, J.leaf_states, n, p);
   }
   if (tid == 0) {
@@ -134,7 +137,8 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
         s.scen = S.leaf[4][p];
         if (!M.terminal(s)) steps += 1;
         uint64_t key;
-        rint = (int)M.step(s, aa, depth, key);
+        const uint32_t sw[2] = {S.sense[0][p], 0u};
+        rint = (int)M.step(s, aa, depth, key, sw);
         code = (int)(key & 3u) + 3 * (int)(key >> 62);
         codes[p] = (uint8_t)code;
       }
@@ -289,7 +293,8 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
         s.scen = S.leaf[4][p];
         if (!M.terminal(s)) steps += 1;
         uint64_t key;
-        rint = (int)M.step(s, aa, depth, key);
+        const uint32_t sw[2] = {S.sense[0][p], S.sense[1][p]};
+        rint = (int)M.step(s, aa, depth, key, sw);
         code = (int)(key & 0xFu) + 9 * (int)(key >> 62);
         codes[p] = (uint8_t)code;
       }

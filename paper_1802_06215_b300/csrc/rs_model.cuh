@@ -45,7 +45,12 @@ struct RSModel {
     return t;
   }
 
-  __device__ __forceinline__ int robot_step(RSS& s, int r, int a, int depth, int& z) const {
+  // One robot's part of g. A Sense reading draws the scenario's sensor word
+  // (Philox purpose 2, element r) unless the caller passes it in `sense`:
+  // the word depends on the scenario and the depth only, so a leaf's actions
+  // share it.
+  __device__ __forceinline__ int robot_step(RSS& s, int r, int a, int depth, int& z,
+                                            const uint32_t* sense = nullptr) const {
     z = 0;
     uint32_t p = s.pos[r];
     if ((p >> 16) & 1u) return 0;
@@ -73,8 +78,8 @@ struct RSModel {
       int i = a - 5;
       int rx = sh->rock_xy[i] & 0xFF, ry = sh->rock_xy[i] >> 8;
       int dx = x - rx, dy = y - ry;
-      U4 rnd = scen_random(seed, s.scen, (uint32_t)depth, 2u, (uint32_t)r, plan_step);
-      bool correct = (uint64_t)rnd.x < __ldg(thresh + dx * dx + dy * dy);
+      const uint32_t u = sense != nullptr ? sense[r] : sense_word(s.scen, depth, r);
+      bool correct = (uint64_t)u < __ldg(thresh + dx * dx + dy * dy);
       bool is_good = (s.good >> i) & 1u;
       z = (correct == is_good) ? 1 : 2;
     }
@@ -82,16 +87,23 @@ struct RSModel {
     return reward;
   }
 
-  // g(s, a, phi_depth); returns the reward, writes the observation key.
-  __device__ __forceinline__ float step(RSS& s, int a, int depth, uint64_t& key) const {
+  // The sensor word of scenario `scen` for robot r at `depth`.
+  __device__ __forceinline__ uint32_t sense_word(uint32_t scen, int depth, int r) const {
+    return scen_random(seed, scen, (uint32_t)depth, 2u, (uint32_t)r, plan_step).x;
+  }
+
+  // g(s, a, phi_depth); returns the reward, writes the observation key. The
+  // robots' sensor words may be passed in (sense_word of each robot).
+  __device__ __forceinline__ float step(RSS& s, int a, int depth, uint64_t& key,
+                                        const uint32_t* sense = nullptr) const {
     int z0, z1 = 0, rew;
     if (R == 1) {
-      rew = robot_step(s, 0, a, depth, z0);
+      rew = robot_step(s, 0, a, depth, z0, sense);
       key = (uint64_t)z0;
     } else {
       int a0 = a / per, a1 = a - a0 * per;
-      rew = robot_step(s, 0, a0, depth, z0);
-      rew += robot_step(s, 1, a1, depth, z1);
+      rew = robot_step(s, 0, a0, depth, z0, sense);
+      rew += robot_step(s, 1, a1, depth, z1, sense);
       key = (uint64_t)(z0 * 3 + z1);
     }
     if (terminal(s)) key |= kTermBit;
