@@ -180,6 +180,12 @@ void dsp_destroy_model(dsp_model* m) {
   if (m->dwork) cudaFree(m->dwork);
   if (m->policy) cudaFree(m->policy);
   for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
+  for (dsp_staging_slot* sl : m->staging) {
+    cudaEventSynchronize(sl->done);
+    cudaEventDestroy(sl->done);
+    cudaFreeHost(sl->host);
+    delete sl;
+  }
   if (m->queue) dsp_queue_destroy(m->queue);
   if (m->pool) cudaMemPoolDestroy(m->pool);
   delete m->host;
@@ -385,6 +391,44 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// A pinned staging slot of at least `bytes` whose last copy has run, or a new
+// one; null if pinned memory cannot be had (the caller then copies from its
+// own pageable buffers). Pinned sources keep cudaMemcpyAsync asynchronous, so
+// a call returns without waiting for the work queued before it.
+static dsp_staging_slot* take_staging(dsp_model* m, size_t bytes) {
+  std::lock_guard<std::mutex> lock(m->staging_mu);
+  for (dsp_staging_slot* sl : m->staging)
+    if (!sl->busy && sl->cap >= bytes && cudaEventQuery(sl->done) == cudaSuccess) {
+      sl->busy = true;
+      return sl;
+    }
+  dsp_staging_slot* sl = new dsp_staging_slot();
+  sl->cap = std::max<size_t>((bytes + 0xFFFFF) & ~(size_t)0xFFFFF, 1 << 20);
+  if (cudaHostAlloc(&sl->host, sl->cap, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    delete sl;
+    return nullptr;
+  }
+  if (cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(sl->host);
+    delete sl;
+    return nullptr;
+  }
+  sl->busy = true;
+  m->staging.push_back(sl);
+  return sl;
+}
+
+// Marks the slot's copy (already enqueued on st) and frees the slot for reuse
+// once that copy has run.
+static cudaError_t release_staging(dsp_model* m, dsp_staging_slot* sl, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(sl->done, st);
+  std::lock_guard<std::mutex> lock(m->staging_mu);
+  sl->busy = false;
+  return e;
+}
+
 // Copies the job table (and the car's unit table or Rock Sample's item
 // offsets) to stream-ordered device memory, takes the Rock Sample item list
 // from the same allocation and launches the expansion kernels.
@@ -406,16 +450,35 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   void* dunits = buf + align256(jb);
   unsigned int* counters = (unsigned int*)(buf + align256(jb) + align256(ub));
   uint32_t* items = (uint32_t*)(buf + align256(jb) + align256(ub) + 256);
-  e = cudaMemcpyAsync(djobs, jobs, jb, cudaMemcpyHostToDevice, st);
   const int* dorder = car ? nullptr : (const int*)((const long long*)dunits + plan.item_base.size());
-  if (e == cudaSuccess && car)
-    e = cudaMemcpyAsync(dunits, plan.units.data(), ub, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && !car) {
-    e = cudaMemcpyAsync(dunits, plan.item_base.data(), sizeof(long long) * plan.item_base.size(),
-                        cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync((void*)dorder, plan.order.data(), sizeof(int) * plan.order.size(), cudaMemcpyHostToDevice,
-                          st);
+  // the job table and the unit table (or item offsets and order) in one copy
+  // from pinned staging laid out like the device buffer
+  const size_t hb = align256(jb) + ub;
+  dsp_staging_slot* sl = take_staging(m, hb);
+  if (sl != nullptr) {
+    unsigned char* hs = (unsigned char*)sl->host;
+    std::memcpy(hs, jobs, jb);
+    if (car) {
+      std::memcpy(hs + align256(jb), plan.units.data(), ub);
+    } else {
+      std::memcpy(hs + align256(jb), plan.item_base.data(), sizeof(long long) * plan.item_base.size());
+      std::memcpy(hs + align256(jb) + sizeof(long long) * plan.item_base.size(), plan.order.data(),
+                  sizeof(int) * plan.order.size());
+    }
+    e = cudaMemcpyAsync(buf, hs, hb, cudaMemcpyHostToDevice, st);
+    cudaError_t er = release_staging(m, sl, st);
+    if (e == cudaSuccess) e = er;
+  } else {
+    e = cudaMemcpyAsync(djobs, jobs, jb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && car)
+      e = cudaMemcpyAsync(dunits, plan.units.data(), ub, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !car) {
+      e = cudaMemcpyAsync(dunits, plan.item_base.data(), sizeof(long long) * plan.item_base.size(),
+                          cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void*)dorder, plan.order.data(), sizeof(int) * plan.order.size(),
+                            cudaMemcpyHostToDevice, st);
+    }
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 256, st);
   if (e == cudaSuccess) {

@@ -7,6 +7,15 @@
 
 #include "common.cuh"
 
+// Pinned host staging for one call's job table: reused once the copy that
+// last read it has run (its event).
+struct dsp_staging_slot {
+  void* host = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+};
+
 struct dsp_model {
   dsp_model_desc desc;
   dsp::DevModel* host = nullptr;     // host copy of the constant block
@@ -25,6 +34,8 @@ struct dsp_model {
   bool timing = false;               // record events around the expansion kernels
   std::mutex timing_mu;
   std::vector<cudaEvent_t> timing_events;  // start, end per dsp_expand_leaves call
+  std::mutex staging_mu;
+  std::vector<dsp_staging_slot*> staging;  // pinned copies of the calls' job tables
 };
 
 namespace dsp {
