@@ -711,23 +711,37 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
   M.nkey = rs_keys;
   const int tid = threadIdx.x, lane = tid & 31;
   unsigned long long steps = 0, last_work = global_ns();
+  unsigned int backoff = 256;  // idle sleep, doubled while nothing comes (ns)
   __syncthreads();
   while (true) {
-    // a new job from the ring, if one is published (no waiting)
-    if (tid == 0) {
+    // a new job from the ring, if one is published (no waiting); warp 0 reads
+    // the descriptor from host memory with all lanes at once
+    if (tid < 32) {
       long long ticket = -1;
-      const unsigned long long h = *(volatile unsigned long long*)head;
-      if (ld_acquire_sys(ring.seq + (h % ring.cap)) == h + 1 && atomicCAS(head, h, h + 1) == h) {
-        ticket = (long long)h;
-        const int slot = (int)(h % ring.cap);
+      if (lane == 0) {
+        const unsigned long long h = *(volatile unsigned long long*)head;
+        if (ld_acquire_sys(ring.seq + (h % ring.cap)) == h + 1 && atomicCAS(head, h, h + 1) == h)
+          ticket = (long long)h;
+      }
+      __syncwarp();
+      ticket = __shfl_sync(0xFFFFFFFFu, ticket, 0);
+      if (ticket >= 0) {
+        constexpr int kWords = (int)(sizeof(dsp_leaf_job) / 4);
+        const int slot = (int)(ticket % ring.cap);
         const volatile uint32_t* src = (const volatile uint32_t*)(ring.jobs + slot);
         uint32_t* dst = (uint32_t*)&S.J;
-        for (int w = 0; w < (int)(sizeof(dsp_leaf_job) / 4); ++w) dst[w] = src[w];
-        jcopy[slot] = S.J;
-        s_plan_step = *(volatile unsigned int*)(ring.plan_step + slot);
+        uint32_t* dcopy = (uint32_t*)(jcopy + slot);
+        for (int w = lane; w < kWords; w += 32) {
+          const uint32_t x = src[w];
+          dst[w] = x;
+          dcopy[w] = x;
+        }
+        if (lane == 0) s_plan_step = *(volatile unsigned int*)(ring.plan_step + slot);
       }
-      s_ticket = ticket;
-      s_work = 0;
+      if (lane == 0) {
+        s_ticket = ticket;
+        s_work = 0;
+      }
     }
     __syncthreads();
     const long long ticket = s_ticket;
@@ -785,7 +799,13 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       const bool busy = ticket >= 0 || s_work != 0;
       if (busy) last_work = now;
       s_exit = !busy && (*(volatile unsigned int*)ring.close != 0u || now - last_work > idle_ns);
-      if (!busy && !s_exit) __nanosleep(1000);
+      if (busy) backoff = 256;
+      if (!busy && !s_exit) {
+        // idle CTAs back off, so their polling leaves the working CTAs'
+        // issue slots and the shared claim words alone
+        __nanosleep(backoff);
+        backoff = min(backoff * 2u, 16384u);
+      }
     }
     __syncthreads();
     if (s_exit) break;
