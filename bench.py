@@ -44,7 +44,24 @@ WORKLOADS = {
                                          "jobs, |Phi_b|~U{1..500}, depth~U{0..10}", (16, 0.5, 1)),
     "car50": (inputs.car50, 1024, "car among 50 pedestrians, |A|=3, K=500, D=50; 1024 leaf jobs, "
                                   "|Phi_b|~U{1..500}, depth~U{0..10}", (4, 0.1, 0)),
+    # variants of the same kernels (--sweep)
+    "car6": (lambda: inputs.car_p(6), 1024, "car among 6 pedestrians, |A|=3, K=500, D=50; 1024 leaf jobs",
+             (4, 0.1, 0)),
+    "car12": (lambda: inputs.car_p(12), 1024, "car among 12 pedestrians, |A|=3, K=500, D=50; 1024 leaf jobs",
+              (4, 0.1, 0)),
+    "car20": (lambda: inputs.car_p(20), 1024, "car among 20 pedestrians, |A|=3, K=500, D=50; 1024 leaf jobs",
+              (4, 0.1, 0)),
+    "mars11_11": (inputs.mars11_11, 512, "two-robot Rock Sample 11x11, 11 rocks, |A|=256, K=500, D=90; 512 leaf "
+                                         "jobs", (16, 0.5, 1)),
+    "mars20_20": (inputs.mars20_20, 512, "two-robot Rock Sample 20x20, 20 rocks, |A|=625, K=500, D=90; 512 leaf "
+                                         "jobs", (16, 0.5, 1)),
+    "rs15_15_k100": (lambda: inputs.rs15_15_k(100), 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=100, D=90; "
+                                                         "4096 leaf jobs, |Phi_b|~U{1..100}", (4, 0.5, 0)),
+    "rs15_15_k250": (lambda: inputs.rs15_15_k(250), 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=250, D=90; "
+                                                         "4096 leaf jobs, |Phi_b|~U{1..250}", (4, 0.5, 0)),
 }
+SWEEP = ["car6", "car12", "car20", "car50", "rs15_15_k100", "rs15_15_k250", "rs15_15", "mars11_11", "mars15_15",
+         "mars20_20"]
 SMS, LANES_PER_SM, MAX_SM_MHZ = 148, 128, 2032.0
 try:
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
@@ -78,6 +95,7 @@ def parse():
     p.add_argument("--plan-seconds", type=float, default=0.1)
     p.add_argument("--learned-rollouts", type=int, default=0,
                    help="time only the learned-policy rollout kernel on this many start states and exit")
+    p.add_argument("--sweep", default="", help="'all' or comma-separated workloads: one line per variant")
     p.add_argument("--ref-step-seconds", type=float, default=60.0,
                    help="cap on the oracle's time per step in the reference arm")
     return p.parse_args()
@@ -549,6 +567,56 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def sweep(args):
+    """Variants of the same kernels (crowd sizes, map sizes and joint action
+    counts, numbers of scenarios): one JSON line per workload with its
+    device-resident rate, kernel time and ALU roofline fraction. Each point
+    times `--steps` expansions after `--warmup` (L2 flushed before each) and
+    counts algorithmic ops with the oracle on the leading jobs for 2 s."""
+    import torch
+    from paper_1802_06215_b300 import _dsp, batch, build
+    build.build()
+    peak_tops = SMS * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    names = args.sweep.split(",") if args.sweep != "all" else SWEEP
+    for name in names:
+        mk, njobs, desc, _ = WORKLOADS[name]
+        cfg = mk()
+        m = batch.Model(cfg)
+        jobs = inputs.job_stream(cfg, args.jobs or njobs, 1000)
+        jb = batch.JobBatch(m, jobs)
+        for _ in range(args.warmup):
+            jb.run()
+        torch.cuda.synchronize()
+        m.reset_counters()
+        _dsp.dsp_kernel_timing(m.h, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record()
+            jb.run()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        kms, calls = _dsp.dsp_kernel_timing(m.h, False)
+        steps, status = m.counters()
+        if status != 0:
+            raise RuntimeError(f"{name}: device status word {status}")
+        t_ms = sum(a.elapsed_time(b) for a, b in ev)
+        r1 = cpu_oracle_run(cfg, jobs, 2.0, 1)
+        ops = r1["ops"] / max(1, r1["steps"])
+        achieved = ops * (steps / args.steps) / (kms / calls / 1000.0) / 1e12
+        print(json.dumps({"sweep": name, "config": desc, "value": steps / (t_ms / 1000.0),
+                          "unit": "scenario-steps/s", "ms_per_step": t_ms / args.steps,
+                          "kernel_ms_per_launch": kms / calls, "scenario_steps_per_step": steps / args.steps,
+                          "leaf_expansions_per_s": len(jobs) / (t_ms / args.steps / 1000.0),
+                          "ops_per_scenario_step": ops, "roofline": {"bound": "alu", "achieved": achieved,
+                                                                     "peak": peak_tops, "unit": "Tops/s",
+                                                                     "frac": achieved / peak_tops},
+                          "cpu_oracle_1core": r1["steps"] / r1["seconds"]}), flush=True)
+        m.close()
+        del jb
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -561,6 +629,9 @@ def main():
     elif args.learned_rollouts:
         if rank == 0:
             learned_rollouts(args)
+    elif args.sweep:
+        if rank == 0:
+            sweep(args)
     else:
         run_ours(args, rank, world)
 

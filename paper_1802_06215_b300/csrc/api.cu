@@ -301,7 +301,7 @@ dsp_status dsp_set_tuning(dsp_model* m, int32_t block, int32_t tps) {
 dsp_status dsp_get_tuning(const dsp_model* m, int32_t* block, int32_t* tps) {
   if (!m || !block || !tps) return fail(DSP_E_INVALID, "dsp_get_tuning: NULL argument");
   *block = m->tune_block > 0 ? m->tune_block : 256;
-  *tps = m->tune_tps > 0 ? m->tune_tps : 32;
+  *tps = m->tune_tps > 0 ? m->tune_tps : (m->host->kind == DSP_MODEL_CAR ? car_default_tps(m->host->P) : 32);
   return DSP_OK;
 }
 

@@ -61,7 +61,7 @@ extern "C" dsp_status dsp_autotune(dsp_model* m, const dsp_leaf_job* jobs, int32
   m->tune_block = bb;
   m->tune_tps = bt;
   *best_block = bb > 0 ? bb : 256;
-  *best_tps = bt > 0 ? bt : 32;  // the default lane count (used by the car only)
+  *best_tps = bt > 0 ? bt : (m->host->kind == DSP_MODEL_CAR ? car_default_tps(m->host->P) : 32);  // car only
   *best_ms = best;
   return DSP_OK;
 }

@@ -32,9 +32,14 @@ __device__ __forceinline__ uint64_t splitmix_mix(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// Pairs a lane may own with TPS lanes per scenario: enough for kMaxPeds by
+// default, or KP when the model's crowd is known to fit (KP * TPS pairs).
 template <int TPS>
+constexpr int kDefaultPairs = (kMaxPeds / 2 + TPS - 1) / TPS;
+
+template <int TPS, int KP = kDefaultPairs<TPS>>
 struct CarLane {
-  static constexpr int kPairs = (kMaxPeds / 2 + TPS - 1) / TPS;  // pairs a lane may own
+  static constexpr int kPairs = KP;  // pairs a lane may own
   float px[2 * kPairs], py[2 * kPairs];
   // 2 bits per owned pedestrian: 64 bits once a lane owns more than 16
   using Goals = typename std::conditional<(2 * kPairs > 16), unsigned long long, uint32_t>::type;
@@ -45,7 +50,7 @@ struct CarLane {
   uint32_t scen;
 };
 
-template <int TPS>
+template <int TPS, int KP = kDefaultPairs<TPS>>
 struct CarModel {
   const CarShared* sh;
   int P, D;
@@ -62,7 +67,7 @@ struct CarModel {
   }
 
   // Loads scenario i of a state block into the lane's share of the group.
-  __device__ __forceinline__ void load(CarLane<TPS>& L, const uint32_t* b, int cap, int i) const {
+  __device__ __forceinline__ void load(CarLane<TPS, KP>& L, const uint32_t* b, int cap, int i) const {
     L.s = __uint_as_float(b[i]);
     uint32_t w1 = b[cap + i];
     L.v = (int)(w1 & 0xFFu);
@@ -70,7 +75,7 @@ struct CarModel {
     L.scen = b[2 * cap + i];
     L.goals = 0;
 #pragma unroll
-    for (int k = 0; k < CarLane<TPS>::kPairs; ++k) {
+    for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k) {
       int q = gl + k * TPS;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -79,7 +84,7 @@ struct CarModel {
           L.px[2 * k + e] = __uint_as_float(b[(size_t)(4 + j) * cap + i]);
           L.py[2 * k + e] = __uint_as_float(b[(size_t)(4 + P + j) * cap + i]);
           uint32_t gw = b[(size_t)(4 + 2 * P + j / 4) * cap + i];
-          L.goals |= (typename CarLane<TPS>::Goals)((gw >> (8 * (j % 4))) & 3u) << (2 * (2 * k + e));
+          L.goals |= (typename CarLane<TPS, KP>::Goals)((gw >> (8 * (j % 4))) & 3u) << (2 * (2 * k + e));
         } else {
           L.px[2 * k + e] = 0.0f;
           L.py[2 * k + e] = 0.0f;
@@ -90,7 +95,7 @@ struct CarModel {
 
   // Writes the group's scenario to slot i; lanes with valid = false write
   // nothing but still take part in the goal-word shuffles.
-  __device__ __forceinline__ void store(const CarLane<TPS>& L, uint32_t* b, int cap, int i, bool valid) const {
+  __device__ __forceinline__ void store(const CarLane<TPS, KP>& L, uint32_t* b, int cap, int i, bool valid) const {
     if (valid && gl == 0) {
       b[i] = __float_as_uint(L.s);
       b[cap + i] = (uint32_t)L.v | ((uint32_t)L.term << 8);
@@ -98,7 +103,7 @@ struct CarModel {
       b[3 * cap + i] = 0u;
     }
 #pragma unroll
-    for (int k = 0; k < CarLane<TPS>::kPairs; ++k) {
+    for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k) {
       int q = gl + k * TPS;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -112,13 +117,13 @@ struct CarModel {
     // goal words: four pedestrians (two pairs) per word; the lane owning the
     // word's first pair gathers the second pair's goals from its owner
 #pragma unroll
-    for (int k = 0; k < CarLane<TPS>::kPairs; ++k) {
+    for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k) {
       int q = gl + k * TPS;
       uint32_t mine = (uint32_t)(L.goals >> (4 * k)) & 15u;
       int q2 = q + 1;
       int src = gbase + (q2 % TPS);
       int k2 = q2 / TPS;
-      const typename CarLane<TPS>::Goals other_all = __shfl_sync(0xFFFFFFFFu, L.goals, src);
+      const typename CarLane<TPS, KP>::Goals other_all = __shfl_sync(0xFFFFFFFFu, L.goals, src);
       uint32_t other = (uint32_t)(other_all >> (4 * k2)) & 15u;
       if (valid && (q & 1) == 0 && 2 * q < P) {
         uint32_t w = (mine & 3u) | ((mine >> 2) << 8);
@@ -137,7 +142,7 @@ struct CarModel {
   // Returns the reward; sets danger (policy input of the next state) and, with
   // kKey, the observation key.
   template <bool kKey>
-  __device__ __forceinline__ float step(CarLane<TPS>& L, bool live, int a, int t, uint32_t ufail,
+  __device__ __forceinline__ float step(CarLane<TPS, KP>& L, bool live, int a, int t, uint32_t ufail,
                                         bool& danger, uint64_t& key) const {
     float r = 0.0f;
     bool fails = (uint64_t)ufail < fail_thresh;
@@ -150,7 +155,7 @@ struct CarModel {
     bool coll = false, dang = false;
     uint64_t ksum = 0;
 #pragma unroll
-    for (int k = 0; k < CarLane<TPS>::kPairs; ++k) {
+    for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k) {
       int q = gl + k * TPS;
       if (2 * q < P) {
         U4 rp = live ? scen_random(seed, L.scen, (uint32_t)t, 3u, (uint32_t)q, plan_step) : U4{0, 0, 0, 0};
@@ -211,13 +216,13 @@ struct CarModel {
     return r;
   }
 
-  __device__ __forceinline__ int policy(const CarLane<TPS>& L, bool danger) const {
+  __device__ __forceinline__ int policy(const CarLane<TPS, KP>& L, bool danger) const {
     return danger ? 2 : (L.v < 3 ? 0 : 1);
   }
 
   // u: the goal bonus at the earliest step the car could reach the goal
   // accelerating every step.
-  __device__ __forceinline__ float upper(const CarLane<TPS>& L) const {
+  __device__ __forceinline__ float upper(const CarLane<TPS, KP>& L) const {
     if (L.term) return 0.0f;
     float ss = L.s;
     int vv = L.v, t = 0;
@@ -231,11 +236,11 @@ struct CarModel {
   }
 
   // Danger ahead in the current state (policy input), group-wide.
-  __device__ __forceinline__ bool danger_now(const CarLane<TPS>& L) const {
+  __device__ __forceinline__ bool danger_now(const CarLane<TPS, KP>& L) const {
     float cx = __fadd_rn(-10.0f, L.s), cy = 20.0f;
     bool dang = false;
 #pragma unroll
-    for (int k = 0; k < CarLane<TPS>::kPairs; ++k) {
+    for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k) {
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         int j = 2 * (gl + k * TPS) + e;
@@ -252,7 +257,7 @@ struct CarModel {
   // the same number of iterations (until every group in the warp is done);
   // `valid` is false for lanes without a scenario. The action-failure words of
   // TPS depths are drawn at once, one per lane, and broadcast.
-  __device__ __forceinline__ float rollout(CarLane<TPS>& L, bool valid, bool danger, int t0,
+  __device__ __forceinline__ float rollout(CarLane<TPS, KP>& L, bool valid, bool danger, int t0,
                                            unsigned long long& steps) const {
     float v = 0.0f;
     int t = t0;
@@ -280,9 +285,10 @@ struct CarModel {
 };
 
 // A group's view of the model: TPS consecutive lanes share one scenario.
-template <int TPS>
-__device__ __forceinline__ CarModel<TPS> make_car_model(const DevModel* gm, const CarShared* sh, uint32_t plan_step) {
-  CarModel<TPS> M;
+template <int TPS, int KP = kDefaultPairs<TPS>>
+__device__ __forceinline__ CarModel<TPS, KP> make_car_model(const DevModel* gm, const CarShared* sh,
+                                                            uint32_t plan_step) {
+  CarModel<TPS, KP> M;
   M.sh = sh;
   M.P = gm->P;
   M.D = gm->D;

@@ -29,8 +29,8 @@ struct CarUnitSmem {
   dsp_leaf_job job;
 };
 
-template <int TPS>
-__global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
+template <int TPS, int KP = kDefaultPairs<TPS>>
+__global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                          const dsp_leaf_job* __restrict__ jobs,
                                                          const int4* __restrict__ units, int n_units,
                                                          unsigned int* head, uint32_t plan_step,
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(cons
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CarUnitSmem& S = *reinterpret_cast<CarUnitSmem*>(smem_raw);
   load_car_consts(S.c, gm);
-  CarModel<TPS> M = make_car_model<TPS>(gm, &S.c, plan_step);
+  CarModel<TPS, KP> M = make_car_model<TPS, KP>(gm, &S.c, plan_step);
   const int P = M.P;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int groups = nthr / TPS, g = tid / TPS;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(cons
     for (int base = 0; base < n; base += groups) {
       const int p = base + g;
       const bool valid = p < n;
-      CarLane<TPS> L;
+      CarLane<TPS, KP> L;
       if (valid) {
         M.load(L, job.parent, job.parent_cap, job.idx[p]);
       } else {
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(cons
         L.scen = 0;
         L.goals = 0;
 #pragma unroll
-        for (int k = 0; k < 2 * CarLane<TPS>::kPairs; ++k) L.px[k] = L.py[k] = 0.0f;
+        for (int k = 0; k < 2 * CarLane<TPS, KP>::kPairs; ++k) L.px[k] = L.py[k] = 0.0f;
       }
       bool danger = false;
       uint64_t key = 0;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256, TPS >= 16 ? 4 : 1) car_expand_kernel(cons
         uint32_t* ob = obs + (size_t)p * kCarObsWords;
         if (M.gl == 0) ob[0] = (uint32_t)L.v | ((uint32_t)L.term << 8);
 #pragma unroll
-        for (int k = 0; k < CarLane<TPS>::kPairs; ++k)
+        for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k)
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             int j = 2 * (M.gl + k * TPS) + e;
@@ -226,14 +226,15 @@ __global__ void __launch_bounds__(256) car_rollout_kernel(const DevModel* __rest
   if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
-template <int TPS>
+template <int TPS, int KP = kDefaultPairs<TPS>>
 cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units, unsigned int* head,
                        CarItems items, cudaStream_t st) {
   size_t smem = sizeof(CarUnitSmem);
-  cudaError_t e = cudaFuncSetAttribute(car_expand_kernel<TPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(car_expand_kernel<TPS, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, car_expand_kernel<TPS>, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, car_expand_kernel<TPS, KP>, 256, smem);
   per_sm = std::max(1, per_sm);
   int grid = std::max(1, std::min(n_units, per_sm * m->num_sms));
   // observation slots, one per CTA, stream-ordered so that launches on other
@@ -242,8 +243,8 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
   uint32_t* scratch = nullptr;
   e = cudaMallocFromPoolAsync((void**)&scratch, need, m->pool, st);
   if (e != cudaSuccess) return e;
-  car_expand_kernel<TPS><<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, head, m->plan_step,
-                                                   scratch, items);
+  car_expand_kernel<TPS, KP><<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, head,
+                                                       m->plan_step, scratch, items);
   e = cudaGetLastError();
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   return e != cudaSuccess ? e : e2;
@@ -251,12 +252,28 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
 
 }  // namespace
 
+int car_default_tps(int P) {
+  const int pairs = (P + 1) / 2;
+  int tps = 4;
+  while (tps < pairs && tps < 32) tps *= 2;
+  return tps;
+}
+
+// With the crowd fitting one pair per lane, the kernel that holds one pair
+// per lane (fewer registers, no idle pair slots) runs.
 cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
                               unsigned int* head, CarItems items, cudaStream_t st) {
-  switch (m->tune_tps > 0 ? m->tune_tps : 32) {
-    case 4: return launch_tps<4>(m, djobs, dunits, n_units, head, items, st);
-    case 8: return launch_tps<8>(m, djobs, dunits, n_units, head, items, st);
-    case 16: return launch_tps<16>(m, djobs, dunits, n_units, head, items, st);
+  const int pairs = (m->host->P + 1) / 2;
+  switch (m->tune_tps > 0 ? m->tune_tps : car_default_tps(m->host->P)) {
+    case 4:
+      return pairs <= 4 ? launch_tps<4, 1>(m, djobs, dunits, n_units, head, items, st)
+                        : launch_tps<4>(m, djobs, dunits, n_units, head, items, st);
+    case 8:
+      return pairs <= 8 ? launch_tps<8, 1>(m, djobs, dunits, n_units, head, items, st)
+                        : launch_tps<8>(m, djobs, dunits, n_units, head, items, st);
+    case 16:
+      return pairs <= 16 ? launch_tps<16, 1>(m, djobs, dunits, n_units, head, items, st)
+                         : launch_tps<16>(m, djobs, dunits, n_units, head, items, st);
     default: return launch_tps<32>(m, djobs, dunits, n_units, head, items, st);
   }
 }

@@ -53,6 +53,9 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
 dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
                          cudaStream_t st);
 
+// Lanes per car scenario when untuned: enough for one pedestrian pair per
+// lane (4 to 32).
+int car_default_tps(int P);
 cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
                               unsigned int* head, CarItems items, cudaStream_t st);
 // Learned-policy rollouts of the car expansion's items; counter: a device

@@ -81,6 +81,28 @@ def car50():
     return car_config(P=50, K=500, D=50, seed=0)
 
 
+# Variants of the same kernels (Sec. IV: crowd sizes, map sizes, numbers of
+# scenarios).
+def car_p(P):
+    """Car among P pedestrians, K=500, D=50."""
+    return car_config(P=P, K=500, D=50, seed=0)
+
+
+def mars11_11():
+    """Two robots on an 11x11 map with 11 rocks, 256 joint actions, K=500, D=90."""
+    return grid_config(11, 11, K=500, D=90, seed=0, robots=2)
+
+
+def mars20_20():
+    """Two robots on a 20x20 map with 20 rocks, 625 joint actions, K=500, D=90."""
+    return grid_config(20, 20, K=500, D=90, seed=0, robots=2)
+
+
+def rs15_15_k(K):
+    """rs15_15 with K scenarios (at most 512 in this build)."""
+    return grid_config(15, 15, K=K, D=90, seed=0)
+
+
 def words(cfg):
     return 5 if cfg.kind in (GRID, MULTIGRID) else 4 + 2 * cfg.P + (cfg.P + 3) // 4
 

@@ -101,6 +101,29 @@ def test_expand_parity(dsp, tps):
     m.close()
 
 
+@pytest.mark.parametrize("P", [6, 12, 20])
+def test_expand_parity_crowd_sizes(dsp, P):
+    """The crowd sizes of the pedestrian-count study: each lane owns fewer
+    pairs, and some lanes none."""
+    cfg = I.car_p(P)
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    jobs = I.job_stream(cfg, 6, 23 + P, max_scen=70)
+    jb = dsp.JobBatch(m, jobs)
+    m.reset_counters()
+    jb.run()
+    steps, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    total = 0
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        _cmp(res[k], o, f"P{P} job {k}")
+        total += o["steps"]
+    assert steps == total
+    m.close()
+
+
 def test_expand_shared_observations(dsp):
     """Scenarios with identical pedestrians and goals (no noise, no action
     failure) share observations, so children hold several scenarios."""

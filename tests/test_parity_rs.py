@@ -25,7 +25,19 @@ def rs32_32():
     return I.grid_config(32, 32, K=100, D=120, seed=3)
 
 
-CONFIGS = {"rs7_8": I.rs7_8, "rs15_15": I.rs15_15, "mars15_15": I.mars15_15, "rs32_32": rs32_32}
+def mars11_11():
+    """Two robots, 11x11 and 11 rocks: 256 joint actions (K = 200 keeps the
+    oracle quick)."""
+    return I.grid_config(11, 11, K=200, D=90, seed=0, robots=2)
+
+
+def mars20_20():
+    """Two robots, 20x20 and 20 rocks: 625 joint actions."""
+    return I.grid_config(20, 20, K=200, D=90, seed=0, robots=2)
+
+
+CONFIGS = {"rs7_8": I.rs7_8, "rs15_15": I.rs15_15, "mars15_15": I.mars15_15, "rs32_32": rs32_32,
+           "mars11_11": mars11_11, "mars20_20": mars20_20}
 
 
 def _cmp_expand(g, o, n, tag=""):
