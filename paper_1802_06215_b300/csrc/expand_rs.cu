@@ -648,11 +648,24 @@ __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned l
   asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-constexpr unsigned int kClosed = 0xFFFFFFFFu;
+// Claim word of a ring slot: the ticket's low 16 bits << 48 | the job's chunk
+// count << 24 | the next chunk (count 0: closed). Warps claim chunks with
+// atomicAdd, which always succeeds, so claims never retry on a busy word: the
+// returned word names the slot's current job (its data were written before it
+// was published) and whether chunks were left. A warp adds only after reading
+// that chunks remain, so the next-chunk field passes the count by at most the
+// number of warps times the grain and never reaches the count's bits.
+__device__ __forceinline__ unsigned long long claim_word(unsigned long long ticket, unsigned int nchunks) {
+  return ((ticket & 0xFFFFull) << 48) | ((unsigned long long)nchunks << 24);
+}
+__device__ __forceinline__ unsigned int claim_next(unsigned long long w) { return (unsigned int)(w & 0xFFFFFFu); }
+__device__ __forceinline__ unsigned int claim_count(unsigned long long w) {
+  return (unsigned int)((w >> 24) & 0xFFFFFFu);
+}
 
 // The job in `slot` is finished: close its claim word, publish done, free the slot.
 __device__ __forceinline__ void queue_complete(const QueueRing& ring, int slot, unsigned long long ticket) {
-  atomicExch(&ring.share[slot].claim, ((ticket & 0xFFFFFFFFull) << 32) | kClosed);
+  atomicExch(&ring.share[slot].claim, claim_word(ticket, 0u));
   __threadfence_system();
   st_release_sys(ring.done + slot, ticket + 1);
   st_release_sys(ring.seq + slot, ticket + (unsigned long long)ring.cap);
@@ -668,26 +681,29 @@ __device__ __forceinline__ int queue_claim_chunk(const QueueRing& ring, unsigned
     for (int attempt = 0; attempt < 4; ++attempt) {
       const int s = (start + base + lane) % ring.cap;
       bool can = false;
-      unsigned long long c = 0;
       if (base + lane < ring.cap) {
-        c = ld_acquire_gpu(&ring.share[s].claim);
-        const unsigned int idx = (unsigned int)(c & 0xFFFFFFFFull);
-        can = idx != kClosed && idx < *(volatile unsigned int*)&ring.share[s].nchunks;
+        const unsigned long long c = ld_acquire_gpu(&ring.share[s].claim);
+        can = claim_next(c) < claim_count(c);
       }
       const unsigned int ready = __ballot_sync(0xFFFFFFFFu, can);
       if (ready == 0u) break;
-      const int leader = __ffs(ready) - 1;
-      unsigned int got = 0;
+      // lanes with a claimable slot spread the warp over them
+      const int pick = __fns(ready, 0, 1 + (int)(((blockIdx.x >> 1) + (threadIdx.x >> 5)) % __popc(ready)));
+      const int leader = pick >= 0 ? pick : __ffs(ready) - 1;
+      unsigned int got = 0, first = 0;
       if (lane == leader) {
-        const unsigned int idx = (unsigned int)(c & 0xFFFFFFFFull);
-        const unsigned int n = *(volatile unsigned int*)&ring.share[s].nchunks;
-        const unsigned int g = min(*(volatile unsigned int*)&ring.share[s].grain, n - idx);
-        got = atomicCAS(&ring.share[s].claim, c, c + g) == c ? g : 0u;
+        const unsigned int g = max(1u, *(volatile unsigned int*)&ring.share[s].grain);
+        const unsigned long long old = atomicAdd(&ring.share[s].claim, (unsigned long long)g);
+        first = claim_next(old);
+        const unsigned int n = claim_count(old);
+        got = first < n ? min(g, n - first) : 0u;
+        if (got) __threadfence();  // the job's data, published before its claim word
       }
+      __syncwarp();
       got = __shfl_sync(0xFFFFFFFFu, got, leader);
       if (got) {
         count = got;
-        chunk = __shfl_sync(0xFFFFFFFFu, (unsigned int)(c & 0xFFFFFFFFull), leader);
+        chunk = __shfl_sync(0xFFFFFFFFu, first, leader);
         return __shfl_sync(0xFFFFFFFFu, s, leader);
       }
     }
@@ -770,7 +786,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
           sh.grain = (unsigned int)max(1LL, min(16LL, nchunks / 256));
           sh.plan_step = s_plan_step;
           __threadfence();
-          atomicExch(&sh.claim, ((unsigned long long)ticket & 0xFFFFFFFFull) << 32);
+          atomicExch(&sh.claim, claim_word((unsigned long long)ticket, (unsigned int)nchunks));
         }
       }
     }

@@ -30,7 +30,7 @@ cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const
 // Device view of the job ring (device addresses of mapped pinned host memory).
 // Work sharing of one ring slot's job across the grid (device memory).
 struct QueueShare {
-  unsigned long long claim;   // (ticket & 0xFFFFFFFF) << 32 | next chunk; chunk 0xFFFFFFFF: closed
+  unsigned long long claim;   // (ticket & 0xFFFF) << 48 | chunk count << 24 | next chunk; count 0: closed
   unsigned long long ticket;  // full ticket of the published job
   unsigned int nchunks;       // rollout chunks of 32 items
   unsigned int remaining;     // chunks not yet finished

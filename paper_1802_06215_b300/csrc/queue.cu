@@ -153,7 +153,7 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
   if (e == cudaSuccess) {
     std::vector<dsp::QueueShare> init(capacity);
     for (dsp::QueueShare& sh : init) {
-      sh.claim = 0xFFFFFFFFull;  // closed
+      sh.claim = 0ull;  // closed (no chunks)
       sh.ticket = 0;
       sh.nchunks = 0;
       sh.remaining = 0;
