@@ -160,6 +160,7 @@ class Search {
   };
 
   Node* new_node() {
+    std::lock_guard<std::mutex> lock(pool_mu_);
     pool_.emplace_back(new Node());
     return pool_.back().get();
   }
@@ -307,8 +308,9 @@ class Search {
     return DSP_OK;
   }
 
-  // Children of an expanded leaf from its copied results (caller holds the
-  // tree lock in free-running mode).
+  // Children of an expanded leaf from its copied results. The leaf is claimed
+  // by the calling thread, and other threads stop at an unexpanded leaf, so
+  // this runs without the tree lock; publish() then marks the leaf expanded.
   void create_children(Node* b, const dsp_leaf_job& J, const JobOut& jo, const char* hsmall) {
     const int32_t* cnt = (const int32_t*)(hsmall + jo.o_cnt);
     const int32_t* off = (const int32_t*)(hsmall + jo.o_off);
@@ -350,6 +352,11 @@ class Search {
       q.U = q.R + gamma_ * su;
       q.L = q.R + gamma_ * sl;
     }
+  }
+
+  // Makes a leaf whose children exist visible to the search (caller holds the
+  // tree lock in free-running mode).
+  void publish(Node* b) {
     b->expanded = true;
     refresh(b);
   }
@@ -389,10 +396,11 @@ class Search {
     e = cudaMemcpyAsync(host, dsmall, total, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: results copy");
+    for (int k = 0; k < L; ++k) create_children(leaves[k], jobs[k], jo[k], host + base[k]);
     {
       std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
       if (p_.deterministic == 0) lock.lock();
-      for (int k = 0; k < L; ++k) create_children(leaves[k], jobs[k], jo[k], host + base[k]);
+      for (int k = 0; k < L; ++k) publish(leaves[k]);
     }
     expansions_ += L;
     return DSP_OK;
@@ -410,6 +418,7 @@ class Search {
   Node* root_ = nullptr;
   uint16_t* d_ident_ = nullptr;
   std::mutex tree_mu_;
+  std::mutex pool_mu_;  // the node pool (children are made outside the tree lock)
   std::atomic<int> expansions_{0};
   dsp_queue* queue_ = nullptr;  // free running with use_queue: the shared device job queue
   int rounds_ = 0;
@@ -482,13 +491,11 @@ dsp_status Search::run_threads() {
         }
         backup(t);
         t.leaf->claimed = false;
+        if (root_->expanded && root_->U - root_->L <= p_.target_gap) stop = true;
       } else {
         std::lock_guard<std::mutex> lock(tree_mu_);
         backup(t);
         if (in_flight.load() == 0) stop = true;  // nothing left worth expanding
-      }
-      {
-        std::lock_guard<std::mutex> lock(tree_mu_);
         if (root_->expanded && root_->U - root_->L <= p_.target_gap) stop = true;
       }
       if (p_.time_limit_s > 0) {
