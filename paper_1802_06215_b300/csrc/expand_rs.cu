@@ -666,6 +666,7 @@ __device__ __forceinline__ unsigned int claim_count(unsigned long long w) {
 // The job in `slot` is finished: close its claim word, publish done, free the slot.
 __device__ __forceinline__ void queue_complete(const QueueRing& ring, int slot, unsigned long long ticket) {
   atomicExch(&ring.share[slot].claim, claim_word(ticket, 0u));
+  atomicAdd(ring.finished, 1ull);
   __threadfence_system();
   st_release_sys(ring.done + slot, ticket + 1);
   st_release_sys(ring.seq + slot, ticket + (unsigned long long)ring.cap);
@@ -814,7 +815,13 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       const unsigned long long now = global_ns();
       const bool busy = ticket >= 0 || s_work != 0;
       if (busy) last_work = now;
-      s_exit = !busy && (*(volatile unsigned int*)ring.close != 0u || now - last_work > idle_ns);
+      // a CTA stays while any claimed job is unfinished (its chunks may still
+      // be published), up to a hard second of idling
+      const bool drained =
+          *(volatile unsigned long long*)ring.finished == *(volatile unsigned long long*)head;
+      const unsigned long long idle = now - last_work;
+      s_exit = !busy && (*(volatile unsigned int*)ring.close != 0u || idle > idle_ns) &&
+               (drained || idle > 1000000000ull);
       if (busy) backoff = 256;
       if (!busy && !s_exit) {
         // idle CTAs back off, so their polling leaves the working CTAs'

@@ -44,6 +44,7 @@ struct QueueRing {
   unsigned int* close;       // nonzero: exit once no job is ready
   unsigned int* plan_step;   // [cap] plan step (fourth Philox counter word) of the slot's job
   QueueShare* share;         // [cap] device memory
+  unsigned long long* finished;  // device: jobs completed (consumed tickets - finished = jobs in flight)
   int cap;
 };
 size_t rs_queue_slot_words(int robots, int num_actions);

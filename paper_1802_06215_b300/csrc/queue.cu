@@ -33,6 +33,7 @@ struct dsp_queue {
   uint32_t* d_scratch = nullptr;         // device: one rollout-item list per ring slot
   dsp_leaf_job* d_jcopy = nullptr;       // device: one job copy per ring slot
   dsp::QueueShare* d_share = nullptr;    // device: work sharing per ring slot
+  unsigned long long* d_finished = nullptr;  // device: jobs completed
   size_t slot_words = 0;
   int grid = 0;
   unsigned long long idle_ns = 0;
@@ -147,6 +148,9 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
     e = cudaMalloc(&q->d_head, sizeof(unsigned long long));
   }
   if (e == cudaSuccess) e = cudaMemset(q->d_head, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_finished, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(q->d_finished, 0, sizeof(unsigned long long));
+  q->ring.finished = q->d_finished;
   if (e == cudaSuccess) e = cudaMalloc(&q->d_scratch, sizeof(uint32_t) * q->slot_words * (size_t)capacity);
   if (e == cudaSuccess) e = cudaMalloc(&q->d_jcopy, sizeof(dsp_leaf_job) * (size_t)capacity);
   if (e == cudaSuccess) e = cudaMalloc(&q->d_share, sizeof(dsp::QueueShare) * (size_t)capacity);
@@ -256,6 +260,7 @@ void dsp_queue_destroy(dsp_queue* q) {
   if (q->d_scratch) cudaFree(q->d_scratch);
   if (q->d_jcopy) cudaFree(q->d_jcopy);
   if (q->d_share) cudaFree(q->d_share);
+  if (q->d_finished) cudaFree(q->d_finished);
   if (q->host) cudaFreeHost(q->host);
   delete q;
 }

@@ -157,6 +157,7 @@ class Search {
     std::vector<Node*> path;
     std::vector<int> acts;
     Node* leaf = nullptr;
+    long long epoch = 0;  // leaves published when the trial was selected
   };
 
   Node* new_node() {
@@ -229,6 +230,7 @@ class Search {
   // Forward search of one trial from the root (caller holds the tree lock).
   Trial select() {
     Trial t;
+    t.epoch = published_;
     Node* b = root_;
     t.path.push_back(b);
     while (true) {
@@ -359,6 +361,7 @@ class Search {
   void publish(Node* b) {
     b->expanded = true;
     refresh(b);
+    published_ += 1;
   }
 
   // Expands leaves as one batch on `st` and creates their children in order.
@@ -419,6 +422,7 @@ class Search {
   uint16_t* d_ident_ = nullptr;
   std::mutex tree_mu_;
   std::mutex pool_mu_;  // the node pool (children are made outside the tree lock)
+  long long published_ = 0;  // leaves made visible (guarded by the tree lock)
   std::atomic<int> expansions_{0};
   dsp_queue* queue_ = nullptr;  // free running with use_queue: the shared device job queue
   int rounds_ = 0;
@@ -495,7 +499,9 @@ dsp_status Search::run_threads() {
       } else {
         std::lock_guard<std::mutex> lock(tree_mu_);
         backup(t);
-        if (in_flight.load() == 0) stop = true;  // nothing left worth expanding
+        // nothing left worth expanding: no expansion in flight and none
+        // published since this trial looked (else the tree changed: retry)
+        if (in_flight.load() == 0 && t.epoch == published_) stop = true;
         if (root_->expanded && root_->U - root_->L <= p_.target_gap) stop = true;
       }
       if (p_.time_limit_s > 0) {
