@@ -95,6 +95,8 @@ def parse():
     p.add_argument("--plan-seconds", type=float, default=0.1)
     p.add_argument("--learned-rollouts", type=int, default=0,
                    help="time only the learned-policy rollout kernel on this many start states and exit")
+    p.add_argument("--plan-scaling", default="", choices=["", "rs15_15", "mars15_15"],
+                   help="planning throughput against search threads (per-leaf launches vs the device queue)")
     p.add_argument("--sweep", default="", help="'all' or comma-separated workloads: one line per variant")
     p.add_argument("--ref-step-seconds", type=float, default=60.0,
                    help="cap on the oracle's time per step in the reference arm")
@@ -617,6 +619,38 @@ def sweep(args):
         del jb
 
 
+def plan_scaling(args):
+    """Planning throughput against search threads, per-leaf launches against
+    the device job queue: three planning steps of 0.3 s per (threads, path)
+    from the benchmark's root belief, xi < 0 so that no trial ends without a
+    leaf (the machinery's rate, not the planner's). One JSON line per point:
+    median, min and max expansions/s."""
+    from paper_1802_06215_b300 import _dsp, batch, build
+    build.build()
+    mk = WORKLOADS[args.plan_scaling][0]
+    cfg = mk()
+    m = batch.Model(cfg)
+    b = root_states(cfg, np.random.default_rng(99))
+
+    def plan(threads, q, secs):
+        p = _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=secs, c_a=1.0, c_o=0.5, xi=-1.0,
+                                   target_gap=-1.0, deterministic=0, use_queue=q)
+        return _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+
+    plan(4, 0, 0.2)
+    plan(4, 1, 0.2)
+    for threads in (1, 2, 4, 8, 16, 32):
+        for q in (0, 1):
+            r = []
+            for _ in range(3):
+                g = plan(threads, q, 0.3)
+                r.append(g["expansions"] / g["seconds"])
+            print(json.dumps({"plan_scaling": args.plan_scaling, "threads": threads,
+                              "path": "device queue" if q else "per-leaf launches",
+                              "expansions_per_s": statistics.median(r), "min": min(r), "max": max(r)}), flush=True)
+    m.close()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -632,6 +666,9 @@ def main():
     elif args.sweep:
         if rank == 0:
             sweep(args)
+    elif args.plan_scaling:
+        if rank == 0:
+            plan_scaling(args)
     else:
         run_ours(args, rank, world)
 
