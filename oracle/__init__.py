@@ -29,7 +29,7 @@ class _Model(C.Structure):
         ("gamma", C.c_float), ("K", C.c_int32), ("D", C.c_int32), ("seed", C.c_uint64),
         ("plan_step", C.c_uint32), ("rock_cells", C.POINTER(C.c_int32)),
         ("path_len", C.c_float), ("dt", C.c_float), ("ped_speed", C.c_float), ("sigma", C.c_float),
-        ("fail_p", C.c_double), ("fp64", C.c_int32),
+        ("fail_p", C.c_double), ("fp64", C.c_int32), ("sense_p", C.c_double),
     ]
 
 
@@ -104,7 +104,8 @@ class Model:
         self.c = _Model(kind=cfg.kind, n=cfg.n, m=cfg.m, P=cfg.P, gamma=cfg.gamma, K=cfg.K, D=cfg.D,
                         seed=cfg.seed, plan_step=cfg.plan_step if plan_step is None else plan_step,
                         rock_cells=_p(self._rocks, _I32), path_len=cfg.path_len, dt=cfg.dt,
-                        ped_speed=cfg.ped_speed, sigma=cfg.sigma, fail_p=cfg.fail_p, fp64=1 if fp64 else 0)
+                        ped_speed=cfg.ped_speed, sigma=cfg.sigma, fail_p=cfg.fail_p, fp64=1 if fp64 else 0,
+                        sense_p=getattr(cfg, "sense_p", 0.03))
 
     @property
     def words(self):
@@ -113,6 +114,8 @@ class Model:
     def num_actions(self):
         if self.cfg.kind == 2:
             return 3
+        if self.cfg.kind == 3:
+            return 9
         a = 5 + self.cfg.m
         return a if self.cfg.kind == 0 else a * a
 

@@ -16,7 +16,7 @@ using namespace orc;
 extern "C" {
 
 typedef struct {
-  int32_t kind;  // 0 grid (1 robot), 1 multigrid (2 robots), 2 car
+  int32_t kind;  // 0 grid (1 robot), 1 multigrid (2 robots), 2 car, 3 navigation
   int32_t n, m, P;
   float gamma;
   int32_t K, D;
@@ -24,8 +24,9 @@ typedef struct {
   uint32_t plan_step;
   const int32_t* rock_cells;  // m entries, x | y << 8
   float path_len, dt, ped_speed, sigma;
-  double fail_p;
-  int32_t fp64;  // 1: FP64 oracle, 0: FP32 oracle
+  double fail_p;  // car: accelerate/decelerate failure; navigation: move failure
+  int32_t fp64;   // 1: FP64 oracle, 0: FP32 oracle
+  double sense_p;  // navigation: probability that one adjacent-cell reading is wrong
 } orc_model;
 
 typedef struct {
@@ -116,6 +117,21 @@ Car<Real> make_car(const orc_model* d) {
   return m;
 }
 
+template <class Real>
+Nav<Real> make_nav(const orc_model* d) {
+  Nav<Real> m;
+  m.n = d->n;
+  m.gamma = d->gamma;
+  m.K = d->K;
+  m.D = d->D;
+  m.seed = d->seed;
+  m.plan_step = d->plan_step;
+  m.fail_p = d->fail_p;
+  m.sense_p = d->sense_p;
+  m.init();
+  return m;
+}
+
 Hist hist_from(const int8_t* h) {
   Hist x{};
   if (h)
@@ -138,6 +154,13 @@ int with_model(const orc_model* d, F f) {
       f(make_car<double>(d));
     else
       f(make_car<float>(d));
+    return 0;
+  }
+  if (d->kind == 3) {
+    if (d->fp64)
+      f(make_nav<double>(d));
+    else
+      f(make_nav<float>(d));
     return 0;
   }
   return 1;
@@ -168,6 +191,7 @@ void orc_gauss_table(double* out64, float* out32) {
 
 int32_t orc_state_words(const orc_model* d) {
   if (d->kind == 2) return 4 + 2 * d->P + (d->P + 3) / 4;
+  if (d->kind == 3) return 2 + (d->n * d->n + 31) / 32;
   return 5;
 }
 

@@ -32,6 +32,7 @@
 
 #include "car.hpp"
 #include "rocksample.hpp"
+#include "nav.hpp"
 
 namespace orc {
 
@@ -47,6 +48,10 @@ bool same_obs(const RockSample<R>&, const RSState&, const RSState&) {
 template <class R>
 bool same_obs(const Car<R>& m, const CarState<R>& a, const CarState<R>& b) {
   return m.observe_state(a) == m.observe_state(b);
+}
+template <class R>
+bool same_obs(const Nav<R>&, const NavState&, const NavState&) {
+  return true;
 }
 
 // Eq. lb for one scenario: roll the default policy from depth t0 until the

@@ -12,13 +12,15 @@ State block format (the boundary's, see include/dsp.h): a uint32 array of shape
   Car (4 + 2P + ceil(P/4) words): f0 s (float bits), f1 v | terminal<<8,
   f2 scenario id, f3 zero, P words pedestrian x, P words y (float bits),
   goals four to a word.
+  Navigation (2 + ceil(n*n/32) words): f0 x | y<<8 | terminal<<16, then the
+  occupancy map (bit c of cell c = y*n + x), then the scenario id.
 """
 from dataclasses import dataclass, field, replace
 from typing import Optional
 
 import numpy as np
 
-GRID, MULTIGRID, CAR = 0, 1, 2
+GRID, MULTIGRID, CAR, NAV = 0, 1, 2, 3
 
 
 @dataclass
@@ -38,6 +40,7 @@ class Config:
     ped_speed: float = 1.2
     sigma: float = 0.1
     fail_p: float = 0.01
+    sense_p: float = 0.03
 
     def with_(self, **kw):
         return replace(self, **kw)
@@ -103,8 +106,98 @@ def rs15_15_k(K):
     return grid_config(15, 15, K=K, D=90, seed=0)
 
 
+def nav_config(n=13, K=500, D=90, seed=0):
+    """Navigation in a partially known n x n map: 9 actions, moves fail with
+    p = 0.03, each of the 8 adjacent-cell readings is wrong with p = 0.03."""
+    return Config(kind=NAV, n=n, m=0, P=0, K=K, D=D, seed=seed, rock_cells=np.zeros(1, np.int32), fail_p=0.03,
+                  sense_p=0.03)
+
+
+def nav13():
+    """The paper's 13x13 navigation map, K=500, D=90."""
+    return nav_config(13, K=500, D=90, seed=0)
+
+
 def words(cfg):
-    return 5 if cfg.kind in (GRID, MULTIGRID) else 4 + 2 * cfg.P + (cfg.P + 3) // 4
+    if cfg.kind in (GRID, MULTIGRID):
+        return 5
+    if cfg.kind == NAV:
+        return 2 + (cfg.n * cfg.n + 31) // 32
+    return 4 + 2 * cfg.P + (cfg.P + 3) // 4
+
+
+def nav_layout(cfg):
+    """The map's known cells: (free, occupied) boolean arrays of shape (n, n)
+    indexed [y, x]. Start row y = 0 and the goal (n/2, n-1) are known free;
+    the wall row y = n/2 is known occupied except its two gates (x = n/4 and
+    n-1-n/4); 20 landmark cells (drawn once per world seed, off the start
+    row, the wall row and the goal) are known occupied. Every other cell,
+    the gates included, is unknown to the robot (124 of 169 on 13 x 13)."""
+    n = cfg.n
+    free = np.zeros((n, n), bool)
+    occ = np.zeros((n, n), bool)
+    free[0, :] = True
+    free[n - 1, n // 2] = True
+    wall = n // 2
+    gates = (n // 4, n - 1 - n // 4)
+    occ[wall, :] = True
+    for g in gates:
+        occ[wall, g] = False
+    rng = np.random.default_rng([cfg.seed, 0x4E41564C])
+    cand = [(y, x) for y in range(1, n) for x in range(n) if y != wall and not (y == n - 1 and x == n // 2)]
+    for k in rng.choice(len(cand), size=min(20, len(cand)), replace=False):
+        occ[cand[k]] = True
+    return free, occ
+
+
+def nav_maps(cfg, count, rng, p_occ=0.1):
+    """Occupancy maps of `count` scenarios, uint32 words (ceil(n*n/32), count):
+    known cells as the layout says, one gate open (uniform), the other unknown
+    cells occupied with probability p_occ."""
+    n = cfg.n
+    free, occ = nav_layout(cfg)
+    known = free | occ
+    wall = n // 2
+    gates = (n // 4, n - 1 - n // 4)
+    cells = rng.random((count, n, n)) < p_occ
+    cells = np.where(known[None], occ[None], cells)
+    open_g = rng.integers(0, 2, count)
+    cells[:, wall, gates[0]] = open_g != 0
+    cells[:, wall, gates[1]] = open_g == 0
+    flat = cells.reshape(count, n * n)
+    mw = (n * n + 31) // 32
+    out = np.zeros((mw, count), np.uint32)
+    for c in range(n * n):
+        out[c // 32] |= flat[:, c].astype(np.uint32) << np.uint32(c % 32)
+    return out, cells
+
+
+def nav_block(cfg, count, rng, pos=None, spread=0, scen=None, p_occ=0.1, maps=None):
+    """Random navigation scenarios: a map per scenario (nav_maps), and the
+    robot at `pos` (x, y), within `spread` cells of it (localisation
+    uncertainty), or uniform on the start row; never on an occupied cell."""
+    n = cfg.n
+    words_map, cells = nav_maps(cfg, count, rng, p_occ) if maps is None else maps
+    b = np.zeros((words(cfg), count), np.uint32)
+    mw = (n * n + 31) // 32
+    b[1:1 + mw] = words_map
+    xs = np.zeros(count, np.int64)
+    ys = np.zeros(count, np.int64)
+    for i in range(count):
+        for _ in range(64):
+            if pos is None:
+                x, y = int(rng.integers(0, n)), 0
+            else:
+                x = int(np.clip(pos[0] + rng.integers(-spread, spread + 1), 0, n - 1))
+                y = int(np.clip(pos[1] + rng.integers(-spread, spread + 1), 0, n - 1))
+            if not cells[i, y, x] and not (x == n // 2 and y == n - 1):
+                break
+        else:  # no free cell found near pos: the start row is free
+            x, y = int(rng.integers(0, n)), 0
+        xs[i], ys[i] = x, y
+    b[0] = (xs.astype(np.uint32) | (ys.astype(np.uint32) << 8))
+    b[1 + mw] = (np.arange(count) if scen is None else scen).astype(np.uint32)
+    return b
 
 
 def _f32_bits(a):
@@ -187,6 +280,8 @@ class Job:
 def _num_actions(cfg):
     if cfg.kind == CAR:
         return 3
+    if cfg.kind == NAV:
+        return 9
     a = 5 + cfg.m
     return a if cfg.kind == GRID else a * a
 
@@ -231,6 +326,16 @@ def job_stream(cfg, n_jobs, seed, max_scen=None, depth_max=10, min_scen=1):
                 last = a
             else:
                 last = -1
+        elif cfg.kind == NAV:
+            # a tree node's scenarios: one map each, the robot within a cell of
+            # a common position (localisation uncertainty grows with depth)
+            y0 = int(rng.integers(0, min(cfg.n - 1, depth + 1)))
+            x0 = int(rng.integers(0, cfg.n))
+            parent = nav_block(cfg, pc, rng, pos=(x0, y0), spread=1 if depth > 0 else 0, scen=scen)
+            hist = np.zeros(32, np.int8)
+            if depth > 0:
+                hist[0] = np.array([rng.integers(0, 256)], np.uint8).view(np.int8)[0]
+            last = int(rng.integers(0, 9)) if depth > 0 else -1
         else:
             s0 = float(rng.uniform(0.0, 20.0))
             v0 = int(rng.integers(0, 4))
