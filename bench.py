@@ -264,6 +264,8 @@ def root_states(cfg, rng):
         base = (rng.uniform(0, 40, cfg.P), rng.uniform(0, 40, cfg.P))
         b = inputs.car_block(cfg, cfg.K, rng, s=0.0, v=0, base=base, jitter=0.0)
         return b
+    if cfg.kind == inputs.NAV:
+        return inputs.nav_block(cfg, cfg.K, rng)
     pos = [(0, cfg.n // 2), (0, cfg.n // 2 - 1)][: (2 if cfg.kind == inputs.MULTIGRID else 1)]
     return inputs.rs_block(cfg, cfg.K, rng, pos=pos)
 

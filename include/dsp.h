@@ -59,7 +59,12 @@ typedef enum {
   DSP_E_DEVICE = 7       /* a kernel reported an error in its status word */
 } dsp_status;
 
-typedef enum { DSP_MODEL_GRID = 0, DSP_MODEL_MULTIGRID = 1, DSP_MODEL_CAR = 2 } dsp_model_kind;
+typedef enum {
+  DSP_MODEL_GRID = 0,      /* Rock Sample, one robot */
+  DSP_MODEL_MULTIGRID = 1, /* Rock Sample, two robots */
+  DSP_MODEL_CAR = 2,       /* car among pedestrians */
+  DSP_MODEL_NAV = 3        /* navigation in a partially known map */
+} dsp_model_kind;
 
 typedef struct dsp_model dsp_model; /* opaque, owned by the library */
 
@@ -67,7 +72,7 @@ typedef struct dsp_model dsp_model; /* opaque, owned by the library */
  * with K scenarios and horizon D (Sec. III-A, Eq. lb). Caller-owned POD. */
 typedef struct {
   int32_t kind;               /* dsp_model_kind */
-  int32_t n;                  /* Rock Sample map side (2..32) */
+  int32_t n;                  /* map side: Rock Sample 2..32, navigation 5..16 */
   int32_t m;                  /* Rock Sample rocks (1..32) */
   int32_t P;                  /* car: pedestrians (1..64) */
   float gamma;                /* discount */
@@ -77,7 +82,8 @@ typedef struct {
   uint32_t plan_step;         /* fourth Philox counter word */
   const int32_t* rock_cells;  /* host, m entries x | y<<8, distinct cells */
   float path_len, dt, ped_speed, sigma; /* car: path length, time step, walking speed, noise */
-  double fail_p;              /* car: probability that accelerate/decelerate fails */
+  double fail_p;              /* car: accelerate/decelerate fails; navigation: a move fails */
+  double sense_p;             /* navigation: one adjacent-cell reading is wrong */
 } dsp_model_desc;
 
 /* Creates a model: validates the descriptor, builds its constant tables
@@ -90,7 +96,8 @@ void dsp_destroy_model(dsp_model* model);
 
 int32_t dsp_state_words(const dsp_model* model);  /* words per scenario */
 int32_t dsp_num_actions(const dsp_model* model);  /* |A| */
-/* Max children per action the result arrays need (grid 4, multigrid 10, car
+/* Max children per action the result arrays need (grid 4, multigrid 10,
+ * navigation 257 (8-bit reading or terminal), car
  * n_scen). */
 int32_t dsp_max_children(const dsp_model* model, int32_t n_scen);
 

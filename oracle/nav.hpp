@@ -168,6 +168,7 @@ struct Nav {
     } else {
       d = cheb(s.x, s.y, goal_x(), goal_y());
     }
+    if (d < 1) d = 1;  // a live robot standing on the goal (not reachable by g)
     return (Real)20 * G[d - 1];
   }
 

@@ -26,7 +26,7 @@ class dsp_model_desc(C.Structure):
         ("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("P", C.c_int32), ("gamma", C.c_float),
         ("K", C.c_int32), ("D", C.c_int32), ("seed", C.c_uint64), ("plan_step", C.c_uint32),
         ("rock_cells", C.POINTER(C.c_int32)), ("path_len", C.c_float), ("dt", C.c_float),
-        ("ped_speed", C.c_float), ("sigma", C.c_float), ("fail_p", C.c_double),
+        ("ped_speed", C.c_float), ("sigma", C.c_float), ("fail_p", C.c_double), ("sense_p", C.c_double),
     ]
 
 
@@ -94,7 +94,7 @@ def desc_from_config(cfg):
     d = dsp_model_desc(kind=cfg.kind, n=cfg.n, m=cfg.m, P=cfg.P, gamma=cfg.gamma, K=cfg.K, D=cfg.D, seed=cfg.seed,
                        plan_step=cfg.plan_step, rock_cells=rocks.ctypes.data_as(C.POINTER(C.c_int32)),
                        path_len=cfg.path_len, dt=cfg.dt, ped_speed=cfg.ped_speed, sigma=cfg.sigma,
-                       fail_p=cfg.fail_p)
+                       fail_p=cfg.fail_p, sense_p=getattr(cfg, "sense_p", 0.03))
     d._keep = rocks
     return d
 

@@ -74,7 +74,7 @@ dsp_status dsp_create_model(const dsp_model_desc* d, dsp_model** out) {
   if (!out) return fail(DSP_E_INVALID, "dsp_create_model: out is NULL");
   *out = nullptr;
   if (!d) return fail(DSP_E_INVALID, "dsp_create_model: desc is NULL");
-  if (d->kind < 0 || d->kind > 2) return fail(DSP_E_INVALID, "unknown model kind %d", d->kind);
+  if (d->kind < 0 || d->kind > 3) return fail(DSP_E_INVALID, "unknown model kind %d", d->kind);
   if (d->K < 1 || d->K > kMaxScen) return fail(DSP_E_INVALID, "K=%d outside 1..%d", d->K, kMaxScen);
   if (d->D < 1 || d->D > kGammaLen - 6) return fail(DSP_E_INVALID, "D=%d outside 1..%d", d->D, kGammaLen - 6);
   if (!(d->gamma > 0.0f && d->gamma <= 1.0f)) return fail(DSP_E_INVALID, "gamma must be in (0, 1]");
@@ -121,6 +121,20 @@ dsp_status dsp_create_model(const dsp_model_desc* d, dsp_model** out) {
           h->nkey[i * nn + y * d->n + x] = (uint16_t)((dist << 7) | (i << 2) | (dist == 0 ? 0 : mv));
         }
     }
+  } else if (d->kind == DSP_MODEL_NAV) {
+    if (d->n < 5 || d->n > 16) {
+      delete h;
+      return fail(DSP_E_INVALID, "navigation map side n=%d outside 5..16", d->n);
+    }
+    if (!(d->fail_p >= 0.0 && d->fail_p <= 1.0) || !(d->sense_p >= 0.0 && d->sense_p <= 1.0)) {
+      delete h;
+      return fail(DSP_E_INVALID, "navigation probabilities outside [0, 1]");
+    }
+    h->n = d->n;
+    h->num_actions = 9;
+    h->words = 2 + (d->n * d->n + 31) / 32;
+    h->fail_thresh = (uint64_t)std::floor(d->fail_p * 4294967296.0);
+    h->sense_thresh = (uint64_t)std::floor(d->sense_p * 4294967296.0);
   } else {
     if (d->P < 1 || d->P > kMaxPeds) {
       delete h;
@@ -196,7 +210,8 @@ int32_t dsp_state_words(const dsp_model* m) { return m ? m->host->words : 0; }
 int32_t dsp_num_actions(const dsp_model* m) { return m ? m->host->num_actions : 0; }
 int32_t dsp_max_children(const dsp_model* m, int32_t n_scen) {
   if (!m) return 0;
-  int z = m->host->kind == DSP_MODEL_GRID ? 4 : (m->host->kind == DSP_MODEL_MULTIGRID ? 10 : n_scen);
+  const int kind = m->host->kind;
+  int z = kind == DSP_MODEL_GRID ? 4 : (kind == DSP_MODEL_MULTIGRID ? 10 : (kind == DSP_MODEL_NAV ? 257 : n_scen));
   return std::min(z, n_scen);
 }
 
@@ -210,7 +225,7 @@ dsp_status dsp_get_table(const dsp_model* m, int32_t which, void* out, int32_t* 
   if (!m || !out || !count) return fail(DSP_E_INVALID, "dsp_get_table: NULL argument");
   const DevModel* h = m->host;
   if (which == 0) {
-    int n = h->kind == DSP_MODEL_CAR ? 0 : 2 * (h->n - 1) * (h->n - 1) + 1;
+    int n = (h->kind == DSP_MODEL_CAR || h->kind == DSP_MODEL_NAV) ? 0 : 2 * (h->n - 1) * (h->n - 1) + 1;
     std::memcpy(out, h->thresh, n * sizeof(uint64_t));
     *count = n;
   } else if (which == 1) {
@@ -237,6 +252,8 @@ dsp_status dsp_step(const dsp_model* m, const uint32_t* in, int32_t in_cap, int3
   if (m->host->kind == DSP_MODEL_CAR)
     e = launch_car_step(m->dmodel, m->host->P, in, in_cap, count, actions, depth, out, out_cap, keys, rewards,
                         m->plan_step, st);
+  else if (m->host->kind == DSP_MODEL_NAV)
+    e = launch_nav_step(m->dmodel, in, in_cap, count, actions, depth, out, out_cap, keys, rewards, m->plan_step, st);
   else
     e = launch_rs_step(m->dmodel, m->host->robots, in, in_cap, count, actions, depth, out, out_cap, keys, rewards,
                        m->plan_step, st);
@@ -257,6 +274,8 @@ dsp_status dsp_rollout(const dsp_model* m, const uint32_t* block, int32_t cap, i
   if (m->host->kind == DSP_MODEL_CAR)
     e = launch_car_rollout(m->dmodel, m->host->P, m->dwork, block, cap, count, start_depth, value, m->plan_step,
                            st);
+  else if (m->host->kind == DSP_MODEL_NAV)
+    e = launch_nav_rollout(m->dmodel, m->dwork, block, cap, count, hist, start_depth, value, m->plan_step, st);
   else
     e = launch_rs_rollout(m->dmodel, m->host->robots, m->dwork, block, cap, count, hist, start_depth, value,
                           m->plan_step, st);
@@ -359,7 +378,7 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
     if (J.child_cap < 1 || !J.child_count || !J.child_off || !J.child_key || !J.rew_sum || !J.u_sum || !J.l_sum ||
         !J.perm)
       return fail(DSP_E_INVALID, "job %d: result buffer missing", j);
-    if (h->kind == DSP_MODEL_CAR) {
+    if (h->kind == DSP_MODEL_CAR || h->kind == DSP_MODEL_NAV) {
       for (int a = 0; a < J.n_actions; ++a) plan.units.push_back(make_int4(j, a, 1, 0));
     } else {
       plan.item_base.push_back(plan.total_items);
@@ -370,7 +389,7 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
   // Largest work first (units and jobs are independent, so the order changes
   // no result): persistent CTAs that pull work in this order end together
   // instead of waiting on one large unit drawn last.
-  if (h->kind == DSP_MODEL_CAR) {
+  if (h->kind == DSP_MODEL_CAR || h->kind == DSP_MODEL_NAV) {
     std::stable_sort(plan.units.begin(), plan.units.end(), [&](const int4& x, const int4& y) {
       return jobs[x.x].n_scen > jobs[y.x].n_scen;
     });
@@ -435,12 +454,13 @@ static cudaError_t release_staging(dsp_model* m, dsp_staging_slot* sl, cudaStrea
 dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
                          cudaStream_t st) {
   const DevModel* h = m->host;
-  const bool car = h->kind == DSP_MODEL_CAR;
+  const bool car = h->kind == DSP_MODEL_CAR, nav = h->kind == DSP_MODEL_NAV;
+  const bool by_unit = car || nav;  // (job, action) units instead of Rock Sample's item list
   size_t jb = sizeof(dsp_leaf_job) * (size_t)n_jobs;
-  size_t ub = car ? sizeof(int4) * plan.units.size()
+  size_t ub = by_unit ? sizeof(int4) * plan.units.size()
                   : sizeof(long long) * plan.item_base.size() + sizeof(int) * plan.order.size();
   const bool car_items = car && m->policy_on;
-  size_t ib = car ? (car_items ? sizeof(uint32_t) * (size_t)(h->words + 2) * (size_t)plan.total_items : 0)
+  size_t ib = by_unit ? (car_items ? sizeof(uint32_t) * (size_t)(h->words + 2) * (size_t)plan.total_items : 0)
                   : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
   size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
   unsigned char* buf = nullptr;
@@ -450,7 +470,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   void* dunits = buf + align256(jb);
   unsigned int* counters = (unsigned int*)(buf + align256(jb) + align256(ub));
   uint32_t* items = (uint32_t*)(buf + align256(jb) + align256(ub) + 256);
-  const int* dorder = car ? nullptr : (const int*)((const long long*)dunits + plan.item_base.size());
+  const int* dorder = by_unit ? nullptr : (const int*)((const long long*)dunits + plan.item_base.size());
   // the job table and the unit table (or item offsets and order) in one copy
   // from pinned staging laid out like the device buffer
   const size_t hb = align256(jb) + ub;
@@ -458,7 +478,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   if (sl != nullptr) {
     unsigned char* hs = (unsigned char*)sl->host;
     std::memcpy(hs, jobs, jb);
-    if (car) {
+    if (by_unit) {
       std::memcpy(hs + align256(jb), plan.units.data(), ub);
     } else {
       std::memcpy(hs + align256(jb), plan.item_base.data(), sizeof(long long) * plan.item_base.size());
@@ -470,9 +490,9 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
     if (e == cudaSuccess) e = er;
   } else {
     e = cudaMemcpyAsync(djobs, jobs, jb, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && car)
+    if (e == cudaSuccess && by_unit)
       e = cudaMemcpyAsync(dunits, plan.units.data(), ub, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !car) {
+    if (e == cudaSuccess && !by_unit) {
       e = cudaMemcpyAsync(dunits, plan.item_base.data(), sizeof(long long) * plan.item_base.size(),
                           cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess)
@@ -492,6 +512,8 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
       CarItems ci{car_items ? items : nullptr, plan.total_items, h->words};
       e = launch_car_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, ci, st);
       if (e == cudaSuccess && car_items) e = launch_car_rollout_mlp_items(m, djobs, ci, counters + 1, st);
+    } else if (nav) {
+      e = launch_nav_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
       e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, rs_key_words(h), m->dwork, djobs,

@@ -19,6 +19,8 @@ extern "C" dsp_status dsp_autotune(dsp_model* m, const dsp_leaf_job* jobs, int32
   std::vector<std::pair<int, int>> cands;
   if (m->host->kind == DSP_MODEL_CAR)
     cands = {{0, 4}, {0, 8}, {0, 16}, {0, 32}};
+  else if (m->host->kind == DSP_MODEL_NAV)
+    cands = {{0, 0}};  // one launch shape
   else
     cands = {{128, 0}, {256, 0}, {512, 0}};
   const int keep_block = m->tune_block, keep_tps = m->tune_tps;

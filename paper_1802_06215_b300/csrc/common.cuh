@@ -28,7 +28,8 @@ struct DevModel {
   uint64_t seed;
   float gamma;
   float path_len, dt, ped_speed, sigma, stride;
-  uint64_t fail_thresh;
+  uint64_t fail_thresh;                 // car: action failure; navigation: move failure
+  uint64_t sense_thresh;                // navigation: a wrong adjacent-cell reading
   int rock_xy[kMaxRocks];               // x | y << 8
   uint8_t cell_rock[kMaxSide * kMaxSide]; // rock index at cell y*n+x, 0xFF none
   float G[kGammaLen];                   // gamma^k in FP32

@@ -989,7 +989,7 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
   using namespace dsp;
   if (!m) return fail(DSP_E_INVALID, "dsp_expand_leaves_noalloc: model is NULL");
   if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(DSP_E_INVALID, "dsp_expand_leaves_noalloc: bad job array");
-  if (m->host->kind == DSP_MODEL_CAR)
+  if (m->host->kind != DSP_MODEL_GRID && m->host->kind != DSP_MODEL_MULTIGRID)
     return fail(DSP_E_UNSUPPORTED, "dsp_expand_leaves_noalloc: Rock Sample models only");
   if (n_jobs == 0) return DSP_OK;
   if (n_jobs > kNoAllocJobs)

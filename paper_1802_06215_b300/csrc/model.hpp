@@ -53,6 +53,14 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
 dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
                          cudaStream_t st);
 
+cudaError_t launch_nav_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
+                              unsigned int* head, cudaStream_t st);
+cudaError_t launch_nav_step(const DevModel* gm, const uint32_t* in, int in_cap, int count, const int32_t* actions,
+                            int depth, uint32_t* out, int out_cap, uint64_t* keys, float* rewards, uint32_t plan_step,
+                            cudaStream_t st);
+cudaError_t launch_nav_rollout(const DevModel* gm, DevWork* work, const uint32_t* block, int cap, int count,
+                               const int8_t* hist, int start_depth, float* value, uint32_t plan_step,
+                               cudaStream_t st);
 // Lanes per car scenario when untuned: enough for one pedestrian pair per
 // lane (4 to 32).
 int car_default_tps(int P);

@@ -112,7 +112,8 @@ extern "C" {
 dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, dsp_queue** out) {
   if (!m || !out) return fail(DSP_E_INVALID, "dsp_queue_create: NULL argument");
   *out = nullptr;
-  if (m->host->kind == DSP_MODEL_CAR) return fail(DSP_E_UNSUPPORTED, "dsp_queue_create: Rock Sample models only");
+  if (m->host->kind != DSP_MODEL_GRID && m->host->kind != DSP_MODEL_MULTIGRID)
+    return fail(DSP_E_UNSUPPORTED, "dsp_queue_create: Rock Sample models only");
   if (capacity < 1 || capacity > (1 << 20)) return fail(DSP_E_INVALID, "dsp_queue_create: capacity %d", capacity);
   if (idle_ns == 0) idle_ns = 2000000ull;
   dsp_queue* q = new dsp_queue();

@@ -396,7 +396,7 @@ dsp_status dsp_set_policy(dsp_model* m, const dsp_mlp* mlp) {
     m->policy_on = false;
     return DSP_OK;
   }
-  if (m->host->kind == DSP_MODEL_MULTIGRID)
+  if (m->host->kind == DSP_MODEL_MULTIGRID || m->host->kind == DSP_MODEL_NAV)
     return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: the learned policy serves one-robot Rock Sample and the car");
   if (m->host->num_actions + 1 > kMlpOut)
     return fail(DSP_E_UNSUPPORTED, "dsp_set_policy: more than 31 actions (the network's last used logit defers)");

@@ -168,6 +168,10 @@ class Search {
 
   void observe(int8_t* h, int a, uint64_t key) const {
     if (kind_ == DSP_MODEL_CAR) return;
+    if (kind_ == DSP_MODEL_NAV) {  // the last reading is the default policy's history
+      if (!(key & (1ull << 62))) h[0] = (int8_t)(uint8_t)(key & 0xFFu);
+      return;
+    }
     int z = (int)(key & ~(1ull << 62));
     int acts[2], zs[2], robots = kind_ == DSP_MODEL_GRID ? 1 : 2;
     if (robots == 1) {

@@ -27,6 +27,8 @@ def root_states(cfg, rng, n=None):
     if cfg.kind == I.CAR:
         base = (rng.uniform(0, 40, cfg.P), rng.uniform(0, 40, cfg.P))
         return I.car_block(cfg, n, rng, s=0.0, v=1, base=base, jitter=0.0)
+    if cfg.kind == I.NAV:
+        return I.nav_block(cfg, n, rng)
     pos = [(0, cfg.n // 2), (0, cfg.n // 2 - 1)][: (2 if cfg.kind == I.MULTIGRID else 1)]
     return I.rs_block(cfg, n, rng, pos=pos)
 
@@ -51,6 +53,7 @@ def plan_both(env, cfg, b, **kw):
     ("mars small", lambda: I.grid_config(7, 4, K=40, D=30, seed=3, robots=2), dict(threads=4, rounds=8, c_a=1.0,
                                                                                    c_o=0.5)),
     ("car small", lambda: I.car_config(P=10, K=40, D=20, seed=2), dict(threads=2, rounds=6, c_a=1.0, c_o=0.5)),
+    ("navigation 13x13", lambda: I.nav_config(13, K=60, D=40, seed=2), dict(threads=4, rounds=8, c_a=1.0, c_o=0.5)),
 ])
 def test_deterministic_rounds_match_oracle(env, name, cfg_fn, kw):
     cfg = cfg_fn()
