@@ -55,13 +55,15 @@ WORKLOADS = {
                                          "jobs", (16, 0.5, 1)),
     "mars20_20": (inputs.mars20_20, 512, "two-robot Rock Sample 20x20, 20 rocks, |A|=625, K=500, D=90; 512 leaf "
                                          "jobs", (16, 0.5, 1)),
+    "nav13": (inputs.nav13, 512, "navigation in a partially known 13x13 map, |A|=9, 8-bit readings, K=500, D=90; "
+                                 "512 leaf jobs, |Phi_b|~U{1..500}, depth~U{0..10}", (4, 0.5, 0)),
     "rs15_15_k100": (lambda: inputs.rs15_15_k(100), 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=100, D=90; "
                                                          "4096 leaf jobs, |Phi_b|~U{1..100}", (4, 0.5, 0)),
     "rs15_15_k250": (lambda: inputs.rs15_15_k(250), 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=250, D=90; "
                                                          "4096 leaf jobs, |Phi_b|~U{1..250}", (4, 0.5, 0)),
 }
 SWEEP = ["car6", "car12", "car20", "car50", "rs15_15_k100", "rs15_15_k250", "rs15_15", "mars11_11", "mars15_15",
-         "mars20_20"]
+         "mars20_20", "nav13"]
 SMS, LANES_PER_SM, MAX_SM_MHZ = 148, 128, 2032.0
 try:
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
@@ -72,6 +74,7 @@ METRIC = "scenario-steps/sec and leaf expansions/sec at K=500, D=90 (fraction of
 KERNEL_SOURCES = {
     "rs": ["expand_rs.cu", "rs_model.cuh", "rs_common.cuh", "common.cuh"],
     "car": ["expand_car.cu", "car_model.cuh", "group.cuh", "common.cuh"],
+    "nav": ["expand_nav.cu", "nav_model.cuh", "group.cuh", "common.cuh"],
 }
 
 
@@ -204,7 +207,7 @@ def cpu_oracle_run(cfg, jobs, seconds, threads):
 
 
 def _dtype(cfg):
-    return "f32" if cfg.kind == inputs.CAR else "int32"
+    return "f32" if cfg.kind in (inputs.CAR, inputs.NAV) else "int32"
 
 
 def run_reference(args, rank, world):
@@ -420,7 +423,7 @@ def run_ours(args, rank, world):
     for _ in range(max(3, args.warmup)):
         jb.run()
     torch.cuda.synchronize()
-    kernels_per_step = 1 if cfg.kind == inputs.CAR else 2
+    kernels_per_step = 1 if cfg.kind in (inputs.CAR, inputs.NAV) else 2
 
     # device-resident timing (L2 flushed before every step, outside the events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -498,7 +501,7 @@ def run_ours(args, rank, world):
     # the model creates its queue (and the kernel's graph) on the first such
     # step and keeps it, so the second step is what a replanning loop sees
     planning_queue = None
-    if not args.no_plan and cfg.kind != inputs.CAR and not plan[2]:
+    if not args.no_plan and cfg.kind in (inputs.GRID, inputs.MULTIGRID) and not plan[2]:
         first = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
         planning_queue = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
         planning_queue["first_step_with_queue_creation"] = {k: first[k] for k in ("expansions", "seconds",
@@ -529,7 +532,7 @@ def run_ours(args, rank, world):
                          f"{r1['seconds']:.1f} s", "ops_per_scenario_step": ops_per_step,
                "all_cores": {"value": rn["steps"] / rn["seconds"], "cores": cores,
                              "sample": f"first {rn['jobs']} jobs on {cores} threads, {rn['seconds']:.1f} s"}}
-    kind = "car" if cfg.kind == inputs.CAR else "rs"
+    kind = {inputs.CAR: "car", inputs.NAV: "nav"}.get(cfg.kind, "rs")
     avg_kernel_s = kernel_ms / max(1, kernel_calls) / 1000.0
     peak_tops = SMS * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     roof = None
@@ -540,8 +543,8 @@ def run_ours(args, rank, world):
                 "frac": achieved / peak_tops, "traffic": traffic,
                 "peak_source": "derived: 148 SMs x 128 lanes x 2032 MHz (one 32-bit op per lane per clock)",
                 "probe_tops": probe_tops, "ops_per_scenario_step": ops_per_step,
-                "kernel": ("rs_group_kernel + rs_rollout_items_kernel (one expansion)" if kind == "rs"
-                           else "car_expand_kernel"),
+                "kernel": {"rs": "rs_group_kernel + rs_rollout_items_kernel (one expansion)",
+                           "car": "car_expand_kernel", "nav": "nav_expand_kernel"}[kind],
                 "kernel_ms_per_launch": avg_kernel_s * 1000.0,
                 "achieved_hbm_gbs": (jb.input_bytes + jb.output_bytes) / avg_kernel_s / 1e9}
     line = {

@@ -33,7 +33,7 @@ __device__ __forceinline__ void load_gamma(float* G, const DevModel* gm) {
   for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) G[k] = gm->G[k];
 }
 
-__global__ void __launch_bounds__(256) nav_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__global__ void __launch_bounds__(256, 4) nav_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                          const dsp_leaf_job* __restrict__ jobs,
                                                          const int4* __restrict__ units, int n_units,
                                                          unsigned int* head, uint32_t plan_step) {
