@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) nav_rollout_kernel(const DevModel* __rest
   const NavModel M = make_nav(gm, G, plan_step);
   unsigned long long steps = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const NavS s = M.load(block, cap, i);
+    NavS s = M.load(block, cap, i);
     const uint32_t last = hist != nullptr ? (uint32_t)(uint8_t)hist[(size_t)32 * i] : 0u;
     value[i] = M.rollout(s, last, start_depth, steps);
   }

@@ -73,6 +73,13 @@ struct NavModel {
     b[(size_t)(1 + mw) * cap + i] = s.scen;
   }
 
+  // Bit k-1 of the observation: neighbour k's occupancy, flipped by its word.
+  __device__ __forceinline__ uint32_t reading(const NavS& s, int k, uint32_t u) const {
+    const bool occ = occupied(s, s.x + dx(k), s.y + dy(k));
+    const bool flip = (uint64_t)u < sense_thresh;
+    return (uint32_t)(occ != flip) << (k - 1);
+  }
+
   // g(s, a, phi_t); returns the reward, writes the observation key.
   __device__ __forceinline__ float step(NavS& s, int a, int t, uint64_t& key) const {
     if (s.term) {
@@ -108,14 +115,15 @@ struct NavModel {
     }
     const U4 w0 = scen_random(seed, s.scen, (uint32_t)t, 2u, 0u, plan_step);
     const U4 w1 = scen_random(seed, s.scen, (uint32_t)t, 2u, 1u, plan_step);
-    const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
     uint32_t z = 0;
-#pragma unroll
-    for (int k = 1; k <= 8; ++k) {
-      const bool occ = occupied(s, s.x + dx(k), s.y + dy(k));
-      const bool flip = (uint64_t)w[k - 1] < sense_thresh;
-      z |= (uint32_t)(occ != flip) << (k - 1);
-    }
+    z |= reading(s, 1, w0.x);
+    z |= reading(s, 2, w0.y);
+    z |= reading(s, 3, w0.z);
+    z |= reading(s, 4, w0.w);
+    z |= reading(s, 5, w1.x);
+    z |= reading(s, 6, w1.y);
+    z |= reading(s, 7, w1.z);
+    z |= reading(s, 8, w1.w);
     key = z;
     return r;
   }
@@ -148,7 +156,7 @@ struct NavModel {
   }
 
   // Eq. lb from depth t0 with the last reading `last`; the tail is 0.
-  __device__ __forceinline__ float rollout(NavS s, uint32_t last, int t0, unsigned long long& steps) const {
+  __device__ __forceinline__ float rollout(NavS& s, uint32_t last, int t0, unsigned long long& steps) const {
     float v = 0.0f;
     int t = t0;
     while (t < D && !s.term) {
