@@ -47,10 +47,15 @@ struct NavModel {
   __device__ __forceinline__ bool occupied(const NavS& s, int x, int y) const {
     if (x < 0 || y < 0 || x >= n || y >= n) return true;
     const int c = y * n + x;
-    uint32_t w = 0;
-#pragma unroll
-    for (int k = 0; k < kNavMaxWords; ++k)
-      if (k == (c >> 5)) w = s.occ[k];
+    const int k = c >> 5;
+    // a select tree over the eight words keeps the map in registers
+    const uint32_t a01 = (k & 1) ? s.occ[1] : s.occ[0];
+    const uint32_t a23 = (k & 1) ? s.occ[3] : s.occ[2];
+    const uint32_t a45 = (k & 1) ? s.occ[5] : s.occ[4];
+    const uint32_t a67 = (k & 1) ? s.occ[7] : s.occ[6];
+    const uint32_t b03 = (k & 2) ? a23 : a01;
+    const uint32_t b47 = (k & 2) ? a67 : a45;
+    const uint32_t w = (k & 4) ? b47 : b03;
     return (w >> (c & 31)) & 1u;
   }
 
