@@ -44,6 +44,11 @@ class _SearchResult(C.Structure):
                 ("signature", C.c_uint64)]
 
 
+class _PomcpResult(C.Structure):
+    _fields_ = [("action", C.c_int32), ("value", C.c_double), ("nodes", C.c_int32), ("simulations", C.c_int32),
+                ("rollouts", C.c_int32), ("steps", C.c_uint64), ("signature", C.c_uint64)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -201,6 +206,21 @@ class Model:
         return dict(root_u=res.root_u, root_l=res.root_l, action=res.action, nodes=res.nodes,
                     expansions=res.expansions, rounds=res.rounds, steps=res.steps, signature=res.signature,
                     root_na=na)
+
+    def pomcp(self, root_block, hist, rounds=10, batch=64, c=1.0):
+        """POMCP-style planning from the root scenarios (oracle/pomcp.hpp)."""
+        root_block = np.ascontiguousarray(root_block, np.uint32)
+        w, n = root_block.shape
+        h = np.zeros(32, np.int8) if hist is None else np.ascontiguousarray(hist, np.int8)
+        na = self.num_actions()
+        q = np.zeros(na, np.float64)
+        nav = np.zeros(na, np.int32)
+        out = _PomcpResult()
+        rc = lib().orc_pomcp(C.byref(self.c), _p(root_block, _U32), C.c_int32(n), _p(h, _I8), C.c_int32(rounds),
+                             C.c_int32(batch), C.c_double(c), C.byref(out), _p(q, _F64), _p(nav, _I32))
+        assert rc == 0
+        return dict(action=out.action, value=out.value, nodes=out.nodes, simulations=out.simulations,
+                    rollouts=out.rollouts, steps=out.steps, signature=out.signature, root_q=q, root_na=nav)
 
     def exhaustive(self, block, hist, depth):
         block = np.ascontiguousarray(block, np.uint32)

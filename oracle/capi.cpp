@@ -10,6 +10,7 @@
 
 #include "despot.hpp"
 #include "mlp.hpp"
+#include "pomcp.hpp"
 
 using namespace orc;
 
@@ -298,6 +299,39 @@ int32_t orc_plan(const orc_model* d, const uint32_t* root_block, int32_t n, cons
     out->signature = r.signature;
     if (root_na)
       for (size_t a = 0; a < r.root_na.size(); ++a) root_na[a] = r.root_na[a];
+  });
+}
+
+typedef struct {
+  int32_t action;
+  double value;
+  int32_t nodes, simulations, rollouts;
+  uint64_t steps, signature;
+} orc_pomcp_result;
+
+// POMCP-style planning (pomcp.hpp) from the given root scenarios.
+int32_t orc_pomcp(const orc_model* d, const uint32_t* root_block, int32_t n, const int8_t* hist, int32_t rounds,
+                  int32_t batch, double c, orc_pomcp_result* out, double* root_q, int32_t* root_na) {
+  return with_model(d, [&](const auto& m) {
+    auto st = unpack_all(m, root_block, n, n);
+    using S = typename decltype(st)::value_type;
+    PomcpParams prm;
+    prm.rounds = rounds;
+    prm.batch = batch;
+    prm.c = c;
+    Pomcp<std::decay_t<decltype(m)>, S> pc(m, prm);
+    PomcpResult r = pc.plan(st, hist_from(hist));
+    out->action = r.action;
+    out->value = r.value;
+    out->nodes = r.nodes;
+    out->simulations = r.simulations;
+    out->rollouts = r.rollouts;
+    out->steps = r.steps;
+    out->signature = r.signature;
+    for (size_t a = 0; a < r.root_q.size(); ++a) {
+      if (root_q) root_q[a] = r.root_q[a];
+      if (root_na) root_na[a] = r.root_na[a];
+    }
   });
 }
 
