@@ -244,6 +244,46 @@ dsp_status dsp_plan_nodes(dsp_model* model, const uint32_t* root_states, int32_t
                           const dsp_search_params* params, dsp_search_result* result, int32_t* root_visits,
                           int32_t min_scen, int32_t cap, dsp_plan_node* nodes, uint32_t* states, int32_t* count);
 
+/* POMCP-style planning (the single-scenario-per-path variant the paper names
+ * among its future directions, Sec. V) on the same models and scenario
+ * streams, with the GPU as the rollout service. UCT over histories: each
+ * simulation carries one root scenario (simulation i of the plan takes
+ * scenario i mod n) down the tree and rolls the default policy out from the
+ * first new node. A round runs `batch` simulations level by level: at each
+ * level the live simulations, in index order, choose by UCB1 on the action
+ * values as they stood at the round's start plus one virtual visit per
+ * earlier choice of the same action at the same node in this round (an
+ * unvisited action first, lowest index on ties); one dsp_step call steps them
+ * all; a simulation moves to the child of (action, observation), creating it
+ * if new. It stops at a terminal outcome, at depth D (value 0 below), or at a
+ * node created in this round, where it takes a rollout: one dsp_rollout call
+ * per start depth. Backups run in simulation order: N += 1, N(a) += 1,
+ * Q(a) += (G - Q(a)) / N(a) with G the discounted return. Nodes are numbered
+ * in creation order (level, then simulation index).
+ * root_states: HOST state block of n scenarios (capacity n). hist: HOST,
+ * 32 counters (NULL = zeros). root_q / root_na: HOST arrays of |A| entries
+ * (may be NULL). Planning stops after `rounds` rounds, or after time_limit_s
+ * (> 0) at the end of a round. DSP_E_INVALID for bad arguments. */
+typedef struct {
+  int32_t rounds;       /* rounds of simulations, >= 1 */
+  int32_t batch;        /* simulations per round, 1..65536 */
+  double c;             /* UCB1 exploration constant */
+  double time_limit_s;  /* 0 = none */
+} dsp_pomcp_params;
+
+typedef struct {
+  int32_t action;           /* argmax_a Q(root, a) over visited actions, lowest index on ties */
+  double value;             /* Q(root, action) */
+  int32_t nodes, simulations, rollouts, rounds;
+  uint64_t scenario_steps;  /* g calls on live scenarios (tree steps and rollouts) */
+  uint64_t signature;       /* digest of the tree in creation order */
+  double seconds;
+} dsp_pomcp_result;
+
+dsp_status dsp_pomcp_plan(dsp_model* model, const uint32_t* root_states, int32_t n, const int8_t* hist,
+                          const dsp_pomcp_params* params, dsp_pomcp_result* result, double* root_q,
+                          int32_t* root_na);
+
 /* Launch shape of dsp_expand_leaves (the paper's fixed mapping of actions to
  * blocks and scenarios to threads, Sec. III-D, made a tunable): block = CTA
  * size of the Rock Sample rollout phase (128, 256 or 512; the car kernel runs

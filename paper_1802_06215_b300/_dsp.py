@@ -208,6 +208,36 @@ def dsp_plan(h, root_states, hist, params, num_actions):
     return out
 
 
+class dsp_pomcp_params(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("batch", C.c_int32), ("c", C.c_double), ("time_limit_s", C.c_double)]
+
+
+class dsp_pomcp_result(C.Structure):
+    _fields_ = [("action", C.c_int32), ("value", C.c_double), ("nodes", C.c_int32), ("simulations", C.c_int32),
+                ("rollouts", C.c_int32), ("rounds", C.c_int32), ("scenario_steps", C.c_uint64),
+                ("signature", C.c_uint64), ("seconds", C.c_double)]
+
+
+def dsp_pomcp_plan(h, root_states, hist, params, num_actions):
+    """POMCP-style planning; root_states: numpy uint32 (words, n); hist: numpy int8[32] or None."""
+    import numpy as np
+    rs = np.ascontiguousarray(root_states, dtype=np.uint32)
+    n = rs.shape[1]
+    hs = None if hist is None else np.ascontiguousarray(hist, dtype=np.int8)
+    res = dsp_pomcp_result()
+    q = np.zeros(num_actions, np.float64)
+    na = np.zeros(num_actions, np.int32)
+    L = lib()
+    L.dsp_pomcp_plan.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(dsp_pomcp_params),
+                                 C.POINTER(dsp_pomcp_result), C.c_void_p, C.c_void_p]
+    check(L.dsp_pomcp_plan(h, rs.ctypes.data, n, None if hs is None else hs.ctypes.data, C.byref(params),
+                           C.byref(res), q.ctypes.data, na.ctypes.data))
+    out = {f: getattr(res, f) for f, _ in dsp_pomcp_result._fields_}
+    out["root_q"] = q
+    out["root_na"] = na
+    return out
+
+
 def dsp_queue_create(h, capacity, idle_ns=0):
     L = lib()
     L.dsp_queue_create.argtypes = [C.c_void_p, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]

@@ -40,6 +40,37 @@ struct dsp_model {
 
 namespace dsp {
 
+// The history update a node's child takes from its observation key (the
+// default policies' input): Rock Sample belief counters (+-1 per Sense
+// reading, clamped to +-127), the navigation's last reading in counter 0, and
+// nothing for the car.
+inline void host_observe(int kind, int per_robot, int8_t* h, int a, uint64_t key) {
+  if (kind == DSP_MODEL_CAR) return;
+  if (kind == DSP_MODEL_NAV) {
+    if (!(key & (1ull << 62))) h[0] = (int8_t)(uint8_t)(key & 0xFFu);
+    return;
+  }
+  const int z = (int)(key & ~(1ull << 62));
+  int acts[2], zs[2];
+  const int robots = kind == DSP_MODEL_GRID ? 1 : 2;
+  if (robots == 1) {
+    acts[0] = a;
+    zs[0] = z;
+  } else {
+    acts[0] = a / per_robot;
+    acts[1] = a % per_robot;
+    zs[0] = z / 3;
+    zs[1] = z % 3;
+  }
+  for (int r = 0; r < robots; ++r) {
+    if (acts[r] >= 5 && zs[r] != 0) {
+      const int i = acts[r] - 5;
+      const int v = (int)h[i] + (zs[r] == 1 ? 1 : -1);
+      h[i] = (int8_t)(v > 127 ? 127 : (v < -127 ? -127 : v));
+    }
+  }
+}
+
 dsp_status fail(dsp_status st, const char* fmt, ...);
 dsp_status cuda_fail(cudaError_t e, const char* what);
 

@@ -166,31 +166,7 @@ class Search {
     return pool_.back().get();
   }
 
-  void observe(int8_t* h, int a, uint64_t key) const {
-    if (kind_ == DSP_MODEL_CAR) return;
-    if (kind_ == DSP_MODEL_NAV) {  // the last reading is the default policy's history
-      if (!(key & (1ull << 62))) h[0] = (int8_t)(uint8_t)(key & 0xFFu);
-      return;
-    }
-    int z = (int)(key & ~(1ull << 62));
-    int acts[2], zs[2], robots = kind_ == DSP_MODEL_GRID ? 1 : 2;
-    if (robots == 1) {
-      acts[0] = a;
-      zs[0] = z;
-    } else {
-      acts[0] = a / per_;
-      acts[1] = a % per_;
-      zs[0] = z / 3;
-      zs[1] = z % 3;
-    }
-    for (int r = 0; r < robots; ++r) {
-      if (acts[r] >= 5 && zs[r] != 0) {
-        int i = acts[r] - 5;
-        int v = (int)h[i] + (zs[r] == 1 ? 1 : -1);
-        h[i] = (int8_t)(v > 127 ? 127 : (v < -127 ? -127 : v));
-      }
-    }
-  }
+  void observe(int8_t* h, int a, uint64_t key) const { host_observe(kind_, per_, h, a, key); }
 
   void refresh(Node* b) {
     double bu = -std::numeric_limits<double>::infinity(), bl = bu;
