@@ -100,6 +100,8 @@ def parse():
                    help="time only the learned-policy rollout kernel on this many start states and exit")
     p.add_argument("--plan-scaling", default="", choices=["", "rs15_15", "mars15_15"],
                    help="planning throughput against search threads (per-leaf launches vs the device queue)")
+    p.add_argument("--pomcp", default="", choices=[""] + list(WORKLOADS),
+                   help="POMCP-style planner with GPU rollouts against the oracle's (one line per batch size)")
     p.add_argument("--sweep", default="", help="'all' or comma-separated workloads: one line per variant")
     p.add_argument("--ref-step-seconds", type=float, default=60.0,
                    help="cap on the oracle's time per step in the reference arm")
@@ -656,6 +658,39 @@ def plan_scaling(args):
     m.close()
 
 
+def pomcp_rate(args):
+    """The POMCP-style planner (dsp_pomcp_plan) with the GPU as its rollout
+    service, against the oracle's planner on one host core over the same
+    rounds from the benchmark's root belief: simulations, rollouts and
+    scenario-steps per second, and whether both planned the same tree."""
+    import oracle
+    from paper_1802_06215_b300 import _dsp, batch, build
+    build.build()
+    mk = WORKLOADS[args.pomcp][0]
+    cfg = mk()
+    m = batch.Model(cfg)
+    b = root_states(cfg, np.random.default_rng(99))
+    for bsz in (256, 1024, 4096):
+        p = _dsp.dsp_pomcp_params(rounds=2, batch=bsz, c=10.0, time_limit_s=0.0)
+        _dsp.dsp_pomcp_plan(m.h, b, None, p, m.num_actions)  # warm
+        rounds = max(2, 16384 // bsz)
+        p = _dsp.dsp_pomcp_params(rounds=rounds, batch=bsz, c=10.0, time_limit_s=0.0)
+        g = _dsp.dsp_pomcp_plan(m.h, b, None, p, m.num_actions)
+        t0 = time.perf_counter()
+        o = oracle.Model(cfg).pomcp(b, None, rounds=rounds, batch=bsz, c=10.0)
+        to = time.perf_counter() - t0
+        print(json.dumps({"pomcp": args.pomcp, "batch": bsz, "rounds": g["rounds"], "seconds": g["seconds"],
+                          "simulations_per_s": g["simulations"] / g["seconds"],
+                          "rollouts_per_s": g["rollouts"] / g["seconds"],
+                          "scenario_steps_per_s": g["scenario_steps"] / g["seconds"],
+                          "nodes": g["nodes"], "root_value": g["value"], "action": g["action"],
+                          "same_tree_as_oracle": bool(o["signature"] == g["signature"] and
+                                                      np.array_equal(o["root_q"], g["root_q"])),
+                          "oracle_1core": {"seconds": to, "simulations_per_s": o["simulations"] / to,
+                                           "scenario_steps_per_s": o["steps"] / to}}), flush=True)
+    m.close()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -674,6 +709,9 @@ def main():
     elif args.plan_scaling:
         if rank == 0:
             plan_scaling(args)
+    elif args.pomcp:
+        if rank == 0:
+            pomcp_rate(args)
     else:
         run_ours(args, rank, world)
 
