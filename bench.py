@@ -425,7 +425,7 @@ def run_ours(args, rank, world):
     for _ in range(max(3, args.warmup)):
         jb.run()
     torch.cuda.synchronize()
-    kernels_per_step = 1 if cfg.kind in (inputs.CAR, inputs.NAV) else 2
+    kernels_per_step = 1 if cfg.kind == inputs.CAR else 2
 
     # device-resident timing (L2 flushed before every step, outside the events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]

@@ -378,6 +378,8 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
     if (J.child_cap < 1 || !J.child_count || !J.child_off || !J.child_key || !J.rew_sum || !J.u_sum || !J.l_sum ||
         !J.perm)
       return fail(DSP_E_INVALID, "job %d: result buffer missing", j);
+    if ((long long)J.n_actions * J.child_cap >= (1LL << 24))
+      return fail(DSP_E_UNSUPPORTED, "job %d: n_actions * child_cap >= 2^24", j);
     if (h->kind == DSP_MODEL_CAR || h->kind == DSP_MODEL_NAV) {
       for (int a = 0; a < J.n_actions; ++a) plan.units.push_back(make_int4(j, a, 1, 0));
     } else {
@@ -397,6 +399,7 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
     for (int4& u : plan.units) {
       u.z = (int)plan.total_items;
       plan.total_items += jobs[u.x].n_scen;
+      if (plan.total_items >= (1LL << 31)) return fail(DSP_E_UNSUPPORTED, "more than 2^31 (action, scenario) items");
     }
   } else {
     plan.order.resize(n_jobs);
@@ -460,8 +463,9 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   size_t ub = by_unit ? sizeof(int4) * plan.units.size()
                   : sizeof(long long) * plan.item_base.size() + sizeof(int) * plan.order.size();
   const bool car_items = car && m->policy_on;
-  size_t ib = by_unit ? (car_items ? sizeof(uint32_t) * (size_t)(h->words + 2) * (size_t)plan.total_items : 0)
-                  : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
+  size_t ib = car   ? (car_items ? sizeof(uint32_t) * (size_t)(h->words + 2) * (size_t)plan.total_items : 0)
+              : nav ? sizeof(uint32_t) * (size_t)nav_item_fields(h->n) * (size_t)plan.total_items
+                    : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
   size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
   unsigned char* buf = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, total, m->pool, st);
@@ -513,7 +517,8 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
       e = launch_car_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, ci, st);
       if (e == cudaSuccess && car_items) e = launch_car_rollout_mlp_items(m, djobs, ci, counters + 1, st);
     } else if (nav) {
-      e = launch_nav_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, st);
+      e = launch_nav_expand(m, djobs, (const int4*)dunits, (int)plan.units.size(), counters, items,
+                            plan.total_items, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
       e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, rs_key_words(h), m->dwork, djobs,

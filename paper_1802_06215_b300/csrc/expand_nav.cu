@@ -1,11 +1,20 @@
 // Leaf expansion for navigation in a partially known map (Sec. III-D on the
-// task of Sec. IV-A). One (job, action) unit per CTA pass, largest jobs
-// first; one thread per scenario: gather + update by the action into the
-// leaf, the expansion step g with its 8-bit observation, u0, and the
-// default-policy rollout to depth D in registers. The unit's scenarios are
-// grouped by observation with the shared-memory hash of group.cuh (the key is
-// the observation itself, so no further comparison is needed), and the
-// children's reward, u and l sums are exact int64 fixed-point atomics.
+// task of Sec. IV-A), in two launches.
+//
+// Phase A (nav_group_kernel): one (job, action) unit per CTA pass, largest
+// jobs first; one thread per scenario: gather + update by the action into the
+// leaf, the expansion step g with its 8-bit observation and u0. The unit's
+// scenarios are grouped by observation with the shared-memory hash of
+// group.cuh (the key is the observation itself, so no further comparison is
+// needed); the children's reward and u sums are exact int64 fixed-point
+// atomics, and each scenario's state after the step goes to a rollout item.
+//
+// Phase B (nav_rollout_items_kernel): the default-policy rollouts (Eq. lb) of
+// all items without a barrier. Each scenario carries its own map, so rollouts
+// differ in length; a lane whose rollout ends takes the next item of its
+// warp's chunk (and the warp the next chunk) before the next step, so the
+// lanes stay busy, and adds its value to the child's int64 l sum with one
+// atomic (exact in any order).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,28 +29,34 @@ namespace dsp {
 namespace {
 
 struct NavUnitSmem {
-  float G[kGammaLen];
+  NavTables T;
   uint64_t key[kMaxScen];
-  float rew[kMaxScen], uval[kMaxScen], lval[kMaxScen];
+  float rew[kMaxScen], uval[kMaxScen];
   GroupSmem grp;
-  unsigned long long sr[kMaxScen], su[kMaxScen], sl[kMaxScen];
+  unsigned long long sr[kMaxScen], su[kMaxScen];
   int unit;
   dsp_leaf_job job;
 };
 
-__device__ __forceinline__ void load_gamma(float* G, const DevModel* gm) {
-  for (int k = threadIdx.x; k < kGammaLen; k += blockDim.x) G[k] = gm->G[k];
-}
+// Rollout items, field-major with stride `total`: word 0 = x | y << 8 |
+// terminal << 16 | last reading << 24, then the mw map words, the scenario
+// id, depth << 24 | result slot (action offset * child_cap + child), job.
+struct NavItems {
+  uint32_t* base;
+  long long total;
+  int mw;
+  __device__ __forceinline__ uint32_t* f(int k) const { return base + (size_t)k * (size_t)total; }
+};
 
-__global__ void __launch_bounds__(256, 4) nav_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
-                                                         const dsp_leaf_job* __restrict__ jobs,
-                                                         const int4* __restrict__ units, int n_units,
-                                                         unsigned int* head, uint32_t plan_step) {
+__global__ void __launch_bounds__(256, 4) nav_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                        const dsp_leaf_job* __restrict__ jobs,
+                                                        const int4* __restrict__ units, int n_units,
+                                                        unsigned int* head, NavItems items, uint32_t plan_step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NavUnitSmem& S = *reinterpret_cast<NavUnitSmem*>(smem_raw);
-  load_gamma(S.G, gm);
-  const NavModel M = make_nav(gm, S.G, plan_step);
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  load_nav_tables(S.T, gm);
+  const NavModel M = make_nav(gm, &S.T, plan_step);
+  const int tid = threadIdx.x, nthr = blockDim.x, mw = M.mw;
   unsigned long long steps = 0;
   __syncthreads();
   while (true) {
@@ -58,6 +73,7 @@ __global__ void __launch_bounds__(256, 4) nav_expand_kernel(const DevModel* __re
     const int a = job.first_action + un.y;
     const bool first_unit = un.y == 0;
     const uint32_t last0 = (uint32_t)(uint8_t)job.hist[0];
+    const long long ibase = un.z;
     for (int p = tid; p < n; p += nthr) {
       NavS s = M.load(job.parent, job.parent_cap, job.idx[p]);
       if (job.last_action >= 0) {  // update by the action into this leaf
@@ -65,25 +81,32 @@ __global__ void __launch_bounds__(256, 4) nav_expand_kernel(const DevModel* __re
         uint64_t k0;
         M.step(s, job.last_action, depth - 1, k0);
       }
-      if (first_unit && job.leaf_states != nullptr) M.store(s, job.leaf_states, n, p);
+      const int src = job.idx[p];
+      if (first_unit && job.leaf_states != nullptr) {
+        M.store_pos(s, job.leaf_states, n, p);
+        M.copy_map(job.parent, job.parent_cap, src, job.leaf_states, n, p);
+      }
       // Eq. expand with the observation key
       if (!s.term) steps += 1;
       uint64_t key;
       const float r = M.step(s, a, depth, key);
-      // Eq. ub (the tail heuristic is zero at depth D) and Eq. lb from the
-      // child's history: the reading just taken
+      // Eq. ub (the tail heuristic is zero at depth D); Eq. lb starts from the
+      // child's history, whose last reading is the one just taken
       const float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(s);
       const uint32_t last = (key & kTermBit) ? last0 : (uint32_t)(key & 0xFFu);
-      const float lv = s.term ? 0.0f : M.rollout(s, last, depth + 1, steps);
+      const long long it = ibase + p;
+      items.f(0)[it] = (uint32_t)s.x | ((uint32_t)s.y << 8) | ((uint32_t)s.term << 16) | (last << 24);
+#pragma unroll
+      for (int k = 0; k < kNavMaxWords; ++k)
+        if (k < mw) items.f(1 + k)[it] = job.parent[(size_t)(1 + k) * job.parent_cap + src];
+      items.f(1 + mw)[it] = s.scen;
       S.key[p] = key;
       S.rew[p] = r;
       S.uval[p] = uv;
-      S.lval[p] = lv;
     }
     for (int c = tid; c < n; c += nthr) {
       S.sr[c] = 0;
       S.su[c] = 0;
-      S.sl[c] = 0;
     }
     __syncthreads();
     group_by_key(S.grp, S.key, n);
@@ -92,7 +115,6 @@ __global__ void __launch_bounds__(256, 4) nav_expand_kernel(const DevModel* __re
       const int c = S.grp.gcid[q];
       atomicAdd(&S.sr[c], (unsigned long long)to_fixed(S.rew[q]));
       atomicAdd(&S.su[c], (unsigned long long)to_fixed(S.uval[q]));
-      atomicAdd(&S.sl[c], (unsigned long long)to_fixed(S.lval[q]));
     }
     __syncthreads();
     const int cap = job.child_cap;
@@ -108,11 +130,14 @@ __global__ void __launch_bounds__(256, 4) nav_expand_kernel(const DevModel* __re
       job.child_key[o] = S.key[S.grp.cfirst[c]];
       job.rew_sum[o] = (long long)S.sr[c];
       job.u_sum[o] = (long long)S.su[c];
-      job.l_sum[o] = (long long)S.sl[c];
+      job.l_sum[o] = 0;  // phase B adds the rollouts
     }
     for (int q = tid; q < n; q += nthr) {
       const int c = S.grp.gcid[q];
       job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
+      const long long it = ibase + q;
+      items.f(2 + mw)[it] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
+      items.f(3 + mw)[it] = (uint32_t)un.x;
     }
     __syncthreads();
   }
@@ -120,20 +145,141 @@ __global__ void __launch_bounds__(256, 4) nav_expand_kernel(const DevModel* __re
   if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+constexpr int kNavItemWords = kNavMaxWords + 4;
+constexpr int kWarpsB = 8;  // phase-B CTA: 256 threads
+
+// Per warp, two 32-item chunks of the item list in shared memory: the one the
+// lanes take items from and the next, copied in with cp.async while the
+// current one is rolled out, so that a lane that takes an item reads shared
+// memory instead of waiting on global memory.
+struct NavStage {
+  uint32_t w[2][kNavItemWords][32];
+};
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Claims the next chunk for the warp and starts copying it into buffer b;
+// returns the chunk's item count (0: none left).
+__device__ __forceinline__ int stage_chunk(NavStage& st, int b, const NavItems& items, unsigned int* chunk_head,
+                                           long long nchunks, int nf, int lane) {
+  long long ch = 0;
+  if (lane == 0) ch = (long long)atomicAdd(chunk_head, 1u);
+  ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
+  if (ch >= nchunks) return 0;
+  const long long it = ch * 32 + lane;
+  if (it < items.total)
+    for (int k = 0; k < nf; ++k) cp_async4(&st.w[b][k][lane], items.f(k) + it);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  return (int)min(32LL, items.total - ch * 32);
+}
+
+__global__ void __launch_bounds__(256, 4) nav_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                                const dsp_leaf_job* __restrict__ jobs,
+                                                                NavItems items, unsigned int* chunk_head,
+                                                                uint32_t plan_step) {
+  __shared__ NavTables T;
+  __shared__ NavStage stage[kWarpsB];
+  load_nav_tables(T, gm);
+  __syncthreads();
+  const NavModel M = make_nav(gm, &T, plan_step);
+  const int lane = threadIdx.x & 31, mw = M.mw, nf = mw + 4;
+  NavStage& st = stage[threadIdx.x >> 5];
+  const uint32_t lt = lanemask_lt();
+  const long long nchunks = (items.total + 31) >> 5;
+  // warp-uniform: buffer in use, items handed out of it, its size, the next's size
+  int cur = 0, off = 0;
+  int cur_n = stage_chunk(st, 0, items, chunk_head, nchunks, nf, lane);
+  int next_n = cur_n ? stage_chunk(st, 1, items, chunk_head, nchunks, nf, lane) : 0;
+  if (next_n)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  bool have = false;  // this lane holds an item
+  NavS s{};
+  uint32_t last = 0, slot = 0, job = 0;
+  int t = 0, t0 = 0;
+  float v = 0.0f;
+  unsigned long long steps = 0;
+  while (true) {
+    // idle lanes take the next items, in lane order
+    uint32_t idle = __ballot_sync(0xFFFFFFFFu, !have);
+    while (idle != 0u && (off < cur_n || next_n > 0)) {
+      if (off >= cur_n) {  // switch to the next chunk, start copying the one after
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        cur ^= 1;
+        cur_n = next_n;
+        off = 0;
+        next_n = stage_chunk(st, cur ^ 1, items, chunk_head, nchunks, nf, lane);
+      }
+      const int give = min(__popc(idle), cur_n - off);
+      const int rank = __popc(idle & lt);
+      if (!have && rank < give) {
+        const int i = off + rank;
+        const uint32_t w0 = st.w[cur][0][i];
+        s.x = (int)(w0 & 0xFFu);
+        s.y = (int)((w0 >> 8) & 0xFFu);
+        s.term = (w0 >> 16) & 1u;
+        last = w0 >> 24;
+        M.set_rows(s, [&](int k) { return st.w[cur][1 + k][i]; });
+        s.scen = st.w[cur][1 + mw][i];
+        s.nb = s.term ? 0u : M.neighbourhood(s);
+        const uint32_t meta = st.w[cur][2 + mw][i];
+        job = st.w[cur][3 + mw][i];
+        slot = meta & 0xFFFFFFu;
+        t0 = (int)(meta >> 24) + 1;
+        t = t0;
+        v = 0.0f;
+        have = true;
+      }
+      off += give;
+      idle = __ballot_sync(0xFFFFFFFFu, !have);
+    }
+    if (__ballot_sync(0xFFFFFFFFu, have) == 0u) break;
+    // one step of the default policy (the body of NavModel::rollout)
+    if (have && t < M.D && !s.term) {
+      uint64_t key;
+      const float r = M.step(s, M.policy(last), t, key);
+      steps += 1;
+      if (!(key & kTermBit)) last = (uint32_t)(key & 0xFFu);
+      v = __fadd_rn(v, __fmul_rn(T.G[t - t0], r));
+      t += 1;
+    }
+    if (have && (t >= M.D || s.term)) {
+      const long long fl = to_fixed(v);
+      if (fl != 0) atomicAdd((unsigned long long*)(jobs[job].l_sum + slot), (unsigned long long)fl);
+      have = false;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if (lane == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
 // dsp_step: one g call per scenario.
-__global__ void __launch_bounds__(256) nav_step_kernel(const DevModel* __restrict__ gm, const uint32_t* in,
+__global__ void __launch_bounds__(256, 4) nav_step_kernel(const DevModel* __restrict__ gm, const uint32_t* in,
                                                        int in_cap, int count, const int32_t* actions, int depth,
                                                        uint32_t* out, int out_cap, uint64_t* keys, float* rewards,
                                                        uint32_t plan_step) {
-  __shared__ float G[kGammaLen];
-  load_gamma(G, gm);
+  __shared__ NavTables T;
+  load_nav_tables(T, gm);
   __syncthreads();
-  const NavModel M = make_nav(gm, G, plan_step);
+  const NavModel M = make_nav(gm, &T, plan_step);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     NavS s = M.load(in, in_cap, i);
     uint64_t key;
     const float r = M.step(s, actions[i], depth, key);
-    M.store(s, out, out_cap, i);
+    M.store_pos(s, out, out_cap, i);
+    M.copy_map(in, in_cap, i, out, out_cap, i);
     keys[i] = key;
     rewards[i] = r;
   }
@@ -141,14 +287,14 @@ __global__ void __launch_bounds__(256) nav_step_kernel(const DevModel* __restric
 
 // dsp_rollout: Eq. lb per scenario from start_depth; the last reading is byte 0
 // of the scenario's 32-byte history (0 without a history).
-__global__ void __launch_bounds__(256) nav_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__global__ void __launch_bounds__(256, 4) nav_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                           const uint32_t* block, int cap, int count,
                                                           const int8_t* hist, int start_depth, float* value,
                                                           uint32_t plan_step) {
-  __shared__ float G[kGammaLen];
-  load_gamma(G, gm);
+  __shared__ NavTables T;
+  load_nav_tables(T, gm);
   __syncthreads();
-  const NavModel M = make_nav(gm, G, plan_step);
+  const NavModel M = make_nav(gm, &T, plan_step);
   unsigned long long steps = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     NavS s = M.load(block, cap, i);
@@ -161,15 +307,26 @@ __global__ void __launch_bounds__(256) nav_rollout_kernel(const DevModel* __rest
 
 }  // namespace
 
+int nav_item_fields(int n) { return (n * n + 31) / 32 + 4; }
+
 cudaError_t launch_nav_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
-                              unsigned int* head, cudaStream_t st) {
+                              unsigned int* counters, uint32_t* items, long long total_items, cudaStream_t st) {
   const size_t smem = sizeof(NavUnitSmem);
-  cudaError_t e = cudaFuncSetAttribute(nav_expand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(nav_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nav_expand_kernel, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nav_group_kernel, 256, smem);
   const int grid = std::max(1, std::min(n_units, std::max(1, per_sm) * m->num_sms));
-  nav_expand_kernel<<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, head, m->plan_step);
+  const NavItems it{items, total_items, (m->host->n * m->host->n + 31) / 32};
+  nav_group_kernel<<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, counters, it, m->plan_step);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int per_sm_b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, nav_rollout_items_kernel, 32 * kWarpsB, 0);
+  const long long warps = (total_items + 31) / 32;
+  const int grid_b = (int)std::max(
+      1LL, std::min((warps + kWarpsB - 1) / kWarpsB, (long long)std::max(1, per_sm_b) * m->num_sms));
+  nav_rollout_items_kernel<<<grid_b, 32 * kWarpsB, 0, st>>>(m->dmodel, m->dwork, djobs, it, counters + 1, m->plan_step);
   return cudaGetLastError();
 }
 

@@ -84,8 +84,12 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
 dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
                          cudaStream_t st);
 
+// Navigation expansion: phase A groups each (job, action) unit and writes one
+// rollout item per scenario (nav_item_fields(n) words each, field-major);
+// phase B rolls the items out. counters[0] and counters[1] start at 0.
+int nav_item_fields(int n);
 cudaError_t launch_nav_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
-                              unsigned int* head, cudaStream_t st);
+                              unsigned int* counters, uint32_t* items, long long total_items, cudaStream_t st);
 cudaError_t launch_nav_step(const DevModel* gm, const uint32_t* in, int in_cap, int count, const int32_t* actions,
                             int depth, uint32_t* out, int out_cap, uint64_t* keys, float* rewards, uint32_t plan_step,
                             cudaStream_t st);
