@@ -158,10 +158,9 @@ typedef struct {
  * nothing; n_actions * child_cap >= 2^24 in a job, or more than 2^31
  * (action, scenario) pairs in the call, returns DSP_E_UNSUPPORTED. Asynchronous
  * on `stream`. Work buffers (job table, rollout-item list, about 28 B per
- * (action, scenario) for one robot, 4 * (ceil(n^2 / 32) + 4) B for
- * navigation) come from a memory pool the model owns; the pool keeps its
- * largest size mapped until dsp_destroy_model, so repeated calls do not map
- * memory again. */
+ * (action, scenario) for one robot, 52 B for navigation) come from a memory
+ * pool the model owns; the pool keeps its largest size mapped until
+ * dsp_destroy_model, so repeated calls do not map memory again. */
 dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
 /* Device job queue (Sec. III-D, node-level parallelism: the paper launches one

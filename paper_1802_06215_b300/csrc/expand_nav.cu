@@ -38,13 +38,15 @@ struct NavUnitSmem {
   dsp_leaf_job job;
 };
 
-// Rollout items, field-major with stride `total`: word 0 = x | y << 8 |
-// terminal << 16 | last reading << 24, then the mw map words, the scenario
-// id, depth << 24 | result slot (action offset * child_cap + child), job.
+// Rollout items, field-major with stride `total`, the state as phase B
+// holds it in registers: word 0 = x | y << 4 | terminal << 8 | neighbours
+// << 9 | last reading << 17, then the kNavRowWords row words of the map, the
+// scenario id, depth << 24 | result slot (action offset * child_cap + child),
+// job.
+constexpr int kNavItemWords = kNavRowWords + 4;
 struct NavItems {
   uint32_t* base;
   long long total;
-  int mw;
   __device__ __forceinline__ uint32_t* f(int k) const { return base + (size_t)k * (size_t)total; }
 };
 
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(256, 4) nav_group_kernel(const DevModel* __res
   NavUnitSmem& S = *reinterpret_cast<NavUnitSmem*>(smem_raw);
   load_nav_tables(S.T, gm);
   const NavModel M = make_nav(gm, &S.T, plan_step);
-  const int tid = threadIdx.x, nthr = blockDim.x, mw = M.mw;
+  const int tid = threadIdx.x, nthr = blockDim.x;
   unsigned long long steps = 0;
   __syncthreads();
   while (true) {
@@ -95,11 +97,10 @@ __global__ void __launch_bounds__(256, 4) nav_group_kernel(const DevModel* __res
       const float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(s);
       const uint32_t last = (key & kTermBit) ? last0 : (uint32_t)(key & 0xFFu);
       const long long it = ibase + p;
-      items.f(0)[it] = (uint32_t)s.x | ((uint32_t)s.y << 8) | ((uint32_t)s.term << 16) | (last << 24);
+      items.f(0)[it] = (uint32_t)s.x | ((uint32_t)s.y << 4) | ((uint32_t)s.term << 8) | (s.nb << 9) | (last << 17);
 #pragma unroll
-      for (int k = 0; k < kNavMaxWords; ++k)
-        if (k < mw) items.f(1 + k)[it] = job.parent[(size_t)(1 + k) * job.parent_cap + src];
-      items.f(1 + mw)[it] = s.scen;
+      for (int k = 0; k < kNavRowWords; ++k) items.f(1 + k)[it] = s.R[k];
+      items.f(1 + kNavRowWords)[it] = s.scen;
       S.key[p] = key;
       S.rew[p] = r;
       S.uval[p] = uv;
@@ -136,8 +137,8 @@ __global__ void __launch_bounds__(256, 4) nav_group_kernel(const DevModel* __res
       const int c = S.grp.gcid[q];
       job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
       const long long it = ibase + q;
-      items.f(2 + mw)[it] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
-      items.f(3 + mw)[it] = (uint32_t)un.x;
+      items.f(2 + kNavRowWords)[it] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
+      items.f(3 + kNavRowWords)[it] = (uint32_t)un.x;
     }
     __syncthreads();
   }
@@ -151,7 +152,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-constexpr int kNavItemWords = kNavMaxWords + 4;
 constexpr int kWarpsB = 8;  // phase-B CTA: 256 threads
 
 // Per warp, two 32-item chunks of the item list in shared memory: the one the
@@ -170,14 +170,15 @@ __device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
 // Claims the next chunk for the warp and starts copying it into buffer b;
 // returns the chunk's item count (0: none left).
 __device__ __forceinline__ int stage_chunk(NavStage& st, int b, const NavItems& items, unsigned int* chunk_head,
-                                           long long nchunks, int nf, int lane) {
+                                           long long nchunks, int lane) {
   long long ch = 0;
   if (lane == 0) ch = (long long)atomicAdd(chunk_head, 1u);
   ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
   if (ch >= nchunks) return 0;
   const long long it = ch * 32 + lane;
   if (it < items.total)
-    for (int k = 0; k < nf; ++k) cp_async4(&st.w[b][k][lane], items.f(k) + it);
+#pragma unroll
+    for (int k = 0; k < kNavItemWords; ++k) cp_async4(&st.w[b][k][lane], items.f(k) + it);
   asm volatile("cp.async.commit_group;" ::: "memory");
   return (int)min(32LL, items.total - ch * 32);
 }
@@ -191,14 +192,14 @@ __global__ void __launch_bounds__(256, 4) nav_rollout_items_kernel(const DevMode
   load_nav_tables(T, gm);
   __syncthreads();
   const NavModel M = make_nav(gm, &T, plan_step);
-  const int lane = threadIdx.x & 31, mw = M.mw, nf = mw + 4;
+  const int lane = threadIdx.x & 31;
   NavStage& st = stage[threadIdx.x >> 5];
   const uint32_t lt = lanemask_lt();
   const long long nchunks = (items.total + 31) >> 5;
   // warp-uniform: buffer in use, items handed out of it, its size, the next's size
   int cur = 0, off = 0;
-  int cur_n = stage_chunk(st, 0, items, chunk_head, nchunks, nf, lane);
-  int next_n = cur_n ? stage_chunk(st, 1, items, chunk_head, nchunks, nf, lane) : 0;
+  int cur_n = stage_chunk(st, 0, items, chunk_head, nchunks, lane);
+  int next_n = cur_n ? stage_chunk(st, 1, items, chunk_head, nchunks, lane) : 0;
   if (next_n)
     asm volatile("cp.async.wait_group 1;" ::: "memory");
   else
@@ -220,22 +221,23 @@ __global__ void __launch_bounds__(256, 4) nav_rollout_items_kernel(const DevMode
         cur ^= 1;
         cur_n = next_n;
         off = 0;
-        next_n = stage_chunk(st, cur ^ 1, items, chunk_head, nchunks, nf, lane);
+        next_n = stage_chunk(st, cur ^ 1, items, chunk_head, nchunks, lane);
       }
       const int give = min(__popc(idle), cur_n - off);
       const int rank = __popc(idle & lt);
       if (!have && rank < give) {
         const int i = off + rank;
         const uint32_t w0 = st.w[cur][0][i];
-        s.x = (int)(w0 & 0xFFu);
-        s.y = (int)((w0 >> 8) & 0xFFu);
-        s.term = (w0 >> 16) & 1u;
-        last = w0 >> 24;
-        M.set_rows(s, [&](int k) { return st.w[cur][1 + k][i]; });
-        s.scen = st.w[cur][1 + mw][i];
-        s.nb = s.term ? 0u : M.neighbourhood(s);
-        const uint32_t meta = st.w[cur][2 + mw][i];
-        job = st.w[cur][3 + mw][i];
+        s.x = (int)(w0 & 0xFu);
+        s.y = (int)((w0 >> 4) & 0xFu);
+        s.term = (w0 >> 8) & 1u;
+        s.nb = (w0 >> 9) & 0xFFu;
+        last = (w0 >> 17) & 0xFFu;
+#pragma unroll
+        for (int k = 0; k < kNavRowWords; ++k) s.R[k] = st.w[cur][1 + k][i];
+        s.scen = st.w[cur][1 + kNavRowWords][i];
+        const uint32_t meta = st.w[cur][2 + kNavRowWords][i];
+        job = st.w[cur][3 + kNavRowWords][i];
         slot = meta & 0xFFFFFFu;
         t0 = (int)(meta >> 24) + 1;
         t = t0;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(256, 4) nav_rollout_kernel(const DevModel* __r
 
 }  // namespace
 
-int nav_item_fields(int n) { return (n * n + 31) / 32 + 4; }
+int nav_item_fields(int) { return kNavItemWords; }
 
 cudaError_t launch_nav_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
                               unsigned int* counters, uint32_t* items, long long total_items, cudaStream_t st) {
@@ -317,7 +319,7 @@ cudaError_t launch_nav_expand(dsp_model* m, const dsp_leaf_job* djobs, const int
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nav_group_kernel, 256, smem);
   const int grid = std::max(1, std::min(n_units, std::max(1, per_sm) * m->num_sms));
-  const NavItems it{items, total_items, (m->host->n * m->host->n + 31) / 32};
+  const NavItems it{items, total_items};
   nav_group_kernel<<<grid, 256, smem, st>>>(m->dmodel, m->dwork, djobs, dunits, n_units, counters, it, m->plan_step);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
