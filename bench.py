@@ -546,7 +546,8 @@ def run_ours(args, rank, world):
                 "peak_source": "derived: 148 SMs x 128 lanes x 2032 MHz (one 32-bit op per lane per clock)",
                 "probe_tops": probe_tops, "ops_per_scenario_step": ops_per_step,
                 "kernel": {"rs": "rs_group_kernel + rs_rollout_items_kernel (one expansion)",
-                           "car": "car_expand_kernel", "nav": "nav_expand_kernel"}[kind],
+                           "car": "car_expand_kernel",
+                           "nav": "nav_group_kernel + nav_rollout_items_kernel (one expansion)"}[kind],
                 "kernel_ms_per_launch": avg_kernel_s * 1000.0,
                 "achieved_hbm_gbs": (jb.input_bytes + jb.output_bytes) / avg_kernel_s / 1e9}
     line = {

@@ -155,11 +155,16 @@ struct NavModel {
       key = kTermBit;
       return 0.0f;
     }
+    // the step's three Philox draws (move failure, two blocks of sensor
+    // words), independent chains issued together; staying does not use the
+    // first, a terminal outcome not the others
+    const uint32_t u = scen_random(seed, s.scen, (uint32_t)t, 1u, 0u, plan_step).x;
+    const U4 w0 = scen_random(seed, s.scen, (uint32_t)t, 2u, 0u, plan_step);
+    const U4 w1 = scen_random(seed, s.scen, (uint32_t)t, 2u, 1u, plan_step);
     float r;
     if (a == 0) {
       r = -0.2f;
     } else {
-      const uint32_t u = scen_random(seed, s.scen, (uint32_t)t, 1u, 0u, plan_step).x;
       if (fail_all || u < fail_th) {
         r = -0.1f;
       } else if ((s.nb >> (a - 1)) & 1u) {
@@ -180,8 +185,6 @@ struct NavModel {
       key = kTermBit;
       return r;
     }
-    const U4 w0 = scen_random(seed, s.scen, (uint32_t)t, 2u, 0u, plan_step);
-    const U4 w1 = scen_random(seed, s.scen, (uint32_t)t, 2u, 1u, plan_step);
     uint32_t f;
     if (sense_all) {
       f = 0xFFu;
