@@ -629,10 +629,11 @@ def sweep(args):
 
 def plan_scaling(args):
     """Planning throughput against search threads, per-leaf launches against
-    the device job queue: three planning steps of 0.3 s per (threads, path)
-    from the benchmark's root belief, xi < 0 so that no trial ends without a
-    leaf (the machinery's rate, not the planner's). One JSON line per point:
-    median, min and max expansions/s."""
+    the device job queue, per-node atomics against one tree lock: three
+    planning steps of 0.3 s per (threads, path, tree) from the benchmark's
+    root belief, xi < 0 so that no trial ends without a leaf (the machinery's
+    rate, not the planner's). One JSON line per point: median, min and max
+    expansions/s."""
     from paper_1802_06215_b300 import _dsp, batch, build
     build.build()
     mk = WORKLOADS[args.plan_scaling][0]
@@ -640,22 +641,25 @@ def plan_scaling(args):
     m = batch.Model(cfg)
     b = root_states(cfg, np.random.default_rng(99))
 
-    def plan(threads, q, secs):
+    def plan(threads, q, lock, secs):
         p = _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=secs, c_a=1.0, c_o=0.5, xi=-1.0,
-                                   target_gap=-1.0, deterministic=0, use_queue=q)
+                                   target_gap=-1.0, deterministic=0, use_queue=q, tree_lock=lock)
         return _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
 
-    plan(4, 0, 0.2)
-    plan(4, 1, 0.2)
+    plan(4, 0, 0, 0.2)
+    plan(4, 1, 0, 0.2)
     for threads in (1, 2, 4, 8, 16, 32):
         for q in (0, 1):
-            r = []
-            for _ in range(3):
-                g = plan(threads, q, 0.3)
-                r.append(g["expansions"] / g["seconds"])
-            print(json.dumps({"plan_scaling": args.plan_scaling, "threads": threads,
-                              "path": "device queue" if q else "per-leaf launches",
-                              "expansions_per_s": statistics.median(r), "min": min(r), "max": max(r)}), flush=True)
+            for lock in (0, 1):
+                r = []
+                for _ in range(3):
+                    g = plan(threads, q, lock, 0.3)
+                    r.append(g["expansions"] / g["seconds"])
+                print(json.dumps({"plan_scaling": args.plan_scaling, "threads": threads,
+                                  "path": "device queue" if q else "per-leaf launches",
+                                  "tree": "one tree lock" if lock else "per-node atomics",
+                                  "expansions_per_s": statistics.median(r), "min": min(r), "max": max(r)}),
+                      flush=True)
     m.close()
 
 

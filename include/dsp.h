@@ -202,6 +202,10 @@ typedef struct {
   int32_t use_queue;     /* free running, Rock Sample: threads submit their leaves to one device job queue
                             (dsp_queue_*) instead of launching their own expansions; the model keeps that
                             queue (capacity max(64, 4 x threads)) until dsp_destroy_model */
+  int32_t tree_lock;     /* free running: 0 = select and back up on per-node atomics without a lock (a leaf
+                            claimed by compare-and-swap, counts as atomic increments, bounds as atomic stores;
+                            the tree's bounds are recomputed bottom-up once the threads join); 1 = under
+                            one tree lock */
 } dsp_search_params;
 
 typedef struct {

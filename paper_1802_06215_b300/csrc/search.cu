@@ -16,8 +16,16 @@
 //    their leaves are expanded as one batch, and they back up in thread
 //    order, so the tree is reproducible bit for bit;
 //  - free running: T std::threads, each with its own CUDA stream
-//    (Sec. III-D, node-level parallelism), selecting and backing up under one
-//    tree lock and expanding concurrently.
+//    (Sec. III-D, node-level parallelism), expanding concurrently. They select
+//    and back up either on per-node atomics, without a lock (the default: a
+//    leaf is claimed by compare-and-swap, visit and virtual-loss counts are
+//    atomic increments, bounds are atomic stores recomputed from the children,
+//    children are published with release ordering), or under one tree lock.
+//    Without the lock two backups through a node may interleave and leave it
+//    a bound computed from an older child value: still a bound (the older
+//    value is looser), and the next backup through the node refreshes it; a
+//    bottom-up pass over the tree after the threads join makes every node
+//    exact again.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -71,10 +79,20 @@ class Arena {
   size_t cap_ = 0, off_ = 0;
 };
 
+template <class T>
+T ld(const std::atomic<T>& x) {
+  return x.load(std::memory_order_relaxed);
+}
+template <class T>
+void wr(std::atomic<T>& x, T v) {
+  x.store(v, std::memory_order_relaxed);
+}
+
 struct Node;
 struct QBranch {
-  double R = 0, U = 0, L = 0;
-  std::vector<Node*> ch;
+  double R = 0;                 // set before the node is published
+  std::atomic<double> U{0.0}, L{0.0};
+  std::vector<Node*> ch;        // set before the node is published, then read-only
 };
 struct Node {
   int depth = 0, n = 0;
@@ -86,12 +104,15 @@ struct Node {
   uint16_t* d_perm = nullptr;      // grouped positions written by the expansion
   int8_t hist[32] = {};
   uint64_t key = 0;
-  bool term = false, expanded = false, claimed = false;
-  double U = 0, L = 0;
-  long long N = 0;
-  std::vector<long long> Na;
-  int vl = 0;
-  std::vector<QBranch> q;
+  bool term = false;
+  std::atomic<bool> expanded{false};  // children published (release / acquire)
+  std::atomic<bool> claimed{false};   // a thread is expanding this leaf
+  std::atomic<double> U{0.0}, L{0.0};
+  std::atomic<long long> N{0};
+  std::unique_ptr<std::atomic<long long>[]> Na;
+  std::atomic<int> vl{0};
+  std::unique_ptr<QBranch[]> q;
+  int nq = 0;
 };
 
 // Pinned host buffer of one search thread, grown on demand.
@@ -165,39 +186,50 @@ class Search {
     pool_.emplace_back(new Node());
     return pool_.back().get();
   }
+  // count new nodes in creation order under one acquisition of the pool lock
+  void new_nodes(int count, std::vector<Node*>& out) {
+    out.clear();
+    std::lock_guard<std::mutex> lock(pool_mu_);
+    for (int k = 0; k < count; ++k) {
+      pool_.emplace_back(new Node());
+      out.push_back(pool_.back().get());
+    }
+  }
 
   void observe(int8_t* h, int a, uint64_t key) const { host_observe(kind_, per_, h, a, key); }
 
   void refresh(Node* b) {
     double bu = -std::numeric_limits<double>::infinity(), bl = bu;
-    for (auto& q : b->q) {
-      bu = std::max(bu, q.U);
-      bl = std::max(bl, q.L);
+    for (int a = 0; a < b->nq; ++a) {
+      bu = std::max(bu, ld(b->q[a].U));
+      bl = std::max(bl, ld(b->q[a].L));
     }
-    b->U = bu;
-    b->L = bl;
+    wr(b->U, bu);
+    wr(b->L, bl);
   }
   void refresh_action(Node* b, int a) {
     QBranch& q = b->q[a];
     double su = 0, sl = 0;
     for (Node* c : q.ch) {
-      su += c->U;
-      sl += c->L;
+      su += ld(c->U);
+      sl += ld(c->L);
     }
-    q.U = q.R + gamma_ * su;
-    q.L = q.R + gamma_ * sl;
+    wr(q.U, q.R + gamma_ * su);
+    wr(q.L, q.R + gamma_ * sl);
   }
 
   int choose_action(Node* b) const {
     int best = 0;
     double bestv = -std::numeric_limits<double>::infinity();
-    for (int a = 0; a < (int)b->q.size(); ++a) {
-      double v = b->q[a].U / b->W;
+    const long long N = ld(b->N);
+    for (int a = 0; a < b->nq; ++a) {
+      double v = ld(b->q[a].U) / b->W;
       if (p_.c_a != 0) {
-        if (b->Na[a] == 0)
+        const long long na = ld(b->Na[a]);
+        if (na == 0)
           v = std::numeric_limits<double>::infinity();
         else
-          v += p_.c_a * std::sqrt(std::log((double)b->n * (double)b->N) / ((double)b->n * (double)b->Na[a]));
+          v += p_.c_a * std::sqrt(std::log((double)b->n * (double)N) / ((double)b->n * (double)na));
       }
       if (v > bestv) {
         bestv = v;
@@ -207,28 +239,34 @@ class Search {
     return best;
   }
 
-  // Forward search of one trial from the root (caller holds the tree lock).
+  // Forward search of one trial from the root (under the tree lock, or on
+  // the nodes' atomics). A leaf is taken by compare-and-swap on its claim
+  // flag; in_flight_ counts it before the claim can be seen.
   Trial select() {
     Trial t;
-    t.epoch = published_;
+    t.epoch = published_.load();
     Node* b = root_;
     t.path.push_back(b);
     while (true) {
-      if (!b->expanded) {
-        if (b->depth < D_ && !b->term && !b->claimed) {
-          b->claimed = true;
-          t.leaf = b;
+      if (!b->expanded.load(std::memory_order_acquire)) {
+        if (b->depth < D_ && !b->term && !ld(b->claimed)) {
+          in_flight_.fetch_add(1);
+          bool free = false;
+          if (b->claimed.compare_exchange_strong(free, true))
+            t.leaf = b;
+          else
+            in_flight_.fetch_sub(1);
         }
         return t;
       }
-      b->N += 1;
+      b->N.fetch_add(1, std::memory_order_relaxed);
       int a = choose_action(b);
-      b->Na[a] += 1;
-      double eps0 = root_->U - root_->L;
+      b->Na[a].fetch_add(1, std::memory_order_relaxed);
+      double eps0 = ld(root_->U) - ld(root_->L);
       Node* best = nullptr;
       double beste = -std::numeric_limits<double>::infinity();
       for (Node* c : b->q[a].ch) {
-        double e = (c->U - c->L) - c->W * p_.xi * eps0 - p_.c_o * eps0 * (double)c->vl;
+        double e = (ld(c->U) - ld(c->L)) - c->W * p_.xi * eps0 - p_.c_o * eps0 * (double)ld(c->vl);
         if (e > beste) {
           beste = e;
           best = c;
@@ -236,7 +274,7 @@ class Search {
       }
       t.acts.push_back(a);
       if (best == nullptr || !(beste > 0)) return t;
-      best->vl += 1;
+      best->vl.fetch_add(1, std::memory_order_relaxed);
       t.path.push_back(best);
       b = best;
     }
@@ -245,11 +283,23 @@ class Search {
   void backup(Trial& t) {
     for (int i = (int)t.path.size() - 1; i >= 0; --i) {
       Node* b = t.path[i];
-      if (i < (int)t.acts.size() && b->expanded) {
+      if (i < (int)t.acts.size() && b->expanded.load(std::memory_order_acquire)) {
         refresh_action(b, t.acts[i]);
         refresh(b);
       }
-      if (i > 0) b->vl -= 1;
+      if (i > 0) b->vl.fetch_sub(1, std::memory_order_relaxed);
+    }
+  }
+
+  // Every expanded node's bounds recomputed from its children, children first
+  // (a node is created after its parent): after lock-free threads, whose
+  // interleaved backups may have left a node an older (looser) bound.
+  void settle() {
+    for (auto it = pool_.rbegin(); it != pool_.rend(); ++it) {
+      Node* b = it->get();
+      if (!b->expanded.load(std::memory_order_acquire)) continue;
+      for (int a = 0; a < b->nq; ++a) refresh_action(b, a);
+      refresh(b);
     }
   }
 
@@ -293,6 +343,7 @@ class Search {
   // Children of an expanded leaf from its copied results. The leaf is claimed
   // by the calling thread, and other threads stop at an unexpanded leaf, so
   // this runs without the tree lock; publish() then marks the leaf expanded.
+  // The nodes of one expansion come from the pool in one batch.
   void create_children(Node* b, const dsp_leaf_job& J, const JobOut& jo, const char* hsmall) {
     const int32_t* cnt = (const int32_t*)(hsmall + jo.o_cnt);
     const int32_t* off = (const int32_t*)(hsmall + jo.o_off);
@@ -302,9 +353,16 @@ class Search {
     const int64_t* ls = (const int64_t*)(hsmall + jo.o_l);
     b->d_states = J.leaf_states;
     b->d_perm = J.perm;
-    b->q.assign(na_, QBranch());
-    b->Na.assign(na_, 0);
+    b->q.reset(new QBranch[na_]);
+    b->nq = na_;
+    b->Na.reset(new std::atomic<long long>[na_]);
+    for (int a = 0; a < na_; ++a) wr(b->Na[a], 0LL);
     const int cap = jo.cap, n = b->n;
+    int total = 0;
+    for (int a = 0; a < na_; ++a) total += std::min(cnt[a], cap);
+    std::vector<Node*> made;
+    new_nodes(total, made);
+    int next = 0;
     for (int a = 0; a < na_; ++a) {
       QBranch& q = b->q[a];
       int nc = std::min(cnt[a], cap);
@@ -313,7 +371,7 @@ class Search {
       q.R = ((double)rsum / 4294967296.0) / K_;
       double su = 0, sl = 0;
       for (int c = 0; c < nc; ++c) {
-        Node* ch = new_node();
+        Node* ch = made[next++];
         int o0 = off[(size_t)a * (cap + 1) + c], o1 = off[(size_t)a * (cap + 1) + c + 1];
         ch->depth = b->depth + 1;
         ch->n = o1 - o0;
@@ -325,23 +383,26 @@ class Search {
         ch->term = (ch->key >> 62) & 1u;
         std::memcpy(ch->hist, b->hist, 32);
         observe(ch->hist, a, ch->key);
-        ch->U = ((double)us[(size_t)a * cap + c] / 4294967296.0) / K_;
-        ch->L = ((double)ls[(size_t)a * cap + c] / 4294967296.0) / K_;
+        const double cu = ((double)us[(size_t)a * cap + c] / 4294967296.0) / K_;
+        const double cl = ((double)ls[(size_t)a * cap + c] / 4294967296.0) / K_;
+        wr(ch->U, cu);
+        wr(ch->L, cl);
         q.ch.push_back(ch);
-        su += ch->U;
-        sl += ch->L;
+        su += cu;
+        sl += cl;
       }
-      q.U = q.R + gamma_ * su;
-      q.L = q.R + gamma_ * sl;
+      wr(q.U, q.R + gamma_ * su);
+      wr(q.L, q.R + gamma_ * sl);
     }
   }
 
-  // Makes a leaf whose children exist visible to the search (caller holds the
-  // tree lock in free-running mode).
+  // Makes a leaf whose children exist visible to the search (under the tree
+  // lock when the threads use it): bounds first, then the flag with release
+  // ordering, so that a thread that sees the flag sees the children.
   void publish(Node* b) {
-    b->expanded = true;
     refresh(b);
-    published_ += 1;
+    b->expanded.store(true, std::memory_order_release);
+    published_.fetch_add(1);
   }
 
   // Expands leaves as one batch on `st` and creates their children in order.
@@ -382,7 +443,7 @@ class Search {
     for (int k = 0; k < L; ++k) create_children(leaves[k], jobs[k], jo[k], host + base[k]);
     {
       std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
-      if (p_.deterministic == 0) lock.lock();
+      if (p_.deterministic == 0 && p_.tree_lock != 0) lock.lock();
       for (int k = 0; k < L; ++k) publish(leaves[k]);
     }
     expansions_ += L;
@@ -400,9 +461,11 @@ class Search {
   std::vector<std::unique_ptr<Node>> pool_;
   Node* root_ = nullptr;
   uint16_t* d_ident_ = nullptr;
-  std::mutex tree_mu_;
-  std::mutex pool_mu_;  // the node pool (children are made outside the tree lock)
-  long long published_ = 0;  // leaves made visible (guarded by the tree lock)
+  std::mutex tree_mu_;   // free running with tree_lock: selection and backup
+  std::mutex pool_mu_;   // the node pool (children are made outside the tree lock)
+  std::atomic<long long> published_{0};  // leaves made visible
+  std::atomic<int> in_flight_{0};        // leaves claimed and not yet backed up
+  std::atomic<long long> started_{0};    // expansions begun (free running)
   std::atomic<int> expansions_{0};
   dsp_queue* queue_ = nullptr;  // free running with use_queue: the shared device job queue
   int rounds_ = 0;
@@ -425,9 +488,10 @@ dsp_status Search::run_rounds() {
       if (s != DSP_OK) break;
     }
     for (auto& t : trials) backup(t);
-    for (Node* l : leaves) l->claimed = false;
+    for (Node* l : leaves) wr(l->claimed, false);
+    in_flight_.fetch_sub((int)leaves.size());
     rounds_ += 1;
-    if (root_->expanded && root_->U - root_->L <= p_.target_gap) break;
+    if (root_->expanded.load() && ld(root_->U) - ld(root_->L) <= p_.target_gap) break;
     if (leaves.empty()) break;
   }
   cudaStreamDestroy(st);
@@ -437,14 +501,16 @@ dsp_status Search::run_rounds() {
 dsp_status Search::run_threads() {
   auto t0 = std::chrono::steady_clock::now();
   std::atomic<bool> stop{false};
-  std::atomic<int> in_flight{0};
   std::vector<dsp_status> status(p_.threads, DSP_OK);
   const long long budget = (long long)p_.threads * p_.rounds;
-  long long started = 0;  // expansions begun (guarded by the tree lock)
+  const bool locked = p_.tree_lock != 0;
+  auto gap_reached = [&]() {
+    return root_->expanded.load(std::memory_order_acquire) && ld(root_->U) - ld(root_->L) <= p_.target_gap;
+  };
   auto worker = [&](int tid) {
     cudaSetDevice(m_->device);
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t stream;
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
       status[tid] = fail(DSP_E_CUDA, "dsp_plan: stream");
       stop = true;
       return;
@@ -453,36 +519,42 @@ dsp_status Search::run_threads() {
     while (!stop.load()) {
       Trial t;
       {
-        std::lock_guard<std::mutex> lock(tree_mu_);
+        std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
+        if (locked) lock.lock();
         if (stop.load()) break;
-        if (started >= budget) {  // every budgeted expansion is taken
+        if (started_.load() >= budget) {  // every budgeted expansion is taken
           stop = true;
           break;
         }
         t = select();
-        if (t.leaf) {
-          in_flight += 1;
-          started += 1;
+        if (t.leaf && started_.fetch_add(1) >= budget) {  // another thread took the last one
+          backup(t);
+          wr(t.leaf->claimed, false);
+          in_flight_.fetch_sub(1);
+          stop = true;
+          break;
         }
       }
       if (t.leaf) {
-        dsp_status s = expand_batch({t.leaf}, st, staging);
-        std::lock_guard<std::mutex> lock(tree_mu_);
-        in_flight -= 1;
+        dsp_status s = expand_batch({t.leaf}, stream, staging);
+        std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
+        if (locked) lock.lock();
         if (s != DSP_OK) {
           status[tid] = s;
           stop = true;
         }
         backup(t);
-        t.leaf->claimed = false;
-        if (root_->expanded && root_->U - root_->L <= p_.target_gap) stop = true;
+        wr(t.leaf->claimed, false);
+        in_flight_.fetch_sub(1);  // after the publish and the backup
+        if (gap_reached()) stop = true;
       } else {
-        std::lock_guard<std::mutex> lock(tree_mu_);
+        std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
+        if (locked) lock.lock();
         backup(t);
         // nothing left worth expanding: no expansion in flight and none
         // published since this trial looked (else the tree changed: retry)
-        if (in_flight.load() == 0 && t.epoch == published_) stop = true;
-        if (root_->expanded && root_->U - root_->L <= p_.target_gap) stop = true;
+        if (in_flight_.load() == 0 && t.epoch == published_.load()) stop = true;
+        if (gap_reached()) stop = true;
       }
       if (p_.time_limit_s > 0) {
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -490,11 +562,12 @@ dsp_status Search::run_threads() {
       }
       if (!t.leaf && !stop.load()) std::this_thread::yield();
     }
-    cudaStreamDestroy(st);
+    cudaStreamDestroy(stream);
   };
   std::vector<std::thread> th;
   for (int i = 0; i < p_.threads; ++i) th.emplace_back(worker, i);
   for (auto& x : th) x.join();
+  if (!locked) settle();
   for (auto s : status)
     if (s != DSP_OK) return s;
   return DSP_OK;
@@ -545,17 +618,17 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   s = dsp_read_counters(m_, &steps1, &status);
   if (s != DSP_OK) return s;
   if (status != 0) return fail(DSP_E_DEVICE, "dsp_plan: device status word %u", status);
-  out->root_u = root_->U;
-  out->root_l = root_->L;
+  out->root_u = ld(root_->U);
+  out->root_l = ld(root_->L);
   out->nodes = (int32_t)pool_.size();
   out->expansions = expansions_.load();
   out->rounds = rounds_;
   out->scenario_steps = steps1 - steps0;
   int best = -1;
   double bl = -std::numeric_limits<double>::infinity();
-  for (int a = 0; a < (int)root_->q.size(); ++a)
-    if (root_->q[a].L > bl) {
-      bl = root_->q[a].L;
+  for (int a = 0; a < root_->nq; ++a)
+    if (ld(root_->q[a].L) > bl) {
+      bl = ld(root_->q[a].L);
       best = a;
     }
   out->action = best;
@@ -563,15 +636,16 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   for (auto& up : pool_) {
     Node* v = up.get();
     uint64_t ub, lb;
-    std::memcpy(&ub, &v->U, 8);
-    std::memcpy(&lb, &v->L, 8);
+    const double vu = ld(v->U), vlo = ld(v->L);
+    std::memcpy(&ub, &vu, 8);
+    std::memcpy(&lb, &vlo, 8);
     sig = mix64(sig ^ (uint64_t)v->depth) ^ v->key;
     sig = mix64(sig ^ ub) ^ lb;
-    sig = mix64(sig ^ (uint64_t)v->n ^ ((uint64_t)v->N << 32));
+    sig = mix64(sig ^ (uint64_t)v->n ^ ((uint64_t)ld(v->N) << 32));
   }
   out->signature = sig;
   if (visits)
-    for (int a = 0; a < (int)root_->Na.size(); ++a) visits[a] = (int32_t)root_->Na[a];
+    for (int a = 0; a < root_->nq; ++a) visits[a] = (int32_t)ld(root_->Na[a]);
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return DSP_OK;
 }
@@ -584,17 +658,17 @@ dsp_status Search::export_nodes(int min_scen, int cap, dsp_plan_node* nodes, uin
   for (auto& up : pool_) {
     if (k >= cap) break;
     const Node* v = up.get();
-    if (!v->expanded || v->term || v->n < min_scen || v->d_states == nullptr) continue;
+    if (!v->expanded.load() || v->term || v->n < min_scen || v->d_states == nullptr) continue;
     dsp_plan_node& o = nodes[k];
     o.depth = v->depth;
     o.n = v->n;
-    o.visits = (int32_t)v->N;
-    o.U = v->U;
-    o.L = v->L;
+    o.visits = (int32_t)ld(v->N);
+    o.U = ld(v->U);
+    o.L = ld(v->L);
     std::memcpy(o.hist, v->hist, 32);
     int best = 0;
-    for (int a = 1; a < (int)v->q.size(); ++a)
-      if (v->q[a].L > v->q[best].L) best = a;
+    for (int a = 1; a < v->nq; ++a)
+      if (ld(v->q[a].L) > ld(v->q[best].L)) best = a;
     o.action = best;
     if (states) {
       cudaError_t e = cudaMemcpy2D(one.data(), 4, v->d_states, (size_t)v->n * 4, 4, words_, cudaMemcpyDeviceToHost);

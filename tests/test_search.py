@@ -78,10 +78,12 @@ def test_search_converges_to_exhaustive_optimum(env):
     assert abs(g["root_u"] - vstar) < 1e-5 and abs(g["root_l"] - vstar) < 1e-5
 
 
+@pytest.mark.parametrize("tree_lock", [0, 1])
 @pytest.mark.parametrize("threads", [1, 4, 16])
-def test_free_running_threads_valid(env, threads):
-    """Free-running threads with PO-UCT and virtual loss: bounds stay around
-    the exhaustive optimum and the budget holds."""
+def test_free_running_threads_valid(env, threads, tree_lock):
+    """Free-running threads with PO-UCT and virtual loss, on per-node atomics
+    or under one tree lock: bounds stay around the exhaustive optimum and the
+    budget holds."""
     _dsp, batch = env
     cfg = I.Config(kind=I.MULTIGRID, n=3, m=2, K=6, D=4, seed=4,
                    rock_cells=np.array([1 | (1 << 8), 2], np.int32))
@@ -89,7 +91,7 @@ def test_free_running_threads_valid(env, threads):
     vstar = oracle.Model(cfg, fp64=True).exhaustive(b, None, 0)
     m = batch.Model(cfg)
     p = _dsp.dsp_search_params(threads=threads, rounds=20, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95,
-                               target_gap=0.0, deterministic=0)
+                               target_gap=0.0, deterministic=0, tree_lock=tree_lock)
     g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
     assert g["root_l"] <= vstar + 1e-5 and vstar <= g["root_u"] + 1e-5
     assert 1 <= g["expansions"] <= threads * 20
@@ -142,3 +144,23 @@ def test_mars15_16_threads_queue(env):
     assert g["root_l"] <= g["root_u"] + 1e-9
     assert g["expansions"] >= 16
     m.close()
+
+
+@pytest.mark.parametrize("tree_lock", [0, 1])
+def test_free_running_one_thread_is_the_rounds_search(env, tree_lock):
+    """One free-running thread selects, expands and backs up in the order of
+    one-trial deterministic rounds, so on per-node atomics (with the final
+    bottom-up pass) or under the tree lock it builds the same tree as the
+    oracle's search: equal digest, bounds and visits."""
+    _dsp, batch = env
+    cfg = I.rs7_8()
+    b = root_states(cfg, np.random.default_rng(7))
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=1, rounds=30, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, tree_lock=tree_lock)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    m.close()
+    o = oracle.Model(cfg).plan(b, None, threads=1, rounds=30, c_a=1.0, c_o=0.5, xi=0.95, target_gap=0.0)
+    assert g["signature"] == o["signature"]
+    assert g["root_u"] == o["root_u"] and g["root_l"] == o["root_l"]
+    assert np.array_equal(g["root_visits"], o["root_na"])
