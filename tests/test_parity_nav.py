@@ -22,7 +22,11 @@ def dsp():
 
 
 CONFIGS = {"nav13": I.nav13, "nav13 noisy": lambda: I.nav13().with_(fail_p=0.2, sense_p=0.2),
-           "nav9": lambda: I.nav_config(9, K=200, D=60, seed=5), "nav16": lambda: I.nav_config(16, K=200, D=60, seed=6)}
+           "nav9": lambda: I.nav_config(9, K=200, D=60, seed=5), "nav16": lambda: I.nav_config(16, K=200, D=60, seed=6),
+           # the smallest map with every move failing and every reading flipped
+           # (thresholds of 2^32), and an odd map without noise
+           "nav5 p=1": lambda: I.nav_config(5, K=100, D=60, seed=7).with_(fail_p=1.0, sense_p=1.0),
+           "nav15 p=0": lambda: I.nav_config(15, K=200, D=60, seed=8).with_(fail_p=0.0, sense_p=0.0)}
 
 
 @pytest.mark.parametrize("name", list(CONFIGS))
