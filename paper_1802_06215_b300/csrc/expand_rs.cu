@@ -577,13 +577,18 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st) {
   Items<R> items{item_buf, total_items};
-  // Each warp expands whole actions, so the CTA takes as many warps as give
-  // every warp the same number of a job's actions (20 actions: 10 warps of 2;
-  // 400: 16 of 25).
+  // Each warp expands whole actions: as many warps as give every warp the
+  // same number of a job's actions (20 actions: 10 warps of 2; 400: 16 of
+  // 25). One robot with at least two jobs per CTA slot: at most five warps
+  // (20 actions: 5 of 4), so that six CTAs fit per SM and a CTA waiting at a
+  // job's barriers leaves others running (4096 jobs of 15x15: 0.280 against
+  // 0.295 ms). With fewer jobs the wider CTA finishes the largest job sooner
+  // (512 jobs: 55 against 72 us).
   int block_a = kBlockA;
   {
     const int na = std::max(1, num_actions);
-    const int per_warp = (na + kWarpsA - 1) / kWarpsA;
+    const bool narrow = R == 1 && n_jobs >= 12 * num_sms;
+    const int per_warp = narrow ? (na + 4) / 5 : (na + kWarpsA - 1) / kWarpsA;
     block_a = 32 * ((na + per_warp - 1) / per_warp);
   }
   int per_sm_a = 0;
