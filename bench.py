@@ -99,7 +99,9 @@ def parse():
     p.add_argument("--learned-rollouts", type=int, default=0,
                    help="time only the learned-policy rollout kernel on this many start states and exit")
     p.add_argument("--plan-scaling", default="", choices=["", "rs15_15", "mars15_15"],
-                   help="planning throughput against search threads (per-leaf launches vs the device queue)")
+                   help="planning throughput against search threads (per-leaf launches, batched launches, "
+                        "the device queue)")
+    p.add_argument("--plan-locks", action="store_true", help="--plan-scaling: also under one tree lock")
     p.add_argument("--pomcp", default="", choices=[""] + list(WORKLOADS),
                    help="POMCP-style planner with GPU rollouts against the oracle's (one line per batch size)")
     p.add_argument("--sweep", default="", help="'all' or comma-separated workloads: one line per variant")
@@ -628,12 +630,12 @@ def sweep(args):
 
 
 def plan_scaling(args):
-    """Planning throughput against search threads, per-leaf launches against
-    the device job queue, per-node atomics against one tree lock: three
-    planning steps of 0.3 s per (threads, path, tree) from the benchmark's
-    root belief, xi < 0 so that no trial ends without a leaf (the machinery's
-    rate, not the planner's). One JSON line per point: median, min and max
-    expansions/s."""
+    """Planning throughput against search threads: per-leaf launches, batched
+    launches and the device job queue on per-node atomics (with --plan-locks
+    also under one tree lock): three planning steps of 0.3 s per (threads,
+    path) from the benchmark's root belief, xi < 0 so that no trial ends
+    without a leaf (the machinery's rate, not the planner's). One JSON line per
+    point: median, min and max expansions/s."""
     from paper_1802_06215_b300 import _dsp, batch, build
     build.build()
     mk = WORKLOADS[args.plan_scaling][0]
@@ -641,25 +643,27 @@ def plan_scaling(args):
     m = batch.Model(cfg)
     b = root_states(cfg, np.random.default_rng(99))
 
-    def plan(threads, q, lock, secs):
+    def plan(threads, q, lock, bsz, secs):
         p = _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=secs, c_a=1.0, c_o=0.5, xi=-1.0,
-                                   target_gap=-1.0, deterministic=0, use_queue=q, tree_lock=lock)
+                                   target_gap=-1.0, deterministic=0, use_queue=q, tree_lock=lock, batch=bsz)
         return _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
 
-    plan(4, 0, 0, 0.2)
-    plan(4, 1, 0, 0.2)
+    paths = [(0, 0, 0, "per-leaf launches"), (0, 0, 64, "batched launches (up to 64 leaves)"),
+             (1, 0, 0, "device queue")]
+    if args.plan_locks:
+        paths += [(0, 1, 0, "per-leaf launches"), (1, 1, 0, "device queue")]
+    for q, lock, bsz, _ in paths:
+        plan(4, q, lock, bsz, 0.2)
     for threads in (1, 2, 4, 8, 16, 32):
-        for q in (0, 1):
-            for lock in (0, 1):
-                r = []
-                for _ in range(3):
-                    g = plan(threads, q, lock, 0.3)
-                    r.append(g["expansions"] / g["seconds"])
-                print(json.dumps({"plan_scaling": args.plan_scaling, "threads": threads,
-                                  "path": "device queue" if q else "per-leaf launches",
-                                  "tree": "one tree lock" if lock else "per-node atomics",
-                                  "expansions_per_s": statistics.median(r), "min": min(r), "max": max(r)}),
-                      flush=True)
+        for q, lock, bsz, name in paths:
+            r = []
+            for _ in range(3):
+                g = plan(threads, q, lock, bsz, 0.3)
+                r.append(g["expansions"] / g["seconds"])
+            print(json.dumps({"plan_scaling": args.plan_scaling, "threads": threads, "path": name,
+                              "tree": "one tree lock" if lock else "per-node atomics",
+                              "expansions_per_s": statistics.median(r), "min": min(r), "max": max(r)}),
+                  flush=True)
     m.close()
 
 

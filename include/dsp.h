@@ -206,6 +206,9 @@ typedef struct {
                             claimed by compare-and-swap, counts as atomic increments, bounds as atomic stores;
                             the tree's bounds are recomputed bottom-up once the threads join); 1 = under
                             one tree lock */
+  int32_t batch;         /* free running without the queue: > 1 = threads hand their claimed leaves to one
+                            dispatching thread, which expands up to `batch` of them per dsp_expand_leaves
+                            launch and backs them up; <= 1 = every thread launches its own leaf */
 } dsp_search_params;
 
 typedef struct {

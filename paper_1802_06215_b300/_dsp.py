@@ -181,7 +181,7 @@ def dsp_alu_probe(sink, iters, stream=0):
 class dsp_search_params(C.Structure):
     _fields_ = [("threads", C.c_int32), ("rounds", C.c_int32), ("time_limit_s", C.c_double), ("c_a", C.c_double),
                 ("c_o", C.c_double), ("xi", C.c_double), ("target_gap", C.c_double), ("deterministic", C.c_int32),
-                ("use_queue", C.c_int32), ("tree_lock", C.c_int32)]
+                ("use_queue", C.c_int32), ("tree_lock", C.c_int32), ("batch", C.c_int32)]
 
 
 class dsp_search_result(C.Structure):

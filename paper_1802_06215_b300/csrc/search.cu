@@ -406,12 +406,41 @@ class Search {
   }
 
   // Expands leaves as one batch on `st` and creates their children in order.
+  // The GPU part of a batch (job tables, launch or queue, result copy into
+  // `pinned`) and the host part (children, publishing), separable so that a
+  // dispatcher can let the next batch launch while it makes this one's nodes.
+  struct BatchOut {
+    std::vector<dsp_leaf_job> jobs;
+    std::vector<JobOut> jo;
+    std::vector<size_t> base;
+    const char* host = nullptr;
+  };
   dsp_status expand_batch(const std::vector<Node*>& leaves, cudaStream_t st, Pinned& pinned) {
+    BatchOut bo;
+    dsp_status s = expand_gpu(leaves, st, pinned, bo);
+    if (s != DSP_OK) return s;
+    finish_batch(leaves, bo);
+    return DSP_OK;
+  }
+  void finish_batch(const std::vector<Node*>& leaves, const BatchOut& bo) {
+    const int L = (int)leaves.size();
+    for (int k = 0; k < L; ++k) create_children(leaves[k], bo.jobs[k], bo.jo[k], bo.host + bo.base[k]);
+    {
+      std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
+      if (p_.deterministic == 0 && p_.tree_lock != 0) lock.lock();
+      for (int k = 0; k < L; ++k) publish(leaves[k]);
+    }
+    expansions_ += L;
+  }
+  dsp_status expand_gpu(const std::vector<Node*>& leaves, cudaStream_t st, Pinned& pinned, BatchOut& bo) {
     int L = (int)leaves.size();
-    std::vector<dsp_leaf_job> jobs(L);
-    std::vector<JobOut> jo(L);
+    std::vector<dsp_leaf_job>& jobs = bo.jobs;
+    std::vector<JobOut>& jo = bo.jo;
+    std::vector<size_t>& base = bo.base;
+    jobs.resize(L);
+    jo.resize(L);
+    base.resize(L);
     size_t total = 0;
-    std::vector<size_t> base(L);
     for (int k = 0; k < L; ++k) {
       jo[k].layout(na_, dsp_max_children(m_, leaves[k]->n));
       base[k] = total;
@@ -440,13 +469,7 @@ class Search {
     e = cudaMemcpyAsync(host, dsmall, total, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: results copy");
-    for (int k = 0; k < L; ++k) create_children(leaves[k], jobs[k], jo[k], host + base[k]);
-    {
-      std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
-      if (p_.deterministic == 0 && p_.tree_lock != 0) lock.lock();
-      for (int k = 0; k < L; ++k) publish(leaves[k]);
-    }
-    expansions_ += L;
+    bo.host = host;
     return DSP_OK;
   }
 
@@ -507,6 +530,55 @@ dsp_status Search::run_threads() {
   auto gap_reached = [&]() {
     return root_->expanded.load(std::memory_order_acquire) && ld(root_->U) - ld(root_->L) <= p_.target_gap;
   };
+  // Batched launches (batch > 1, no queue): a thread that claims a leaf hands
+  // its trial to the pending list and tries to become the dispatcher; the
+  // dispatcher expands everything pending (up to `batch` leaves per launch) in
+  // one dsp_expand_leaves call on its own stream, creates and publishes the
+  // children, and backs the trials up, while the other threads go on
+  // selecting. After releasing the role it looks again, so no trial is left
+  // behind by a push that met a busy dispatcher.
+  const bool batched = p_.batch > 1 && queue_ == nullptr;
+  std::mutex pend_mu, disp_mu;
+  std::vector<Trial> pending;
+  auto dispatch = [&](cudaStream_t stream, Pinned& staging, int tid) {
+    while (true) {
+      if (!disp_mu.try_lock()) return;  // the dispatcher will look again after it lets go
+      std::vector<Trial> take;
+      {
+        std::lock_guard<std::mutex> lock(pend_mu);
+        const size_t k = std::min(pending.size(), (size_t)p_.batch);
+        for (size_t i = 0; i < k; ++i) take.push_back(std::move(pending[i]));
+        pending.erase(pending.begin(), pending.begin() + (long)k);
+      }
+      if (take.empty()) {
+        disp_mu.unlock();
+        std::lock_guard<std::mutex> lock(pend_mu);
+        if (pending.empty()) return;
+        continue;
+      }
+      std::vector<Node*> leaves;
+      for (auto& x : take) leaves.push_back(x.leaf);
+      BatchOut bo;
+      dsp_status s = expand_gpu(leaves, stream, staging, bo);
+      disp_mu.unlock();  // the next batch may launch while this one's nodes are made
+      if (s == DSP_OK) {
+        finish_batch(leaves, bo);
+      } else {
+        status[tid] = s;
+        stop = true;
+      }
+      {
+        std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
+        if (locked) lock.lock();
+        for (auto& x : take) {
+          backup(x);
+          wr(x.leaf->claimed, false);
+        }
+      }
+      in_flight_.fetch_sub((int)take.size());  // after the publishes and the backups
+      if (gap_reached()) stop = true;
+    }
+  };
   auto worker = [&](int tid) {
     cudaSetDevice(m_->device);
     cudaStream_t stream;
@@ -517,6 +589,18 @@ dsp_status Search::run_threads() {
     }
     Pinned staging;
     while (!stop.load()) {
+      if (batched) {
+        size_t np;
+        {
+          std::lock_guard<std::mutex> lock(pend_mu);
+          np = pending.size();
+        }
+        if (np >= (size_t)p_.batch) {  // a full batch waits: expand it rather than select further ahead
+          dispatch(stream, staging, tid);
+          std::this_thread::yield();
+          continue;
+        }
+      }
       Trial t;
       {
         std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
@@ -535,7 +619,13 @@ dsp_status Search::run_threads() {
           break;
         }
       }
-      if (t.leaf) {
+      if (t.leaf && batched) {
+        {
+          std::lock_guard<std::mutex> lock(pend_mu);
+          pending.push_back(std::move(t));
+        }
+        dispatch(stream, staging, tid);
+      } else if (t.leaf) {
         dsp_status s = expand_batch({t.leaf}, stream, staging);
         std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
         if (locked) lock.lock();
@@ -548,6 +638,7 @@ dsp_status Search::run_threads() {
         in_flight_.fetch_sub(1);  // after the publish and the backup
         if (gap_reached()) stop = true;
       } else {
+        if (batched) dispatch(stream, staging, tid);
         std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
         if (locked) lock.lock();
         backup(t);
@@ -562,6 +653,7 @@ dsp_status Search::run_threads() {
       }
       if (!t.leaf && !stop.load()) std::this_thread::yield();
     }
+    if (batched) dispatch(stream, staging, tid);  // what is still pending
     cudaStreamDestroy(stream);
   };
   std::vector<std::thread> th;

@@ -146,21 +146,56 @@ def test_mars15_16_threads_queue(env):
     m.close()
 
 
-@pytest.mark.parametrize("tree_lock", [0, 1])
-def test_free_running_one_thread_is_the_rounds_search(env, tree_lock):
+@pytest.mark.parametrize("tree_lock,launch_batch", [(0, 0), (1, 0), (0, 8), (1, 8)])
+def test_free_running_one_thread_is_the_rounds_search(env, tree_lock, launch_batch):
     """One free-running thread selects, expands and backs up in the order of
-    one-trial deterministic rounds, so on per-node atomics (with the final
-    bottom-up pass) or under the tree lock it builds the same tree as the
-    oracle's search: equal digest, bounds and visits."""
+    one-trial deterministic rounds (with batched launches it dispatches its
+    own leaf at once), so on per-node atomics (with the final bottom-up pass)
+    or under the tree lock it builds the same tree as the oracle's search:
+    equal digest, bounds and visits."""
     _dsp, batch = env
     cfg = I.rs7_8()
     b = root_states(cfg, np.random.default_rng(7))
     m = batch.Model(cfg)
     p = _dsp.dsp_search_params(threads=1, rounds=30, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95,
-                               target_gap=0.0, deterministic=0, tree_lock=tree_lock)
+                               target_gap=0.0, deterministic=0, tree_lock=tree_lock, batch=launch_batch)
     g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
     m.close()
     o = oracle.Model(cfg).plan(b, None, threads=1, rounds=30, c_a=1.0, c_o=0.5, xi=0.95, target_gap=0.0)
     assert g["signature"] == o["signature"]
     assert g["root_u"] == o["root_u"] and g["root_l"] == o["root_l"]
     assert np.array_equal(g["root_visits"], o["root_na"])
+
+
+@pytest.mark.parametrize("tree_lock", [0, 1])
+@pytest.mark.parametrize("threads", [4, 16])
+def test_free_running_batched_launches_valid(env, threads, tree_lock):
+    """Threads handing their leaves to one dispatcher that expands up to 8 per
+    launch: bounds around the exhaustive optimum, the budget holds."""
+    _dsp, batch = env
+    cfg = I.Config(kind=I.MULTIGRID, n=3, m=2, K=6, D=4, seed=4,
+                   rock_cells=np.array([1 | (1 << 8), 2], np.int32))
+    b = root_states(cfg, np.random.default_rng(4))
+    vstar = oracle.Model(cfg, fp64=True).exhaustive(b, None, 0)
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=threads, rounds=20, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, tree_lock=tree_lock, batch=8)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    assert g["root_l"] <= vstar + 1e-5 and vstar <= g["root_u"] + 1e-5
+    assert 1 <= g["expansions"] <= threads * 20
+    m.close()
+
+
+def test_free_running_batched_rs15(env):
+    """15x15 with 16 threads and up to 64 leaves per launch for 0.5 s: valid
+    bounds, many expansions."""
+    _dsp, batch = env
+    cfg = I.rs15_15()
+    b = root_states(cfg, np.random.default_rng(2))
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=16, rounds=100000, time_limit_s=0.5, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, batch=64)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    assert g["root_l"] <= g["root_u"] + 1e-9
+    assert g["expansions"] >= 16 and g["seconds"] < 5.0
+    m.close()
