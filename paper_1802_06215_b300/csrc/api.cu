@@ -355,9 +355,9 @@ dsp_status dsp_reset_counters(dsp_model* m, void* stream) {
 
 namespace dsp {
 
-// Validates the jobs and plans the launch: car units are (job, action); Rock
-// Sample jobs get the first index of their rollout items (n_scen * n_actions
-// each, in job order).
+// Validates the jobs and plans the launch: car and navigation units are (job,
+// action), each with the first index of its rollout items; Rock Sample jobs
+// get the first index of theirs (n_scen * n_actions each, in job order).
 dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan) {
   const DevModel* h = m->host;
   plan.units.clear();
@@ -395,7 +395,7 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
     std::stable_sort(plan.units.begin(), plan.units.end(), [&](const int4& x, const int4& y) {
       return jobs[x.x].n_scen > jobs[y.x].n_scen;
     });
-    // first rollout item of each unit (used when a learned policy rolls out)
+    // first rollout item of each unit (navigation's phase B, the car's learned rollouts)
     for (int4& u : plan.units) {
       u.z = (int)plan.total_items;
       plan.total_items += jobs[u.x].n_scen;
@@ -451,9 +451,9 @@ static cudaError_t release_staging(dsp_model* m, dsp_staging_slot* sl, cudaStrea
   return e;
 }
 
-// Copies the job table (and the car's unit table or Rock Sample's item
-// offsets) to stream-ordered device memory, takes the Rock Sample item list
-// from the same allocation and launches the expansion kernels.
+// Copies the job table (and the unit table, or Rock Sample's item offsets) to
+// stream-ordered device memory, takes the rollout-item list from the same
+// allocation and launches the expansion kernels.
 dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
                          cudaStream_t st) {
   const DevModel* h = m->host;
