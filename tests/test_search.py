@@ -199,3 +199,23 @@ def test_free_running_batched_rs15(env):
     assert g["root_l"] <= g["root_u"] + 1e-9
     assert g["expansions"] >= 16 and g["seconds"] < 5.0
     m.close()
+
+
+@pytest.mark.parametrize("launch_batch", [0, 32])
+def test_lock_free_tree_bounds_consistent(env, launch_batch):
+    """16 lock-free threads for 0.5 s on 15x15, then the exported tree: every
+    expanded node keeps U >= L, the root's bounds are the first node's, and
+    the visit counts of the root's actions add up to the root's visits."""
+    _dsp, batch = env
+    cfg = I.rs15_15()
+    b = root_states(cfg, np.random.default_rng(5))
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=16, rounds=100000, time_limit_s=0.5, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, batch=launch_batch)
+    g, nodes, _ = _dsp.dsp_plan_nodes(m.h, b, None, p, m.num_actions, 1, 100000, m.words)
+    m.close()
+    assert len(nodes) >= 2
+    assert np.all(nodes["U"] >= nodes["L"] - 1e-9)
+    root = nodes[0]
+    assert root["depth"] == 0 and root["U"] == g["root_u"] and root["L"] == g["root_l"]
+    assert int(g["root_visits"].sum()) == int(root["visits"])
