@@ -51,7 +51,7 @@ struct RSGroupSmem {
   int acid[kWarpsA][kCodes];           // child index of the code
   unsigned long long sr[kWarpsA][kCodes];  // exact reward sum (fixed point)
   uint32_t pm_job;
-  int job;
+  int job, part;
   dsp_leaf_job J;
   uint8_t code1[kWarpsA][kMaxScen];    // each warp's observation codes of its current action
 };
@@ -63,16 +63,18 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // Gather + update of the job in S.J into S.leaf (and J.leaf_states), and the
-// job's positive-counter mask. Ends with a barrier.
+// job's positive-counter mask. Ends with a barrier. Only the job's first unit
+// (`first`) counts the update steps and writes the leaf's states.
 template <int R>
-__device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& M, unsigned long long& steps) {
+__device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& M, bool first,
+                                              unsigned long long& steps) {
   const int tid = threadIdx.x;
   const dsp_leaf_job& J = S.J;
   const int n = J.n_scen, depth = J.depth;
   for (int p = tid; p < n; p += (int)blockDim.x) {
     RSS s = M.load(J.parent, J.parent_cap, J.idx[p]);
     if (J.last_action >= 0) {
-      if (!M.terminal(s)) steps += 1;
+      if (!M.terminal(s) && first) steps += 1;
       uint64_t k;
       M.step(s, J.last_action, depth - 1, k);
     }
@@ -83,7 +85,7 @@ __device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& 
     S.leaf[4][p] = s.scen;
 #pragma unroll
     for (int r = 0; r < R; ++r) S.sense[r][p] = M.sense_word(s.scen, depth, r);
-    if (J.leaf_states != nullptr) M.store(s, J.leaf_states, n, p);
+    if (first && J.leaf_states != nullptr) M.store(s, J.leaf_states, n, p);
   }
   if (tid == 0) {
     uint32_t h[8];
@@ -109,7 +111,7 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
                               DevWork* work, unsigned long long& steps) {
   constexpr int kC = 6;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  gather_update<1>(S, M, steps);
+  gather_update<1>(S, M, true, steps);
   const dsp_leaf_job& J = S.J;
   const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
   const uint32_t lt = lanemask_lt();
@@ -256,10 +258,10 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
 // shared tables. Lanes with the same code meet through __match_any_sync and
 // their leader updates the code's row; the warp's own __syncwarp orders the
 // updates. The result is identical to the general grouping.
-__device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long long ibase, Items<2> items,
-                              DevWork* work, unsigned long long& steps) {
+__device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long long ibase, int a_begin, int a_end,
+                              bool first_unit, Items<2> items, DevWork* work, unsigned long long& steps) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  gather_update<2>(S, M, steps);
+  gather_update<2>(S, M, first_unit, steps);
   const dsp_leaf_job& J = S.J;
   const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
   const uint32_t lt = lanemask_lt();
@@ -271,7 +273,7 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
   int* cid = S.acid[warp];
   unsigned long long* rsum = S.sr[warp];
   const int nwarps = (int)(blockDim.x >> 5);
-  for (int a = warp; a < A; a += nwarps) {
+  for (int a = a_begin + warp; a < a_end; a += nwarps) {
     const int aa = J.first_action + a;
     const int a0 = aa / M.per, a1 = aa - a0 * M.per;
     if (lane < kCodes) {
@@ -386,12 +388,15 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
 }
 
 template <int R>
-__device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase,
-                                          Items<R> items, DevWork* work, unsigned long long& steps) {
+// One unit of phase A: actions [a_begin, a_end) of job j (one robot: always
+// the whole job); `first` marks the job's first unit.
+__device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase, int a_begin,
+                                          int a_end, bool first, Items<R> items, DevWork* work,
+                                          unsigned long long& steps) {
   if constexpr (R == 1)
     rs1_group_job(S, M, j, ibase, items, work, steps);
   else
-    rs2_group_job(S, M, j, ibase, items, work, steps);
+    rs2_group_job(S, M, j, ibase, a_begin, a_end, first, items, work, steps);
 }
 
 template <int R>
@@ -400,22 +405,35 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
                                                              const long long* __restrict__ item_base,
                                                              const int* __restrict__ order, int n_jobs,
                                                              unsigned int* head, uint32_t plan_step,
-                                                             Items<R> items) {
+                                                             Items<R> items, int splits) {
   __shared__ RSGroupSmem S;
   load_rs_consts(S.c, gm);
   const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
   unsigned long long steps = 0;
   __syncthreads();
+  // unit k: part k % splits of job order[k / splits], its actions in runs of
+  // a multiple of the CTA's warps
+  const int nwarps = (int)(blockDim.x >> 5);
   while (true) {
     if (threadIdx.x == 0) {
       const int k = (int)atomicAdd(head, 1u);
-      S.job = k < n_jobs ? (order != nullptr ? order[k] : k) : n_jobs;
+      const int q = k / splits;
+      S.job = q < n_jobs ? (order != nullptr ? order[q] : q) : n_jobs;
+      S.part = k - q * splits;
       if (S.job < n_jobs) S.J = jobs[S.job];
     }
     __syncthreads();
     const int j = S.job;
     if (j >= n_jobs) break;
-    group_job<R>(S, M, j, item_base[j], items, work, steps);
+    const int A = S.J.n_actions;
+    const int run = nwarps * ((A + splits * nwarps - 1) / (splits * nwarps));
+    const int a_begin = S.part * run, a_end = min(A, a_begin + run);
+    // both ways end at a barrier (group_job's last), so thread 0 may take the
+    // next unit (the condition is the same for the whole CTA)
+    if (a_begin < a_end)
+      group_job<R>(S, M, j, item_base[j], a_begin, a_end, S.part == 0, items, work, steps);
+    else
+      __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
@@ -594,8 +612,12 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
   int per_sm_a = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, rs_group_kernel<R>, block_a, 0);
   int grid_a = std::max(1, std::min(n_jobs, std::max(1, per_sm_a) * num_sms));
+  // two robots: a job's hundreds of actions split over several CTAs (runs of
+  // about 80), so that the largest jobs do not leave a tail
+  const int splits = R == 2 ? std::max(1, num_actions / 80) : 1;
+  grid_a = std::max(1, std::min(n_jobs * splits, std::max(1, per_sm_a) * num_sms));
   rs_group_kernel<R><<<grid_a, block_a, 0, st>>>(gm, work, jobs, item_base, order, n_jobs, counters, plan_step,
-                                                  items);
+                                                  items, splits);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (policy != nullptr && R == 1)
@@ -774,7 +796,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       M.plan_step = s_plan_step;
       if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
         Items<R> items{scratch + (size_t)slot * slot_words, (long long)n * S.J.n_actions};
-        group_job<R>(S, M, 0, 0, items, work, steps);
+        group_job<R>(S, M, 0, 0, 0, S.J.n_actions, true, items, work, steps);
         nchunks = (items.total + 31) >> 5;
       }
       __threadfence();  // every thread's phase-A results, before the job is published
