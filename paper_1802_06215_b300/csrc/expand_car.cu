@@ -19,15 +19,20 @@ namespace {
 
 constexpr int kCarObsWords = kMaxPeds + 1;  // speed | terminal, then one word per pedestrian
 
+// The children's int64 sums reuse the grouping's hash table (keys and first
+// positions, 12 KB), which is dead once group_by_key has returned: 51 KB per
+// CTA, so that four CTAs share an SM.
 struct CarUnitSmem {
   CarShared c;
   uint64_t key[kMaxScen];
   float rew[kMaxScen], uval[kMaxScen], lval[kMaxScen];
   GroupSmem grp;
-  unsigned long long sr[kMaxScen], su[kMaxScen], sl[kMaxScen];
   int unit;
   dsp_leaf_job job;
 };
+static_assert(sizeof(GroupSmem::tkey) >= 2 * kMaxScen * sizeof(unsigned long long) &&
+                  sizeof(GroupSmem::tfirst) >= kMaxScen * sizeof(unsigned long long),
+              "the sums alias the hash table");
 
 template <int TPS, int KP = kDefaultPairs<TPS>>
 __global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
@@ -118,14 +123,18 @@ __global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expan
         S.lval[p] = lv;
       }
     }
-    for (int c = tid; c < n; c += nthr) {
-      S.sr[c] = 0;
-      S.su[c] = 0;
-      S.sl[c] = 0;
-    }
     __syncthreads();
     group_by_key(S.grp, S.key, n);
     const int nchild = S.grp.nchild;
+    unsigned long long* sr = reinterpret_cast<unsigned long long*>(S.grp.tkey);
+    unsigned long long* su = sr + kMaxScen;
+    unsigned long long* sl = reinterpret_cast<unsigned long long*>(S.grp.tfirst);
+    for (int c = tid; c < nchild; c += nthr) {
+      sr[c] = 0;
+      su[c] = 0;
+      sl[c] = 0;
+    }
+    __syncthreads();
     // full-observation check of every member against its child's first member
     for (int q = tid; q < n; q += nthr) {
       int c = S.grp.gcid[q];
@@ -137,9 +146,9 @@ __global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expan
         for (int w = 1; w <= P; ++w) same = same && (a0[w] == a1[w]);
         if (!same) report(work, kStatusKeyClash);
       }
-      atomicAdd(&S.sr[c], (unsigned long long)to_fixed(S.rew[q]));
-      atomicAdd(&S.su[c], (unsigned long long)to_fixed(S.uval[q]));
-      atomicAdd(&S.sl[c], (unsigned long long)to_fixed(S.lval[q]));
+      atomicAdd(&sr[c], (unsigned long long)to_fixed(S.rew[q]));
+      atomicAdd(&su[c], (unsigned long long)to_fixed(S.uval[q]));
+      atomicAdd(&sl[c], (unsigned long long)to_fixed(S.lval[q]));
     }
     __syncthreads();
     const int cap = job.child_cap;
@@ -153,9 +162,9 @@ __global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expan
     for (int c = tid; c < ncw; c += nthr) {
       size_t o = (size_t)ao * cap + c;
       job.child_key[o] = S.key[S.grp.cfirst[c]];
-      job.rew_sum[o] = (long long)S.sr[c];
-      job.u_sum[o] = (long long)S.su[c];
-      job.l_sum[o] = (long long)S.sl[c];
+      job.rew_sum[o] = (long long)sr[c];
+      job.u_sum[o] = (long long)su[c];
+      job.l_sum[o] = (long long)sl[c];
     }
     for (int q = tid; q < n; q += nthr) {
       int c = S.grp.gcid[q];
