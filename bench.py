@@ -61,9 +61,13 @@ WORKLOADS = {
                                                          "4096 leaf jobs, |Phi_b|~U{1..100}", (4, 0.5, 0)),
     "rs15_15_k250": (lambda: inputs.rs15_15_k(250), 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=250, D=90; "
                                                          "4096 leaf jobs, |Phi_b|~U{1..250}", (4, 0.5, 0)),
+    "rs15_15_k1000": (lambda: inputs.rs15_15_k(1000), 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=1000, D=90; "
+                                                           "4096 leaf jobs, |Phi_b|~U{1..1000}", (4, 0.5, 0)),
+    "rs15_15_k5000": (lambda: inputs.rs15_15_k(5000), 4096, "Rock Sample 15x15, 15 rocks, |A|=20, K=5000, D=90; "
+                                                           "4096 leaf jobs, |Phi_b|~U{1..5000}", (4, 0.5, 0)),
 }
-SWEEP = ["car6", "car12", "car20", "car50", "rs15_15_k100", "rs15_15_k250", "rs15_15", "mars11_11", "mars15_15",
-         "mars20_20", "nav13"]
+SWEEP = ["car6", "car12", "car20", "car50", "rs15_15_k100", "rs15_15_k250", "rs15_15", "rs15_15_k1000",
+         "rs15_15_k5000", "mars11_11", "mars15_15", "mars20_20", "nav13"]
 SMS, LANES_PER_SM, MAX_SM_MHZ = 148, 128, 2032.0
 try:
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:

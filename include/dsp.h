@@ -76,7 +76,7 @@ typedef struct {
   int32_t m;                  /* Rock Sample rocks (1..32) */
   int32_t P;                  /* car: pedestrians (1..64) */
   float gamma;                /* discount */
-  int32_t K;                  /* scenarios per planning step (1..512) */
+  int32_t K;                  /* scenarios per planning step (1..512; one-robot Rock Sample 1..8192) */
   int32_t D;                  /* maximum depth (1..250) */
   uint64_t seed;              /* Philox key */
   uint32_t plan_step;         /* fourth Philox counter word */
@@ -131,7 +131,9 @@ dsp_status dsp_rollout(const dsp_model* model, const uint32_t* block, int32_t ca
 typedef struct {
   const uint32_t* parent; /* state block holding the parent's scenario list */
   int32_t parent_cap;     /* its capacity (field stride) */
-  int32_t n_scen;         /* |Phi_b|, 1..512 */
+  int32_t n_scen;         /* |Phi_b|, 1..512; one-robot Rock Sample: up to 8192, above 512 only
+                             with leaf_states (phase A keeps those leaves there, not in shared
+                             memory); the device queue takes at most 512 */
   const uint16_t* idx;    /* n_scen positions of the leaf's scenarios in parent */
   int32_t last_action;    /* action into this leaf, applied at depth-1 ("update");
                              -1: parent already holds the leaf's states (a root) */

@@ -75,7 +75,8 @@ dsp_status dsp_create_model(const dsp_model_desc* d, dsp_model** out) {
   *out = nullptr;
   if (!d) return fail(DSP_E_INVALID, "dsp_create_model: desc is NULL");
   if (d->kind < 0 || d->kind > 3) return fail(DSP_E_INVALID, "unknown model kind %d", d->kind);
-  if (d->K < 1 || d->K > kMaxScen) return fail(DSP_E_INVALID, "K=%d outside 1..%d", d->K, kMaxScen);
+  const int max_k = d->kind == DSP_MODEL_GRID ? kMaxScenLarge : kMaxScen;
+  if (d->K < 1 || d->K > max_k) return fail(DSP_E_INVALID, "K=%d outside 1..%d", d->K, max_k);
   if (d->D < 1 || d->D > kGammaLen - 6) return fail(DSP_E_INVALID, "D=%d outside 1..%d", d->D, kGammaLen - 6);
   if (!(d->gamma > 0.0f && d->gamma <= 1.0f)) return fail(DSP_E_INVALID, "gamma must be in (0, 1]");
   DevModel* h = new DevModel();
@@ -365,8 +366,11 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
   plan.total_items = 0;
   for (int j = 0; j < n_jobs; ++j) {
     const dsp_leaf_job& J = jobs[j];
-    if (J.n_scen < 1 || J.n_scen > kMaxScen)
-      return fail(DSP_E_UNSUPPORTED, "job %d: n_scen=%d outside 1..%d", j, J.n_scen, kMaxScen);
+    const int max_n = h->kind == DSP_MODEL_GRID ? kMaxScenLarge : kMaxScen;
+    if (J.n_scen < 1 || J.n_scen > max_n)
+      return fail(DSP_E_UNSUPPORTED, "job %d: n_scen=%d outside 1..%d", j, J.n_scen, max_n);
+    if (J.n_scen > kMaxScen && J.leaf_states == nullptr)
+      return fail(DSP_E_UNSUPPORTED, "job %d: more than %d scenarios need leaf_states", j, kMaxScen);
     if (J.n_actions < 1 || J.first_action < 0 || J.first_action + J.n_actions > h->num_actions)
       return fail(DSP_E_INVALID, "job %d: actions [%d,%d) outside 0..%d", j, J.first_action,
                   J.first_action + J.n_actions, h->num_actions);

@@ -14,6 +14,10 @@ constexpr int kGammaLen = 256;
 constexpr int kGaussLen = 4096;
 constexpr int kMaxPeds = 64;
 constexpr int kMaxScen = 512;
+// One-robot Rock Sample jobs may hold up to kMaxScenLarge scenarios: those above
+// kMaxScen take phase A's global-memory path (their leaf states in the job's
+// leaf-state block instead of shared memory).
+constexpr int kMaxScenLarge = 8192;
 constexpr uint64_t kTermBit = 1ull << 62;
 
 // Device status word bits.

@@ -250,6 +250,156 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
   __syncthreads();
 }
 
+// Phase A for one robot when a job holds more scenarios than shared memory
+// takes (kMaxScen < n <= kMaxScenLarge): the gather writes the leaf's states
+// to the job's leaf-state block in global memory (it stays in L2) instead of
+// shared memory, and the second pass recomputes each scenario's sensor word,
+// step and observation code instead of keeping them. The placement is the
+// same as rs1_group_job's, so the result is identical.
+__device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, long long ibase, Items<1> items,
+                                    DevWork* work, unsigned long long& steps) {
+  constexpr int kC = 6;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const dsp_leaf_job& J = S.J;
+  const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
+  uint32_t* const L = J.leaf_states;  // field-major, capacity n (required by the host for n > kMaxScen)
+  for (int p = tid; p < n; p += (int)blockDim.x) {
+    RSS s = M.load(J.parent, J.parent_cap, J.idx[p]);
+    if (J.last_action >= 0) {
+      if (!M.terminal(s)) steps += 1;
+      uint64_t k;
+      M.step(s, J.last_action, depth - 1, k);
+    }
+    M.store(s, L, n, p);
+  }
+  if (tid == 0) {
+    uint32_t h[8];
+    const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = hw[k];
+    S.pm_job = positive_mask(h, M.m);
+  }
+  __syncthreads();
+  const uint32_t lt = lanemask_lt();
+  const uint32_t pm_job = S.pm_job;
+  const int nwarps = (int)(blockDim.x >> 5);
+  for (int a = warp; a < A; a += nwarps) {
+    const int aa = J.first_action + a;
+    int cnt[kC], first[kC], rsum[kC];  // |reward sum| <= 100 * 8192 fits 32 bits
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      cnt[c] = 0;
+      first[c] = 0x7FFFFFFF;
+      rsum[c] = 0;
+    }
+    for (int w = 0; w * 32 < n; ++w) {
+      const int p = w * 32 + lane;
+      int code = kC, rint = 0;
+      if (p < n) {
+        RSS s = M.load(L, n, p);
+        if (!M.terminal(s)) steps += 1;
+        uint64_t key;
+        const uint32_t sw[2] = {M.sense_word(s.scen, depth, 0), 0u};
+        rint = (int)M.step(s, aa, depth, key, sw);
+        code = (int)(key & 3u) + 3 * (int)(key >> 62);
+      }
+      const uint32_t present = __reduce_or_sync(0xFFFFFFFFu, code < kC ? 1u << code : 0u);
+#pragma unroll
+      for (int c = 0; c < kC; ++c) {
+        if (present & (1u << c)) {
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
+          if (cnt[c] == 0) first[c] = w * 32 + __ffs(b) - 1;
+          cnt[c] += __popc(b);
+          rsum[c] += __reduce_add_sync(0xFFFFFFFFu, code == c ? rint : 0);
+        }
+      }
+    }
+    int cid[kC], off[kC], nch = 0;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      cid[c] = -1;
+      off[c] = 0;
+      if (cnt[c] > 0) {
+        nch += 1;
+        int k = 0, o = 0;
+#pragma unroll
+        for (int c2 = 0; c2 < kC; ++c2)
+          if (cnt[c2] > 0 && first[c2] < first[c]) {
+            k += 1;
+            o += cnt[c2];
+          }
+        cid[c] = k;
+        off[c] = o;
+      }
+    }
+    if (lane == 0) {
+      J.child_count[a] = nch;
+      if (nch > cap) report(work, kStatusOverflow);
+      if (nch <= cap) J.child_off[(size_t)a * (cap + 1) + nch] = n;
+#pragma unroll
+      for (int c = 0; c < kC; ++c)
+        if (cnt[c] > 0 && cid[c] < cap) {
+          const size_t o = (size_t)a * cap + cid[c];
+          J.child_off[(size_t)a * (cap + 1) + cid[c]] = off[c];
+          J.child_key[o] = (uint64_t)(c % 3) | ((uint64_t)(c / 3) << 62);
+          J.rew_sum[o] = (long long)rsum[c] * 4294967296LL;
+          J.u_sum[o] = 0;
+          J.l_sum[o] = 0;
+        }
+    }
+    uint32_t pm_z[3] = {pm_job, pm_job, pm_job};
+    if (aa >= 5) {
+      const int i = aa - 5;
+      const int c0 = (int)J.hist[i];
+      const int cg = min(c0 + 1, 127), cb = max(c0 - 1, -127);
+      pm_z[1] = cg > 0 ? (pm_job | (1u << i)) : (pm_job & ~(1u << i));
+      pm_z[2] = cb > 0 ? (pm_job | (1u << i)) : (pm_job & ~(1u << i));
+    }
+    int run[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) run[c] = 0;
+    for (int w = 0; w * 32 < n; ++w) {
+      const int p = w * 32 + lane;
+      int code = kC;
+      RSS s;
+      if (p < n) {
+        s = M.load(L, n, p);
+        uint64_t key;
+        const uint32_t sw[2] = {M.sense_word(s.scen, depth, 0), 0u};
+        M.step(s, aa, depth, key, sw);
+        code = (int)(key & 3u) + 3 * (int)(key >> 62);
+      }
+      int q = 0, mycid = 0;
+#pragma unroll
+      for (int c = 0; c < kC; ++c) {
+        if (cnt[c] > 0) {
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
+          if (code == c) {
+            q = off[c] + run[c] + __popc(b & lt);
+            mycid = cid[c];
+          }
+          run[c] += __popc(b);
+        }
+      }
+      if (p < n) {
+        J.perm[(size_t)a * n + q] = (uint16_t)p;
+        const int z = code % 3;
+        const uint32_t pm = z == 1 ? pm_z[1] : (z == 2 ? pm_z[2] : pm_z[0]);
+        const size_t it = (size_t)(ibase + (long long)a * n + q);
+        items.f(0)[it] = s.pos[0];
+        items.f(1)[it] = s.good;
+        items.f(2)[it] = s.sampled;
+        items.f(3)[it] = s.scen;
+        items.f(4)[it] = pm;
+        items.f(5)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1));
+        items.f(6)[it] = (uint32_t)j;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
 // Phase A for two robots, organised like rs1_group_job: each warp expands
 // whole actions in two passes over 32-scenario chunks. The codes (z0 * 3 + z1
 // and whether the step ended the world, up to 18) are too many for
@@ -387,15 +537,19 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
   __syncthreads();
 }
 
-template <int R>
 // One unit of phase A: actions [a_begin, a_end) of job j (one robot: always
-// the whole job); `first` marks the job's first unit.
+// the whole job); `first` marks the job's first unit. kLarge: one-robot jobs
+// above kMaxScen scenarios may occur (not in the queue, which refuses them).
+template <int R, bool kLarge = true>
 __device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase, int a_begin,
                                           int a_end, bool first, Items<R> items, DevWork* work,
                                           unsigned long long& steps) {
-  if constexpr (R == 1)
-    rs1_group_job(S, M, j, ibase, items, work, steps);
-  else
+  if constexpr (R == 1) {
+    if (kLarge && S.J.n_scen > kMaxScen)
+      rs1_group_job_large(S, M, j, ibase, items, work, steps);
+    else
+      rs1_group_job(S, M, j, ibase, items, work, steps);
+  } else
     rs2_group_job(S, M, j, ibase, a_begin, a_end, first, items, work, steps);
 }
 
@@ -796,7 +950,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       M.plan_step = s_plan_step;
       if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
         Items<R> items{scratch + (size_t)slot * slot_words, (long long)n * S.J.n_actions};
-        group_job<R>(S, M, 0, 0, 0, S.J.n_actions, true, items, work, steps);
+        group_job<R, false>(S, M, 0, 0, 0, S.J.n_actions, true, items, work, steps);
         nchunks = (items.total + 31) >> 5;
       }
       __threadfence();  // every thread's phase-A results, before the job is published

@@ -188,6 +188,8 @@ dsp_status dsp_queue_submit(dsp_queue* q, const dsp_leaf_job* job, uint64_t time
   }
   if (q->m->policy_on) return fail(DSP_E_UNSUPPORTED, "dsp_queue_submit: the queue rolls out the heuristic policy");
   ExpandPlan plan;
+  if (job->n_scen > kMaxScen)
+    return fail(DSP_E_UNSUPPORTED, "dsp_queue_submit: n_scen=%d above %d", job->n_scen, kMaxScen);
   dsp_status vs = plan_units(q->m, job, 1, plan);  // validation only
   if (vs != DSP_OK) return vs;
   // Claim ticket t only once its slot is free (the consumer of ticket t - cap

@@ -102,7 +102,7 @@ def mars20_20():
 
 
 def rs15_15_k(K):
-    """rs15_15 with K scenarios (at most 512 in this build)."""
+    """rs15_15 with K scenarios (up to 8192 for one robot)."""
     return grid_config(15, 15, K=K, D=90, seed=0)
 
 

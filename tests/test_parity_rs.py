@@ -213,3 +213,39 @@ def test_expand_parity_block_sizes(dsp, block):
         o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
         _cmp_expand(res[k], o, len(j.idx), f"block {block} job {k}")
     m.close()
+
+
+def test_expand_parity_large_jobs(dsp):
+    """One robot with K = 5000: jobs above 512 scenarios take phase A's
+    global-memory path (leaf states in the job's leaf-state block); children,
+    grouped positions, leaf states and the fixed-point sums bit for bit, next
+    to small jobs of the same launch."""
+    cfg = I.rs15_15_k(5000)
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    import dataclasses
+    jobs = I.job_stream(cfg, 6, 21)
+    jobs += [dataclasses.replace(jobs[0], idx=jobs[0].idx[:300].copy()),
+             dataclasses.replace(jobs[2], idx=jobs[2].idx[:513].copy())]
+    assert max(len(j.idx) for j in jobs) > 512 and min(len(j.idx) for j in jobs) <= 512
+    jb = dsp.JobBatch(m, jobs)
+    m.reset_counters()
+    jb.run()
+    steps, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    total = 0
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        g = res[k]
+        assert np.array_equal(g["leaf"], o["leaf"]), k
+        assert np.array_equal(g["child_count"], o["child_count"]), k
+        for a in range(m.num_actions):
+            nc = int(o["child_count"][a])
+            for f in ("key", "rew", "u", "l"):
+                assert np.array_equal(g[f][a][:nc], o[f][a][:nc]), (k, a, f)
+            assert np.array_equal(g["child_off"][a][: nc + 1], o["child_off"][a][: nc + 1]), (k, a)
+        assert np.array_equal(g["perm"], o["perm"]), k
+        total += o["steps"]
+    assert steps == total
+    m.close()
