@@ -223,7 +223,8 @@ typedef struct {
 } dsp_search_result;
 
 /* One planning step (Sec. III-A forward search, leaf initialisation on the
- * GPU, Eq. backup): builds a DESPOT tree over the n root scenarios
+ * GPU, Eq. backup): builds a DESPOT tree over the n root scenarios (n <= K;
+ * at most 512, or 8192 for one-robot Rock Sample without the device queue)
  * (root_states: HOST state block of capacity n; hist: HOST 32 belief
  * counters or NULL) with T threads, scenario-based PO-UCT for actions,
  * weighted excess uncertainty minus virtual loss for observations, one trial =

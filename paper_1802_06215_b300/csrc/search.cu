@@ -773,6 +773,14 @@ dsp_status Search::export_nodes(int min_scen, int cap, dsp_plan_node* nodes, uin
   return DSP_OK;
 }
 
+// Root scenarios a plan may take: one-robot Rock Sample expands leaves of up
+// to kMaxScenLarge scenarios (every leaf here has its leaf-state block),
+// except through the device queue, which takes at most kMaxScen.
+int max_root_scenarios(const dsp_model* m, const dsp_search_params* p) {
+  const bool queue = p->use_queue && !p->deterministic;
+  return m->host->kind == DSP_MODEL_GRID && !queue ? kMaxScenLarge : kMaxScen;
+}
+
 }  // namespace
 }  // namespace dsp
 
@@ -780,7 +788,8 @@ extern "C" dsp_status dsp_plan(dsp_model* m, const uint32_t* root_states, int32_
                                const dsp_search_params* p, dsp_search_result* out, int32_t* root_visits) {
   using namespace dsp;
   if (!m || !root_states || !p || !out) return fail(DSP_E_INVALID, "dsp_plan: NULL argument");
-  if (n < 1 || n > kMaxScen || n > m->host->K) return fail(DSP_E_INVALID, "dsp_plan: %d root scenarios", n);
+  if (n < 1 || n > max_root_scenarios(m, p) || n > m->host->K)
+    return fail(DSP_E_INVALID, "dsp_plan: %d root scenarios", n);
   if (p->threads < 1 || p->threads > 256) return fail(DSP_E_INVALID, "dsp_plan: threads %d", p->threads);
   if (p->rounds < 1) return fail(DSP_E_INVALID, "dsp_plan: rounds %d", p->rounds);
   std::memset(out, 0, sizeof(*out));
@@ -796,7 +805,8 @@ extern "C" dsp_status dsp_plan_nodes(dsp_model* m, const uint32_t* root_states, 
   if (!nodes || !count || cap < 0) return fail(DSP_E_INVALID, "dsp_plan_nodes: NULL node buffer");
   *count = 0;
   if (!m || !root_states || !p || !out) return fail(DSP_E_INVALID, "dsp_plan_nodes: NULL argument");
-  if (n < 1 || n > kMaxScen || n > m->host->K) return fail(DSP_E_INVALID, "dsp_plan_nodes: %d root scenarios", n);
+  if (n < 1 || n > max_root_scenarios(m, p) || n > m->host->K)
+    return fail(DSP_E_INVALID, "dsp_plan_nodes: %d root scenarios", n);
   if (p->threads < 1 || p->threads > 256) return fail(DSP_E_INVALID, "dsp_plan_nodes: threads %d", p->threads);
   if (p->rounds < 1) return fail(DSP_E_INVALID, "dsp_plan_nodes: rounds %d", p->rounds);
   std::memset(out, 0, sizeof(*out));

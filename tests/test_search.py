@@ -219,3 +219,14 @@ def test_lock_free_tree_bounds_consistent(env, launch_batch):
     root = nodes[0]
     assert root["depth"] == 0 and root["U"] == g["root_u"] and root["L"] == g["root_l"]
     assert int(g["root_visits"].sum()) == int(root["visits"])
+
+
+def test_deterministic_rounds_large_root(env):
+    """One robot with 2000 root scenarios (leaves above 512 take phase A's
+    global-memory path): the deterministic search equals the oracle's."""
+    cfg = I.rs15_15_k(2000)
+    b = root_states(cfg, np.random.default_rng(11))
+    g, o = plan_both(env, cfg, b, threads=2, rounds=4, c_a=1.0, c_o=0.5)
+    assert g["signature"] == o["signature"]
+    assert g["root_u"] == o["root_u"] and g["root_l"] == o["root_l"] and g["action"] == o["action"]
+    assert g["scenario_steps"] == o["steps"]
