@@ -8,9 +8,8 @@ may import this package; the product library never calls it and shares no
 code with it.
 
 Parity status: every function here is pinned by tests under `tests/` marked
-"not gpu" (closed forms, invariants, exhaustive enumeration), except Philox,
-whose published known-answer vectors are not available offline: it is pinned
-by its round structure and by statistical tests only.
+"not gpu" (closed forms, invariants, exhaustive enumeration, hand-worked
+goldens); Philox4x32-10 by the generator's published known-answer vectors.
 """
 import ctypes as C
 import os

@@ -11,7 +11,7 @@
 // + - * / sqrt, no contraction), Real = double is the FP64 oracle that checks
 // the FP32 one.
 //
-// Readings where the paper is silent (listed in the design doc): the path is the
+// Readings where the paper is silent: the path is the
 // line y = 20 from x = -10 for 60 m through the region [0,40]^2; speeds are
 // 0..3 m/s in 1 m/s steps; the four goals are the region's corners; a
 // pedestrian walks ped_speed*dt toward its goal (or lands on it when closer)

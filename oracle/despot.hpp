@@ -14,7 +14,7 @@
 //  * exhaustive expansion to depth D of the same scenario tree, the optimal
 //    value the bounds must bracket.
 //
-// Readings (listed in the design doc): per-scenario values are in the model's Real
+// Readings where the paper is silent: per-scenario values are in the model's Real
 // type in time order; sums over scenarios are exact int64 fixed point with
 // scale 2^-32; children are ordered by the first position at which their
 // observation occurs, members in their original order; node values are kept

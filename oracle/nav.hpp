@@ -10,7 +10,7 @@
 // probability 0.03. Staying costs 0.2, a move 0.1, a crash 1; reaching the goal
 // gives 20 and ends the world.
 //
-// Readings where the paper is silent (all listed in the design doc):
+// Readings where the paper is silent:
 //  * layout: wall row y = n/2 occupied except the gates at x = n/4 and
 //    x = n-1-n/4, exactly one of them open; goal (n/2, n-1); start row y = 0;
 //    the state holds the full occupancy map (known and unknown cells alike);

@@ -5,7 +5,7 @@
 // streams: UCT over histories, each simulation carrying one scenario down the
 // tree and a default-policy rollout at the first new node.
 //
-// Batched reading (listed in the design doc; it is what lets rollouts go to a GPU
+// Batched reading (where the paper is silent; it is what lets rollouts go to a GPU
 // in batches): a round runs `batch` simulations level by level. Simulation i
 // of the plan takes root scenario i mod n. At each level the live simulations,
 // in index order, choose an action at their node by UCB1 on the action values

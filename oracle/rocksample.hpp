@@ -7,7 +7,7 @@
 // -10 for a bad one, +10 for leaving by the east border; the world ends when
 // every robot has left.
 //
-// Readings where the paper is silent (all listed in the design doc):
+// Readings where the paper is silent:
 //  * actions per robot: 0 N (y+1), 1 E (x+1), 2 S (y-1), 3 W (x-1), 4 Sample,
 //    5+i Sense rock i; joint action a = a0 * (5+m) + a1;
 //  * a move off the N/S/W border, or Sample where no rock lies, is illegal:
