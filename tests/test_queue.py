@@ -1,11 +1,13 @@
 """Device job queue: many host threads submit leaves of uneven |Phi_b| to one
-persistent kernel; results must equal dsp_expand_leaves bit for bit."""
+persistent kernel; every job's results must equal the CPU oracle's leaf
+expansion (Eq. expand, newnodes, ub, lb) bit for bit, and dsp_expand_leaves's."""
 import threading
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1802_06215_b300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +49,23 @@ def _rs32_32():
     return I.grid_config(32, 32, K=100, D=120, seed=3)
 
 
+def _cmp_oracle(cfg, m, jobs, results, plan_steps=None):
+    """Each job's queue results against the oracle's expansion of the same leaf."""
+    oms = {}
+    for k, (j, g) in enumerate(zip(jobs, results)):
+        ps = cfg.plan_step if plan_steps is None else plan_steps[k]
+        om = oms.setdefault(ps, oracle.Model(cfg, plan_step=ps))
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        assert np.array_equal(g["leaf"], o["leaf"]), (k, "leaf")
+        assert np.array_equal(g["child_count"], o["child_count"]), (k, "child_count")
+        assert np.array_equal(g["perm"], o["perm"]), (k, "perm")
+        for a in range(len(o["child_count"])):
+            nc = int(o["child_count"][a])
+            assert np.array_equal(g["child_off"][a][: nc + 1], o["child_off"][a][: nc + 1]), (k, a, "off")
+            for f in ("key", "rew", "u", "l"):
+                assert np.array_equal(g[f][a][:nc], o[f][a][:nc]), (k, a, f)
+
+
 @pytest.mark.parametrize("mk,njobs,threads", [(I.mars15_15, 48, 16), (I.rs15_15, 96, 16), (I.rs7_8, 40, 4),
                                               (_rs32_32, 24, 4)])
 def test_queue_matches_batch(env, mk, njobs, threads):
@@ -65,9 +84,33 @@ def test_queue_matches_batch(env, mk, njobs, threads):
     assert submitted == njobs and launches >= 1
     _, status = m.counters()
     assert status == 0
-    for k, (a, b) in enumerate(zip(ref.all_results(), out.all_results())):
+    got = out.all_results()
+    for k, (a, b) in enumerate(zip(ref.all_results(), got)):
         for f in FIELDS:
             assert np.array_equal(a[f], b[f]), (k, f)
+    _cmp_oracle(cfg, m, jobs, got)
+    m.close()
+
+
+def test_queue_two_robots_sixteen_producers_oracle(env):
+    """Two robots on 15x15 with 15 rocks (400 joint actions), K = 500, D = 90:
+    16 host threads submit 64 leaves with |Phi_b| ~ U{1..500} and depth ~
+    U{0..10} into one persistent kernel; every job equals the oracle."""
+    torch, _dsp, batch = env
+    cfg = I.mars15_15()
+    m = batch.Model(cfg)
+    jobs = I.job_stream(cfg, 64, 41)
+    sizes = [len(j.idx) for j in jobs]
+    assert min(sizes) < 100 and max(sizes) > 400
+    out = batch.JobBatch(m, jobs)
+    q = _dsp.dsp_queue_create(m.h, 32)
+    _run_threads(_dsp, q, out, 16)
+    launches, submitted = _dsp.dsp_queue_stats(q)
+    _dsp.dsp_queue_destroy(q)
+    assert submitted == len(jobs)
+    _, status = m.counters()
+    assert status == 0
+    _cmp_oracle(cfg, m, jobs, out.all_results())
     m.close()
 
 
@@ -90,9 +133,11 @@ def test_queue_relaunch_after_idle(env):
     launches, submitted = _dsp.dsp_queue_stats(q)
     _dsp.dsp_queue_destroy(q)
     assert submitted == 12 and launches >= 2
-    for k, (a, b) in enumerate(zip(ref.all_results(), out.all_results())):
+    got = out.all_results()
+    for k, (a, b) in enumerate(zip(ref.all_results(), got)):
         for f in FIELDS:
             assert np.array_equal(a[f], b[f]), (k, f)
+    _cmp_oracle(cfg, m, jobs, got)
     m.close()
 
 
@@ -147,6 +192,7 @@ def test_queue_jobs_keep_their_plan_step(env):
     for k in range(len(jobs)):
         for f in FIELDS:
             assert np.array_equal(refs[steps[k]][k][f], got[k][f]), (k, f)
+    _cmp_oracle(cfg, m, jobs, got, plan_steps=steps)
     _, status = m.counters()
     assert status == 0
     m.close()
