@@ -1117,6 +1117,13 @@ cudaError_t launch_rs_rollout(const DevModel* gm, int robots, DevWork* work, con
 // two kernels run on a fixed scratch array that the library keeps in device
 // memory for the life of the process. Its size caps one call at
 // kNoAllocJobs jobs and kNoAllocItems (action, scenario) items.
+//
+// The job table, the jobs' item offsets and their phase-A order reach the
+// device in one copy from a static host array, page-locked once per process
+// (cudaHostRegister pins the array; it allocates nothing), so a call does not
+// wait for the work queued before it on its stream. The array is reused once
+// the previous call's copy has run; a call made before then waits for that copy.
+#include <cstring>
 #include <mutex>
 
 #include "model.hpp"
@@ -1128,21 +1135,37 @@ constexpr int kNoAllocJobs = 8192;
 constexpr long long kNoAllocItems = 1LL << 20;
 constexpr size_t kNoAllocJobBytes = ((sizeof(dsp_leaf_job) * kNoAllocJobs + 255) / 256) * 256;
 constexpr size_t kNoAllocBaseBytes = sizeof(long long) * kNoAllocJobs;
+constexpr size_t kNoAllocOrderBytes = sizeof(int) * kNoAllocJobs;
+constexpr size_t kNoAllocTableBytes = kNoAllocJobBytes + kNoAllocBaseBytes + kNoAllocOrderBytes;
 constexpr size_t kNoAllocCounterBytes = 256;
 constexpr size_t kNoAllocItemBytes = sizeof(uint32_t) * 8 * (size_t)kNoAllocItems;  // 8 = most item fields
-constexpr size_t kNoAllocBytes = kNoAllocJobBytes + kNoAllocBaseBytes + kNoAllocCounterBytes + kNoAllocItemBytes;
+constexpr size_t kNoAllocBytes = kNoAllocTableBytes + kNoAllocCounterBytes + kNoAllocItemBytes;
+constexpr size_t kNoAllocHostBytes = (kNoAllocTableBytes + 4095) / 4096 * 4096;
 
 // One copy per GPU that loads the library, held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+// Host side of the copies: laid out like the front of the device array.
+alignas(4096) static unsigned char g_noalloc_host[kNoAllocHostBytes];
+
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[256] = {};
+cudaEvent_t g_noalloc_copied[256] = {};  // per device: the last table copy from g_noalloc_host
+cudaEvent_t g_noalloc_last = nullptr;    // the event of the most recent copy on any device
+bool g_noalloc_host_tried = false;
 
 // Device address of the scratch array on `device`, looked up once per device
-// with that device current (the array's name in host code is only a stand-in).
-dsp_status noalloc_scratch(int device, unsigned char** out) {
+// with that device current (the array's name in host code is only a stand-in),
+// and that device's copy event. Called with g_noalloc_mu held.
+dsp_status noalloc_setup(int device, unsigned char** out) {
   if (device < 0 || device >= 256) return fail(DSP_E_UNSUPPORTED, "device %d out of range", device);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_host_tried) {
+    // pinned for every context; if pinning is refused the copies stay correct
+    // but come from pageable memory, which may make the host wait
+    g_noalloc_host_tried = true;
+    if (cudaHostRegister(g_noalloc_host, kNoAllocHostBytes, cudaHostRegisterPortable) != cudaSuccess)
+      cudaGetLastError();
+  }
   if (g_noalloc_addr[device] == nullptr) {
     int cur = -1;
     cudaError_t e = cudaGetDevice(&cur);
@@ -1152,11 +1175,14 @@ dsp_status noalloc_scratch(int device, unsigned char** out) {
       if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc: cudaSetDevice");
     }
     void* p = nullptr;
+    cudaEvent_t ev = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     cudaError_t e2 = cur != device ? cudaSetDevice(cur) : cudaSuccess;
-    if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc: cudaGetSymbolAddress");
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc: set-up on the device");
     if (e2 != cudaSuccess) return cuda_fail(e2, "dsp_expand_leaves_noalloc: restoring the device");
     g_noalloc_addr[device] = p;
+    g_noalloc_copied[device] = ev;
   }
   *out = (unsigned char*)g_noalloc_addr[device];
   return DSP_OK;
@@ -1172,6 +1198,9 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
   if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(DSP_E_INVALID, "dsp_expand_leaves_noalloc: bad job array");
   if (m->host->kind != DSP_MODEL_GRID && m->host->kind != DSP_MODEL_MULTIGRID)
     return fail(DSP_E_UNSUPPORTED, "dsp_expand_leaves_noalloc: Rock Sample models only");
+  if (m->timing)
+    return fail(DSP_E_UNSUPPORTED,
+                "dsp_expand_leaves_noalloc: kernel timing is on (its events are created per call); turn it off");
   if (n_jobs == 0) return DSP_OK;
   if (n_jobs > kNoAllocJobs)
     return fail(DSP_E_UNSUPPORTED, "dsp_expand_leaves_noalloc: %d jobs, the fixed scratch holds at most %d", n_jobs,
@@ -1183,25 +1212,35 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
     return fail(DSP_E_UNSUPPORTED,
                 "dsp_expand_leaves_noalloc: %lld (action, scenario) items, the fixed scratch holds at most %lld",
                 plan.total_items, kNoAllocItems);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   unsigned char* base = nullptr;
-  vs = noalloc_scratch(m->device, &base);
+  vs = noalloc_setup(m->device, &base);
   if (vs != DSP_OK) return vs;
   cudaStream_t st = (cudaStream_t)stream;
+  // table layout of this call: jobs, then (256-byte aligned) item offsets and order
+  const size_t jb = ((sizeof(dsp_leaf_job) * (size_t)n_jobs + 255) / 256) * 256;
+  const size_t span = jb + (sizeof(long long) + sizeof(int)) * (size_t)n_jobs;
   dsp_leaf_job* djobs = (dsp_leaf_job*)base;
-  long long* dbase = (long long*)(base + kNoAllocJobBytes);
-  unsigned int* counters = (unsigned int*)(base + kNoAllocJobBytes + kNoAllocBaseBytes);
-  uint32_t* items = (uint32_t*)(base + kNoAllocJobBytes + kNoAllocBaseBytes + kNoAllocCounterBytes);
-  cudaError_t e = cudaMemcpyAsync(djobs, jobs, sizeof(dsp_leaf_job) * (size_t)n_jobs, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dbase, plan.item_base.data(), sizeof(long long) * plan.item_base.size(),
-                        cudaMemcpyHostToDevice, st);
+  long long* dbase = (long long*)(base + jb);
+  int* dorder = (int*)(dbase + n_jobs);
+  unsigned int* counters = (unsigned int*)(base + kNoAllocTableBytes);
+  uint32_t* items = (uint32_t*)(base + kNoAllocTableBytes + kNoAllocCounterBytes);
+  // the host array is free once the previous call's copy has run
+  cudaError_t e = g_noalloc_last ? cudaEventSynchronize(g_noalloc_last) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc: waiting for the previous copy");
+  std::memcpy(g_noalloc_host, jobs, sizeof(dsp_leaf_job) * (size_t)n_jobs);
+  std::memcpy(g_noalloc_host + jb, plan.item_base.data(), sizeof(long long) * (size_t)n_jobs);
+  std::memcpy(g_noalloc_host + jb + sizeof(long long) * (size_t)n_jobs, plan.order.data(),
+              sizeof(int) * (size_t)n_jobs);
+  e = cudaMemcpyAsync(base, g_noalloc_host, span, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(g_noalloc_copied[m->device], st);
+  if (e == cudaSuccess) g_noalloc_last = g_noalloc_copied[m->device];
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kNoAllocCounterBytes, st);
   if (e == cudaSuccess) {
     int block_b = m->tune_block > 0 ? m->tune_block : 256;
     e = launch_rs_expand(m->dmodel, m->host->robots, m->host->num_actions, rs_key_words(m->host), m->dwork, djobs,
-                         dbase, nullptr, n_jobs,
-                         plan.total_items, items,
-                         counters, m->plan_step, m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st);
+                         dbase, dorder, n_jobs, plan.total_items, items, counters, m->plan_step, m->num_sms,
+                         block_b, m->policy_on ? m->policy : nullptr, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc launch");
   return DSP_OK;
