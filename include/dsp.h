@@ -325,16 +325,26 @@ dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
  *    contents; the counters the kernels need at zero are cleared on the
  *    stream at the start of each call. Calls that overlap on the GPU (other
  *    streams, other threads) race on the array: order them on one stream.
- * Arguments, outputs and asynchrony are those of dsp_expand_leaves; `jobs` is
- * a host array, copied before return. */
+ *  - Host copies: `jobs` (a host array) is copied into one static host array
+ *    of the library, page-locked once per process (it is pinned, not
+ *    allocated), and from there to the device. So the call returns without
+ *    waiting for earlier work on `stream`, except when the previous call's
+ *    copy has not run yet: then it waits for that copy. If the system refuses
+ *    to page-lock the array, the copy comes from pageable memory and the host
+ *    may wait for the stream's earlier work.
+ *  - Kernel timing (dsp_kernel_timing) creates events per call, so while it
+ *    is on this entry point returns DSP_E_UNSUPPORTED.
+ * Arguments, outputs, validation and the jobs' largest-first order are those
+ * of dsp_expand_leaves. */
 dsp_status dsp_expand_leaves_noalloc(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
 /* Learned default policy pi0 (the paper's pi0 is a hand-written default
  * policy, Sec. III-D, Eq. lb; this one is learned): an MLP 64 -> 256 -> 256 -> 32
- * with ReLU hidden layers whose first |A| logits score the actions, trained by
- * imitation (softmax cross-entropy) on (state features, planner action)
- * pairs. FP32 master weights with Adam; BF16 copies feed the tensor-core
- * GEMMs (FP32 accumulation). Packed FP32 parameter layout (input-major):
+ * with ReLU hidden layers whose first |A| logits score the actions and logit
+ * |A| defers to the heuristic, trained with softmax cross-entropy on (state
+ * features, action label) pairs (the shipped weights: approximate policy
+ * iteration labels; planner imitation labels also work). FP32 master weights
+ * with Adam; BF16 copies feed the tensor-core GEMMs (FP32 accumulation). Packed FP32 parameter layout (input-major):
  * W1[64][256] b1[256] W2[256][256] b2[256] W3[256][32] b3[32] (90656 floats).
  * Features of one-robot Rock Sample: x/n, y/n, then per rock (rock x - x)/n,
  * (rock y - y)/n, clamp(counter, -3, 3)/3, sampled; zero-padded to 64. */
@@ -371,11 +381,18 @@ dsp_status dsp_mlp_train_step(dsp_mlp* mlp, const float* X, const int32_t* y, in
  * or the car (DSP_E_UNSUPPORTED for two robots); the device job queue keeps
  * the heuristic policy. */
 dsp_status dsp_set_policy(dsp_model* model, const dsp_mlp* mlp);
-/* dsp_rollout with the learned policy, also recording the action of every
- * step: actions (device, count x D int32, may be NULL) gets at
- * [i * D + (t - start_depth)] the action taken at depth t. */
+/* dsp_rollout with the learned policy, also recording every step's action
+ * and the network's output that chose it:
+ *  - actions (device, count x D int32, may be NULL) gets at
+ *    [i * D + (t - start_depth)] the action taken at depth t;
+ *  - logits (device, count x D x 32 FP32, 16-byte aligned, may be NULL) gets
+ *    at [(i * D + (t - start_depth)) * 32 + c] logit c of that step as the
+ *    tensor-core tile computed it (FP32 accumulator + bias), all 32 columns,
+ *    before the allowed-action mask.
+ * Entries of steps after a rollout ended are left as they were. */
 dsp_status dsp_rollout_logged(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
-                              const int8_t* hist, int32_t start_depth, float* value, int32_t* actions, void* stream);
+                              const int8_t* hist, int32_t start_depth, float* value, int32_t* actions,
+                              float* logits, void* stream);
 
 /* Policy features (the learned policy's input, the same function the learned
  * rollout evaluates): out (device, count x 64 FP32, 16-byte aligned); block:

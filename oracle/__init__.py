@@ -295,10 +295,12 @@ def features_car(model, block):
     return out
 
 
-def rollout_learned(model, block, hist, start_depth, weights, logged=None, tol=1e-2):
+def rollout_learned(model, block, hist, start_depth, weights, logged=None, tol=1e-2, want_logits=False):
     """Learned-policy rollout values (one-robot Rock Sample or the car); with `logged` actions
     (count x D) it replays them and returns, per scenario, the steps whose
-    logged action loses to the network's argmax by more than `tol`."""
+    logged action loses to the network's argmax by more than `tol`. With
+    want_logits it also returns the logits of every step (count x D x 32,
+    NaN after the rollout ends)."""
     block = np.ascontiguousarray(block, np.uint32)
     w, cap = block.shape
     h = None if hist is None else np.ascontiguousarray(hist, np.int8).reshape(cap, 32)
@@ -307,9 +309,12 @@ def rollout_learned(model, block, hist, start_depth, weights, logged=None, tol=1
     bad = np.zeros(cap, np.int32)
     lg = None if logged is None else np.ascontiguousarray(logged, np.int32)
     steps = C.c_uint64(0)
+    lo = np.full((cap, model.cfg.D, MLP_OUT), np.nan) if want_logits else None
     rc = lib().orc_rollout_learned(C.byref(model.c), _p(block, _U32), C.c_int32(cap), C.c_int32(cap),
                                    None if h is None else _p(h, _I8), C.c_int32(start_depth), *ptrs,
                                    None if lg is None else _p(lg, _I32), C.c_double(tol), _p(vals, _F64),
-                                   _p(bad, _I32), C.byref(steps))
+                                   _p(bad, _I32), C.byref(steps), None if lo is None else _p(lo, _F64))
     assert rc == 0
+    if want_logits:
+        return vals, bad, steps.value, lo
     return vals, bad, steps.value

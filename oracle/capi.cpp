@@ -422,7 +422,8 @@ int32_t orc_features_rs(const orc_model* d, const uint32_t* block, int32_t cap, 
 static int32_t rollout_learned_car(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count,
                                    int32_t start_depth, const double* W1, const double* b1, const double* W2,
                                    const double* b2, const double* W3, const double* b3, const int32_t* logged,
-                                   double tol, double* values, int32_t* disagree, uint64_t* steps) {
+                                   double tol, double* values, int32_t* disagree, uint64_t* steps,
+                                   double* logits_out) {
   Car<float> m = make_car<float>(d);
   Net w{W1, b1, W2, b2, W3, b3};
   const int na = m.num_actions();
@@ -438,6 +439,8 @@ static int32_t rollout_learned_car(const orc_model* d, const uint32_t* block, in
       double x64[kMlpIn], lg[kMlpOut];
       for (int q = 0; q < kMlpIn; ++q) x64[q] = (double)fx[q];
       forward_bf16(w, x64, lg);
+      if (logits_out)
+        for (int q = 0; q < kMlpOut; ++q) logits_out[((size_t)i * m.D + k) * kMlpOut + q] = lg[q];
       int best = 0;
       for (int a = 1; a <= na; ++a)
         if (lg[a] > lg[best]) best = a;
@@ -498,14 +501,15 @@ static bool learned_allowed(const RockSample<float>& m, const RSState& s, const 
 // action. With `logged` (count x D actions) the rollout follows the logged
 // actions instead and counts, per scenario, the steps whose logged action is
 // neither this choice nor reachable by a column (an allowed action, or defer
-// for the heuristic's action) within `tol` of the best logit.
+// for the heuristic's action) within `tol` of the best logit. `logits_out`
+// (count x D x 32, may be null) gets the network's logits of every step.
 int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count,
                             const int8_t* hist, int32_t start_depth, const double* W1, const double* b1,
                             const double* W2, const double* b2, const double* W3, const double* b3,
                             const int32_t* logged, double tol, double* values, int32_t* disagree,
-                            uint64_t* steps) {
+                            uint64_t* steps, double* logits_out) {
   if (d->kind == 2) return rollout_learned_car(d, block, cap, count, start_depth, W1, b1, W2, b2, W3, b3, logged, tol,
-                                              values, disagree, steps);
+                                              values, disagree, steps, logits_out);
   if (d->kind != 0) return 1;
   RockSample<float> m = make_rs<float>(d);
   Net w{W1, b1, W2, b2, W3, b3};
@@ -528,6 +532,8 @@ int32_t orc_rollout_learned(const orc_model* d, const uint32_t* block, int32_t c
       double x64[kMlpIn], lg[kMlpOut];
       for (int q = 0; q < kMlpIn; ++q) x64[q] = (double)fx[q];
       forward_bf16(w, x64, lg);
+      if (logits_out)
+        for (int q = 0; q < kMlpOut; ++q) logits_out[((size_t)i * m.D + k) * kMlpOut + q] = lg[q];
       int best = -1;
       for (int a = 0; a <= na; ++a)
         if ((a == na || learned_allowed(m, s, h, a)) && (best < 0 || lg[a] > lg[best])) best = a;

@@ -375,14 +375,18 @@ def dsp_set_policy(model_h, mlp_h):
     check(L.dsp_set_policy(model_h, mlp_h))
 
 
-def dsp_rollout_logged(model_h, block_ptr, cap, count, hist_ptr, start_depth, value_ptr, actions_ptr=0, stream=0):
+def dsp_rollout_logged(model_h, block_ptr, cap, count, hist_ptr, start_depth, value_ptr, actions_ptr=0, stream=0,
+                       logits_ptr=0):
     """dsp_rollout with the learned policy; actions (device count x D int32)
-    receives the action of every step, -1 after the rollout ends."""
+    receives the action of every step, logits (device count x D x 32 FP32)
+    the tensor-core tile's logits of every step; entries after a rollout
+    ends are left untouched."""
     L = lib()
     L.dsp_rollout_logged.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
-                                     C.c_void_p, C.c_void_p, C.c_void_p]
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     check(L.dsp_rollout_logged(model_h, C.c_void_p(block_ptr), cap, count, C.c_void_p(hist_ptr), start_depth,
-                               C.c_void_p(value_ptr), C.c_void_p(actions_ptr or None), C.c_void_p(stream)))
+                               C.c_void_p(value_ptr), C.c_void_p(actions_ptr or None), C.c_void_p(logits_ptr or None),
+                               C.c_void_p(stream)))
 
 
 class dsp_plan_node(C.Structure):

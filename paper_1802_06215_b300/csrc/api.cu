@@ -269,7 +269,7 @@ dsp_status dsp_rollout(const dsp_model* m, const uint32_t* block, int32_t cap, i
   if (!block || !value) return fail(DSP_E_INVALID, "dsp_rollout: NULL buffer");
   if (start_depth < 0 || start_depth > m->host->D)
     return fail(DSP_E_INVALID, "dsp_rollout: start depth %d outside 0..D", start_depth);
-  if (m->policy_on) return dsp_rollout_logged(m, block, cap, count, hist, start_depth, value, nullptr, stream);
+  if (m->policy_on) return dsp_rollout_logged(m, block, cap, count, hist, start_depth, value, nullptr, nullptr, stream);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (m->host->kind == DSP_MODEL_CAR)

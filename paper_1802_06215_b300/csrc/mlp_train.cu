@@ -1,9 +1,12 @@
-// Training of the learned default policy pi0 by imitation (softmax
-// cross-entropy on the planner's chosen actions) with this library's own
-// kernels: BF16 GEMMs on the tensor cores (mma.sync m16n8k16, FP32
-// accumulation) with fused epilogues, softmax cross-entropy, column sums for
-// the bias gradients, and Adam on FP32 master weights with BF16 copies for the
-// next step.
+// Training of the learned default policy pi0: softmax cross-entropy on
+// (state features, action label) pairs with this library's own kernels: BF16
+// GEMMs on the tensor cores (mma.sync m16n8k16, FP32 accumulation) with fused
+// epilogues, softmax cross-entropy, column sums for the bias gradients, and
+// Adam on FP32 master weights with BF16 copies for the next step. The labels
+// are the caller's: the shipped weights were trained on approximate
+// policy-iteration labels (the best allowed action by a leaf expansion's Q
+// estimate, else "defer" to the heuristic); planner imitation labels go
+// through the same step.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -107,7 +107,8 @@ cudaError_t launch_car_rollout_mlp_items(dsp_model* m, const dsp_leaf_job* jobs,
                                          cudaStream_t st);
 // Learned-policy rollouts of single car scenarios (dsp_rollout_logged).
 cudaError_t launch_car_rollout_logged(const dsp_model* m, const uint32_t* block, int cap, int count, int start_depth,
-                                      float* value, int32_t* actions, unsigned int* counter, cudaStream_t st);
+                                      float* value, int32_t* actions, float* logits, unsigned int* counter,
+                                      cudaStream_t st);
 // Learned-policy features of car states (dsp_features).
 cudaError_t launch_car_features(const dsp_model* m, const uint32_t* block, int cap, int count, float* out,
                                 cudaStream_t st);

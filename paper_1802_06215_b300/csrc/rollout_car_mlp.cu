@@ -113,6 +113,7 @@ struct CarTcSmem {
   CarShared c;
   int act[kRows];                 // the chosen action of each row
   int heur[kRows];                // the heuristic policy's action of each row (defer)
+  long long lrow[kRows];          // logged rollouts: the row's logits slot (item * D + step), or -1
   unsigned long long mbar;
   uint32_t tmem_base;
 };
@@ -124,6 +125,7 @@ struct CarItemSource {
   int cap, count, start_depth;
   float* value;
   int32_t* log;              // [count][D] actions, or null
+  float* logits;             // [count][D][32] logits of every step (bias added), or null
   unsigned int* next;
 };
 
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) car_rollout_tc_kernel(const DevMo
           *reinterpret_cast<uint4*>(S.x + kmajor_off(row, 8 * c, kMlpIn)) =
               make_uint4(pr[4 * c], pr[4 * c + 1], pr[4 * c + 2], pr[4 * c + 3]);
         S.heur[row] = M.policy(L, danger);
+        S.lrow[row] = alive ? item * M.D + (t - t0) : -1LL;
       }
     }
     fence_async_smem();
@@ -227,6 +230,13 @@ __global__ void __launch_bounds__(kThreads, 1) car_rollout_tc_kernel(const DevMo
     if (tid < kRows) {
       const int best = masked_argmax(lg, S.W.b3, 0xFu, na);
       S.act[tid] = best == na ? S.heur[tid] : best;
+      if (!kExpand && src.logits && S.lrow[tid] >= 0) {
+        float4* o = reinterpret_cast<float4*>(src.logits + (size_t)S.lrow[tid] * kMlpOut);
+#pragma unroll
+        for (int q = 0; q < kMlpOut / 4; ++q)
+          o[q] = make_float4(__fadd_rn(lg[4 * q], S.W.b3[4 * q]), __fadd_rn(lg[4 * q + 1], S.W.b3[4 * q + 1]),
+                             __fadd_rn(lg[4 * q + 2], S.W.b3[4 * q + 2]), __fadd_rn(lg[4 * q + 3], S.W.b3[4 * q + 3]));
+      }
     }
     __syncthreads();
     // step the pair's scenario (every lane calls: the step takes group ballots)
@@ -304,7 +314,8 @@ cudaError_t launch_car_rollout_mlp_items(dsp_model* m, const dsp_leaf_job* jobs,
 }
 
 cudaError_t launch_car_rollout_logged(const dsp_model* m, const uint32_t* block, int cap, int count, int start_depth,
-                                      float* value, int32_t* actions, unsigned int* counter, cudaStream_t st) {
+                                      float* value, int32_t* actions, float* logits, unsigned int* counter,
+                                      cudaStream_t st) {
   CarItemSource src{};
   src.block = block;
   src.cap = cap;
@@ -312,6 +323,7 @@ cudaError_t launch_car_rollout_logged(const dsp_model* m, const uint32_t* block,
   src.start_depth = start_depth;
   src.value = value;
   src.log = actions;
+  src.logits = logits;
   src.next = counter;
   return launch_car_mlp<false>(m, src, count, st);
 }

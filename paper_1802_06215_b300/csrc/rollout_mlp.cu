@@ -116,6 +116,7 @@ struct ItemSource {
   const int8_t* hist;
   float* value;
   int32_t* log;  // [count][D] actions, or null
+  float* logits;  // [count][D][32] logits of every step (bias added), or null
   unsigned int* next;  // item counter
 };
 
@@ -282,6 +283,13 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
       const int best = masked_argmax(lg, S.W.b3, allow, na);
       const int a = best == na ? heur : best;
       if (!kExpand && src.log) src.log[(size_t)item * M.D + (t - t0)] = a;
+      if (!kExpand && src.logits) {
+        float4* o = reinterpret_cast<float4*>(src.logits + ((size_t)item * M.D + (t - t0)) * kMlpOut);
+#pragma unroll
+        for (int q = 0; q < kMlpOut / 4; ++q)
+          o[q] = make_float4(__fadd_rn(lg[4 * q], S.W.b3[4 * q]), __fadd_rn(lg[4 * q + 1], S.W.b3[4 * q + 1]),
+                             __fadd_rn(lg[4 * q + 2], S.W.b3[4 * q + 2]), __fadd_rn(lg[4 * q + 3], S.W.b3[4 * q + 3]));
+      }
       uint64_t key;
       float r = M.step(s, a, t, key);
       M.observe(h, pm, a, key);
@@ -425,10 +433,11 @@ dsp_status dsp_set_policy(dsp_model* m, const dsp_mlp* mlp) {
 
 dsp_status dsp_rollout_logged(const dsp_model* m, const uint32_t* block, int32_t cap, int32_t count,
                               const int8_t* hist, int32_t start_depth, float* value, int32_t* actions,
-                              void* stream) {
+                              float* logits, void* stream) {
   if (!m) return fail(DSP_E_INVALID, "dsp_rollout_logged: model is NULL");
   if (!m->policy_on) return fail(DSP_E_UNSUPPORTED, "dsp_rollout_logged: no learned policy set");
   if (count < 0 || cap < count || !block || !value) return fail(DSP_E_INVALID, "dsp_rollout_logged: bad buffers");
+  if (((uintptr_t)logits & 15) != 0) return fail(DSP_E_INVALID, "dsp_rollout_logged: logits must be 16-byte aligned");
   if (start_depth < 0 || start_depth > m->host->D) return fail(DSP_E_INVALID, "dsp_rollout_logged: start depth");
   if (count == 0) return DSP_OK;
   cudaStream_t st = (cudaStream_t)stream;
@@ -444,9 +453,10 @@ dsp_status dsp_rollout_logged(const dsp_model* m, const uint32_t* block, int32_t
     src.hist = hist;
     src.value = value;
     src.log = actions;
+    src.logits = logits;
     src.next = counter;
     if (m->host->kind == DSP_MODEL_CAR)
-      e = launch_car_rollout_logged(m, block, cap, count, start_depth, value, actions, counter, st);
+      e = launch_car_rollout_logged(m, block, cap, count, start_depth, value, actions, logits, counter, st);
     else
       e = launch_mlp<false>(m->dmodel, m->dwork, (const uint8_t*)m->policy, src, m->plan_step, m->num_sms, count,
                             st);

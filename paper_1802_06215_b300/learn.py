@@ -19,10 +19,14 @@ trained on all labels so far (`dsp_mlp_train_step`: BF16 tensor-core forward
 and backward, FP32 master weights, Adam) and installed (`dsp_set_policy`) as
 pi_{k+1}.
 
-Planner imitation (`harvest`, the `train` command): planner episodes on fresh
-world seeds, with Bayes belief updates (sensor accuracy 0.5 + 0.5 * 2^(-d/20),
-Sec. IV-A); every expanded tree node exported by `dsp_plan_nodes` gives its
-features (`dsp_features`) and argmax_a L(b, a).
+Planner imitation (`harvest`, the `train` command; NOT how the shipped weights
+were made): planner episodes on fresh world seeds, with Bayes belief updates
+(sensor accuracy 0.5 + 0.5 * 2^(-d/20), Sec. IV-A); every expanded tree node
+exported by `dsp_plan_nodes` gives its features (`dsp_features`) and
+argmax_a L(b, a). A network trained this way, without the allowed-action rule
+or defer, looped on illegal or useless actions and gave a lower l0 than the
+heuristic, so `train` writes only to the file given by `--out` and never to
+the shipped weights.
 
 PyTorch only holds device buffers here; every step of the computation runs in
 the library's kernels.
@@ -743,6 +747,8 @@ def main(argv=None):
                      {"config": "rs15_15", "method": "approximate policy iteration",
                                                   "iterations": hl})
     elif a.cmd == "train":
+        if not a.out:
+            ap.error("train (planner imitation, not used for the shipped weights) needs --out")
         policy, init, meta = None, None, {"iterations": []}
         X_all, Y_all = [], []
         for it in range(a.iterations):
@@ -757,8 +763,9 @@ def main(argv=None):
             if policy is not None:
                 _dsp.dsp_mlp_destroy(policy)
             policy = h
-        meta.update({"config": "rs15_15", "steps": a.steps, "plan_seconds": a.plan_seconds, "epochs": a.epochs})
-        save_weights(a.out or a.weights or "paper_1802_06215_b300/weights/rs15_15_pi0.npz", policy, meta)
+        meta.update({"config": "rs15_15", "method": "planner imitation", "steps": a.steps,
+                     "plan_seconds": a.plan_seconds, "epochs": a.epochs})
+        save_weights(a.out, policy, meta)
     else:
         policy, meta = load_weights(a.weights or "paper_1802_06215_b300/weights/rs15_15_pi0.npz")
         roots = eval_roots(cfg, range(9000, 9000 + a.eval_worlds), a.eval_steps, 0.05)

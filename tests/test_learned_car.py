@@ -48,14 +48,35 @@ def install(_dsp, m, w):
     return h
 
 
+TOL = 1e-2
+
+
 def logged(torch, _dsp, m, cfg, b, d0):
+    """Values, actions and the tensor-core tile's logits of every step."""
     n = b.shape[1]
     bd = torch.tensor(np.ascontiguousarray(b).view(np.int32), device="cuda")
     val = torch.zeros(n, dtype=torch.float32, device="cuda")
     act = torch.full((n, cfg.D), -1, dtype=torch.int32, device="cuda")
-    _dsp.dsp_rollout_logged(m.h, bd.data_ptr(), n, n, 0, d0, val.data_ptr(), act.data_ptr())
+    lg = torch.full((n, cfg.D, 32), float("nan"), dtype=torch.float32, device="cuda")
+    _dsp.dsp_rollout_logged(m.h, bd.data_ptr(), n, n, 0, d0, val.data_ptr(), act.data_ptr(),
+                            logits_ptr=lg.data_ptr())
     torch.cuda.synchronize()
-    return val.cpu().numpy(), act.cpu().numpy()
+    return val.cpu().numpy(), act.cpu().numpy(), lg.cpu().numpy()
+
+
+def check_replay(om, b, d0, w, val, act, glog):
+    """Oracle replay of the logged actions: values bit for bit, no logged
+    action trailing the oracle's best logit by more than 1e-2 (argmax agreement
+    wherever the top-2 margin exceeds 1e-2), and every logit of every step
+    within |g - o| <= 1e-2 (1 + |o|)."""
+    ov, bad, steps, olog = oracle.rollout_learned(om, b, None, d0, w, logged=act, tol=TOL, want_logits=True)
+    assert np.array_equal(val.astype(np.float64), ov)
+    assert bad.sum() == 0
+    live = act >= 0
+    assert int(live.sum()) == steps
+    assert np.array_equal(np.isfinite(glog[..., 0]), live) and np.array_equal(np.isfinite(olog[..., 0]), live)
+    g, o = glog[live].astype(np.float64), olog[live]
+    assert np.all(np.abs(g - o) <= TOL * (1.0 + np.abs(o))), float((np.abs(g - o) / (1 + np.abs(o))).max())
 
 
 @pytest.mark.parametrize("P", [50, 7])
@@ -85,10 +106,8 @@ def test_car_learned_rollout_replays_in_oracle(env, seed):
     rng = np.random.default_rng(seed)
     b = I.car_block(cfg, 300, rng)
     for d0 in (0, 30):
-        val, act = logged(torch, _dsp, m, cfg, b, d0)
-        ov, bad, _ = oracle.rollout_learned(oracle.Model(cfg), b, None, d0, w, logged=act, tol=5e-2)
-        assert np.array_equal(val.astype(np.float64), ov)
-        assert bad.sum() == 0
+        val, act, glog = logged(torch, _dsp, m, cfg, b, d0)
+        check_replay(oracle.Model(cfg), b, d0, w, val, act, glog)
         assert len(set(act[act >= 0].tolist())) >= 2
     _, st = m.counters()
     assert st == 0
@@ -145,9 +164,8 @@ def test_car_learned_expansion(env):
             assert np.array_equal(g["rew"][a][:nc], o["rew"][a][:nc])
             assert np.array_equal(g["u"][a][:nc], o["u"][a][:nc])
             nxt, _, _ = om.step(leaf, np.full(n, a, np.int32), j.depth)
-            val, act = logged(torch, _dsp, m, cfg, nxt, j.depth + 1)
-            ov, bad, _ = oracle.rollout_learned(om, nxt, None, j.depth + 1, w, logged=act, tol=5e-2)
-            assert np.array_equal(val.astype(np.float64), ov) and bad.sum() == 0
+            val, act, glog = logged(torch, _dsp, m, cfg, nxt, j.depth + 1)
+            check_replay(om, nxt, j.depth + 1, w, val, act, glog)
             fixed = np.round(val.astype(np.float64) * 2 ** 32).astype(np.int64)
             for c in range(nc):
                 mem = g["perm"][a][g["child_off"][a][c]:g["child_off"][a][c + 1]]
