@@ -95,6 +95,8 @@ def parse():
     p.add_argument("--no-plan", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
     p.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
+    p.add_argument("--no-companions", action="store_true",
+                   help="measure only --workload (a default rs15_15 run also measures car50 under its own key)")
     p.add_argument("--episodes", type=int, default=0,
                    help="run planner episodes on this many held-out Rock Sample 15x15 worlds (heuristic and learned "
                         "default policy) and exit")
@@ -294,18 +296,22 @@ def planning_step(_dsp, m, cfg, plan):
             "scenario_steps_per_s": g["scenario_steps"] / g["seconds"], "action": g["action"]}
 
 
-def learned_step(_dsp, batch, m, cfg, jobs, seconds):
+def learned_step(_dsp, batch, m, cfg, jobs, seconds, n_beliefs=32):
     """The learned default policy (shipped weights) against the heuristic one:
-    root gap after planning steps of equal time from beliefs along heuristic-
-    planner episodes, and the tensor-core rate of the in-rollout network over
-    a learned-policy expansion of the first 256 jobs."""
+    root gap after planning steps of equal time (xi = 0 and target gap 0, so
+    that both searches run to the time limit) from held-out beliefs along
+    heuristic-planner episodes, and the tensor-core rate of the in-rollout
+    network over a learned-policy expansion of the first 256 jobs."""
     import torch
     from paper_1802_06215_b300 import learn
     car = cfg.kind == inputs.CAR
     path = os.path.join(ROOT, "paper_1802_06215_b300", "weights", "car50_pi0.npz" if car else "rs15_15_pi0.npz")
     h, meta = learn.load_weights(path)
-    roots = learn.car_roots(cfg, 6, 9000) if car else learn.eval_roots(cfg, [9000, 9001], 3, 0.05)
-    cmp_ = learn.compare(cfg, h, roots, seconds)
+    if car:
+        roots = learn.car_roots(cfg, n_beliefs, 9000)
+    else:
+        roots = learn.eval_roots(cfg, range(9000, 9000 + (n_beliefs + 1) // 2), 2, 0.05)[:n_beliefs]
+    cmp_ = learn.compare(cfg, h, roots, seconds, xi=0.0, target_gap=0.0)
     sub = batch.JobBatch(m, jobs[:256])
     _dsp.dsp_set_policy(m.h, h)
     sub.run()
@@ -410,19 +416,16 @@ def learned_rollouts(args):
     m.close()
 
 
-def run_ours(args, rank, world):
+def measure(args, name, rank, world, dist, local, headline=True):
+    """One workload: device-resident rate (L2 flushed before every timed step),
+    end-to-end rate through pinned host buffers, kernel time and ALU roofline,
+    the oracle's CPU baseline, and (rank 0) planning and learned-policy
+    comparisons. Returns the JSON line's fields (None on ranks > 0)."""
     import torch
-    local = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    from paper_1802_06215_b300 import _dsp, batch, build
-    build.build()
-    mk, njobs, desc, plan = WORKLOADS[args.workload]
+    from paper_1802_06215_b300 import _dsp, batch
+    mk, njobs, desc, plan = WORKLOADS[name]
     cfg = mk()
-    njobs = args.jobs or njobs
+    njobs = (args.jobs or njobs) if headline else njobs
     jobs = inputs.job_stream(cfg, njobs, 1000 + rank)
     m = batch.Model(cfg)
     jb = batch.JobBatch(m, jobs)
@@ -499,10 +502,8 @@ def run_ours(args, rank, world):
     probe_tops = probe_ops / (p0.elapsed_time(p1) / 1000.0) / 1e12
 
     if rank != 0:
-        if dist:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
+        m.close()
+        return None
     clocks = clk.summary()
     planning = None if args.no_plan else planning_step(_dsp, m, cfg, plan)
     # the same planning step with the leaves going through the device job queue;
@@ -526,15 +527,16 @@ def run_ours(args, rank, world):
                      "default": list(default)}
         _dsp.dsp_set_tuning(m.h, *default)
     learned = None
-    if not args.no_learned and args.workload in ("rs15_15", "car50"):
+    if not args.no_learned and name in ("rs15_15", "car50"):
         learned = learned_step(_dsp, batch, m, cfg, jobs, plan[1])
     cpu = None
     ops_per_step = None
     if not args.no_cpu_baseline:
-        r1 = cpu_oracle_run(cfg, jobs, args.cpu_seconds, 1)
+        secs = args.cpu_seconds if headline else args.cpu_seconds / 2
+        r1 = cpu_oracle_run(cfg, jobs, secs, 1)
         ops_per_step = r1["ops"] / max(1, r1["steps"])
         cores = os.cpu_count() or 1
-        rn = cpu_oracle_run(cfg, jobs, args.cpu_seconds / 2, cores)
+        rn = cpu_oracle_run(cfg, jobs, secs / 2, cores)
         cpu = {"value": r1["steps"] / r1["seconds"], "unit": "scenario-steps/s", "cores": 1, "kind": "oracle",
                "sample": f"first {r1['jobs']} of the {njobs} jobs of this workload, single-threaded, "
                          f"{r1['seconds']:.1f} s", "ops_per_scenario_step": ops_per_step,
@@ -546,7 +548,7 @@ def run_ours(args, rank, world):
     roof = None
     if ops_per_step:
         achieved = ops_per_step * steps_per_launch / avg_kernel_s / 1e12
-        traffic = measured_traffic(args.workload, kind)
+        traffic = measured_traffic(name, kind)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": traffic,
                 "peak_source": "derived: 148 SMs x 128 lanes x 2032 MHz (one 32-bit op per lane per clock)",
@@ -560,7 +562,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "scenario-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": _dtype(cfg), "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {desc}", "jobs_per_step": njobs,
+        "config": {"workload": f"{name}: {desc}", "jobs_per_step": njobs,
                    "l2": "256 MiB buffer written before every timed step (outside the events)"},
         "leaf_expansions_per_s": njobs * world / (t_ms / 1000.0),
         "scenario_steps_per_step": steps_per_launch,
@@ -577,7 +579,36 @@ def run_ours(args, rank, world):
         "learned_pi0": learned,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    m.close()
+    return line
+
+
+# Workloads measured beside the headline one in a default run (the driving
+# task among 50 pedestrians beside Rock Sample 15x15), each under its own key.
+COMPANIONS = {"rs15_15": ["car50"]}
+
+
+def run_ours(args, rank, world):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1802_06215_b300 import build
+    build.build()
+    line = measure(args, args.workload, rank, world, dist, local)
+    extra = {}
+    if not args.no_companions:
+        for name in COMPANIONS.get(args.workload, []):
+            extra[name] = measure(args, name, rank, world, dist, local, headline=False)
+    if rank == 0:
+        for name, sub in extra.items():
+            sub.pop("metric", None)
+            sub.pop("n_gpus", None)
+            line[name] = sub
+        print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -95,9 +95,9 @@ def start_word(cfg):
     return np.uint32(0 | ((cfg.n // 2) << 8))
 
 
-def search_params(seconds, threads=4):
+def search_params(seconds, threads=4, xi=0.95, target_gap=0.0):
     return _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=seconds, c_a=1.0, c_o=0.5,
-                                  xi=0.95, target_gap=0.0, deterministic=0, use_queue=0)
+                                  xi=xi, target_gap=target_gap, deterministic=0, use_queue=0)
 
 
 def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node_cap=1 << 15, harvest=True):
@@ -665,9 +665,12 @@ def car_roots(cfg, count, seed):
     return roots
 
 
-def compare(cfg, policy, roots, seconds, threads=4):
+def compare(cfg, policy, roots, seconds, threads=4, xi=0.95, target_gap=0.0):
     """Root gap u - l after one planning step of `seconds` from each root
-    belief, heuristic pi0 then learned pi0, on the same random streams."""
+    belief, heuristic pi0 then learned pi0, on the same random streams. With
+    xi = 0 and target_gap = 0 a search stops at its time limit only (a path
+    ends at a zero-gap node or depth D), so both policies plan for the same
+    time; each arm reports the seconds it took."""
     model = batch.Model(cfg)
     rows = []
     for k, (root, hist) in enumerate(roots):
@@ -675,18 +678,29 @@ def compare(cfg, policy, roots, seconds, threads=4):
         for name, pol in (("heuristic", None), ("learned", policy)):
             _dsp.dsp_set_policy(model.h, pol)
             model.set_plan_step(0x40000000 + k)
-            r = _dsp.dsp_plan(model.h, root, hist, search_params(seconds, threads), model.num_actions)
+            r = _dsp.dsp_plan(model.h, root, hist, search_params(seconds, threads, xi, target_gap),
+                              model.num_actions)
             row[name] = {"gap": r["root_u"] - r["root_l"], "u": r["root_u"], "l": r["root_l"],
                          "action": int(r["action"]), "expansions": r["expansions"], "seconds": r["seconds"]}
         rows.append(row)
     model.close()
-    out = {"beliefs": len(rows), "planning_time_s": seconds, "threads": threads}
+    out = {"beliefs": len(rows), "planning_time_s": seconds, "threads": threads, "xi": xi,
+           "target_gap": target_gap}
     for name in ("heuristic", "learned"):
+        secs = [r[name]["seconds"] for r in rows]
         out[name] = {"mean_root_gap": float(np.mean([r[name]["gap"] for r in rows])),
                      "mean_root_l": float(np.mean([r[name]["l"] for r in rows])),
                      "mean_root_u": float(np.mean([r[name]["u"] for r in rows])),
                      "mean_expansions": float(np.mean([r[name]["expansions"] for r in rows])),
-                     "decisions_per_s": len(rows) / sum(r[name]["seconds"] for r in rows)}
+                     "mean_seconds": float(np.mean(secs)), "min_seconds": float(np.min(secs)),
+                     "max_seconds": float(np.max(secs)),
+                     # searches that ended before 95 % of the budget: with the root gap
+                     # closed (nothing left to plan), or for another reason
+                     "ended_early_gap_closed": int(sum(r[name]["seconds"] < 0.95 * seconds and
+                                                       r[name]["gap"] <= 1e-9 for r in rows)),
+                     "ended_early_other": int(sum(r[name]["seconds"] < 0.95 * seconds and
+                                                  r[name]["gap"] > 1e-9 for r in rows)),
+                     "decisions_per_s": len(rows) / sum(secs)}
     out["decision_agreement"] = float(np.mean([r["heuristic"]["action"] == r["learned"]["action"] for r in rows]))
     out["learned_tighter"] = float(np.mean([r["learned"]["gap"] < r["heuristic"]["gap"] for r in rows]))
     return out
