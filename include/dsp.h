@@ -235,6 +235,36 @@ typedef struct {
 dsp_status dsp_plan(dsp_model* model, const uint32_t* root_states, int32_t n, const int8_t* hist,
                     const dsp_search_params* params, dsp_search_result* result, int32_t* root_visits);
 
+/* dsp_plan over several GPUs: node-level parallelism (Sec. III-D), the
+ * paper's independent leaf expansions spread over devices. models: n_models
+ * (1..64) models, one per GPU (each created with that GPU current), from the
+ * same description, plan step and policy (DSP_E_INVALID otherwise). The
+ * expansion with global index e of the step goes to models[e mod n_models]
+ * (dsp_route_leaves); the new node's states and grouped positions stay on
+ * that GPU, and a leaf whose parent's states live on another GPU first gets
+ * them (and its scenario positions) by a peer copy on its own stream. The
+ * model tables and the policy are replicated by construction (one model per
+ * GPU); no kernel reads another GPU's memory; each expansion's small
+ * results come back through host memory, which owns the tree. The root's
+ * states go to models[0]. The device queue serves one model
+ * (DSP_E_UNSUPPORTED with use_queue and n_models > 1, free running).
+ * Deterministic rounds give the same tree as dsp_plan on one model, since an
+ * expansion's results do not depend on the GPU that computes it. Results
+ * and arguments otherwise as dsp_plan; scenario_steps sums all models. */
+dsp_status dsp_plan_multi(dsp_model* const* models, int32_t n_models, const uint32_t* root_states, int32_t n,
+                          const int8_t* hist, const dsp_search_params* params, dsp_search_result* result,
+                          int32_t* root_visits);
+
+/* The routing rule of dsp_plan_multi, on the host only (touches no GPU):
+ * for n_leaves leaves that are expansions first_expansion, first_expansion
+ * + 1, ... of a step, whose parents' states live on models parent_model[k]
+ * (0..n_models-1), target[k] = (first_expansion + k) mod n_models and
+ * copy[k] = 1 where target[k] != parent_model[k] (the parent's states and
+ * the leaf's positions must be copied first), else 0. HOST arrays of
+ * n_leaves entries. DSP_E_INVALID for bad arguments. */
+dsp_status dsp_route_leaves(int32_t n_leaves, int64_t first_expansion, int32_t n_models, const int32_t* parent_model,
+                            int32_t* target, int32_t* copy);
+
 /* One node of a finished planning step, as dsp_plan_nodes exports it. */
 typedef struct {
   int32_t depth;   /* tree depth, root 0 */
@@ -304,6 +334,48 @@ dsp_status dsp_pomcp_plan(dsp_model* model, const uint32_t* root_states, int32_t
  * other values. */
 dsp_status dsp_set_tuning(dsp_model* model, int32_t block, int32_t tps);
 dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
+
+/* The whole launch shape of dsp_expand_leaves (and of
+ * dsp_expand_leaves_noalloc). The paper fixes the mapping of work to the GPU
+ * (an action per thread block, a scenario per thread, factored elements per
+ * warp; Sec. III-D); every field here is a measured choice instead. 0 keeps
+ * each field's default.
+ *  - block_b: rollout phase CTA size, Rock Sample (128, 256 or 512; default
+ *    256): the scenarios (items) per CTA, one per thread.
+ *  - ctas_b: rollout phase CTAs per SM, Rock Sample and navigation (1..32,
+ *    capped by what fits; default as many as fit).
+ *  - warps_a: Rock Sample grouping phase, warps per CTA (1..16): with A
+ *    actions each warp expands about A / warps_a whole actions of a job
+ *    (default: 5 warps with 12 or more jobs per SM for one robot, else up to
+ *    16 warps of equal action counts).
+ *  - tps: car, lanes sharing one scenario (4, 8, 16 or 32; default the
+ *    smallest that gives each lane at most one pedestrian pair): the
+ *    within-step split over pedestrians; with more pairs than lanes each lane
+ *    takes several.
+ *  - ctas_car: car kernel CTAs per SM (1..32, capped by what fits).
+ * One-robot Rock Sample has no within-step work to split (the default
+ * policy reads one table entry per candidate rock), so its scenarios map one
+ * to a thread. DSP_E_INVALID for values outside these sets. */
+typedef struct {
+  int32_t block_b, ctas_b, warps_a, tps, ctas_car;
+} dsp_launch_shape;
+dsp_status dsp_set_launch_shape(dsp_model* model, const dsp_launch_shape* shape);
+dsp_status dsp_get_launch_shape(const dsp_model* model, dsp_launch_shape* shape);
+
+/* Autotuner over the launch shape: times dsp_expand_leaves on the caller's
+ * jobs (HOST array; results are written to their buffers) for the default
+ * shape and for every candidate of the model's kind, `reps` timed calls
+ * each after one warm-up (CUDA events on `stream`), and keeps the fastest.
+ *  - Rock Sample: block_b {128, 256, 512} x ctas_b {as many as fit, 6, 4} x
+ *    warps_a {default, 5, 10} (two robots: {default, 8, 16}).
+ *  - car: tps {4, 8, 16, 32} x ctas_car {as many as fit, 3, 2}.
+ *  - navigation: ctas_b {as many as fit, 6, 4, 2}.
+ * best: the chosen shape (set in the model); best_ms / default_ms: mean time
+ * per call of the chosen and the default shape; tried: candidates timed
+ * (each may be NULL). Results of every call are identical whatever the
+ * shape. */
+dsp_status dsp_autotune_shape(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, int32_t reps, void* stream,
+                              dsp_launch_shape* best, float* best_ms, float* default_ms, int32_t* tried);
 
 /* dsp_expand_leaves for callers that must not allocate device memory while
  * they plan (the paper has no counterpart). dsp_expand_leaves takes its work

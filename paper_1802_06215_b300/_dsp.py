@@ -166,6 +166,46 @@ def dsp_set_tuning(h, block, tps):
     check(lib().dsp_set_tuning(h, block, tps))
 
 
+class dsp_launch_shape(C.Structure):
+    _fields_ = [("block_b", C.c_int32), ("ctas_b", C.c_int32), ("warps_a", C.c_int32), ("tps", C.c_int32),
+                ("ctas_car", C.c_int32)]
+
+
+SHAPE_FIELDS = tuple(f for f, _ in dsp_launch_shape._fields_)
+
+
+def dsp_set_launch_shape(h, **shape):
+    """Fields of dsp_launch_shape (missing ones 0 = default)."""
+    s = dsp_launch_shape(**{k: int(shape.get(k, 0)) for k in SHAPE_FIELDS})
+    L = lib()
+    L.dsp_set_launch_shape.argtypes = [C.c_void_p, C.POINTER(dsp_launch_shape)]
+    check(L.dsp_set_launch_shape(h, C.byref(s)))
+
+
+def dsp_get_launch_shape(h):
+    s = dsp_launch_shape()
+    L = lib()
+    L.dsp_get_launch_shape.argtypes = [C.c_void_p, C.POINTER(dsp_launch_shape)]
+    check(L.dsp_get_launch_shape(h, C.byref(s)))
+    return {k: getattr(s, k) for k in SHAPE_FIELDS}
+
+
+def dsp_autotune_shape(h, jobs_array, n_jobs, reps=3, stream=0):
+    """Times the default and every candidate launch shape on the jobs, keeps
+    the fastest in the model; returns {shape fields..., ms, default_ms, tried}."""
+    best = dsp_launch_shape()
+    bms, dms, tried = C.c_float(0), C.c_float(0), C.c_int32(0)
+    L = lib()
+    L.dsp_autotune_shape.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                     C.POINTER(dsp_launch_shape), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                     C.POINTER(C.c_int32)]
+    check(L.dsp_autotune_shape(h, C.cast(jobs_array, C.c_void_p), n_jobs, reps, C.c_void_p(stream), C.byref(best),
+                               C.byref(bms), C.byref(dms), C.byref(tried)))
+    out = {k: getattr(best, k) for k in SHAPE_FIELDS}
+    out.update(ms=bms.value, default_ms=dms.value, tried=tried.value)
+    return out
+
+
 def dsp_get_tuning(h):
     b, t = C.c_int32(0), C.c_int32(0)
     check(lib().dsp_get_tuning(h, C.byref(b), C.byref(t)))
@@ -206,6 +246,41 @@ def dsp_plan(h, root_states, hist, params, num_actions):
     out = {f: getattr(res, f) for f, _ in dsp_search_result._fields_}
     out["root_visits"] = visits
     return out
+
+
+def dsp_plan_multi(hs, root_states, hist, params, num_actions):
+    """dsp_plan with leaf expansions routed over several models (one per GPU);
+    hs: list of model handles."""
+    import numpy as np
+    rs = np.ascontiguousarray(root_states, dtype=np.uint32)
+    n = rs.shape[1]
+    hv = None if hist is None else np.ascontiguousarray(hist, dtype=np.int8)
+    arr = (C.c_void_p * len(hs))(*hs)
+    res = dsp_search_result()
+    visits = np.zeros(num_actions, np.int32)
+    L = lib()
+    L.dsp_plan_multi.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                 C.POINTER(dsp_search_params), C.POINTER(dsp_search_result), C.c_void_p]
+    check(L.dsp_plan_multi(C.cast(arr, C.c_void_p), len(hs), rs.ctypes.data, n,
+                           None if hv is None else hv.ctypes.data, C.byref(params), C.byref(res),
+                           visits.ctypes.data))
+    out = {f: getattr(res, f) for f, _ in dsp_search_result._fields_}
+    out["root_visits"] = visits
+    return out
+
+
+def dsp_route_leaves(n_models, first_expansion, parent_model):
+    """(target model, copy flag) per leaf: the host-only routing rule of
+    dsp_plan_multi."""
+    import numpy as np
+    pm = np.ascontiguousarray(parent_model, dtype=np.int32)
+    k = len(pm)
+    tgt = np.zeros(k, np.int32)
+    cp = np.zeros(k, np.int32)
+    L = lib()
+    L.dsp_route_leaves.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    check(L.dsp_route_leaves(k, first_expansion, n_models, pm.ctypes.data, tgt.ctypes.data, cp.ctypes.data))
+    return tgt, cp
 
 
 class dsp_pomcp_params(C.Structure):

@@ -1,8 +1,10 @@
-"""Autotuner cache: the launch shape dsp_autotune measured, kept per (model,
-K, |A|, horizon, GPU) in a JSON file so later runs reuse it.
+"""Autotuner cache: the launch shape dsp_autotune_shape measured, kept per
+(model, K, |A|, horizon, GPU) in a JSON file so later runs reuse it.
 
-The measuring itself runs in the CUDA library (dsp_autotune); this module
-only builds the cache key and reads and writes the file.
+The measuring itself runs in the CUDA library (dsp_autotune_shape: the
+rollout phase's CTA size and CTAs per SM, the grouping phase's warps per CTA,
+the car's lanes per scenario and CTAs per SM); this module only builds the
+cache key and reads and writes the file.
 """
 import ctypes as C
 import json
@@ -33,6 +35,7 @@ def _store(path, cache):
 
 
 def dsp_autotune(h, jobs_array, n_jobs, reps=5, stream=0):
+    """The library's narrower tuner (rollout CTA size, car lanes per scenario)."""
     L = _dsp.lib()
     L.dsp_autotune.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32), C.POINTER(C.c_float)]
@@ -42,21 +45,22 @@ def dsp_autotune(h, jobs_array, n_jobs, reps=5, stream=0):
     return {"block": b.value, "tps": t.value, "ms": ms.value}
 
 
-def autotune(model, batch, gpu_name, cache_path=None, reps=5, measure=None):
+def autotune(model, batch, gpu_name, cache_path=None, reps=3, measure=None):
     """Sets the model's launch shape from the cache, or measures it on `batch`
     (a JobBatch) and stores it. `measure(model, batch, reps)` replaces the
-    library call (for tests of the cache)."""
+    library call (for tests of the cache); it returns the shape fields and
+    "ms". Returns the shape with "cached"."""
     key = cache_key(model.cfg, model.num_actions, gpu_name)
     cache = _load(cache_path)
     if key in cache:
         best = cache[key]
-        _dsp.dsp_set_tuning(model.h, best["block"], best["tps"])
+        _dsp.dsp_set_launch_shape(model.h, **{k: best[k] for k in _dsp.SHAPE_FIELDS})
         return dict(best, cached=True)
     if measure is None:
-        best = dsp_autotune(model.h, batch.descs, len(batch.jobs), reps)
+        best = _dsp.dsp_autotune_shape(model.h, batch.descs, len(batch.jobs), reps)
     else:
         best = measure(model, batch, reps)
-        _dsp.dsp_set_tuning(model.h, best["block"], best["tps"])
-    cache[key] = {"block": best["block"], "tps": best["tps"], "ms": best["ms"]}
+        _dsp.dsp_set_launch_shape(model.h, **{k: best.get(k, 0) for k in _dsp.SHAPE_FIELDS})
+    cache[key] = {k: best.get(k, 0) for k in _dsp.SHAPE_FIELDS + ("ms", "default_ms")}
     _store(cache_path, cache)
     return dict(best, cached=False)

@@ -325,6 +325,34 @@ dsp_status dsp_get_tuning(const dsp_model* m, int32_t* block, int32_t* tps) {
   return DSP_OK;
 }
 
+dsp_status dsp_set_launch_shape(dsp_model* m, const dsp_launch_shape* s) {
+  if (!m || !s) return fail(DSP_E_INVALID, "dsp_set_launch_shape: NULL argument");
+  if (!(s->block_b == 0 || s->block_b == 128 || s->block_b == 256 || s->block_b == 512))
+    return fail(DSP_E_INVALID, "dsp_set_launch_shape: block_b %d not in {0,128,256,512}", s->block_b);
+  if (!(s->tps == 0 || s->tps == 4 || s->tps == 8 || s->tps == 16 || s->tps == 32))
+    return fail(DSP_E_INVALID, "dsp_set_launch_shape: tps %d not in {0,4,8,16,32}", s->tps);
+  if (s->ctas_b < 0 || s->ctas_b > 32 || s->ctas_car < 0 || s->ctas_car > 32)
+    return fail(DSP_E_INVALID, "dsp_set_launch_shape: CTAs per SM outside 0..32");
+  if (s->warps_a < 0 || s->warps_a > 16)
+    return fail(DSP_E_INVALID, "dsp_set_launch_shape: warps_a %d outside 0..16", s->warps_a);
+  m->tune_block = s->block_b;
+  m->tune_ctas_b = s->ctas_b;
+  m->tune_warps_a = s->warps_a;
+  m->tune_tps = s->tps;
+  m->tune_ctas_car = s->ctas_car;
+  return DSP_OK;
+}
+
+dsp_status dsp_get_launch_shape(const dsp_model* m, dsp_launch_shape* s) {
+  if (!m || !s) return fail(DSP_E_INVALID, "dsp_get_launch_shape: NULL argument");
+  s->block_b = m->tune_block;
+  s->ctas_b = m->tune_ctas_b;
+  s->warps_a = m->tune_warps_a;
+  s->tps = m->tune_tps;
+  s->ctas_car = m->tune_ctas_car;
+  return DSP_OK;
+}
+
 dsp_status dsp_kernel_timing(dsp_model* m, int32_t enable, double* total_ms, int32_t* calls) {
   if (!m) return fail(DSP_E_INVALID, "dsp_kernel_timing: model is NULL");
   std::lock_guard<std::mutex> lock(m->timing_mu);
@@ -529,7 +557,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
                            (const long long*)dunits, dorder,
                            n_jobs,
                            plan.total_items, items, counters, m->plan_step, m->num_sms, block_b,
-                           m->policy_on ? m->policy : nullptr, st);
+                           m->policy_on ? m->policy : nullptr, st, m->tune_warps_a, m->tune_ctas_b);
     }
     if (m->timing) {
       cudaEventRecord(ev[1], st);

@@ -244,6 +244,7 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, car_expand_kernel<TPS, KP>, 256, smem);
+  if (m->tune_ctas_car > 0) per_sm = std::min(per_sm, m->tune_ctas_car);
   per_sm = std::max(1, per_sm);
   int grid = std::max(1, std::min(n_units, per_sm * m->num_sms));
   // observation slots, one per CTA, stream-ordered so that launches on other

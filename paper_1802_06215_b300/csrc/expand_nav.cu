@@ -325,6 +325,7 @@ cudaError_t launch_nav_expand(dsp_model* m, const dsp_leaf_job* djobs, const int
   if (e != cudaSuccess) return e;
   int per_sm_b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, nav_rollout_items_kernel, 32 * kWarpsB, 0);
+  if (m->tune_ctas_b > 0) per_sm_b = std::min(per_sm_b, m->tune_ctas_b);
   const long long warps = (total_items + 31) / 32;
   const int grid_b = (int)std::max(
       1LL, std::min((warps + kWarpsB - 1) / kWarpsB, (long long)std::max(1, per_sm_b) * m->num_sms));

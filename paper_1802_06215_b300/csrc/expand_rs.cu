@@ -747,7 +747,8 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
 template <int R>
 cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
-                             uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st) {
+                             uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st,
+                             int warps_a, int ctas_b) {
   Items<R> items{item_buf, total_items};
   // Each warp expands whole actions: as many warps as give every warp the
   // same number of a job's actions (20 actions: 10 warps of 2; 400: 16 of
@@ -756,8 +757,11 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
   // job's barriers leaves others running (4096 jobs of 15x15: 0.280 against
   // 0.295 ms). With fewer jobs the wider CTA finishes the largest job sooner
   // (512 jobs: 55 against 72 us).
+  // warps_a (the launch shape's grouping-phase warps, 1..16) replaces the rule.
   int block_a = kBlockA;
-  {
+  if (warps_a > 0) {
+    block_a = 32 * std::min(warps_a, kWarpsA);
+  } else {
     const int na = std::max(1, num_actions);
     const bool narrow = R == 1 && n_jobs >= 12 * num_sms;
     const int per_warp = narrow ? (na + 4) / 5 : (na + kWarpsA - 1) / kWarpsA;
@@ -781,6 +785,7 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
   const size_t key_bytes = sizeof(uint16_t) * (size_t)key_words;
   int per_sm_b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, rs_rollout_items_kernel<R>, block_b, key_bytes);
+  if (ctas_b > 0) per_sm_b = std::min(per_sm_b, ctas_b);
   long long chunks = (total_items + 31) / 32;
   long long want = (chunks + block_b / 32 - 1) / (block_b / 32);
   int grid_b = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm_b) * num_sms));
@@ -1072,12 +1077,12 @@ cudaError_t rs_set_key_smem(int robots, int key_words) {
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, int key_words, DevWork* work,
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf, unsigned int* counters, uint32_t plan_step,
-                             int num_sms, int block_b, const void* policy, cudaStream_t st) {
+                             int num_sms, int block_b, const void* policy, cudaStream_t st, int warps_a, int ctas_b) {
   if (robots == 1)
     return launch_two_phase<1>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items,
-                               item_buf, counters, plan_step, num_sms, block_b, policy, st);
+                               item_buf, counters, plan_step, num_sms, block_b, policy, st, warps_a, ctas_b);
   return launch_two_phase<2>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items, item_buf,
-                             counters, plan_step, num_sms, block_b, nullptr, st);
+                             counters, plan_step, num_sms, block_b, nullptr, st, warps_a, ctas_b);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,
@@ -1240,7 +1245,7 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
     int block_b = m->tune_block > 0 ? m->tune_block : 256;
     e = launch_rs_expand(m->dmodel, m->host->robots, m->host->num_actions, rs_key_words(m->host), m->dwork, djobs,
                          dbase, dorder, n_jobs, plan.total_items, items, counters, m->plan_step, m->num_sms,
-                         block_b, m->policy_on ? m->policy : nullptr, st);
+                         block_b, m->policy_on ? m->policy : nullptr, st, m->tune_warps_a, m->tune_ctas_b);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc launch");
   return DSP_OK;

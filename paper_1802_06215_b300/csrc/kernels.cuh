@@ -22,7 +22,7 @@ cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, in
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
-                             const void* policy, cudaStream_t st);
+                             const void* policy, cudaStream_t st, int warps_a = 0, int ctas_b = 0);
 // Learned-policy rollout phase over the item list (one robot).
 cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs,
                                         uint32_t* item_buf, long long total_items, unsigned int* counter,

@@ -27,8 +27,12 @@ struct dsp_model {
   cudaMemPool_t pool = nullptr;      // stream-ordered work buffers; keeps its peak size until destroy
   dsp_queue* queue = nullptr;        // device job queue of the tree search, kept across planning steps
   int queue_cap = 0;
-  int tune_block = 0;                // CTA size chosen by the autotuner (0 = default)
-  int tune_tps = 0;                  // car: threads per scenario (0 = default)
+  // launch shape (dsp_set_launch_shape / the autotuner); 0 = default
+  int tune_block = 0;                // rollout phase CTA size (Rock Sample)
+  int tune_tps = 0;                  // car: threads per scenario
+  int tune_ctas_b = 0;               // rollout phase CTAs per SM (Rock Sample, navigation)
+  int tune_warps_a = 0;              // Rock Sample grouping phase: warps per CTA
+  int tune_ctas_car = 0;             // car kernel CTAs per SM
   void* policy = nullptr;            // learned pi0 for rollouts (device, transposed BF16 weights)
   bool policy_on = false;
   bool timing = false;               // record events around the expansion kernels

@@ -50,10 +50,12 @@ uint64_t mix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-// Device memory for one plan: bump allocation from 256 MB chunks.
+// Device memory for one plan on one GPU: bump allocation from 256 MB chunks.
 class Arena {
  public:
+  explicit Arena(int device) : device_(device) {}
   ~Arena() {
+    if (!chunks_.empty()) cudaSetDevice(device_);
     for (void* p : chunks_) cudaFree(p);
   }
   cudaError_t alloc(size_t bytes, void** out) {
@@ -62,7 +64,8 @@ class Arena {
     if (chunks_.empty() || off_ + bytes > cap_) {
       size_t cap = std::max(bytes, (size_t)256 << 20);
       void* p = nullptr;
-      cudaError_t e = cudaMalloc(&p, cap);
+      cudaError_t e = cudaSetDevice(device_);
+      if (e == cudaSuccess) e = cudaMalloc(&p, cap);
       if (e != cudaSuccess) return e;
       chunks_.push_back(p);
       cap_ = cap;
@@ -74,6 +77,7 @@ class Arena {
   }
 
  private:
+  int device_;
   std::mutex mu_;
   std::vector<void*> chunks_;
   size_t cap_ = 0, off_ = 0;
@@ -101,6 +105,7 @@ struct Node {
   int pa = -1;                     // action into this node
   const uint16_t* d_idx = nullptr; // positions in the parent's states (device)
   uint32_t* d_states = nullptr;    // own states once expanded (root: the given ones)
+  int dev = 0;                     // model (GPU) that holds d_states and d_perm
   uint16_t* d_perm = nullptr;      // grouped positions written by the expansion
   int8_t hist[32] = {};
   uint64_t key = 0;
@@ -158,16 +163,45 @@ struct JobOut {
   }
 };
 
+// One CUDA stream per model (GPU) for one search thread.
+struct Streams {
+  std::vector<cudaStream_t> st;
+  std::vector<int> dev;
+  ~Streams() {
+    for (size_t g = 0; g < st.size(); ++g) {
+      cudaSetDevice(dev[g]);
+      cudaStreamDestroy(st[g]);
+    }
+  }
+  cudaError_t make(const std::vector<dsp_model*>& models) {
+    for (dsp_model* m : models) {
+      cudaStream_t x = nullptr;
+      cudaError_t e = cudaSetDevice(m->device);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+      st.push_back(x);
+      dev.push_back(m->device);
+    }
+    return cudaSetDevice(models[0]->device);
+  }
+};
+
 class Search {
  public:
-  Search(dsp_model* m, const dsp_search_params& p) : m_(m), p_(p) {
-    na_ = m->host->num_actions;
-    K_ = (double)m->host->K;
-    gamma_ = (double)m->host->gamma;
-    D_ = m->host->D;
-    words_ = m->host->words;
-    kind_ = m->host->kind;
-    per_ = m->host->per_robot;
+  // models: one per GPU, built from one description; leaf expansions are
+  // routed over them (node-level parallelism, Sec. III-D). models[0] holds
+  // the root's states.
+  Search(const std::vector<dsp_model*>& models, const dsp_search_params& p)
+      : models_(models), m_(models[0]), p_(p) {
+    na_ = m_->host->num_actions;
+    K_ = (double)m_->host->K;
+    gamma_ = (double)m_->host->gamma;
+    D_ = m_->host->D;
+    words_ = m_->host->words;
+    kind_ = m_->host->kind;
+    per_ = m_->host->per_robot;
+    for (dsp_model* m : models_) arenas_.emplace_back(new Arena(m->device));
+    ident_.assign(models_.size(), nullptr);
   }
 
   dsp_status run(const uint32_t* root_host, int n, const int8_t* hist, dsp_search_result* out, int32_t* visits);
@@ -303,32 +337,48 @@ class Search {
     }
   }
 
-  // Device buffers and the job descriptor of one leaf (caller prepares `jo`).
-  dsp_status prepare(Node* b, dsp_leaf_job& J, const JobOut& jo, char* dsmall) {
+  // Device buffers and the job descriptor of one leaf on model g (caller
+  // prepares `jo`, with model g's GPU current). With `copy` the states its
+  // scenarios come from (the parent's, or the root's given ones) and its
+  // scenario positions are first copied from the GPU that holds them, on `st`.
+  dsp_status prepare(Node* b, int g, bool copy, dsp_leaf_job& J, const JobOut& jo, char* dsmall, cudaStream_t st) {
     int n = b->n;
     std::memset(&J, 0, sizeof(J));
-    if (b->parent == nullptr) {
-      J.parent = b->d_states;
-      J.parent_cap = n;
-      J.idx = d_ident_;
-      J.last_action = -1;
-    } else {
-      J.parent = b->parent->d_states;
-      J.parent_cap = b->parent->n;
-      J.idx = b->d_idx;
-      J.last_action = b->pa;
+    Arena& ar = *arenas_[g];
+    const Node* src = b->parent != nullptr ? b->parent : b;
+    const uint32_t* pstates = src->d_states;
+    const uint16_t* idx = b->parent != nullptr ? b->d_idx : ident_[g];
+    void* p = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (copy) {
+      const size_t sb = (size_t)words_ * src->n * 4;
+      e = ar.alloc(sb, &p);
+      if (e == cudaSuccess)
+        e = cudaMemcpyPeerAsync(p, models_[g]->device, pstates, models_[src->dev]->device, sb, st);
+      if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: parent states to the leaf's GPU");
+      pstates = (const uint32_t*)p;
+      if (b->parent != nullptr) {
+        e = ar.alloc((size_t)n * 2, &p);
+        if (e == cudaSuccess)
+          e = cudaMemcpyPeerAsync(p, models_[g]->device, idx, models_[src->dev]->device, (size_t)n * 2, st);
+        if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: scenario positions to the leaf's GPU");
+        idx = (const uint16_t*)p;
+      }
     }
+    J.parent = pstates;
+    J.parent_cap = src->n;
+    J.idx = idx;
+    J.last_action = b->parent != nullptr ? b->pa : -1;
     J.n_scen = n;
     J.depth = b->depth;
     std::memcpy(J.hist, b->hist, 32);
     J.first_action = 0;
     J.n_actions = na_;
     J.child_cap = jo.cap;
-    void* p = nullptr;
-    cudaError_t e = arena_.alloc((size_t)words_ * n * 4, &p);
+    e = ar.alloc((size_t)words_ * n * 4, &p);
     if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: node states");
     J.leaf_states = (uint32_t*)p;
-    e = arena_.alloc((size_t)na_ * n * 2, &p);
+    e = ar.alloc((size_t)na_ * n * 2, &p);
     if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: grouped positions");
     J.perm = (uint16_t*)p;
     J.child_count = (int32_t*)(dsmall + jo.o_cnt);
@@ -344,7 +394,7 @@ class Search {
   // by the calling thread, and other threads stop at an unexpanded leaf, so
   // this runs without the tree lock; publish() then marks the leaf expanded.
   // The nodes of one expansion come from the pool in one batch.
-  void create_children(Node* b, const dsp_leaf_job& J, const JobOut& jo, const char* hsmall) {
+  void create_children(Node* b, int dev, const dsp_leaf_job& J, const JobOut& jo, const char* hsmall) {
     const int32_t* cnt = (const int32_t*)(hsmall + jo.o_cnt);
     const int32_t* off = (const int32_t*)(hsmall + jo.o_off);
     const uint64_t* key = (const uint64_t*)(hsmall + jo.o_key);
@@ -353,6 +403,7 @@ class Search {
     const int64_t* ls = (const int64_t*)(hsmall + jo.o_l);
     b->d_states = J.leaf_states;
     b->d_perm = J.perm;
+    b->dev = dev;
     b->q.reset(new QBranch[na_]);
     b->nq = na_;
     b->Na.reset(new std::atomic<long long>[na_]);
@@ -413,9 +464,10 @@ class Search {
     std::vector<dsp_leaf_job> jobs;
     std::vector<JobOut> jo;
     std::vector<size_t> base;
+    std::vector<int32_t> dev;  // the model each leaf was expanded on
     const char* host = nullptr;
   };
-  dsp_status expand_batch(const std::vector<Node*>& leaves, cudaStream_t st, Pinned& pinned) {
+  dsp_status expand_batch(const std::vector<Node*>& leaves, Streams& st, Pinned& pinned) {
     BatchOut bo;
     dsp_status s = expand_gpu(leaves, st, pinned, bo);
     if (s != DSP_OK) return s;
@@ -424,7 +476,8 @@ class Search {
   }
   void finish_batch(const std::vector<Node*>& leaves, const BatchOut& bo) {
     const int L = (int)leaves.size();
-    for (int k = 0; k < L; ++k) create_children(leaves[k], bo.jobs[k], bo.jo[k], bo.host + bo.base[k]);
+    for (int k = 0; k < L; ++k)
+      create_children(leaves[k], bo.dev[k], bo.jobs[k], bo.jo[k], bo.host + bo.base[k]);
     {
       std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
       if (p_.deterministic == 0 && p_.tree_lock != 0) lock.lock();
@@ -432,42 +485,82 @@ class Search {
     }
     expansions_ += L;
   }
-  dsp_status expand_gpu(const std::vector<Node*>& leaves, cudaStream_t st, Pinned& pinned, BatchOut& bo) {
-    int L = (int)leaves.size();
+  // The GPU part of a batch: the leaves are routed over the models (the
+  // expansion with global index e goes to model e mod G, dsp_route_leaves);
+  // each model expands its leaves in one dsp_expand_leaves call on its own
+  // stream (or through the device queue), and every model's small results
+  // come back into one pinned host buffer.
+  dsp_status expand_gpu(const std::vector<Node*>& leaves, Streams& st, Pinned& pinned, BatchOut& bo) {
+    const int L = (int)leaves.size(), G = (int)models_.size();
     std::vector<dsp_leaf_job>& jobs = bo.jobs;
     std::vector<JobOut>& jo = bo.jo;
     std::vector<size_t>& base = bo.base;
     jobs.resize(L);
     jo.resize(L);
     base.resize(L);
-    size_t total = 0;
+    bo.dev.resize(L);
+    std::vector<int32_t> pdev(L), copy(L);
+    for (int k = 0; k < L; ++k) pdev[k] = leaves[k]->parent != nullptr ? leaves[k]->parent->dev : leaves[k]->dev;
+    const long long e0 = routed_.fetch_add(L);
+    dsp_status s = dsp_route_leaves(L, e0, G, pdev.data(), bo.dev.data(), copy.data());
+    if (s != DSP_OK) return s;
+    std::vector<size_t> dev_total(G, 0), local(L), host_off(G, 0);
     for (int k = 0; k < L; ++k) {
       jo[k].layout(na_, dsp_max_children(m_, leaves[k]->n));
-      base[k] = total;
-      total += jo[k].bytes;
+      local[k] = dev_total[bo.dev[k]];
+      dev_total[bo.dev[k]] += jo[k].bytes;
     }
-    void* dsmall = nullptr;
-    cudaError_t e = arena_.alloc(total, &dsmall);
-    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: results");
+    size_t total = 0;
+    for (int g = 0; g < G; ++g) {
+      host_off[g] = total;
+      total += dev_total[g];
+    }
+    std::vector<char*> dsmall(G, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int g = 0; g < G; ++g) {
+      if (dev_total[g] == 0) continue;
+      void* p = nullptr;
+      e = arenas_[g]->alloc(dev_total[g], &p);
+      if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: results");
+      dsmall[g] = (char*)p;
+    }
     for (int k = 0; k < L; ++k) {
-      dsp_status s = prepare(leaves[k], jobs[k], jo[k], (char*)dsmall + base[k]);
+      const int g = bo.dev[k];
+      base[k] = host_off[g] + local[k];
+      e = cudaSetDevice(models_[g]->device);
+      if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: device");
+      s = prepare(leaves[k], g, copy[k] != 0, jobs[k], jo[k], dsmall[g] + local[k], st.st[g]);
       if (s != DSP_OK) return s;
     }
-    dsp_status s = DSP_OK;
     if (queue_ != nullptr) {
-      // through the device job queue: publish, wait (bounded), then copy
+      // through the device job queue (one model): publish, wait (bounded), then copy
       std::vector<uint64_t> tickets(L);
       for (int k = 0; k < L && s == DSP_OK; ++k) s = dsp_queue_submit(queue_, &jobs[k], 10000000000ull, &tickets[k]);
       for (int k = 0; k < L && s == DSP_OK; ++k) s = dsp_queue_wait(queue_, tickets[k], 60000000000ull);
+    } else if (G == 1) {
+      s = dsp_expand_leaves(m_, jobs.data(), L, st.st[0]);
     } else {
-      s = dsp_expand_leaves(m_, jobs.data(), L, st);
+      std::vector<dsp_leaf_job> mine;
+      for (int g = 0; g < G && s == DSP_OK; ++g) {
+        mine.clear();
+        for (int k = 0; k < L; ++k)
+          if (bo.dev[k] == g) mine.push_back(jobs[k]);
+        if (mine.empty()) continue;
+        e = cudaSetDevice(models_[g]->device);
+        if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: device");
+        s = dsp_expand_leaves(models_[g], mine.data(), (int)mine.size(), st.st[g]);
+      }
     }
     if (s != DSP_OK) return s;
     e = pinned.reserve(total);
     if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: pinned results");
     char* host = pinned.p;
-    e = cudaMemcpyAsync(host, dsmall, total, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int g = 0; g < G && e == cudaSuccess; ++g)
+      if (dev_total[g] > 0) e = cudaMemcpyAsync(host + host_off[g], dsmall[g], dev_total[g], cudaMemcpyDeviceToHost,
+                                                st.st[g]);
+    for (int g = 0; g < G && e == cudaSuccess; ++g)
+      if (dev_total[g] > 0) e = cudaStreamSynchronize(st.st[g]);
+    if (e == cudaSuccess && G > 1) e = cudaSetDevice(m_->device);
     if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: results copy");
     bo.host = host;
     return DSP_OK;
@@ -476,14 +569,16 @@ class Search {
   dsp_status run_rounds();
   dsp_status run_threads();
 
+  std::vector<dsp_model*> models_;
   dsp_model* m_;
   dsp_search_params p_;
   int na_, D_, words_, kind_, per_;
   double K_, gamma_;
-  Arena arena_;
+  std::vector<std::unique_ptr<Arena>> arenas_;  // per model: the tree's device memory on its GPU
   std::vector<std::unique_ptr<Node>> pool_;
   Node* root_ = nullptr;
-  uint16_t* d_ident_ = nullptr;
+  std::vector<uint16_t*> ident_;                // per model: positions 0..n-1 of the root's scenarios
+  std::atomic<long long> routed_{0};            // expansions routed so far
   std::mutex tree_mu_;   // free running with tree_lock: selection and backup
   std::mutex pool_mu_;   // the node pool (children are made outside the tree lock)
   std::atomic<long long> published_{0};  // leaves made visible
@@ -495,8 +590,8 @@ class Search {
 };
 
 dsp_status Search::run_rounds() {
-  cudaStream_t st;
-  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  Streams st;
+  cudaError_t e = st.make(models_);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: stream");
   Pinned staging;
   dsp_status s = DSP_OK;
@@ -517,7 +612,6 @@ dsp_status Search::run_rounds() {
     if (root_->expanded.load() && ld(root_->U) - ld(root_->L) <= p_.target_gap) break;
     if (leaves.empty()) break;
   }
-  cudaStreamDestroy(st);
   return s;
 }
 
@@ -540,7 +634,7 @@ dsp_status Search::run_threads() {
   const bool batched = p_.batch > 1 && queue_ == nullptr;
   std::mutex pend_mu, disp_mu;
   std::vector<Trial> pending;
-  auto dispatch = [&](cudaStream_t stream, Pinned& staging, int tid) {
+  auto dispatch = [&](Streams& stream, Pinned& staging, int tid) {
     while (true) {
       if (!disp_mu.try_lock()) return;  // the dispatcher will look again after it lets go
       std::vector<Trial> take;
@@ -581,8 +675,8 @@ dsp_status Search::run_threads() {
   };
   auto worker = [&](int tid) {
     cudaSetDevice(m_->device);
-    cudaStream_t stream;
-    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+    Streams stream;
+    if (stream.make(models_) != cudaSuccess) {
       status[tid] = fail(DSP_E_CUDA, "dsp_plan: stream");
       stop = true;
       return;
@@ -654,7 +748,6 @@ dsp_status Search::run_threads() {
       if (!t.leaf && !stop.load()) std::this_thread::yield();
     }
     if (batched) dispatch(stream, staging, tid);  // what is still pending
-    cudaStreamDestroy(stream);
   };
   std::vector<std::thread> th;
   for (int i = 0; i < p_.threads; ++i) th.emplace_back(worker, i);
@@ -673,23 +766,34 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   root_->W = (double)n / K_;
   if (hist) std::memcpy(root_->hist, hist, 32);
   void* p = nullptr;
-  cudaError_t e = arena_.alloc((size_t)words_ * n * 4, &p);
+  cudaError_t e = arenas_[0]->alloc((size_t)words_ * n * 4, &p);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: root states");
   root_->d_states = (uint32_t*)p;
+  root_->dev = 0;
   e = cudaMemcpy(root_->d_states, root_host, (size_t)words_ * n * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: root upload");
-  e = arena_.alloc((size_t)n * 2, &p);
-  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: identity");
-  d_ident_ = (uint16_t*)p;
   std::vector<uint16_t> ident(n);
   for (int i = 0; i < n; ++i) ident[i] = (uint16_t)i;
-  e = cudaMemcpy(d_ident_, ident.data(), (size_t)n * 2, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: identity upload");
+  for (size_t g = 0; g < models_.size(); ++g) {
+    e = arenas_[g]->alloc((size_t)n * 2, &p);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: identity");
+    ident_[g] = (uint16_t*)p;
+    e = cudaMemcpy(ident_[g], ident.data(), (size_t)n * 2, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: identity upload");
+  }
+  e = cudaSetDevice(m_->device);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan: device");
   uint64_t steps0 = 0, steps1 = 0;
   uint32_t status = 0;
-  dsp_status s = dsp_read_counters(m_, &steps0, &status);
-  if (s != DSP_OK) return s;
-  if (!p_.deterministic && p_.use_queue) {
+  dsp_status s = DSP_OK;
+  for (dsp_model* m : models_) {
+    uint64_t x = 0;
+    uint32_t st = 0;
+    s = dsp_read_counters(m, &x, &st);
+    if (s != DSP_OK) return s;
+    steps0 += x;
+  }
+  if (!p_.deterministic && p_.use_queue && models_.size() == 1) {
     // the model keeps its queue (and the persistent kernel's graph) across
     // planning steps; every job carries the plan step it was submitted under
     const int want = std::max(64, 4 * p_.threads);
@@ -706,9 +810,16 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   }
   s = p_.deterministic ? run_rounds() : run_threads();
   queue_ = nullptr;
+  cudaSetDevice(m_->device);
   if (s != DSP_OK) return s;
-  s = dsp_read_counters(m_, &steps1, &status);
-  if (s != DSP_OK) return s;
+  for (dsp_model* m : models_) {
+    uint64_t x = 0;
+    uint32_t st = 0;
+    s = dsp_read_counters(m, &x, &st);
+    if (s != DSP_OK) return s;
+    steps1 += x;
+    status |= st;
+  }
   if (status != 0) return fail(DSP_E_DEVICE, "dsp_plan: device status word %u", status);
   out->root_u = ld(root_->U);
   out->root_l = ld(root_->L);
@@ -793,7 +904,47 @@ extern "C" dsp_status dsp_plan(dsp_model* m, const uint32_t* root_states, int32_
   if (p->threads < 1 || p->threads > 256) return fail(DSP_E_INVALID, "dsp_plan: threads %d", p->threads);
   if (p->rounds < 1) return fail(DSP_E_INVALID, "dsp_plan: rounds %d", p->rounds);
   std::memset(out, 0, sizeof(*out));
-  Search s(m, *p);
+  Search s({m}, *p);
+  return s.run(root_states, n, hist, out, root_visits);
+}
+
+extern "C" dsp_status dsp_route_leaves(int32_t n_leaves, int64_t first_expansion, int32_t n_models,
+                                       const int32_t* parent_model, int32_t* target, int32_t* copy) {
+  using namespace dsp;
+  if (n_leaves < 0 || n_models < 1 || first_expansion < 0 || (n_leaves > 0 && (!parent_model || !target || !copy)))
+    return fail(DSP_E_INVALID, "dsp_route_leaves: bad argument");
+  for (int32_t k = 0; k < n_leaves; ++k) {
+    if (parent_model[k] < 0 || parent_model[k] >= n_models)
+      return fail(DSP_E_INVALID, "dsp_route_leaves: leaf %d: parent model %d of %d", k, parent_model[k], n_models);
+    target[k] = (int32_t)((first_expansion + k) % n_models);
+    copy[k] = target[k] != parent_model[k] ? 1 : 0;
+  }
+  return DSP_OK;
+}
+
+extern "C" dsp_status dsp_plan_multi(dsp_model* const* models, int32_t n_models, const uint32_t* root_states,
+                                     int32_t n, const int8_t* hist, const dsp_search_params* p,
+                                     dsp_search_result* out, int32_t* root_visits) {
+  using namespace dsp;
+  if (!models || n_models < 1 || n_models > 64) return fail(DSP_E_INVALID, "dsp_plan_multi: %d models", n_models);
+  for (int32_t g = 0; g < n_models; ++g)
+    if (!models[g]) return fail(DSP_E_INVALID, "dsp_plan_multi: model %d is NULL", g);
+  if (!root_states || !p || !out) return fail(DSP_E_INVALID, "dsp_plan_multi: NULL argument");
+  for (int32_t g = 1; g < n_models; ++g)
+    if (std::memcmp(models[g]->host, models[0]->host, sizeof(DevModel)) != 0 ||
+        models[g]->plan_step != models[0]->plan_step || models[g]->policy_on != models[0]->policy_on)
+      return fail(DSP_E_INVALID, "dsp_plan_multi: model %d differs from model 0 (description, plan step or policy)",
+                  g);
+  if (n_models > 1 && p->use_queue && !p->deterministic)
+    return fail(DSP_E_UNSUPPORTED, "dsp_plan_multi: the device queue serves one model");
+  if (n < 1 || n > max_root_scenarios(models[0], p) || n > models[0]->host->K)
+    return fail(DSP_E_INVALID, "dsp_plan_multi: %d root scenarios", n);
+  if (p->threads < 1 || p->threads > 256) return fail(DSP_E_INVALID, "dsp_plan_multi: threads %d", p->threads);
+  if (p->rounds < 1) return fail(DSP_E_INVALID, "dsp_plan_multi: rounds %d", p->rounds);
+  std::memset(out, 0, sizeof(*out));
+  cudaError_t e = cudaSetDevice(models[0]->device);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_plan_multi: device");
+  Search s(std::vector<dsp_model*>(models, models + n_models), *p);
   return s.run(root_states, n, hist, out, root_visits);
 }
 
@@ -810,7 +961,7 @@ extern "C" dsp_status dsp_plan_nodes(dsp_model* m, const uint32_t* root_states, 
   if (p->threads < 1 || p->threads > 256) return fail(DSP_E_INVALID, "dsp_plan_nodes: threads %d", p->threads);
   if (p->rounds < 1) return fail(DSP_E_INVALID, "dsp_plan_nodes: rounds %d", p->rounds);
   std::memset(out, 0, sizeof(*out));
-  Search s(m, *p);
+  Search s({m}, *p);
   dsp_status st = s.run(root_states, n, hist, out, root_visits);
   if (st != DSP_OK) return st;
   return s.export_nodes(min_scen, cap, nodes, states, count);
