@@ -94,7 +94,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plan", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
-    p.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
+    p.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
+    p.add_argument("--plan-worlds", type=int, default=16,
+                   help="rs15_15: planner episodes on this many seeded worlds (100 steps, 4 threads, 200 trials each)")
     p.add_argument("--no-companions", action="store_true",
                    help="measure only --workload (a default rs15_15 run also measures car50 under its own key)")
     p.add_argument("--episodes", type=int, default=0,
@@ -436,6 +438,27 @@ def measure(args, name, rank, world, dist, local, headline=True):
     torch.cuda.synchronize()
     kernels_per_step = 1 if cfg.kind == inputs.CAR else 2
 
+    # the launch shape the timed region runs: the autotuner's choice on this
+    # job batch (kept per model, K, |A| and GPU; the default shape is timed
+    # beside it afterwards)
+    autotuned = None
+    if not args.no_autotune:
+        from paper_1802_06215_b300 import autotune as AT
+        cache = os.environ.get("DSP_TUNE_CACHE") or None
+        best = AT.autotune(m, jb, torch.cuda.get_device_name(), cache, reps=3)
+        autotuned = {"shape": {k: best[k] for k in _dsp.SHAPE_FIELDS}, "cached": best["cached"],
+                     "tuning_ms_per_call": best.get("ms"), "default_tuning_ms_per_call": best.get("default_ms"),
+                     "candidates_timed": best.get("tried"), "jobs": njobs,
+                     "search_space": {
+                         inputs.CAR: "tps {4,8,16,32} x ctas_car {fit,3,2}",
+                         inputs.NAV: "ctas_b {fit,6,4,2}"}.get(
+                             cfg.kind, "block_b {128,256,512} x ctas_b {fit,6,4} x warps_a {default,5,10} "
+                                       "(two robots {default,8,16})"),
+                     "note": "0 = the field's default; the timed region runs this shape"}
+        for _ in range(2):
+            jb.run()
+        torch.cuda.synchronize()
+
     # device-resident timing (L2 flushed before every step, outside the events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     m.reset_counters()
@@ -458,6 +481,22 @@ def measure(args, name, rank, world, dist, local, headline=True):
     t_ms, steps_all = combine_ranks(sum(times), steps_total, dist, "cuda")
     value = steps_all / (t_ms / 1000.0)
     steps_per_launch = steps_total / args.steps
+    if autotuned is not None:
+        # the default shape on the same jobs, for comparison (not the headline)
+        tuned_shape = _dsp.dsp_get_launch_shape(m.h)
+        _dsp.dsp_set_launch_shape(m.h)
+        nd = max(20, args.steps // 4)
+        jb.run()
+        d_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nd)]
+        for k in range(nd):
+            flush.zero_()
+            d_ev[k][0].record(stream)
+            jb.run()
+            d_ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        _dsp.dsp_set_launch_shape(m.h, **tuned_shape)
+        autotuned["default_shape_ms_per_step"] = sum(a.elapsed_time(b) for a, b in d_ev) / nd
+        autotuned["tuned_shape_ms_per_step"] = t_ms / args.steps
 
     # end to end through the public call: every step copies its inputs in from
     # pinned host memory and every result out, inside the timed region. Two
@@ -515,17 +554,18 @@ def measure(args, name, rank, world, dist, local, headline=True):
         planning_queue = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
         planning_queue["first_step_with_queue_creation"] = {k: first[k] for k in ("expansions", "seconds",
                                                                                    "expansions_per_s")}
-    # the autotuner's choice of launch shape on the first 512 jobs (after the
-    # timed region, which ran the default shape; the default is kept after)
-    autotuned = None
-    if not args.no_autotune:
-        from paper_1802_06215_b300 import autotune as AT
-        sub = batch.JobBatch(m, jobs[:512])
-        default = _dsp.dsp_get_tuning(m.h)
-        best = AT.dsp_autotune(m.h, sub.descs, len(sub.jobs), reps=3)
-        autotuned = {"jobs": len(sub.jobs), "block": best["block"], "tps": best["tps"], "ms": best["ms"],
-                     "default": list(default)}
-        _dsp.dsp_set_tuning(m.h, *default)
+    # the planning workload of the 15x15 task as stated: 16 seeded worlds, up
+    # to 100 planning steps each (the episode ends when the robot exits), 4
+    # search threads, each step 50 rounds of 4 trials (no time limit), the
+    # belief updated by Bayes' rule after every real step
+    planning_episodes = None
+    if not args.no_plan and name == "rs15_15" and args.plan_worlds > 0:
+        from paper_1802_06215_b300 import learn
+        t0 = time.perf_counter()
+        planning_episodes = learn.run_episodes(cfg, range(9000, 9000 + args.plan_worlds), 100, 0.0, threads=4,
+                                               rounds=50)
+        planning_episodes.update({"steps_per_world_max": 100, "threads": 4, "trials_per_step": 200,
+                                  "wall_seconds": time.perf_counter() - t0, "world_seeds": "9000.."})
     learned = None
     if not args.no_learned and name in ("rs15_15", "car50"):
         learned = learned_step(_dsp, batch, m, cfg, jobs, plan[1])
@@ -575,6 +615,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
         "cpu_baseline": cpu,
         "planning": planning,
         "planning_queue": planning_queue,
+        "planning_episodes": planning_episodes,
         "autotune": autotuned,
         "learned_pi0": learned,
         "clocks": clocks,

@@ -95,12 +95,15 @@ def start_word(cfg):
     return np.uint32(0 | ((cfg.n // 2) << 8))
 
 
-def search_params(seconds, threads=4, xi=0.95, target_gap=0.0):
-    return _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=seconds, c_a=1.0, c_o=0.5,
+def search_params(seconds, threads=4, xi=0.95, target_gap=0.0, rounds=10 ** 7):
+    """Free-running search: `threads` x `rounds` trials at most, `seconds` of
+    planning (0 = no time limit)."""
+    return _dsp.dsp_search_params(threads=threads, rounds=rounds, time_limit_s=seconds, c_a=1.0, c_o=0.5,
                                   xi=xi, target_gap=target_gap, deterministic=0, use_queue=0)
 
 
-def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node_cap=1 << 15, harvest=True):
+def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node_cap=1 << 15, harvest=True,
+            rounds=10 ** 7):
     """One planner episode. Returns the discounted return, the visited roots
     (state block, counters) and, when harvesting, the exported nodes."""
     rng = np.random.default_rng([world_seed, 0xBE11EF])
@@ -109,13 +112,13 @@ def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node
     belief = Belief(cfg, world[0, 0])
     ret, disc = 0.0, 1.0
     roots, states, hists, labels, decisions, gaps = [], [], [], [], 0, []
-    t_plan = 0.0
+    t_plan, expansions, scen_steps = 0.0, 0, 0
     for t in range(steps):
         K = cfg.K
         root = belief.scenarios(rng, K)
         roots.append((root, belief.hist.copy()))
         model.set_plan_step((world_seed * 1000 + t) & 0x7FFFFFFF)
-        p = search_params(seconds, threads)
+        p = search_params(seconds, threads, rounds=rounds)
         if harvest:
             res, rec, st = _dsp.dsp_plan_nodes(model.h, root, belief.hist, p, model.num_actions, min_scen,
                                                node_cap, model.words)
@@ -126,6 +129,8 @@ def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node
         else:
             res = _dsp.dsp_plan(model.h, root, belief.hist, p, model.num_actions)
         t_plan += res["seconds"]
+        expansions += res["expansions"]
+        scen_steps += res["scenario_steps"]
         gaps.append(res["root_u"] - res["root_l"])
         decisions += 1
         a = int(res["action"])
@@ -137,7 +142,8 @@ def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node
         world = nxt
         if (int(key[0]) >> 62) & 1 or (int(nxt[0, 0]) >> 16) & 1:
             break
-    out = {"return": ret, "roots": roots, "decisions": decisions, "plan_seconds": t_plan, "gaps": gaps}
+    out = {"return": ret, "roots": roots, "decisions": decisions, "plan_seconds": t_plan, "gaps": gaps,
+           "expansions": expansions, "scenario_steps": scen_steps}
     if harvest and states:
         out["states"] = np.concatenate(states, axis=1)
         out["hist"] = np.concatenate(hists, axis=0)
@@ -469,23 +475,29 @@ def policy_iteration(cfg, iterations=4, n_random=60000, n_onpolicy=4000, Kq=64, 
     return policy, hist_log
 
 
-def run_episodes(cfg, world_seeds, steps, seconds, policy=None, threads=4):
+def run_episodes(cfg, world_seeds, steps, seconds, policy=None, threads=4, rounds=10 ** 7):
     """Planner episodes on the given worlds (Sec. IV-A task, belief updated by
     Bayes' rule after every real step): mean discounted return, decisions per
     second of planning time and mean root gap at decision time; `policy` (a
-    dsp_mlp handle) replaces the heuristic default policy in the rollouts."""
+    dsp_mlp handle) replaces the heuristic default policy in the rollouts.
+    Each decision plans for `seconds` (0 = no limit) and at most `threads` x
+    `rounds` trials."""
     model = batch.Model(cfg)
     _dsp.dsp_set_policy(model.h, policy)
-    rets, dec, secs, gaps = [], 0, 0.0, []
+    rets, dec, secs, gaps, exps, ssteps = [], 0, 0.0, [], 0, 0
     for s in world_seeds:
-        ep = episode(model, cfg, s, steps, seconds, threads, harvest=False)
+        ep = episode(model, cfg, s, steps, seconds, threads, harvest=False, rounds=rounds)
         rets.append(ep["return"])
         dec += ep["decisions"]
         secs += ep["plan_seconds"]
         gaps += ep["gaps"]
+        exps += ep["expansions"]
+        ssteps += ep["scenario_steps"]
     model.close()
     return {"worlds": len(rets), "mean_return": float(np.mean(rets)), "min_return": float(np.min(rets)),
-            "decisions": dec, "decisions_per_s": dec / max(secs, 1e-9), "mean_root_gap": float(np.mean(gaps))}
+            "decisions": dec, "plan_seconds": secs, "decisions_per_s": dec / max(secs, 1e-9),
+            "mean_root_gap": float(np.mean(gaps)), "expansions": exps,
+            "expansions_per_s": exps / max(secs, 1e-9), "scenario_steps_per_s": ssteps / max(secs, 1e-9)}
 
 
 # ---------------------------------------------------------------- the car ----
