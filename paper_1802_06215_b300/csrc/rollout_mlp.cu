@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 
 #include "kernels.cuh"
 #include "mlp.cuh"
@@ -27,38 +28,25 @@ namespace {
 using namespace tc;
 
 
-constexpr int kDxy = 63;          // rock offsets -31..31 (map side <= 32)
-
-struct TcSmem {
-  Weights W;
-  uint8_t x[kRows * kMlpIn * 2];      // A of layer 1: M = 128, K = 64 (features)
-  uint32_t fdxy[kDxy * kDxy];          // BF16 pair ((float)dx / n, (float)dy / n), dx, dy in -31..31
-  uint32_t fcs[14];                    // BF16 pair (clamp(c) / 3, sampled), c in -3..3
-  RSShared c;
-  unsigned long long mbar;            // completion of each layer's MMAs
-  uint32_t tmem_base;
+// Per-CTA tables of the feature pairs that depend on one rock. The offset
+// pair ((float)dx / n, (float)dy / n) for dx, dy in -(n-1) .. n-1 is one BF16
+// pair per entry, (2n-1)^2 entries of 4 bytes; where that table does not fit
+// in shared memory (n = 32) the pair is computed from a 2n-1 entry table of
+// single BF16 values. The counter/sampled pair is fcs[(c + 3) * 2 + sampled].
+struct FeatTables {
+  const uint32_t* pair;   // (2n-1)^2 pairs, or null
+  const uint16_t* one;    // 2n-1 single values (dx + n - 1)
+  const uint32_t* fcs;
+  int n;
 };
-
-// The BF16 feature pairs that depend on one rock, tabulated per CTA with the
-// arithmetic of rs_features: fdxy[(dx + 31) * 63 + dy + 31] for the offset
-// pair and fcs[(c + 3) * 2 + sampled] for the counter/sampled pair.
-__device__ __forceinline__ void build_feature_tables(uint32_t* fdxy, uint32_t* fcs, int n) {
-  const float inv_n = 1.0f / (float)n;
-  const float third = 1.0f / 3.0f;
-  for (int i = threadIdx.x; i < kDxy * kDxy; i += blockDim.x) {
-    const int dx = i / kDxy - 31, dy = i % kDxy - 31;
-    fdxy[i] = pack_bf16((float)dx * inv_n, (float)dy * inv_n);
-  }
-  for (int i = threadIdx.x; i < 14; i += blockDim.x) fcs[i] = pack_bf16((float)(i / 2 - 3) * third, (i & 1) ? 1.0f : 0.0f);
-}
 
 // The row's features (the feature map of rs_features, same arithmetic) as
 // BF16 pairs straight into the layer-1 A tile: pair 0 = (x/n, y/n), pairs
 // 1 + 2r = ((rock x - x)/n, (rock y - y)/n), 2 + 2r = (clamp(c_r)/3, sampled_r),
 // zero beyond 1 + 2m. Fully unrolled, so nothing goes through local memory.
-__device__ __forceinline__ void write_features(uint8_t* xs, int row, int n, int m, const int* rock_xy, uint32_t pos,
-                                               uint32_t sampled, const uint32_t (&h)[8], const uint32_t* fdxy,
-                                               const uint32_t* fcs) {
+__device__ __forceinline__ void write_features(uint8_t* xs, int row, int m, const int* rock_xy, uint32_t pos,
+                                               uint32_t sampled, const uint32_t (&h)[8], const FeatTables& T) {
+  const int n = T.n, w = 2 * n - 1;
   const float inv_n = 1.0f / (float)n;
   const int x = (int)(pos & 0xFFu), y = (int)((pos >> 8) & 0xFFu);
   uint32_t pr[kMlpIn / 2];
@@ -69,8 +57,10 @@ __device__ __forceinline__ void write_features(uint8_t* xs, int row, int n, int 
       const int rxy = rock_xy[r];
       int c = (int)(int8_t)((h[r >> 2] >> (8 * (r & 3))) & 0xFFu);
       c = c > 3 ? 3 : (c < -3 ? -3 : c);
-      pr[1 + 2 * r] = fdxy[((rxy & 0xFF) - x + 31) * kDxy + ((rxy >> 8) - y + 31)];
-      pr[2 + 2 * r] = fcs[(c + 3) * 2 + (int)((sampled >> r) & 1u)];
+      const int dx = (rxy & 0xFF) - x + n - 1, dy = (rxy >> 8) - y + n - 1;
+      pr[1 + 2 * r] = T.pair != nullptr ? T.pair[dx * w + dy]
+                                        : ((uint32_t)T.one[dx] | ((uint32_t)T.one[dy] << 16));
+      pr[2 + 2 * r] = T.fcs[(c + 3) * 2 + (int)((sampled >> r) & 1u)];
     } else {
       pr[1 + 2 * r] = 0u;
       pr[2 + 2 * r] = 0u;
@@ -120,35 +110,86 @@ struct ItemSource {
   unsigned int* next;  // item counter
 };
 
-// A CTA keeps 128 live scenarios (rows, one per thread) and advances them one
-// step at a time: each row writes its features (BF16) into the layer-1 A tile
-// in shared memory, one elected thread issues the three layers as tcgen05.mma
-// (M = 128, BF16 in, FP32 accumulators in tensor memory, weights resident in
-// shared memory as the B operands, the hidden activations fed back through
-// tensor memory as the A operand), and after each layer's completion every
-// thread reads its own row from tensor memory: bias + ReLU + BF16 for the
-// hidden layers, then the masked argmax of its logits. A row whose scenario
-// ends adds its value to its child and takes the next item at once.
+// Shared memory of the learned rollout: the policy (B operands), one layer-1
+// A tile per row tile, the model's constants and the feature tables (the
+// pair table last, sized (2n-1)^2 at launch when it fits).
+struct TcSmem {
+  Weights W;
+  uint8_t x[2][kRows * kMlpIn * 2];   // A of layer 1 per tile: M = 128, K = 64 (features)
+  RSShared c;
+  uint32_t fcs[14];                   // BF16 pair (clamp(c) / 3, sampled), c in -3..3
+  uint16_t one[2 * kMaxSide];         // BF16 of (float)d / n, d in -(n-1)..n-1
+  unsigned long long mbar[2];         // completion of each tile's MMAs
+  uint32_t tmem_base;
+  uint32_t pair[1];                   // (2n-1)^2 offset pairs when they fit (dynamic)
+};
+constexpr size_t kTcSmemMax = 227 * 1024;
+
+__host__ __device__ constexpr size_t tc_pair_bytes(int n) { return (size_t)(2 * n - 1) * (2 * n - 1) * 4; }
+__host__ __device__ constexpr bool tc_pair_fits(int n) { return offsetof(TcSmem, pair) + tc_pair_bytes(n) <= kTcSmemMax; }
+
+// The learned policy's rollouts, one-robot Rock Sample. A CTA holds two
+// tiles of 128 live scenarios (rows), one per warpgroup, each thread owning
+// one row. Per step, each tile independently: its rows write their features
+// (BF16) into the tile's layer-1 A operand in shared memory; the tile's
+// first thread issues layer 1, both halves of layer 2 and layer 3 as
+// tcgen05.mma (M = 128, BF16 in, FP32 accumulators in the tile's 256
+// tensor-memory columns, weights resident in shared memory as the B
+// operands, hidden activations fed back through tensor memory as the A
+// operand), each committed to the tile's mbarrier; after each completion
+// every thread reads its own row: bias + ReLU + BF16 for the hidden layers,
+// then the masked argmax of its logits and g. While one tile is in its
+// epilogues or its scalar step, the tensor pipe runs the other tile's
+// layers. A row whose scenario ends adds its value to its child and takes
+// the next item at once, so the tiles stay full until the item list runs out.
 template <bool kExpand>
 __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                                     const uint8_t* __restrict__ policy,
                                                                     ItemSource src, uint32_t plan_step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5, half = tid >> 7;
-  const bool owner = half == 0;  // the thread that holds the row's scenario
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tile = tid >> 7, row = tid & 127, bar = 1 + tile;
   load_rs_consts(S.c, gm);
   load_weights(S.W, policy);
-  build_feature_tables(S.fdxy, S.fcs, gm->n);
-  const uint32_t mbar = smem_u32(&S.mbar);
-  setup(mbar, smem_u32(&S.tmem_base));
+  const int n = gm->n;
+  const bool pairs = tc_pair_fits(n);
+  {
+    const float inv_n = 1.0f / (float)n;
+    const float third = 1.0f / 3.0f;
+    const int w = 2 * n - 1;
+    if (pairs)
+      for (int i = tid; i < w * w; i += blockDim.x) {
+        const int dx = i / w - (n - 1), dy = i % w - (n - 1);
+        S.pair[i] = pack_bf16((float)dx * inv_n, (float)dy * inv_n);
+      }
+    for (int i = tid; i < w; i += blockDim.x) {
+      const __nv_bfloat16 b = __float2bfloat16_rn((float)(i - (n - 1)) * inv_n);
+      S.one[i] = *reinterpret_cast<const uint16_t*>(&b);
+    }
+    for (int i = tid; i < 14; i += blockDim.x) S.fcs[i] = pack_bf16((float)(i / 2 - 3) * third, (i & 1) ? 1.0f : 0.0f);
+  }
+  if (tid == 0) {
+    for (int g = 0; g < 2; ++g)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[g])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
   fence_async_smem();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const uint32_t tmem = S.tmem_base;
-  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
-  const uint32_t sx = smem_u32(S.x);
+  const FeatTables T{pairs ? S.pair : nullptr, S.one, S.fcs, n};
+  const uint32_t tbase = S.tmem_base + (uint32_t)tile * kTileCols;          // the tile's columns
+  const uint32_t trow = tbase + ((uint32_t)(32 * (warp & 3)) << 16);       // this warp's lanes
+  const uint32_t sx = smem_u32(S.x[tile]);
+  const uint32_t mbar = smem_u32(&S.mbar[tile]);
+  const bool issuer = row == 0;
 
   const RSModel<1> M = make_rs<1>(gm, &S.c, plan_step);
   const int na = gm->num_actions;
@@ -199,15 +240,21 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
       pst = 3;
     }
   };
-  if (owner) {
-    advance();
-    advance();
-    advance();
-  }
+  advance();
+  advance();
+  advance();
+  // one step of the network: waits (bounded) for the tile's MMAs, agreed by
+  // the tile's threads
+  auto wait_layer = [&]() -> bool {
+    const bool ok = tile_and(bar, mbar_wait(mbar, phase));
+    phase ^= 1u;
+    fence_after_sync();
+    return ok;
+  };
   while (true) {
-    // rows whose scenario ended take the fetched item (an item that needs no
-    // rollout is settled at once and the row waits for the next fetch)
-    while (owner && !alive && pst == 3) {
+    // a row whose scenario ended takes the fetched item (an item that needs
+    // no rollout is settled at once and the row waits for the next fetch)
+    while (!alive && pst == 3) {
       const long long it = pit;
       pst = 0;
       item = it;
@@ -248,35 +295,73 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
         }
       }
     }
-    // features of the row's state and counters, BF16 into the A tile
-    if (owner) {
-      if (alive) {
-        write_features(S.x, tid, M.n, M.m, S.c.rock_xy, s.pos[0], s.sampled, h, S.fdxy, S.fcs);
-      } else {
+    // features of the row's state and counters, BF16 into the tile's A operand
+    if (alive) {
+      write_features(S.x[tile], row, M.m, S.c.rock_xy, s.pos[0], s.sampled, h, T);
+    } else {
 #pragma unroll
-        for (int c = 0; c < kMlpIn / 8; ++c)
-          *reinterpret_cast<uint4*>(S.x + kmajor_off(tid, 8 * c, kMlpIn)) = make_uint4(0u, 0u, 0u, 0u);
-      }
+      for (int c = 0; c < kMlpIn / 8; ++c)
+        *reinterpret_cast<uint4*>(S.x[tile] + kmajor_off(row, 8 * c, kMlpIn)) = make_uint4(0u, 0u, 0u, 0u);
     }
     fence_async_smem();
-    if (!__syncthreads_or((alive || (owner && pst != 4)) ? 1 : 0)) break;
-    // the network; while layer 1 runs: the row's allowed actions, the
-    // heuristic's action and the next fetch stage
-    const bool ok = run_layers(S.W, sx, tmem, trow, mbar, phase, half, [&]() {
-      if (owner) {
-        if (alive) {
-          allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << na);
-          heur = M.policy(s, pm);
-        }
-        advance();
-      }
-    });
-    if (!ok) {
+    if (!tile_or(bar, alive || pst != 4)) break;
+    // layer 1; meanwhile the row's allowed actions, the heuristic's action
+    // and the next fetch stage
+    if (issuer) issue_layer1(S.W, sx, tbase, mbar);
+    if (alive) {
+      allow = learned_allow(S.c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << na);
+      heur = M.policy(s, pm);
+    }
+    advance();
+    if (!wait_layer()) {
+      failed = true;
+      break;
+    }
+    epilogue1_inplace(trow, S.W.b1);
+    fence_before_sync();
+    tile_sync(bar);
+    // layer 2, first half; its BF16 outputs wait in registers
+    if (issuer) issue_layer2_half(S.W, tbase, tbase + 128, 0, mbar);
+    if (!wait_layer()) {
+      failed = true;
+      break;
+    }
+    uint32_t h2a[64];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float acc[32];
+      tmem_ld32(trow + 128 + 32 * c, acc);
+      relu_pack32(acc, S.W.b2 + 32 * c, h2a + 16 * c);
+    }
+    fence_before_sync();
+    tile_sync(bar);
+    // layer 2, second half; then H2 replaces H1 in columns 0..127
+    if (issuer) issue_layer2_half(S.W, tbase, tbase + 128, 1, mbar);
+    if (!wait_layer()) {
+      failed = true;
+      break;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_st16p(trow + 16 * c, h2a + 16 * c);
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+      float acc[32];
+      uint32_t packed[16];
+      tmem_ld32(trow + 128 + 32 * c, acc);
+      relu_pack32(acc, S.W.b2 + 128 + 32 * c, packed);
+      tmem_st16p(trow + 64 + 16 * c, packed);
+    }
+    tmem_wait_st();
+    fence_before_sync();
+    tile_sync(bar);
+    // layer 3: the logits
+    if (issuer) issue_layer3(S.W, tbase, tbase + 128, mbar);
+    if (!wait_layer()) {
       failed = true;
       break;
     }
     float lg[32];
-    if (owner) tmem_ld32(trow + kColL, lg);
+    tmem_ld32(trow + 128, lg);
     fence_before_sync();
     if (alive) {
       // argmax over the allowed actions and defer (column na), lowest index on ties
@@ -308,7 +393,18 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
       }
     }
   }
-  teardown(tmem, mbar, phase, failed, work);
+  // a tile whose layer timed out reports it and waits (bounded) for its MMAs
+  // in flight before the tensor memory is freed
+  if (failed && issuer) {
+    report(work, kStatusTimeout);
+    mbar_wait(mbar, phase ^ 1u);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(kTmemCols)
+                 : "memory");
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
@@ -342,11 +438,13 @@ __global__ void pack_policy(const float* master, uint8_t* pol) {
 template <bool kExpand>
 cudaError_t launch_mlp(const DevModel* gm, DevWork* work, const uint8_t* policy, const ItemSource& src,
                        uint32_t plan_step, int num_sms, long long total, cudaStream_t st) {
-  size_t smem = sizeof(TcSmem);
+  // the whole opt-in shared memory: the pair table's size depends on the map
+  // side, which the kernel reads from the model (one CTA per SM either way)
+  const size_t smem = kTcSmemMax;
   cudaError_t e = cudaFuncSetAttribute(rs_rollout_tc_kernel<kExpand>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  int grid = (int)std::max(1LL, std::min<long long>((total + kRows - 1) / kRows, (long long)num_sms));
+  int grid = (int)std::max(1LL, std::min<long long>((total + 2 * kRows - 1) / (2 * kRows), (long long)num_sms));
   rs_rollout_tc_kernel<kExpand><<<grid, kThreads, smem, st>>>(gm, work, policy, src, plan_step);
   return cudaGetLastError();
 }

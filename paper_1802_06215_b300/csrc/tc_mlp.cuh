@@ -324,5 +324,134 @@ __device__ __forceinline__ int masked_argmax(const float (&lg)[32], const float*
   return xi[0];
 }
 
+// ---------------------------------------------------------------------------
+// Two tiles per CTA. A CTA of 256 threads holds two 128-row tiles, one per
+// warpgroup (warps 0-3 tile 0, warps 4-7 tile 1; every thread owns one row
+// of its tile and reaches that row's TMEM lane), each with 256 of the 512
+// tensor-memory columns. While one tile runs its epilogues and its scalar
+// step (argmax, g, features), the tensor pipe works on the other's layers.
+// A tile's 256 columns (relative to its base):
+//  - layer 1: the FP32 accumulator in 0..255; its epilogue packs the BF16
+//    activations H1 in place into 0..127 (chunk c of 32 columns goes to
+//    16c.., columns already read);
+//  - layer 2 in two N = 128 halves, each accumulating in 128..255 with H1 in
+//    0..127 as the A operand; the first half's BF16 outputs wait in
+//    registers while the second half runs, then H2 fills 0..127 (H1 is dead);
+//  - layer 3: the logits in 128..159 with H2 as the A operand.
+constexpr uint32_t kTileCols = 256;
+
+// Named barrier of one tile's 128 threads (ids 1 and 2; 0 is __syncthreads).
+// The threads of a warp may reach it apart (after a bounded spin on an
+// mbarrier, or a branch taken by one thread), so the barriers are the
+// non-aligned forms, with the warp reconverged before and after (the
+// tensor-memory loads and stores that follow need the whole warp).
+__device__ __forceinline__ void tile_sync(int id) {
+  __syncwarp();
+  asm volatile("barrier.cta.sync %0, 128;" ::"r"(id) : "memory");
+  __syncwarp();
+}
+__device__ __forceinline__ bool tile_and(int id, bool p) {
+  uint32_t r;
+  __syncwarp();
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbarrier.cta.red.and.pred q, %2, 128, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(id)
+      : "memory");
+  __syncwarp();
+  return r != 0;
+}
+__device__ __forceinline__ bool tile_or(int id, bool p) {
+  uint32_t r;
+  __syncwarp();
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbarrier.cta.red.or.pred q, %2, 128, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(id)
+      : "memory");
+  __syncwarp();
+  return r != 0;
+}
+
+// 16 columns of 32-bit words from r[0..15] into the warp's 32 lanes.
+__device__ __forceinline__ void tmem_st16p(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::
+          "r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+// Two FP32 values rounded to a BF16 pair (lo in the low half) with negative
+// results clamped to zero, in one conversion: the same values as rounding
+// max(x, 0), up to the sign of a zero.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// ReLU(accumulator + bias) of 32 FP32 columns, rounded to 16 BF16 pairs.
+__device__ __forceinline__ void relu_pack32(const float (&acc)[32], const float* bias, uint32_t* out) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    out[j] = pack_bf16_relu(__fadd_rn(acc[2 * j], bias[2 * j]), __fadd_rn(acc[2 * j + 1], bias[2 * j + 1]));
+}
+
+// Layer 1 of a tile (issuing thread): D (256 FP32 columns at d) = X W1^T,
+// X the tile's features in shared memory at sx; commits to mbar.
+__device__ __forceinline__ void issue_layer1(const Weights& W, uint32_t sx, uint32_t d, uint32_t mbar) {
+  constexpr uint32_t kId = idesc_bf16(kRows, kMlpHid);
+  const uint32_t sw1 = smem_u32(W.w1);
+  fence_after_sync();
+#pragma unroll
+  for (int k = 0; k < kMlpIn / 16; ++k)
+    mma_ss(d, smem_desc(sx + 256 * k, 128, (kMlpIn / 8) * 128), smem_desc(sw1 + 256 * k, 128, (kMlpIn / 8) * 128),
+           kId, k > 0);
+  mma_commit(mbar);
+}
+
+// Half h of layer 2 (issuing thread): D (128 FP32 columns at d) = H1 (BF16
+// pairs in tensor memory at a) times rows 128h .. 128h + 127 of W2, transposed.
+__device__ __forceinline__ void issue_layer2_half(const Weights& W, uint32_t a, uint32_t d, int h, uint32_t mbar) {
+  constexpr uint32_t kId = idesc_bf16(kRows, 128);
+  const uint32_t sw2 = smem_u32(W.w2) + (uint32_t)h * (128 / 8) * (kMlpHid / 8) * 128;
+  fence_after_sync();
+#pragma unroll 4
+  for (int k = 0; k < kMlpHid / 16; ++k)
+    mma_ts(d, a + 8 * k, smem_desc(sw2 + 256 * k, 128, (kMlpHid / 8) * 128), kId, k > 0);
+  mma_commit(mbar);
+}
+
+// Layer 3 (issuing thread): logits (32 FP32 columns at d) = H2 (at a) W3^T.
+__device__ __forceinline__ void issue_layer3(const Weights& W, uint32_t a, uint32_t d, uint32_t mbar) {
+  constexpr uint32_t kId = idesc_bf16(kRows, kMlpOut);
+  const uint32_t sw3 = smem_u32(W.w3);
+  fence_after_sync();
+#pragma unroll 4
+  for (int k = 0; k < kMlpHid / 16; ++k)
+    mma_ts(d, a + 8 * k, smem_desc(sw3 + 256 * k, 128, (kMlpHid / 8) * 128), kId, k > 0);
+  mma_commit(mbar);
+}
+
+// Layer 1's epilogue for the thread's row (trow = the tile's base column on
+// the row's lane): H1 = BF16(ReLU(D + b1)) packed in place into columns
+// 0..127 (chunk c of 32 accumulator columns to 16c..16c+15, columns the
+// thread has already read).
+__device__ __forceinline__ void epilogue1_inplace(uint32_t trow, const float* b1) {
+#pragma unroll 1
+  for (int c = 0; c < kMlpHid / 32; ++c) {
+    float acc[32];
+    uint32_t packed[16];
+    tmem_ld32(trow + 32 * c, acc);
+    relu_pack32(acc, b1 + 32 * c, packed);
+    tmem_st16p(trow + 16 * c, packed);
+  }
+  tmem_wait_st();
+}
+
 }  // namespace tc
 }  // namespace dsp

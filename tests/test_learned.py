@@ -89,10 +89,12 @@ def check_replay(om, b, hist, d0, w, val, act, glog):
     return steps, float(err.max())
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_learned_rollout_replays_in_oracle(env, seed):
+@pytest.mark.parametrize("seed,side", [(1, 15), (2, 15), (3, 15), (4, 32), (5, 7)])
+def test_learned_rollout_replays_in_oracle(env, seed, side):
+    """Random networks on 300 states; the 32x32 map takes the kernel's
+    feature path without the pair table (it does not fit in shared memory)."""
     torch, _dsp, batch = env
-    cfg = I.rs15_15().with_(D=40)
+    cfg = I.rs15_15().with_(D=40) if side == 15 else I.grid_config(side, min(15, side), K=500, D=40, seed=side)
     m = batch.Model(cfg)
     w = weights(seed)
     hm = install(_dsp, m, w)
