@@ -195,6 +195,7 @@ void dsp_destroy_model(dsp_model* m) {
   if (m->dwork) cudaFree(m->dwork);
   if (m->policy) cudaFree(m->policy);
   for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : m->timing_pool) cudaEventDestroy(ev);
   for (dsp_staging_slot* sl : m->staging) {
     cudaEventSynchronize(sl->done);
     cudaEventDestroy(sl->done);
@@ -366,7 +367,7 @@ dsp_status dsp_kernel_timing(dsp_model* m, int32_t enable, double* total_ms, int
     tot += ms;
     n += 1;
   }
-  for (cudaEvent_t ev : m->timing_events) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : m->timing_events) m->timing_pool.push_back(ev);
   m->timing_events.clear();
   m->timing = enable != 0;
   if (total_ms) *total_ms = tot;
@@ -434,11 +435,13 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
       if (plan.total_items >= (1LL << 31)) return fail(DSP_E_UNSUPPORTED, "more than 2^31 (action, scenario) items");
     }
   } else {
+    // sorted on a contiguous (work, index) array: the order of a stable sort
+    // by decreasing work, without touching the job table again
+    std::vector<std::pair<long long, int>> key(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) key[j] = {-(long long)jobs[j].n_scen * jobs[j].n_actions, j};
+    std::sort(key.begin(), key.end());
     plan.order.resize(n_jobs);
-    for (int j = 0; j < n_jobs; ++j) plan.order[j] = j;
-    std::stable_sort(plan.order.begin(), plan.order.end(), [&](int x, int y) {
-      return (long long)jobs[x].n_scen * jobs[x].n_actions > (long long)jobs[y].n_scen * jobs[y].n_actions;
-    });
+    for (int j = 0; j < n_jobs; ++j) plan.order[j] = key[j].second;
   }
   return DSP_OK;
 }
@@ -483,6 +486,20 @@ static cudaError_t release_staging(dsp_model* m, dsp_staging_slot* sl, cudaStrea
   return e;
 }
 
+// Two timing events from the model's pool (created once, returned to the pool
+// when dsp_kernel_timing has read them).
+static void take_timing_events(dsp_model* m, cudaEvent_t (&ev)[2]) {
+  std::lock_guard<std::mutex> lock(m->timing_mu);
+  for (int k = 0; k < 2; ++k) {
+    if (!m->timing_pool.empty()) {
+      ev[k] = m->timing_pool.back();
+      m->timing_pool.pop_back();
+    } else {
+      cudaEventCreate(&ev[k]);
+    }
+  }
+}
+
 // Copies the job table (and the unit table, or Rock Sample's item offsets) to
 // stream-ordered device memory, takes the rollout-item list from the same
 // allocation and launches the expansion kernels.
@@ -497,7 +514,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   const bool car_items = car && m->policy_on;
   size_t ib = car   ? (car_items ? sizeof(uint32_t) * (size_t)(h->words + 2) * (size_t)plan.total_items : 0)
               : nav ? sizeof(uint32_t) * (size_t)nav_item_fields(h->n) * (size_t)plan.total_items
-                    : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots) * (size_t)plan.total_items;
+                    : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots, m->policy_on) * (size_t)plan.total_items;
   size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
   unsigned char* buf = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, total, m->pool, st);
@@ -540,8 +557,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   if (e == cudaSuccess) {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (m->timing) {
-      cudaEventCreate(&ev[0]);
-      cudaEventCreate(&ev[1]);
+      take_timing_events(m, ev);
       cudaEventRecord(ev[0], st);
     }
     if (car) {

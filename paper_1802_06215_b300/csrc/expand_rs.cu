@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -236,13 +238,7 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
         const int z = code % 3;
         const uint32_t pm = z == 1 ? pm_z[1] : (z == 2 ? pm_z[2] : pm_z[0]);
         const size_t it = (size_t)(ibase + (long long)a * n + q);
-        items.f(0)[it] = s.pos[0];
-        items.f(1)[it] = s.good;
-        items.f(2)[it] = s.sampled;
-        items.f(3)[it] = s.scen;
-        items.f(4)[it] = pm;
-        items.f(5)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1));
-        items.f(6)[it] = (uint32_t)j;
+        items.put(it, s, pm, ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1)), (uint32_t)j);
       }
     }
     __syncwarp();
@@ -386,13 +382,7 @@ __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, 
         const int z = code % 3;
         const uint32_t pm = z == 1 ? pm_z[1] : (z == 2 ? pm_z[2] : pm_z[0]);
         const size_t it = (size_t)(ibase + (long long)a * n + q);
-        items.f(0)[it] = s.pos[0];
-        items.f(1)[it] = s.good;
-        items.f(2)[it] = s.sampled;
-        items.f(3)[it] = s.scen;
-        items.f(4)[it] = pm;
-        items.f(5)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1));
-        items.f(6)[it] = (uint32_t)j;
+        items.put(it, s, pm, ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1)), (uint32_t)j);
       }
     }
     __syncwarp();
@@ -522,14 +512,7 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
         uint32_t pm = S.pm_job;
         M.observe(h, pm, aa, (uint64_t)(code % 9));
         const size_t it = (size_t)(ibase + (long long)a * n + q);
-        items.f(0)[it] = s.pos[0];
-        items.f(1)[it] = s.pos[1];
-        items.f(2)[it] = s.good;
-        items.f(3)[it] = s.sampled;
-        items.f(4)[it] = s.scen;
-        items.f(5)[it] = pm;
-        items.f(6)[it] = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1));
-        items.f(7)[it] = (uint32_t)j;
+        items.put(it, s, pm, ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1)), (uint32_t)j);
       }
       __syncwarp();
     }
@@ -617,15 +600,8 @@ __device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_
     long long fu = 0, fl = 0;
     if (ok) {
       RSS s;
-      s.pos[0] = items.f(0)[it];
-      int f = 1;
-      s.pos[1] = R == 2 ? items.f(f++)[it] : 0u;
-      s.good = items.f(f++)[it];
-      s.sampled = items.f(f++)[it];
-      s.scen = items.f(f++)[it];
-      const uint32_t pm = items.f(f++)[it];
-      const uint32_t meta = items.f(f++)[it];
-      job = items.f(f++)[it];
+      uint32_t pm, meta;  // compact items: pm is the candidate mask, sampled 0
+      items.get_compact((size_t)it, s, pm, meta, job);
       slot = meta & 0xFFFFFFu;
       const int depth = (int)(meta >> 24);
       float u = 0.0f, v = 0.0f;
@@ -744,12 +720,40 @@ __global__ void rs_rollout_kernel(const DevModel* __restrict__ gm, DevWork* work
   if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
+// CTAs per SM of a kernel at a CTA size and dynamic shared memory, asked of
+// the runtime once per (kernel, size, memory, device) and kept: the answer
+// never changes, and the query costs host time on every launch otherwise.
+template <class K>
+int occupancy_cached(K kernel, int block, size_t smem) {
+  struct Entry {
+    const void* k;
+    int block, dev;
+    size_t smem;
+    int per_sm;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const void* key = reinterpret_cast<const void*>(kernel);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+      if (e.k == key && e.block == block && e.smem == smem && e.dev == dev) return e.per_sm;
+  }
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  cache.push_back({key, block, dev, smem, n});
+  return n;
+}
+
 template <int R>
 cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st,
                              int warps_a, int ctas_b) {
-  Items<R> items{item_buf, total_items};
+  Items<R> items{item_buf, total_items, policy != nullptr && R == 1};
   // Each warp expands whole actions: as many warps as give every warp the
   // same number of a job's actions (20 actions: 10 warps of 2; 400: 16 of
   // 25). One robot with at least two jobs per CTA slot: at most five warps
@@ -767,8 +771,7 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
     const int per_warp = narrow ? (na + 4) / 5 : (na + kWarpsA - 1) / kWarpsA;
     block_a = 32 * ((na + per_warp - 1) / per_warp);
   }
-  int per_sm_a = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, rs_group_kernel<R>, block_a, 0);
+  int per_sm_a = occupancy_cached(rs_group_kernel<R>, block_a, 0);
   int grid_a = std::max(1, std::min(n_jobs, std::max(1, per_sm_a) * num_sms));
   // two robots: a job's hundreds of actions split over several CTAs (runs of
   // about 80), so that the largest jobs do not leave a tail
@@ -783,8 +786,7 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
                                        num_sms, st);
   // phase B keeps the policy-key table in shared memory (limit set by rs_set_key_smem)
   const size_t key_bytes = sizeof(uint16_t) * (size_t)key_words;
-  int per_sm_b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, rs_rollout_items_kernel<R>, block_b, key_bytes);
+  int per_sm_b = occupancy_cached(rs_rollout_items_kernel<R>, block_b, key_bytes);
   if (ctas_b > 0) per_sm_b = std::min(per_sm_b, ctas_b);
   long long chunks = (total_items + 31) / 32;
   long long want = (chunks + block_b / 32 - 1) / (block_b / 32);
@@ -954,7 +956,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       long long nchunks = 0;
       M.plan_step = s_plan_step;
       if (n > 0) {  // a job with no scenarios is a placeholder: nothing to do
-        Items<R> items{scratch + (size_t)slot * slot_words, (long long)n * S.J.n_actions};
+        Items<R> items{scratch + (size_t)slot * slot_words, (long long)n * S.J.n_actions, false};
         group_job<R, false>(S, M, 0, 0, 0, S.J.n_actions, true, items, work, steps);
         nchunks = (items.total + 31) >> 5;
       }
@@ -984,7 +986,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
       const int slot = queue_claim_chunk(ring, chunk, count);
       if (slot < 0) break;
       const dsp_leaf_job* J = jcopy + slot;
-      Items<R> items{scratch + (size_t)slot * slot_words, (long long)J->n_scen * J->n_actions};
+      Items<R> items{scratch + (size_t)slot * slot_words, (long long)J->n_scen * J->n_actions, false};
       M.plan_step = *(volatile unsigned int*)&ring.share[slot].plan_step;
       for (unsigned int k = 0; k < count; ++k) rs_rollout_chunk<R>(M, J, items, chunk + k, steps);
       __threadfence();  // every lane's sums, before the chunks count as done
@@ -1025,10 +1027,13 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_queue_kernel(const DevModel* __
 
 }  // namespace
 
-int rs_item_fields(int robots) { return robots == 2 ? Items<2>::kFields : Items<1>::kFields; }
+int rs_item_fields(int robots, bool full) {
+  if (full) return robots == 2 ? Items<2>::kFields : Items<1>::kFields;
+  return robots == 2 ? Items<2>::kCompactFields : Items<1>::kCompactFields;
+}
 
 size_t rs_queue_slot_words(int robots, int num_actions) {
-  return (size_t)rs_item_fields(robots) * (size_t)kMaxScen * (size_t)num_actions;
+  return (size_t)rs_item_fields(robots, false) * (size_t)kMaxScen * (size_t)num_actions;
 }
 
 // The persistent kernel keeps the policy-key table in dynamic shared memory.

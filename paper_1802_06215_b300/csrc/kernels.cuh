@@ -7,7 +7,7 @@
 namespace dsp {
 
 // Rock Sample: words per rollout item of the two-phase expansion.
-int rs_item_fields(int robots);
+int rs_item_fields(int robots, bool full);  // words per rollout item (full: learned-policy layout)
 // Rock Sample two-phase expansion: phase A over n_jobs jobs (item_base[j] =
 // first item of job j, total_items in all), phase B over the item list.
 // counters: two device uints, zero on entry (job head, chunk head).

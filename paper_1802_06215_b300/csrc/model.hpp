@@ -38,6 +38,7 @@ struct dsp_model {
   bool timing = false;               // record events around the expansion kernels
   std::mutex timing_mu;
   std::vector<cudaEvent_t> timing_events;  // start, end per dsp_expand_leaves call
+  std::vector<cudaEvent_t> timing_pool;    // events read back, for reuse
   std::mutex staging_mu;
   std::vector<dsp_staging_slot*> staging;  // pinned copies of the calls' job tables
 };
@@ -100,6 +101,20 @@ cudaError_t launch_nav_step(const DevModel* gm, const uint32_t* in, int in_cap, 
 cudaError_t launch_nav_rollout(const DevModel* gm, DevWork* work, const uint32_t* block, int cap, int count,
                                const int8_t* hist, int start_depth, float* value, uint32_t plan_step,
                                cudaStream_t st);
+struct QueueRing;  // kernels.cuh
+// Persistent queue kernels of the navigation and car models (queue.cu):
+// set-up (shared-memory limit, CTAs per SM), scratch sizes and the launch.
+// Navigation: per ring slot, one job's rollout items (slot_words each);
+// car: per CTA, one observation scratch.
+cudaError_t nav_queue_setup(int* per_sm);
+size_t nav_queue_slot_words(const dsp_model* m);
+cudaError_t launch_nav_queue(dsp_model* m, QueueRing ring, unsigned long long* head, uint32_t* scratch,
+                             size_t slot_words, dsp_leaf_job* jcopy, unsigned long long idle_ns, int grid,
+                             cudaStream_t st);
+cudaError_t car_queue_setup(const dsp_model* m, int* per_sm);
+size_t car_queue_scratch_words(int grid);
+cudaError_t launch_car_queue(dsp_model* m, QueueRing ring, unsigned long long* head, uint32_t* scratch,
+                             dsp_leaf_job* jcopy, unsigned long long idle_ns, int grid, cudaStream_t st);
 // Lanes per car scenario when untuned: enough for one pedestrian pair per
 // lane (4 to 32).
 int car_default_tps(int P);
@@ -113,6 +128,10 @@ cudaError_t launch_car_rollout_mlp_items(dsp_model* m, const dsp_leaf_job* jobs,
 cudaError_t launch_car_rollout_logged(const dsp_model* m, const uint32_t* block, int cap, int count, int start_depth,
                                       float* value, int32_t* actions, float* logits, unsigned int* counter,
                                       cudaStream_t st);
+// Default policies per state (dsp_default_policy).
+cudaError_t launch_car_policy(const dsp_model* m, const uint32_t* block, int cap, int count, int32_t* actions,
+                              cudaStream_t st);
+cudaError_t launch_nav_policy(const DevModel* gm, const int8_t* hist, int count, int32_t* actions, cudaStream_t st);
 // Learned-policy features of car states (dsp_features).
 cudaError_t launch_car_features(const dsp_model* m, const uint32_t* block, int cap, int count, float* out,
                                 cudaStream_t st);

@@ -242,14 +242,30 @@ struct RSModel {
     return key;
   }
 
-  // Applies one robot's heuristic action (decided on the state before either
-  // robot moved) to the unpacked state: E while no target is left (exit from
-  // the last column), else the key's move, or Sample when the key's distance
-  // is 0 (the rock leaves the candidate set). Returns the reward.
-  __device__ __forceinline__ int apply_heuristic(int& x, int& y, bool& ex, int key, uint32_t& good,
-                                                 uint32_t& cand) const {
+  // The heuristic's target of one robot at cell y*n+x among the non-empty
+  // rock set cand (the smallest policy key: nearest rock, lowest index on
+  // ties): its coordinates and bit.
+  __device__ __forceinline__ void target(int x, int y, uint32_t cand, int& tx, int& ty, uint32_t& tbit) const {
+    const int i = (nearest_key(y * n + x, cand) >> 2) & 31;
+    const int rxy = sh->rock_xy[i];
+    tx = rxy & 0xFF;
+    ty = rxy >> 8;
+    tbit = 1u << i;
+  }
+
+  // One heuristic step of one robot with its target carried between steps
+  // (no target: E, the exit from the last column). Between two samples the
+  // target cannot change: a step toward it lowers its Manhattan distance by
+  // one and any other rock's by at most one, so no other rock overtakes it,
+  // and on a tie the lower index that already won keeps winning. So the
+  // policy's action equals a fresh scan's at every step; the scan runs only
+  // after a sample changed the rock set. On the target's cell: Sample (the
+  // rock leaves the set, the robot retargets). Else the move toward it, x
+  // before y. Returns the reward.
+  __device__ __forceinline__ int heuristic_step(int& x, int& y, bool& ex, int& tx, int& ty, uint32_t& tbit,
+                                                uint32_t& good, uint32_t& cand) const {
     if (ex) return 0;
-    if (key == 0xFFFF) {
+    if (tbit == 0) {
       if (x == n - 1) {
         ex = true;
         return 10;
@@ -257,18 +273,17 @@ struct RSModel {
       x += 1;
       return 0;
     }
-    if (key < 128) {
-      const uint32_t bit = 1u << (key >> 2);
-      const int r = (good & bit) ? 10 : -10;
-      good &= ~bit;
-      cand &= ~bit;
+    if (x == tx && y == ty) {
+      const int r = (good & tbit) ? 10 : -10;
+      good &= ~tbit;
+      cand &= ~tbit;
+      tbit = 0;
       return r;
     }
-    const int a = key & 3;
-    if (a & 1)
-      x += 2 - a;
+    if (x != tx)
+      x += tx > x ? 1 : -1;
     else
-      y += 1 - a;
+      y += ty > y ? 1 : -1;
     return 0;
   }
 
@@ -276,22 +291,34 @@ struct RSModel {
   // both robots decide on the state before the step (the joint heuristic
   // policy), robot 0 acts first (a rock both stand on is sampled by robot 0,
   // robot 1's Sample then finds it bad), an exited robot does nothing, the
-  // rewards are summed, and the world ends when both have exited.
+  // rewards are summed, and the world ends when both have exited. Targets
+  // are carried between steps (heuristic_step). A sample removes one rock
+  // from the shared set; the argmin over the rest is unchanged unless it was
+  // that rock, so a robot retakes its target, before the next step, exactly
+  // when its target has left the set.
   __device__ __forceinline__ float rollout_two(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
     int x0 = (int)(s.pos[0] & 0xFFu), y0 = (int)((s.pos[0] >> 8) & 0xFFu);
     int x1 = (int)(s.pos[1] & 0xFFu), y1 = (int)((s.pos[1] >> 8) & 0xFFu);
     bool ex0 = (s.pos[0] >> 16) & 1u, ex1 = (s.pos[1] >> 16) & 1u;
     uint32_t good = s.good, cand = pmask & ~s.sampled;  // cand loses each sampled rock
+    int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+    uint32_t tb0 = 0, tb1 = 0;
     float v = 0.0f;
     int t = t0;
     while (t < D && !(ex0 && ex1)) {
-      int k0 = 0xFFFF, k1 = 0xFFFF;
-      if (cand != 0) {
-        if (!ex0) k0 = nearest_key(y0 * n + x0, cand);
-        if (!ex1) k1 = nearest_key(y1 * n + x1, cand);
+      if (!ex0 && (tb0 & cand) == 0) {
+        tb0 = 0;
+        if (cand != 0) target(x0, y0, cand, tx0, ty0, tb0);
       }
-      int reward = apply_heuristic(x0, y0, ex0, k0, good, cand);
-      reward += apply_heuristic(x1, y1, ex1, k1, good, cand);
+      if (!ex1 && (tb1 & cand) == 0) {
+        tb1 = 0;
+        if (cand != 0) target(x1, y1, cand, tx1, ty1, tb1);
+      }
+      // robot 1's target was taken on the state before robot 0 acts: its
+      // Sample of a rock robot 0 just took finds it bad, as the joint step's
+      // order has it
+      int reward = heuristic_step(x0, y0, ex0, tx0, ty0, tb0, good, cand);
+      reward += heuristic_step(x1, y1, ex1, tx1, ty1, tb1, good, cand);
       if (reward != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)reward));
       t += 1;
     }
@@ -309,41 +336,29 @@ struct RSModel {
   // The heuristic policy only moves and samples, and its moves never leave
   // the map except E from the last column (the exit), so each step is one
   // branch on the action: E while no believed-good unsampled rock is left,
-  // else the policy key's move toward the nearest one, or Sample on it.
-  // Rewards, their order and the step count are those of step() and policy().
+  // else a step toward the target (carried between steps, retaken after
+  // each sample: heuristic_step), or Sample on it. Rewards, their order and
+  // the step count are those of step() and policy().
   __device__ __forceinline__ float rollout_one(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
     const uint32_t p0 = s.pos[0];
     int x = (int)(p0 & 0xFFu), y = (int)((p0 >> 8) & 0xFFu);
     bool ex = (p0 >> 16) & 1u;
     uint32_t good = s.good, cand = pmask & ~s.sampled;  // cand loses each sampled rock
+    int tx = 0, ty = 0;
+    uint32_t tbit = 0;
+    if (!ex && cand != 0) target(x, y, cand, tx, ty, tbit);
     float v = 0.0f;
     int t = t0;
     if (!ex) {
       for (; t < D; ++t) {
-        if (cand == 0) {
-          if (x == n - 1) {
-            v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], 10.0f));
-            ex = true;
-            ++t;
-            break;
-          }
-          x += 1;
-        } else {
-          const int key = nearest_key(y * n + x, cand);
-          if (key < 128) {
-            const uint32_t bit = 1u << (key >> 2);
-            const float r = (good & bit) ? 10.0f : -10.0f;
-            good &= ~bit;
-            cand &= ~bit;
-            v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
-          } else {
-            const int a = key & 3;
-            if (a & 1)
-              x += 2 - a;
-            else
-              y += 1 - a;
-          }
+        const uint32_t before = cand;
+        const int r = heuristic_step(x, y, ex, tx, ty, tbit, good, cand);
+        if (r != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)r));
+        if (ex) {
+          ++t;
+          break;
         }
+        if (cand != before && cand != 0) target(x, y, cand, tx, ty, tbit);
       }
     }
     steps += (unsigned long long)(t - t0);
