@@ -13,6 +13,7 @@
 #include "car_model.cuh"
 #include "group.cuh"
 #include "model.hpp"
+#include "queue_ring.cuh"
 
 namespace dsp {
 namespace {
@@ -34,6 +35,137 @@ static_assert(sizeof(GroupSmem::tkey) >= 2 * kMaxScen * sizeof(unsigned long lon
                   sizeof(GroupSmem::tfirst) >= kMaxScen * sizeof(unsigned long long),
               "the sums alias the hash table");
 
+// One (job, action) unit of the car expansion by the whole CTA, the job's
+// descriptor in S.job: gather + update into the leaf, the expansion step
+// with its observation key, u0, and the rollout (or, with a learned policy,
+// the stepped state into the item list at item_base), then the grouping by
+// key with the full-observation check, the per-child sums and the results
+// of action offset `ao`. obs: the CTA's observation scratch. Ends with a
+// barrier.
+template <int TPS, int KP>
+__device__ __forceinline__ void car_unit(CarUnitSmem& S, const CarModel<TPS, KP>& M, int ao, long long item_base,
+                                         int job_index, uint32_t* obs, const CarItems& items, DevWork* work,
+                                         unsigned long long& steps) {
+  const int P = M.P;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int groups = nthr / TPS, g = tid / TPS;
+  const dsp_leaf_job& job = S.job;
+  const int n = job.n_scen, depth = job.depth;
+  const int a = job.first_action + ao;
+  const bool first_unit = ao == 0;
+  for (int base = 0; base < n; base += groups) {
+    const int p = base + g;
+    const bool valid = p < n;
+    CarLane<TPS, KP> L;
+    if (valid) {
+      M.load(L, job.parent, job.parent_cap, job.idx[p]);
+    } else {
+      L.s = 0.0f;
+      L.v = 0;
+      L.term = true;
+      L.scen = 0;
+      L.goals = 0;
+#pragma unroll
+      for (int k = 0; k < 2 * CarLane<TPS, KP>::kPairs; ++k) L.px[k] = L.py[k] = 0.0f;
+    }
+    bool danger = false;
+    uint64_t key = 0;
+    if (job.last_action >= 0) {  // update by the action into this leaf
+      bool live = valid && !L.term;
+      if (live && M.gl == 0 && first_unit) steps += 1;
+      uint32_t uf = M.fail_word(L.scen, depth - 1);
+      M.template step<false>(L, live, job.last_action, depth - 1, uf, danger, key);
+    }
+    if (first_unit && job.leaf_states != nullptr) M.store(L, job.leaf_states, n, p, valid);
+    // Eq. expand with the observation key
+    bool live = valid && !L.term;
+    if (live && M.gl == 0) steps += 1;
+    uint32_t uf = M.fail_word(L.scen, depth);
+    float r = M.template step<true>(L, live, a, depth, uf, danger, key);
+    if (valid) {
+      uint32_t* ob = obs + (size_t)p * kCarObsWords;
+      if (M.gl == 0) ob[0] = (uint32_t)L.v | ((uint32_t)L.term << 8);
+#pragma unroll
+      for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          int j = 2 * (M.gl + k * TPS) + e;
+          if (j < P) {
+            int qx = (int)floorf(__fmul_rn(2.0f, L.px[2 * k + e]));
+            int qy = (int)floorf(__fmul_rn(2.0f, L.py[2 * k + e]));
+            ob[1 + j] = (uint32_t)(uint16_t)(int16_t)qx | ((uint32_t)(uint16_t)(int16_t)qy << 16);
+          }
+        }
+    }
+    // Eq. ub (the tail heuristic is zero at depth D) and Eq. lb; with a
+    // learned policy the stepped state goes to the item list instead and the
+    // learned-rollout kernel adds the rollout values afterwards
+    float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(L);
+    float lv = 0.0f;
+    if (items.base != nullptr)
+      M.store(L, items.base, (int)items.total, item_base + p, valid);
+    else
+      lv = M.rollout(L, valid, danger, depth + 1, steps);
+    if (valid && M.gl == 0) {
+      S.key[p] = key;
+      S.rew[p] = r;
+      S.uval[p] = uv;
+      S.lval[p] = lv;
+    }
+  }
+  __syncthreads();
+  group_by_key(S.grp, S.key, n);
+  const int nchild = S.grp.nchild;
+  unsigned long long* sr = reinterpret_cast<unsigned long long*>(S.grp.tkey);
+  unsigned long long* su = sr + kMaxScen;
+  unsigned long long* sl = reinterpret_cast<unsigned long long*>(S.grp.tfirst);
+  for (int c = tid; c < nchild; c += nthr) {
+    sr[c] = 0;
+    su[c] = 0;
+    sl[c] = 0;
+  }
+  __syncthreads();
+  // full-observation check of every member against its child's first member
+  for (int q = tid; q < n; q += nthr) {
+    int c = S.grp.gcid[q];
+    int f = S.grp.cfirst[c];
+    if (f != q) {
+      const uint32_t* a0 = obs + (size_t)f * kCarObsWords;
+      const uint32_t* a1 = obs + (size_t)q * kCarObsWords;
+      bool same = a0[0] == a1[0];
+      for (int w = 1; w <= P; ++w) same = same && (a0[w] == a1[w]);
+      if (!same) report(work, kStatusKeyClash);
+    }
+    atomicAdd(&sr[c], (unsigned long long)to_fixed(S.rew[q]));
+    atomicAdd(&su[c], (unsigned long long)to_fixed(S.uval[q]));
+    atomicAdd(&sl[c], (unsigned long long)to_fixed(S.lval[q]));
+  }
+  __syncthreads();
+  const int cap = job.child_cap;
+  if (tid == 0) {
+    job.child_count[ao] = nchild;
+    if (nchild > cap) report(work, kStatusOverflow);
+  }
+  const int ncw = min(nchild, cap);
+  for (int c = tid; c <= ncw; c += nthr) job.child_off[(size_t)ao * (cap + 1) + c] = c < nchild ? S.grp.coff[c] : n;
+  for (int c = tid; c < ncw; c += nthr) {
+    size_t o = (size_t)ao * cap + c;
+    job.child_key[o] = S.key[S.grp.cfirst[c]];
+    job.rew_sum[o] = (long long)sr[c];
+    job.u_sum[o] = (long long)su[c];
+    job.l_sum[o] = (long long)sl[c];
+  }
+  for (int q = tid; q < n; q += nthr) {
+    int c = S.grp.gcid[q];
+    job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
+    if (items.base != nullptr) {
+      items.meta()[item_base + q] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
+      items.job()[item_base + q] = (uint32_t)job_index;
+    }
+  }
+  __syncthreads();
+}
+
 template <int TPS, int KP = kDefaultPairs<TPS>>
 __global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                          const dsp_leaf_job* __restrict__ jobs,
@@ -44,9 +176,7 @@ __global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expan
   CarUnitSmem& S = *reinterpret_cast<CarUnitSmem*>(smem_raw);
   load_car_consts(S.c, gm);
   CarModel<TPS, KP> M = make_car_model<TPS, KP>(gm, &S.c, plan_step);
-  const int P = M.P;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int groups = nthr / TPS, g = tid / TPS;
+  const int tid = threadIdx.x;
   uint32_t* obs = scratch + (size_t)blockIdx.x * kMaxScen * kCarObsWords;
   unsigned long long steps = 0;
   __syncthreads();
@@ -59,122 +189,7 @@ __global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expan
     const int4 un = units[u];
     if (tid == 0) S.job = jobs[un.x];
     __syncthreads();
-    const dsp_leaf_job& job = S.job;
-    const int n = job.n_scen, depth = job.depth;
-    const int a = job.first_action + un.y;
-    const bool first_unit = un.y == 0;
-    for (int base = 0; base < n; base += groups) {
-      const int p = base + g;
-      const bool valid = p < n;
-      CarLane<TPS, KP> L;
-      if (valid) {
-        M.load(L, job.parent, job.parent_cap, job.idx[p]);
-      } else {
-        L.s = 0.0f;
-        L.v = 0;
-        L.term = true;
-        L.scen = 0;
-        L.goals = 0;
-#pragma unroll
-        for (int k = 0; k < 2 * CarLane<TPS, KP>::kPairs; ++k) L.px[k] = L.py[k] = 0.0f;
-      }
-      bool danger = false;
-      uint64_t key = 0;
-      if (job.last_action >= 0) {  // update by the action into this leaf
-        bool live = valid && !L.term;
-        if (live && M.gl == 0 && first_unit) steps += 1;
-        uint32_t uf = M.fail_word(L.scen, depth - 1);
-        M.template step<false>(L, live, job.last_action, depth - 1, uf, danger, key);
-      }
-      if (first_unit && job.leaf_states != nullptr) M.store(L, job.leaf_states, n, p, valid);
-      // Eq. expand with the observation key
-      bool live = valid && !L.term;
-      if (live && M.gl == 0) steps += 1;
-      uint32_t uf = M.fail_word(L.scen, depth);
-      float r = M.template step<true>(L, live, a, depth, uf, danger, key);
-      if (valid) {
-        uint32_t* ob = obs + (size_t)p * kCarObsWords;
-        if (M.gl == 0) ob[0] = (uint32_t)L.v | ((uint32_t)L.term << 8);
-#pragma unroll
-        for (int k = 0; k < CarLane<TPS, KP>::kPairs; ++k)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            int j = 2 * (M.gl + k * TPS) + e;
-            if (j < P) {
-              int qx = (int)floorf(__fmul_rn(2.0f, L.px[2 * k + e]));
-              int qy = (int)floorf(__fmul_rn(2.0f, L.py[2 * k + e]));
-              ob[1 + j] = (uint32_t)(uint16_t)(int16_t)qx | ((uint32_t)(uint16_t)(int16_t)qy << 16);
-            }
-          }
-      }
-      // Eq. ub (the tail heuristic is zero at depth D) and Eq. lb; with a
-      // learned policy the stepped state goes to the item list instead and the
-      // learned-rollout kernel adds the rollout values afterwards
-      float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(L);
-      float lv = 0.0f;
-      if (items.base != nullptr)
-        M.store(L, items.base, (int)items.total, un.z + p, valid);
-      else
-        lv = M.rollout(L, valid, danger, depth + 1, steps);
-      if (valid && M.gl == 0) {
-        S.key[p] = key;
-        S.rew[p] = r;
-        S.uval[p] = uv;
-        S.lval[p] = lv;
-      }
-    }
-    __syncthreads();
-    group_by_key(S.grp, S.key, n);
-    const int nchild = S.grp.nchild;
-    unsigned long long* sr = reinterpret_cast<unsigned long long*>(S.grp.tkey);
-    unsigned long long* su = sr + kMaxScen;
-    unsigned long long* sl = reinterpret_cast<unsigned long long*>(S.grp.tfirst);
-    for (int c = tid; c < nchild; c += nthr) {
-      sr[c] = 0;
-      su[c] = 0;
-      sl[c] = 0;
-    }
-    __syncthreads();
-    // full-observation check of every member against its child's first member
-    for (int q = tid; q < n; q += nthr) {
-      int c = S.grp.gcid[q];
-      int f = S.grp.cfirst[c];
-      if (f != q) {
-        const uint32_t* a0 = obs + (size_t)f * kCarObsWords;
-        const uint32_t* a1 = obs + (size_t)q * kCarObsWords;
-        bool same = a0[0] == a1[0];
-        for (int w = 1; w <= P; ++w) same = same && (a0[w] == a1[w]);
-        if (!same) report(work, kStatusKeyClash);
-      }
-      atomicAdd(&sr[c], (unsigned long long)to_fixed(S.rew[q]));
-      atomicAdd(&su[c], (unsigned long long)to_fixed(S.uval[q]));
-      atomicAdd(&sl[c], (unsigned long long)to_fixed(S.lval[q]));
-    }
-    __syncthreads();
-    const int cap = job.child_cap;
-    const int ao = un.y;
-    if (tid == 0) {
-      job.child_count[ao] = nchild;
-      if (nchild > cap) report(work, kStatusOverflow);
-    }
-    const int ncw = min(nchild, cap);
-    for (int c = tid; c <= ncw; c += nthr) job.child_off[(size_t)ao * (cap + 1) + c] = c < nchild ? S.grp.coff[c] : n;
-    for (int c = tid; c < ncw; c += nthr) {
-      size_t o = (size_t)ao * cap + c;
-      job.child_key[o] = S.key[S.grp.cfirst[c]];
-      job.rew_sum[o] = (long long)sr[c];
-      job.u_sum[o] = (long long)su[c];
-      job.l_sum[o] = (long long)sl[c];
-    }
-    for (int q = tid; q < n; q += nthr) {
-      int c = S.grp.gcid[q];
-      job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
-      if (items.base != nullptr) {
-        items.meta()[un.z + q] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
-        items.job()[un.z + q] = (uint32_t)un.x;
-      }
-    }
-    __syncthreads();
+    car_unit<TPS, KP>(S, M, un.y, un.z, un.x, obs, items, work, steps);
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
@@ -235,6 +250,66 @@ __global__ void __launch_bounds__(256) car_rollout_kernel(const DevModel* __rest
   if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
+// Persistent queue kernel of the car: a CTA claims a published job, runs its
+// actions as units (car_unit, heuristic rollouts) with its own observation
+// scratch, then publishes the job done. Idle CTAs back off and exit after
+// idle_ns without a job; the host relaunches the kernel when jobs come.
+template <int TPS, int KP = kDefaultPairs<TPS>>
+__global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1)
+    car_queue_kernel(const DevModel* __restrict__ gm, DevWork* work, QueueRing ring, unsigned long long* head,
+                     uint32_t* scratch, dsp_leaf_job* jcopy, unsigned long long idle_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CarUnitSmem& S = *reinterpret_cast<CarUnitSmem*>(smem_raw);
+  __shared__ long long s_ticket;
+  __shared__ unsigned int s_plan_step;
+  __shared__ int s_exit;
+  load_car_consts(S.c, gm);
+  CarModel<TPS, KP> M = make_car_model<TPS, KP>(gm, &S.c, 0u);
+  const int tid = threadIdx.x;
+  uint32_t* obs = scratch + (size_t)blockIdx.x * kMaxScen * kCarObsWords;
+  const CarItems none{nullptr, 0, 0};
+  unsigned long long steps = 0, last_work = qring::now_ns();
+  unsigned int backoff = 256;
+  __syncthreads();
+  while (true) {
+    if (tid < 32) {
+      const long long t = qring::take_job(ring, head, &S.job, jcopy, &s_plan_step);
+      if (tid == 0) s_ticket = t;
+    }
+    __syncthreads();
+    const long long ticket = s_ticket;
+    if (ticket >= 0) {
+      M.plan_step = s_plan_step;
+      for (int ao = 0; ao < S.job.n_actions; ++ao) car_unit<TPS, KP>(S, M, ao, 0, 0, obs, none, work, steps);
+      __threadfence();  // every thread's results, before the job is published done
+      __syncthreads();
+      if (tid == 0) qring::finish_job(ring, (unsigned long long)ticket);
+    }
+    if (tid == 0) s_exit = qring::idle_exit(ring, ticket >= 0, last_work, backoff, idle_ns);
+    __syncthreads();
+    if (s_exit) break;
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
+template <int TPS, int KP>
+cudaError_t queue_tps(dsp_model* m, QueueRing ring, unsigned long long* head, uint32_t* scratch, dsp_leaf_job* jcopy,
+                      unsigned long long idle_ns, int grid, cudaStream_t st) {
+  car_queue_kernel<TPS, KP><<<grid, 256, sizeof(CarUnitSmem), st>>>(m->dmodel, m->dwork, ring, head, scratch, jcopy,
+                                                                     idle_ns);
+  return cudaGetLastError();
+}
+
+template <int TPS, int KP>
+cudaError_t queue_tps_setup(int* per_sm) {
+  const size_t smem = sizeof(CarUnitSmem);
+  cudaError_t e =
+      cudaFuncSetAttribute(car_queue_kernel<TPS, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, car_queue_kernel<TPS, KP>, 256, smem);
+  return e;
+}
+
 template <int TPS, int KP = kDefaultPairs<TPS>>
 cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units, unsigned int* head,
                        CarItems items, cudaStream_t st) {
@@ -285,6 +360,39 @@ cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int
       return pairs <= 16 ? launch_tps<16, 1>(m, djobs, dunits, n_units, head, items, st)
                          : launch_tps<16>(m, djobs, dunits, n_units, head, items, st);
     default: return launch_tps<32>(m, djobs, dunits, n_units, head, items, st);
+  }
+}
+
+// The persistent queue kernel's lanes per scenario: the expansion's untuned
+// default for the crowd (one pedestrian pair per lane where the crowd fits).
+// Sets the kernel's shared-memory limit (before any capture) and returns the
+// CTAs that fit per SM.
+cudaError_t car_queue_setup(const dsp_model* m, int* per_sm) {
+  const int pairs = (m->host->P + 1) / 2;
+  switch (car_default_tps(m->host->P)) {
+    case 4: return pairs <= 4 ? queue_tps_setup<4, 1>(per_sm) : queue_tps_setup<4, kDefaultPairs<4>>(per_sm);
+    case 8: return pairs <= 8 ? queue_tps_setup<8, 1>(per_sm) : queue_tps_setup<8, kDefaultPairs<8>>(per_sm);
+    case 16: return pairs <= 16 ? queue_tps_setup<16, 1>(per_sm) : queue_tps_setup<16, kDefaultPairs<16>>(per_sm);
+    default: return queue_tps_setup<32, kDefaultPairs<32>>(per_sm);
+  }
+}
+
+size_t car_queue_scratch_words(int grid) { return (size_t)grid * kMaxScen * kCarObsWords; }
+
+cudaError_t launch_car_queue(dsp_model* m, QueueRing ring, unsigned long long* head, uint32_t* scratch,
+                             dsp_leaf_job* jcopy, unsigned long long idle_ns, int grid, cudaStream_t st) {
+  const int pairs = (m->host->P + 1) / 2;
+  switch (car_default_tps(m->host->P)) {
+    case 4:
+      return pairs <= 4 ? queue_tps<4, 1>(m, ring, head, scratch, jcopy, idle_ns, grid, st)
+                        : queue_tps<4, kDefaultPairs<4>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
+    case 8:
+      return pairs <= 8 ? queue_tps<8, 1>(m, ring, head, scratch, jcopy, idle_ns, grid, st)
+                        : queue_tps<8, kDefaultPairs<8>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
+    case 16:
+      return pairs <= 16 ? queue_tps<16, 1>(m, ring, head, scratch, jcopy, idle_ns, grid, st)
+                         : queue_tps<16, kDefaultPairs<16>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
+    default: return queue_tps<32, kDefaultPairs<32>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
   }
 }
 

@@ -23,6 +23,7 @@
 #include "group.cuh"
 #include "model.hpp"
 #include "nav_model.cuh"
+#include "queue_ring.cuh"
 
 namespace dsp {
 
@@ -50,6 +51,87 @@ struct NavItems {
   __device__ __forceinline__ uint32_t* f(int k) const { return base + (size_t)k * (size_t)total; }
 };
 
+// One (job, action) unit of phase A by the whole CTA, the job's descriptor
+// in S.job: gather + update into the leaf, the step with its 8-bit reading,
+// u0 and one rollout item per scenario at item_base (job index job_index in
+// the items), then the grouping by reading, the exact reward and u sums and
+// the results of action offset `ao` (l sums start at zero; phase B adds the
+// rollouts). Ends with a barrier.
+__device__ __forceinline__ void nav_unit(NavUnitSmem& S, const NavModel& M, int ao, long long item_base, int job_index,
+                                         const NavItems& items, DevWork* work, unsigned long long& steps) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const dsp_leaf_job& job = S.job;
+  const int n = job.n_scen, depth = job.depth;
+  const int a = job.first_action + ao;
+  const bool first_unit = ao == 0;
+  const uint32_t last0 = (uint32_t)(uint8_t)job.hist[0];
+  const long long ibase = item_base;
+  for (int p = tid; p < n; p += nthr) {
+    NavS s = M.load(job.parent, job.parent_cap, job.idx[p]);
+    if (job.last_action >= 0) {  // update by the action into this leaf
+      if (!s.term && first_unit) steps += 1;
+      uint64_t k0;
+      M.step(s, job.last_action, depth - 1, k0);
+    }
+    const int src = job.idx[p];
+    if (first_unit && job.leaf_states != nullptr) {
+      M.store_pos(s, job.leaf_states, n, p);
+      M.copy_map(job.parent, job.parent_cap, src, job.leaf_states, n, p);
+    }
+    // Eq. expand with the observation key
+    if (!s.term) steps += 1;
+    uint64_t key;
+    const float r = M.step(s, a, depth, key);
+    // Eq. ub (the tail heuristic is zero at depth D); Eq. lb starts from the
+    // child's history, whose last reading is the one just taken
+    const float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(s);
+    const uint32_t last = (key & kTermBit) ? last0 : (uint32_t)(key & 0xFFu);
+    const long long it = ibase + p;
+    items.f(0)[it] = (uint32_t)s.x | ((uint32_t)s.y << 4) | ((uint32_t)s.term << 8) | (s.nb << 9) | (last << 17);
+#pragma unroll
+    for (int k = 0; k < kNavRowWords; ++k) items.f(1 + k)[it] = s.R[k];
+    items.f(1 + kNavRowWords)[it] = s.scen;
+    S.key[p] = key;
+    S.rew[p] = r;
+    S.uval[p] = uv;
+  }
+  for (int c = tid; c < n; c += nthr) {
+    S.sr[c] = 0;
+    S.su[c] = 0;
+  }
+  __syncthreads();
+  group_by_key(S.grp, S.key, n);
+  const int nchild = S.grp.nchild;
+  for (int q = tid; q < n; q += nthr) {
+    const int c = S.grp.gcid[q];
+    atomicAdd(&S.sr[c], (unsigned long long)to_fixed(S.rew[q]));
+    atomicAdd(&S.su[c], (unsigned long long)to_fixed(S.uval[q]));
+  }
+  __syncthreads();
+  const int cap = job.child_cap;
+  if (tid == 0) {
+    job.child_count[ao] = nchild;
+    if (nchild > cap) report(work, kStatusOverflow);
+  }
+  const int ncw = min(nchild, cap);
+  for (int c = tid; c <= ncw; c += nthr) job.child_off[(size_t)ao * (cap + 1) + c] = c < nchild ? S.grp.coff[c] : n;
+  for (int c = tid; c < ncw; c += nthr) {
+    const size_t o = (size_t)ao * cap + c;
+    job.child_key[o] = S.key[S.grp.cfirst[c]];
+    job.rew_sum[o] = (long long)S.sr[c];
+    job.u_sum[o] = (long long)S.su[c];
+    job.l_sum[o] = 0;  // phase B adds the rollouts
+  }
+  for (int q = tid; q < n; q += nthr) {
+    const int c = S.grp.gcid[q];
+    job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
+    const long long it = ibase + q;
+    items.f(2 + kNavRowWords)[it] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
+    items.f(3 + kNavRowWords)[it] = (uint32_t)job_index;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256, 4) nav_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                         const dsp_leaf_job* __restrict__ jobs,
                                                         const int4* __restrict__ units, int n_units,
@@ -58,7 +140,7 @@ __global__ void __launch_bounds__(256, 4) nav_group_kernel(const DevModel* __res
   NavUnitSmem& S = *reinterpret_cast<NavUnitSmem*>(smem_raw);
   load_nav_tables(S.T, gm);
   const NavModel M = make_nav(gm, &S.T, plan_step);
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   unsigned long long steps = 0;
   __syncthreads();
   while (true) {
@@ -70,77 +152,7 @@ __global__ void __launch_bounds__(256, 4) nav_group_kernel(const DevModel* __res
     const int4 un = units[u];
     if (tid == 0) S.job = jobs[un.x];
     __syncthreads();
-    const dsp_leaf_job& job = S.job;
-    const int n = job.n_scen, depth = job.depth;
-    const int a = job.first_action + un.y;
-    const bool first_unit = un.y == 0;
-    const uint32_t last0 = (uint32_t)(uint8_t)job.hist[0];
-    const long long ibase = un.z;
-    for (int p = tid; p < n; p += nthr) {
-      NavS s = M.load(job.parent, job.parent_cap, job.idx[p]);
-      if (job.last_action >= 0) {  // update by the action into this leaf
-        if (!s.term && first_unit) steps += 1;
-        uint64_t k0;
-        M.step(s, job.last_action, depth - 1, k0);
-      }
-      const int src = job.idx[p];
-      if (first_unit && job.leaf_states != nullptr) {
-        M.store_pos(s, job.leaf_states, n, p);
-        M.copy_map(job.parent, job.parent_cap, src, job.leaf_states, n, p);
-      }
-      // Eq. expand with the observation key
-      if (!s.term) steps += 1;
-      uint64_t key;
-      const float r = M.step(s, a, depth, key);
-      // Eq. ub (the tail heuristic is zero at depth D); Eq. lb starts from the
-      // child's history, whose last reading is the one just taken
-      const float uv = (depth + 1 >= M.D) ? 0.0f : M.upper(s);
-      const uint32_t last = (key & kTermBit) ? last0 : (uint32_t)(key & 0xFFu);
-      const long long it = ibase + p;
-      items.f(0)[it] = (uint32_t)s.x | ((uint32_t)s.y << 4) | ((uint32_t)s.term << 8) | (s.nb << 9) | (last << 17);
-#pragma unroll
-      for (int k = 0; k < kNavRowWords; ++k) items.f(1 + k)[it] = s.R[k];
-      items.f(1 + kNavRowWords)[it] = s.scen;
-      S.key[p] = key;
-      S.rew[p] = r;
-      S.uval[p] = uv;
-    }
-    for (int c = tid; c < n; c += nthr) {
-      S.sr[c] = 0;
-      S.su[c] = 0;
-    }
-    __syncthreads();
-    group_by_key(S.grp, S.key, n);
-    const int nchild = S.grp.nchild;
-    for (int q = tid; q < n; q += nthr) {
-      const int c = S.grp.gcid[q];
-      atomicAdd(&S.sr[c], (unsigned long long)to_fixed(S.rew[q]));
-      atomicAdd(&S.su[c], (unsigned long long)to_fixed(S.uval[q]));
-    }
-    __syncthreads();
-    const int cap = job.child_cap;
-    const int ao = un.y;
-    if (tid == 0) {
-      job.child_count[ao] = nchild;
-      if (nchild > cap) report(work, kStatusOverflow);
-    }
-    const int ncw = min(nchild, cap);
-    for (int c = tid; c <= ncw; c += nthr) job.child_off[(size_t)ao * (cap + 1) + c] = c < nchild ? S.grp.coff[c] : n;
-    for (int c = tid; c < ncw; c += nthr) {
-      const size_t o = (size_t)ao * cap + c;
-      job.child_key[o] = S.key[S.grp.cfirst[c]];
-      job.rew_sum[o] = (long long)S.sr[c];
-      job.u_sum[o] = (long long)S.su[c];
-      job.l_sum[o] = 0;  // phase B adds the rollouts
-    }
-    for (int q = tid; q < n; q += nthr) {
-      const int c = S.grp.gcid[q];
-      job.perm[(size_t)ao * n + S.grp.coff[c] + S.grp.rank[q]] = (uint16_t)q;
-      const long long it = ibase + q;
-      items.f(2 + kNavRowWords)[it] = ((uint32_t)depth << 24) | (uint32_t)(ao * cap + min(c, cap - 1));
-      items.f(3 + kNavRowWords)[it] = (uint32_t)un.x;
-    }
-    __syncthreads();
+    nav_unit(S, M, un.y, un.z, un.x, items, work, steps);
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
@@ -183,17 +195,13 @@ __device__ __forceinline__ int stage_chunk(NavStage& st, int b, const NavItems& 
   return (int)min(32LL, items.total - ch * 32);
 }
 
-__global__ void __launch_bounds__(256, 4) nav_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
-                                                                const dsp_leaf_job* __restrict__ jobs,
-                                                                NavItems items, unsigned int* chunk_head,
-                                                                uint32_t plan_step) {
-  __shared__ NavTables T;
-  __shared__ NavStage stage[kWarpsB];
-  load_nav_tables(T, gm);
-  __syncthreads();
-  const NavModel M = make_nav(gm, &T, plan_step);
+// Phase B for one warp: takes 32-item chunks of the item list from
+// chunk_head (staged in st), rolls each item out with lane refill, and adds
+// each value to its child's l sum in jobs[job].
+__device__ __forceinline__ void nav_rollout_warp(const NavModel& M, const NavTables& T, NavStage& st,
+                                                 const NavItems& items, unsigned int* chunk_head,
+                                                 const dsp_leaf_job* jobs, unsigned long long& steps) {
   const int lane = threadIdx.x & 31;
-  NavStage& st = stage[threadIdx.x >> 5];
   const uint32_t lt = lanemask_lt();
   const long long nchunks = (items.total + 31) >> 5;
   // warp-uniform: buffer in use, items handed out of it, its size, the next's size
@@ -210,7 +218,6 @@ __global__ void __launch_bounds__(256, 4) nav_rollout_items_kernel(const DevMode
   uint32_t last = 0, slot = 0, job = 0;
   int t = 0, t0 = 0;
   float v = 0.0f;
-  unsigned long long steps = 0;
   while (true) {
     // idle lanes take the next items, in lane order
     uint32_t idle = __ballot_sync(0xFFFFFFFFu, !have);
@@ -263,8 +270,78 @@ __global__ void __launch_bounds__(256, 4) nav_rollout_items_kernel(const DevMode
       have = false;
     }
   }
+}
+
+__global__ void __launch_bounds__(256, 4) nav_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                                const dsp_leaf_job* __restrict__ jobs,
+                                                                NavItems items, unsigned int* chunk_head,
+                                                                uint32_t plan_step) {
+  __shared__ NavTables T;
+  __shared__ NavStage stage[kWarpsB];
+  load_nav_tables(T, gm);
+  __syncthreads();
+  const NavModel M = make_nav(gm, &T, plan_step);
+  const int lane = threadIdx.x & 31;
+  unsigned long long steps = 0;
+  nav_rollout_warp(M, T, stage[threadIdx.x >> 5], items, chunk_head, jobs, steps);
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
+// Persistent queue kernel of navigation: a CTA claims a published job, runs
+// phase A for each of its actions (nav_unit) into the slot's item list, then
+// its warps roll the job's items out (nav_rollout_warp, chunks taken from a
+// shared counter), and it publishes the job done. Idle CTAs back off and exit
+// after idle_ns without a job; the host relaunches the kernel when jobs come.
+struct NavQueueSmem {
+  NavUnitSmem u;
+  NavStage stage[kWarpsB];
+  unsigned int chunk_head;
+  long long ticket;
+  unsigned int plan_step;
+  int exit;
+};
+
+__global__ void __launch_bounds__(256, 2) nav_queue_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                          QueueRing ring, unsigned long long* head,
+                                                          uint32_t* scratch, size_t slot_words, dsp_leaf_job* jcopy,
+                                                          unsigned long long idle_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  NavQueueSmem& Q = *reinterpret_cast<NavQueueSmem*>(smem_raw);
+  NavUnitSmem& S = Q.u;
+  load_nav_tables(S.T, gm);
+  NavModel M = make_nav(gm, &S.T, 0u);
+  const int tid = threadIdx.x;
+  unsigned long long steps = 0, last_work = qring::now_ns();
+  unsigned int backoff = 256;
+  __syncthreads();
+  while (true) {
+    if (tid < 32) {
+      const long long t = qring::take_job(ring, head, &S.job, jcopy, &Q.plan_step);
+      if (tid == 0) {
+        Q.ticket = t;
+        Q.chunk_head = 0;
+      }
+    }
+    __syncthreads();
+    const long long ticket = Q.ticket;
+    if (ticket >= 0) {
+      const int slot = (int)(ticket % ring.cap);
+      M.plan_step = Q.plan_step;
+      const NavItems items{scratch + (size_t)slot * slot_words, (long long)S.job.n_scen * S.job.n_actions};
+      for (int ao = 0; ao < S.job.n_actions; ++ao)
+        nav_unit(S, M, ao, (long long)ao * S.job.n_scen, 0, items, work, steps);
+      nav_rollout_warp(M, S.T, Q.stage[tid >> 5], items, &Q.chunk_head, jcopy + slot, steps);
+      __threadfence();  // every thread's sums, before the job is published done
+      __syncthreads();
+      if (tid == 0) qring::finish_job(ring, (unsigned long long)ticket);
+    }
+    if (tid == 0) Q.exit = qring::idle_exit(ring, ticket >= 0, last_work, backoff, idle_ns);
+    __syncthreads();
+    if (Q.exit) break;
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if ((tid & 31) == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
 // dsp_step: one g call per scenario.
@@ -330,6 +407,42 @@ cudaError_t launch_nav_expand(dsp_model* m, const dsp_leaf_job* djobs, const int
   const int grid_b = (int)std::max(
       1LL, std::min((warps + kWarpsB - 1) / kWarpsB, (long long)std::max(1, per_sm_b) * m->num_sms));
   nav_rollout_items_kernel<<<grid_b, 32 * kWarpsB, 0, st>>>(m->dmodel, m->dwork, djobs, it, counters + 1, m->plan_step);
+  return cudaGetLastError();
+}
+
+cudaError_t nav_queue_setup(int* per_sm) {
+  const size_t smem = sizeof(NavQueueSmem);
+  cudaError_t e = cudaFuncSetAttribute(nav_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, nav_queue_kernel, 256, smem);
+  return e;
+}
+
+size_t nav_queue_slot_words(const dsp_model* m) {
+  return (size_t)kNavItemWords * (size_t)kMaxScen * (size_t)m->host->num_actions;
+}
+
+cudaError_t launch_nav_queue(dsp_model* m, QueueRing ring, unsigned long long* head, uint32_t* scratch,
+                             size_t slot_words, dsp_leaf_job* jcopy, unsigned long long idle_ns, int grid,
+                             cudaStream_t st) {
+  nav_queue_kernel<<<grid, 256, sizeof(NavQueueSmem), st>>>(m->dmodel, m->dwork, ring, head, scratch, slot_words,
+                                                            jcopy, idle_ns);
+  return cudaGetLastError();
+}
+
+// The navigation default policy per state: it reads only the last reading,
+// kept in counter 0 of the history.
+__global__ void nav_policy_kernel(const DevModel* __restrict__ gm, const int8_t* __restrict__ hist, int count,
+                                  int32_t* __restrict__ actions) {
+  __shared__ NavTables T;
+  load_nav_tables(T, gm);
+  __syncthreads();
+  const NavModel M = make_nav(gm, &T, 0u);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) actions[i] = M.policy((uint32_t)(uint8_t)hist[32 * (size_t)i]);
+}
+
+cudaError_t launch_nav_policy(const DevModel* gm, const int8_t* hist, int count, int32_t* actions, cudaStream_t st) {
+  nav_policy_kernel<<<(count + 255) / 256, 256, 0, st>>>(gm, hist, count, actions);
   return cudaGetLastError();
 }
 

@@ -1,12 +1,14 @@
 // Device job queue of leaf expansions (host side). Many search threads submit
 // leaf jobs of uneven |Phi_b| into a ring in mapped pinned host memory; one
-// persistent kernel (rs_queue_kernel), launched from a CUDA graph, pulls them
-// (node-level parallelism of Sec. III-D with the per-leaf launches replaced by
-// one resident kernel). A monitor thread relaunches the kernel whenever jobs
-// are pending and it has exited after idling; every wait, on the host and on
-// the device, is bounded.
+// persistent kernel of the model's kind (rs_queue_kernel, car_queue_kernel,
+// nav_queue_kernel), launched from a CUDA graph, pulls them (node-level
+// parallelism of Sec. III-D with the per-leaf launches replaced by one
+// resident kernel). A monitor thread relaunches the kernel whenever jobs are
+// pending and it has exited after idling; every wait, on the host and on the
+// device, is bounded.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -34,7 +36,8 @@ struct dsp_queue {
   dsp_leaf_job* d_jcopy = nullptr;       // device: one job copy per ring slot
   dsp::QueueShare* d_share = nullptr;    // device: work sharing per ring slot
   unsigned long long* d_finished = nullptr;  // device: jobs completed
-  size_t slot_words = 0;
+  size_t slot_words = 0;                 // per-slot rollout items (Rock Sample, navigation)
+  size_t scratch_words = 0;              // all of d_scratch
   int grid = 0;
   unsigned long long idle_ns = 0;
   cudaStream_t stream = nullptr;
@@ -60,10 +63,16 @@ dsp_status build_graph(dsp_queue* q) {
   cudaGraph_t g;
   cudaError_t e = cudaStreamBeginCapture(q->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_queue: begin capture");
-  cudaError_t el = launch_rs_queue(q->m->dmodel, q->m->host->robots, rs_key_words(q->m->host), q->m->dwork,
-                                   q->ring, q->d_head,
-                                   q->d_scratch, q->slot_words, q->d_jcopy, q->idle_ns, q->grid,
-                                   q->stream);
+  cudaError_t el;
+  const int kind = q->m->host->kind;
+  if (kind == DSP_MODEL_CAR)
+    el = launch_car_queue(q->m, q->ring, q->d_head, q->d_scratch, q->d_jcopy, q->idle_ns, q->grid, q->stream);
+  else if (kind == DSP_MODEL_NAV)
+    el = launch_nav_queue(q->m, q->ring, q->d_head, q->d_scratch, q->slot_words, q->d_jcopy, q->idle_ns, q->grid,
+                          q->stream);
+  else
+    el = launch_rs_queue(q->m->dmodel, q->m->host->robots, rs_key_words(q->m->host), q->m->dwork, q->ring,
+                         q->d_head, q->d_scratch, q->slot_words, q->d_jcopy, q->idle_ns, q->grid, q->stream);
   e = cudaStreamEndCapture(q->stream, &g);
   if (el != cudaSuccess) return cuda_fail(el, "dsp_queue: capture launch");
   if (e != cudaSuccess) return cuda_fail(e, "dsp_queue: end capture");
@@ -112,8 +121,6 @@ extern "C" {
 dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, dsp_queue** out) {
   if (!m || !out) return fail(DSP_E_INVALID, "dsp_queue_create: NULL argument");
   *out = nullptr;
-  if (m->host->kind != DSP_MODEL_GRID && m->host->kind != DSP_MODEL_MULTIGRID)
-    return fail(DSP_E_UNSUPPORTED, "dsp_queue_create: Rock Sample models only");
   if (capacity < 1 || capacity > (1 << 20)) return fail(DSP_E_INVALID, "dsp_queue_create: capacity %d", capacity);
   if (idle_ns == 0) idle_ns = 2000000ull;
   dsp_queue* q = new dsp_queue();
@@ -144,15 +151,33 @@ dsp_status dsp_queue_create(dsp_model* m, int32_t capacity, uint64_t idle_ns, ds
     q->ring.plan_step = (unsigned int*)(q->ring.jobs + capacity);
     q->ring.close = q->ring.plan_step + capacity;
     q->ring.cap = capacity;
-    q->grid = rs_queue_blocks_per_sm(m->host->robots, rs_key_words(m->host)) * m->num_sms;
-    q->slot_words = rs_queue_slot_words(m->host->robots, m->host->num_actions);
-    e = cudaMalloc(&q->d_head, sizeof(unsigned long long));
+    // the kernel's CTAs per SM (its shared-memory limit is set here, before
+    // any capture) and its scratch: per ring slot (Rock Sample, navigation:
+    // one job's rollout items) or per CTA (car: one observation scratch)
+    size_t scratch_words = 0;
+    int per_sm = 1;
+    if (m->host->kind == DSP_MODEL_CAR) {
+      e = car_queue_setup(m, &per_sm);
+      q->grid = std::max(1, per_sm) * m->num_sms;
+      scratch_words = car_queue_scratch_words(q->grid);
+    } else if (m->host->kind == DSP_MODEL_NAV) {
+      e = nav_queue_setup(&per_sm);
+      q->grid = std::max(1, per_sm) * m->num_sms;
+      q->slot_words = nav_queue_slot_words(m);
+      scratch_words = q->slot_words * (size_t)capacity;
+    } else {
+      q->grid = rs_queue_blocks_per_sm(m->host->robots, rs_key_words(m->host)) * m->num_sms;
+      q->slot_words = rs_queue_slot_words(m->host->robots, m->host->num_actions);
+      scratch_words = q->slot_words * (size_t)capacity;
+    }
+    q->scratch_words = scratch_words;
+    if (e == cudaSuccess) e = cudaMalloc(&q->d_head, sizeof(unsigned long long));
   }
   if (e == cudaSuccess) e = cudaMemset(q->d_head, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&q->d_finished, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(q->d_finished, 0, sizeof(unsigned long long));
   q->ring.finished = q->d_finished;
-  if (e == cudaSuccess) e = cudaMalloc(&q->d_scratch, sizeof(uint32_t) * q->slot_words * (size_t)capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_scratch, sizeof(uint32_t) * q->scratch_words);
   if (e == cudaSuccess) e = cudaMalloc(&q->d_jcopy, sizeof(dsp_leaf_job) * (size_t)capacity);
   if (e == cudaSuccess) e = cudaMalloc(&q->d_share, sizeof(dsp::QueueShare) * (size_t)capacity);
   if (e == cudaSuccess) {

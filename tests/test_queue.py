@@ -114,6 +114,54 @@ def test_queue_two_robots_sixteen_producers_oracle(env):
     m.close()
 
 
+@pytest.mark.parametrize("mk,njobs,threads", [(I.car50, 24, 8), (lambda: I.car_p(6), 16, 4), (I.nav13, 32, 16)])
+def test_queue_car_and_navigation_oracle(env, mk, njobs, threads):
+    """The car among 50 and 6 pedestrians and navigation in a partially known
+    map through their own persistent queue kernels: host threads submit
+    leaves of uneven |Phi_b| (1..500); every job equals the oracle's expansion
+    (the car bit for bit in FP32, as the batch call) and the batch call's."""
+    torch, _dsp, batch = env
+    cfg = mk()
+    m = batch.Model(cfg)
+    jobs = I.job_stream(cfg, njobs, 19)
+    ref = batch.JobBatch(m, jobs)
+    ref.run()
+    torch.cuda.synchronize()
+    out = batch.JobBatch(m, jobs)
+    q = _dsp.dsp_queue_create(m.h, 16)
+    _run_threads(_dsp, q, out, threads)
+    launches, submitted = _dsp.dsp_queue_stats(q)
+    _dsp.dsp_queue_destroy(q)
+    assert submitted == njobs and launches >= 1
+    _, status = m.counters()
+    assert status == 0
+    got = out.all_results()
+    for k, (a, b) in enumerate(zip(ref.all_results(), got)):
+        for f in FIELDS:
+            assert np.array_equal(a[f], b[f]), (k, f)
+    _cmp_oracle(cfg, m, jobs, got)
+    m.close()
+
+
+def test_queue_car_refuses_learned_policy(env):
+    torch, _dsp, batch = env
+    from paper_1802_06215_b300 import learn
+    import os
+    cfg = I.car50()
+    m = batch.Model(cfg)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    h, _ = learn.load_weights(os.path.join(root, "paper_1802_06215_b300", "weights", "car50_pi0.npz"))
+    _dsp.dsp_set_policy(m.h, h)
+    jb = batch.JobBatch(m, I.job_stream(cfg, 1, 3, max_scen=20))
+    q = _dsp.dsp_queue_create(m.h, 4)
+    with pytest.raises(_dsp.DspError) as e:
+        _dsp.dsp_queue_submit(q, jb.descs[0], 1000)
+    assert e.value.status == _dsp.DSP_E_UNSUPPORTED
+    _dsp.dsp_queue_destroy(q)
+    _dsp.dsp_mlp_destroy(h)
+    m.close()
+
+
 def test_queue_relaunch_after_idle(env):
     """With a 50 us idle limit the kernel's bounded wait runs out between
     bursts; the monitor relaunches it and every job still completes."""
@@ -153,11 +201,6 @@ def test_queue_rejects_bad_input(env):
         _dsp.dsp_queue_submit(q, bad, 1000)
     assert e.value.status in (_dsp.DSP_E_INVALID, _dsp.DSP_E_UNSUPPORTED)
     _dsp.dsp_queue_destroy(q)
-    car = batch.Model(I.car50())
-    with pytest.raises(_dsp.DspError) as e:
-        _dsp.dsp_queue_create(car.h, 8)
-    assert e.value.status == _dsp.DSP_E_UNSUPPORTED
-    car.close()
     m.close()
 
 
