@@ -170,11 +170,16 @@ dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t
  * kernel, launched from a CUDA graph, pulls leaf jobs that many host threads
  * submit). Jobs go into a ring of `capacity` slots in mapped pinned host
  * memory; the kernel takes them in ticket order, expands each (same results
- * as dsp_expand_leaves; a job's rollouts are shared by every CTA of the grid)
- * and marks it done; it exits after idle_ns nanoseconds
+ * as dsp_expand_leaves) and marks it done; it exits after idle_ns nanoseconds
  * without a job (0 = 2 ms) and a monitor thread relaunches it when jobs are
- * pending. Rock Sample models only (DSP_E_UNSUPPORTED for the car). All job
- * pointers are device memory. submit and wait are thread-safe. */
+ * pending. Every model has its kernel: Rock Sample (a job's phase A on the
+ * CTA that claims it, its rollout chunks shared by every CTA of the grid),
+ * navigation (phase A and the job's rollouts on the claiming CTA) and the car
+ * (the job's actions as units on the claiming CTA, lanes per scenario as the
+ * expansion's default). Jobs of at most 512 scenarios (DSP_E_UNSUPPORTED
+ * above); the kernels roll out the heuristic policy (DSP_E_UNSUPPORTED at
+ * submit while a learned policy is set). All job pointers are device memory.
+ * submit and wait are thread-safe. */
 typedef struct dsp_queue dsp_queue;
 dsp_status dsp_queue_create(dsp_model* model, int32_t capacity, uint64_t idle_ns, dsp_queue** out);
 /* Publishes one job (copied, with the model's plan step at this moment: the
@@ -201,7 +206,7 @@ typedef struct {
   double target_gap;     /* stop once the root gap U - L is at most this */
   int32_t deterministic; /* 1: rounds (select in thread order, one batched expansion, backups in thread order);
                             0: free-running threads, one CUDA stream each */
-  int32_t use_queue;     /* free running, Rock Sample: threads submit their leaves to one device job queue
+  int32_t use_queue;     /* free running: threads submit their leaves to one device job queue
                             (dsp_queue_*) instead of launching their own expansions; the model keeps that
                             queue (capacity max(64, 4 x threads)) until dsp_destroy_model */
   int32_t tree_lock;     /* free running: 0 = select and back up on per-node atomics without a lock (a leaf
@@ -465,6 +470,19 @@ dsp_status dsp_set_policy(dsp_model* model, const dsp_mlp* mlp);
 dsp_status dsp_rollout_logged(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
                               const int8_t* hist, int32_t start_depth, float* value, int32_t* actions,
                               float* logits, void* stream);
+
+/* The hand-written default policy pi0 of the model's rollouts (Sec. III-D,
+ * Eq. lb) per state, and the learned policy's allowed actions, on the GPU,
+ * so that training code labels states with the very functions the rollouts
+ * run. block: device state block of capacity cap; hist: device count x 32
+ * belief counters (Rock Sample; navigation: counter 0 holds the last
+ * reading; may be NULL for the car); actions (device, count int32) gets the
+ * action (two robots: the joint action a0 * (5 + m) + a1); allowed (device,
+ * count uint32, may be NULL; one-robot Rock Sample only, DSP_E_UNSUPPORTED
+ * otherwise) gets bit a set for every action the learned policy may take
+ * and bit |A| (defer). Asynchronous on `stream`. */
+dsp_status dsp_default_policy(const dsp_model* model, const uint32_t* block, int32_t cap, int32_t count,
+                              const int8_t* hist, int32_t* actions, uint32_t* allowed, void* stream);
 
 /* Policy features (the learned policy's input, the same function the learned
  * rollout evaluates): out (device, count x 64 FP32, 16-byte aligned); block:

@@ -295,6 +295,19 @@ def features_car(model, block):
     return out
 
 
+def learned_allowed(model, block, hist):
+    """Bits of the actions the learned policy may take per one-robot Rock
+    Sample state (bit |A|, defer, always set)."""
+    block = np.ascontiguousarray(block, np.uint32)
+    w, cap = block.shape
+    h = None if hist is None else np.ascontiguousarray(hist, np.int8).reshape(cap, 32)
+    out = np.zeros(cap, np.uint32)
+    rc = lib().orc_learned_allowed(C.byref(model.c), _p(block, _U32), C.c_int32(cap), C.c_int32(cap),
+                                   None if h is None else _p(h, _I8), _p(out, _U32))
+    assert rc == 0
+    return out
+
+
 def rollout_learned(model, block, hist, start_depth, weights, logged=None, tol=1e-2, want_logits=False):
     """Learned-policy rollout values (one-robot Rock Sample or the car); with `logged` actions
     (count x D) it replays them and returns, per scenario, the steps whose

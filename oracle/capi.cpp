@@ -493,6 +493,24 @@ static bool learned_allowed(const RockSample<float>& m, const RSState& s, const 
   return !((s.sampled >> i) & 1u) && h.c[i] < 3 && h.c[i] > -3;
 }
 
+// The learned policy's allowed actions per state of one-robot Rock Sample
+// (learned_allowed), as bits, with bit |A| (defer) always set.
+int32_t orc_learned_allowed(const orc_model* d, const uint32_t* block, int32_t cap, int32_t count,
+                            const int8_t* hist, uint32_t* bits) {
+  if (d->kind != 0) return 1;
+  RockSample<float> m = make_rs<float>(d);
+  const int na = m.num_actions();
+  for (int i = 0; i < count; ++i) {
+    RSState s = m.unpack(block, cap, i);
+    Hist h = hist_from(hist ? hist + 32 * (size_t)i : nullptr);
+    uint32_t b = 1u << na;
+    for (int a = 0; a < na; ++a)
+      if (learned_allowed(m, s, h, a)) b |= 1u << a;
+    bits[i] = b;
+  }
+  return 0;
+}
+
 // Default-policy rollout (Eq. lb) of one-robot Rock Sample with the learned
 // policy: at every step the features of (state, counters) go through the
 // network in its BF16/FP32 form; the argmax of logits 0..|A| over the allowed

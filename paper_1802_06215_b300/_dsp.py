@@ -450,6 +450,32 @@ def dsp_set_policy(model_h, mlp_h):
     check(L.dsp_set_policy(model_h, mlp_h))
 
 
+def default_policy(model_h, block, hist=None, want_allowed=False):
+    """dsp_default_policy on host arrays: block (words, count) uint32, hist
+    (count, 32) int8 or None. Returns actions (count,) int32 and, with
+    want_allowed, the allowed-action bits (count,) uint32."""
+    import numpy as np
+    import torch
+    b = np.ascontiguousarray(block, dtype=np.uint32)
+    count = b.shape[1]
+    bd = torch.tensor(b.view(np.int32), device="cuda")
+    hd = None if hist is None else torch.tensor(np.ascontiguousarray(hist, dtype=np.int8).reshape(count, 32),
+                                                 device="cuda")
+    act = torch.zeros(count, dtype=torch.int32, device="cuda")
+    al = torch.zeros(count, dtype=torch.int32, device="cuda") if want_allowed else None
+    L = lib()
+    L.dsp_default_policy.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
+    st = torch.cuda.current_stream().cuda_stream
+    check(L.dsp_default_policy(model_h, C.c_void_p(bd.data_ptr()), count, count,
+                               C.c_void_p(hd.data_ptr() if hd is not None else None), C.c_void_p(act.data_ptr()),
+                               C.c_void_p(al.data_ptr() if al is not None else None), C.c_void_p(st)))
+    torch.cuda.synchronize()
+    if want_allowed:
+        return act.cpu().numpy(), al.cpu().numpy().view(np.uint32)
+    return act.cpu().numpy()
+
+
 def dsp_rollout_logged(model_h, block_ptr, cap, count, hist_ptr, start_depth, value_ptr, actions_ptr=0, stream=0,
                        logits_ptr=0):
     """dsp_rollout with the learned policy; actions (device count x D int32)

@@ -290,6 +290,20 @@ __global__ void car_features_kernel(const DevModel* __restrict__ gm, const uint3
   }
 }
 
+// The car's hand-written default policy per state (kTPS lanes per state).
+__global__ void car_policy_kernel(const DevModel* __restrict__ gm, const uint32_t* __restrict__ block, int cap,
+                                  int count, int32_t* __restrict__ actions) {
+  __shared__ CarShared c;
+  load_car_consts(c, gm);
+  __syncthreads();
+  const CarModel<kTPS> M = make_car_model<kTPS>(gm, &c, 0u);
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) / kTPS;
+  CarLane<kTPS> L;
+  M.load(L, block, cap, i < count ? i : 0);
+  const int a = M.policy(L, M.danger_now(L));
+  if (i < count && M.gl == 0) actions[i] = a;
+}
+
 template <bool kExpand>
 cudaError_t launch_car_mlp(const dsp_model* m, const CarItemSource& src, long long total, cudaStream_t st) {
   size_t smem = sizeof(CarTcSmem);
@@ -332,6 +346,13 @@ cudaError_t launch_car_features(const dsp_model* m, const uint32_t* block, int c
                                 cudaStream_t st) {
   const int threads = 256, per = threads / kTPS;
   car_features_kernel<<<(count + per - 1) / per, threads, 0, st>>>(m->dmodel, block, cap, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_car_policy(const dsp_model* m, const uint32_t* block, int cap, int count, int32_t* actions,
+                              cudaStream_t st) {
+  const int threads = 256, per = threads / kTPS;
+  car_policy_kernel<<<(count + per - 1) / per, threads, 0, st>>>(m->dmodel, block, cap, count, actions);
   return cudaGetLastError();
 }
 

@@ -456,9 +456,31 @@ cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const
                                         const void* policy, uint32_t plan_step, int num_sms, cudaStream_t st) {
   ItemSource src{};
   src.jobs = jobs;
-  src.items = Items<1>{item_buf, total_items};
+  src.items = Items<1>{item_buf, total_items, true};
   src.next = counter;
   return launch_mlp<true>(gm, work, (const uint8_t*)policy, src, plan_step, num_sms, total_items, st);
+}
+
+// The hand-written default policy of Rock Sample per state (the joint
+// action for two robots) and, for one robot, the learned policy's allowed
+// actions with the defer column.
+template <int R>
+__global__ void rs_policy_kernel(const DevModel* __restrict__ gm, const uint32_t* __restrict__ block, int cap,
+                                 int count, const int8_t* __restrict__ hist, int32_t* __restrict__ actions,
+                                 uint32_t* __restrict__ allowed) {
+  __shared__ RSShared c;
+  load_rs_consts(c, gm);
+  __syncthreads();
+  const RSModel<R> M = make_rs<R>(gm, &c, 0u);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const RSS s = M.load(block, cap, i);
+  uint32_t h[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) h[k] = hist ? *reinterpret_cast<const uint32_t*>(hist + 32 * (size_t)i + 4 * k) : 0u;
+  actions[i] = M.policy(s, positive_mask(h, M.m));
+  if (R == 1 && allowed)
+    allowed[i] = learned_allow(c, M.n, M.m, s.pos[0], s.sampled, h) | (1u << gm->num_actions);
 }
 
 __global__ void features_kernel(const DevModel* __restrict__ gm, const uint32_t* __restrict__ block, int cap,
@@ -494,6 +516,32 @@ dsp_status dsp_features(const dsp_model* m, const uint32_t* block, int32_t cap, 
   features_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m->dmodel, block, cap, count, hist, out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_features");
+}
+
+dsp_status dsp_default_policy(const dsp_model* m, const uint32_t* block, int32_t cap, int32_t count,
+                              const int8_t* hist, int32_t* actions, uint32_t* allowed, void* stream) {
+  if (!m) return fail(DSP_E_INVALID, "dsp_default_policy: model is NULL");
+  const int kind = m->host->kind;
+  if (count < 0 || cap < count || (count > 0 && (!actions || (kind != DSP_MODEL_NAV && !block) ||
+                                                 (kind == DSP_MODEL_NAV && !hist))))
+    return fail(DSP_E_INVALID, "dsp_default_policy: bad buffers");
+  if (allowed && kind != DSP_MODEL_GRID)
+    return fail(DSP_E_UNSUPPORTED, "dsp_default_policy: allowed actions are one-robot Rock Sample's");
+  if (count == 0) return DSP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (kind == DSP_MODEL_CAR) {
+    e = launch_car_policy(m, block, cap, count, actions, st);
+  } else if (kind == DSP_MODEL_NAV) {
+    e = launch_nav_policy(m->dmodel, hist, count, actions, st);
+  } else if (kind == DSP_MODEL_GRID) {
+    rs_policy_kernel<1><<<(count + 255) / 256, 256, 0, st>>>(m->dmodel, block, cap, count, hist, actions, allowed);
+    e = cudaGetLastError();
+  } else {
+    rs_policy_kernel<2><<<(count + 255) / 256, 256, 0, st>>>(m->dmodel, block, cap, count, hist, actions, nullptr);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_default_policy");
 }
 
 dsp_status dsp_set_policy(dsp_model* m, const dsp_mlp* mlp) {

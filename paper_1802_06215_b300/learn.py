@@ -48,19 +48,18 @@ SENSE0 = 5                 # first Sense action of one-robot Rock Sample
 SAMPLE = 4
 
 
-def sensor_accuracy(d):
-    return 0.5 + 0.5 * 2.0 ** (-d / 20.0)
-
-
 class Belief:
     """Belief of one-robot Rock Sample: observed position and sampled mask,
     independent posteriors P(rock i good), and the belief counters (sensed good
-    minus sensed bad per rock) that the planner and the policies read."""
+    minus sensed bad per rock) that the planner and the policies read. The
+    sensor's accuracy at squared distance d2 is thresh[d2] / 2^32, from the
+    sensor table the model's kernels read (dsp_get_table)."""
 
-    def __init__(self, cfg, pos_word, sampled=0):
+    def __init__(self, cfg, pos_word, thresh, sampled=0):
         self.cfg = cfg
         self.pos = int(pos_word)
         self.sampled = int(sampled)
+        self.thresh = np.asarray(thresh)
         self.p = np.full(cfg.m, 0.5)
         self.hist = np.zeros(32, np.int8)
 
@@ -82,7 +81,8 @@ class Belief:
             if z in (1, 2):
                 x, y = self.pos & 0xFF, (self.pos >> 8) & 0xFF
                 c = int(self.cfg.rock_cells[r])
-                q = sensor_accuracy(math.hypot((c & 0xFF) - x, (c >> 8) - y))
+                d2 = ((c & 0xFF) - x) ** 2 + ((c >> 8) - y) ** 2
+                q = float(self.thresh[d2]) / 4294967296.0
                 like_good, like_bad = (q, 1 - q) if z == 1 else (1 - q, q)
                 p = self.p[r]
                 self.p[r] = p * like_good / (p * like_good + (1 - p) * like_bad)
@@ -109,7 +109,7 @@ def episode(model, cfg, world_seed, steps, seconds, threads=4, min_scen=16, node
     rng = np.random.default_rng([world_seed, 0xBE11EF])
     world = inputs.rs_block(cfg, 1, rng, pos=[(0, cfg.n // 2)])
     world[4] = 0
-    belief = Belief(cfg, world[0, 0])
+    belief = Belief(cfg, world[0, 0], model.table(0))
     ret, disc = 0.0, 1.0
     roots, states, hists, labels, decisions, gaps = [], [], [], [], 0, []
     t_plan, expansions, scen_steps = 0.0, 0, 0
@@ -231,48 +231,27 @@ def accuracy(h, X, Y, n_actions, batch_size):
     return hits / max(len(Y), 1)
 
 
-def allowed_mask(cfg, pos, sampled, hist):
+def _rs_block(pos, sampled):
+    """State block of one-robot Rock Sample states given their positions and
+    sampled masks (the other fields do not enter the policies)."""
+    b = np.zeros((5, len(pos)), np.uint32)
+    b[0] = pos
+    b[3] = sampled
+    return b
+
+
+def allowed_mask(model, cfg, pos, sampled, hist):
     """(count, |A| + 1) bool: the actions the learned policy may take (the
-    same rule the learned rollout applies): no move off the N, S or W border,
-    no Sample off an unsampled rock, no Sense of a sampled rock or of one whose
-    counter reads +-3; East and column |A| (defer to the heuristic) always."""
-    n, m = cfg.n, cfg.m
-    x, y = (pos & 0xFF).astype(np.int64), ((pos >> 8) & 0xFF).astype(np.int64)
-    cnt = len(pos)
-    al = np.zeros((cnt, 6 + m), bool)
-    al[:, 5 + m] = True
-    al[:, 0] = y < n - 1
-    al[:, 1] = True
-    al[:, 2] = y > 0
-    al[:, 3] = x > 0
-    cells = np.asarray(cfg.rock_cells, np.int64)
-    samp = (sampled[:, None].astype(np.int64) >> np.arange(m)) & 1
-    on = (cells[None, :] & 0xFF) == x[:, None]
-    on &= (cells[None, :] >> 8) == y[:, None]
-    al[:, 4] = (on & (samp == 0)).any(axis=1)
-    h = hist[:, :m].astype(np.int64)
-    al[:, 5:5 + m] = (samp == 0) & (h < 3) & (h > -3)
-    return al
+    library's own rule, as the learned rollout applies it; column |A| defers
+    to the heuristic)."""
+    _, bits = _dsp.default_policy(model.h, _rs_block(pos, sampled), hist, want_allowed=True)
+    return ((bits[:, None].astype(np.uint64) >> np.arange(6 + cfg.m, dtype=np.uint64)) & 1).astype(bool)
 
 
-def heuristic_action(cfg, pos, sampled, hist):
-    """The hand-written default policy's action (one robot): Sample a
-    believed-good (counter > 0, unsampled) rock underfoot, else step towards
-    the nearest one (Manhattan, lowest index on ties, x before y), else E."""
-    m = cfg.m
-    x, y = (pos & 0xFF).astype(np.int64), ((pos >> 8) & 0xFF).astype(np.int64)
-    cells = np.asarray(cfg.rock_cells, np.int64)
-    rx, ry = cells & 0xFF, cells >> 8
-    samp = (sampled[:, None].astype(np.int64) >> np.arange(m)) & 1
-    believed = (hist[:, :m].astype(np.int64) > 0) & (samp == 0)
-    d = np.abs(rx[None, :] - x[:, None]) + np.abs(ry[None, :] - y[:, None])
-    d = np.where(believed, d, 1 << 30)
-    best = np.argmin(d, axis=1)
-    bd = d[np.arange(len(pos)), best]
-    tx, ty = rx[best], ry[best]
-    a = np.where(tx > x, 1, np.where(tx < x, 3, np.where(ty > y, 0, 2)))
-    a = np.where(bd == 0, 4, a)
-    return np.where(bd >= (1 << 30), 1, a).astype(np.int32)
+def heuristic_action(model, pos, sampled, hist):
+    """The hand-written default policy's action (one robot), computed by the
+    library's rollout policy."""
+    return _dsp.default_policy(model.h, _rs_block(pos, sampled), hist)
 
 
 def counter_posterior(c, q=0.85):
@@ -294,8 +273,8 @@ def q_labels(model, cfg, pos, sampled, hist, depth, rng, Kq=128, chunk=2048, thr
     na = 5 + m_
     labels = np.zeros(len(pos), np.int32)
     margin = np.zeros(len(pos))
-    al = allowed_mask(cfg, pos, sampled, hist)[:, :na]
-    ha = heuristic_action(cfg, pos, sampled, hist)
+    al = allowed_mask(model, cfg, pos, sampled, hist)[:, :na]
+    ha = heuristic_action(model, pos, sampled, hist)
     bits = np.arange(m_, dtype=np.uint32)
     for s0 in range(0, len(pos), chunk):
         jobs = []
@@ -502,20 +481,10 @@ def run_episodes(cfg, world_seeds, steps, seconds, policy=None, threads=4, round
 
 # ---------------------------------------------------------------- the car ----
 
-def car_heuristic_action(cfg, block):
-    """The car's hand-written default policy on a state block: Decelerate (2)
-    when a pedestrian is within 4 m ahead in the 2 m corridor, else Accelerate
-    (0) below 3 m/s, else Maintain (1)."""
-    P = cfg.P
-    s = block[0].view(np.float32)
-    v = (block[1] & 0xFF).astype(np.int64)
-    px = block[4:4 + P].view(np.float32)
-    py = block[4 + P:4 + 2 * P].view(np.float32)
-    cx = np.float32(-10.0) + s
-    ex = px - cx[None, :]
-    ey = py - np.float32(20.0)
-    danger = ((ex > 0) & (ex <= 4) & (ey >= -1) & (ey <= 1)).any(axis=0)
-    return np.where(danger, 2, np.where(v < 3, 0, 1)).astype(np.int32)
+def car_heuristic_action(model, block):
+    """The car's hand-written default policy on a state block, computed by
+    the library's rollout policy."""
+    return _dsp.default_policy(model.h, block)
 
 
 def car_states(cfg, count, rng):
@@ -550,7 +519,7 @@ def car_q_labels(model, cfg, block, depth, rng, Kq=64, chunk=1024, thr=2.0):
     heuristic's by more than thr."""
     n = block.shape[1]
     labels = np.zeros(n, np.int32)
-    ha = car_heuristic_action(cfg, block)
+    ha = car_heuristic_action(model, block)
     na = model.num_actions
     for s0 in range(0, n, chunk):
         jobs = []
