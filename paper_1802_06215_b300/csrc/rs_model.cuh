@@ -334,31 +334,55 @@ struct RSModel {
 
   // The same rollout for one robot with the state unpacked into registers.
   // The heuristic policy only moves and samples, and its moves never leave
-  // the map except E from the last column (the exit), so each step is one
-  // branch on the action: E while no believed-good unsampled rock is left,
-  // else a step toward the target (carried between steps, retaken after
-  // each sample: heuristic_step), or Sample on it. Rewards, their order and
-  // the step count are those of step() and policy().
+  // the map except E from the last column (the exit). With the target
+  // carried (heuristic_step), a rollout is a run of segments, each step of
+  // which is one g step: the moves toward the target, one cell per step, x
+  // before y (the direction along each axis is fixed for the segment), then
+  // Sample on it, which takes the rock out of the set and retakes the
+  // target; with no target left, E until the exit. Rewards, their order and
+  // the step count are those of step() and policy() at every step.
   __device__ __forceinline__ float rollout_one(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
     const uint32_t p0 = s.pos[0];
     int x = (int)(p0 & 0xFFu), y = (int)((p0 >> 8) & 0xFFu);
     bool ex = (p0 >> 16) & 1u;
     uint32_t good = s.good, cand = pmask & ~s.sampled;  // cand loses each sampled rock
-    int tx = 0, ty = 0;
-    uint32_t tbit = 0;
-    if (!ex && cand != 0) target(x, y, cand, tx, ty, tbit);
     float v = 0.0f;
     int t = t0;
     if (!ex) {
-      for (; t < D; ++t) {
-        const uint32_t before = cand;
-        const int r = heuristic_step(x, y, ex, tx, ty, tbit, good, cand);
-        if (r != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)r));
-        if (ex) {
-          ++t;
+      while (t < D) {
+        if (cand == 0) {
+          // E each step; from the last column E exits (+10)
+          while (t < D && x < n - 1) {
+            x += 1;
+            ++t;
+          }
+          if (t < D) {
+            v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], 10.0f));
+            ex = true;
+            ++t;
+          }
           break;
         }
-        if (cand != before && cand != 0) target(x, y, cand, tx, ty, tbit);
+        int tx, ty;
+        uint32_t tbit;
+        target(x, y, cand, tx, ty, tbit);
+        const int sx = tx > x ? 1 : -1, sy = ty > y ? 1 : -1;
+        // one move per step toward the target: x first, then y
+        while (t < D && x != tx) {
+          x += sx;
+          ++t;
+        }
+        while (t < D && y != ty) {
+          y += sy;
+          ++t;
+        }
+        if (t >= D) break;
+        // on the target's cell: Sample
+        const float r = (good & tbit) ? 10.0f : -10.0f;
+        good &= ~tbit;
+        cand &= ~tbit;
+        v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], r));
+        ++t;
       }
     }
     steps += (unsigned long long)(t - t0);

@@ -314,6 +314,32 @@ class Search {
     }
   }
 
+  // Whether a descent without any virtual loss would reach a leaf worth
+  // expanding (read-only). With several threads the stop rule asks it, so
+  // that the virtual loss of trials still selecting on other threads, which
+  // can make every branch look not worth it for a moment, never ends the
+  // search. (One thread has no such trials and keeps the plain rule, the
+  // rounds search's.)
+  bool leaf_left() const {
+    Node* b = root_;
+    while (true) {
+      if (!b->expanded.load(std::memory_order_acquire)) return b->depth < D_ && !b->term && !ld(b->claimed);
+      const int a = choose_action(b);
+      const double eps0 = ld(root_->U) - ld(root_->L);
+      Node* best = nullptr;
+      double beste = -std::numeric_limits<double>::infinity();
+      for (Node* c : b->q[a].ch) {
+        const double e = (ld(c->U) - ld(c->L)) - c->W * p_.xi * eps0;
+        if (e > beste) {
+          beste = e;
+          best = c;
+        }
+      }
+      if (best == nullptr || !(beste > 0)) return false;
+      b = best;
+    }
+  }
+
   void backup(Trial& t) {
     for (int i = (int)t.path.size() - 1; i >= 0; --i) {
       Node* b = t.path[i];
@@ -736,9 +762,11 @@ dsp_status Search::run_threads() {
         std::unique_lock<std::mutex> lock(tree_mu_, std::defer_lock);
         if (locked) lock.lock();
         backup(t);
-        // nothing left worth expanding: no expansion in flight and none
-        // published since this trial looked (else the tree changed: retry)
-        if (in_flight_.load() == 0 && t.epoch == published_.load()) stop = true;
+        // nothing left worth expanding: no expansion in flight, none
+        // published since this trial looked (else the tree changed: retry),
+        // and no leaf reachable without the other threads' virtual loss
+        if (in_flight_.load() == 0 && t.epoch == published_.load() && (p_.threads == 1 || !leaf_left()))
+          stop = true;
         if (gap_reached()) stop = true;
       }
       if (p_.time_limit_s > 0) {

@@ -167,6 +167,29 @@ def test_free_running_one_thread_is_the_rounds_search(env, tree_lock, launch_bat
     assert np.array_equal(g["root_visits"], o["root_na"])
 
 
+@pytest.mark.parametrize("name,cfg_fn", [
+    ("rs7_8", I.rs7_8),
+    ("car small", lambda: I.car_config(P=10, K=40, D=20, seed=2)),
+    ("navigation 13x13", lambda: I.nav_config(13, K=60, D=40, seed=2)),
+])
+def test_one_thread_through_queue_is_the_rounds_search(env, name, cfg_fn):
+    """One free-running thread whose leaves go through the device job queue
+    (each model's persistent kernel) builds the oracle's tree: equal digest,
+    bounds and visits."""
+    _dsp, batch = env
+    cfg = cfg_fn()
+    b = root_states(cfg, np.random.default_rng(7))
+    m = batch.Model(cfg)
+    p = _dsp.dsp_search_params(threads=1, rounds=12, time_limit_s=0.0, c_a=1.0, c_o=0.5, xi=0.95,
+                               target_gap=0.0, deterministic=0, use_queue=1)
+    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    m.close()
+    o = oracle.Model(cfg).plan(b, None, threads=1, rounds=12, c_a=1.0, c_o=0.5, xi=0.95, target_gap=0.0)
+    assert g["signature"] == o["signature"], name
+    assert g["root_u"] == o["root_u"] and g["root_l"] == o["root_l"], name
+    assert np.array_equal(g["root_visits"], o["root_na"]), name
+
+
 @pytest.mark.parametrize("tree_lock", [0, 1])
 @pytest.mark.parametrize("threads", [4, 16])
 def test_free_running_batched_launches_valid(env, threads, tree_lock):
