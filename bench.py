@@ -337,6 +337,8 @@ def learned_step(_dsp, batch, m, cfg, jobs, seconds, n_beliefs=32):
              "rs_group_kernel + rs_rollout_tc_kernel (learned-policy expansion of 256 jobs; tcgen05.mma BF16, TMEM "
              "accumulators)")
     peak = MEASURED.get("bf16_tflops")
+    if not car:
+        cmp_["training"] = training_step_rate(_dsp, na, peak)
     cmp_["weights"] = os.path.relpath(path, ROOT)
     cmp_["tensor_roofline"] = {
         "bound": "tensor", "achieved": tflops, "unit": "TFLOP/s", "peak": peak,
@@ -344,6 +346,30 @@ def learned_step(_dsp, batch, m, cfg, jobs, seconds, n_beliefs=32):
         "flop_per_scenario_step": flop, "scenario_steps": steps / 3, "kernel_ms_per_launch": kms / max(calls, 1),
         "kernel": kname}
     return cmp_
+
+
+def training_step_rate(_dsp, na, peak, batch=16384, steps=20):
+    """The policy network's training step (dsp_mlp_train_step: BF16 forward
+    and backward GEMMs with FP32 accumulation, softmax cross-entropy, Adam)
+    on random features and labels: samples/s and the GEMMs' rate against the
+    BF16 peak (6 B (64*256 + 256*256 + 256*32) flop per step)."""
+    import torch
+    h = _dsp.dsp_mlp_create(batch, 7)
+    X = torch.rand((batch, 64), dtype=torch.float32, device="cuda")
+    y = torch.randint(0, na + 1, (batch,), dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        _dsp.dsp_mlp_train_step(h, X.data_ptr(), y.data_ptr(), batch, na + 1, 1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _dsp.dsp_mlp_train_step(h, X.data_ptr(), y.data_ptr(), batch, na + 1, 1e-3)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    _dsp.dsp_mlp_destroy(h)
+    flop = 6 * batch * (64 * 256 + 256 * 256 + 256 * 32)
+    return {"batch": batch, "ms_per_step": dt * 1000.0, "samples_per_s": batch / dt,
+            "tflops": flop / dt / 1e12, "frac_of_bf16_peak": flop / dt / 1e12 / peak if peak else None,
+            "note": "wall time per step (the loss is read back every step); mma.sync 64x64 tiles"}
 
 
 def combine_ranks(t_ms, steps, dist, device):

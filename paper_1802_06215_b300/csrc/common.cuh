@@ -85,9 +85,43 @@ __device__ __forceinline__ U4 scen_random(uint64_t seed, uint32_t scen, uint32_t
                   (uint32_t)(seed >> 32));
 }
 
-// FP32 value -> int64 fixed point 2^-32, round to nearest even. x * 2^32 is
-// exact in FP32 (power-of-two scale), so this is the exact rounding of x.
-__device__ __forceinline__ long long to_fixed(float x) { return __float2ll_rn(__fmul_rn(x, 4294967296.0f)); }
+// FP32 value -> int64 fixed point 2^-32, round to nearest even: the exact
+// rounding of x * 2^32. Done on x's IEEE-754 fields with integer operations:
+// the float -> int64 conversion instruction runs on the FP64 pipe, which is
+// narrow on this part, and its result latency stalled the rollout warps.
+// A finite x = (-1)^s * M * 2^(E - 150) (M with its implicit one; E = 1 and
+// no implicit one for subnormals), so x * 2^32 = M * 2^(E - 118): a left
+// shift for E >= 118, else M / 2^r (r = 118 - E) rounded half to even, which
+// is 0 for r >= 25 (M < 2^24). |x| >= 2^31 (E >= 158, and inf and NaN) takes
+// the conversion instruction, whose saturation it keeps.
+__device__ __forceinline__ long long to_fixed(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const int E = (int)((b >> 23) & 0xFFu);
+  if (E >= 158) return __float2ll_rn(__fmul_rn(x, 4294967296.0f));
+  const uint32_t M = (b & 0x7FFFFFu) | (E ? 0x800000u : 0u);
+  const int e = E ? E : 1;
+  long long v;
+  if (e >= 118) {
+    v = (long long)M << (e - 118);
+  } else {
+    const int r = 118 - e;
+    uint32_t q = 0;
+    if (r < 25) {
+      q = M >> r;
+      const uint32_t rem = M & ((1u << r) - 1u), half = 1u << (r - 1);
+      q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+    }
+    v = (long long)q;
+  }
+  return (b >> 31) ? -v : v;
+}
+
+// Adds v to a child's fixed-point sum: a reduction on global memory with no
+// value returned, so the warp does not wait for it (atomicAdd through a
+// generic pointer becomes an atomic that returns the old value).
+__device__ __forceinline__ void sum_add(int64_t* p, long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ void report(DevWork* w, uint32_t bits) { atomicOr(&w->status, bits); }
 

@@ -266,7 +266,7 @@ __device__ __forceinline__ void nav_rollout_warp(const NavModel& M, const NavTab
     }
     if (have && (t >= M.D || s.term)) {
       const long long fl = to_fixed(v);
-      if (fl != 0) atomicAdd((unsigned long long*)(jobs[job].l_sum + slot), (unsigned long long)fl);
+      if (fl != 0) sum_add(jobs[job].l_sum + slot, fl);
       have = false;
     }
   }

@@ -588,20 +588,24 @@ __device__ __forceinline__ long long warp_sum64(long long x) {
   return (long long)h * 4294967296LL + (long long)b * 65536LL + (long long)a;
 }
 
-// Phase B for one 32-item chunk of the item list (one whole warp calls it).
+// Phase B for one 32-item chunk (one whole warp calls it), the lane's compact
+// item given (ok: the lane holds an item): u0 and the rollout, then the sums
+// into the children. The child's sum pointers are read from the job table
+// before the rollout, so their latency hides behind it.
 template <int R>
-__device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_leaf_job* __restrict__ jobs,
-                                                 Items<R> items, long long chunk, unsigned long long& steps) {
+__device__ __forceinline__ void rs_rollout_values(const RSModel<R>& M, const dsp_leaf_job* __restrict__ jobs, bool ok,
+                                                  const RSS& s, uint32_t pm, uint32_t meta, uint32_t job,
+                                                  unsigned long long& steps) {
   const int lane = threadIdx.x & 31;
   {
-    const long long it = chunk * 32 + lane;
-    const bool ok = it < items.total;
-    uint32_t job = 0xFFFFFFFFu, slot = 0;
+    uint32_t slot = 0;
     long long fu = 0, fl = 0;
+    int64_t* usum = nullptr;
+    int64_t* lsum = nullptr;
+    if (!ok) job = 0xFFFFFFFFu;
     if (ok) {
-      RSS s;
-      uint32_t pm, meta;  // compact items: pm is the candidate mask, sampled 0
-      items.get_compact((size_t)it, s, pm, meta, job);
+      usum = jobs[job].u_sum;
+      lsum = jobs[job].l_sum;
       slot = meta & 0xFFFFFFu;
       const int depth = (int)(meta >> 24);
       float u = 0.0f, v = 0.0f;
@@ -622,9 +626,8 @@ __device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_
       fu = warp_sum64(fu);
       fl = warp_sum64(fl);
       if (lane == 0 && ok) {
-        const dsp_leaf_job* J = jobs + job;
-        atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)fu);
-        atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)fl);
+        sum_add(usum + slot, fu);
+        sum_add(lsum + slot, fl);
       }
       return;
     }
@@ -642,34 +645,123 @@ __device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_
     }
     const bool last = lane == 31 || ((starts >> (lane + 1)) & 1u);
     if (ok && last) {
-      const dsp_leaf_job* J = jobs + job;
-      atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)fu);
-      atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)fl);
+      sum_add(usum + slot, fu);
+      sum_add(lsum + slot, fl);
     }
   }
 }
 
+// Phase B for one 32-item chunk of the item list read from global memory.
 template <int R>
-__global__ void __launch_bounds__(512, 4) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_leaf_job* __restrict__ jobs,
+                                                 Items<R> items, long long chunk, unsigned long long& steps) {
+  const long long it = chunk * 32 + (threadIdx.x & 31);
+  const bool ok = it < items.total;
+  RSS s;
+  uint32_t pm = 0, meta = 0, job = 0;  // compact items: pm is the candidate mask, sampled 0
+  if (ok) items.get_compact((size_t)it, s, pm, meta, job);
+  rs_rollout_values<R>(M, jobs, ok, s, pm, meta, job, steps);
+}
+
+// Per warp, two chunks of compact items in shared memory: the one being
+// rolled out and the next, copied in with cp.async meanwhile, so that a
+// chunk's item loads do not stall the warp (its rollouts are short now).
+template <int R>
+__device__ __forceinline__ void stage_items(uint32_t* buf, const Items<R>& items, long long chunk) {
+  constexpr int F = Items<R>::kCompactFields;
+  const int lane = threadIdx.x & 31;
+  const long long it = chunk * 32 + lane;
+  if (it < items.total)
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(buf + k * 32 + lane);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(items.f(k) + it) : "memory");
+    }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int R>
+constexpr size_t rs_stage_bytes(int block) {
+  return (size_t)(block / 32) * 2 * Items<R>::kCompactFields * 32 * sizeof(uint32_t);
+}
+__host__ __device__ constexpr size_t rs_key_bytes_aligned(size_t key_bytes) { return (key_bytes + 15) & ~(size_t)15; }
+
+template <int R>
+__global__ void __launch_bounds__(512, R == 1 ? 4 : 3) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                               const dsp_leaf_job* __restrict__ jobs,
                                                               Items<R> items, unsigned int* chunk_head,
                                                               uint32_t plan_step) {
   __shared__ RSShared c;
-  extern __shared__ uint16_t rs_keys[];
+  extern __shared__ __align__(16) uint16_t rs_keys[];
   load_rs_consts(c, gm);
   load_rs_keys(rs_keys, gm);
   __syncthreads();
   RSModel<R> M = make_rs<R>(gm, &c, plan_step);
   M.nkey = rs_keys;
+  constexpr int F = Items<R>::kCompactFields;
   const int lane = threadIdx.x & 31;
+  uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(rs_keys) +
+                                                rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)gm->m * gm->n * gm->n)) +
+                    (size_t)(threadIdx.x >> 5) * 2 * F * 32;
   const long long nchunks = (items.total + 31) >> 5;
   unsigned long long steps = 0;
-  while (true) {
-    long long chunk = 0;
-    if (lane == 0) chunk = (long long)atomicAdd(chunk_head, 1u);
-    chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
-    if (chunk >= nchunks) break;
-    rs_rollout_chunk<R>(M, jobs, items, chunk, steps);
+  // Chunks are claimed from one counter, kClaimBatch at a time: every warp of
+  // the grid draws from it, and one atomic per 32-item chunk came near the
+  // rate at which the memory system serves atomics on one address (the
+  // warps then queued on it). Lane 0 holds the rest of its batch. A chunk
+  // is claimed one step ahead of its staging: the claim for the chunk after
+  // next is made before a chunk's rollouts and read after them.
+  constexpr unsigned int kClaimBatch = 4;
+  unsigned int batch_next = 0, batch_left = 0;  // lane 0
+  auto next_chunk = [&]() {
+    if (batch_left == 0) {
+      batch_next = atomicAdd(chunk_head, kClaimBatch);
+      batch_left = kClaimBatch;
+    }
+    --batch_left;
+    return batch_next++;
+  };
+  auto claim = [&]() {
+    long long ch = 0;
+    if (lane == 0) ch = (long long)next_chunk();
+    return __shfl_sync(0xFFFFFFFFu, ch, 0);
+  };
+  long long cur = claim();
+  if (cur < nchunks) stage_items<R>(stage, items, cur);
+  long long nxt = cur < nchunks ? claim() : nchunks;
+  if (nxt < nchunks) stage_items<R>(stage + F * 32, items, nxt);
+  unsigned int pending = 0;  // lane 0: the claim in flight
+  if (nxt < nchunks && lane == 0) pending = next_chunk();
+  int b = 0;
+  while (cur < nchunks) {
+    if (nxt < nchunks)
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const uint32_t* w = stage + b * F * 32;
+    const bool ok = cur * 32 + lane < items.total;
+    RSS s;
+    s.pos[0] = w[lane];
+    s.pos[1] = R == 2 ? w[32 + lane] : 0u;
+    s.good = w[(R == 2 ? 2 : 1) * 32 + lane];
+    s.sampled = 0u;
+    s.scen = 0u;
+    const uint32_t cand = w[(R == 2 ? 3 : 2) * 32 + lane];
+    const uint32_t meta = w[(R == 2 ? 4 : 3) * 32 + lane];
+    const uint32_t job = w[(R == 2 ? 5 : 4) * 32 + lane];
+    __syncwarp();  // the buffer is read: the chunk after next may go there
+    cur = nxt;
+    b ^= 1;
+    if (cur < nchunks) {
+      // cur < nchunks: the claim issued one chunk ago names the chunk to stage now
+      nxt = (long long)__shfl_sync(0xFFFFFFFFu, pending, 0);
+      if (nxt < nchunks) {
+        stage_items<R>(stage + (b ^ 1) * F * 32, items, nxt);
+        if (lane == 0) pending = next_chunk();
+      }
+    }
+    rs_rollout_values<R>(M, jobs, ok, s, cand, meta, job, steps);
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);
@@ -785,7 +877,7 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
     return launch_rs_rollout_mlp_items(gm, work, jobs, item_buf, total_items, counters + 1, policy, plan_step,
                                        num_sms, st);
   // phase B keeps the policy-key table in shared memory (limit set by rs_set_key_smem)
-  const size_t key_bytes = sizeof(uint16_t) * (size_t)key_words;
+  const size_t key_bytes = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words) + rs_stage_bytes<R>(block_b);
   int per_sm_b = occupancy_cached(rs_rollout_items_kernel<R>, block_b, key_bytes);
   if (ctas_b > 0) per_sm_b = std::min(per_sm_b, ctas_b);
   long long chunks = (total_items + 31) / 32;
@@ -1072,11 +1164,13 @@ cudaError_t launch_rs_queue(const DevModel* gm, int robots, int key_words, DevWo
 }
 
 cudaError_t rs_set_key_smem(int robots, int key_words) {
-  const size_t bytes = sizeof(uint16_t) * (size_t)key_words;
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the key table and the item staging of the largest CTA (512 threads)
+  const size_t keys = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words);
   if (robots == 1)
-    return cudaFuncSetAttribute(rs_rollout_items_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaFuncSetAttribute(rs_rollout_items_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaFuncSetAttribute(rs_rollout_items_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(keys + rs_stage_bytes<1>(512)));
+  return cudaFuncSetAttribute(rs_rollout_items_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(keys + rs_stage_bytes<2>(512)));
 }
 
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, int key_words, DevWork* work,

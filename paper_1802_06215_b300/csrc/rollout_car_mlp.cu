@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) car_rollout_tc_kernel(const DevMo
         alive = true;
       } else if (M.gl == 0) {  // nothing to roll out (the car's tail value is zero)
         if (kExpand)
-          atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)to_fixed(v));
+          sum_add(J->l_sum + slot, to_fixed(v));
         else
           src.value[it] = v;
       }
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1) car_rollout_tc_kernel(const DevMo
       if (L.term || t >= M.D) {
         if (M.gl == 0) {
           if (kExpand)
-            atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)to_fixed(v));
+            sum_add(J->l_sum + slot, to_fixed(v));
           else
             src.value[item] = v;
         }

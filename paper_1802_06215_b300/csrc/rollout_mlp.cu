@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
       } else {
         if (!M.terminal(s)) v = __fadd_rn(v, __fmul_rn(S.c.G[M.D - t0], M.tail(s)));
         if (kExpand) {
-          atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)to_fixed(u));
-          atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)to_fixed(v));
+          sum_add(J->u_sum + slot, to_fixed(u));
+          sum_add(J->l_sum + slot, to_fixed(v));
         } else {
           src.value[it] = v;
         }
@@ -384,8 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
       if (M.terminal(s) || t >= M.D) {
         if (!M.terminal(s)) v = __fadd_rn(v, __fmul_rn(S.c.G[M.D - t0], M.tail(s)));
         if (kExpand) {
-          atomicAdd((unsigned long long*)(J->u_sum + slot), (unsigned long long)to_fixed(u));
-          atomicAdd((unsigned long long*)(J->l_sum + slot), (unsigned long long)to_fixed(v));
+          sum_add(J->u_sum + slot, to_fixed(u));
+          sum_add(J->l_sum + slot, to_fixed(v));
         } else {
           src.value[item] = v;
         }
