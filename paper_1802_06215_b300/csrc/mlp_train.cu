@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -36,22 +37,26 @@ namespace {
 
 constexpr int kTile = 64, kTileK = 32, kPad = 8;
 
-enum Epilogue { kStoreF32 = 0, kBiasReluBf16 = 1, kBiasF32 = 2, kMaskReluBf16 = 3 };
+// kAddF32 adds the tile into Cf with FP32 atomics: the split-K form, where
+// gridDim.z CTAs each reduce one slice of K into the same zeroed output.
+enum Epilogue { kStoreF32 = 0, kBiasReluBf16 = 1, kBiasF32 = 2, kMaskReluBf16 = 3, kAddF32 = 4 };
 
 // C[M][N] = op(A)[M][K] op(B)[K][N]. A: row-major [M][K] (TA = false) or
 // stored [K][M] (TA = true); B: stored [K][N] (TB = false) or [N][K]
-// (TB = true). 128 threads, a 64 x 64 tile, warps 2 x 2 of 32 x 32.
+// (TB = true). 128 threads, a 64 x 64 tile, warps 2 x 2 of 32 x 32. The CTA
+// at blockIdx.z takes K's slice [z * kslice, (z + 1) * kslice).
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16* __restrict__ A, int lda,
                                                  const __nv_bfloat16* __restrict__ B, int ldb, int M, int N, int K,
                                                  float* Cf, __nv_bfloat16* Cb, int ldc, const float* bias,
-                                                 const __nv_bfloat16* mask) {
+                                                 const __nv_bfloat16* mask, int kslice) {
   __shared__ __align__(16) __nv_bfloat16 sA[kTile][kTileK + kPad];
   __shared__ __align__(16) __nv_bfloat16 sB[kTile][kTileK + kPad];  // [n][k]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
   const int g = lane >> 2, t = lane & 3;
+  const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -60,16 +65,21 @@ __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16* __restrict
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.0f;
   const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int k0 = 0; k0 < K; k0 += kTileK) {
+  for (int k0 = kb; k0 < ke; k0 += kTileK) {
+    // consecutive threads take consecutive addresses of each operand: along
+    // k for a row-major A and a [N][K] B, along m or n for the others
     for (int e = tid; e < kTile * kTileK; e += 128) {
-      int r = e / kTileK, c = e % kTileK;
-      int m = m0 + r, k = k0 + c;
+      const int r = TA ? e % kTile : e / kTileK, c = TA ? e / kTile : e % kTileK;
+      const int m = m0 + r, k = k0 + c;
       __nv_bfloat16 va = zero;
-      if (m < M && k < K) va = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+      if (m < M && k < ke) va = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
       sA[r][c] = va;
-      int n = n0 + r;
+    }
+    for (int e = tid; e < kTile * kTileK; e += 128) {
+      const int r = TB ? e / kTileK : e % kTile, c = TB ? e % kTileK : e / kTile;
+      const int n = n0 + r, k = k0 + c;
       __nv_bfloat16 vb = zero;
-      if (n < N && k < K) vb = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+      if (n < N && k < ke) vb = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
       sB[r][c] = vb;
     }
     __syncthreads();
@@ -115,6 +125,8 @@ __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16* __restrict
         size_t o = (size_t)m * ldc + n;
         if (EPI == kStoreF32) {
           Cf[o] = v;
+        } else if (EPI == kAddF32) {
+          atomicAdd(Cf + o, v);
         } else if (EPI == kBiasReluBf16) {
           v += bias[n];
           Cb[o] = __float2bfloat16_rn(v > 0.0f ? v : 0.0f);
@@ -134,28 +146,35 @@ __global__ void to_bf16(const float* x, __nv_bfloat16* y, size_t n) {
 // Per row: loss -log softmax(logits[:na])[y] (summed into *loss) and
 // dlogits = (softmax - onehot) / B (zero past na), in BF16.
 __global__ void softmax_ce(const float* logits, const int32_t* y, int B, int na, __nv_bfloat16* dl, float* loss) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B) return;
-  const float* l = logits + (size_t)i * kMlpOut;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < B;
+  const float* l = logits + (size_t)(live ? i : 0) * kMlpOut;
   float mx = l[0];
   for (int a = 1; a < na; ++a) mx = fmaxf(mx, l[a]);
   float z = 0.0f;
   for (int a = 0; a < na; ++a) z += expf(l[a] - mx);
-  int yi = y[i];
-  atomicAdd(loss, -(l[yi] - mx - logf(z)));
+  const int yi = live ? y[i] : 0;
+  float li = live ? -(l[yi] - mx - logf(z)) : 0.0f;
+  for (int o = 16; o > 0; o >>= 1) li += __shfl_down_sync(0xFFFFFFFFu, li, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, li);  // one atomic per warp
+  if (!live) return;
   for (int a = 0; a < kMlpOut; ++a) {
     float p = a < na ? expf(l[a] - mx) / z : 0.0f;
     dl[(size_t)i * kMlpOut + a] = __float2bfloat16_rn((p - (a == yi ? 1.0f : 0.0f)) / (float)B);
   }
 }
 
-// out[n] = sum over rows of x[row][n].
+// out[n] += sum over rows of x[row][n]: CTA b sums rows [b * kColRows,
+// (b + 1) * kColRows) for every column (one thread per column) and adds its
+// partial sums into the zeroed out.
+constexpr int kColRows = 128;
 __global__ void col_sum(const __nv_bfloat16* x, int rows, int cols, float* out) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = threadIdx.x;
   if (n >= cols) return;
+  const int r0 = blockIdx.x * kColRows, r1 = min(rows, r0 + kColRows);
   float s = 0.0f;
-  for (int r = 0; r < rows; ++r) s += __bfloat162float(x[(size_t)r * cols + n]);
-  out[n] = s;
+  for (int r = r0; r < r1; ++r) s += __bfloat162float(x[(size_t)r * cols + n]);
+  atomicAdd(out + n, s);
 }
 
 __global__ void adam(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,
@@ -181,8 +200,20 @@ __global__ void pack_weights_bf16(const float* master, __nv_bfloat16* wb) {
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K, float* Cf,
                  __nv_bfloat16* Cb, int ldc, const float* bias, const __nv_bfloat16* mask, cudaStream_t st) {
-  dim3 grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile);
-  gemm_bf16<TA, TB, EPI><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, Cb, ldc, bias, mask);
+  // a long K over few output tiles (the weight gradients, K = batch) is
+  // split so that the grid covers the SMs; the slices add into Cf
+  int splits = 1;
+  const int tiles = ((N + kTile - 1) / kTile) * ((M + kTile - 1) / kTile);
+  if (EPI == kAddF32) splits = std::max(1, std::min((K + 511) / 512, (4 * 148 + tiles - 1) / tiles));
+  const int kslice = ((K + splits - 1) / splits + kTileK - 1) / kTileK * kTileK;
+  splits = (K + kslice - 1) / kslice;
+  dim3 grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile, splits);
+  gemm_bf16<TA, TB, EPI><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, Cb, ldc, bias, mask, kslice);
+  return cudaGetLastError();
+}
+
+cudaError_t col_sums(const __nv_bfloat16* x, int rows, int cols, float* out, cudaStream_t st) {
+  col_sum<<<(rows + kColRows - 1) / kColRows, cols, 0, st>>>(x, rows, cols, out);
   return cudaGetLastError();
 }
 
@@ -208,26 +239,27 @@ cudaError_t backward(dsp_mlp* q, const int32_t* y, int B, int na, cudaStream_t s
   const __nv_bfloat16* W2 = q->wb + kMlpIn * kMlpHid;
   const __nv_bfloat16* W3 = W2 + kMlpHid * kMlpHid;
   cudaMemsetAsync(q->loss, 0, sizeof(float), st);
+  cudaMemsetAsync(q->grad, 0, kMlpParams * sizeof(float), st);  // the split-K GEMMs and column sums add into it
   softmax_ce<<<(B + 127) / 128, 128, 0, st>>>(q->logits, y, B, na, q->dl, q->loss);
   // dW3 = H2^T dL, db3 = colsum(dL)
-  cudaError_t e = gemm<true, false, kStoreF32>(q->h2, kMlpHid, q->dl, kMlpOut, kMlpHid, kMlpOut, B,
+  cudaError_t e = gemm<true, false, kAddF32>(q->h2, kMlpHid, q->dl, kMlpOut, kMlpHid, kMlpOut, B,
                                                q->grad + kOffW3, nullptr, kMlpOut, nullptr, nullptr, st);
-  col_sum<<<1, kMlpOut, 0, st>>>(q->dl, B, kMlpOut, q->grad + kOffB3);
+  if (e == cudaSuccess) e = col_sums(q->dl, B, kMlpOut, q->grad + kOffB3, st);
   // dH2 = (dL W3^T) masked by H2 > 0
   if (e == cudaSuccess)
     e = gemm<false, true, kMaskReluBf16>(q->dl, kMlpOut, W3, kMlpOut, B, kMlpHid, kMlpOut, nullptr, q->dh2, kMlpHid,
                                          nullptr, q->h2, st);
   if (e == cudaSuccess)
-    e = gemm<true, false, kStoreF32>(q->h1, kMlpHid, q->dh2, kMlpHid, kMlpHid, kMlpHid, B, q->grad + kOffW2,
+    e = gemm<true, false, kAddF32>(q->h1, kMlpHid, q->dh2, kMlpHid, kMlpHid, kMlpHid, B, q->grad + kOffW2,
                                      nullptr, kMlpHid, nullptr, nullptr, st);
-  col_sum<<<1, kMlpHid, 0, st>>>(q->dh2, B, kMlpHid, q->grad + kOffB2);
+  if (e == cudaSuccess) e = col_sums(q->dh2, B, kMlpHid, q->grad + kOffB2, st);
   if (e == cudaSuccess)
     e = gemm<false, true, kMaskReluBf16>(q->dh2, kMlpHid, W2, kMlpHid, B, kMlpHid, kMlpHid, nullptr, q->dh1,
                                          kMlpHid, nullptr, q->h1, st);
   if (e == cudaSuccess)
-    e = gemm<true, false, kStoreF32>(q->xb, kMlpIn, q->dh1, kMlpHid, kMlpIn, kMlpHid, B, q->grad + kOffW1, nullptr,
+    e = gemm<true, false, kAddF32>(q->xb, kMlpIn, q->dh1, kMlpHid, kMlpIn, kMlpHid, B, q->grad + kOffW1, nullptr,
                                      kMlpHid, nullptr, nullptr, st);
-  col_sum<<<1, kMlpHid, 0, st>>>(q->dh1, B, kMlpHid, q->grad + kOffB1);
+  if (e == cudaSuccess) e = col_sums(q->dh1, B, kMlpHid, q->grad + kOffB1, st);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
 }
