@@ -95,6 +95,9 @@ def parse():
     p.add_argument("--no-plan", action="store_true")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-policy comparison")
     p.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
+    p.add_argument("--shape", default="",
+                   help="run this launch shape, untuned: comma-separated field=value of dsp_launch_shape "
+                        "(e.g. rs_form=2,block_b=256)")
     p.add_argument("--plan-worlds", type=int, default=16,
                    help="rs15_15: planner episodes on this many seeded worlds (100 steps, 4 threads, 200 trials each)")
     p.add_argument("--no-companions", action="store_true",
@@ -468,7 +471,13 @@ def measure(args, name, rank, world, dist, local, headline=True):
     # job batch (kept per model, K, |A| and GPU; the default shape is timed
     # beside it afterwards)
     autotuned = None
-    if not args.no_autotune:
+    if args.shape:
+        fields = dict(kv.split("=") for kv in args.shape.split(","))
+        unknown = set(fields) - set(_dsp.SHAPE_FIELDS)
+        if unknown:
+            raise SystemExit(f"--shape: unknown fields {sorted(unknown)}")
+        _dsp.dsp_set_launch_shape(m.h, **{k: int(v) for k, v in fields.items()})
+    elif not args.no_autotune:
         from paper_1802_06215_b300 import autotune as AT
         cache = os.environ.get("DSP_TUNE_CACHE") or None
         best = AT.autotune(m, jb, torch.cuda.get_device_name(), cache, reps=3)
@@ -479,7 +488,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
                          inputs.CAR: "tps {4,8,16,32} x ctas_car {fit,3,2}",
                          inputs.NAV: "ctas_b {fit,6,4,2}"}.get(
                              cfg.kind, "block_b {128,256,512} x ctas_b {fit,6,4} x warps_a {default,5,10} "
-                                       "(two robots {default,8,16})"),
+                                       "(two robots {default,8,16}); one robot x rs_form {blocks,items}"),
                      "note": "0 = the field's default; the timed region runs this shape"}
         for _ in range(2):
             jb.run()
@@ -614,12 +623,15 @@ def measure(args, name, rank, world, dist, local, headline=True):
     roof = None
     if ops_per_step:
         achieved = ops_per_step * steps_per_launch / avg_kernel_s / 1e12
-        traffic = measured_traffic(name, kind)
+        # one-robot Rock Sample's block form has its own row
+        blocks = cfg.kind == inputs.GRID and _dsp.dsp_get_launch_shape(m.h)["rs_form"] == 1
+        traffic = measured_traffic(name + ("_blocks" if blocks else ""), kind)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": traffic,
                 "peak_source": "derived: 148 SMs x 128 lanes x 2032 MHz (one 32-bit op per lane per clock)",
                 "probe_tops": probe_tops, "ops_per_scenario_step": ops_per_step,
-                "kernel": {"rs": "rs_group_kernel + rs_rollout_items_kernel (one expansion)",
+                "kernel": {"rs": "rs_group_kernel + " + ("rs_rollout_blocks_kernel" if blocks else
+                                                          "rs_rollout_items_kernel") + " (one expansion)",
                            "car": "car_expand_kernel",
                            "nav": "nav_group_kernel + nav_rollout_items_kernel (one expansion)"}[kind],
                 "kernel_ms_per_launch": avg_kernel_s * 1000.0,
@@ -637,6 +649,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
                 "method": "dsp_expand_leaves on two job arenas and two streams taking alternate steps; "
                           "wall time from the first upload to the last result, L2 flush in each step"},
         "gpu_launches": args.steps * kernels_per_step,
+        "launch_shape": _dsp.dsp_get_launch_shape(m.h),
         "roofline": roof,
         "cpu_baseline": cpu,
         "planning": planning,
@@ -697,6 +710,9 @@ def sweep(args):
         mk, njobs, desc, _ = WORKLOADS[name]
         cfg = mk()
         m = batch.Model(cfg)
+        if args.shape:  # fields that do not apply to the workload's model keep their defaults
+            fields = {k: int(v) for k, v in (kv.split("=") for kv in args.shape.split(","))}
+            _dsp.dsp_set_launch_shape(m.h, **fields)
         jobs = inputs.job_stream(cfg, args.jobs or njobs, 1000)
         jb = batch.JobBatch(m, jobs)
         for _ in range(args.warmup):

@@ -358,11 +358,19 @@ dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
  *    within-step split over pedestrians; with more pairs than lanes each lane
  *    takes several.
  *  - ctas_car: car kernel CTAs per SM (1..32, capped by what fits).
+ *  - rs_form: one-robot Rock Sample with the heuristic default policy, how
+ *    the grouping phase hands its (action, scenario) pairs to the rollout
+ *    phase (dsp_expand_leaves only; the no-allocation entry point always
+ *    uses items): 1 = blocks (the leaf's states, 12 B per scenario, and the
+ *    grouped positions; the rollout phase rebuilds each pair's child state
+ *    and mask: no per-pair list, about a seventh of the DRAM traffic),
+ *    2 = items (a 20 B rollout item per pair, written by the grouping phase
+ *    and read back; fewer instructions). Default 2.
  * One-robot Rock Sample has no within-step work to split (the default
  * policy reads one table entry per candidate rock), so its scenarios map one
  * to a thread. DSP_E_INVALID for values outside these sets. */
 typedef struct {
-  int32_t block_b, ctas_b, warps_a, tps, ctas_car;
+  int32_t block_b, ctas_b, warps_a, tps, ctas_car, rs_form;
 } dsp_launch_shape;
 dsp_status dsp_set_launch_shape(dsp_model* model, const dsp_launch_shape* shape);
 dsp_status dsp_get_launch_shape(const dsp_model* model, dsp_launch_shape* shape);
@@ -372,7 +380,8 @@ dsp_status dsp_get_launch_shape(const dsp_model* model, dsp_launch_shape* shape)
  * shape and for every candidate of the model's kind, `reps` timed calls
  * each after one warm-up (CUDA events on `stream`), and keeps the fastest.
  *  - Rock Sample: block_b {128, 256, 512} x ctas_b {as many as fit, 6, 4} x
- *    warps_a {default, 5, 10} (two robots: {default, 8, 16}).
+ *    warps_a {default, 5, 10} (two robots: {default, 8, 16}); one robot
+ *    with the heuristic policy also x rs_form {blocks, items}.
  *  - car: tps {4, 8, 16, 32} x ctas_car {as many as fit, 3, 2}.
  *  - navigation: ctas_b {as many as fit, 6, 4, 2}.
  * best: the chosen shape (set in the model); best_ms / default_ms: mean time

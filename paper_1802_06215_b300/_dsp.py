@@ -168,7 +168,7 @@ def dsp_set_tuning(h, block, tps):
 
 class dsp_launch_shape(C.Structure):
     _fields_ = [("block_b", C.c_int32), ("ctas_b", C.c_int32), ("warps_a", C.c_int32), ("tps", C.c_int32),
-                ("ctas_car", C.c_int32)]
+                ("ctas_car", C.c_int32), ("rs_form", C.c_int32)]
 
 
 SHAPE_FIELDS = tuple(f for f, _ in dsp_launch_shape._fields_)

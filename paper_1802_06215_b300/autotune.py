@@ -3,7 +3,8 @@
 
 The measuring itself runs in the CUDA library (dsp_autotune_shape: the
 rollout phase's CTA size and CTAs per SM, the grouping phase's warps per CTA,
-the car's lanes per scenario and CTAs per SM); this module only builds the
+the car's lanes per scenario and CTAs per SM, one-robot Rock Sample's
+rollout-phase form); this module only builds the
 cache key and reads and writes the file.
 """
 import ctypes as C
@@ -54,7 +55,7 @@ def autotune(model, batch, gpu_name, cache_path=None, reps=3, measure=None):
     cache = _load(cache_path)
     if key in cache:
         best = cache[key]
-        _dsp.dsp_set_launch_shape(model.h, **{k: best[k] for k in _dsp.SHAPE_FIELDS})
+        _dsp.dsp_set_launch_shape(model.h, **{k: best.get(k, 0) for k in _dsp.SHAPE_FIELDS})
         return dict(best, cached=True)
     if measure is None:
         best = _dsp.dsp_autotune_shape(model.h, batch.descs, len(batch.jobs), reps)

@@ -289,7 +289,7 @@ dsp_status dsp_expand_leaves(dsp_model* m, const dsp_leaf_job* jobs, int32_t n_j
   if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(DSP_E_INVALID, "dsp_expand_leaves: bad job array");
   if (n_jobs == 0) return DSP_OK;
   ExpandPlan plan;
-  dsp_status vs = plan_units(m, jobs, n_jobs, plan);
+  dsp_status vs = plan_units(m, jobs, n_jobs, plan, true);
   if (vs != DSP_OK) return vs;
   return launch_expand(m, jobs, n_jobs, plan, (cudaStream_t)stream);
 }
@@ -336,11 +336,14 @@ dsp_status dsp_set_launch_shape(dsp_model* m, const dsp_launch_shape* s) {
     return fail(DSP_E_INVALID, "dsp_set_launch_shape: CTAs per SM outside 0..32");
   if (s->warps_a < 0 || s->warps_a > 16)
     return fail(DSP_E_INVALID, "dsp_set_launch_shape: warps_a %d outside 0..16", s->warps_a);
+  if (s->rs_form < 0 || s->rs_form > 2)
+    return fail(DSP_E_INVALID, "dsp_set_launch_shape: rs_form %d outside 0..2", s->rs_form);
   m->tune_block = s->block_b;
   m->tune_ctas_b = s->ctas_b;
   m->tune_warps_a = s->warps_a;
   m->tune_tps = s->tps;
   m->tune_ctas_car = s->ctas_car;
+  m->tune_rs_form = s->rs_form;
   return DSP_OK;
 }
 
@@ -351,6 +354,7 @@ dsp_status dsp_get_launch_shape(const dsp_model* m, dsp_launch_shape* s) {
   s->warps_a = m->tune_warps_a;
   s->tps = m->tune_tps;
   s->ctas_car = m->tune_ctas_car;
+  s->rs_form = m->tune_rs_form;
   return DSP_OK;
 }
 
@@ -388,11 +392,15 @@ namespace dsp {
 // Validates the jobs and plans the launch: car and navigation units are (job,
 // action), each with the first index of its rollout items; Rock Sample jobs
 // get the first index of theirs (n_scen * n_actions each, in job order).
-dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan) {
+dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan, bool allow_blocks) {
   const DevModel* h = m->host;
   plan.units.clear();
   plan.item_base.clear();
-  plan.total_items = 0;
+  plan.unit_base.clear();
+  plan.scen_base.clear();
+  plan.total_items = plan.total_blocks = plan.total_scen = 0;
+  plan.blocks = allow_blocks && h->kind != DSP_MODEL_CAR && h->kind != DSP_MODEL_NAV && h->robots == 1 &&
+                !m->policy_on && m->tune_rs_form == 1;
   for (int j = 0; j < n_jobs; ++j) {
     const dsp_leaf_job& J = jobs[j];
     const int max_n = h->kind == DSP_MODEL_GRID ? kMaxScenLarge : kMaxScen;
@@ -415,6 +423,12 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
       return fail(DSP_E_UNSUPPORTED, "job %d: n_actions * child_cap >= 2^24", j);
     if (h->kind == DSP_MODEL_CAR || h->kind == DSP_MODEL_NAV) {
       for (int a = 0; a < J.n_actions; ++a) plan.units.push_back(make_int4(j, a, 1, 0));
+    } else if (plan.blocks) {
+      plan.unit_base.push_back(plan.total_blocks);
+      plan.scen_base.push_back(plan.total_scen);
+      plan.total_blocks += (long long)J.n_actions * ((J.n_scen + 31) / 32);
+      plan.total_scen += J.n_scen;
+      plan.total_items += (long long)J.n_scen * J.n_actions;
     } else {
       plan.item_base.push_back(plan.total_items);
       plan.total_items += (long long)J.n_scen * J.n_actions;
@@ -509,12 +523,17 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   const bool car = h->kind == DSP_MODEL_CAR, nav = h->kind == DSP_MODEL_NAV;
   const bool by_unit = car || nav;  // (job, action) units instead of Rock Sample's item list
   size_t jb = sizeof(dsp_leaf_job) * (size_t)n_jobs;
-  size_t ub = by_unit ? sizeof(int4) * plan.units.size()
-                  : sizeof(long long) * plan.item_base.size() + sizeof(int) * plan.order.size();
+  // Rock Sample: per-job offsets (item list: first item; block form: first
+  // block and first leaf scenario), then the phase-A order
+  const size_t nb = plan.blocks ? 2 * plan.unit_base.size() : plan.item_base.size();
+  size_t ub = by_unit ? sizeof(int4) * plan.units.size() : sizeof(long long) * nb + sizeof(int) * plan.order.size();
   const bool car_items = car && m->policy_on;
+  // block form: the leaves' states (3 words a scenario), then each block's job
   size_t ib = car   ? (car_items ? sizeof(uint32_t) * (size_t)(h->words + 2) * (size_t)plan.total_items : 0)
               : nav ? sizeof(uint32_t) * (size_t)nav_item_fields(h->n) * (size_t)plan.total_items
-                    : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots, m->policy_on) * (size_t)plan.total_items;
+              : plan.blocks
+                  ? align256(sizeof(uint32_t) * 3 * (size_t)plan.total_scen) + sizeof(int) * (size_t)plan.total_blocks
+                  : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots, m->policy_on) * (size_t)plan.total_items;
   size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
   unsigned char* buf = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, total, m->pool, st);
@@ -523,7 +542,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
   void* dunits = buf + align256(jb);
   unsigned int* counters = (unsigned int*)(buf + align256(jb) + align256(ub));
   uint32_t* items = (uint32_t*)(buf + align256(jb) + align256(ub) + 256);
-  const int* dorder = by_unit ? nullptr : (const int*)((const long long*)dunits + plan.item_base.size());
+  const int* dorder = by_unit ? nullptr : (const int*)((const long long*)dunits + nb);
   // the job table and the unit table (or item offsets and order) in one copy
   // from pinned staging laid out like the device buffer
   const size_t hb = align256(jb) + ub;
@@ -533,6 +552,11 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
     std::memcpy(hs, jobs, jb);
     if (by_unit) {
       std::memcpy(hs + align256(jb), plan.units.data(), ub);
+    } else if (plan.blocks) {
+      const size_t n = plan.unit_base.size();
+      std::memcpy(hs + align256(jb), plan.unit_base.data(), sizeof(long long) * n);
+      std::memcpy(hs + align256(jb) + sizeof(long long) * n, plan.scen_base.data(), sizeof(long long) * n);
+      std::memcpy(hs + align256(jb) + sizeof(long long) * nb, plan.order.data(), sizeof(int) * plan.order.size());
     } else {
       std::memcpy(hs + align256(jb), plan.item_base.data(), sizeof(long long) * plan.item_base.size());
       std::memcpy(hs + align256(jb) + sizeof(long long) * plan.item_base.size(), plan.order.data(),
@@ -545,7 +569,16 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
     e = cudaMemcpyAsync(djobs, jobs, jb, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && by_unit)
       e = cudaMemcpyAsync(dunits, plan.units.data(), ub, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !by_unit) {
+    if (e == cudaSuccess && !by_unit && plan.blocks) {
+      const size_t n = plan.unit_base.size();
+      e = cudaMemcpyAsync(dunits, plan.unit_base.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync((long long*)dunits + n, plan.scen_base.data(), sizeof(long long) * n,
+                            cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void*)dorder, plan.order.data(), sizeof(int) * plan.order.size(),
+                            cudaMemcpyHostToDevice, st);
+    } else if (e == cudaSuccess && !by_unit) {
       e = cudaMemcpyAsync(dunits, plan.item_base.data(), sizeof(long long) * plan.item_base.size(),
                           cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess)
@@ -569,11 +602,19 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
                             plan.total_items, st);
     } else {
       int block_b = m->tune_block > 0 ? m->tune_block : 256;
+      LeafBlocks lb;
+      if (plan.blocks) {
+        const size_t n = plan.unit_base.size();
+        lb.leaf = items;
+        lb.unit_base = (const long long*)dunits;
+        lb.scen_base = (const long long*)dunits + n;
+        lb.chunk_job = (int*)((unsigned char*)items + align256(sizeof(uint32_t) * 3 * (size_t)plan.total_scen));
+      }
       e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, rs_key_words(h), m->dwork, djobs,
-                           (const long long*)dunits, dorder,
-                           n_jobs,
-                           plan.total_items, items, counters, m->plan_step, m->num_sms, block_b,
-                           m->policy_on ? m->policy : nullptr, st, m->tune_warps_a, m->tune_ctas_b);
+                           (const long long*)dunits, dorder, n_jobs,
+                           plan.blocks ? plan.total_blocks : plan.total_items, items, counters, m->plan_step,
+                           m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st, m->tune_warps_a,
+                           m->tune_ctas_b, plan.blocks ? &lb : nullptr);
     }
     if (m->timing) {
       cudaEventRecord(ev[1], st);

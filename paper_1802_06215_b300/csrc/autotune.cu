@@ -3,7 +3,8 @@
 // elements to warps; Sec. III-D); here the mapping is a parameter: the CTA
 // size and CTAs per SM of the rollout phase, the grouping phase's warps per
 // CTA (actions per warp), the lanes that share one car scenario
-// (element-level parallelism) and the car kernel's CTAs per SM. Each
+// (element-level parallelism), the car kernel's CTAs per SM and, for one
+// robot, whether the rollout phase reads items or rebuilds them. Each
 // candidate is timed with CUDA events on the caller's jobs and the fastest
 // is kept in the model.
 #include <cuda_runtime.h>
@@ -101,21 +102,25 @@ extern "C" dsp_status dsp_autotune_shape(dsp_model* m, const dsp_leaf_job* jobs,
   const int kind = m->host->kind;
   if (kind == DSP_MODEL_CAR) {
     for (int tps : {4, 8, 16, 32})
-      for (int c : {0, 3, 2}) cands.push_back({0, 0, 0, tps, c});
+      for (int c : {0, 3, 2}) cands.push_back({0, 0, 0, tps, c, 0});
   } else if (kind == DSP_MODEL_NAV) {
-    for (int c : {0, 6, 4, 2}) cands.push_back({0, c, 0, 0, 0});
+    for (int c : {0, 6, 4, 2}) cands.push_back({0, c, 0, 0, 0, 0});
   } else {
-    const bool two = kind == DSP_MODEL_MULTIGRID;
-    for (int b : {128, 256, 512})
-      for (int c : {0, 6, 4})
-        for (int w : {0, two ? 8 : 5, two ? 16 : 10}) cands.push_back({b, c, w, 0, 0});
+    const bool two = m->host->robots == 2;
+    // the rollout phase's two forms (one robot, heuristic policy)
+    std::vector<int> forms = {0};
+    if (!two && !m->policy_on) forms = {1, 2};
+    for (int f : forms)
+      for (int b : {128, 256, 512})
+        for (int c : {0, 6, 4})
+          for (int w : {0, two ? 8 : 5, two ? 16 : 10}) cands.push_back({b, c, w, 0, 0, f});
   }
   dsp_launch_shape keep;
   dsp_get_launch_shape(m, &keep);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(DSP_E_CUDA, "dsp_autotune_shape: events");
-  const dsp_launch_shape dflt = {0, 0, 0, 0, 0};
+  const dsp_launch_shape dflt = {0, 0, 0, 0, 0, 0};
   dsp_set_launch_shape(m, &dflt);
   float dms = 0.0f;
   dsp_status s = time_shape(m, jobs, n_jobs, reps, st, e0, e1, &dms);

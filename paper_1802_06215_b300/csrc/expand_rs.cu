@@ -64,6 +64,21 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Writes job j's compact leaf states (given one at a time by the caller's
+// loop over p) and its block table entries.
+__device__ __forceinline__ void put_leaf(const LeafBlocks& lb, int j, int n, int p, uint32_t pos, uint32_t good,
+                                         uint32_t sampled) {
+  uint32_t* L = lb.leaf + 3 * lb.scen_base[j];
+  L[p] = pos;
+  L[n + p] = good;
+  L[2 * n + p] = sampled;
+}
+__device__ __forceinline__ void put_blocks(const LeafBlocks& lb, int j, int n, int A) {
+  const long long u0 = lb.unit_base[j];
+  const int nu = A * ((n + 31) >> 5);
+  for (int u = threadIdx.x; u < nu; u += (int)blockDim.x) lb.chunk_job[u0 + u] = j;
+}
+
 // Gather + update of the job in S.J into S.leaf (and J.leaf_states), and the
 // job's positive-counter mask. Ends with a barrier. Only the job's first unit
 // (`first`) counts the update steps and writes the leaf's states.
@@ -110,12 +125,17 @@ __device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& 
 // that draw no random numbers (a Sense leaves the state as it was). The result
 // is identical to the general grouping; no barrier is needed inside the job.
 __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long long ibase, Items<1> items,
-                              DevWork* work, unsigned long long& steps) {
+                              DevWork* work, unsigned long long& steps, const LeafBlocks& lb) {
   constexpr int kC = 6;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   gather_update<1>(S, M, true, steps);
   const dsp_leaf_job& J = S.J;
   const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
+  const bool blocks = lb.leaf != nullptr;
+  if (blocks) {
+    for (int p = tid; p < n; p += (int)blockDim.x) put_leaf(lb, j, n, p, S.leaf[0][p], S.leaf[2][p], S.leaf[3][p]);
+    put_blocks(lb, j, n, A);
+  }
   const uint32_t lt = lanemask_lt();
   uint8_t* codes = S.code1[warp];
   const uint32_t pm_job = S.pm_job;
@@ -223,7 +243,8 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
           run[c] += __popc(b);
         }
       }
-      if (p < n) {
+      if (p < n) J.perm[(size_t)a * n + q] = (uint16_t)p;
+      if (p < n && !blocks) {
         RSS s;
         s.pos[0] = S.leaf[0][p];
         s.pos[1] = 0u;
@@ -234,7 +255,6 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
           uint64_t k;
           M.step(s, aa, depth, k);
         }
-        J.perm[(size_t)a * n + q] = (uint16_t)p;
         const int z = code % 3;
         const uint32_t pm = z == 1 ? pm_z[1] : (z == 2 ? pm_z[2] : pm_z[0]);
         const size_t it = (size_t)(ibase + (long long)a * n + q);
@@ -253,7 +273,7 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
 // step and observation code instead of keeping them. The placement is the
 // same as rs1_group_job's, so the result is identical.
 __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, long long ibase, Items<1> items,
-                                    DevWork* work, unsigned long long& steps) {
+                                    DevWork* work, unsigned long long& steps, const LeafBlocks& lb) {
   constexpr int kC = 6;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const dsp_leaf_job& J = S.J;
@@ -267,7 +287,9 @@ __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, 
       M.step(s, J.last_action, depth - 1, k);
     }
     M.store(s, L, n, p);
+    if (lb.leaf != nullptr) put_leaf(lb, j, n, p, s.pos[0], s.good, s.sampled);
   }
+  if (lb.leaf != nullptr) put_blocks(lb, j, n, A);
   if (tid == 0) {
     uint32_t h[8];
     const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
@@ -377,8 +399,8 @@ __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, 
           run[c] += __popc(b);
         }
       }
-      if (p < n) {
-        J.perm[(size_t)a * n + q] = (uint16_t)p;
+      if (p < n) J.perm[(size_t)a * n + q] = (uint16_t)p;
+      if (p < n && lb.leaf == nullptr) {
         const int z = code % 3;
         const uint32_t pm = z == 1 ? pm_z[1] : (z == 2 ? pm_z[2] : pm_z[0]);
         const size_t it = (size_t)(ibase + (long long)a * n + q);
@@ -526,12 +548,12 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
 template <int R, bool kLarge = true>
 __device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase, int a_begin,
                                           int a_end, bool first, Items<R> items, DevWork* work,
-                                          unsigned long long& steps) {
+                                          unsigned long long& steps, const LeafBlocks& lb = LeafBlocks{}) {
   if constexpr (R == 1) {
     if (kLarge && S.J.n_scen > kMaxScen)
-      rs1_group_job_large(S, M, j, ibase, items, work, steps);
+      rs1_group_job_large(S, M, j, ibase, items, work, steps, lb);
     else
-      rs1_group_job(S, M, j, ibase, items, work, steps);
+      rs1_group_job(S, M, j, ibase, items, work, steps, lb);
   } else
     rs2_group_job(S, M, j, ibase, a_begin, a_end, first, items, work, steps);
 }
@@ -542,7 +564,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
                                                              const long long* __restrict__ item_base,
                                                              const int* __restrict__ order, int n_jobs,
                                                              unsigned int* head, uint32_t plan_step,
-                                                             Items<R> items, int splits) {
+                                                             Items<R> items, int splits, LeafBlocks lb) {
   __shared__ RSGroupSmem S;
   load_rs_consts(S.c, gm);
   const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
@@ -568,7 +590,8 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
     // both ways end at a barrier (group_job's last), so thread 0 may take the
     // next unit (the condition is the same for the whole CTA)
     if (a_begin < a_end)
-      group_job<R>(S, M, j, item_base[j], a_begin, a_end, S.part == 0, items, work, steps);
+      group_job<R>(S, M, j, item_base != nullptr ? item_base[j] : 0, a_begin, a_end, S.part == 0, items, work,
+                   steps, lb);
     else
       __syncthreads();
   }
@@ -587,6 +610,26 @@ __device__ __forceinline__ long long warp_sum64(long long x) {
   const int h = __reduce_add_sync(0xFFFFFFFFu, hi);
   return (long long)h * 4294967296LL + (long long)b * 65536LL + (long long)a;
 }
+
+// A warp's chunk claims, used by its lane 0 and kept in shared memory (one
+// record per warp) so that no register carries them through the rollouts.
+// Every warp of the grid draws chunks from one counter; one atomic per
+// 32-item chunk came near the rate at which the memory system serves atomics
+// on one address, and the warps queued on the claims. So a claim takes
+// kBatch chunks, handed out one at a time.
+constexpr int kMaxWarpsB = 16;  // rollout-phase CTAs of at most 512 threads
+struct ChunkClaims {
+  static constexpr unsigned int kBatch = 4;
+  unsigned int next, left;
+  __device__ __forceinline__ unsigned int take(unsigned int* head) {
+    if (left == 0) {
+      next = atomicAdd(head, kBatch);
+      left = kBatch;
+    }
+    --left;
+    return next++;
+  }
+};
 
 // Phase B for one 32-item chunk (one whole warp calls it), the lane's compact
 // item given (ok: the lane holds an item): u0 and the rollout, then the sums
@@ -703,35 +746,26 @@ __global__ void __launch_bounds__(512, R == 1 ? 4 : 3) rs_rollout_items_kernel(c
   uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(rs_keys) +
                                                 rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)gm->m * gm->n * gm->n)) +
                     (size_t)(threadIdx.x >> 5) * 2 * F * 32;
-  const long long nchunks = (items.total + 31) >> 5;
+  // chunks of 32 items (fewer than 2^26: the list holds fewer than 2^31)
+  const unsigned int nchunks = (unsigned int)((items.total + 31) >> 5);
   unsigned long long steps = 0;
-  // Chunks are claimed from one counter, kClaimBatch at a time: every warp of
-  // the grid draws from it, and one atomic per 32-item chunk came near the
-  // rate at which the memory system serves atomics on one address (the
-  // warps then queued on it). Lane 0 holds the rest of its batch. A chunk
-  // is claimed one step ahead of its staging: the claim for the chunk after
-  // next is made before a chunk's rollouts and read after them.
-  constexpr unsigned int kClaimBatch = 4;
-  unsigned int batch_next = 0, batch_left = 0;  // lane 0
-  auto next_chunk = [&]() {
-    if (batch_left == 0) {
-      batch_next = atomicAdd(chunk_head, kClaimBatch);
-      batch_left = kClaimBatch;
-    }
-    --batch_left;
-    return batch_next++;
-  };
+  // Chunks are claimed ChunkClaims::kBatch at a time, and one step ahead of
+  // their staging: the claim for the chunk after next is made before a
+  // chunk's rollouts and read after them.
+  __shared__ ChunkClaims claims[kMaxWarpsB];
+  ChunkClaims& cc = claims[threadIdx.x >> 5];
+  if (lane == 0) cc.left = 0;
   auto claim = [&]() {
-    long long ch = 0;
-    if (lane == 0) ch = (long long)next_chunk();
+    unsigned int ch = 0;
+    if (lane == 0) ch = cc.take(chunk_head);
     return __shfl_sync(0xFFFFFFFFu, ch, 0);
   };
-  long long cur = claim();
+  unsigned int cur = claim();
   if (cur < nchunks) stage_items<R>(stage, items, cur);
-  long long nxt = cur < nchunks ? claim() : nchunks;
+  unsigned int nxt = cur < nchunks ? claim() : nchunks;
   if (nxt < nchunks) stage_items<R>(stage + F * 32, items, nxt);
   unsigned int pending = 0;  // lane 0: the claim in flight
-  if (nxt < nchunks && lane == 0) pending = next_chunk();
+  if (nxt < nchunks && lane == 0) pending = cc.take(chunk_head);
   int b = 0;
   while (cur < nchunks) {
     if (nxt < nchunks)
@@ -740,7 +774,7 @@ __global__ void __launch_bounds__(512, R == 1 ? 4 : 3) rs_rollout_items_kernel(c
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncwarp();
     const uint32_t* w = stage + b * F * 32;
-    const bool ok = cur * 32 + lane < items.total;
+    const bool ok = (long long)cur * 32 + lane < items.total;
     RSS s;
     s.pos[0] = w[lane];
     s.pos[1] = R == 2 ? w[32 + lane] : 0u;
@@ -755,13 +789,116 @@ __global__ void __launch_bounds__(512, R == 1 ? 4 : 3) rs_rollout_items_kernel(c
     b ^= 1;
     if (cur < nchunks) {
       // cur < nchunks: the claim issued one chunk ago names the chunk to stage now
-      nxt = (long long)__shfl_sync(0xFFFFFFFFu, pending, 0);
+      nxt = __shfl_sync(0xFFFFFFFFu, pending, 0);
       if (nxt < nchunks) {
         stage_items<R>(stage + (b ^ 1) * F * 32, items, nxt);
-        if (lane == 0) pending = next_chunk();
+        if (lane == 0) pending = cc.take(chunk_head);
       }
     }
     rs_rollout_values<R>(M, jobs, ok, s, cand, meta, job, steps);
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if (lane == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
+// Phase B in block form for one chunk u (one robot, heuristic default
+// policy): the 32 grouped positions [32 b, 32 b + 32) of action a of job j =
+// chunk_job[u], where u - unit_base[j] = a * ceil(n / 32) + b. Each lane
+// rebuilds the item phase A would have written for its grouped position q:
+// the scenario p = perm[a][q] and its leaf state; the child whose offset
+// range holds q, and that child's observation z; the child's
+// positive-counter mask (the leaf's, with a Sense reading's +-1 on its
+// rock's counter); and the state after a move or Sample (a Sense leaves it as
+// it was). Then u0, the rollout and the sums as for a stored item.
+__device__ __forceinline__ void rs_block_values(const RSModel<1>& M, const dsp_leaf_job* __restrict__ jobs,
+                                                const LeafBlocks& lb, unsigned int u, int j,
+                                                unsigned long long& steps) {
+  const int lane = threadIdx.x & 31;
+  const dsp_leaf_job* J = jobs + j;
+  const int n = J->n_scen, cap = J->child_cap, depth = J->depth;
+  const int nb = (n + 31) >> 5;
+  const int local = (int)((long long)u - lb.unit_base[j]);
+  const int a = local / nb;
+  const int q = (local - a * nb) * 32 + lane;
+  const int aa = J->first_action + a;
+  const bool ok = q < n;
+  // the child of grouped position q: the last whose offset is <= q (at most
+  // six children, in lanes 0..nc-1)
+  const int nc = min(J->child_count[a], cap);
+  const int myoff = lane < nc ? J->child_off[(size_t)a * (cap + 1) + lane] : 0;
+  const uint32_t myz = lane < nc ? (uint32_t)(J->child_key[(size_t)a * cap + lane] & 3u) : 0u;
+  int ci = 0;
+  for (int k = 1; k < nc; ++k) ci += q >= __shfl_sync(0xFFFFFFFFu, myoff, k) ? 1 : 0;
+  const int z = (int)__shfl_sync(0xFFFFFFFFu, myz, ci);
+  // the leaf's positive-counter mask, rock i's counter in lane i
+  const int hv = lane < M.m ? (int)J->hist[lane] : 0;
+  uint32_t pm = __ballot_sync(0xFFFFFFFFu, hv > 0);
+  if (aa >= 5) {  // Sense rock i: a good reading adds one, a bad one takes one (clamped to +-127)
+    const int i = aa - 5;
+    const int c0 = __shfl_sync(0xFFFFFFFFu, hv, i);
+    const int c = z == 1 ? min(c0 + 1, 127) : (z == 2 ? max(c0 - 1, -127) : c0);
+    pm = c > 0 ? (pm | (1u << i)) : (pm & ~(1u << i));
+  }
+  RSS s;
+  s.pos[0] = 0u;
+  s.pos[1] = 0u;
+  s.good = 0u;
+  s.sampled = 0u;
+  s.scen = 0u;
+  if (ok) {
+    const int p = J->perm[(size_t)a * n + q];
+    const uint32_t* L = lb.leaf + 3 * lb.scen_base[j];
+    s.pos[0] = L[p];
+    s.good = L[n + p];
+    s.sampled = L[2 * n + p];
+    if (aa < 5) {
+      uint64_t k;
+      M.step(s, aa, depth, k);
+    }
+  }
+  const uint32_t cand = pm & ~s.sampled;
+  s.sampled = 0u;
+  const uint32_t meta = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(ci, cap - 1));
+  rs_rollout_values<1>(M, jobs, ok, s, cand, meta, (uint32_t)j, steps);
+}
+
+// Phase B in block form: warps claim chunks as rs_rollout_items_kernel does
+// and read each chunk's job one chunk ahead.
+__global__ void __launch_bounds__(512, 4) rs_rollout_blocks_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                                   const dsp_leaf_job* __restrict__ jobs,
+                                                                   int n_jobs, LeafBlocks lb, unsigned int nchunks,
+                                                                   unsigned int* chunk_head, uint32_t plan_step) {
+  __shared__ RSShared c;
+  extern __shared__ __align__(16) uint16_t rs_keys[];
+  load_rs_consts(c, gm);
+  load_rs_keys(rs_keys, gm);
+  __syncthreads();
+  RSModel<1> M = make_rs<1>(gm, &c, plan_step);
+  M.nkey = rs_keys;
+  const int lane = threadIdx.x & 31;
+  unsigned long long steps = 0;
+  __shared__ ChunkClaims claims[kMaxWarpsB];
+  ChunkClaims& cc = claims[threadIdx.x >> 5];
+  if (lane == 0) cc.left = 0;
+  unsigned int pending = 0;  // lane 0: the claim in flight
+  if (lane == 0) pending = cc.take(chunk_head);
+  unsigned int cur = __shfl_sync(0xFFFFFFFFu, pending, 0);
+  int jcur = cur < nchunks ? lb.chunk_job[cur] : 0;
+  if (lane == 0 && cur < nchunks) pending = cc.take(chunk_head);
+  while (cur < nchunks) {
+    // the claim made one chunk ago; its job is loaded now and read next time
+    const unsigned int nxt = __shfl_sync(0xFFFFFFFFu, pending, 0);
+    int jnxt = 0;
+    if (nxt < nchunks) {
+      jnxt = lb.chunk_job[nxt];
+      if (lane == 0) pending = cc.take(chunk_head);
+    }
+    if ((unsigned)jcur < (unsigned)n_jobs)  // the grouping phase wrote every block's job
+      rs_block_values(M, jobs, lb, cur, jcur, steps);
+    else if (lane == 0)
+      report(work, kStatusBadJob);
+    cur = nxt;
+    jcur = jnxt;
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);
@@ -844,8 +981,11 @@ template <int R>
 cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st,
-                             int warps_a, int ctas_b) {
-  Items<R> items{item_buf, total_items, policy != nullptr && R == 1};
+                             int warps_a, int ctas_b, LeafBlocks lb) {
+  // block form (lb.leaf set; one robot, heuristic policy): no item list,
+  // total_items counts the 32-position blocks
+  const bool blocks = lb.leaf != nullptr;
+  Items<R> items{blocks ? nullptr : item_buf, blocks ? 0 : total_items, policy != nullptr && R == 1};
   // Each warp expands whole actions: as many warps as give every warp the
   // same number of a job's actions (20 actions: 10 warps of 2; 400: 16 of
   // 25). One robot with at least two jobs per CTA slot: at most five warps
@@ -869,13 +1009,25 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
   // about 80), so that the largest jobs do not leave a tail
   const int splits = R == 2 ? std::max(1, num_actions / 80) : 1;
   grid_a = std::max(1, std::min(n_jobs * splits, std::max(1, per_sm_a) * num_sms));
-  rs_group_kernel<R><<<grid_a, block_a, 0, st>>>(gm, work, jobs, item_base, order, n_jobs, counters, plan_step,
-                                                  items, splits);
+  rs_group_kernel<R><<<grid_a, block_a, 0, st>>>(gm, work, jobs, blocks ? nullptr : item_base, order, n_jobs,
+                                                  counters, plan_step, items, splits, lb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (policy != nullptr && R == 1)
     return launch_rs_rollout_mlp_items(gm, work, jobs, item_buf, total_items, counters + 1, policy, plan_step,
                                        num_sms, st);
+  if constexpr (R == 1) {
+    if (blocks) {
+      const size_t kb = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words);
+      int per_sm = occupancy_cached(rs_rollout_blocks_kernel, block_b, kb);
+      if (ctas_b > 0) per_sm = std::min(per_sm, ctas_b);
+      const long long want = (total_items + block_b / 32 - 1) / (block_b / 32);
+      const int grid = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm) * num_sms));
+      rs_rollout_blocks_kernel<<<grid, block_b, kb, st>>>(gm, work, jobs, n_jobs, lb, (unsigned int)total_items,
+                                                           counters + 1, plan_step);
+      return cudaGetLastError();
+    }
+  }
   // phase B keeps the policy-key table in shared memory (limit set by rs_set_key_smem)
   const size_t key_bytes = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words) + rs_stage_bytes<R>(block_b);
   int per_sm_b = occupancy_cached(rs_rollout_items_kernel<R>, block_b, key_bytes);
@@ -1166,9 +1318,13 @@ cudaError_t launch_rs_queue(const DevModel* gm, int robots, int key_words, DevWo
 cudaError_t rs_set_key_smem(int robots, int key_words) {
   // the key table and the item staging of the largest CTA (512 threads)
   const size_t keys = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words);
-  if (robots == 1)
+  if (robots == 1) {
+    cudaError_t e = cudaFuncSetAttribute(rs_rollout_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)keys);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(rs_rollout_items_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(keys + rs_stage_bytes<1>(512)));
+  }
   return cudaFuncSetAttribute(rs_rollout_items_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(keys + rs_stage_bytes<2>(512)));
 }
@@ -1176,12 +1332,15 @@ cudaError_t rs_set_key_smem(int robots, int key_words) {
 cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, int key_words, DevWork* work,
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf, unsigned int* counters, uint32_t plan_step,
-                             int num_sms, int block_b, const void* policy, cudaStream_t st, int warps_a, int ctas_b) {
+                             int num_sms, int block_b, const void* policy, cudaStream_t st, int warps_a, int ctas_b,
+                             const LeafBlocks* blocks) {
+  const LeafBlocks lb = (blocks != nullptr && robots == 1 && policy == nullptr) ? *blocks : LeafBlocks{};
+  if (blocks != nullptr && lb.leaf == nullptr) return cudaErrorInvalidValue;  // block form: one robot, heuristic
   if (robots == 1)
     return launch_two_phase<1>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items,
-                               item_buf, counters, plan_step, num_sms, block_b, policy, st, warps_a, ctas_b);
+                               item_buf, counters, plan_step, num_sms, block_b, policy, st, warps_a, ctas_b, lb);
   return launch_two_phase<2>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items, item_buf,
-                             counters, plan_step, num_sms, block_b, nullptr, st, warps_a, ctas_b);
+                             counters, plan_step, num_sms, block_b, nullptr, st, warps_a, ctas_b, lb);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,

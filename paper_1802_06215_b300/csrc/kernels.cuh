@@ -6,6 +6,20 @@
 
 namespace dsp {
 
+// Phase A's output for the block form of phase B (one robot, heuristic
+// default policy), in place of the rollout-item list: job j's leaf states
+// (position, good, sampled; field-major, n_scen each) at 3 * scen_base[j]
+// words of `leaf`, and chunk_job[u] = j for each of the job's 32-position
+// blocks u in [unit_base[j], unit_base[j] + n_actions * ceil(n_scen / 32)).
+// Phase B rebuilds each (action, scenario)'s item from these, the grouped
+// positions and the children's offsets and keys. leaf == nullptr: items.
+struct LeafBlocks {
+  uint32_t* leaf = nullptr;
+  const long long* scen_base = nullptr;
+  const long long* unit_base = nullptr;
+  int* chunk_job = nullptr;
+};
+
 // Rock Sample: words per rollout item of the two-phase expansion.
 int rs_item_fields(int robots, bool full);  // words per rollout item (full: learned-policy layout)
 // Rock Sample two-phase expansion: phase A over n_jobs jobs (item_base[j] =
@@ -14,6 +28,8 @@ int rs_item_fields(int robots, bool full);  // words per rollout item (full: lea
 // policy: learned pi0 for the rollout phase (one robot), or null for the
 // heuristic policy.
 // order: phase A takes jobs in this order (null: index order).
+// blocks: the block form (one robot, heuristic policy only): item_base and
+// item_buf are unused and total_items is the number of 32-position blocks.
 // Raises the rollout phase's dynamic shared-memory limit to hold the model's
 // policy-key table (m * n * n keys); called once when the model is created.
 cudaError_t rs_set_key_smem(int robots, int key_words);
@@ -22,7 +38,8 @@ cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, in
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
-                             const void* policy, cudaStream_t st, int warps_a = 0, int ctas_b = 0);
+                             const void* policy, cudaStream_t st, int warps_a = 0, int ctas_b = 0,
+                             const LeafBlocks* blocks = nullptr);
 // Learned-policy rollout phase over the item list (one robot).
 cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs,
                                         uint32_t* item_buf, long long total_items, unsigned int* counter,

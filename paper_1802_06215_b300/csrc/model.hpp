@@ -33,6 +33,7 @@ struct dsp_model {
   int tune_ctas_b = 0;               // rollout phase CTAs per SM (Rock Sample, navigation)
   int tune_warps_a = 0;              // Rock Sample grouping phase: warps per CTA
   int tune_ctas_car = 0;             // car kernel CTAs per SM
+  int tune_rs_form = 0;              // one-robot Rock Sample rollout phase: 1 blocks, 2 items (0: items)
   void* policy = nullptr;            // learned pi0 for rollouts (device, transposed BF16 weights)
   bool policy_on = false;
   bool timing = false;               // record events around the expansion kernels
@@ -84,8 +85,16 @@ struct ExpandPlan {
   std::vector<long long> item_base;   // Rock Sample: first rollout item of each job
   std::vector<int> order;             // Rock Sample: jobs by decreasing n_scen * n_actions (phase-A order)
   long long total_items = 0;
+  // Rock Sample, block form of the rollout phase (one robot, heuristic
+  // policy): first 32-position block and first leaf scenario of each job
+  bool blocks = false;
+  std::vector<long long> unit_base, scen_base;
+  long long total_blocks = 0, total_scen = 0;
 };
-dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan);
+// allow_blocks: the block form may be planned (dsp_expand_leaves); the
+// no-allocation entry point and the queue's validation plan items.
+dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan,
+                      bool allow_blocks = false);
 dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,
                          cudaStream_t st);
 

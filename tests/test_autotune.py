@@ -21,7 +21,8 @@ def test_cache_key_and_roundtrip(tmp_path, monkeypatch):
     monkeypatch.setattr(_dsp, "dsp_set_launch_shape", lambda h, **kw: calls.append(kw))
 
     def measure(model, batch, reps):
-        return {"block_b": 512, "ctas_b": 4, "warps_a": 10, "tps": 0, "ctas_car": 0, "ms": 1.5, "default_ms": 1.7}
+        return {"block_b": 512, "ctas_b": 4, "warps_a": 10, "tps": 0, "ctas_car": 0, "rs_form": 2, "ms": 1.5,
+                "default_ms": 1.7}
 
     path = str(tmp_path / "tune.json")
     r1 = autotune.autotune(FakeModel(), None, "NVIDIA B300", path, measure=measure)
@@ -31,7 +32,7 @@ def test_cache_key_and_roundtrip(tmp_path, monkeypatch):
     assert data[key]["block_b"] == 512 and data[key]["warps_a"] == 10 and "B300" in key and "K500" in key
     r2 = autotune.autotune(FakeModel(), None, "NVIDIA B300", path, measure=None)
     assert r2["cached"] is True and calls[-1] == {"block_b": 512, "ctas_b": 4, "warps_a": 10, "tps": 0,
-                                                  "ctas_car": 0}
+                                                  "ctas_car": 0, "rs_form": 2}
     # another GPU name is another entry
     r3 = autotune.autotune(FakeModel(), None, "other GPU", path, measure=measure)
     assert r3["cached"] is False and len(json.load(open(path))) == 2

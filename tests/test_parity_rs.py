@@ -249,3 +249,39 @@ def test_expand_parity_large_jobs(dsp):
         total += o["steps"]
     assert steps == total
     m.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("name", ["rs7_8", "rs15_15", "rs32_32", "rs15_15_k5000"])
+def test_expand_parity_rollout_forms(dsp, name, form):
+    """Both forms of the one-robot rollout phase give the oracle's result:
+    blocks (the rollout phase rebuilds each (action, scenario)'s child state
+    and mask from the leaf states, grouped positions and the children's
+    offsets and keys) and items (a stored rollout item per pair). Ragged jobs
+    with roots and updated leaves, an action subset, |Phi_b| = 1 and 33 (a
+    ragged last block), and, at K = 5000, jobs above 512 scenarios next to
+    small ones."""
+    import dataclasses
+    from paper_1802_06215_b300 import _dsp
+    cfg = I.rs15_15_k(5000) if name == "rs15_15_k5000" else (rs32_32() if name == "rs32_32" else getattr(I, name)())
+    m = dsp.Model(cfg)
+    _dsp.dsp_set_launch_shape(m.h, rs_form=form)
+    om = oracle.Model(cfg)
+    jobs = I.job_stream(cfg, 8, 31)
+    jobs += [dataclasses.replace(jobs[0], idx=jobs[0].idx[:1].copy()),
+             dataclasses.replace(jobs[1], idx=jobs[1].idx[:33].copy(), first_action=3,
+                                 n_actions=m.num_actions - 5)]
+    jb = dsp.JobBatch(m, jobs)
+    m.reset_counters()
+    jb.run()
+    steps, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    total = 0
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, a0=j.first_action, na=j.n_actions,
+                      cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"{name} form {form} job {k}")
+        total += o["steps"]
+    assert steps == total
+    m.close()
