@@ -534,7 +534,10 @@ def measure(args, name, rank, world, dist, local, headline=True):
         autotuned["tuned_shape_ms_per_step"] = t_ms / args.steps
 
     # end to end through the public call: every step copies its inputs in from
-    # pinned host memory and every result out, inside the timed region. Two
+    # pinned host memory and the results a host search reads out (each
+    # child's count, offsets, key and sums; the leaf states and grouped
+    # positions stay on the device for the children's expansions, as in
+    # dsp_plan), inside the timed region. Two
     # job arenas on two streams take alternate steps (double buffering), so
     # one step's transfers overlap the other's kernels; the time is the wall
     # time of all steps, first copy to last result.
@@ -635,7 +638,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
                            "car": "car_expand_kernel",
                            "nav": "nav_group_kernel + nav_rollout_items_kernel (one expansion)"}[kind],
                 "kernel_ms_per_launch": avg_kernel_s * 1000.0,
-                "achieved_hbm_gbs": (jb.input_bytes + jb.output_bytes) / avg_kernel_s / 1e9}
+                "achieved_hbm_gbs": jb.total_bytes / avg_kernel_s / 1e9}
     line = {
         "metric": METRIC, "value": value, "unit": "scenario-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -647,7 +650,10 @@ def measure(args, name, rank, world, dist, local, headline=True):
         "e2e": {"value": e2_value, "unit": "scenario-steps/s", "h2d_bytes_per_step": jb.input_bytes,
                 "d2h_bytes_per_step": jb.output_bytes,
                 "method": "dsp_expand_leaves on two job arenas and two streams taking alternate steps; "
-                          "wall time from the first upload to the last result, L2 flush in each step"},
+                          "wall time from the first upload to the last result, L2 flush in each step; "
+                          "read back: each child's count, offsets, key and reward/u/l sums (what dsp_plan's "
+                          "search reads); the leaf states and grouped positions stay on the device",
+                "device_resident_bytes_per_step": jb.device_out_bytes},
         "gpu_launches": args.steps * kernels_per_step,
         "launch_shape": _dsp.dsp_get_launch_shape(m.h),
         "roofline": roof,

@@ -89,9 +89,13 @@ class Model:
 
 
 class JobBatch:
-    """Jobs packed in one device arena; inputs first (parents, indexes), then
-    results. `host_inputs` is a pinned copy of the input part for end-to-end
-    runs that copy inputs in and results out every step."""
+    """Jobs packed in one device arena: inputs first (parents, indexes), then
+    the results that stay on the device (each leaf's states and grouped
+    positions: the parent block and index lists of the children's later
+    expansions), then the per-child results a host tree search reads (counts,
+    offsets, keys, reward, u and l sums). `host_inputs` is a pinned copy of
+    the input part for end-to-end runs that copy inputs in and the host-read
+    results out every step, as dsp_plan does."""
 
     def __init__(self, model, jobs, device="cuda", child_cap=None):
         self.model = model
@@ -114,15 +118,19 @@ class JobBatch:
             cap = model.max_children(n) if child_cap is None else child_cap
             e["n"], e["na"], e["cap"] = n, na, cap
             e["leaf"] = off; off = _align(off + 4 * W * n)
+            e["perm"] = off; off = _align(off + 2 * na * n)
+        self.host_out_start = off
+        for j, na, e in zip(jobs, na_all, layout):
+            cap = e["cap"]
             e["cc"] = off; off = _align(off + 4 * na)
             e["co"] = off; off = _align(off + 4 * na * (cap + 1))
             e["key"] = off; off = _align(off + 8 * na * cap)
             e["rew"] = off; off = _align(off + 8 * na * cap)
             e["u"] = off; off = _align(off + 8 * na * cap)
             e["l"] = off; off = _align(off + 8 * na * cap)
-            e["perm"] = off; off = _align(off + 2 * na * n)
         self.total_bytes = off
-        self.output_bytes = off - self.input_bytes
+        self.device_out_bytes = self.host_out_start - self.input_bytes  # leaf states, grouped positions
+        self.output_bytes = off - self.host_out_start  # what download_outputs copies
         self.layout = layout
         host = torch.zeros(self.input_bytes, dtype=torch.uint8, pin_memory=True)
         hn = host.numpy()
@@ -168,10 +176,11 @@ class JobBatch:
         self.arena[: self.input_bytes].copy_(self.host_inputs, non_blocking=True)
 
     def download_outputs(self):
-        """Device -> host copy of every result array (pinned)."""
+        """Device -> host copy (pinned) of the per-child results a host tree
+        search reads; leaf states and grouped positions stay on the device."""
         if self.host_outputs is None:
             self.host_outputs = torch.zeros(self.output_bytes, dtype=torch.uint8, pin_memory=True)
-        self.host_outputs.copy_(self.arena[self.input_bytes:], non_blocking=True)
+        self.host_outputs.copy_(self.arena[self.host_out_start:], non_blocking=True)
         return self.host_outputs
 
     def results(self, k):
