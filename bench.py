@@ -372,7 +372,8 @@ def training_step_rate(_dsp, na, peak, batch=16384, steps=20):
     flop = 6 * batch * (64 * 256 + 256 * 256 + 256 * 32)
     return {"batch": batch, "ms_per_step": dt * 1000.0, "samples_per_s": batch / dt,
             "tflops": flop / dt / 1e12, "frac_of_bf16_peak": flop / dt / 1e12 / peak if peak else None,
-            "note": "wall time per step (the loss is read back every step); mma.sync 64x64 tiles, weight gradients split over the batch"}
+            "note": "wall time per step (the loss is read back every step); tcgen05 GEMMs, 128-row tiles, FP32 "
+                    "accumulators in tensor memory, weight gradients split over the batch"}
 
 
 def combine_ranks(t_ms, steps, dist, device):

@@ -1,7 +1,8 @@
 // Training of the learned default policy pi0: softmax cross-entropy on
 // (state features, action label) pairs with this library's own kernels: BF16
-// GEMMs on the tensor cores (mma.sync m16n8k16, FP32 accumulation) with fused
-// epilogues, softmax cross-entropy, column sums for the bias gradients, and
+// GEMMs on the fifth-generation tensor cores (tcgen05.mma, FP32 accumulators
+// in tensor memory) with fused epilogues, softmax cross-entropy, column sums
+// for the bias gradients, and
 // Adam on FP32 master weights with BF16 copies for the next step. The labels
 // are the caller's: the shipped weights were trained on approximate
 // policy-iteration labels (the best allowed action by a leaf expansion's Q
@@ -17,136 +18,295 @@
 #include <vector>
 
 #include "mlp.cuh"
+#include "tc_mlp.cuh"
 #include "model.hpp"
 
 struct dsp_mlp {
   int max_batch = 0;
+  int ldt = 0;                 // row length of the transposed activations: max_batch rounded up to 128
   long long step = 0;
   float* master = nullptr;     // device FP32 parameters (packed)
   float* adam_m = nullptr;     // device Adam first moments
   float* adam_v = nullptr;     // device Adam second moments
   float* grad = nullptr;       // device FP32 gradients (packed)
-  __nv_bfloat16* wb = nullptr; // device BF16 copies of W1, W2, W3 (input-major)
+  __nv_bfloat16* wb = nullptr; // device BF16 W1, W2, W3 input-major ([in][out]): B operands of the backward pass
+  __nv_bfloat16* wt = nullptr; // device BF16 W1, W2, W3 output-major ([out][in]): B operands of the forward pass
+  // activations and their gradients, row-major [batch][features] and
+  // transposed [features][ldt] (the K-major operands of the weight gradients)
   __nv_bfloat16 *xb = nullptr, *h1 = nullptr, *h2 = nullptr, *dl = nullptr, *dh1 = nullptr, *dh2 = nullptr;
+  __nv_bfloat16 *xt = nullptr, *h1t = nullptr, *h2t = nullptr, *dlt = nullptr, *dh1t = nullptr, *dh2t = nullptr;
   float* logits = nullptr;
   float* loss = nullptr;       // device scalar
+  float* ws = nullptr;          // split-K partial weight gradients: kMaxSplits x 256 x 256
+  unsigned int* status = nullptr;  // device: nonzero once a tensor-core wait ran out
 };
 
 namespace dsp {
 namespace {
 
-constexpr int kTile = 64, kTileK = 32, kPad = 8;
+// ------------------------------------------------------------------ GEMM ---
+// C = A B^T on the fifth-generation tensor cores: A [M][K] and B [N][K], both
+// BF16 with K contiguous (the canonical K-major operands), FP32 accumulators
+// in tensor memory. A CTA of 128 threads owns a 128-row tile of C and all N
+// (<= 256) columns; grid.y splits K into slices whose partial tiles add into
+// C (weight gradients, K = batch). Two pipeline stages of 64 along K: all
+// threads copy a stage's operands into shared memory with cp.async in the
+// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix), thread 0
+// issues its four K = 16 MMAs and commits them to the stage's mbarrier, and
+// the next stage's copy overlaps them. Each thread then reads its row from
+// tensor memory for the epilogue. Every wait is bounded; a wait that runs
+// out sets *status.
+constexpr int kTileM = 128;   // rows per CTA: the MMA's M
+constexpr int kStageK = 64;   // K per pipeline stage
+constexpr int kGemmThreads = 128;
 
-// kAddF32 adds the tile into Cf with FP32 atomics: the split-K form, where
-// gridDim.z CTAs each reduce one slice of K into the same zeroed output.
-enum Epilogue { kStoreF32 = 0, kBiasReluBf16 = 1, kBiasF32 = 2, kMaskReluBf16 = 3, kAddF32 = 4 };
+// kBiasRelu: ReLU(acc + bias) as BF16 (hidden layers); kBiasF32: acc + bias
+// (logits); kMaskRelu: acc where mask > 0, else 0, as BF16 (the gradient
+// through a ReLU); kPartialF32: the K slice's partial tile, to slab
+// blockIdx.y of a workspace that reduce_splits sums (weight gradients; the
+// sum does not depend on timing, so the gradient is reproducible).
+enum Epilogue { kBiasRelu = 0, kBiasF32 = 1, kMaskRelu = 2, kPartialF32 = 3 };
+constexpr int kSplitCTAs = 148;  // split-K: about one CTA per SM over the grid
+constexpr int kMaxSplits = (kSplitCTAs + 1) / 2;  // for the two 128-row tiles of a 256-row weight gradient
 
-// C[M][N] = op(A)[M][K] op(B)[K][N]. A: row-major [M][K] (TA = false) or
-// stored [K][M] (TA = true); B: stored [K][N] (TB = false) or [N][K]
-// (TB = true). 128 threads, a 64 x 64 tile, warps 2 x 2 of 32 x 32. The CTA
-// at blockIdx.z takes K's slice [z * kslice, (z + 1) * kslice).
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16* __restrict__ A, int lda,
-                                                 const __nv_bfloat16* __restrict__ B, int ldb, int M, int N, int K,
-                                                 float* Cf, __nv_bfloat16* Cb, int ldc, const float* bias,
-                                                 const __nv_bfloat16* mask, int kslice) {
-  __shared__ __align__(16) __nv_bfloat16 sA[kTile][kTileK + kPad];
-  __shared__ __align__(16) __nv_bfloat16 sB[kTile][kTileK + kPad];  // [n][k]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
-  const int g = lane >> 2, t = lane & 3;
-  const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.0f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int k0 = kb; k0 < ke; k0 += kTileK) {
-    // consecutive threads take consecutive addresses of each operand: along
-    // k for a row-major A and a [N][K] B, along m or n for the others
-    for (int e = tid; e < kTile * kTileK; e += 128) {
-      const int r = TA ? e % kTile : e / kTileK, c = TA ? e / kTile : e % kTileK;
-      const int m = m0 + r, k = k0 + c;
-      __nv_bfloat16 va = zero;
-      if (m < M && k < ke) va = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
-      sA[r][c] = va;
-    }
-    for (int e = tid; e < kTile * kTileK; e += 128) {
-      const int r = TB ? e / kTileK : e % kTile, c = TB ? e % kTileK : e / kTile;
-      const int n = n0 + r, k = k0 + c;
-      __nv_bfloat16 vb = zero;
-      if (n < N && k < ke) vb = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
-      sB[r][c] = vb;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTileK; kk += 16) {
-      uint32_t af[2][4], bf[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        int r = wm + 16 * i + g;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&sA[r][kk + 2 * t]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][kk + 2 * t]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&sA[r][kk + 2 * t + 8]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][kk + 2 * t + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        int c = wn + 8 * j + g;
-        bf[j][0] = *reinterpret_cast<const uint32_t*>(&sB[c][kk + 2 * t]);
-        bf[j][1] = *reinterpret_cast<const uint32_t*>(&sB[c][kk + 2 * t + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        int m = m0 + wm + 16 * i + g + (c >= 2 ? 8 : 0);
-        int n = n0 + wn + 8 * j + 2 * t + (c & 1);
-        if (m >= M || n >= N) continue;
-        float v = acc[i][j][c];
-        size_t o = (size_t)m * ldc + n;
-        if (EPI == kStoreF32) {
-          Cf[o] = v;
-        } else if (EPI == kAddF32) {
-          atomicAdd(Cf + o, v);
-        } else if (EPI == kBiasReluBf16) {
-          v += bias[n];
-          Cb[o] = __float2bfloat16_rn(v > 0.0f ? v : 0.0f);
-        } else if (EPI == kBiasF32) {
-          Cf[o] = v + bias[n];
-        } else {
-          Cb[o] = __float2bfloat16_rn(__bfloat162float(mask[o]) > 0.0f ? v : 0.0f);
-        }
-      }
+struct GemmArgs {
+  const __nv_bfloat16* A;
+  int lda;                      // [M][K] (rows of A beyond M read as 0)
+  const __nv_bfloat16* B;
+  int ldb;                      // [N][K]
+  int M, N, K;                  // K: a multiple of 8 (beyond K: 0)
+  int kslice;                   // K per CTA along grid.y, a multiple of kStageK
+  const float* bias;            // [N]
+  const __nv_bfloat16* mask;    // [M][ldc]
+  __nv_bfloat16* Cb;            // BF16 result [M][ldc]
+  int ldc;
+  __nv_bfloat16* Ct;            // its transpose [N][ldt], rows of the tile beyond M written as 0; or null
+  int ldt;
+  float* Cf;                    // kBiasF32: [M][ldm] row-major; kPartialF32: workspace [splits][M][N]
+  long long ldm;
+  unsigned int* status;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 
-__global__ void to_bf16(const float* x, __nv_bfloat16* y, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = __float2bfloat16_rn(x[i]);
+template <int EPI, int N>
+__global__ void __launch_bounds__(kGemmThreads) gemm_tc(GemmArgs g) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr uint32_t kBytesA = kTileM * kStageK * 2, kBytesB = N * kStageK * 2, kStage = kBytesA + kBytesB;
+  constexpr uint32_t kCols = N;  // 32, 64 or 256 FP32 columns (a power of two, at least 32)
+  constexpr uint32_t kIdesc = tc::idesc_bf16(kTileM, N);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kTileM;
+  const int kb = blockIdx.y * g.kslice, ke = min(g.K, kb + g.kslice);
+  const int nk = ke > kb ? (ke - kb + kStageK - 1) / kStageK : 0;
+  const uint32_t mb0 = tc::smem_u32(&mbar[0]), mb1 = tc::smem_u32(&mbar[1]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  // stage s <- K columns [kb + 64 c, kb + 64 c + 64) of the tile's A rows and all B rows
+  auto load = [&](int c, int s) {
+    const int k0 = kb + c * kStageK;
+    const uint32_t sa = tc::smem_u32(smem + s * kStage), sb = sa + kBytesA;
+    for (int i = tid; i < kTileM * (kStageK / 8); i += kGemmThreads) {
+      const int r = i / (kStageK / 8), ch = i % (kStageK / 8), m = m0 + r, k = k0 + 8 * ch;
+      const bool in = m < g.M && k < ke;
+      cp_async16(sa + tc::kmajor_off(r, 8 * ch, kStageK), in ? (const void*)(g.A + (size_t)m * g.lda + k) : g.A,
+                 in ? 16u : 0u);
+    }
+    for (int i = tid; i < N * (kStageK / 8); i += kGemmThreads) {
+      const int r = i / (kStageK / 8), ch = i % (kStageK / 8), k = k0 + 8 * ch;
+      const bool in = r < g.N && k < ke;
+      cp_async16(sb + tc::kmajor_off(r, 8 * ch, kStageK), in ? (const void*)(g.B + (size_t)r * g.ldb + k) : g.B,
+                 in ? 16u : 0u);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  bool ok = true;
+  if (nk > 0) load(0, 0);
+  for (int c = 0; c < nk; ++c) {
+    const int s = c & 1;
+    if (c + 1 < nk) {
+      // stage s ^ 1 last held chunk c - 1: its MMAs must be done reading it
+      if (c >= 1) ok = tc::mbar_wait(s ? mb0 : mb1, ((c - 1) >> 1) & 1) && ok;
+      load(c + 1, s ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    tc::fence_async_smem();  // this thread's copies, visible to the tensor cores
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(smem + s * kStage), sb = sa + kBytesA;
+      const int k16 = min(kStageK / 16, (ke - (kb + c * kStageK) + 15) / 16);
+      for (int k = 0; k < k16; ++k)
+        tc::mma_ss(tmem, tc::smem_desc(sa + 256 * k, 128, (kStageK / 8) * 128),
+                   tc::smem_desc(sb + 256 * k, 128, (kStageK / 8) * 128), kIdesc, (c > 0 || k > 0) ? 1u : 0u);
+      tc::mma_commit(s ? mb1 : mb0);
+    }
+  }
+  if (nk > 0) ok = tc::mbar_wait(((nk - 1) & 1) ? mb1 : mb0, ((nk - 1) >> 1) & 1) && ok;
+  tc::fence_after_sync();
+  if (!ok && g.status != nullptr) atomicOr(g.status, 1u);
+
+  // epilogue: thread (warp, lane) owns row m0 + 32 warp + lane (tensor-memory lane 32 warp + lane)
+  const int m = m0 + 32 * warp + lane;
+  const bool row = m < g.M;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  // the pipeline's stages are dead now: each warp's 32 x 32 transpose tile
+  __nv_bfloat16(*tp)[34] = reinterpret_cast<__nv_bfloat16(*)[34]>(smem + warp * 32 * 34 * 2);
+  if (nk > 0 && ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(trow + c0, v);
+      if (EPI == kPartialF32) {
+        if (row) {
+          float4* dst = reinterpret_cast<float4*>(g.Cf + ((size_t)blockIdx.y * g.M + m) * N + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      } else if (EPI == kBiasF32) {
+        if (row) {
+          float4* dst = reinterpret_cast<float4*>(g.Cf + (size_t)m * g.ldm + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            dst[q] = make_float4(__fadd_rn(v[4 * q], g.bias[c0 + 4 * q]), __fadd_rn(v[4 * q + 1], g.bias[c0 + 4 * q + 1]),
+                                 __fadd_rn(v[4 * q + 2], g.bias[c0 + 4 * q + 2]),
+                                 __fadd_rn(v[4 * q + 3], g.bias[c0 + 4 * q + 3]));
+        }
+      } else {
+        __nv_bfloat16 mk[32];
+        if (EPI == kMaskRelu) {
+          uint4* mv = reinterpret_cast<uint4*>(mk);
+          const uint4* src = reinterpret_cast<const uint4*>(g.mask + (size_t)m * g.ldc + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) mv[q] = row ? src[q] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        __nv_bfloat16 o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float x;
+          if (EPI == kBiasRelu)
+            x = fmaxf(__fadd_rn(v[j], g.bias[c0 + j]), 0.0f);
+          else
+            x = __bfloat162float(mk[j]) > 0.0f ? v[j] : 0.0f;
+          o[j] = __float2bfloat16_rn(row ? x : 0.0f);
+        }
+        if (row) {
+          uint4* dst = reinterpret_cast<uint4*>(g.Cb + (size_t)m * g.ldc + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
+        }
+        if (g.Ct != nullptr) {
+          // through the warp's tile: lane r writes row r, then lane j reads
+          // column j and stores its 32 rows as 64 contiguous bytes
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tp[lane][j] = o[j];
+          __syncwarp();
+          __nv_bfloat16 col[32];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) col[r] = tp[r][lane];
+          uint4* dst = reinterpret_cast<uint4*>(g.Ct + (size_t)(c0 + lane) * g.ldt + m0 + 32 * warp);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(col)[q];
+          __syncwarp();
+        }
+      }
+    }
+  }
+  // a wait that ran out: wait once more (bounded) for the last MMAs before
+  // the tensor memory is freed
+  if (nk > 0 && !ok) tc::mbar_wait(((nk - 1) & 1) ? mb1 : mb0, ((nk - 1) >> 1) & 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+template <int EPI, int N>
+cudaError_t gemm(GemmArgs g, cudaStream_t st, int* splits_out = nullptr) {
+  constexpr size_t smem = 2 * (size_t)(kTileM * kStageK * 2 + N * kStageK * 2) + 64;
+  static bool attr = false;  // set once per process (the attribute is per function)
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc<EPI, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int splits = 1;
+  const int tiles = (g.M + kTileM - 1) / kTileM;
+  if (EPI == kPartialF32) {  // about one CTA per SM, at most kMaxSplits slabs
+    const int chunks = (g.K + kStageK - 1) / kStageK;
+    splits = std::max(1, std::min({chunks, (kSplitCTAs + tiles - 1) / tiles, kMaxSplits}));
+    g.kslice = ((chunks + splits - 1) / splits) * kStageK;
+    splits = (g.K + g.kslice - 1) / g.kslice;
+  } else {
+    g.kslice = ((g.K + kStageK - 1) / kStageK) * kStageK;
+  }
+  gemm_tc<EPI, N><<<dim3(tiles, splits), kGemmThreads, smem, st>>>(g);
+  if (splits_out != nullptr) *splits_out = splits;
+  return cudaGetLastError();
+}
+
+// out[m * ldm + n * ldn] = sum over the split-K slabs of ws[s][m][n].
+__global__ void reduce_splits(const float* __restrict__ ws, int splits, int M, int N, float* out, int ldm,
+                              int ldn) {
+  const int total = M * N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (int s = 0; s < splits; ++s) acc += ws[(size_t)s * total + i];
+    out[(size_t)(i / N) * ldm + (size_t)(i % N) * ldn] = acc;
+  }
+}
+
+// A weight gradient C[M][N] = A B^T over K = the padded batch, split over K,
+// summed into out[m * ldm + n * ldn].
+template <int N>
+cudaError_t weight_grad(GemmArgs g, float* ws, float* out, int ldm, int ldn, cudaStream_t st) {
+  g.Cf = ws;
+  int splits = 1;
+  cudaError_t e = gemm<kPartialF32, N>(g, st, &splits);
+  if (e != cudaSuccess) return e;
+  reduce_splits<<<(g.M * N + 255) / 256, 256, 0, st>>>(ws, splits, g.M, N, out, ldm, ldn);
+  return cudaGetLastError();
+}
+
+// X (FP32 [B][64]) -> xb (BF16, row-major) and xt ([64][ldt], zero for rows
+// B .. rounded up to the tile).
+__global__ void to_bf16(const float* x, __nv_bfloat16* xb, __nv_bfloat16* xt, int B, int Bpad, int ldt) {
+  const size_t n = (size_t)Bpad * kMlpIn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % kMlpIn), b = (int)(i / kMlpIn);
+    const __nv_bfloat16 v = __float2bfloat16_rn(b < B ? x[i] : 0.0f);
+    if (b < B) xb[i] = v;
+    xt[(size_t)k * ldt + b] = v;
+  }
 }
 
 // Per row: loss -log softmax(logits[:na])[y] (summed into *loss) and
-// dlogits = (softmax - onehot) / B (zero past na), in BF16.
-__global__ void softmax_ce(const float* logits, const int32_t* y, int B, int na, __nv_bfloat16* dl, float* loss) {
+// dlogits = (softmax - onehot) / B (zero past na), in BF16, row-major and
+// transposed (rows B .. Bpad of the transpose are 0).
+__global__ void softmax_ce(const float* logits, const int32_t* y, int B, int Bpad, int na, __nv_bfloat16* dl,
+                           __nv_bfloat16* dlt, int ldt, float* loss) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bpad) return;
   const bool live = i < B;
   const float* l = logits + (size_t)(live ? i : 0) * kMlpOut;
   float mx = l[0];
@@ -156,18 +316,19 @@ __global__ void softmax_ce(const float* logits, const int32_t* y, int B, int na,
   const int yi = live ? y[i] : 0;
   float li = live ? -(l[yi] - mx - logf(z)) : 0.0f;
   for (int o = 16; o > 0; o >>= 1) li += __shfl_down_sync(0xFFFFFFFFu, li, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, li);  // one atomic per warp
-  if (!live) return;
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, li);  // one atomic per warp (Bpad is a multiple of 32)
   for (int a = 0; a < kMlpOut; ++a) {
-    float p = a < na ? expf(l[a] - mx) / z : 0.0f;
-    dl[(size_t)i * kMlpOut + a] = __float2bfloat16_rn((p - (a == yi ? 1.0f : 0.0f)) / (float)B);
+    const float p = a < na ? expf(l[a] - mx) / z : 0.0f;
+    const __nv_bfloat16 d = __float2bfloat16_rn(live ? (p - (a == yi ? 1.0f : 0.0f)) / (float)B : 0.0f);
+    if (live) dl[(size_t)i * kMlpOut + a] = d;
+    dlt[(size_t)a * ldt + i] = d;
   }
 }
 
 // out[n] += sum over rows of x[row][n]: CTA b sums rows [b * kColRows,
 // (b + 1) * kColRows) for every column (one thread per column) and adds its
 // partial sums into the zeroed out.
-constexpr int kColRows = 128;
+constexpr int kColRows = 32;
 __global__ void col_sum(const __nv_bfloat16* x, int rows, int cols, float* out) {
   const int n = threadIdx.x;
   if (n >= cols) return;
@@ -189,27 +350,24 @@ __global__ void adam(float* p, float* m, float* v, const float* g, int n, float 
   }
 }
 
-__global__ void pack_weights_bf16(const float* master, __nv_bfloat16* wb) {
+// BF16 copies of the master weights, input-major ([in][out], wb) and
+// output-major ([out][in], wt).
+__global__ void pack_weights_bf16(const float* master, __nv_bfloat16* wb, __nv_bfloat16* wt) {
   const int n1 = kMlpIn * kMlpHid, n2 = kMlpHid * kMlpHid, n3 = kMlpHid * kMlpOut;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2 + n3; i += gridDim.x * blockDim.x) {
-    float v = i < n1 ? master[kOffW1 + i] : (i < n1 + n2 ? master[kOffW2 + i - n1] : master[kOffW3 + i - n1 - n2]);
-    wb[i] = __float2bfloat16_rn(v);
+    int base, in_dim, out_dim, off;
+    if (i < n1) {
+      base = 0, in_dim = kMlpIn, out_dim = kMlpHid, off = kOffW1;
+    } else if (i < n1 + n2) {
+      base = n1, in_dim = kMlpHid, out_dim = kMlpHid, off = kOffW2;
+    } else {
+      base = n1 + n2, in_dim = kMlpHid, out_dim = kMlpOut, off = kOffW3;
+    }
+    const int r = i - base, in = r / out_dim, out = r % out_dim;
+    const __nv_bfloat16 v = __float2bfloat16_rn(master[off + r]);
+    wb[i] = v;
+    wt[base + out * in_dim + in] = v;
   }
-}
-
-template <bool TA, bool TB, int EPI>
-cudaError_t gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K, float* Cf,
-                 __nv_bfloat16* Cb, int ldc, const float* bias, const __nv_bfloat16* mask, cudaStream_t st) {
-  // a long K over few output tiles (the weight gradients, K = batch) is
-  // split so that the grid covers the SMs; the slices add into Cf
-  int splits = 1;
-  const int tiles = ((N + kTile - 1) / kTile) * ((M + kTile - 1) / kTile);
-  if (EPI == kAddF32) splits = std::max(1, std::min((K + 511) / 512, (4 * 148 + tiles - 1) / tiles));
-  const int kslice = ((K + splits - 1) / splits + kTileK - 1) / kTileK * kTileK;
-  splits = (K + kslice - 1) / kslice;
-  dim3 grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile, splits);
-  gemm_bf16<TA, TB, EPI><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, Cb, ldc, bias, mask, kslice);
-  return cudaGetLastError();
 }
 
 cudaError_t col_sums(const __nv_bfloat16* x, int rows, int cols, float* out, cudaStream_t st) {
@@ -217,50 +375,79 @@ cudaError_t col_sums(const __nv_bfloat16* x, int rows, int cols, float* out, cud
   return cudaGetLastError();
 }
 
-// Forward pass on X (device, FP32, B x 64): xb, h1, h2 (BF16) and logits.
+int pad_rows(int B) { return (B + kTileM - 1) / kTileM * kTileM; }
+
+GemmArgs gemm_args(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+                   unsigned int* status) {
+  GemmArgs g{};
+  g.A = A, g.lda = lda, g.B = B, g.ldb = ldb, g.M = M, g.N = N, g.K = K, g.status = status;
+  return g;
+}
+
+// Forward pass on X (device, FP32, B x 64): xb, xt, h1, h1t, h2, h2t (BF16)
+// and the logits (FP32).
 cudaError_t forward(dsp_mlp* q, const float* X, int B, cudaStream_t st) {
-  const __nv_bfloat16* W1 = q->wb;
-  const __nv_bfloat16* W2 = q->wb + kMlpIn * kMlpHid;
-  const __nv_bfloat16* W3 = W2 + kMlpHid * kMlpHid;
-  to_bf16<<<64, 256, 0, st>>>(X, q->xb, (size_t)B * kMlpIn);
-  cudaError_t e = gemm<false, false, kBiasReluBf16>(q->xb, kMlpIn, W1, kMlpHid, B, kMlpHid, kMlpIn, nullptr, q->h1,
-                                                    kMlpHid, q->master + kOffB1, nullptr, st);
-  if (e == cudaSuccess)
-    e = gemm<false, false, kBiasReluBf16>(q->h1, kMlpHid, W2, kMlpHid, B, kMlpHid, kMlpHid, nullptr, q->h2, kMlpHid,
-                                          q->master + kOffB2, nullptr, st);
-  if (e == cudaSuccess)
-    e = gemm<false, false, kBiasF32>(q->h2, kMlpHid, W3, kMlpOut, B, kMlpOut, kMlpHid, q->logits, nullptr, kMlpOut,
-                                     q->master + kOffB3, nullptr, st);
+  const int Bp = pad_rows(B);
+  const __nv_bfloat16* W1t = q->wt;
+  const __nv_bfloat16* W2t = q->wt + kMlpIn * kMlpHid;
+  const __nv_bfloat16* W3t = W2t + kMlpHid * kMlpHid;
+  to_bf16<<<256, 256, 0, st>>>(X, q->xb, q->xt, B, Bp, q->ldt);
+  // H1 = ReLU(X W1 + b1): A = X [B][64], B operand W1^T [256][64]
+  GemmArgs g = gemm_args(q->xb, kMlpIn, W1t, kMlpIn, B, kMlpHid, kMlpIn, q->status);
+  g.bias = q->master + kOffB1, g.Cb = q->h1, g.ldc = kMlpHid, g.Ct = q->h1t, g.ldt = q->ldt;
+  cudaError_t e = gemm<kBiasRelu, kMlpHid>(g, st);
+  // H2 = ReLU(H1 W2 + b2)
+  g = gemm_args(q->h1, kMlpHid, W2t, kMlpHid, B, kMlpHid, kMlpHid, q->status);
+  g.bias = q->master + kOffB2, g.Cb = q->h2, g.ldc = kMlpHid, g.Ct = q->h2t, g.ldt = q->ldt;
+  if (e == cudaSuccess) e = gemm<kBiasRelu, kMlpHid>(g, st);
+  // logits = H2 W3 + b3
+  g = gemm_args(q->h2, kMlpHid, W3t, kMlpHid, B, kMlpOut, kMlpHid, q->status);
+  g.bias = q->master + kOffB3, g.Cf = q->logits, g.ldm = kMlpOut;
+  if (e == cudaSuccess) e = gemm<kBiasF32, kMlpOut>(g, st);
   return e;
 }
 
-// Loss and packed FP32 gradient into q->grad (after a forward pass).
+// Loss and packed FP32 gradient into q->grad (after a forward pass). The
+// weight gradients reduce over the batch: K = the padded batch of the
+// transposed activations (the padding is 0).
 cudaError_t backward(dsp_mlp* q, const int32_t* y, int B, int na, cudaStream_t st) {
+  const int Bp = pad_rows(B);
   const __nv_bfloat16* W2 = q->wb + kMlpIn * kMlpHid;
   const __nv_bfloat16* W3 = W2 + kMlpHid * kMlpHid;
   cudaMemsetAsync(q->loss, 0, sizeof(float), st);
-  cudaMemsetAsync(q->grad, 0, kMlpParams * sizeof(float), st);  // the split-K GEMMs and column sums add into it
-  softmax_ce<<<(B + 127) / 128, 128, 0, st>>>(q->logits, y, B, na, q->dl, q->loss);
-  // dW3 = H2^T dL, db3 = colsum(dL)
-  cudaError_t e = gemm<true, false, kAddF32>(q->h2, kMlpHid, q->dl, kMlpOut, kMlpHid, kMlpOut, B,
-                                               q->grad + kOffW3, nullptr, kMlpOut, nullptr, nullptr, st);
+  cudaMemsetAsync(q->grad, 0, kMlpParams * sizeof(float), st);  // the bias column sums add into it
+  softmax_ce<<<Bp / 128, 128, 0, st>>>(q->logits, y, B, Bp, na, q->dl, q->dlt, q->ldt, q->loss);
+  // dW3[in][out] = sum_b H2[b][in] dL[b][out]: C[M = in][N = out], A = H2^T, B operand dL^T
+  GemmArgs g = gemm_args(q->h2t, q->ldt, q->dlt, q->ldt, kMlpHid, kMlpOut, Bp, q->status);
+  cudaError_t e = weight_grad<kMlpOut>(g, q->ws, q->grad + kOffW3, kMlpOut, 1, st);
   if (e == cudaSuccess) e = col_sums(q->dl, B, kMlpOut, q->grad + kOffB3, st);
-  // dH2 = (dL W3^T) masked by H2 > 0
-  if (e == cudaSuccess)
-    e = gemm<false, true, kMaskReluBf16>(q->dl, kMlpOut, W3, kMlpOut, B, kMlpHid, kMlpOut, nullptr, q->dh2, kMlpHid,
-                                         nullptr, q->h2, st);
-  if (e == cudaSuccess)
-    e = gemm<true, false, kAddF32>(q->h1, kMlpHid, q->dh2, kMlpHid, kMlpHid, kMlpHid, B, q->grad + kOffW2,
-                                     nullptr, kMlpHid, nullptr, nullptr, st);
+  // dH2 = (dL W3^T) where H2 > 0: A = dL [B][32], B operand W3 [256 in][32 out]
+  g = gemm_args(q->dl, kMlpOut, W3, kMlpOut, B, kMlpHid, kMlpOut, q->status);
+  g.mask = q->h2, g.Cb = q->dh2, g.ldc = kMlpHid, g.Ct = q->dh2t, g.ldt = q->ldt;
+  if (e == cudaSuccess) e = gemm<kMaskRelu, kMlpHid>(g, st);
+  // dW2[in][out] = sum_b H1[b][in] dH2[b][out]
+  g = gemm_args(q->h1t, q->ldt, q->dh2t, q->ldt, kMlpHid, kMlpHid, Bp, q->status);
+  if (e == cudaSuccess) e = weight_grad<kMlpHid>(g, q->ws, q->grad + kOffW2, kMlpHid, 1, st);
   if (e == cudaSuccess) e = col_sums(q->dh2, B, kMlpHid, q->grad + kOffB2, st);
-  if (e == cudaSuccess)
-    e = gemm<false, true, kMaskReluBf16>(q->dh2, kMlpHid, W2, kMlpHid, B, kMlpHid, kMlpHid, nullptr, q->dh1,
-                                         kMlpHid, nullptr, q->h1, st);
-  if (e == cudaSuccess)
-    e = gemm<true, false, kAddF32>(q->xb, kMlpIn, q->dh1, kMlpHid, kMlpIn, kMlpHid, B, q->grad + kOffW1, nullptr,
-                                     kMlpHid, nullptr, nullptr, st);
+  // dH1 = (dH2 W2^T) where H1 > 0: B operand W2 [256 in][256 out]
+  g = gemm_args(q->dh2, kMlpHid, W2, kMlpHid, B, kMlpHid, kMlpHid, q->status);
+  g.mask = q->h1, g.Cb = q->dh1, g.ldc = kMlpHid, g.Ct = q->dh1t, g.ldt = q->ldt;
+  if (e == cudaSuccess) e = gemm<kMaskRelu, kMlpHid>(g, st);
+  // dW1[in][out] = sum_b X[b][in] dH1[b][out], as C[M = out][N = in] (A = dH1^T,
+  // B operand X^T), written transposed
+  g = gemm_args(q->dh1t, q->ldt, q->xt, q->ldt, kMlpHid, kMlpIn, Bp, q->status);
+  if (e == cudaSuccess) e = weight_grad<kMlpIn>(g, q->ws, q->grad + kOffW1, 1, kMlpHid, st);
   if (e == cudaSuccess) e = col_sums(q->dh1, B, kMlpHid, q->grad + kOffB1, st);
   if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+// The tensor-core status word: a wait that ran out makes the call fail.
+cudaError_t check_status(dsp_mlp* q, cudaStream_t st, bool* timed_out) {
+  unsigned int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, q->status, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *timed_out = h != 0;
   return e;
 }
 
@@ -276,14 +463,25 @@ dsp_status dsp_mlp_create(int32_t max_batch, uint64_t seed, dsp_mlp** out) {
   *out = nullptr;
   dsp_mlp* q = new dsp_mlp();
   q->max_batch = max_batch;
+  q->ldt = pad_rows(max_batch);
   const size_t P = kMlpParams * sizeof(float);
   const size_t W = (size_t)(kMlpIn * kMlpHid + kMlpHid * kMlpHid + kMlpHid * kMlpOut) * sizeof(__nv_bfloat16);
-  const size_t B = (size_t)max_batch;
+  const size_t B = (size_t)max_batch, T = (size_t)q->ldt;
   cudaError_t e = cudaMalloc(&q->master, P);
   if (e == cudaSuccess) e = cudaMalloc(&q->adam_m, P);
   if (e == cudaSuccess) e = cudaMalloc(&q->adam_v, P);
   if (e == cudaSuccess) e = cudaMalloc(&q->grad, P);
   if (e == cudaSuccess) e = cudaMalloc(&q->wb, W);
+  if (e == cudaSuccess) e = cudaMalloc(&q->wt, W);
+  if (e == cudaSuccess) e = cudaMalloc(&q->xt, T * kMlpIn * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&q->h1t, T * kMlpHid * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&q->h2t, T * kMlpHid * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&q->dh1t, T * kMlpHid * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&q->dh2t, T * kMlpHid * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&q->dlt, T * kMlpOut * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&q->ws, (size_t)kMaxSplits * kMlpHid * kMlpHid * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&q->status, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(q->status, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&q->xb, B * kMlpIn * 2);
   if (e == cudaSuccess) e = cudaMalloc(&q->h1, B * kMlpHid * 2);
   if (e == cudaSuccess) e = cudaMalloc(&q->h2, B * kMlpHid * 2);
@@ -320,8 +518,9 @@ dsp_status dsp_mlp_create(int32_t max_batch, uint64_t seed, dsp_mlp** out) {
 
 void dsp_mlp_destroy(dsp_mlp* q) {
   if (!q) return;
-  void* ptrs[] = {q->master, q->adam_m, q->adam_v, q->grad, q->wb, q->xb, q->h1, q->h2, q->dh1, q->dh2, q->dl,
-                  q->logits, q->loss};
+  void* ptrs[] = {q->master, q->adam_m, q->adam_v, q->grad, q->wb,  q->wt,  q->xb,   q->h1,   q->h2,     q->dh1,
+                  q->dh2,    q->dl,     q->xt,     q->h1t, q->h2t, q->dh1t, q->dh2t, q->dlt, q->logits, q->loss,
+                  q->ws,     q->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete q;
@@ -331,7 +530,7 @@ dsp_status dsp_mlp_set_weights(dsp_mlp* q, const float* host) {
   if (!q || !host) return fail(DSP_E_INVALID, "dsp_mlp_set_weights: NULL argument");
   cudaError_t e = cudaMemcpy(q->master, host, kMlpParams * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    pack_weights_bf16<<<128, 256>>>(q->master, q->wb);
+    pack_weights_bf16<<<128, 256>>>(q->master, q->wb, q->wt);
     e = cudaDeviceSynchronize();
   }
   return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_mlp_set_weights");
@@ -348,7 +547,10 @@ dsp_status dsp_mlp_forward(dsp_mlp* q, const float* X, int32_t B, float* logits,
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = forward(q, X, B, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(logits, q->logits, (size_t)B * kMlpOut * 4, cudaMemcpyDeviceToDevice, st);
-  return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_mlp_forward");
+  bool timed_out = false;
+  if (e == cudaSuccess) e = check_status(q, st, &timed_out);
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_mlp_forward");
+  return timed_out ? fail(DSP_E_TIMEOUT, "dsp_mlp_forward: a tensor-core wait ran out") : DSP_OK;
 }
 
 dsp_status dsp_mlp_grad(dsp_mlp* q, const float* X, const int32_t* y, int32_t B, int32_t n_actions, float* loss,
@@ -362,9 +564,11 @@ dsp_status dsp_mlp_grad(dsp_mlp* q, const float* X, const int32_t* y, int32_t B,
   if (e == cudaSuccess) e = cudaMemcpyAsync(&l, q->loss, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && grad_host)
     e = cudaMemcpyAsync(grad_host, q->grad, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  bool timed_out = false;
+  if (e == cudaSuccess) e = check_status(q, st, &timed_out);
   *loss = l / (float)B;
-  return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_mlp_grad");
+  if (e != cudaSuccess) return cuda_fail(e, "dsp_mlp_grad");
+  return timed_out ? fail(DSP_E_TIMEOUT, "dsp_mlp_grad: a tensor-core wait ran out") : DSP_OK;
 }
 
 dsp_status dsp_mlp_train_step(dsp_mlp* q, const float* X, const int32_t* y, int32_t B, int32_t n_actions, float lr,
@@ -379,14 +583,16 @@ dsp_status dsp_mlp_train_step(dsp_mlp* q, const float* X, const int32_t* y, int3
   const float c1 = 1.0f - (float)std::pow(b1, (double)q->step), c2 = 1.0f - (float)std::pow(b2, (double)q->step);
   if (e == cudaSuccess) {
     adam<<<256, 256, 0, st>>>(q->master, q->adam_m, q->adam_v, q->grad, kMlpParams, lr, b1, b2, 1e-8f, c1, c2);
-    pack_weights_bf16<<<128, 256, 0, st>>>(q->master, q->wb);
+    pack_weights_bf16<<<128, 256, 0, st>>>(q->master, q->wb, q->wt);
     e = cudaGetLastError();
   }
   if (loss) {
     float l = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, q->loss, 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    bool timed_out = false;
+    if (e == cudaSuccess) e = check_status(q, st, &timed_out);
     *loss = l / (float)B;
+    if (e == cudaSuccess && timed_out) return fail(DSP_E_TIMEOUT, "dsp_mlp_train_step: a tensor-core wait ran out");
   }
   return e == cudaSuccess ? DSP_OK : cuda_fail(e, "dsp_mlp_train_step");
 }

@@ -60,34 +60,40 @@ def test_forward_matches_oracle(env):
 
 
 def test_gradient_matches_oracle(env):
+    """Batches of 1000, 300 and 1 rows on one network, in that order: ragged
+    last tiles, and smaller batches after larger ones (the weight gradients
+    reduce over the batch padded to the tile, so the padding must read as
+    0)."""
     torch, _dsp = env
     w = make_weights(3)
     h = _dsp.dsp_mlp_create(1024, 0)
     _dsp.dsp_mlp_set_weights(h, _dsp.pack_params(w))
     rng = np.random.default_rng(4)
-    # Labels: the network's second-best action for half the rows, random for
-    # the rest. Per-example gradients then add up instead of cancelling (with
-    # purely random labels the batch gradient is a small difference of large
-    # terms and BF16 rounding of each term dominates it).
-    B, na = 128, 20
-    X = bf16_exact(rng.normal(0, 1, (B, 64)))
-    lg = oracle.mlp_forward(w, X)[:, :na]
-    y = np.argsort(lg, axis=1)[:, -2].astype(np.int32)
-    y[::2] = rng.integers(0, na, B // 2)
-    Xd = torch.tensor(X, device="cuda")
-    yd = torch.tensor(y, device="cuda")
-    loss, flat = _dsp.dsp_mlp_grad(h, Xd.data_ptr(), yd.data_ptr(), B, na)
-    g = _dsp.unpack_params(flat)
-    # BF16-aware: the oracle's FP64 backward at the BF16 forward's activations
-    oloss, og = oracle.mlp_loss_grad(w, X, y, na, bf16_forward=True)
-    assert abs(loss - oloss) <= 1e-2 * abs(oloss)
-    rels = {k: float(np.linalg.norm(g[k] - og[k]) / np.linalg.norm(og[k])) for k in og}
-    assert all(r <= 1e-2 for r in rels.values()), rels
-    # and the exact FP64 gradient within what the BF16 forward moves the
-    # logits by (a few per cent, see test_forward_matches_oracle)
-    _, ge = oracle.mlp_loss_grad(w, X, y, na)
-    rele = {k: float(np.linalg.norm(g[k] - ge[k]) / np.linalg.norm(ge[k])) for k in ge}
-    assert all(r <= 8e-2 for r in rele.values()), rele
+    na = 20
+    for B in (1000, 300, 1):
+        # Labels: the network's second-best action for half the rows, random
+        # for the rest. Per-example gradients then add up instead of
+        # cancelling (with purely random labels the batch gradient is a
+        # small difference of large terms and BF16 rounding of each term
+        # dominates it).
+        X = bf16_exact(rng.normal(0, 1, (B, 64)))
+        lg = oracle.mlp_forward(w, X)[:, :na]
+        y = np.argsort(lg, axis=1)[:, -2].astype(np.int32)
+        y[::2] = rng.integers(0, na, (B + 1) // 2)
+        Xd = torch.tensor(X, device="cuda")
+        yd = torch.tensor(y, device="cuda")
+        loss, flat = _dsp.dsp_mlp_grad(h, Xd.data_ptr(), yd.data_ptr(), B, na)
+        g = _dsp.unpack_params(flat)
+        # BF16-aware: the oracle's FP64 backward at the BF16 forward's activations
+        oloss, og = oracle.mlp_loss_grad(w, X, y, na, bf16_forward=True)
+        assert abs(loss - oloss) <= 1e-2 * abs(oloss), B
+        rels = {k: float(np.linalg.norm(g[k] - og[k]) / np.linalg.norm(og[k])) for k in og}
+        assert all(r <= 1e-2 for r in rels.values()), (B, rels)
+        # and the exact FP64 gradient within what the BF16 forward moves the
+        # logits by (a few per cent, see test_forward_matches_oracle)
+        _, ge = oracle.mlp_loss_grad(w, X, y, na)
+        rele = {k: float(np.linalg.norm(g[k] - ge[k]) / np.linalg.norm(ge[k])) for k in ge}
+        assert all(r <= 8e-2 for r in rele.values()), (B, rele)
     _dsp.dsp_mlp_destroy(h)
 
 
