@@ -167,23 +167,49 @@ def features(model, states, hist):
     return f.cpu().numpy()
 
 
-def harvest(cfg, world_seeds, steps, seconds, policy=None, threads=4, min_scen=16, log=print):
-    """(features, labels) from planner episodes on the given world seeds; with
-    `policy` (a dsp_mlp handle) the planner's rollouts use it."""
+def imitation_labels(model, cfg, states, hist, actions):
+    """The planner's chosen actions at tree nodes as training labels: |A|
+    (defer to the heuristic) where the planner chose the heuristic's action,
+    else the action. Returns (keep, labels): keep marks the pairs whose action
+    the learned policy may take (the library's allowed-action rule)."""
+    pos, sampled = states[0], states[3]
+    keep = allowed_mask(model, cfg, pos, sampled, hist)[np.arange(len(actions)), actions]
+    heur = heuristic_action(model, pos, sampled, hist)
+    return keep, np.where(actions == heur, model.num_actions, actions).astype(np.int32)
+
+
+def harvest(cfg, world_seeds, steps, seconds, policy=None, threads=4, min_scen=16, defer=True, log=print):
+    """(features, labels) from planner episodes on the given world seeds: at
+    every exported tree node (a belief with at least `min_scen` scenarios),
+    the action the planner's search chose there. With `defer` the label is
+    |A| ("defer to the heuristic") where the planner chose the heuristic's
+    action, and pairs whose action the learned policy may not take (the
+    library's allowed-action rule, which the learned rollout applies) are
+    dropped. With `policy` (a dsp_mlp handle) the planner's rollouts use it."""
     model = batch.Model(cfg)
     if policy is not None:
         _dsp.dsp_set_policy(model.h, policy)
     X, Y, rets = [], [], []
+    kept = seen = 0
     t0 = time.time()
     for s in world_seeds:
         ep = episode(model, cfg, s, steps, seconds, threads, min_scen)
         rets.append(ep["return"])
         if "states" in ep:
-            X.append(features(model, ep["states"], ep["hist"]))
-            Y.append(ep["labels"])
+            y = ep["labels"].astype(np.int32)
+            x = features(model, ep["states"], ep["hist"])
+            if defer:
+                ok, y = imitation_labels(model, cfg, ep["states"], ep["hist"], y)
+                seen += len(y)
+                kept += int(ok.sum())
+                x, y = x[ok], y[ok]
+            X.append(x)
+            Y.append(y)
         log(f"world {s}: return {ep['return']:.2f}, {ep['decisions']} decisions, "
             f"{sum(len(y) for y in Y)} pairs, {time.time() - t0:.0f} s")
     model.close()
+    if defer and seen:
+        log(f"allowed pairs kept: {kept} of {seen}")
     return np.concatenate(X), np.concatenate(Y), rets
 
 
@@ -718,6 +744,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--weights", default=None, help="weights file (default: the shipped one of the task)")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--init", default=None, help="api: start from these weights (e.g. the imitation network)")
     ap.add_argument("--eval-worlds", type=int, default=8)
     ap.add_argument("--eval-steps", type=int, default=8)
     ap.add_argument("--eval-seconds", type=float, default=1.0)
@@ -737,13 +764,18 @@ def main(argv=None):
         print(json.dumps(compare(ccfg, policy, car_roots(ccfg, a.eval_worlds, 9000), a.eval_seconds)))
         return
     if a.cmd == "api":
-        policy, hl = policy_iteration(cfg, iterations=a.iterations, epochs=a.epochs)
-        save_weights(a.out or a.weights or "paper_1802_06215_b300/weights/rs15_15_pi0.npz", policy,
-                     {"config": "rs15_15", "method": "approximate policy iteration",
-                                                  "iterations": hl})
+        init, init_meta = None, None
+        if a.init:
+            z = np.load(a.init)
+            init, init_meta = z["params"], json.loads(str(z["meta"]))
+        policy, hl = policy_iteration(cfg, iterations=a.iterations, epochs=a.epochs, init=init)
+        meta = {"config": "rs15_15", "method": "approximate policy iteration", "iterations": hl}
+        if init_meta is not None:
+            meta.update({"method": "planner imitation, then approximate policy iteration", "init": init_meta})
+        save_weights(a.out or a.weights or "paper_1802_06215_b300/weights/rs15_15_pi0.npz", policy, meta)
     elif a.cmd == "train":
         if not a.out:
-            ap.error("train (planner imitation, not used for the shipped weights) needs --out")
+            ap.error("train (planner imitation) needs --out")
         policy, init, meta = None, None, {"iterations": []}
         X_all, Y_all = [], []
         for it in range(a.iterations):
@@ -751,14 +783,16 @@ def main(argv=None):
             X, Y, rets = harvest(cfg, seeds, a.steps, a.plan_seconds, policy=policy)
             X_all.append(X)
             Y_all.append(Y)
-            h, acc = train(np.concatenate(X_all), np.concatenate(Y_all), 20, epochs=a.epochs, seed=it)
+            # 20 actions and the defer label
+            h, acc = train(np.concatenate(X_all), np.concatenate(Y_all), 21, epochs=a.epochs, seed=it)
             meta["iterations"].append({"worlds": seeds, "pairs": int(sum(len(y) for y in Y_all)),
                                        "mean_return": float(np.mean(rets)), "val_accuracy": acc})
             print(json.dumps(meta["iterations"][-1]))
             if policy is not None:
                 _dsp.dsp_mlp_destroy(policy)
             policy = h
-        meta.update({"config": "rs15_15", "method": "planner imitation", "steps": a.steps,
+        meta.update({"config": "rs15_15", "method": "planner imitation (defer labels, allowed actions)",
+                     "steps": a.steps,
                      "plan_seconds": a.plan_seconds, "epochs": a.epochs})
         save_weights(a.out, policy, meta)
     else:

@@ -1,9 +1,11 @@
 """What the trained network gains over the method without it: the shipped
-weights (approximate policy iteration, `learn api --iterations 4 --epochs 30`)
-against the heuristic default policy, in rollout value (the l0 it gives) and
-in the root gap u - l after planning steps of equal time; and two iterations
-of policy iteration from scratch already beating the heuristic from the start
-belief."""
+weights (imitation of the plain planner's chosen actions, `learn train`, then
+approximate policy iteration from that network, `learn api --init`) against
+the heuristic default policy, in rollout value (the l0 it gives) and in the
+root gap u - l after planning steps of equal time; two iterations of policy
+iteration from scratch already beating the heuristic from the start belief;
+and the imitation labels' rules (defer where the planner chose the
+heuristic's action, only actions the learned policy may take)."""
 import os
 
 import numpy as np
@@ -98,3 +100,24 @@ def test_trained_car_policy_tightens_root_gap(env):
     assert out["learned"]["mean_root_gap"] < out["heuristic"]["mean_root_gap"], out
     assert out["learned"]["mean_root_l"] > out["heuristic"]["mean_root_l"], out
     _dsp.dsp_mlp_destroy(h)
+
+
+def test_imitation_labels_follow_the_planner(env):
+    """Tree nodes of one planner episode: each kept label is the planner's
+    action, or |A| exactly where that action is the heuristic's; a pair is
+    dropped exactly when the learned policy may not take the action."""
+    _dsp, batch, learn = env
+    cfg = I.rs15_15()
+    m = batch.Model(cfg)
+    ep = learn.episode(m, cfg, 1234, 6, 0.05, min_scen=16)
+    assert "states" in ep and len(ep["labels"]) > 50
+    st, hist, act = ep["states"], ep["hist"], ep["labels"].astype(np.int32)
+    keep, y = learn.imitation_labels(m, cfg, st, hist, act)
+    heur = learn.heuristic_action(m, st[0], st[3], hist)
+    allowed = learn.allowed_mask(m, cfg, st[0], st[3], hist)
+    na = m.num_actions
+    assert np.array_equal(keep, allowed[np.arange(len(act)), act])
+    assert np.array_equal(y == na, act == heur)
+    assert np.all(y[act != heur] == act[act != heur])
+    assert 0 < keep.sum() and np.all((y >= 0) & (y <= na))
+    m.close()
