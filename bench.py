@@ -646,7 +646,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
         "vs_baseline": None, "dtype": _dtype(cfg), "data": "synthetic",
         "config": {"workload": f"{name}: {desc}", "jobs_per_step": njobs,
                    "l2": "256 MiB buffer written before every timed step (outside the events)"},
-        "leaf_expansions_per_s": njobs * world / (t_ms / 1000.0),
+        "leaf_expansions_per_s": njobs * world * args.steps / (t_ms / 1000.0),
         "scenario_steps_per_step": steps_per_launch,
         "e2e": {"value": e2_value, "unit": "scenario-steps/s", "h2d_bytes_per_step": jb.input_bytes,
                 "d2h_bytes_per_step": jb.output_bytes,
