@@ -328,10 +328,11 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
     }
     uint32_t h2a[64];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float acc[32];
-      tmem_ld32(trow + 128 + 32 * c, acc);
-      relu_pack32(acc, S.W.b2 + 32 * c, h2a + 16 * c);
+    for (int c = 0; c < 2; ++c) {
+      float acc[64];
+      tmem_ld64(trow + 128 + 64 * c, acc);
+      relu_pack32(*reinterpret_cast<const float(*)[32]>(acc), S.W.b2 + 64 * c, h2a + 32 * c);
+      relu_pack32(*reinterpret_cast<const float(*)[32]>(acc + 32), S.W.b2 + 64 * c + 32, h2a + 32 * c + 16);
     }
     fence_before_sync();
     tile_sync(bar);
@@ -344,12 +345,14 @@ __global__ void __launch_bounds__(kThreads, 1) rs_rollout_tc_kernel(const DevMod
 #pragma unroll
     for (int c = 0; c < 4; ++c) tmem_st16p(trow + 16 * c, h2a + 16 * c);
 #pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-      float acc[32];
-      uint32_t packed[16];
-      tmem_ld32(trow + 128 + 32 * c, acc);
-      relu_pack32(acc, S.W.b2 + 128 + 32 * c, packed);
-      tmem_st16p(trow + 64 + 16 * c, packed);
+    for (int c = 0; c < 2; ++c) {
+      float acc[64];
+      uint32_t packed[32];
+      tmem_ld64(trow + 128 + 64 * c, acc);
+      relu_pack32(*reinterpret_cast<const float(*)[32]>(acc), S.W.b2 + 128 + 64 * c, packed);
+      relu_pack32(*reinterpret_cast<const float(*)[32]>(acc + 32), S.W.b2 + 128 + 64 * c + 32, packed + 16);
+      tmem_st16p(trow + 64 + 32 * c, packed);
+      tmem_st16p(trow + 64 + 32 * c + 16, packed + 16);
     }
     tmem_wait_st();
     fence_before_sync();

@@ -395,6 +395,8 @@ __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
 }
 
 // ReLU(accumulator + bias) of 32 FP32 columns, rounded to 16 BF16 pairs.
+// (Reading the bias four floats at a time was 4 % slower in the learned
+// rollout on B300.)
 __device__ __forceinline__ void relu_pack32(const float (&acc)[32], const float* bias, uint32_t* out) {
 #pragma unroll
   for (int j = 0; j < 16; ++j)
@@ -439,16 +441,18 @@ __device__ __forceinline__ void issue_layer3(const Weights& W, uint32_t a, uint3
 
 // Layer 1's epilogue for the thread's row (trow = the tile's base column on
 // the row's lane): H1 = BF16(ReLU(D + b1)) packed in place into columns
-// 0..127 (chunk c of 32 accumulator columns to 16c..16c+15, columns the
-// thread has already read).
+// 0..127 (chunk c of 64 accumulator columns to 32c..32c+31, columns the
+// thread has already read). 64 columns per load: one wait per 64.
 __device__ __forceinline__ void epilogue1_inplace(uint32_t trow, const float* b1) {
 #pragma unroll 1
-  for (int c = 0; c < kMlpHid / 32; ++c) {
-    float acc[32];
-    uint32_t packed[16];
-    tmem_ld32(trow + 32 * c, acc);
-    relu_pack32(acc, b1 + 32 * c, packed);
-    tmem_st16p(trow + 16 * c, packed);
+  for (int c = 0; c < kMlpHid / 64; ++c) {
+    float acc[64];
+    uint32_t packed[32];
+    tmem_ld64(trow + 64 * c, acc);
+    relu_pack32(*reinterpret_cast<const float(*)[32]>(acc), b1 + 64 * c, packed);
+    relu_pack32(*reinterpret_cast<const float(*)[32]>(acc + 32), b1 + 64 * c + 32, packed + 16);
+    tmem_st16p(trow + 32 * c, packed);
+    tmem_st16p(trow + 32 * c + 16, packed + 16);
   }
   tmem_wait_st();
 }
