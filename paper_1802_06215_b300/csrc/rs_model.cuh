@@ -287,6 +287,30 @@ struct RSModel {
     return 0;
   }
 
+  // Steps before a robot's next event under the carried target: the moves to
+  // the target cell (Manhattan distance; its Sample follows), or with no
+  // target the E moves to the last column (its exit follows); never for an
+  // exited robot.
+  __device__ __forceinline__ int event_steps(int x, int y, bool ex, int tx, int ty, uint32_t tbit) const {
+    if (ex) return 1 << 30;
+    if (tbit == 0) return n - 1 - x;
+    return abs(tx - x) + abs(ty - y);
+  }
+
+  // k of those moves at once (k <= event_steps): toward the target, x before
+  // y, or east.
+  __device__ __forceinline__ void move_steps(int& x, int& y, bool ex, int tx, int ty, uint32_t tbit, int k) const {
+    if (ex || k == 0) return;
+    if (tbit == 0) {
+      x += k;
+      return;
+    }
+    const int mx = min(k, abs(tx - x));
+    x += tx > x ? mx : -mx;
+    const int my = k - mx;
+    y += ty > y ? my : -my;
+  }
+
   // The same rollout for two robots with the state unpacked into registers:
   // both robots decide on the state before the step (the joint heuristic
   // policy), robot 0 acts first (a rock both stand on is sampled by robot 0,
@@ -295,7 +319,8 @@ struct RSModel {
   // are carried between steps (heuristic_step). A sample removes one rock
   // from the shared set; the argmin over the rest is unchanged unless it was
   // that rock, so a robot retakes its target, before the next step, exactly
-  // when its target has left the set.
+  // when its target has left the set. Between events (a Sample, an exit)
+  // the steps are moves only and are taken together.
   __device__ __forceinline__ float rollout_two(RSS s, uint32_t pmask, int t0, unsigned long long& steps) const {
     int x0 = (int)(s.pos[0] & 0xFFu), y0 = (int)((s.pos[0] >> 8) & 0xFFu);
     int x1 = (int)(s.pos[1] & 0xFFu), y1 = (int)((s.pos[1] >> 8) & 0xFFu);
@@ -314,9 +339,18 @@ struct RSModel {
         tb1 = 0;
         if (cand != 0) target(x1, y1, cand, tx1, ty1, tb1);
       }
-      // robot 1's target was taken on the state before robot 0 acts: its
-      // Sample of a rock robot 0 just took finds it bad, as the joint step's
-      // order has it
+      // Until the first robot's next event (its Sample on the target cell,
+      // or its exit from the last column) both robots only move, one cell
+      // per step, and no target changes: jump those steps (their rewards
+      // are 0, which leaves v as it is) and move both robots there at once.
+      const int k = min(min(event_steps(x0, y0, ex0, tx0, ty0, tb0), event_steps(x1, y1, ex1, tx1, ty1, tb1)), D - t);
+      move_steps(x0, y0, ex0, tx0, ty0, tb0, k);
+      move_steps(x1, y1, ex1, tx1, ty1, tb1, k);
+      t += k;
+      if (t >= D) break;
+      // the event step: robot 1's target was taken on the state before
+      // robot 0 acts, so its Sample of a rock robot 0 just took finds it
+      // bad, as the joint step's order has it
       int reward = heuristic_step(x0, y0, ex0, tx0, ty0, tb0, good, cand);
       reward += heuristic_step(x1, y1, ex1, tx1, ty1, tb1, good, cand);
       if (reward != 0) v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], (float)reward));
