@@ -386,10 +386,9 @@ struct RSModel {
       while (t < D) {
         if (cand == 0) {
           // E each step; from the last column E exits (+10)
-          while (t < D && x < n - 1) {
-            x += 1;
-            ++t;
-          }
+          const int ke = min(n - 1 - x, D - t);
+          x += ke;
+          t += ke;
           if (t < D) {
             v = __fadd_rn(v, __fmul_rn(sh->G[t - t0], 10.0f));
             ex = true;
@@ -401,15 +400,14 @@ struct RSModel {
         uint32_t tbit;
         target(x, y, cand, tx, ty, tbit);
         const int sx = tx > x ? 1 : -1, sy = ty > y ? 1 : -1;
-        // one move per step toward the target: x first, then y
-        while (t < D && x != tx) {
-          x += sx;
-          ++t;
-        }
-        while (t < D && y != ty) {
-          y += sy;
-          ++t;
-        }
+        // one move per step toward the target: x first, then y (taken
+        // together, up to the horizon)
+        const int kx = min(abs(tx - x), D - t);
+        x += sx * kx;
+        t += kx;
+        const int ky = min(abs(ty - y), D - t);
+        y += sy * ky;
+        t += ky;
         if (t >= D) break;
         // on the target's cell: Sample
         const float r = (good & tbit) ? 10.0f : -10.0f;
