@@ -136,6 +136,24 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
     for (int p = tid; p < n; p += (int)blockDim.x) put_leaf(lb, j, n, p, S.leaf[0][p], S.leaf[2][p], S.leaf[3][p]);
     put_blocks(lb, j, n, A);
   }
+  // A tree node's scenarios share the robot's position and sampled mask (both
+  // observed); they differ in the rocks' states and random streams. When the
+  // job's leaves do (checked here), a move or a terminal leaf gives every
+  // scenario the same step (one child, the grouped positions in their
+  // original order) and a Sense compares each scenario's sensor word with
+  // one threshold. The results are those of the general path below.
+  bool same = true;
+  for (int p = tid; p < n; p += (int)blockDim.x)
+    same = same && S.leaf[0][p] == S.leaf[0][0] && S.leaf[3][p] == S.leaf[3][0];
+  const bool uniform = __syncthreads_and(same ? 1 : 0) != 0;
+  // the shared position and sampled mask (a move's or a terminal leaf's step
+  // reads neither the rocks' states nor the random streams)
+  RSS rep;
+  rep.pos[0] = S.leaf[0][0];
+  rep.pos[1] = 0u;
+  rep.good = 0u;
+  rep.sampled = S.leaf[3][0];
+  rep.scen = 0u;
   const uint32_t lt = lanemask_lt();
   uint8_t* codes = S.code1[warp];
   const uint32_t pm_job = S.pm_job;
@@ -149,10 +167,47 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
       first[c] = 0x7FFFFFFF;
       rsum[c] = 0;
     }
-    for (int w = 0; w * 32 < n; ++w) {
+    const bool rep_term = M.terminal(rep);
+    const bool same_step = uniform && (aa < 4 || rep_term);  // one code and reward for all
+    const bool same_sense = uniform && aa >= 5 && !rep_term;
+    RSS rep_next = rep;
+    int rep_code = 0, rep_r = 0;
+    uint64_t sense_thr = 0;
+    uint32_t sense_bit = 0;
+    if (same_step) {
+      uint64_t key;
+      rep_r = (int)M.step(rep_next, aa, depth, key);
+      rep_code = (int)(key & 3u) + 3 * (int)(key >> 62);
+    } else if (same_sense) {
+      const int i = aa - 5;
+      const int x = (int)(rep.pos[0] & 0xFFu), y = (int)((rep.pos[0] >> 8) & 0xFFu);
+      const int dx = x - (S.c.rock_xy[i] & 0xFF), dy = y - (S.c.rock_xy[i] >> 8);
+      sense_thr = __ldg(M.thresh + dx * dx + dy * dy);
+      sense_bit = 1u << i;
+    }
+    if (same_step) {
+      // (an unrolled loop over the codes keeps the arrays in registers)
+#pragma unroll
+      for (int c = 0; c < kC; ++c)
+        if (c == rep_code) {
+          cnt[c] = n;
+          first[c] = 0;
+          rsum[c] = n * rep_r;
+        }
+      if (!rep_term && lane == 0) steps += (unsigned long long)n;
+    }
+    for (int w = 0; !same_step && w * 32 < n; ++w) {
       const int p = w * 32 + lane;
       int code = kC, rint = 0;
-      if (p < n) {
+      if (p < n && same_sense) {
+        // Sense of rock i: the reading is correct iff the sensor word is
+        // below the threshold of the (shared) distance; z = 1 reads good
+        steps += 1;
+        const bool correct = (uint64_t)S.sense[0][p] < sense_thr;
+        const bool is_good = (S.leaf[2][p] & sense_bit) != 0u;
+        code = correct == is_good ? 1 : 2;
+        codes[p] = (uint8_t)code;
+      } else if (p < n) {
         RSS s;
         s.pos[0] = S.leaf[0][p];
         s.pos[1] = 0u;
@@ -230,17 +285,20 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
     for (int c = 0; c < kC; ++c) run[c] = 0;
     for (int w = 0; w * 32 < n; ++w) {
       const int p = w * 32 + lane;
-      const int code = p < n ? (int)codes[p] : kC;
-      int q = 0, mycid = 0;
+      const int code = p < n ? (same_step ? rep_code : (int)codes[p]) : kC;
+      int q = p, mycid = 0;  // one child: the original order
+      if (!same_step) {
+        q = 0;
 #pragma unroll
-      for (int c = 0; c < kC; ++c) {
-        if (cnt[c] > 0) {  // the action's codes (warp-uniform)
-          const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
-          if (code == c) {
-            q = off[c] + run[c] + __popc(b & lt);
-            mycid = cid[c];
+        for (int c = 0; c < kC; ++c) {
+          if (cnt[c] > 0) {  // the action's codes (warp-uniform)
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, code == c);
+            if (code == c) {
+              q = off[c] + run[c] + __popc(b & lt);
+              mycid = cid[c];
+            }
+            run[c] += __popc(b);
           }
-          run[c] += __popc(b);
         }
       }
       if (p < n) J.perm[(size_t)a * n + q] = (uint16_t)p;
@@ -251,7 +309,11 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
         s.good = S.leaf[2][p];
         s.sampled = S.leaf[3][p];
         s.scen = S.leaf[4][p];
-        if (aa < 5) {
+        if (same_step) {
+          // a move (or a terminal leaf) leaves the rocks as they were
+          s.pos[0] = rep_next.pos[0];
+          s.sampled = rep_next.sampled;
+        } else if (aa < 5) {
           uint64_t k;
           M.step(s, aa, depth, k);
         }

@@ -285,3 +285,40 @@ def test_expand_parity_rollout_forms(dsp, name, form):
         total += o["steps"]
     assert steps == total
     m.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_expand_parity_mixed_leaves(dsp, form):
+    """Leaves whose scenarios differ in the robot's position and sampled mask
+    (not a tree node's, but a valid input) take the grouping phase's general
+    path, next to jobs whose scenarios share them (the fast path): all match
+    the oracle, with roots and updated leaves, in both rollout forms."""
+    from paper_1802_06215_b300 import _dsp
+    cfg = I.rs15_15()
+    m = dsp.Model(cfg)
+    _dsp.dsp_set_launch_shape(m.h, rs_form=form)
+    om = oracle.Model(cfg)
+    rng = np.random.default_rng(17)
+    jobs = []
+    for n, depth, last in [(200, 0, -1), (77, 4, 0), (300, 6, 4), (33, 2, 7)]:
+        pb = I.rs_block(cfg, n, rng)  # per-scenario positions
+        samp = rng.integers(0, 1 << cfg.m, n).astype(np.uint32) & rng.integers(0, 1 << cfg.m, n).astype(np.uint32)
+        pb[3] = samp
+        pb[2] &= ~samp
+        idx = np.arange(n, dtype=np.uint16) if depth == 0 else np.sort(rng.permutation(n)[: n - n // 3]).astype(np.uint16)
+        jobs.append(I.Job(parent=pb, idx=idx, last_action=last, depth=depth, hist=I.random_hist(cfg, rng, depth),
+                          first_action=0, n_actions=m.num_actions))
+    jobs += I.job_stream(cfg, 4, 23)
+    jb = dsp.JobBatch(m, jobs)
+    m.reset_counters()
+    jb.run()
+    steps, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    total = 0
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"mixed job {k} form {form}")
+        total += o["steps"]
+    assert steps == total
+    m.close()
