@@ -564,6 +564,16 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
       J.u_sum[o] = 0;
       J.l_sum[o] = 0;
     }
+    // the child's positive-counter mask depends only on the observation
+    // (z0 * 3 + z1 < 9): lane c holds the one of observation c
+    uint32_t pm_obs = S.pm_job;
+    if (lane < 9) {
+      uint32_t h[8];
+      const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) h[k] = hw[k];
+      M.observe(h, pm_obs, aa, (uint64_t)lane);
+    }
     // pass 2: grouped positions and rollout items; only Sense draws random
     // numbers and it leaves the state as it was, so each robot's other
     // actions are simply applied again
@@ -578,8 +588,8 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
       }
       __syncwarp();
       if (p < n && lane == __ffs(peers) - 1) run[code] += __popc(peers);
+      RSS s;
       if (p < n) {
-        RSS s;
         s.pos[0] = S.leaf[0][p];
         s.pos[1] = S.leaf[1][p];
         s.good = S.leaf[2][p];
@@ -589,12 +599,9 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
         if (a0 < 5) M.robot_step(s, 0, a0, depth, z);
         if (a1 < 5) M.robot_step(s, 1, a1, depth, z);
         J.perm[(size_t)a * n + q] = (uint16_t)p;
-        uint32_t h[8];
-        const uint32_t* hw = reinterpret_cast<const uint32_t*>(J.hist);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) h[k] = hw[k];
-        uint32_t pm = S.pm_job;
-        M.observe(h, pm, aa, (uint64_t)(code % 9));
+      }
+      const uint32_t pm = __shfl_sync(0xFFFFFFFFu, pm_obs, p < n ? code % 9 : 0);
+      if (p < n) {
         const size_t it = (size_t)(ibase + (long long)a * n + q);
         items.put(it, s, pm, ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(mycid, cap - 1)), (uint32_t)j);
       }
