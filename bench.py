@@ -75,6 +75,8 @@ try:
 except (OSError, ValueError):
     MEASURED = {}
 METRIC = "scenario-steps/sec and leaf expansions/sec at K=500, D=90 (fraction of roofline); root gap"
+E2E_LANES = 3  # job arenas (and streams) of the end-to-end measurement
+
 KERNEL_SOURCES = {
     "rs": ["expand_rs.cu", "rs_model.cuh", "rs_common.cuh", "common.cuh"],
     "car": ["expand_car.cu", "car_model.cuh", "group.cuh", "common.cuh"],
@@ -538,13 +540,12 @@ def measure(args, name, rank, world, dist, local, headline=True):
     # pinned host memory and the results a host search reads out (each
     # child's count, offsets, key and sums; the leaf states and grouped
     # positions stay on the device for the children's expansions, as in
-    # dsp_plan), inside the timed region. Two
-    # job arenas on two streams take alternate steps (double buffering), so
-    # one step's transfers overlap the other's kernels; the time is the wall
-    # time of all steps, first copy to last result.
-    jb2 = batch.JobBatch(m, jobs)
-    lanes = [(stream, jb), (torch.cuda.Stream(), jb2)]
-    for s_, b_ in lanes:  # warm both arenas and streams
+    # dsp_plan), inside the timed region. Three
+    # job arenas on three streams take the steps in turn, so that one step's
+    # transfers overlap the others' kernels; the time is the wall time of all
+    # steps, first copy to last result.
+    lanes = [(stream, jb)] + [(torch.cuda.Stream(), batch.JobBatch(m, jobs)) for _ in range(E2E_LANES - 1)]
+    for s_, b_ in lanes:  # warm every arena and stream
         with torch.cuda.stream(s_):
             b_.upload_inputs()
             b_.run(s_)
@@ -552,17 +553,19 @@ def measure(args, name, rank, world, dist, local, headline=True):
     torch.cuda.synchronize()
     e2s, e2e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2s.record(stream)
-    lanes[1][0].wait_event(e2s)
+    for s_, _ in lanes[1:]:
+        s_.wait_event(e2s)
     for k in range(args.steps):
-        s_, b_ = lanes[k % 2]
+        s_, b_ = lanes[k % len(lanes)]
         with torch.cuda.stream(s_):
             flush.zero_()
             b_.upload_inputs()
             b_.run(s_)
             b_.download_outputs()
-    tail = torch.cuda.Event()
-    tail.record(lanes[1][0])
-    stream.wait_event(tail)
+    for s_, _ in lanes[1:]:
+        tail = torch.cuda.Event()
+        tail.record(s_)
+        stream.wait_event(tail)
     e2e_.record(stream)
     torch.cuda.synchronize()
     e2_ms, _ = combine_ranks(e2s.elapsed_time(e2e_), 0, dist, "cuda")
@@ -650,7 +653,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
         "scenario_steps_per_step": steps_per_launch,
         "e2e": {"value": e2_value, "unit": "scenario-steps/s", "h2d_bytes_per_step": jb.input_bytes,
                 "d2h_bytes_per_step": jb.output_bytes,
-                "method": "dsp_expand_leaves on two job arenas and two streams taking alternate steps; "
+                "method": f"dsp_expand_leaves on {E2E_LANES} job arenas and {E2E_LANES} streams taking the steps in turn; "
                           "wall time from the first upload to the last result, L2 flush in each step; "
                           "read back: each child's count, offsets, key and reward/u/l sums (what dsp_plan's "
                           "search reads); the leaf states and grouped positions stay on the device",
