@@ -714,6 +714,28 @@ __device__ __forceinline__ void rs_rollout_values(const RSModel<R>& M, const dsp
     long long fu = 0, fl = 0;
     int64_t* usum = nullptr;
     int64_t* lsum = nullptr;
+    // u0 of a chunk whose items share the robot's cell and the depth (a
+    // child's items do, and so do an action's): rock i's term 10 G[d_i] from
+    // lane i, each lane adding its good rocks' terms in index order, as
+    // upper() does (lane 0 always holds an item)
+    float u_shared = 0.0f;
+    bool shared = false;
+    if constexpr (R == 1) {
+      const uint32_t p0 = __shfl_sync(0xFFFFFFFFu, s.pos[0], 0);
+      const uint32_t d0 = __shfl_sync(0xFFFFFFFFu, meta >> 24, 0);
+      shared = __all_sync(0xFFFFFFFFu, !ok || (s.pos[0] == p0 && (meta >> 24) == d0)) &&
+               !((p0 >> 16) & 1u) && (int)d0 + 1 < M.D;
+      if (shared) {
+        const int x = (int)(p0 & 0xFFu), cell = x + (int)((p0 >> 8) & 0xFFu) * M.n;
+        const float w = lane < M.m ? __fmul_rn(10.0f, M.sh->G[(int)M.nkey[lane * M.nn + cell] >> 7]) : 0.0f;
+        const uint32_t g = s.good;
+        for (int i = 0; i < M.m; ++i) {
+          const float wi = __shfl_sync(0xFFFFFFFFu, w, i);
+          if ((g >> i) & 1u) u_shared = __fadd_rn(u_shared, wi);
+        }
+        u_shared = __fadd_rn(u_shared, __fmul_rn(10.0f, M.sh->G[M.n - 1 - x]));
+      }
+    }
     if (!ok) job = 0xFFFFFFFFu;
     if (ok) {
       if (R == 1) {  // one robot: loaded before its short rollout (two robots: after, fewer registers)
@@ -724,7 +746,7 @@ __device__ __forceinline__ void rs_rollout_values(const RSModel<R>& M, const dsp
       const int depth = (int)(meta >> 24);
       float u = 0.0f, v = 0.0f;
       if (!M.terminal(s)) {
-        u = (depth + 1 >= M.D) ? M.tail(s) : M.upper(s);
+        u = shared ? u_shared : ((depth + 1 >= M.D) ? M.tail(s) : M.upper(s));
         v = M.rollout(s, pm, depth + 1, steps);
       }
       fu = to_fixed(u);
