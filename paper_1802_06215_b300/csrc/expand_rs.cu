@@ -807,7 +807,7 @@ __device__ __forceinline__ void rs_rollout_chunk(const RSModel<R>& M, const dsp_
 // rolled out and the next, copied in with cp.async meanwhile, so that a
 // chunk's item loads do not stall the warp (its rollouts are short now).
 template <int R>
-__device__ __forceinline__ void stage_items(uint32_t* buf, const Items<R>& items, long long chunk) {
+__device__ __forceinline__ void stage_chunk_async(uint32_t* buf, const Items<R>& items, long long chunk) {
   constexpr int F = Items<R>::kCompactFields;
   const int lane = threadIdx.x & 31;
   const long long it = chunk * 32 + lane;
@@ -817,17 +817,71 @@ __device__ __forceinline__ void stage_items(uint32_t* buf, const Items<R>& items
       const unsigned d = (unsigned)__cvta_generic_to_shared(buf + k * 32 + lane);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(items.f(k) + it) : "memory");
     }
+}
+
+// One robot's unit of phase B: two consecutive 32-item chunks, staged
+// together (one commit group).
+constexpr int kUnitChunks = 2;
+template <int R>
+__device__ __forceinline__ void stage_unit(uint32_t* buf, const Items<R>& items, long long unit) {
+  constexpr int F = Items<R>::kCompactFields;
+#pragma unroll
+  for (int c = 0; c < kUnitChunks; ++c) stage_chunk_async<R>(buf + c * F * 32, items, unit * kUnitChunks + c);
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <int R>
 constexpr size_t rs_stage_bytes(int block) {
-  return (size_t)(block / 32) * 2 * Items<R>::kCompactFields * 32 * sizeof(uint32_t);
+  return (size_t)(block / 32) * 2 * kUnitChunks * Items<R>::kCompactFields * 32 * sizeof(uint32_t);
+}
+
+// Phase B for a unit whose 64 items all belong to one child (one robot): the
+// same position, candidate set and depth, so one trajectory (rollout_one2)
+// gives both of each lane's values; u0's per-rock terms come from lane i as
+// in rs_rollout_values, and the child's sums take one warp sum each.
+__device__ __forceinline__ void rs_rollout_pair(const RSModel<1>& M, const dsp_leaf_job* __restrict__ jobs,
+                                                uint32_t pos, uint32_t good_a, uint32_t good_b, uint32_t cand,
+                                                uint32_t meta, uint32_t job, unsigned long long& steps) {
+  const int lane = threadIdx.x & 31;
+  int64_t* usum = jobs[job].u_sum;
+  int64_t* lsum = jobs[job].l_sum;
+  const uint32_t slot = meta & 0xFFFFFFu;
+  const int depth = (int)(meta >> 24);
+  float ua = 0.0f, ub = 0.0f, va = 0.0f, vb = 0.0f;
+  if (!((pos >> 16) & 1u)) {  // not terminal
+    const int x = (int)(pos & 0xFFu);
+    if (depth + 1 >= M.D) {
+      RSS s;
+      s.pos[0] = pos;
+      s.pos[1] = 0u;
+      ua = ub = M.tail(s);
+    } else {
+      const int cell = x + (int)((pos >> 8) & 0xFFu) * M.n;
+      const float w = lane < M.m ? __fmul_rn(10.0f, M.sh->G[(int)M.nkey[lane * M.nn + cell] >> 7]) : 0.0f;
+      for (int i = 0; i < M.m; ++i) {
+        const float wi = __shfl_sync(0xFFFFFFFFu, w, i);
+        if ((good_a >> i) & 1u) ua = __fadd_rn(ua, wi);
+        if ((good_b >> i) & 1u) ub = __fadd_rn(ub, wi);
+      }
+      const float e = __fmul_rn(10.0f, M.sh->G[M.n - 1 - x]);
+      ua = __fadd_rn(ua, e);
+      ub = __fadd_rn(ub, e);
+    }
+    M.rollout_one2(pos, good_a, good_b, cand, depth + 1, va, vb, steps);
+  }
+  const long long fu = warp_sum64(to_fixed(ua) + to_fixed(ub));
+  const long long fl = warp_sum64(to_fixed(va) + to_fixed(vb));
+  if (lane == 0) {
+    sum_add(usum + slot, fu);
+    sum_add(lsum + slot, fl);
+  }
 }
 __host__ __device__ constexpr size_t rs_key_bytes_aligned(size_t key_bytes) { return (key_bytes + 15) & ~(size_t)15; }
 
+// One robot: 42 registers (three 512-thread CTAs per SM) hold a unit's two
+// items without spills (0.557 against 0.567 ms per 15x15 expansion at 32).
 template <int R>
-__global__ void __launch_bounds__(512, 4) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__global__ void __launch_bounds__(512, R == 1 ? 3 : 4) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                               const dsp_leaf_job* __restrict__ jobs,
                                                               Items<R> items, unsigned int* chunk_head,
                                                               uint32_t plan_step) {
@@ -840,9 +894,10 @@ __global__ void __launch_bounds__(512, 4) rs_rollout_items_kernel(const DevModel
   M.nkey = rs_keys;
   constexpr int F = Items<R>::kCompactFields;
   const int lane = threadIdx.x & 31;
+  // each warp's two stages of one unit (rs_stage_bytes per CTA)
   uint32_t* stage = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(rs_keys) +
                                                 rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)gm->m * gm->n * gm->n)) +
-                    (size_t)(threadIdx.x >> 5) * 2 * F * 32;
+                    (size_t)(threadIdx.x >> 5) * 2 * kUnitChunks * F * 32;
   // chunks of 32 items (fewer than 2^26: the list holds fewer than 2^31)
   const unsigned int nchunks = (unsigned int)((items.total + 31) >> 5);
   unsigned long long steps = 0;
@@ -864,50 +919,73 @@ __global__ void __launch_bounds__(512, 4) rs_rollout_items_kernel(const DevModel
     if (lane == 0 && steps) atomicAdd(&work->steps, steps);
     return;
   }
-  // One robot: chunks are claimed ChunkClaims::kBatch at a time, and one
-  // step ahead of their staging: the claim for the chunk after next is made
-  // before a chunk's rollouts and read after them.
+  // One robot: units of two chunks (64 items), claimed ChunkClaims::kBatch
+  // at a time, and one step ahead of their staging: the claim for the unit
+  // after next is made before a unit's rollouts and read after them. A unit
+  // whose 64 items are one child's shares one trajectory (rs_rollout_pair);
+  // any other takes its two chunks one after the other.
+  const unsigned int nunits = (nchunks + kUnitChunks - 1) / kUnitChunks;
   auto claim = [&]() {
     unsigned int ch = 0;
     if (lane == 0) ch = cc.take(chunk_head);
     return __shfl_sync(0xFFFFFFFFu, ch, 0);
   };
+  constexpr int kUnitWords = kUnitChunks * F * 32;
   unsigned int cur = claim();
-  if (cur < nchunks) stage_items<R>(stage, items, cur);
-  unsigned int nxt = cur < nchunks ? claim() : nchunks;
-  if (nxt < nchunks) stage_items<R>(stage + F * 32, items, nxt);
+  if (cur < nunits) stage_unit<R>(stage, items, cur);
+  unsigned int nxt = cur < nunits ? claim() : nunits;
+  if (nxt < nunits) stage_unit<R>(stage + kUnitWords, items, nxt);
   unsigned int pending = 0;  // lane 0: the claim in flight
-  if (nxt < nchunks && lane == 0) pending = cc.take(chunk_head);
+  if (nxt < nunits && lane == 0) pending = cc.take(chunk_head);
   int b = 0;
-  while (cur < nchunks) {
-    if (nxt < nchunks)
+  while (cur < nunits) {
+    if (nxt < nunits)
       asm volatile("cp.async.wait_group 1;" ::: "memory");
     else
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncwarp();
-    const uint32_t* w = stage + b * F * 32;
-    const bool ok = (long long)cur * 32 + lane < items.total;
-    RSS s;
-    s.pos[0] = w[lane];
-    s.pos[1] = R == 2 ? w[32 + lane] : 0u;
-    s.good = w[(R == 2 ? 2 : 1) * 32 + lane];
-    s.sampled = 0u;
-    s.scen = 0u;
-    const uint32_t cand = w[(R == 2 ? 3 : 2) * 32 + lane];
-    const uint32_t meta = w[(R == 2 ? 4 : 3) * 32 + lane];
-    const uint32_t job = w[(R == 2 ? 5 : 4) * 32 + lane];
-    __syncwarp();  // the buffer is read: the chunk after next may go there
+    const uint32_t* w = stage + b * kUnitWords;
+    const long long ia = (long long)cur * (32 * kUnitChunks) + lane;
+    const bool oka = ia < items.total, okb = ia + 32 < items.total;
+    const uint32_t pos_a = w[lane], good_a = w[32 + lane], cand_a = w[64 + lane], meta_a = w[96 + lane],
+                   job_a = w[128 + lane];
+    const uint32_t pos_b = w[F * 32 + lane], good_b = w[F * 32 + 32 + lane], cand_b = w[F * 32 + 64 + lane],
+                   meta_b = w[F * 32 + 96 + lane], job_b = w[F * 32 + 128 + lane];
+    __syncwarp();  // the buffer is read: the unit after next may go there
     cur = nxt;
     b ^= 1;
-    if (cur < nchunks) {
-      // cur < nchunks: the claim issued one chunk ago names the chunk to stage now
+    if (cur < nunits) {
+      // cur < nunits: the claim issued one unit ago names the unit to stage now
       nxt = __shfl_sync(0xFFFFFFFFu, pending, 0);
-      if (nxt < nchunks) {
-        stage_items<R>(stage + (b ^ 1) * F * 32, items, nxt);
+      if (nxt < nunits) {
+        stage_unit<R>(stage + (b ^ 1) * kUnitWords, items, nxt);
         if (lane == 0) pending = cc.take(chunk_head);
       }
     }
-    rs_rollout_values<R>(M, jobs, ok, s, cand, meta, job, steps);
+    // one child for all 64 items (lane 0 always holds an item)
+    const uint32_t p0 = __shfl_sync(0xFFFFFFFFu, pos_a, 0), c0 = __shfl_sync(0xFFFFFFFFu, cand_a, 0);
+    const uint32_t m0 = __shfl_sync(0xFFFFFFFFu, meta_a, 0), j0 = __shfl_sync(0xFFFFFFFFu, job_a, 0);
+    const bool one = __all_sync(0xFFFFFFFFu, oka && okb && pos_a == p0 && pos_b == p0 && cand_a == c0 &&
+                                                 cand_b == c0 && meta_a == m0 && meta_b == m0 && job_a == j0 &&
+                                                 job_b == j0);
+    if constexpr (R == 1) {
+      if (one) {
+        rs_rollout_pair(M, jobs, p0, good_a, good_b, c0, m0, j0, steps);
+        continue;
+      }
+    }
+    RSS s;
+    s.pos[0] = pos_a;
+    s.pos[1] = 0u;
+    s.good = good_a;
+    s.sampled = 0u;
+    s.scen = 0u;
+    rs_rollout_values<R>(M, jobs, oka, s, cand_a, meta_a, job_a, steps);
+    if (__any_sync(0xFFFFFFFFu, okb)) {
+      s.pos[0] = pos_b;
+      s.good = good_b;
+      rs_rollout_values<R>(M, jobs, okb, s, cand_b, meta_b, job_b, steps);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);

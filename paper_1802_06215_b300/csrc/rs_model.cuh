@@ -422,6 +422,60 @@ struct RSModel {
     return v;
   }
 
+  // rollout_one for two scenarios of one child: the same position and
+  // candidate set, so the same trajectory (the heuristic's moves read no
+  // rock state); each scenario adds its own reward at each Sample, with the
+  // operations and in the order rollout_one uses, and both rollouts' steps
+  // are counted. (A sampled rock leaves the candidate set, so no later
+  // reward reads its good bit again.)
+  __device__ __forceinline__ void rollout_one2(uint32_t p0, uint32_t good_a, uint32_t good_b, uint32_t cand, int t0,
+                                               float& va, float& vb, unsigned long long& steps) const {
+    int x = (int)(p0 & 0xFFu), y = (int)((p0 >> 8) & 0xFFu);
+    bool ex = (p0 >> 16) & 1u;
+    va = 0.0f;
+    vb = 0.0f;
+    int t = t0;
+    if (!ex) {
+      while (t < D) {
+        if (cand == 0) {
+          const int ke = min(n - 1 - x, D - t);
+          x += ke;
+          t += ke;
+          if (t < D) {
+            const float e = __fmul_rn(sh->G[t - t0], 10.0f);
+            va = __fadd_rn(va, e);
+            vb = __fadd_rn(vb, e);
+            ex = true;
+            ++t;
+          }
+          break;
+        }
+        int tx, ty;
+        uint32_t tbit;
+        target(x, y, cand, tx, ty, tbit);
+        const int sx = tx > x ? 1 : -1, sy = ty > y ? 1 : -1;
+        const int kx = min(abs(tx - x), D - t);
+        x += sx * kx;
+        t += kx;
+        const int ky = min(abs(ty - y), D - t);
+        y += sy * ky;
+        t += ky;
+        if (t >= D) break;
+        const float g = sh->G[t - t0];
+        va = __fadd_rn(va, __fmul_rn(g, (good_a & tbit) ? 10.0f : -10.0f));
+        vb = __fadd_rn(vb, __fmul_rn(g, (good_b & tbit) ? 10.0f : -10.0f));
+        cand &= ~tbit;
+        ++t;
+      }
+    }
+    steps += 2ull * (unsigned long long)(t - t0);
+    if (!ex) {
+      const float tl = __fmul_rn(sh->G[D - t0], __fmul_rn(10.0f, sh->G[n - 1 - x]));
+      va = __fadd_rn(va, tl);
+      vb = __fadd_rn(vb, tl);
+    }
+  }
+
   __device__ __forceinline__ RSS load(const uint32_t* block, int cap, int i) const {
     RSS s;
     s.pos[0] = block[i];
