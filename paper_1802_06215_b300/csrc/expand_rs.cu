@@ -680,6 +680,31 @@ __device__ __forceinline__ long long warp_sum64(long long x) {
   return (long long)h * 4294967296LL + (long long)b * 65536LL + (long long)a;
 }
 
+// u0 of a state whose robots stand at p0 (and p1) as upper() computes it,
+// split for a warp whose items share the robots' cells: lane i's term of rock
+// i (10 G[d], d the distance of its nearest live robot), and the live
+// robots' exit terms added in robot order.
+template <int R>
+__device__ __forceinline__ float upper_term(const RSModel<R>& M, uint32_t p0, uint32_t p1, int i) {
+  if (i >= M.m) return 0.0f;
+  int bestd = 1 << 30;
+  if (!((p0 >> 16) & 1u))
+    bestd = min(bestd, (int)M.nkey[i * M.nn + (int)(p0 & 0xFFu) + (int)((p0 >> 8) & 0xFFu) * M.n] >> 7);
+  if (R == 2 && !((p1 >> 16) & 1u))
+    bestd = min(bestd, (int)M.nkey[i * M.nn + (int)(p1 & 0xFFu) + (int)((p1 >> 8) & 0xFFu) * M.n] >> 7);
+  return __fmul_rn(10.0f, M.sh->G[bestd]);
+}
+template <int R>
+__device__ __forceinline__ float upper_exits(const RSModel<R>& M, uint32_t p0, uint32_t p1, float u) {
+  if (!((p0 >> 16) & 1u)) u = __fadd_rn(u, __fmul_rn(10.0f, M.sh->G[M.n - 1 - (int)(p0 & 0xFFu)]));
+  if (R == 2 && !((p1 >> 16) & 1u)) u = __fadd_rn(u, __fmul_rn(10.0f, M.sh->G[M.n - 1 - (int)(p1 & 0xFFu)]));
+  return u;
+}
+template <int R>
+__device__ __forceinline__ bool rs_terminal(uint32_t p0, uint32_t p1) {
+  return R == 1 ? ((p0 >> 16) & 1u) != 0u : (((p0 >> 16) & 1u) && ((p1 >> 16) & 1u));
+}
+
 // A warp's chunk claims, used by its lane 0 and kept in shared memory (one
 // record per warp) so that no register carries them through the rollouts.
 // Every warp of the grid draws chunks from one counter; one atomic per
@@ -719,22 +744,20 @@ __device__ __forceinline__ void rs_rollout_values(const RSModel<R>& M, const dsp
     // lane i, each lane adding its good rocks' terms in index order, as
     // upper() does (lane 0 always holds an item)
     float u_shared = 0.0f;
-    bool shared = false;
-    if constexpr (R == 1) {
-      const uint32_t p0 = __shfl_sync(0xFFFFFFFFu, s.pos[0], 0);
-      const uint32_t d0 = __shfl_sync(0xFFFFFFFFu, meta >> 24, 0);
-      shared = __all_sync(0xFFFFFFFFu, !ok || (s.pos[0] == p0 && (meta >> 24) == d0)) &&
-               !((p0 >> 16) & 1u) && (int)d0 + 1 < M.D;
-      if (shared) {
-        const int x = (int)(p0 & 0xFFu), cell = x + (int)((p0 >> 8) & 0xFFu) * M.n;
-        const float w = lane < M.m ? __fmul_rn(10.0f, M.sh->G[(int)M.nkey[lane * M.nn + cell] >> 7]) : 0.0f;
-        const uint32_t g = s.good;
-        for (int i = 0; i < M.m; ++i) {
-          const float wi = __shfl_sync(0xFFFFFFFFu, w, i);
-          if ((g >> i) & 1u) u_shared = __fadd_rn(u_shared, wi);
-        }
-        u_shared = __fadd_rn(u_shared, __fmul_rn(10.0f, M.sh->G[M.n - 1 - x]));
+    const uint32_t p0 = __shfl_sync(0xFFFFFFFFu, s.pos[0], 0);
+    const uint32_t p1 = R == 2 ? __shfl_sync(0xFFFFFFFFu, s.pos[1], 0) : 0u;
+    const uint32_t d0 = __shfl_sync(0xFFFFFFFFu, meta >> 24, 0);
+    const bool shared =
+        __all_sync(0xFFFFFFFFu, !ok || (s.pos[0] == p0 && (R == 1 || s.pos[1] == p1) && (meta >> 24) == d0)) &&
+        !rs_terminal<R>(p0, p1) && (int)d0 + 1 < M.D;
+    if (shared) {
+      const float w = upper_term<R>(M, p0, p1, lane);
+      const uint32_t g = s.good;
+      for (int i = 0; i < M.m; ++i) {
+        const float wi = __shfl_sync(0xFFFFFFFFu, w, i);
+        if ((g >> i) & 1u) u_shared = __fadd_rn(u_shared, wi);
       }
+      u_shared = upper_exits<R>(M, p0, p1, u_shared);
     }
     if (!ok) job = 0xFFFFFFFFu;
     if (ok) {
@@ -835,39 +858,42 @@ constexpr size_t rs_stage_bytes(int block) {
   return (size_t)(block / 32) * 2 * kUnitChunks * Items<R>::kCompactFields * 32 * sizeof(uint32_t);
 }
 
-// Phase B for a unit whose 64 items all belong to one child (one robot): the
-// same position, candidate set and depth, so one trajectory (rollout_one2)
-// gives both of each lane's values; u0's per-rock terms come from lane i as
-// in rs_rollout_values, and the child's sums take one warp sum each.
-__device__ __forceinline__ void rs_rollout_pair(const RSModel<1>& M, const dsp_leaf_job* __restrict__ jobs,
-                                                uint32_t pos, uint32_t good_a, uint32_t good_b, uint32_t cand,
-                                                uint32_t meta, uint32_t job, unsigned long long& steps) {
+// Phase B for a unit whose 64 items all belong to one child: the same
+// positions, candidate set and depth, so one trajectory (rollout_one2, or
+// rollout_two2 for two robots) gives both of each lane's values; u0's
+// per-rock terms come from lane i as in rs_rollout_values, and the child's
+// sums take one warp sum each.
+template <int R>
+__device__ __forceinline__ void rs_rollout_pair(const RSModel<R>& M, const dsp_leaf_job* __restrict__ jobs,
+                                                uint32_t p0, uint32_t p1, uint32_t good_a, uint32_t good_b,
+                                                uint32_t cand, uint32_t meta, uint32_t job,
+                                                unsigned long long& steps) {
   const int lane = threadIdx.x & 31;
   int64_t* usum = jobs[job].u_sum;
   int64_t* lsum = jobs[job].l_sum;
   const uint32_t slot = meta & 0xFFFFFFu;
   const int depth = (int)(meta >> 24);
   float ua = 0.0f, ub = 0.0f, va = 0.0f, vb = 0.0f;
-  if (!((pos >> 16) & 1u)) {  // not terminal
-    const int x = (int)(pos & 0xFFu);
+  if (!rs_terminal<R>(p0, p1)) {
     if (depth + 1 >= M.D) {
       RSS s;
-      s.pos[0] = pos;
-      s.pos[1] = 0u;
+      s.pos[0] = p0;
+      s.pos[1] = p1;
       ua = ub = M.tail(s);
     } else {
-      const int cell = x + (int)((pos >> 8) & 0xFFu) * M.n;
-      const float w = lane < M.m ? __fmul_rn(10.0f, M.sh->G[(int)M.nkey[lane * M.nn + cell] >> 7]) : 0.0f;
+      const float w = upper_term<R>(M, p0, p1, lane);
       for (int i = 0; i < M.m; ++i) {
         const float wi = __shfl_sync(0xFFFFFFFFu, w, i);
         if ((good_a >> i) & 1u) ua = __fadd_rn(ua, wi);
         if ((good_b >> i) & 1u) ub = __fadd_rn(ub, wi);
       }
-      const float e = __fmul_rn(10.0f, M.sh->G[M.n - 1 - x]);
-      ua = __fadd_rn(ua, e);
-      ub = __fadd_rn(ub, e);
+      ua = upper_exits<R>(M, p0, p1, ua);
+      ub = upper_exits<R>(M, p0, p1, ub);
     }
-    M.rollout_one2(pos, good_a, good_b, cand, depth + 1, va, vb, steps);
+    if constexpr (R == 1)
+      M.rollout_one2(p0, good_a, good_b, cand, depth + 1, va, vb, steps);
+    else
+      M.rollout_two2(p0, p1, good_a, good_b, cand, depth + 1, va, vb, steps);
   }
   const long long fu = warp_sum64(to_fixed(ua) + to_fixed(ub));
   const long long fl = warp_sum64(to_fixed(va) + to_fixed(vb));
@@ -878,10 +904,11 @@ __device__ __forceinline__ void rs_rollout_pair(const RSModel<1>& M, const dsp_l
 }
 __host__ __device__ constexpr size_t rs_key_bytes_aligned(size_t key_bytes) { return (key_bytes + 15) & ~(size_t)15; }
 
-// One robot: 42 registers (three 512-thread CTAs per SM) hold a unit's two
-// items without spills (0.557 against 0.567 ms per 15x15 expansion at 32).
+// 42 registers (three 512-thread CTAs per SM) hold a unit's two items
+// without spills (one robot: 0.557 against 0.567 ms per 15x15 expansion at
+// 32).
 template <int R>
-__global__ void __launch_bounds__(512, R == 1 ? 3 : 4) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__global__ void __launch_bounds__(512, 3) rs_rollout_items_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                               const dsp_leaf_job* __restrict__ jobs,
                                                               Items<R> items, unsigned int* chunk_head,
                                                               uint32_t plan_step) {
@@ -908,12 +935,32 @@ __global__ void __launch_bounds__(512, R == 1 ? 3 : 4) rs_rollout_items_kernel(c
     // Two robots: rollouts are long, so reading a chunk's items straight
     // from global memory costs less than staging them (4.40 against
     // 4.68 ms per 512-job launch of 15x15).
+    // Units of two chunks as for one robot: a unit that is one child's walks
+    // one joint trajectory for both of each lane's items.
+    const unsigned int nunits2 = (nchunks + kUnitChunks - 1) / kUnitChunks;
     while (true) {
-      unsigned int ch = 0;
-      if (lane == 0) ch = cc.take(chunk_head);
-      ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
-      if (ch >= nchunks) break;
-      rs_rollout_chunk<R>(M, jobs, items, ch, steps);
+      unsigned int un = 0;
+      if (lane == 0) un = cc.take(chunk_head);
+      un = __shfl_sync(0xFFFFFFFFu, un, 0);
+      if (un >= nunits2) break;
+      const long long ia = (long long)un * (32 * kUnitChunks) + lane;
+      const bool oka = ia < items.total, okb = ia + 32 < items.total;
+      RSS sa, sb;
+      uint32_t cand_a = 0, meta_a = 0, job_a = 0, cand_b = 0, meta_b = 0, job_b = 0;
+      if (oka) items.get_compact((size_t)ia, sa, cand_a, meta_a, job_a);
+      if (okb) items.get_compact((size_t)(ia + 32), sb, cand_b, meta_b, job_b);
+      const uint32_t q0 = __shfl_sync(0xFFFFFFFFu, sa.pos[0], 0), q1 = __shfl_sync(0xFFFFFFFFu, sa.pos[1], 0);
+      const uint32_t c0 = __shfl_sync(0xFFFFFFFFu, cand_a, 0), m0 = __shfl_sync(0xFFFFFFFFu, meta_a, 0);
+      const uint32_t j0 = __shfl_sync(0xFFFFFFFFu, job_a, 0);
+      const bool one = __all_sync(0xFFFFFFFFu, oka && okb && sa.pos[0] == q0 && sb.pos[0] == q0 && sa.pos[1] == q1 &&
+                                                   sb.pos[1] == q1 && cand_a == c0 && cand_b == c0 && meta_a == m0 &&
+                                                   meta_b == m0 && job_a == j0 && job_b == j0);
+      if (one) {
+        rs_rollout_pair<R>(M, jobs, q0, q1, sa.good, sb.good, c0, m0, j0, steps);
+        continue;
+      }
+      rs_rollout_values<R>(M, jobs, oka, sa, cand_a, meta_a, job_a, steps);
+      if (__any_sync(0xFFFFFFFFu, okb)) rs_rollout_values<R>(M, jobs, okb, sb, cand_b, meta_b, job_b, steps);
     }
     for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
     if (lane == 0 && steps) atomicAdd(&work->steps, steps);
@@ -970,7 +1017,7 @@ __global__ void __launch_bounds__(512, R == 1 ? 3 : 4) rs_rollout_items_kernel(c
                                                  job_b == j0);
     if constexpr (R == 1) {
       if (one) {
-        rs_rollout_pair(M, jobs, p0, good_a, good_b, c0, m0, j0, steps);
+        rs_rollout_pair<1>(M, jobs, p0, 0u, good_a, good_b, c0, m0, j0, steps);
         continue;
       }
     }

@@ -422,6 +422,87 @@ struct RSModel {
     return v;
   }
 
+  // heuristic_step for two scenarios of one child that share the robots'
+  // positions, targets and candidate set: the moves and exits are the same,
+  // and a Sample gives each scenario its own reward (added to ra, rb) and
+  // clears the rock in both good masks.
+  __device__ __forceinline__ void heuristic_step2(int& x, int& y, bool& ex, int tx, int ty, uint32_t& tbit,
+                                                  uint32_t& good_a, uint32_t& good_b, uint32_t& cand, int& ra,
+                                                  int& rb) const {
+    if (ex) return;
+    if (tbit == 0) {
+      if (x == n - 1) {
+        ex = true;
+        ra += 10;
+        rb += 10;
+        return;
+      }
+      x += 1;
+      return;
+    }
+    if (x == tx && y == ty) {
+      ra += (good_a & tbit) ? 10 : -10;
+      rb += (good_b & tbit) ? 10 : -10;
+      good_a &= ~tbit;
+      good_b &= ~tbit;
+      cand &= ~tbit;
+      tbit = 0;
+      return;
+    }
+    if (x != tx)
+      x += tx > x ? 1 : -1;
+    else
+      y += ty > y ? 1 : -1;
+  }
+
+  // rollout_two for two scenarios of one child: one joint trajectory (the
+  // robots' moves read no rock state), each scenario's rewards at the event
+  // steps added as rollout_two adds them (a zero reward skipped); both
+  // rollouts' steps are counted.
+  __device__ __forceinline__ void rollout_two2(uint32_t p0, uint32_t p1, uint32_t good_a, uint32_t good_b,
+                                               uint32_t cand, int t0, float& va, float& vb,
+                                               unsigned long long& steps) const {
+    int x0 = (int)(p0 & 0xFFu), y0 = (int)((p0 >> 8) & 0xFFu);
+    int x1 = (int)(p1 & 0xFFu), y1 = (int)((p1 >> 8) & 0xFFu);
+    bool ex0 = (p0 >> 16) & 1u, ex1 = (p1 >> 16) & 1u;
+    int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+    uint32_t tb0 = 0, tb1 = 0;
+    va = 0.0f;
+    vb = 0.0f;
+    int t = t0;
+    while (t < D && !(ex0 && ex1)) {
+      if (!ex0 && (tb0 & cand) == 0) {
+        tb0 = 0;
+        if (cand != 0) target(x0, y0, cand, tx0, ty0, tb0);
+      }
+      if (!ex1 && (tb1 & cand) == 0) {
+        tb1 = 0;
+        if (cand != 0) target(x1, y1, cand, tx1, ty1, tb1);
+      }
+      const int k = min(min(event_steps(x0, y0, ex0, tx0, ty0, tb0), event_steps(x1, y1, ex1, tx1, ty1, tb1)), D - t);
+      move_steps(x0, y0, ex0, tx0, ty0, tb0, k);
+      move_steps(x1, y1, ex1, tx1, ty1, tb1, k);
+      t += k;
+      if (t >= D) break;
+      int ra = 0, rb = 0;
+      heuristic_step2(x0, y0, ex0, tx0, ty0, tb0, good_a, good_b, cand, ra, rb);
+      heuristic_step2(x1, y1, ex1, tx1, ty1, tb1, good_a, good_b, cand, ra, rb);
+      const float g = sh->G[t - t0];
+      if (ra != 0) va = __fadd_rn(va, __fmul_rn(g, (float)ra));
+      if (rb != 0) vb = __fadd_rn(vb, __fmul_rn(g, (float)rb));
+      t += 1;
+    }
+    steps += 2ull * (unsigned long long)(t - t0);
+    if (!(ex0 && ex1)) {
+      float l = 0.0f;
+      if (!ex0) l = __fadd_rn(l, __fmul_rn(10.0f, sh->G[n - 1 - x0]));
+      if (!ex1) l = __fadd_rn(l, __fmul_rn(10.0f, sh->G[n - 1 - x1]));
+      const float tl = __fmul_rn(sh->G[D - t0], l);
+      va = __fadd_rn(va, tl);
+      vb = __fadd_rn(vb, tl);
+    }
+  }
+
   // rollout_one for two scenarios of one child: the same position and
   // candidate set, so the same trajectory (the heuristic's moves read no
   // rock state); each scenario adds its own reward at each Sample, with the
