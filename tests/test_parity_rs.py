@@ -322,3 +322,61 @@ def test_expand_parity_mixed_leaves(dsp, form):
         total += o["steps"]
     assert steps == total
     m.close()
+
+
+def test_expand_parity_two_robots_shared_cells(dsp):
+    """Two robots, leaves that share both positions (as a tree node's do)
+    placed on the joint step's corner cases: both robots on one rock (a
+    joint Sample of the same rock, a Sense after the other robot's Sample),
+    one robot or both already exited, robots on the east and north borders;
+    next to leaves with per-scenario positions and a job split over several
+    action ranges. All match the oracle."""
+    cfg = I.mars11_11()
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    rng = np.random.default_rng(29)
+    rock = [(int(c) & 0xFF, int(c) >> 8) for c in cfg.rock_cells]
+    n1 = cfg.n - 1
+    cases = [
+        # (positions, exited, sampled, n, depth)
+        ([rock[0], rock[0]], (0, 0), 0, 150, 0),
+        ([rock[1], rock[1]], (0, 0), 1 << 2, 64, 3),
+        ([rock[2], rock[3]], (1, 0), 0, 90, 5),
+        ([rock[4], (n1, 0)], (0, 1), 1 << 4, 33, 2),
+        ([(n1, n1), (n1, 5)], (0, 0), 0, 120, 7),
+        ([(0, 0), (3, 3)], (1, 1), 0, 40, 4),
+        ([rock[5], (n1, n1)], (0, 0), 1 << 5, 1, 1),
+    ]
+    jobs = []
+    for pos, ex, samp, n, depth in cases:
+        pb = I.rs_block(cfg, n, rng, pos=pos, sampled=samp, exited=ex)
+        jobs.append(I.Job(parent=pb, idx=np.arange(n, dtype=np.uint16), last_action=-1, depth=depth,
+                          hist=I.random_hist(cfg, rng, depth), first_action=0, n_actions=m.num_actions))
+    for n, depth in [(80, 2), (17, 6)]:
+        pb = I.rs_block(cfg, n, rng)  # per-scenario positions
+        samp = rng.integers(0, 1 << cfg.m, n).astype(np.uint32) & rng.integers(0, 1 << cfg.m, n).astype(np.uint32)
+        pb[3] = samp
+        pb[2] &= ~samp
+        jobs.append(I.Job(parent=pb, idx=np.arange(n, dtype=np.uint16), last_action=-1, depth=depth,
+                          hist=I.random_hist(cfg, rng, depth), first_action=0, n_actions=m.num_actions))
+    # one node's actions in three ranges
+    pb = I.rs_block(cfg, 70, rng, pos=[rock[6], rock[6]])
+    third = m.num_actions // 3
+    for lo, hi in [(0, third), (third, 2 * third), (2 * third, m.num_actions)]:
+        jobs.append(I.Job(parent=pb, idx=np.arange(70, dtype=np.uint16), last_action=-1, depth=3,
+                          hist=np.zeros(32, np.int8), first_action=lo, n_actions=hi - lo))
+    jobs += I.job_stream(cfg, 4, 31)
+    jb = dsp.JobBatch(m, jobs)
+    m.reset_counters()
+    jb.run()
+    steps, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    total = 0
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, a0=j.first_action, na=j.n_actions,
+                      cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"two-robot job {k}")
+        total += o["steps"]
+    assert steps == total
+    m.close()
