@@ -713,8 +713,10 @@ def sweep(args):
     """Variants of the same kernels (crowd sizes, map sizes and joint action
     counts, numbers of scenarios): one JSON line per workload with its
     device-resident rate, kernel time and ALU roofline fraction. Each point
-    times `--steps` expansions after `--warmup` (L2 flushed before each) and
-    counts algorithmic ops with the oracle on the leading jobs for 2 s."""
+    runs the autotuner's launch shape for its batch (unless --shape or
+    --no-autotune), times `--steps` expansions after `--warmup` (L2 flushed
+    before each) and counts algorithmic ops with the oracle on the leading
+    jobs for 2 s."""
     import torch
     from paper_1802_06215_b300 import _dsp, batch, build
     build.build()
@@ -725,11 +727,19 @@ def sweep(args):
         mk, njobs, desc, _ = WORKLOADS[name]
         cfg = mk()
         m = batch.Model(cfg)
+        jobs = inputs.job_stream(cfg, args.jobs or njobs, 1000)
+        jb = batch.JobBatch(m, jobs)
+        tuned = None
         if args.shape:  # fields that do not apply to the workload's model keep their defaults
             fields = {k: int(v) for k, v in (kv.split("=") for kv in args.shape.split(","))}
             _dsp.dsp_set_launch_shape(m.h, **fields)
-        jobs = inputs.job_stream(cfg, args.jobs or njobs, 1000)
-        jb = batch.JobBatch(m, jobs)
+        elif not args.no_autotune:
+            # the autotuner's shape for this batch; its default-shape time beside it
+            from paper_1802_06215_b300 import autotune as AT
+            best = AT.autotune(m, jb, torch.cuda.get_device_name(), None, reps=3)
+            tuned = {"shape": {k: best[k] for k in _dsp.SHAPE_FIELDS}, "tuning_ms_per_call": best.get("ms"),
+                     "default_tuning_ms_per_call": best.get("default_ms"),
+                     "note": "0 = the field's default; the line's times are this shape's"}
         for _ in range(args.warmup):
             jb.run()
         torch.cuda.synchronize()
@@ -757,7 +767,7 @@ def sweep(args):
                           "ops_per_scenario_step": ops, "roofline": {"bound": "alu", "achieved": achieved,
                                                                      "peak": peak_tops, "unit": "Tops/s",
                                                                      "frac": achieved / peak_tops},
-                          "cpu_oracle_1core": r1["steps"] / r1["seconds"]}), flush=True)
+                          "autotune": tuned, "cpu_oracle_1core": r1["steps"] / r1["seconds"]}), flush=True)
         m.close()
         del jb
 

@@ -335,8 +335,8 @@ dsp_status dsp_pomcp_plan(dsp_model* model, const uint32_t* root_states, int32_t
  * blocks and scenarios to threads, Sec. III-D, made a tunable): block = CTA
  * size of the Rock Sample rollout phase (128, 256 or 512; the car kernel runs
  * 256), tps = lanes sharing one car scenario (4, 8, 16 or 32; element-level
- * parallelism). 0 keeps the default (256, 32). Returns DSP_E_INVALID for
- * other values. */
+ * parallelism). 0 keeps the default (256; tps as dsp_set_launch_shape
+ * states). Returns DSP_E_INVALID for other values. */
 dsp_status dsp_set_tuning(dsp_model* model, int32_t block, int32_t tps);
 dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
 
@@ -353,10 +353,12 @@ dsp_status dsp_get_tuning(const dsp_model* model, int32_t* block, int32_t* tps);
  *    actions each warp expands about A / warps_a whole actions of a job
  *    (default: 5 warps with 12 or more jobs per SM for one robot, else up to
  *    16 warps of equal action counts).
- *  - tps: car, lanes sharing one scenario (4, 8, 16 or 32; default the
- *    smallest that gives each lane at most one pedestrian pair): the
- *    within-step split over pedestrians; with more pairs than lanes each lane
- *    takes several.
+ *  - tps: car, lanes sharing one scenario (4, 8, 16 or 32): the within-step
+ *    split over pedestrians; with more pairs than lanes each lane takes
+ *    ceil(pairs / tps) of them (the kernel is sized to that, up to four).
+ *    Default: the tps whose pair slots (tps x pairs per lane) the crowd fills
+ *    best, the largest on a tie (4 for 6 and 20 pedestrians, 8 for 12, 32
+ *    for 50).
  *  - ctas_car: car kernel CTAs per SM (1..32, capped by what fits).
  *  - rs_form: one-robot Rock Sample with the heuristic default policy, how
  *    the grouping phase hands its (action, scenario) pairs to the rollout

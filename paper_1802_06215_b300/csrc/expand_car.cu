@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "car_model.cuh"
 #include "group.cuh"
@@ -166,8 +167,13 @@ __device__ __forceinline__ void car_unit(CarUnitSmem& S, const CarModel<TPS, KP>
   __syncthreads();
 }
 
+// CTAs per SM the register budget is sized for: the pairs a lane holds set
+// the registers it needs
+template <int TPS, int KP>
+constexpr int kCarMinBlocks = (TPS >= 16 || KP == 1) ? 4 : (KP == 2 ? 3 : (KP <= 4 ? 2 : 1));
+
 template <int TPS, int KP = kDefaultPairs<TPS>>
-__global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
+__global__ void __launch_bounds__(256, (kCarMinBlocks<TPS, KP>)) car_expand_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                          const dsp_leaf_job* __restrict__ jobs,
                                                          const int4* __restrict__ units, int n_units,
                                                          unsigned int* head, uint32_t plan_step,
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(256) car_rollout_kernel(const DevModel* __rest
 // scratch, then publishes the job done. Idle CTAs back off and exit after
 // idle_ns without a job; the host relaunches the kernel when jobs come.
 template <int TPS, int KP = kDefaultPairs<TPS>>
-__global__ void __launch_bounds__(256, (TPS >= 16 || KP == 1) ? 4 : 1)
+__global__ void __launch_bounds__(256, (kCarMinBlocks<TPS, KP>))
     car_queue_kernel(const DevModel* __restrict__ gm, DevWork* work, QueueRing ring, unsigned long long* head,
                      uint32_t* scratch, dsp_leaf_job* jcopy, unsigned long long idle_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -335,46 +341,75 @@ cudaError_t launch_tps(dsp_model* m, const dsp_leaf_job* djobs, const int4* duni
   return e != cudaSuccess ? e : e2;
 }
 
-}  // namespace
-
-int car_default_tps(int P) {
-  const int pairs = (P + 1) / 2;
-  int tps = 4;
-  while (tps < pairs && tps < 32) tps *= 2;
-  return tps;
+// Pairs per lane fitted to the crowd: KP = ceil(pairs / TPS) up to four
+// pairs a lane, else the kernel sized for kMaxPeds; f is called with the
+// chosen KP as a std::integral_constant.
+template <int TPS, class F>
+cudaError_t with_fitted_pairs(int pairs, F&& f) {
+  const int kp = (pairs + TPS - 1) / TPS;
+  if (kp <= 1) return f(std::integral_constant<int, 1>{});
+  if constexpr (kDefaultPairs<TPS> > 2)
+    if (kp == 2) return f(std::integral_constant<int, 2>{});
+  if constexpr (kDefaultPairs<TPS> > 3)
+    if (kp == 3) return f(std::integral_constant<int, 3>{});
+  if constexpr (kDefaultPairs<TPS> > 4)
+    if (kp == 4) return f(std::integral_constant<int, 4>{});
+  return f(std::integral_constant<int, kDefaultPairs<TPS>>{});
 }
 
-// With the crowd fitting one pair per lane, the kernel that holds one pair
-// per lane (fewer registers, no idle pair slots) runs.
+// f called with the lanes per scenario tps as a std::integral_constant
+template <class F>
+cudaError_t with_tps(int tps, F&& f) {
+  switch (tps) {
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    default: return f(std::integral_constant<int, 32>{});
+  }
+}
+
+}  // namespace
+
+// The untuned lanes per scenario: the one whose pair slots (TPS lanes x
+// fitted pairs per lane) the crowd fills best; on a tie the most lanes
+// (fewer registers per lane).
+int car_default_tps(int P) {
+  const int pairs = (P + 1) / 2;
+  int best = 32;
+  double best_fill = -1.0;
+  for (int tps : {32, 16, 8, 4}) {
+    int kp = (pairs + tps - 1) / tps;
+    if (kp > 4) kp = (kMaxPeds / 2 + tps - 1) / tps;
+    const double fill = (double)pairs / (double)(tps * std::max(1, kp));
+    if (fill > best_fill + 1e-9) {
+      best_fill = fill;
+      best = tps;
+    }
+  }
+  return best;
+}
+
 cudaError_t launch_car_expand(dsp_model* m, const dsp_leaf_job* djobs, const int4* dunits, int n_units,
                               unsigned int* head, CarItems items, cudaStream_t st) {
   const int pairs = (m->host->P + 1) / 2;
-  switch (m->tune_tps > 0 ? m->tune_tps : car_default_tps(m->host->P)) {
-    case 4:
-      return pairs <= 4 ? launch_tps<4, 1>(m, djobs, dunits, n_units, head, items, st)
-                        : launch_tps<4>(m, djobs, dunits, n_units, head, items, st);
-    case 8:
-      return pairs <= 8 ? launch_tps<8, 1>(m, djobs, dunits, n_units, head, items, st)
-                        : launch_tps<8>(m, djobs, dunits, n_units, head, items, st);
-    case 16:
-      return pairs <= 16 ? launch_tps<16, 1>(m, djobs, dunits, n_units, head, items, st)
-                         : launch_tps<16>(m, djobs, dunits, n_units, head, items, st);
-    default: return launch_tps<32>(m, djobs, dunits, n_units, head, items, st);
-  }
+  return with_tps(m->tune_tps > 0 ? m->tune_tps : car_default_tps(m->host->P), [&](auto t) {
+    constexpr int TPS = decltype(t)::value;
+    return with_fitted_pairs<TPS>(pairs, [&](auto k) {
+      return launch_tps<TPS, decltype(k)::value>(m, djobs, dunits, n_units, head, items, st);
+    });
+  });
 }
 
 // The persistent queue kernel's lanes per scenario: the expansion's untuned
-// default for the crowd (one pedestrian pair per lane where the crowd fits).
-// Sets the kernel's shared-memory limit (before any capture) and returns the
-// CTAs that fit per SM.
+// default for the crowd, with the fitted pairs per lane. Sets the kernel's
+// shared-memory limit (before any capture) and returns the CTAs that fit per
+// SM.
 cudaError_t car_queue_setup(const dsp_model* m, int* per_sm) {
   const int pairs = (m->host->P + 1) / 2;
-  switch (car_default_tps(m->host->P)) {
-    case 4: return pairs <= 4 ? queue_tps_setup<4, 1>(per_sm) : queue_tps_setup<4, kDefaultPairs<4>>(per_sm);
-    case 8: return pairs <= 8 ? queue_tps_setup<8, 1>(per_sm) : queue_tps_setup<8, kDefaultPairs<8>>(per_sm);
-    case 16: return pairs <= 16 ? queue_tps_setup<16, 1>(per_sm) : queue_tps_setup<16, kDefaultPairs<16>>(per_sm);
-    default: return queue_tps_setup<32, kDefaultPairs<32>>(per_sm);
-  }
+  return with_tps(car_default_tps(m->host->P), [&](auto t) {
+    constexpr int TPS = decltype(t)::value;
+    return with_fitted_pairs<TPS>(pairs, [&](auto k) { return queue_tps_setup<TPS, decltype(k)::value>(per_sm); });
+  });
 }
 
 size_t car_queue_scratch_words(int grid) { return (size_t)grid * kMaxScen * kCarObsWords; }
@@ -382,18 +417,12 @@ size_t car_queue_scratch_words(int grid) { return (size_t)grid * kMaxScen * kCar
 cudaError_t launch_car_queue(dsp_model* m, QueueRing ring, unsigned long long* head, uint32_t* scratch,
                              dsp_leaf_job* jcopy, unsigned long long idle_ns, int grid, cudaStream_t st) {
   const int pairs = (m->host->P + 1) / 2;
-  switch (car_default_tps(m->host->P)) {
-    case 4:
-      return pairs <= 4 ? queue_tps<4, 1>(m, ring, head, scratch, jcopy, idle_ns, grid, st)
-                        : queue_tps<4, kDefaultPairs<4>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
-    case 8:
-      return pairs <= 8 ? queue_tps<8, 1>(m, ring, head, scratch, jcopy, idle_ns, grid, st)
-                        : queue_tps<8, kDefaultPairs<8>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
-    case 16:
-      return pairs <= 16 ? queue_tps<16, 1>(m, ring, head, scratch, jcopy, idle_ns, grid, st)
-                         : queue_tps<16, kDefaultPairs<16>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
-    default: return queue_tps<32, kDefaultPairs<32>>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
-  }
+  return with_tps(car_default_tps(m->host->P), [&](auto t) {
+    constexpr int TPS = decltype(t)::value;
+    return with_fitted_pairs<TPS>(pairs, [&](auto k) {
+      return queue_tps<TPS, decltype(k)::value>(m, ring, head, scratch, jcopy, idle_ns, grid, st);
+    });
+  });
 }
 
 cudaError_t launch_car_step(const DevModel* gm, int P, const uint32_t* in, int in_cap, int count,

@@ -101,26 +101,30 @@ def test_expand_parity(dsp, tps):
     m.close()
 
 
-@pytest.mark.parametrize("P", [6, 12, 20])
+@pytest.mark.parametrize("P", [6, 7, 12, 20])
 def test_expand_parity_crowd_sizes(dsp, P):
-    """The crowd sizes of the pedestrian-count study: each lane owns fewer
-    pairs, and some lanes none."""
+    """The crowd sizes of the pedestrian-count study, at the default lanes per
+    scenario and at 4 and 8: each lane owns one to three pedestrian pairs (the
+    kernel sized to the crowd), some lanes fewer or none."""
+    from paper_1802_06215_b300 import _dsp
     cfg = I.car_p(P)
     m = dsp.Model(cfg)
     om = oracle.Model(cfg)
     jobs = I.job_stream(cfg, 6, 23 + P, max_scen=70)
-    jb = dsp.JobBatch(m, jobs)
-    m.reset_counters()
-    jb.run()
-    steps, status = m.counters()
-    assert status == 0
-    res = jb.all_results()
-    total = 0
-    for k, j in enumerate(jobs):
-        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
-        _cmp(res[k], o, f"P{P} job {k}")
-        total += o["steps"]
-    assert steps == total
+    expect = [om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, cap=m.max_children(len(j.idx)))
+              for j in jobs]
+    for tps in (0, 4, 8):
+        _dsp.dsp_set_tuning(m.h, 0, tps)
+        jb = dsp.JobBatch(m, jobs)
+        m.reset_counters()
+        jb.run()
+        steps, status = m.counters()
+        assert status == 0
+        res = jb.all_results()
+        for k, o in enumerate(expect):
+            _cmp(res[k], o, f"P{P} tps{tps} job {k}")
+        assert steps == sum(o["steps"] for o in expect)
+        del jb
     m.close()
 
 
