@@ -102,6 +102,8 @@ def parse():
                         "(e.g. rs_form=2,block_b=256)")
     p.add_argument("--plan-worlds", type=int, default=16,
                    help="rs15_15: planner episodes on this many seeded worlds (100 steps, 4 threads, 200 trials each)")
+    p.add_argument("--e2e-lanes", type=int, default=E2E_LANES,
+                   help="job arenas (and streams) taking the end-to-end steps in turn")
     p.add_argument("--no-companions", action="store_true",
                    help="measure only --workload (a default rs15_15 run also measures car50 under its own key)")
     p.add_argument("--episodes", type=int, default=0,
@@ -550,7 +552,8 @@ def measure(args, name, rank, world, dist, local, headline=True):
     # job arenas on three streams take the steps in turn, so that one step's
     # transfers overlap the others' kernels; the time is the wall time of all
     # steps, first copy to last result.
-    lanes = [(stream, jb)] + [(torch.cuda.Stream(), batch.JobBatch(m, jobs)) for _ in range(E2E_LANES - 1)]
+    n_lanes = max(1, args.e2e_lanes)
+    lanes = [(stream, jb)] + [(torch.cuda.Stream(), batch.JobBatch(m, jobs)) for _ in range(n_lanes - 1)]
     for s_, b_ in lanes:  # warm every arena and stream
         with torch.cuda.stream(s_):
             b_.upload_inputs()
@@ -561,6 +564,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
     e2s.record(stream)
     for s_, _ in lanes[1:]:
         s_.wait_event(e2s)
+    h0 = time.perf_counter()
     for k in range(args.steps):
         s_, b_ = lanes[k % len(lanes)]
         with torch.cuda.stream(s_):
@@ -568,6 +572,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
             b_.upload_inputs()
             b_.run(s_)
             b_.download_outputs()
+    host_ms = (time.perf_counter() - h0) * 1000.0  # the host's enqueueing, before the last result
     for s_, _ in lanes[1:]:
         tail = torch.cuda.Event()
         tail.record(s_)
@@ -663,8 +668,9 @@ def measure(args, name, rank, world, dist, local, headline=True):
         "leaf_expansions_per_s": njobs * world * args.steps / (t_ms / 1000.0),
         "scenario_steps_per_step": steps_per_launch,
         "e2e": {"value": e2_value, "unit": "scenario-steps/s", "h2d_bytes_per_step": jb.input_bytes,
-                "d2h_bytes_per_step": jb.output_bytes,
-                "method": f"dsp_expand_leaves on {E2E_LANES} job arenas and {E2E_LANES} streams taking the steps in turn; "
+                "d2h_bytes_per_step": jb.output_bytes, "ms_per_step": e2_ms / args.steps,
+                "host_enqueue_ms_per_step": host_ms / args.steps,
+                "method": f"dsp_expand_leaves on {n_lanes} job arenas and {n_lanes} streams taking the steps in turn; "
                           "wall time from the first upload to the last result, L2 flush in each step; "
                           "read back: each child's count, offsets, key and reward/u/l sums (what dsp_plan's "
                           "search reads); the leaf states and grouped positions stay on the device",
