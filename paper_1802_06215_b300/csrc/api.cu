@@ -398,9 +398,10 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
   plan.item_base.clear();
   plan.unit_base.clear();
   plan.scen_base.clear();
-  plan.total_items = plan.total_blocks = plan.total_scen = 0;
+  plan.total_items = plan.total_blocks = plan.total_scen = plan.slice_cap = 0;
   plan.blocks = allow_blocks && h->kind != DSP_MODEL_CAR && h->kind != DSP_MODEL_NAV && h->robots == 1 &&
                 !m->policy_on && m->tune_rs_form == 1;
+  plan.slices = allow_blocks && h->kind == DSP_MODEL_GRID && !m->policy_on && !plan.blocks;
   for (int j = 0; j < n_jobs; ++j) {
     const dsp_leaf_job& J = jobs[j];
     const int max_n = h->kind == DSP_MODEL_GRID ? kMaxScenLarge : kMaxScen;
@@ -432,8 +433,12 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
     } else {
       plan.item_base.push_back(plan.total_items);
       plan.total_items += (long long)J.n_scen * J.n_actions;
+      // an action's children (at most 6 observation codes) in runs of at
+      // most kSliceItems
+      if (plan.slices) plan.slice_cap += (long long)J.n_actions * ((J.n_scen + kSliceItems - 1) / kSliceItems + 6);
     }
   }
+  if (plan.slice_cap >= (1LL << 31)) plan.slices = false;
   if (plan.total_items >= (1LL << 31)) return fail(DSP_E_UNSUPPORTED, "more than 2^31 (action, scenario) items");
   // Largest work first (units and jobs are independent, so the order changes
   // no result): persistent CTAs that pull work in this order end together
@@ -534,7 +539,9 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
               : plan.blocks
                   ? align256(sizeof(uint32_t) * 3 * (size_t)plan.total_scen) + sizeof(int) * (size_t)plan.total_blocks
                   : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots, m->policy_on) * (size_t)plan.total_items;
-  size_t total = align256(jb) + align256(ub) + 256 + align256(ib);
+  const bool slices = !by_unit && plan.slices;
+  const size_t sb = slices ? sizeof(uint2) * (size_t)plan.slice_cap : 0;
+  size_t total = align256(jb) + align256(ub) + 256 + align256(ib) + sb;
   unsigned char* buf = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, total, m->pool, st);
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves: work buffers");
@@ -610,11 +617,16 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
         lb.scen_base = (const long long*)dunits + n;
         lb.chunk_job = (int*)((unsigned char*)items + align256(sizeof(uint32_t) * 3 * (size_t)plan.total_scen));
       }
+      Slices sl;
+      if (slices) {
+        sl.list = (uint2*)((unsigned char*)items + align256(ib));
+        sl.cap = (unsigned int)plan.slice_cap;
+      }
       e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, rs_key_words(h), m->dwork, djobs,
                            (const long long*)dunits, dorder, n_jobs,
                            plan.blocks ? plan.total_blocks : plan.total_items, items, counters, m->plan_step,
                            m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st, m->tune_warps_a,
-                           m->tune_ctas_b, plan.blocks ? &lb : nullptr);
+                           m->tune_ctas_b, plan.blocks ? &lb : nullptr, slices ? &sl : nullptr);
     }
     if (m->timing) {
       cudaEventRecord(ev[1], st);

@@ -114,6 +114,29 @@ __device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& 
   __syncthreads();
 }
 
+// An action's slices for the rollout phase: each child's grouped positions
+// (count cnt[c] from offset off[c]) in runs of at most kSliceItems items.
+// Called by one lane; one atomic per action takes the slots.
+template <int kC>
+__device__ __forceinline__ void put_slices(const Slices& sl, long long ibase, int a, int n, const int (&cnt)[kC],
+                                           const int (&off)[kC], DevWork* work) {
+  if (sl.list == nullptr) return;
+  int ns = 0;
+#pragma unroll
+  for (int c = 0; c < kC; ++c) ns += (cnt[c] + kSliceItems - 1) / kSliceItems;
+  if (ns == 0) return;
+  unsigned int k = atomicAdd(sl.count, (unsigned int)ns);
+  if (k + (unsigned int)ns > sl.cap) {
+    report(work, kStatusOverflow);
+    return;
+  }
+  const long long first = ibase + (long long)a * n;
+#pragma unroll
+  for (int c = 0; c < kC; ++c)
+    for (int s = 0; s < cnt[c]; s += kSliceItems)
+      sl.list[k++] = make_uint2((uint32_t)(first + off[c] + s), (uint32_t)min(kSliceItems, cnt[c] - s));
+}
+
 // Phase A for one robot, where an action's scenarios fall into at most a few
 // children: observation z in {0, 1, 2} and whether the step ended the world
 // give 6 codes (a move or Sample gives every scenario of a job one code, a
@@ -125,7 +148,7 @@ __device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& 
 // that draw no random numbers (a Sense leaves the state as it was). The result
 // is identical to the general grouping; no barrier is needed inside the job.
 __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long long ibase, Items<1> items,
-                              DevWork* work, unsigned long long& steps, const LeafBlocks& lb) {
+                              DevWork* work, unsigned long long& steps, const LeafBlocks& lb, const Slices& sl) {
   constexpr int kC = 6;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   gather_update<1>(S, M, true, steps);
@@ -258,6 +281,7 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
       J.child_count[a] = nch;
       if (nch > cap) report(work, kStatusOverflow);
       if (nch <= cap) J.child_off[(size_t)a * (cap + 1) + nch] = n;
+      put_slices<kC>(sl, ibase, a, n, cnt, off, work);
 #pragma unroll
       for (int c = 0; c < kC; ++c)
         if (cnt[c] > 0 && cid[c] < cap) {
@@ -335,7 +359,8 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
 // step and observation code instead of keeping them. The placement is the
 // same as rs1_group_job's, so the result is identical.
 __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, long long ibase, Items<1> items,
-                                    DevWork* work, unsigned long long& steps, const LeafBlocks& lb) {
+                                    DevWork* work, unsigned long long& steps, const LeafBlocks& lb,
+                                    const Slices& sl) {
   constexpr int kC = 6;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const dsp_leaf_job& J = S.J;
@@ -416,6 +441,7 @@ __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, 
       J.child_count[a] = nch;
       if (nch > cap) report(work, kStatusOverflow);
       if (nch <= cap) J.child_off[(size_t)a * (cap + 1) + nch] = n;
+      put_slices<kC>(sl, ibase, a, n, cnt, off, work);
 #pragma unroll
       for (int c = 0; c < kC; ++c)
         if (cnt[c] > 0 && cid[c] < cap) {
@@ -617,12 +643,13 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
 template <int R, bool kLarge = true>
 __device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, int j, long long ibase, int a_begin,
                                           int a_end, bool first, Items<R> items, DevWork* work,
-                                          unsigned long long& steps, const LeafBlocks& lb = LeafBlocks{}) {
+                                          unsigned long long& steps, const LeafBlocks& lb = LeafBlocks{},
+                                          const Slices& sl = Slices{}) {
   if constexpr (R == 1) {
     if (kLarge && S.J.n_scen > kMaxScen)
-      rs1_group_job_large(S, M, j, ibase, items, work, steps, lb);
+      rs1_group_job_large(S, M, j, ibase, items, work, steps, lb, sl);
     else
-      rs1_group_job(S, M, j, ibase, items, work, steps, lb);
+      rs1_group_job(S, M, j, ibase, items, work, steps, lb, sl);
   } else
     rs2_group_job(S, M, j, ibase, a_begin, a_end, first, items, work, steps);
 }
@@ -633,7 +660,8 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
                                                              const long long* __restrict__ item_base,
                                                              const int* __restrict__ order, int n_jobs,
                                                              unsigned int* head, uint32_t plan_step,
-                                                             Items<R> items, int splits, LeafBlocks lb) {
+                                                             Items<R> items, int splits, LeafBlocks lb,
+                                                             Slices sl) {
   __shared__ RSGroupSmem S;
   load_rs_consts(S.c, gm);
   const RSModel<R> M = make_rs<R>(gm, &S.c, plan_step);
@@ -660,7 +688,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
     // next unit (the condition is the same for the whole CTA)
     if (a_begin < a_end)
       group_job<R>(S, M, j, item_base != nullptr ? item_base[j] : 0, a_begin, a_end, S.part == 0, items, work,
-                   steps, lb);
+                   steps, lb, sl);
     else
       __syncthreads();
   }
@@ -1038,6 +1066,127 @@ __global__ void __launch_bounds__(512, 3) rs_rollout_items_kernel(const DevModel
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
+// Phase B over slices (one robot, heuristic default policy): a warp takes
+// one slice at a time (claims in batches as for chunks), lane l its items
+// l, l + 32, l + 64 and l + 96. A slice is one child's: the same slot and
+// job, and in a job whose scenarios share the robot's cell (a tree node's)
+// the same position and candidate set. Then one trajectory
+// (rollout_oneK) gives all of a lane's values, u0's per-rock terms come from
+// lane i as in rs_rollout_values, and the child's sums take one warp sum
+// each. A slice whose items differ in position or candidate set takes
+// rs_rollout_values 32 items at a time. 64 registers (two 512-thread CTAs
+// per SM) hold a lane's four items.
+constexpr int kSliceLanes = kSliceItems / 32;
+__global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevModel* __restrict__ gm, DevWork* work,
+                                                                   const dsp_leaf_job* __restrict__ jobs,
+                                                                   Items<1> items, Slices sl,
+                                                                   unsigned int* slice_head, uint32_t plan_step) {
+  __shared__ RSShared c;
+  extern __shared__ __align__(16) uint16_t rs_keys[];
+  load_rs_consts(c, gm);
+  load_rs_keys(rs_keys, gm);
+  __syncthreads();
+  RSModel<1> M = make_rs<1>(gm, &c, plan_step);
+  M.nkey = rs_keys;
+  const int lane = threadIdx.x & 31;
+  const unsigned int ns = min(*sl.count, sl.cap);
+  unsigned long long steps = 0;
+  __shared__ ChunkClaims claims[kMaxWarpsB];
+  ChunkClaims& cc = claims[threadIdx.x >> 5];
+  if (lane == 0) cc.left = 0;
+  while (true) {
+    unsigned int si = 0;
+    if (lane == 0) si = cc.take(slice_head);
+    si = __shfl_sync(0xFFFFFFFFu, si, 0);
+    if (si >= ns) break;
+    const uint2 d = sl.list[si];
+    const long long st = (long long)d.x;
+    const int cnt = (int)d.y;
+    // (a slice list that overflowed its capacity has flagged the status word;
+    // no entry outside the item list is read)
+    if (cnt < 1 || cnt > kSliceItems || st + cnt > items.total) continue;
+    bool ok[kSliceLanes];
+    uint32_t pos[kSliceLanes], good[kSliceLanes], cand[kSliceLanes], meta[kSliceLanes], job[kSliceLanes];
+#pragma unroll
+    for (int k = 0; k < kSliceLanes; ++k) {
+      ok[k] = lane + 32 * k < cnt;
+      RSS s;
+      s.pos[0] = 0u;
+      s.good = 0u;
+      cand[k] = meta[k] = job[k] = 0u;
+      if (ok[k]) items.get_compact((size_t)(st + lane + 32 * k), s, cand[k], meta[k], job[k]);
+      pos[k] = s.pos[0];
+      good[k] = s.good;
+    }
+    const uint32_t p0 = __shfl_sync(0xFFFFFFFFu, pos[0], 0), c0 = __shfl_sync(0xFFFFFFFFu, cand[0], 0);
+    const uint32_t m0 = __shfl_sync(0xFFFFFFFFu, meta[0], 0), j0 = __shfl_sync(0xFFFFFFFFu, job[0], 0);
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < kSliceLanes; ++k)
+      same = same && (!ok[k] || (pos[k] == p0 && cand[k] == c0 && meta[k] == m0 && job[k] == j0));
+    if (__all_sync(0xFFFFFFFFu, same)) {
+      int64_t* usum = jobs[j0].u_sum;
+      int64_t* lsum = jobs[j0].l_sum;
+      const uint32_t slot = m0 & 0xFFFFFFu;
+      const int depth = (int)(m0 >> 24);
+      float u[kSliceLanes], v[kSliceLanes];
+#pragma unroll
+      for (int k = 0; k < kSliceLanes; ++k) u[k] = v[k] = 0.0f;
+      if (!rs_terminal<1>(p0, 0u)) {
+        if (depth + 1 >= M.D) {
+          RSS s;
+          s.pos[0] = p0;
+          s.pos[1] = 0u;
+          const float tl = M.tail(s);
+#pragma unroll
+          for (int k = 0; k < kSliceLanes; ++k) u[k] = tl;
+        } else {
+          const float w = upper_term<1>(M, p0, 0u, lane);
+          for (int i = 0; i < M.m; ++i) {
+            const float wi = __shfl_sync(0xFFFFFFFFu, w, i);
+#pragma unroll
+            for (int k = 0; k < kSliceLanes; ++k)
+              if ((good[k] >> i) & 1u) u[k] = __fadd_rn(u[k], wi);
+          }
+#pragma unroll
+          for (int k = 0; k < kSliceLanes; ++k) u[k] = upper_exits<1>(M, p0, 0u, u[k]);
+        }
+        int live = 0;
+#pragma unroll
+        for (int k = 0; k < kSliceLanes; ++k) live += ok[k] ? 1 : 0;
+        M.rollout_oneK<kSliceLanes>(p0, good, c0, depth + 1, v, (unsigned long long)live, steps);
+      }
+      long long fu = 0, fl = 0;
+#pragma unroll
+      for (int k = 0; k < kSliceLanes; ++k)
+        if (ok[k]) {
+          fu += to_fixed(u[k]);
+          fl += to_fixed(v[k]);
+        }
+      fu = warp_sum64(fu);
+      fl = warp_sum64(fl);
+      if (lane == 0) {
+        sum_add(usum + slot, fu);
+        sum_add(lsum + slot, fl);
+      }
+      continue;
+    }
+#pragma unroll
+    for (int k = 0; k < kSliceLanes; ++k) {
+      if (32 * k >= cnt) break;
+      RSS s;
+      s.pos[0] = pos[k];
+      s.pos[1] = 0u;
+      s.good = good[k];
+      s.sampled = 0u;
+      s.scen = 0u;
+      rs_rollout_values<1>(M, jobs, ok[k], s, cand[k], meta[k], job[k], steps);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
+  if (lane == 0 && steps) atomicAdd(&work->steps, steps);
+}
+
 // Phase B in block form for one chunk u (one robot, heuristic default
 // policy): the 32 grouped positions [32 b, 32 b + 32) of action a of job j =
 // chunk_job[u], where u - unit_base[j] = a * ceil(n / 32) + b. Each lane
@@ -1218,11 +1367,15 @@ template <int R>
 cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st,
-                             int warps_a, int ctas_b, LeafBlocks lb) {
+                             int warps_a, int ctas_b, LeafBlocks lb, Slices sl) {
   // block form (lb.leaf set; one robot, heuristic policy): no item list,
   // total_items counts the 32-position blocks
   const bool blocks = lb.leaf != nullptr;
   Items<R> items{blocks ? nullptr : item_buf, blocks ? 0 : total_items, policy != nullptr && R == 1};
+  // slices: one robot's heuristic rollouts over the item list; phase A counts
+  // them in counters[2]
+  if (R != 1 || blocks || policy != nullptr) sl = Slices{};
+  if (sl.list != nullptr) sl.count = counters + 2;
   // Each warp expands whole actions: as many warps as give every warp the
   // same number of a job's actions (20 actions: 10 warps of 2; 400: 16 of
   // 25). One robot with at least two jobs per CTA slot: at most five warps
@@ -1247,7 +1400,7 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
   const int splits = R == 2 ? std::max(1, num_actions / 80) : 1;
   grid_a = std::max(1, std::min(n_jobs * splits, std::max(1, per_sm_a) * num_sms));
   rs_group_kernel<R><<<grid_a, block_a, 0, st>>>(gm, work, jobs, blocks ? nullptr : item_base, order, n_jobs,
-                                                  counters, plan_step, items, splits, lb);
+                                                  counters, plan_step, items, splits, lb, sl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (policy != nullptr && R == 1)
@@ -1262,6 +1415,17 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
       const int grid = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm) * num_sms));
       rs_rollout_blocks_kernel<<<grid, block_b, kb, st>>>(gm, work, jobs, n_jobs, lb, (unsigned int)total_items,
                                                            counters + 1, plan_step);
+      return cudaGetLastError();
+    }
+  }
+  if constexpr (R == 1) {
+    if (sl.list != nullptr) {
+      const size_t kb = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words);
+      int per_sm = occupancy_cached(rs_rollout_slices_kernel, block_b, kb);
+      if (ctas_b > 0) per_sm = std::min(per_sm, ctas_b);
+      const long long want = ((long long)sl.cap + block_b / 32 - 1) / (block_b / 32);
+      const int grid = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm) * num_sms));
+      rs_rollout_slices_kernel<<<grid, block_b, kb, st>>>(gm, work, jobs, items, sl, counters + 1, plan_step);
       return cudaGetLastError();
     }
   }
@@ -1560,6 +1724,8 @@ cudaError_t rs_set_key_smem(int robots, int key_words) {
     cudaError_t e = cudaFuncSetAttribute(rs_rollout_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)keys);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rs_rollout_slices_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)keys);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(rs_rollout_items_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(keys + rs_stage_bytes<1>(512)));
   }
@@ -1570,14 +1736,15 @@ cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, in
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf, unsigned int* counters, uint32_t plan_step,
                              int num_sms, int block_b, const void* policy, cudaStream_t st, int warps_a, int ctas_b,
-                             const LeafBlocks* blocks) {
+                             const LeafBlocks* blocks, const Slices* slices) {
   const LeafBlocks lb = (blocks != nullptr && robots == 1 && policy == nullptr) ? *blocks : LeafBlocks{};
   if (blocks != nullptr && lb.leaf == nullptr) return cudaErrorInvalidValue;  // block form: one robot, heuristic
+  const Slices sl = slices != nullptr ? *slices : Slices{};
   if (robots == 1)
     return launch_two_phase<1>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items,
-                               item_buf, counters, plan_step, num_sms, block_b, policy, st, warps_a, ctas_b, lb);
+                               item_buf, counters, plan_step, num_sms, block_b, policy, st, warps_a, ctas_b, lb, sl);
   return launch_two_phase<2>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items, item_buf,
-                             counters, plan_step, num_sms, block_b, nullptr, st, warps_a, ctas_b, lb);
+                             counters, plan_step, num_sms, block_b, nullptr, st, warps_a, ctas_b, lb, sl);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,

@@ -20,6 +20,18 @@ struct LeafBlocks {
   int* chunk_job = nullptr;
 };
 
+// Rock Sample, one robot, heuristic default policy, item list: phase A lists
+// each child's items as slices of at most kSliceItems consecutive items
+// (start, count) at list[0 .. *count), and phase B takes slices instead of
+// fixed chunks, so that the items it rolls out together always belong to one
+// child (one trajectory for all of them). list == nullptr: chunks.
+struct Slices {
+  uint2* list = nullptr;
+  unsigned int* count = nullptr;
+  unsigned int cap = 0;
+};
+constexpr int kSliceItems = 128;
+
 // Rock Sample: words per rollout item of the two-phase expansion.
 int rs_item_fields(int robots, bool full);  // words per rollout item (full: learned-policy layout)
 // Rock Sample two-phase expansion: phase A over n_jobs jobs (item_base[j] =
@@ -39,7 +51,7 @@ cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, in
                              long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
                              const void* policy, cudaStream_t st, int warps_a = 0, int ctas_b = 0,
-                             const LeafBlocks* blocks = nullptr);
+                             const LeafBlocks* blocks = nullptr, const Slices* slices = nullptr);
 // Learned-policy rollout phase over the item list (one robot).
 cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs,
                                         uint32_t* item_buf, long long total_items, unsigned int* counter,

@@ -90,9 +90,14 @@ struct ExpandPlan {
   bool blocks = false;
   std::vector<long long> unit_base, scen_base;
   long long total_blocks = 0, total_scen = 0;
+  // Rock Sample, one robot, heuristic policy, item list: the rollout phase
+  // takes each child's items in slices; at most slice_cap of them
+  bool slices = false;
+  long long slice_cap = 0;
 };
-// allow_blocks: the block form may be planned (dsp_expand_leaves); the
-// no-allocation entry point and the queue's validation plan items.
+// allow_blocks: the block form or slices may be planned (dsp_expand_leaves,
+// which allocates their buffers); the no-allocation entry point and the
+// queue's validation plan items in chunks.
 dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, ExpandPlan& plan,
                       bool allow_blocks = false);
 dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, const ExpandPlan& plan,

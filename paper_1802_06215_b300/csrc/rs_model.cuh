@@ -503,6 +503,60 @@ struct RSModel {
     }
   }
 
+  // rollout_one for K scenarios of one child (the same position, candidate
+  // set and depth, so the same trajectory); each scenario adds its own
+  // reward at each Sample with the operations and in the order rollout_one
+  // uses. `live` marks the scenarios whose steps are counted.
+  template <int K>
+  __device__ __forceinline__ void rollout_oneK(uint32_t p0, const uint32_t (&good)[K], uint32_t cand, int t0,
+                                               float (&v)[K], unsigned long long steps_each,
+                                               unsigned long long& steps) const {
+    int x = (int)(p0 & 0xFFu), y = (int)((p0 >> 8) & 0xFFu);
+    bool ex = (p0 >> 16) & 1u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0.0f;
+    int t = t0;
+    if (!ex) {
+      while (t < D) {
+        if (cand == 0) {
+          const int ke = min(n - 1 - x, D - t);
+          x += ke;
+          t += ke;
+          if (t < D) {
+            const float e = __fmul_rn(sh->G[t - t0], 10.0f);
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = __fadd_rn(v[k], e);
+            ex = true;
+            ++t;
+          }
+          break;
+        }
+        int tx, ty;
+        uint32_t tbit;
+        target(x, y, cand, tx, ty, tbit);
+        const int sx = tx > x ? 1 : -1, sy = ty > y ? 1 : -1;
+        const int kx = min(abs(tx - x), D - t);
+        x += sx * kx;
+        t += kx;
+        const int ky = min(abs(ty - y), D - t);
+        y += sy * ky;
+        t += ky;
+        if (t >= D) break;
+        const float g = __fmul_rn(sh->G[t - t0], 10.0f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = __fadd_rn(v[k], (good[k] & tbit) ? g : -g);
+        cand &= ~tbit;
+        ++t;
+      }
+    }
+    steps += steps_each * (unsigned long long)(t - t0);
+    if (!ex) {
+      const float tl = __fmul_rn(sh->G[D - t0], __fmul_rn(10.0f, sh->G[n - 1 - x]));
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = __fadd_rn(v[k], tl);
+    }
+  }
+
   // rollout_one for two scenarios of one child: the same position and
   // candidate set, so the same trajectory (the heuristic's moves read no
   // rock state); each scenario adds its own reward at each Sample, with the
