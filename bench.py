@@ -649,7 +649,8 @@ def measure(args, name, rank, world, dist, local, headline=True):
                 "peak_source": "derived: 148 SMs x 128 lanes x 2032 MHz (one 32-bit op per lane per clock)",
                 "probe_tops": probe_tops, "ops_per_scenario_step": ops_per_step,
                 "kernel": {"rs": "rs_group_kernel + " + ("rs_rollout_blocks_kernel" if blocks else
-                                                          "rs_rollout_items_kernel") + " (one expansion)",
+                                                          ("rs_rollout_slices_kernel" if cfg.kind == inputs.GRID
+                                                           else "rs_rollout_items_kernel")) + " (one expansion)",
                            "car": "car_expand_kernel",
                            "nav": "nav_group_kernel + nav_rollout_items_kernel (one expansion)"}[kind],
                 "kernel_ms_per_launch": avg_kernel_s * 1000.0,
