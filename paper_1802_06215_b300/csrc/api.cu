@@ -540,7 +540,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
                   ? align256(sizeof(uint32_t) * 3 * (size_t)plan.total_scen) + sizeof(int) * (size_t)plan.total_blocks
                   : sizeof(uint32_t) * (size_t)rs_item_fields(h->robots, m->policy_on) * (size_t)plan.total_items;
   const bool slices = !by_unit && plan.slices;
-  const size_t sb = slices ? sizeof(uint2) * (size_t)plan.slice_cap : 0;
+  const size_t sb = slices ? 2 * sizeof(uint4) * (size_t)plan.slice_cap : 0;
   size_t total = align256(jb) + align256(ub) + 256 + align256(ib) + sb;
   unsigned char* buf = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync((void**)&buf, total, m->pool, st);
@@ -619,7 +619,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
       }
       Slices sl;
       if (slices) {
-        sl.list = (uint2*)((unsigned char*)items + align256(ib));
+        sl.list = (uint4*)((unsigned char*)items + align256(ib));
         sl.cap = (unsigned int)plan.slice_cap;
       }
       e = launch_rs_expand(m->dmodel, h->robots, h->num_actions, rs_key_words(h), m->dwork, djobs,

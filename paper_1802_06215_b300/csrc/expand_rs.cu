@@ -116,10 +116,15 @@ __device__ __forceinline__ void gather_update(RSGroupSmem& S, const RSModel<R>& 
 
 // An action's slices for the rollout phase: each child's grouped positions
 // (count cnt[c] from offset off[c]) in runs of at most kSliceItems items.
-// Called by one lane; one atomic per action takes the slots.
+// Called by one lane; one atomic per action takes the slots. `shared`: the
+// job's scenarios share the robot's cell and sampled mask, so every item of
+// child c has the position pos, the candidate mask pm_z[c % 3] & ~sampled
+// and the child's depth and slot, which the slice carries.
 template <int kC>
 __device__ __forceinline__ void put_slices(const Slices& sl, long long ibase, int a, int n, const int (&cnt)[kC],
-                                           const int (&off)[kC], DevWork* work) {
+                                           const int (&off)[kC], const int (&cid)[kC], int cap, int depth, int j,
+                                           bool shared, uint32_t pos, const uint32_t (&pm_z)[3], uint32_t sampled,
+                                           DevWork* work) {
   if (sl.list == nullptr) return;
   int ns = 0;
 #pragma unroll
@@ -132,9 +137,16 @@ __device__ __forceinline__ void put_slices(const Slices& sl, long long ibase, in
   }
   const long long first = ibase + (long long)a * n;
 #pragma unroll
-  for (int c = 0; c < kC; ++c)
-    for (int s = 0; s < cnt[c]; s += kSliceItems)
-      sl.list[k++] = make_uint2((uint32_t)(first + off[c] + s), (uint32_t)min(kSliceItems, cnt[c] - s));
+  for (int c = 0; c < kC; ++c) {
+    const uint32_t meta = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(cid[c], cap - 1));
+    const uint32_t cand = pm_z[c % 3] & ~sampled;
+    for (int s = 0; s < cnt[c]; s += kSliceItems) {
+      const uint32_t count = (uint32_t)min(kSliceItems, cnt[c] - s) | (shared ? kSliceShared : 0u);
+      sl.list[2 * k] = make_uint4((uint32_t)(first + off[c] + s), count, pos, cand);
+      sl.list[2 * k + 1] = make_uint4(meta, (uint32_t)j, 0u, 0u);
+      ++k;
+    }
+  }
 }
 
 // Phase A for one robot, where an action's scenarios fall into at most a few
@@ -281,7 +293,6 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
       J.child_count[a] = nch;
       if (nch > cap) report(work, kStatusOverflow);
       if (nch <= cap) J.child_off[(size_t)a * (cap + 1) + nch] = n;
-      put_slices<kC>(sl, ibase, a, n, cnt, off, work);
 #pragma unroll
       for (int c = 0; c < kC; ++c)
         if (cnt[c] > 0 && cid[c] < cap) {
@@ -303,6 +314,16 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
       pm_z[1] = cg > 0 ? (pm_job | (1u << i)) : (pm_job & ~(1u << i));
       pm_z[2] = cb > 0 ? (pm_job | (1u << i)) : (pm_job & ~(1u << i));
     }
+    // a shared-position job's children: the state after the step is the job's
+    // (a move or a terminal leaf: rep_next; a Sense: as it was; a Sample on a
+    // rock: that rock sampled, and bad in every scenario), so with a slice
+    // list the items hold only the good masks and the slices the rest
+    const int rock_here = S.c.cell_rock[(int)((rep.pos[0] >> 8) & 0xFFu) * M.n + (int)(rep.pos[0] & 0xFFu)];
+    const uint32_t sample_bit = (uniform && aa == 4 && !rep_term && rock_here != 0xFF) ? (1u << rock_here) : 0u;
+    const bool slim = uniform && sl.list != nullptr && !items.full;
+    if (lane == 0)
+      put_slices<kC>(sl, ibase, a, n, cnt, off, cid, cap, depth, j, slim, same_step ? rep_next.pos[0] : rep.pos[0],
+                     pm_z, same_step ? rep_next.sampled : (rep.sampled | sample_bit), work);
     // grouped positions and rollout items
     int run[kC];
 #pragma unroll
@@ -326,7 +347,9 @@ __device__ void rs1_group_job(RSGroupSmem& S, const RSModel<1>& M, int j, long l
         }
       }
       if (p < n) J.perm[(size_t)a * n + q] = (uint16_t)p;
-      if (p < n && !blocks) {
+      if (p < n && !blocks && slim) {
+        items.put_good((size_t)(ibase + (long long)a * n + q), S.leaf[2][p] & ~sample_bit);
+      } else if (p < n && !blocks) {
         RSS s;
         s.pos[0] = S.leaf[0][p];
         s.pos[1] = 0u;
@@ -441,7 +464,8 @@ __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, 
       J.child_count[a] = nch;
       if (nch > cap) report(work, kStatusOverflow);
       if (nch <= cap) J.child_off[(size_t)a * (cap + 1) + nch] = n;
-      put_slices<kC>(sl, ibase, a, n, cnt, off, work);
+      const uint32_t no_pm[3] = {0u, 0u, 0u};
+      put_slices<kC>(sl, ibase, a, n, cnt, off, cid, cap, depth, j, false, 0u, no_pm, 0u, work);
 #pragma unroll
       for (int c = 0; c < kC; ++c)
         if (cnt[c] > 0 && cid[c] < cap) {
@@ -1070,7 +1094,8 @@ __global__ void __launch_bounds__(512, 3) rs_rollout_items_kernel(const DevModel
 // one slice at a time (claims in batches as for chunks), lane l its items
 // l, l + 32, l + 64 and l + 96. A slice is one child's: the same slot and
 // job, and in a job whose scenarios share the robot's cell (a tree node's)
-// the same position and candidate set. Then one trajectory
+// the same position and candidate set, which the slice then carries (its
+// items hold only their good masks). Then one trajectory
 // (rollout_oneK) gives all of a lane's values, u0's per-rock terms come from
 // lane i as in rs_rollout_values, and the child's sums take one warp sum
 // each. A slice whose items differ in position or candidate set takes
@@ -1099,32 +1124,49 @@ __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevMode
     if (lane == 0) si = cc.take(slice_head);
     si = __shfl_sync(0xFFFFFFFFu, si, 0);
     if (si >= ns) break;
-    const uint2 d = sl.list[si];
-    const long long st = (long long)d.x;
-    const int cnt = (int)d.y;
+    const uint4 d0 = sl.list[2 * si], d1 = sl.list[2 * si + 1];
+    const long long st = (long long)d0.x;
+    const int cnt = (int)(d0.y & 0xFFFFu);
+    const bool shared = (d0.y & kSliceShared) != 0u;
     // (a slice list that overflowed its capacity has flagged the status word;
     // no entry outside the item list is read)
     if (cnt < 1 || cnt > kSliceItems || st + cnt > items.total) continue;
     bool ok[kSliceLanes];
     uint32_t pos[kSliceLanes], good[kSliceLanes], cand[kSliceLanes], meta[kSliceLanes], job[kSliceLanes];
+    uint32_t p0 = d0.z, c0 = d0.w, m0 = d1.x, j0 = d1.y;
+    if (shared) {
+      // the child's state is the slice's; the items hold their good masks
 #pragma unroll
-    for (int k = 0; k < kSliceLanes; ++k) {
-      ok[k] = lane + 32 * k < cnt;
-      RSS s;
-      s.pos[0] = 0u;
-      s.good = 0u;
-      cand[k] = meta[k] = job[k] = 0u;
-      if (ok[k]) items.get_compact((size_t)(st + lane + 32 * k), s, cand[k], meta[k], job[k]);
-      pos[k] = s.pos[0];
-      good[k] = s.good;
+      for (int k = 0; k < kSliceLanes; ++k) {
+        ok[k] = lane + 32 * k < cnt;
+        good[k] = ok[k] ? items.f(1)[st + lane + 32 * k] : 0u;
+        pos[k] = p0;
+        cand[k] = c0;
+        meta[k] = m0;
+        job[k] = j0;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSliceLanes; ++k) {
+        ok[k] = lane + 32 * k < cnt;
+        RSS s;
+        s.pos[0] = 0u;
+        s.good = 0u;
+        cand[k] = meta[k] = job[k] = 0u;
+        if (ok[k]) items.get_compact((size_t)(st + lane + 32 * k), s, cand[k], meta[k], job[k]);
+        pos[k] = s.pos[0];
+        good[k] = s.good;
+      }
+      p0 = __shfl_sync(0xFFFFFFFFu, pos[0], 0);
+      c0 = __shfl_sync(0xFFFFFFFFu, cand[0], 0);
+      m0 = __shfl_sync(0xFFFFFFFFu, meta[0], 0);
+      j0 = __shfl_sync(0xFFFFFFFFu, job[0], 0);
     }
-    const uint32_t p0 = __shfl_sync(0xFFFFFFFFu, pos[0], 0), c0 = __shfl_sync(0xFFFFFFFFu, cand[0], 0);
-    const uint32_t m0 = __shfl_sync(0xFFFFFFFFu, meta[0], 0), j0 = __shfl_sync(0xFFFFFFFFu, job[0], 0);
     bool same = true;
 #pragma unroll
     for (int k = 0; k < kSliceLanes; ++k)
       same = same && (!ok[k] || (pos[k] == p0 && cand[k] == c0 && meta[k] == m0 && job[k] == j0));
-    if (__all_sync(0xFFFFFFFFu, same)) {
+    if (shared || __all_sync(0xFFFFFFFFu, same)) {
       int64_t* usum = jobs[j0].u_sum;
       int64_t* lsum = jobs[j0].l_sum;
       const uint32_t slot = m0 & 0xFFFFFFu;

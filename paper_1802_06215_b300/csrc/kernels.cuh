@@ -21,16 +21,21 @@ struct LeafBlocks {
 };
 
 // Rock Sample, one robot, heuristic default policy, item list: phase A lists
-// each child's items as slices of at most kSliceItems consecutive items
-// (start, count) at list[0 .. *count), and phase B takes slices instead of
-// fixed chunks, so that the items it rolls out together always belong to one
-// child (one trajectory for all of them). list == nullptr: chunks.
+// each child's items as slices of at most kSliceItems consecutive items at
+// list[2 i], list[2 i + 1] for i < *count, and phase B takes slices instead
+// of fixed chunks, so that the items it rolls out together always belong to
+// one child (one trajectory for all of them). A slice is (first item, count
+// | kSliceShared, position, candidate mask) (depth << 24 | slot, job, 0, 0).
+// With kSliceShared (a job whose scenarios share the robot's cell and
+// sampled mask) the child's items hold only their good masks and the slice
+// holds the rest; else the items hold every field. list == nullptr: chunks.
 struct Slices {
-  uint2* list = nullptr;
+  uint4* list = nullptr;
   unsigned int* count = nullptr;
   unsigned int cap = 0;
 };
 constexpr int kSliceItems = 128;
+constexpr uint32_t kSliceShared = 1u << 31;
 
 // Rock Sample: words per rollout item of the two-phase expansion.
 int rs_item_fields(int robots, bool full);  // words per rollout item (full: learned-policy layout)

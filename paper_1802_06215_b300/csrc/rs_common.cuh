@@ -67,6 +67,8 @@ struct Items {
     f(k++)[it] = meta;
     f(k)[it] = job;
   }
+  // a compact item's good mask alone (a child whose other fields its slice holds)
+  __device__ __forceinline__ void put_good(size_t it, uint32_t good) const { f(R == 2 ? 2 : 1)[it] = good; }
   // a compact item: the state for the heuristic rollout (sampled rocks are
   // out of the candidate mask, which takes the positive-counter mask's place)
   __device__ __forceinline__ void get_compact(size_t it, RSS& s, uint32_t& cand, uint32_t& meta, uint32_t& job) const {
