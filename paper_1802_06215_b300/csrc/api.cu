@@ -401,7 +401,8 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
   plan.total_items = plan.total_blocks = plan.total_scen = plan.slice_cap = 0;
   plan.blocks = allow_blocks && h->kind != DSP_MODEL_CAR && h->kind != DSP_MODEL_NAV && h->robots == 1 &&
                 !m->policy_on && m->tune_rs_form == 1;
-  plan.slices = allow_blocks && h->kind == DSP_MODEL_GRID && !m->policy_on && !plan.blocks;
+  plan.slices = allow_blocks && (h->kind == DSP_MODEL_GRID || h->kind == DSP_MODEL_MULTIGRID) && !m->policy_on &&
+                !plan.blocks;
   for (int j = 0; j < n_jobs; ++j) {
     const dsp_leaf_job& J = jobs[j];
     const int max_n = h->kind == DSP_MODEL_GRID ? kMaxScenLarge : kMaxScen;
@@ -435,7 +436,12 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
       plan.total_items += (long long)J.n_scen * J.n_actions;
       // an action's children (at most 6 observation codes) in runs of at
       // most kSliceItems
-      if (plan.slices) plan.slice_cap += (long long)J.n_actions * ((J.n_scen + kSliceItems - 1) / kSliceItems + 6);
+      if (plan.slices) {
+        // one robot: at most 6 observation codes an action, slices of 128;
+        // two robots: 18 codes, slices of 64
+        const int len = h->robots == 1 ? kSliceItems : kSliceItemsTwo, codes = h->robots == 1 ? 6 : 18;
+        plan.slice_cap += (long long)J.n_actions * ((J.n_scen + len - 1) / len + codes);
+      }
     }
   }
   if (plan.slice_cap >= (1LL << 31)) plan.slices = false;

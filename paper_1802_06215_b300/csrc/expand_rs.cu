@@ -533,11 +533,21 @@ __device__ void rs1_group_job_large(RSGroupSmem& S, const RSModel<1>& M, int j, 
 // their leader updates the code's row; the warp's own __syncwarp orders the
 // updates. The result is identical to the general grouping.
 __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long long ibase, int a_begin, int a_end,
-                              bool first_unit, Items<2> items, DevWork* work, unsigned long long& steps) {
+                              bool first_unit, Items<2> items, DevWork* work, unsigned long long& steps,
+                              const Slices& sl) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   gather_update<2>(S, M, first_unit, steps);
   const dsp_leaf_job& J = S.J;
-  const int n = J.n_scen, depth = J.depth, A = J.n_actions, cap = J.child_cap;
+  const int n = J.n_scen, depth = J.depth, cap = J.child_cap;
+  // with a slice list: whether the job's scenarios share both robots' cells
+  // and the sampled mask (a tree node's do), so that each child's items share
+  // their state after the step (the slice holds it; the items their good
+  // masks)
+  bool same = true;
+  if (sl.list != nullptr)
+    for (int p = tid; p < n; p += (int)blockDim.x)
+      same = same && S.leaf[0][p] == S.leaf[0][0] && S.leaf[1][p] == S.leaf[1][0] && S.leaf[3][p] == S.leaf[3][0];
+  const bool slim = sl.list != nullptr && !items.full && __syncthreads_and(same ? 1 : 0) != 0;
   const uint32_t lt = lanemask_lt();
   uint8_t* codes = S.code1[warp];
   int* cnt = S.wcnt[warp];
@@ -624,6 +634,51 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
       for (int k = 0; k < 8; ++k) h[k] = hw[k];
       M.observe(h, pm_obs, aa, (uint64_t)lane);
     }
+    // the children's slices: lane c < kCodes takes code c's, after a scan of
+    // the codes' slice counts; one atomic per action reserves them. A shared
+    // job's state after the step is scenario 0's (both robots' moves and
+    // Samples applied; a Sense leaves it as it was); `clear` holds the rocks
+    // the step sampled, bad in every scenario afterwards.
+    uint32_t clear = 0u;
+    if (sl.list != nullptr) {
+      RSS nxt;
+      nxt.pos[0] = S.leaf[0][0];
+      nxt.pos[1] = S.leaf[1][0];
+      nxt.good = S.leaf[2][0];
+      nxt.sampled = S.leaf[3][0];
+      nxt.scen = S.leaf[4][0];
+      int zz;
+      if (a0 < 5) M.robot_step(nxt, 0, a0, depth, zz);
+      if (a1 < 5) M.robot_step(nxt, 1, a1, depth, zz);
+      clear = nxt.sampled & ~S.leaf[3][0];
+      const int mc = lane < kCodes ? cnt[lane] : 0;
+      const int ns = (mc + kSliceItemsTwo - 1) / kSliceItemsTwo;
+      int incl = ns;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      unsigned int base = 0u;
+      if (lane == 0 && total > 0) base = atomicAdd(sl.count, (unsigned int)total);
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      const uint32_t pmc = __shfl_sync(0xFFFFFFFFu, pm_obs, lane % 9);
+      if (total > 0 && base + (unsigned int)total > sl.cap) {
+        if (lane == 0) report(work, kStatusOverflow);
+      } else if (ns > 0) {
+        unsigned int k = base + (unsigned int)(incl - ns);
+        const uint32_t meta = ((uint32_t)depth << 24) | (uint32_t)(a * cap + min(cid[lane], cap - 1));
+        const uint32_t cand = pmc & ~nxt.sampled;
+        const long long first_it = ibase + (long long)a * n + off[lane];
+        for (int s0 = 0; s0 < mc; s0 += kSliceItemsTwo) {
+          const uint32_t count = (uint32_t)min(kSliceItemsTwo, mc - s0) | (slim ? kSliceShared : 0u);
+          sl.list[2 * k] = make_uint4((uint32_t)(first_it + s0), count, nxt.pos[0], cand);
+          sl.list[2 * k + 1] = make_uint4(meta, (uint32_t)j, nxt.pos[1], 0u);
+          ++k;
+        }
+      }
+    }
     // pass 2: grouped positions and rollout items; only Sense draws random
     // numbers and it leaves the state as it was, so each robot's other
     // actions are simply applied again
@@ -638,6 +693,15 @@ __device__ void rs2_group_job(RSGroupSmem& S, const RSModel<2>& M, int j, long l
       }
       __syncwarp();
       if (p < n && lane == __ffs(peers) - 1) run[code] += __popc(peers);
+      if (slim) {
+        // the item's good mask alone (its slice holds the rest)
+        if (p < n) {
+          J.perm[(size_t)a * n + q] = (uint16_t)p;
+          items.put_good((size_t)(ibase + (long long)a * n + q), S.leaf[2][p] & ~clear);
+        }
+        __syncwarp();
+        continue;
+      }
       RSS s;
       if (p < n) {
         s.pos[0] = S.leaf[0][p];
@@ -675,7 +739,7 @@ __device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, i
     else
       rs1_group_job(S, M, j, ibase, items, work, steps, lb, sl);
   } else
-    rs2_group_job(S, M, j, ibase, a_begin, a_end, first, items, work, steps);
+    rs2_group_job(S, M, j, ibase, a_begin, a_end, first, items, work, steps, sl);
 }
 
 template <int R>
@@ -1090,28 +1154,32 @@ __global__ void __launch_bounds__(512, 3) rs_rollout_items_kernel(const DevModel
   if (lane == 0 && steps) atomicAdd(&work->steps, steps);
 }
 
-// Phase B over slices (one robot, heuristic default policy): a warp takes
-// one slice at a time (claims in batches as for chunks), lane l its items
-// l, l + 32, l + 64 and l + 96. A slice is one child's: the same slot and
-// job, and in a job whose scenarios share the robot's cell (a tree node's)
-// the same position and candidate set, which the slice then carries (its
-// items hold only their good masks). Then one trajectory
-// (rollout_oneK) gives all of a lane's values, u0's per-rock terms come from
-// lane i as in rs_rollout_values, and the child's sums take one warp sum
-// each. A slice whose items differ in position or candidate set takes
-// rs_rollout_values 32 items at a time. 64 registers (two 512-thread CTAs
-// per SM) hold a lane's four items.
-constexpr int kSliceLanes = kSliceItems / 32;
+// Phase B over slices (heuristic default policy): a warp takes one slice at
+// a time (claims in batches as for chunks), lane l its items l, l + 32, ...
+// (four a lane for one robot, two for two). A slice is one child's: the same
+// slot and job, and in a job whose scenarios share the robots' cells (a tree
+// node's) the same positions and candidate set, which the slice then
+// carries (its items hold only their good masks). Then one trajectory
+// (rollout_oneK, or rollout_twoK's joint one) gives all of a lane's values,
+// u0's per-rock terms come from lane i as in rs_rollout_values, and the
+// child's sums take one warp sum each. A slice whose items differ in
+// position or candidate set takes rs_rollout_values 32 items at a time. 64
+// registers (two 512-thread CTAs per SM) hold a lane's items.
+template <int R>
+constexpr int kSliceLen = R == 1 ? kSliceItems : kSliceItemsTwo;
+template <int R>
 __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                                    const dsp_leaf_job* __restrict__ jobs,
-                                                                   Items<1> items, Slices sl,
+                                                                   Items<R> items, Slices sl,
                                                                    unsigned int* slice_head, uint32_t plan_step) {
+  constexpr int kSliceLanes = kSliceLen<R> / 32;
+  constexpr int kGood = R == 2 ? 2 : 1;  // the good field of a compact item
   __shared__ RSShared c;
   extern __shared__ __align__(16) uint16_t rs_keys[];
   load_rs_consts(c, gm);
   load_rs_keys(rs_keys, gm);
   __syncthreads();
-  RSModel<1> M = make_rs<1>(gm, &c, plan_step);
+  RSModel<R> M = make_rs<R>(gm, &c, plan_step);
   M.nkey = rs_keys;
   const int lane = threadIdx.x & 31;
   const unsigned int ns = min(*sl.count, sl.cap);
@@ -1130,17 +1198,19 @@ __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevMode
     const bool shared = (d0.y & kSliceShared) != 0u;
     // (a slice list that overflowed its capacity has flagged the status word;
     // no entry outside the item list is read)
-    if (cnt < 1 || cnt > kSliceItems || st + cnt > items.total) continue;
+    if (cnt < 1 || cnt > kSliceLen<R> || st + cnt > items.total) continue;
     bool ok[kSliceLanes];
-    uint32_t pos[kSliceLanes], good[kSliceLanes], cand[kSliceLanes], meta[kSliceLanes], job[kSliceLanes];
-    uint32_t p0 = d0.z, c0 = d0.w, m0 = d1.x, j0 = d1.y;
+    uint32_t pos[kSliceLanes], pos1[kSliceLanes], good[kSliceLanes], cand[kSliceLanes], meta[kSliceLanes],
+        job[kSliceLanes];
+    uint32_t p0 = d0.z, q1 = d1.z, c0 = d0.w, m0 = d1.x, j0 = d1.y;
     if (shared) {
       // the child's state is the slice's; the items hold their good masks
 #pragma unroll
       for (int k = 0; k < kSliceLanes; ++k) {
         ok[k] = lane + 32 * k < cnt;
-        good[k] = ok[k] ? items.f(1)[st + lane + 32 * k] : 0u;
+        good[k] = ok[k] ? items.f(kGood)[st + lane + 32 * k] : 0u;
         pos[k] = p0;
+        pos1[k] = q1;
         cand[k] = c0;
         meta[k] = m0;
         job[k] = j0;
@@ -1150,14 +1220,16 @@ __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevMode
       for (int k = 0; k < kSliceLanes; ++k) {
         ok[k] = lane + 32 * k < cnt;
         RSS s;
-        s.pos[0] = 0u;
+        s.pos[0] = s.pos[1] = 0u;
         s.good = 0u;
         cand[k] = meta[k] = job[k] = 0u;
         if (ok[k]) items.get_compact((size_t)(st + lane + 32 * k), s, cand[k], meta[k], job[k]);
         pos[k] = s.pos[0];
+        pos1[k] = s.pos[1];
         good[k] = s.good;
       }
       p0 = __shfl_sync(0xFFFFFFFFu, pos[0], 0);
+      q1 = __shfl_sync(0xFFFFFFFFu, pos1[0], 0);
       c0 = __shfl_sync(0xFFFFFFFFu, cand[0], 0);
       m0 = __shfl_sync(0xFFFFFFFFu, meta[0], 0);
       j0 = __shfl_sync(0xFFFFFFFFu, job[0], 0);
@@ -1165,7 +1237,7 @@ __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevMode
     bool same = true;
 #pragma unroll
     for (int k = 0; k < kSliceLanes; ++k)
-      same = same && (!ok[k] || (pos[k] == p0 && cand[k] == c0 && meta[k] == m0 && job[k] == j0));
+      same = same && (!ok[k] || (pos[k] == p0 && pos1[k] == q1 && cand[k] == c0 && meta[k] == m0 && job[k] == j0));
     if (shared || __all_sync(0xFFFFFFFFu, same)) {
       int64_t* usum = jobs[j0].u_sum;
       int64_t* lsum = jobs[j0].l_sum;
@@ -1174,16 +1246,16 @@ __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevMode
       float u[kSliceLanes], v[kSliceLanes];
 #pragma unroll
       for (int k = 0; k < kSliceLanes; ++k) u[k] = v[k] = 0.0f;
-      if (!rs_terminal<1>(p0, 0u)) {
+      if (!rs_terminal<R>(p0, q1)) {
         if (depth + 1 >= M.D) {
           RSS s;
           s.pos[0] = p0;
-          s.pos[1] = 0u;
+          s.pos[1] = q1;
           const float tl = M.tail(s);
 #pragma unroll
           for (int k = 0; k < kSliceLanes; ++k) u[k] = tl;
         } else {
-          const float w = upper_term<1>(M, p0, 0u, lane);
+          const float w = upper_term<R>(M, p0, q1, lane);
           for (int i = 0; i < M.m; ++i) {
             const float wi = __shfl_sync(0xFFFFFFFFu, w, i);
 #pragma unroll
@@ -1191,12 +1263,15 @@ __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevMode
               if ((good[k] >> i) & 1u) u[k] = __fadd_rn(u[k], wi);
           }
 #pragma unroll
-          for (int k = 0; k < kSliceLanes; ++k) u[k] = upper_exits<1>(M, p0, 0u, u[k]);
+          for (int k = 0; k < kSliceLanes; ++k) u[k] = upper_exits<R>(M, p0, q1, u[k]);
         }
         int live = 0;
 #pragma unroll
         for (int k = 0; k < kSliceLanes; ++k) live += ok[k] ? 1 : 0;
-        M.rollout_oneK<kSliceLanes>(p0, good, c0, depth + 1, v, (unsigned long long)live, steps);
+        if constexpr (R == 1)
+          M.template rollout_oneK<kSliceLanes>(p0, good, c0, depth + 1, v, (unsigned long long)live, steps);
+        else
+          M.template rollout_twoK<kSliceLanes>(p0, q1, good, c0, depth + 1, v, (unsigned long long)live, steps);
       }
       long long fu = 0, fl = 0;
 #pragma unroll
@@ -1218,11 +1293,11 @@ __global__ void __launch_bounds__(512, 2) rs_rollout_slices_kernel(const DevMode
       if (32 * k >= cnt) break;
       RSS s;
       s.pos[0] = pos[k];
-      s.pos[1] = 0u;
+      s.pos[1] = pos1[k];
       s.good = good[k];
       s.sampled = 0u;
       s.scen = 0u;
-      rs_rollout_values<1>(M, jobs, ok[k], s, cand[k], meta[k], job[k], steps);
+      rs_rollout_values<R>(M, jobs, ok[k], s, cand[k], meta[k], job[k], steps);
     }
   }
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_down_sync(0xFFFFFFFFu, steps, o);
@@ -1416,7 +1491,7 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
   Items<R> items{blocks ? nullptr : item_buf, blocks ? 0 : total_items, policy != nullptr && R == 1};
   // slices: one robot's heuristic rollouts over the item list; phase A counts
   // them in counters[2]
-  if (R != 1 || blocks || policy != nullptr) sl = Slices{};
+  if (blocks || policy != nullptr) sl = Slices{};
   if (sl.list != nullptr) sl.count = counters + 2;
   // Each warp expands whole actions: as many warps as give every warp the
   // same number of a job's actions (20 actions: 10 warps of 2; 400: 16 of
@@ -1460,16 +1535,14 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
       return cudaGetLastError();
     }
   }
-  if constexpr (R == 1) {
-    if (sl.list != nullptr) {
-      const size_t kb = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words);
-      int per_sm = occupancy_cached(rs_rollout_slices_kernel, block_b, kb);
-      if (ctas_b > 0) per_sm = std::min(per_sm, ctas_b);
-      const long long want = ((long long)sl.cap + block_b / 32 - 1) / (block_b / 32);
-      const int grid = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm) * num_sms));
-      rs_rollout_slices_kernel<<<grid, block_b, kb, st>>>(gm, work, jobs, items, sl, counters + 1, plan_step);
-      return cudaGetLastError();
-    }
+  if (sl.list != nullptr) {
+    const size_t kb = rs_key_bytes_aligned(sizeof(uint16_t) * (size_t)key_words);
+    int per_sm = occupancy_cached(rs_rollout_slices_kernel<R>, block_b, kb);
+    if (ctas_b > 0) per_sm = std::min(per_sm, ctas_b);
+    const long long want = ((long long)sl.cap + block_b / 32 - 1) / (block_b / 32);
+    const int grid = (int)std::max(1LL, std::min<long long>(want, (long long)std::max(1, per_sm) * num_sms));
+    rs_rollout_slices_kernel<R><<<grid, block_b, kb, st>>>(gm, work, jobs, items, sl, counters + 1, plan_step);
+    return cudaGetLastError();
   }
   // phase B keeps the policy-key table in shared memory (limit set by rs_set_key_smem)
   const size_t key_bytes =
@@ -1766,11 +1839,14 @@ cudaError_t rs_set_key_smem(int robots, int key_words) {
     cudaError_t e = cudaFuncSetAttribute(rs_rollout_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)keys);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(rs_rollout_slices_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)keys);
+    e = cudaFuncSetAttribute(rs_rollout_slices_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)keys);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(rs_rollout_items_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(keys + rs_stage_bytes<1>(512)));
   }
+  cudaError_t e2 =
+      cudaFuncSetAttribute(rs_rollout_slices_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)keys);
+  if (e2 != cudaSuccess) return e2;
   return cudaFuncSetAttribute(rs_rollout_items_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)keys);
 }
 

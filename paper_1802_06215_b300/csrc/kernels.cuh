@@ -25,7 +25,8 @@ struct LeafBlocks {
 // list[2 i], list[2 i + 1] for i < *count, and phase B takes slices instead
 // of fixed chunks, so that the items it rolls out together always belong to
 // one child (one trajectory for all of them). A slice is (first item, count
-// | kSliceShared, position, candidate mask) (depth << 24 | slot, job, 0, 0).
+// | kSliceShared, robot 0's position, candidate mask) (depth << 24 | slot,
+// job, robot 1's position, 0).
 // With kSliceShared (a job whose scenarios share the robot's cell and
 // sampled mask) the child's items hold only their good masks and the slice
 // holds the rest; else the items hold every field. list == nullptr: chunks.
@@ -34,7 +35,8 @@ struct Slices {
   unsigned int* count = nullptr;
   unsigned int cap = 0;
 };
-constexpr int kSliceItems = 128;
+constexpr int kSliceItems = 128;    // one robot: four items a lane
+constexpr int kSliceItemsTwo = 64;  // two robots (longer rollouts, more state): two items a lane
 constexpr uint32_t kSliceShared = 1u << 31;
 
 // Rock Sample: words per rollout item of the two-phase expansion.

@@ -455,6 +455,94 @@ struct RSModel {
       y += ty > y ? 1 : -1;
   }
 
+  // heuristic_step2 for K scenarios of one child: the same moves and exits,
+  // each scenario's own reward at a Sample (added to r[k]), the rock cleared
+  // in every good mask.
+  template <int K>
+  __device__ __forceinline__ void heuristic_stepK(int& x, int& y, bool& ex, int tx, int ty, uint32_t& tbit,
+                                                  uint32_t (&good)[K], uint32_t& cand, int (&r)[K]) const {
+    if (ex) return;
+    if (tbit == 0) {
+      if (x == n - 1) {
+        ex = true;
+#pragma unroll
+        for (int k = 0; k < K; ++k) r[k] += 10;
+        return;
+      }
+      x += 1;
+      return;
+    }
+    if (x == tx && y == ty) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        r[k] += (good[k] & tbit) ? 10 : -10;
+        good[k] &= ~tbit;
+      }
+      cand &= ~tbit;
+      tbit = 0;
+      return;
+    }
+    if (x != tx)
+      x += tx > x ? 1 : -1;
+    else
+      y += ty > y ? 1 : -1;
+  }
+
+  // rollout_two for K scenarios of one child (rollout_two2's joint
+  // trajectory, each scenario's rewards added as rollout_two adds them, a
+  // zero reward skipped); steps_each scenarios' steps are counted.
+  template <int K>
+  __device__ __forceinline__ void rollout_twoK(uint32_t p0, uint32_t p1, const uint32_t (&good_in)[K], uint32_t cand,
+                                               int t0, float (&v)[K], unsigned long long steps_each,
+                                               unsigned long long& steps) const {
+    int x0 = (int)(p0 & 0xFFu), y0 = (int)((p0 >> 8) & 0xFFu);
+    int x1 = (int)(p1 & 0xFFu), y1 = (int)((p1 >> 8) & 0xFFu);
+    bool ex0 = (p0 >> 16) & 1u, ex1 = (p1 >> 16) & 1u;
+    int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0;
+    uint32_t tb0 = 0, tb1 = 0;
+    uint32_t good[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      good[k] = good_in[k];
+      v[k] = 0.0f;
+    }
+    int t = t0;
+    while (t < D && !(ex0 && ex1)) {
+      if (!ex0 && (tb0 & cand) == 0) {
+        tb0 = 0;
+        if (cand != 0) target(x0, y0, cand, tx0, ty0, tb0);
+      }
+      if (!ex1 && (tb1 & cand) == 0) {
+        tb1 = 0;
+        if (cand != 0) target(x1, y1, cand, tx1, ty1, tb1);
+      }
+      const int k = min(min(event_steps(x0, y0, ex0, tx0, ty0, tb0), event_steps(x1, y1, ex1, tx1, ty1, tb1)), D - t);
+      move_steps(x0, y0, ex0, tx0, ty0, tb0, k);
+      move_steps(x1, y1, ex1, tx1, ty1, tb1, k);
+      t += k;
+      if (t >= D) break;
+      int r[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) r[q] = 0;
+      heuristic_stepK<K>(x0, y0, ex0, tx0, ty0, tb0, good, cand, r);
+      heuristic_stepK<K>(x1, y1, ex1, tx1, ty1, tb1, good, cand, r);
+      const float g = sh->G[t - t0];
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (r[q] != 0) v[q] = __fadd_rn(v[q], __fmul_rn(g, (float)r[q]));
+      t += 1;
+    }
+    steps += steps_each * (unsigned long long)(t - t0);
+    if (!(ex0 && ex1)) {
+      float l = 0.0f;
+      if (!ex0) l = __fadd_rn(l, __fmul_rn(10.0f, sh->G[n - 1 - x0]));
+      if (!ex1) l = __fadd_rn(l, __fmul_rn(10.0f, sh->G[n - 1 - x1]));
+      const float tl = __fmul_rn(sh->G[D - t0], l);
+#pragma unroll
+      for (int q = 0; q < K; ++q) v[q] = __fadd_rn(v[q], tl);
+    }
+  }
+
   // rollout_two for two scenarios of one child: one joint trajectory (the
   // robots' moves read no rock state), each scenario's rewards at the event
   // steps added as rollout_two adds them (a zero reward skipped); both
