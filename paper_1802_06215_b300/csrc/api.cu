@@ -437,8 +437,7 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
       // an action's children (at most 6 observation codes) in runs of at
       // most kSliceItems
       if (plan.slices) {
-        // one robot: at most 6 observation codes an action, slices of 128;
-        // two robots: 18 codes, slices of 64
+        // one robot: at most 6 observation codes an action; two robots: 18
         const int len = h->robots == 1 ? kSliceItems : kSliceItemsTwo, codes = h->robots == 1 ? 6 : 18;
         plan.slice_cap += (long long)J.n_actions * ((J.n_scen + len - 1) / len + codes);
       }

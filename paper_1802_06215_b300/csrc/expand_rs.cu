@@ -1155,8 +1155,8 @@ __global__ void __launch_bounds__(512, 3) rs_rollout_items_kernel(const DevModel
 }
 
 // Phase B over slices (heuristic default policy): a warp takes one slice at
-// a time (claims in batches as for chunks), lane l its items l, l + 32, ...
-// (four a lane for one robot, two for two). A slice is one child's: the same
+// a time (claims in batches as for chunks), lane l its items l, l + 32,
+// l + 64 and l + 96. A slice is one child's: the same
 // slot and job, and in a job whose scenarios share the robots' cells (a tree
 // node's) the same positions and candidate set, which the slice then
 // carries (its items hold only their good masks). Then one trajectory

@@ -35,8 +35,8 @@ struct Slices {
   unsigned int* count = nullptr;
   unsigned int cap = 0;
 };
-constexpr int kSliceItems = 128;    // one robot: four items a lane
-constexpr int kSliceItemsTwo = 64;  // two robots (longer rollouts, more state): two items a lane
+constexpr int kSliceItems = 128;     // one robot: four items a lane
+constexpr int kSliceItemsTwo = 128;  // two robots: four items a lane as well (no spills at 56 registers)
 constexpr uint32_t kSliceShared = 1u << 31;
 
 // Rock Sample: words per rollout item of the two-phase expansion.
