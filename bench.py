@@ -292,17 +292,31 @@ def root_states(cfg, rng):
     return inputs.rs_block(cfg, cfg.K, rng, pos=pos)
 
 
-def planning_step(_dsp, m, cfg, plan):
+def planning_step(_dsp, m, cfg, plan, reps=5):
+    """`reps` planning steps from the benchmark's root belief, each on its own
+    random streams (plan step), with the WEU exit (xi = 0.95) and the time
+    limit: totals over the steps (a free-running search's tree, and so when
+    its exit rule ends it, varies with the threads' timing), the per-step
+    spread, and the first step's root bounds and action."""
     threads, seconds, use_queue = plan
     b = root_states(cfg, np.random.default_rng(99))
     p = _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=seconds, c_a=1.0, c_o=0.5, xi=0.95,
                                target_gap=0.0, deterministic=0, use_queue=use_queue)
-    g = _dsp.dsp_plan(m.h, b, None, p, m.num_actions)
+    rows = []
+    for r in range(reps):
+        _dsp.dsp_set_plan_step(m.h, 0x50000000 + r)
+        rows.append(_dsp.dsp_plan(m.h, b, None, p, m.num_actions))
+    _dsp.dsp_set_plan_step(m.h, 0)
+    g = rows[0]
+    exps = sum(x["expansions"] for x in rows)
+    secs = sum(x["seconds"] for x in rows)
+    rates = [x["expansions"] / x["seconds"] for x in rows]
     return {"root_u": g["root_u"], "root_l": g["root_l"], "root_gap": g["root_u"] - g["root_l"],
             "threads": threads, "planning_time_s": seconds, "through_queue": bool(use_queue),
-            "expansions": g["expansions"], "nodes": g["nodes"], "seconds": g["seconds"],
-            "expansions_per_s": g["expansions"] / g["seconds"],
-            "scenario_steps_per_s": g["scenario_steps"] / g["seconds"], "action": g["action"]}
+            "planning_steps": reps, "expansions": exps, "nodes": sum(x["nodes"] for x in rows), "seconds": secs,
+            "expansions_per_s": exps / secs,
+            "expansions_per_s_min": min(rates), "expansions_per_s_max": max(rates),
+            "scenario_steps_per_s": sum(x["scenario_steps"] for x in rows) / secs, "action": g["action"]}
 
 
 def learned_step(_dsp, batch, m, cfg, jobs, seconds, n_beliefs=32):
@@ -603,7 +617,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
     # step and keeps it, so the second step is what a replanning loop sees
     planning_queue = None
     if not args.no_plan and cfg.kind in (inputs.GRID, inputs.MULTIGRID) and not plan[2]:
-        first = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
+        first = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1), reps=1)
         planning_queue = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
         planning_queue["first_step_with_queue_creation"] = {k: first[k] for k in ("expansions", "seconds",
                                                                                    "expansions_per_s")}
