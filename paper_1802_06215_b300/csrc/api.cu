@@ -399,6 +399,7 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
   plan.unit_base.clear();
   plan.scen_base.clear();
   plan.total_items = plan.total_blocks = plan.total_scen = plan.slice_cap = 0;
+  plan.large_jobs = false;
   plan.blocks = allow_blocks && h->kind != DSP_MODEL_CAR && h->kind != DSP_MODEL_NAV && h->robots == 1 &&
                 !m->policy_on && m->tune_rs_form == 1;
   plan.slices = allow_blocks && (h->kind == DSP_MODEL_GRID || h->kind == DSP_MODEL_MULTIGRID) && !m->policy_on &&
@@ -410,6 +411,7 @@ dsp_status plan_units(const dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, 
       return fail(DSP_E_UNSUPPORTED, "job %d: n_scen=%d outside 1..%d", j, J.n_scen, max_n);
     if (J.n_scen > kMaxScen && J.leaf_states == nullptr)
       return fail(DSP_E_UNSUPPORTED, "job %d: more than %d scenarios need leaf_states", j, kMaxScen);
+    if (J.n_scen > kMaxScen) plan.large_jobs = true;
     if (J.n_actions < 1 || J.first_action < 0 || J.first_action + J.n_actions > h->num_actions)
       return fail(DSP_E_INVALID, "job %d: actions [%d,%d) outside 0..%d", j, J.first_action,
                   J.first_action + J.n_actions, h->num_actions);
@@ -631,7 +633,7 @@ dsp_status launch_expand(dsp_model* m, const dsp_leaf_job* jobs, int n_jobs, con
                            (const long long*)dunits, dorder, n_jobs,
                            plan.blocks ? plan.total_blocks : plan.total_items, items, counters, m->plan_step,
                            m->num_sms, block_b, m->policy_on ? m->policy : nullptr, st, m->tune_warps_a,
-                           m->tune_ctas_b, plan.blocks ? &lb : nullptr, slices ? &sl : nullptr);
+                           m->tune_ctas_b, plan.blocks ? &lb : nullptr, slices ? &sl : nullptr, plan.large_jobs);
     }
     if (m->timing) {
       cudaEventRecord(ev[1], st);

@@ -742,7 +742,9 @@ __device__ __forceinline__ void group_job(RSGroupSmem& S, const RSModel<R>& M, i
     rs2_group_job(S, M, j, ibase, a_begin, a_end, first, items, work, steps, sl);
 }
 
-template <int R>
+// kLarge: one-robot jobs above kMaxScen scenarios may occur (their path is
+// compiled in only then, so that the common path keeps its registers)
+template <int R, bool kLarge>
 __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __restrict__ gm, DevWork* work,
                                                              const dsp_leaf_job* __restrict__ jobs,
                                                              const long long* __restrict__ item_base,
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(kBlockA, 2) rs_group_kernel(const DevModel* __
     // both ways end at a barrier (group_job's last), so thread 0 may take the
     // next unit (the condition is the same for the whole CTA)
     if (a_begin < a_end)
-      group_job<R>(S, M, j, item_base != nullptr ? item_base[j] : 0, a_begin, a_end, S.part == 0, items, work,
+      group_job<R, kLarge>(S, M, j, item_base != nullptr ? item_base[j] : 0, a_begin, a_end, S.part == 0, items, work,
                    steps, lb, sl);
     else
       __syncthreads();
@@ -1484,7 +1486,7 @@ template <int R>
 cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words, DevWork* work, const dsp_leaf_job* jobs,
                              const long long* item_base, const int* order, int n_jobs, long long total_items, uint32_t* item_buf, unsigned int* counters,
                              uint32_t plan_step, int num_sms, int block_b, const void* policy, cudaStream_t st,
-                             int warps_a, int ctas_b, LeafBlocks lb, Slices sl) {
+                             int warps_a, int ctas_b, LeafBlocks lb, Slices sl, bool large_jobs) {
   // block form (lb.leaf set; one robot, heuristic policy): no item list,
   // total_items counts the 32-position blocks
   const bool blocks = lb.leaf != nullptr;
@@ -1510,14 +1512,22 @@ cudaError_t launch_two_phase(const DevModel* gm, int num_actions, int key_words,
     const int per_warp = narrow ? (na + 4) / 5 : (na + kWarpsA - 1) / kWarpsA;
     block_a = 32 * ((na + per_warp - 1) / per_warp);
   }
-  int per_sm_a = occupancy_cached(rs_group_kernel<R>, block_a, 0);
+  // (two robots have no large-job path)
+  constexpr bool kMayBeLarge = R == 1;
+  const bool large = kMayBeLarge && large_jobs;
+  int per_sm_a = large ? occupancy_cached(rs_group_kernel<R, kMayBeLarge>, block_a, 0)
+                       : occupancy_cached(rs_group_kernel<R, false>, block_a, 0);
   int grid_a = std::max(1, std::min(n_jobs, std::max(1, per_sm_a) * num_sms));
   // two robots: a job's hundreds of actions split over several CTAs (runs of
   // about 80), so that the largest jobs do not leave a tail
   const int splits = R == 2 ? std::max(1, num_actions / 80) : 1;
   grid_a = std::max(1, std::min(n_jobs * splits, std::max(1, per_sm_a) * num_sms));
-  rs_group_kernel<R><<<grid_a, block_a, 0, st>>>(gm, work, jobs, blocks ? nullptr : item_base, order, n_jobs,
-                                                  counters, plan_step, items, splits, lb, sl);
+  if (large)
+    rs_group_kernel<R, kMayBeLarge><<<grid_a, block_a, 0, st>>>(gm, work, jobs, blocks ? nullptr : item_base, order,
+                                                                n_jobs, counters, plan_step, items, splits, lb, sl);
+  else
+    rs_group_kernel<R, false><<<grid_a, block_a, 0, st>>>(gm, work, jobs, blocks ? nullptr : item_base, order,
+                                                          n_jobs, counters, plan_step, items, splits, lb, sl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (policy != nullptr && R == 1)
@@ -1854,15 +1864,16 @@ cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, in
                              const dsp_leaf_job* jobs, const long long* item_base, const int* order, int n_jobs,
                              long long total_items, uint32_t* item_buf, unsigned int* counters, uint32_t plan_step,
                              int num_sms, int block_b, const void* policy, cudaStream_t st, int warps_a, int ctas_b,
-                             const LeafBlocks* blocks, const Slices* slices) {
+                             const LeafBlocks* blocks, const Slices* slices, bool large_jobs) {
   const LeafBlocks lb = (blocks != nullptr && robots == 1 && policy == nullptr) ? *blocks : LeafBlocks{};
   if (blocks != nullptr && lb.leaf == nullptr) return cudaErrorInvalidValue;  // block form: one robot, heuristic
   const Slices sl = slices != nullptr ? *slices : Slices{};
   if (robots == 1)
     return launch_two_phase<1>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items,
-                               item_buf, counters, plan_step, num_sms, block_b, policy, st, warps_a, ctas_b, lb, sl);
+                               item_buf, counters, plan_step, num_sms, block_b, policy, st, warps_a, ctas_b, lb, sl,
+                               large_jobs);
   return launch_two_phase<2>(gm, num_actions, key_words, work, jobs, item_base, order, n_jobs, total_items, item_buf,
-                             counters, plan_step, num_sms, block_b, nullptr, st, warps_a, ctas_b, lb, sl);
+                             counters, plan_step, num_sms, block_b, nullptr, st, warps_a, ctas_b, lb, sl, false);
 }
 
 cudaError_t launch_rs_step(const DevModel* gm, int robots, const uint32_t* in, int in_cap, int count,
@@ -2023,9 +2034,12 @@ extern "C" dsp_status dsp_expand_leaves_noalloc(dsp_model* m, const dsp_leaf_job
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kNoAllocCounterBytes, st);
   if (e == cudaSuccess) {
     int block_b = m->tune_block > 0 ? m->tune_block : 256;
+    bool large = false;
+    for (int k = 0; k < n_jobs && !large; ++k) large = jobs[k].n_scen > kMaxScen;
     e = launch_rs_expand(m->dmodel, m->host->robots, m->host->num_actions, rs_key_words(m->host), m->dwork, djobs,
                          dbase, dorder, n_jobs, plan.total_items, items, counters, m->plan_step, m->num_sms,
-                         block_b, m->policy_on ? m->policy : nullptr, st, m->tune_warps_a, m->tune_ctas_b);
+                         block_b, m->policy_on ? m->policy : nullptr, st, m->tune_warps_a, m->tune_ctas_b, nullptr,
+                         nullptr, large);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dsp_expand_leaves_noalloc launch");
   return DSP_OK;

@@ -47,6 +47,7 @@ int rs_item_fields(int robots, bool full);  // words per rollout item (full: lea
 // policy: learned pi0 for the rollout phase (one robot), or null for the
 // heuristic policy.
 // order: phase A takes jobs in this order (null: index order).
+// large_jobs: some one-robot job may hold more than kMaxScen scenarios.
 // blocks: the block form (one robot, heuristic policy only): item_base and
 // item_buf are unused and total_items is the number of 32-position blocks.
 // Raises the rollout phase's dynamic shared-memory limit to hold the model's
@@ -58,7 +59,8 @@ cudaError_t launch_rs_expand(const DevModel* gm, int robots, int num_actions, in
                              long long total_items, uint32_t* item_buf,
                              unsigned int* counters, uint32_t plan_step, int num_sms, int block_b,
                              const void* policy, cudaStream_t st, int warps_a = 0, int ctas_b = 0,
-                             const LeafBlocks* blocks = nullptr, const Slices* slices = nullptr);
+                             const LeafBlocks* blocks = nullptr, const Slices* slices = nullptr,
+                             bool large_jobs = true);
 // Learned-policy rollout phase over the item list (one robot).
 cudaError_t launch_rs_rollout_mlp_items(const DevModel* gm, DevWork* work, const dsp_leaf_job* jobs,
                                         uint32_t* item_buf, long long total_items, unsigned int* counter,

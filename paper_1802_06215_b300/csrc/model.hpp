@@ -94,6 +94,7 @@ struct ExpandPlan {
   // takes each child's items in slices; at most slice_cap of them
   bool slices = false;
   long long slice_cap = 0;
+  bool large_jobs = false;  // a job holds more than kMaxScen scenarios
 };
 // allow_blocks: the block form or slices may be planned (dsp_expand_leaves,
 // which allocates their buffers); the no-allocation entry point and the
