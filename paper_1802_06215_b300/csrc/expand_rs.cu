@@ -12,16 +12,21 @@
 //     codes, in the warp's rows of shared tables).
 //  2. Number the children by first position (Eq. newnodes), then write the
 //     grouped positions and one rollout item per (action, scenario), in
-//     child-grouped order. Actions that draw no random numbers are re-applied;
-//     Sense leaves the state unchanged.
+//     child-grouped order, and list each child's items as slices of up to
+//     128. Actions that draw no random numbers are re-applied; Sense leaves
+//     the state unchanged. Where the job's scenarios share the robots' cells
+//     and sampled mask (a tree node's), a child's items share their state
+//     after the step: the slice holds it and an item only its good mask.
 // No barrier is needed inside a job. Phase A also writes the children's
 // counts, offsets, keys and reward sums.
 //
-// Phase B (rs_rollout_items_kernel): warps pull 32-item chunks of that list
-// (no barriers, full occupancy), compute u (Eq. ub) and the default-policy
-// rollout (Eq. lb) in registers, and add each run of same-child lanes to the
-// child's int64 fixed-point sums with one atomic (exact in any order). A
-// warp's lanes mostly share a child, so they branch alike.
+// Phase B (rs_rollout_slices_kernel): warps take slices (no barriers), four
+// items a lane, all one child's, so one trajectory of the default policy
+// (Eq. lb, whose moves read no rock state) gives every item's value, with
+// each item's own rewards; u (Eq. ub) comes from per-rock terms computed once
+// per slice, and the child's int64 fixed-point sums take one warp sum and one
+// reduction each (exact in any order). Without a slice list (the
+// no-allocation entry point) rs_rollout_items_kernel takes 32-item chunks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
