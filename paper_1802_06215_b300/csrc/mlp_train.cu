@@ -4,10 +4,10 @@
 // in tensor memory) with fused epilogues, softmax cross-entropy, column sums
 // for the bias gradients, and
 // Adam on FP32 master weights with BF16 copies for the next step. The labels
-// are the caller's: the shipped weights were trained on approximate
-// policy-iteration labels (the best allowed action by a leaf expansion's Q
-// estimate, else "defer" to the heuristic); planner imitation labels go
-// through the same step.
+// are the caller's: the shipped Rock Sample weights were trained first on
+// the plain planner's chosen actions (imitation, "defer" where it chose the
+// heuristic's action), then on approximate policy-iteration labels (the best
+// allowed action by a leaf expansion's Q estimate, else "defer").
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
