@@ -20,16 +20,17 @@ struct LeafBlocks {
   int* chunk_job = nullptr;
 };
 
-// Rock Sample, one robot, heuristic default policy, item list: phase A lists
-// each child's items as slices of at most kSliceItems consecutive items at
-// list[2 i], list[2 i + 1] for i < *count, and phase B takes slices instead
-// of fixed chunks, so that the items it rolls out together always belong to
-// one child (one trajectory for all of them). A slice is (first item, count
-// | kSliceShared, robot 0's position, candidate mask) (depth << 24 | slot,
-// job, robot 1's position, 0).
-// With kSliceShared (a job whose scenarios share the robot's cell and
+// Rock Sample (one or two robots), heuristic default policy, item list:
+// phase A lists each child's items as slices of at most kSliceItems
+// (kSliceItemsTwo) consecutive items at list[2 i], list[2 i + 1] for
+// i < *count, and phase B takes slices instead of fixed chunks, so that the
+// items it rolls out together always belong to one child (one trajectory for
+// all of them). A slice is (first item, count | kSliceShared, robot 0's
+// position, candidate mask) (depth << 24 | slot, job, robot 1's position, 0).
+// With kSliceShared (a job whose scenarios share the robots' cells and the
 // sampled mask) the child's items hold only their good masks and the slice
-// holds the rest; else the items hold every field. list == nullptr: chunks.
+// holds the rest; else the items hold every field and the slice's position
+// and candidate words are unused. list == nullptr: chunks.
 struct Slices {
   uint4* list = nullptr;
   unsigned int* count = nullptr;
