@@ -380,3 +380,42 @@ def test_expand_parity_two_robots_shared_cells(dsp):
         total += o["steps"]
     assert steps == total
     m.close()
+
+
+@pytest.mark.parametrize("name", ["rs15_15", "mars15_15"])
+def test_expand_parity_slice_boundaries(dsp, name):
+    """Children of 1, 127, 128, 129, 256, 257 and 500 items: the rollout
+    phase takes each child's items in slices of up to 128 (a move gives every
+    scenario of a shared-position job one child of n items), so these sizes
+    put a child's last slice at one item, a full slice and one past it; with
+    a leaf of mixed positions beside them (items that take the per-item
+    path). All match the oracle."""
+    cfg = CONFIGS[name]()
+    m = dsp.Model(cfg)
+    om = oracle.Model(cfg)
+    rng = np.random.default_rng(41)
+    robots = 2 if name.startswith("mars") else 1
+    jobs = []
+    for k, n in enumerate([1, 127, 128, 129, 256, 257, 500]):
+        pos = [(int(rng.integers(0, cfg.n - 1)), int(rng.integers(0, cfg.n))) for _ in range(robots)]
+        pb = I.rs_block(cfg, n, rng, pos=pos, sampled=int(1 << (k % cfg.m)))
+        depth = k % 4
+        jobs.append(I.Job(parent=pb, idx=np.arange(n, dtype=np.uint16), last_action=-1, depth=depth,
+                          hist=I.random_hist(cfg, rng, depth), first_action=0, n_actions=m.num_actions))
+    pb = I.rs_block(cfg, 300, rng)  # per-scenario positions
+    jobs.append(I.Job(parent=pb, idx=np.arange(300, dtype=np.uint16), last_action=-1, depth=1,
+                      hist=I.random_hist(cfg, rng, 1), first_action=0, n_actions=m.num_actions))
+    jb = dsp.JobBatch(m, jobs)
+    m.reset_counters()
+    jb.run()
+    steps, status = m.counters()
+    assert status == 0
+    res = jb.all_results()
+    total = 0
+    for k, j in enumerate(jobs):
+        o = om.expand(j.parent, j.idx, j.last_action, j.depth, j.hist, a0=j.first_action, na=j.n_actions,
+                      cap=m.max_children(len(j.idx)))
+        _cmp_expand(res[k], o, len(j.idx), f"{name} job {k}")
+        total += o["steps"]
+    assert steps == total
+    m.close()
