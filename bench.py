@@ -105,7 +105,8 @@ def parse():
     p.add_argument("--e2e-lanes", type=int, default=E2E_LANES,
                    help="job arenas (and streams) taking the end-to-end steps in turn")
     p.add_argument("--no-companions", action="store_true",
-                   help="measure only --workload (a default rs15_15 run also measures car50 under its own key)")
+                   help="measure only --workload (a default rs15_15 run also measures car50 and mars15_15, "
+                        "each under its own key)")
     p.add_argument("--episodes", type=int, default=0,
                    help="run planner episodes on this many held-out Rock Sample 15x15 worlds (heuristic and learned "
                         "default policy) and exit")
@@ -707,7 +708,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
 
 # Workloads measured beside the headline one in a default run (the driving
 # task among 50 pedestrians beside Rock Sample 15x15), each under its own key.
-COMPANIONS = {"rs15_15": ["car50"]}
+COMPANIONS = {"rs15_15": ["car50", "mars15_15"]}
 
 
 def run_ours(args, rank, world):
