@@ -93,10 +93,23 @@ void wr(std::atomic<T>& x, T v) {
 }
 
 struct Node;
+// An action's children: consecutive nodes of their expansion's node array.
+struct Children {
+  Node* first = nullptr;
+  int n = 0;
+  struct It {
+    Node* p;
+    Node* operator*() const { return p; }
+    It& operator++();
+    bool operator!=(const It& o) const { return p != o.p; }
+  };
+  It begin() const;
+  It end() const;
+};
 struct QBranch {
   double R = 0;                 // set before the node is published
   std::atomic<double> U{0.0}, L{0.0};
-  std::vector<Node*> ch;        // set before the node is published, then read-only
+  Children ch;                  // set before the node is published, then read-only
 };
 struct Node {
   int depth = 0, n = 0;
@@ -119,6 +132,12 @@ struct Node {
   std::unique_ptr<QBranch[]> q;
   int nq = 0;
 };
+inline Children::It& Children::It::operator++() {
+  ++p;
+  return *this;
+}
+inline Children::It Children::begin() const { return It{first}; }
+inline Children::It Children::end() const { return It{first + n}; }
 
 // Pinned host buffer of one search thread, grown on demand.
 struct Pinned {
@@ -215,20 +234,18 @@ class Search {
     long long epoch = 0;  // leaves published when the trial was selected
   };
 
-  Node* new_node() {
+  // count new nodes, one array allocated outside the pool lock, listed in
+  // creation order under one acquisition of it
+  Node* new_nodes(int count) {
+    if (count <= 0) return nullptr;
+    std::unique_ptr<Node[]> blk(new Node[count]);
+    Node* p = blk.get();
     std::lock_guard<std::mutex> lock(pool_mu_);
-    pool_.emplace_back(new Node());
-    return pool_.back().get();
+    blocks_.push_back(std::move(blk));
+    for (int k = 0; k < count; ++k) pool_.push_back(p + k);
+    return p;
   }
-  // count new nodes in creation order under one acquisition of the pool lock
-  void new_nodes(int count, std::vector<Node*>& out) {
-    out.clear();
-    std::lock_guard<std::mutex> lock(pool_mu_);
-    for (int k = 0; k < count; ++k) {
-      pool_.emplace_back(new Node());
-      out.push_back(pool_.back().get());
-    }
-  }
+  Node* new_node() { return new_nodes(1); }
 
   void observe(int8_t* h, int a, uint64_t key) const { host_observe(kind_, per_, h, a, key); }
 
@@ -356,7 +373,7 @@ class Search {
   // interleaved backups may have left a node an older (looser) bound.
   void settle() {
     for (auto it = pool_.rbegin(); it != pool_.rend(); ++it) {
-      Node* b = it->get();
+      Node* b = *it;
       if (!b->expanded.load(std::memory_order_acquire)) continue;
       for (int a = 0; a < b->nq; ++a) refresh_action(b, a);
       refresh(b);
@@ -437,8 +454,7 @@ class Search {
     const int cap = jo.cap, n = b->n;
     int total = 0;
     for (int a = 0; a < na_; ++a) total += std::min(cnt[a], cap);
-    std::vector<Node*> made;
-    new_nodes(total, made);
+    Node* made = new_nodes(total);
     int next = 0;
     for (int a = 0; a < na_; ++a) {
       QBranch& q = b->q[a];
@@ -447,8 +463,10 @@ class Search {
       for (int c = 0; c < nc; ++c) rsum += rew[(size_t)a * cap + c];
       q.R = ((double)rsum / 4294967296.0) / K_;
       double su = 0, sl = 0;
+      q.ch.first = made + next;
+      q.ch.n = nc;
       for (int c = 0; c < nc; ++c) {
-        Node* ch = made[next++];
+        Node* ch = made + next++;
         int o0 = off[(size_t)a * (cap + 1) + c], o1 = off[(size_t)a * (cap + 1) + c + 1];
         ch->depth = b->depth + 1;
         ch->n = o1 - o0;
@@ -464,7 +482,6 @@ class Search {
         const double cl = ((double)ls[(size_t)a * cap + c] / 4294967296.0) / K_;
         wr(ch->U, cu);
         wr(ch->L, cl);
-        q.ch.push_back(ch);
         su += cu;
         sl += cl;
       }
@@ -601,7 +618,8 @@ class Search {
   int na_, D_, words_, kind_, per_;
   double K_, gamma_;
   std::vector<std::unique_ptr<Arena>> arenas_;  // per model: the tree's device memory on its GPU
-  std::vector<std::unique_ptr<Node>> pool_;
+  std::vector<Node*> pool_;                      // every node, in creation order
+  std::vector<std::unique_ptr<Node[]>> blocks_;  // the nodes' storage, one array per expansion
   Node* root_ = nullptr;
   std::vector<uint16_t*> ident_;                // per model: positions 0..n-1 of the root's scenarios
   std::atomic<long long> routed_{0};            // expansions routed so far
@@ -864,8 +882,7 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
     }
   out->action = best;
   uint64_t sig = 0x12345678ull;
-  for (auto& up : pool_) {
-    Node* v = up.get();
+  for (Node* v : pool_) {
     uint64_t ub, lb;
     const double vu = ld(v->U), vlo = ld(v->L);
     std::memcpy(&ub, &vu, 8);
@@ -886,9 +903,8 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
 dsp_status Search::export_nodes(int min_scen, int cap, dsp_plan_node* nodes, uint32_t* states, int32_t* count) {
   int k = 0;
   std::vector<uint32_t> one(words_);
-  for (auto& up : pool_) {
+  for (const Node* v : pool_) {
     if (k >= cap) break;
-    const Node* v = up.get();
     if (!v->expanded.load() || v->term || v->n < min_scen || v->d_states == nullptr) continue;
     dsp_plan_node& o = nodes[k];
     o.depth = v->depth;
