@@ -241,9 +241,15 @@ class Search {
     std::unique_ptr<Node[]> blk(new Node[count]);
     Node* p = blk.get();
     std::lock_guard<std::mutex> lock(pool_mu_);
-    blocks_.push_back(std::move(blk));
-    for (int k = 0; k < count; ++k) pool_.push_back(p + k);
+    blocks_.push_back({std::move(blk), count});
+    n_nodes_ += count;
     return p;
+  }
+  // every node in creation order (after the search threads have joined)
+  template <class F>
+  void for_each_node(F&& f) const {
+    for (const NodeBlock& b : blocks_)
+      for (int k = 0; k < b.n; ++k) f(b.p.get() + k);
   }
   Node* new_node() { return new_nodes(1); }
 
@@ -372,12 +378,13 @@ class Search {
   // (a node is created after its parent): after lock-free threads, whose
   // interleaved backups may have left a node an older (looser) bound.
   void settle() {
-    for (auto it = pool_.rbegin(); it != pool_.rend(); ++it) {
-      Node* b = *it;
-      if (!b->expanded.load(std::memory_order_acquire)) continue;
-      for (int a = 0; a < b->nq; ++a) refresh_action(b, a);
-      refresh(b);
-    }
+    for (auto it = blocks_.rbegin(); it != blocks_.rend(); ++it)
+      for (int k = it->n - 1; k >= 0; --k) {
+        Node* b = it->p.get() + k;
+        if (!b->expanded.load(std::memory_order_acquire)) continue;
+        for (int a = 0; a < b->nq; ++a) refresh_action(b, a);
+        refresh(b);
+      }
   }
 
   // Device buffers and the job descriptor of one leaf on model g (caller
@@ -618,8 +625,12 @@ class Search {
   int na_, D_, words_, kind_, per_;
   double K_, gamma_;
   std::vector<std::unique_ptr<Arena>> arenas_;  // per model: the tree's device memory on its GPU
-  std::vector<Node*> pool_;                      // every node, in creation order
-  std::vector<std::unique_ptr<Node[]>> blocks_;  // the nodes' storage, one array per expansion
+  struct NodeBlock {
+    std::unique_ptr<Node[]> p;
+    int n;
+  };
+  std::vector<NodeBlock> blocks_;  // every node, one array per expansion, in creation order
+  long long n_nodes_ = 0;
   Node* root_ = nullptr;
   std::vector<uint16_t*> ident_;                // per model: positions 0..n-1 of the root's scenarios
   std::atomic<long long> routed_{0};            // expansions routed so far
@@ -869,7 +880,7 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
   if (status != 0) return fail(DSP_E_DEVICE, "dsp_plan: device status word %u", status);
   out->root_u = ld(root_->U);
   out->root_l = ld(root_->L);
-  out->nodes = (int32_t)pool_.size();
+  out->nodes = (int32_t)n_nodes_;
   out->expansions = expansions_.load();
   out->rounds = rounds_;
   out->scenario_steps = steps1 - steps0;
@@ -882,7 +893,7 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
     }
   out->action = best;
   uint64_t sig = 0x12345678ull;
-  for (Node* v : pool_) {
+  for_each_node([&](const Node* v) {
     uint64_t ub, lb;
     const double vu = ld(v->U), vlo = ld(v->L);
     std::memcpy(&ub, &vu, 8);
@@ -890,7 +901,7 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
     sig = mix64(sig ^ (uint64_t)v->depth) ^ v->key;
     sig = mix64(sig ^ ub) ^ lb;
     sig = mix64(sig ^ (uint64_t)v->n ^ ((uint64_t)ld(v->N) << 32));
-  }
+  });
   out->signature = sig;
   if (visits)
     for (int a = 0; a < root_->nq; ++a) visits[a] = (int32_t)ld(root_->Na[a]);
@@ -903,26 +914,29 @@ dsp_status Search::run(const uint32_t* root_host, int n, const int8_t* hist, dsp
 dsp_status Search::export_nodes(int min_scen, int cap, dsp_plan_node* nodes, uint32_t* states, int32_t* count) {
   int k = 0;
   std::vector<uint32_t> one(words_);
-  for (const Node* v : pool_) {
-    if (k >= cap) break;
-    if (!v->expanded.load() || v->term || v->n < min_scen || v->d_states == nullptr) continue;
-    dsp_plan_node& o = nodes[k];
-    o.depth = v->depth;
-    o.n = v->n;
-    o.visits = (int32_t)ld(v->N);
-    o.U = ld(v->U);
-    o.L = ld(v->L);
-    std::memcpy(o.hist, v->hist, 32);
-    int best = 0;
-    for (int a = 1; a < v->nq; ++a)
-      if (ld(v->q[a].L) > ld(v->q[best].L)) best = a;
-    o.action = best;
-    if (states) {
-      cudaError_t e = cudaMemcpy2D(one.data(), 4, v->d_states, (size_t)v->n * 4, 4, words_, cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) return cuda_fail(e, "dsp_plan_nodes: node state");
-      for (int w = 0; w < words_; ++w) states[(size_t)w * cap + k] = one[w];
+  for (size_t bi = 0; bi < blocks_.size() && k < cap; ++bi) {
+    for (int bk = 0; bk < blocks_[bi].n && k < cap; ++bk) {
+      const Node* v = blocks_[bi].p.get() + bk;
+      if (!v->expanded.load() || v->term || v->n < min_scen || v->d_states == nullptr) continue;
+      dsp_plan_node& o = nodes[k];
+      o.depth = v->depth;
+      o.n = v->n;
+      o.visits = (int32_t)ld(v->N);
+      o.U = ld(v->U);
+      o.L = ld(v->L);
+      std::memcpy(o.hist, v->hist, 32);
+      int best = 0;
+      for (int a = 1; a < v->nq; ++a)
+        if (ld(v->q[a].L) > ld(v->q[best].L)) best = a;
+      o.action = best;
+      if (states) {
+        cudaError_t e =
+            cudaMemcpy2D(one.data(), 4, v->d_states, (size_t)v->n * 4, 4, words_, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "dsp_plan_nodes: node state");
+        for (int w = 0; w < words_; ++w) states[(size_t)w * cap + k] = one[w];
+      }
+      ++k;
     }
-    ++k;
   }
   *count = k;
   return DSP_OK;
