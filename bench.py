@@ -293,7 +293,7 @@ def root_states(cfg, rng):
     return inputs.rs_block(cfg, cfg.K, rng, pos=pos)
 
 
-def planning_step(_dsp, m, cfg, plan, reps=5):
+def planning_step(_dsp, m, cfg, plan, reps=5, batch=0):
     """`reps` planning steps from the benchmark's root belief, each on its own
     random streams (plan step), with the WEU exit (xi = 0.95) and the time
     limit: totals over the steps (a free-running search's tree, and so when
@@ -302,7 +302,7 @@ def planning_step(_dsp, m, cfg, plan, reps=5):
     threads, seconds, use_queue = plan
     b = root_states(cfg, np.random.default_rng(99))
     p = _dsp.dsp_search_params(threads=threads, rounds=10 ** 7, time_limit_s=seconds, c_a=1.0, c_o=0.5, xi=0.95,
-                               target_gap=0.0, deterministic=0, use_queue=use_queue)
+                               target_gap=0.0, deterministic=0, use_queue=use_queue, batch=batch)
     rows = []
     for r in range(reps):
         _dsp.dsp_set_plan_step(m.h, 0x50000000 + r)
@@ -314,6 +314,7 @@ def planning_step(_dsp, m, cfg, plan, reps=5):
     rates = [x["expansions"] / x["seconds"] for x in rows]
     return {"root_u": g["root_u"], "root_l": g["root_l"], "root_gap": g["root_u"] - g["root_l"],
             "threads": threads, "planning_time_s": seconds, "through_queue": bool(use_queue),
+            "batched_launches_of": batch if batch > 1 else None,
             "planning_steps": reps, "expansions": exps, "nodes": sum(x["nodes"] for x in rows), "seconds": secs,
             "expansions_per_s": exps / secs,
             "expansions_per_s_min": min(rates), "expansions_per_s_max": max(rates),
@@ -626,7 +627,11 @@ def measure(args, name, rank, world, dist, local, headline=True):
     # the model creates its queue (and the kernel's graph) on the first such
     # step and keeps it, so the second step is what a replanning loop sees
     planning_queue = None
+    planning_batched = None
     if not args.no_plan and cfg.kind in (inputs.GRID, inputs.MULTIGRID) and not plan[2]:
+        # the threads' claimed leaves handed to one dispatcher that expands up
+        # to 64 of them per dsp_expand_leaves call
+        planning_batched = planning_step(_dsp, m, cfg, plan, batch=64)
         first = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1), reps=1)
         planning_queue = planning_step(_dsp, m, cfg, (plan[0], plan[1], 1))
         planning_queue["first_step_with_queue_creation"] = {k: first[k] for k in ("expansions", "seconds",
@@ -705,6 +710,7 @@ def measure(args, name, rank, world, dist, local, headline=True):
         "roofline": roof,
         "cpu_baseline": cpu,
         "planning": planning,
+        "planning_batched": planning_batched,
         "planning_queue": planning_queue,
         "planning_episodes": planning_episodes,
         "autotune": autotuned,
