@@ -159,9 +159,12 @@ typedef struct {
  * fixed point 2^-32. Validation failures return DSP_E_INVALID and launch
  * nothing; n_actions * child_cap >= 2^24 in a job, or more than 2^31
  * (action, scenario) pairs in the call, returns DSP_E_UNSUPPORTED. Asynchronous
- * on `stream`. Work buffers (job table, rollout-item list, about 28 B per
- * (action, scenario) for one robot, 52 B for navigation) come from a memory
- * pool the model owns; the pool keeps its largest size mapped until
+ * on `stream`. Work buffers come from a memory pool the model owns: the job
+ * table, the rollout-item list (Rock Sample: 20 B per (action, scenario) for
+ * one robot, 24 B for two, 28 B and 32 B with a learned policy; navigation
+ * 52 B) and, for Rock Sample's heuristic rollouts, the list of each child's
+ * slices (32 B a slice, at most ceil(n_scen / 128) + 6 slices an action for
+ * one robot, + 18 for two). The pool keeps its largest size mapped until
  * dsp_destroy_model, so repeated calls do not map memory again. */
 dsp_status dsp_expand_leaves(dsp_model* model, const dsp_leaf_job* jobs, int32_t n_jobs, void* stream);
 
